@@ -1,0 +1,106 @@
+"""DM Monte Carlo scattering (oracle, FP64).
+
+Eq. dm-update-vels: the new velocity distribution of DM particle i is
+    nu_i' = (1 - sum_j P_ij) delta(v - v_i) + sum_j P_ij delta(v - S_chi(v_i, v^B_ij, Omega_ij))
+Eq. dm-update-prob:  P_ij = (M_j / mu_j) g_ij sigma(v_rel) v_rel dt,  v_rel = |v_i - v^B_ij|
+with v^B_ij one sample of the gas Maxwellian G(v - V_j, T_j/mu_j) per pair, and
+Eq. scatter_chi:     S_chi = v_i + mu_j/(m_chi + mu_j) v_rel (n' - n),  n = (v_i - v^B)/v_rel,
+n' isotropic (Sec. 2.4: isotropic power-law cross section).
+
+Readings (the paper leaves these open):
+  * one categorical draw per DM particle per step (the derivation's form); partners
+    in ascending gas id; running sums C_k = sum_{j<=k} P_ij; with r_i the DM
+    stream's uniform the particle scatters off the first k with r_i < C_k.
+  * if C_last > 1 the categorical is renormalised by C_last (the particle scatters
+    surely, threshold r_i C_last) and the event is counted as a clamp.
+  * Eq. prob_criterion: the output p_ratio_max_i = max_j P_ij / min(0.1,
+    1e-4 ((m_chi + mu_j)/mu_j)^2) tells the caller when dt must shrink.
+  * random numbers: oracle/philox.py stream layout.
+
+Parity: pinned through its parts and through the statistical equivalence with
+the expectation values of App. C (tests/test_oracle_mc.py).
+"""
+import numpy as np
+
+from . import units
+from .kernel import overlap_g_vec
+from .meanfield import pair_geometry
+from .philox import dm_uniforms, pair_normals
+
+NO_PARTNER = 0xFFFFFFFF
+
+
+def pcap(m_chi, mu):
+    """Right-hand side of Eq. prob_criterion."""
+    return np.minimum(0.1, 1e-4 * ((m_chi + mu) / mu) ** 2)
+
+
+def pair_probabilities(dm, gas, pi, pj, params, step, dt, g=None):
+    """Per-pair (P_ij, v^B_ij, v_rel) with the pair's own Philox stream."""
+    if g is None:
+        d = pair_geometry(dm, gas, pi, pj, params["periodic"], params["box"])
+        g = overlap_g_vec(d, dm["h"][pi], gas["h"][pj])
+    z = pair_normals(params["seed"], step, dm["id"][pi].astype(np.uint64), gas["id"][pj].astype(np.uint64))
+    s = np.sqrt(units.varsigma2_kms2(gas["T"][pj], gas["mu"][pj]))
+    vB = gas["vel"][pj] + s[:, None] * z
+    rel = dm["vel"][pi] - vB
+    vrel = np.sqrt(np.sum(rel * rel, axis=1))
+    sig = units.sigma_kpc2(params["sigma0_cm2"]) * (vrel / params["v0_kms"]) ** params["n"]
+    nB = gas["mass"][pj] * units.MSUN_PER_MP / gas["mu"][pj]
+    P = nB * g * sig * vrel * dt
+    return P, vB, vrel
+
+
+def mc_scatter(dm, gas, pi, pj, params, step, dt, g=None):
+    """Return a dict with vel_new[N_chi,3], scattered, partner (gas id), p_ratio_max,
+    C_total, r, clamped, and for diagnostics the running-sum gap to r."""
+    m_chi = params["m_chi_mp"]
+    nd = len(dm["h"])
+    P, vB, vrel = pair_probabilities(dm, gas, pi, pj, params, step, dt, g)
+    r, cth, phi = dm_uniforms(params["seed"], step, dm["id"].astype(np.uint64))
+    ratio = P / pcap(m_chi, gas["mu"][pj])
+    p_ratio_max = np.zeros(nd)
+    np.maximum.at(p_ratio_max, pi, ratio)
+
+    order = np.lexsort((gas["id"][pj], pi))  # per DM, ascending gas id
+    vel_new = dm["vel"].copy()
+    scattered = np.zeros(nd, dtype=bool)
+    partner = np.full(nd, NO_PARTNER, dtype=np.uint64)
+    C_total = np.zeros(nd)
+    clamped = np.zeros(nd, dtype=bool)
+    gap = np.full(nd, np.inf)   # min_k |threshold - C_k| / C_k, for the boundary band
+    starts = np.searchsorted(pi[order], np.arange(nd), side="left")
+    ends = np.searchsorted(pi[order], np.arange(nd), side="right")
+    for i in np.unique(pi):
+        seg = order[starts[i]:ends[i]]
+        C = np.cumsum(P[seg])                # sequential FP64 running sum
+        C_total[i] = C[-1]
+        thr = r[i]
+        if C[-1] > 1.0:
+            clamped[i] = True
+            thr = r[i] * C[-1]
+        gap[i] = np.min(np.abs(thr - C) / C)
+        k = int(np.searchsorted(C, thr, side="right"))   # first k with thr < C_k
+        if k >= seg.size:
+            continue
+        e = seg[k]
+        j = pj[e]
+        mu = gas["mu"][j]
+        n_old = (dm["vel"][i] - vB[e]) / vrel[e]
+        sth = np.sqrt(max(0.0, 1.0 - cth[i] * cth[i]))
+        n_new = np.array([sth * np.cos(phi[i]), sth * np.sin(phi[i]), cth[i]])
+        vel_new[i] = dm["vel"][i] + mu / (m_chi + mu) * vrel[e] * (n_new - n_old)
+        scattered[i] = True
+        partner[i] = gas["id"][j]
+    return dict(vel_new=vel_new, scattered=scattered, partner=partner, p_ratio_max=p_ratio_max,
+                C_total=C_total, r=r, clamped=clamped, gap=gap, P=P, vB=vB, vrel=vrel)
+
+
+def scatter_pair(v_chi, v_B, m_chi, m_B, n_new):
+    """Eqs. scatter_chi and scatter_B for one collision (used by the conservation pin)."""
+    rel = v_chi - v_B
+    vrel = np.linalg.norm(rel)
+    n_old = rel / vrel
+    vc = v_chi + m_B / (m_chi + m_B) * vrel * (n_new - n_old)
+    vb = v_B - m_chi / (m_chi + m_B) * vrel * (n_new - n_old)
+    return vc, vb
