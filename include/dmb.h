@@ -1,0 +1,170 @@
+/*
+ * dmb.h -- C ABI of the GB300 library for the data-parallel hot path of the
+ * hybrid dark matter-baryon interaction step of Hainje & Farrar (arXiv 2603.24688).
+ *
+ * The step (Sec. 2.4, "GIZMO implementation") has three parts:
+ *   1. the cross-species pair set {(i, j): |x_i - x_j| < h_i + h_j} (i: DM, j: gas),
+ *      the pairs whose overlap integral g_ij (Eq. dm-update-prob, App. D) is non-zero;
+ *   2. the mean-field acceleration and heating of every gas particle
+ *      (Eqs. gas-dVdt and gas-dTdt, with A and B of Eqs. scrA/scrB, App. B);
+ *   3. one Monte Carlo scattering draw per DM particle (Eqs. dm-update-vels,
+ *      dm-update-prob, scatter_chi; timestep criterion Eq. prob_criterion).
+ *
+ * Units: lengths kpc, velocities km/s, masses Msun, time kpc/(km/s), temperatures K.
+ * Particle masses m_chi and mu_j are in units of the proton mass.  The cross section
+ * is sigma(v) = sigma0 (v / v0)^n, isotropic (sigma = momentum-transfer sigma_bar).
+ *
+ * Conventions for every entry point:
+ *   - array arguments marked "device" are CUDA device pointers owned by the caller;
+ *     "host" pointers are ordinary host memory owned by the caller;
+ *   - the context owns all scratch (sorted copies, spatial tree, pair lists, overlap
+ *     table) and frees it in dmb_destroy;
+ *   - work is enqueued on the context's stream; calls that return host values
+ *     (n_pairs, sums) synchronise that stream, the others return immediately;
+ *   - results are written in the caller's input order (never in the internal sorted
+ *     order) and depend only on particle ids, not on that order;
+ *   - on failure a call returns a non-zero dmb_status and dmb_last_error() describes
+ *     it; the library never exits or aborts.
+ */
+#ifndef DMB_H
+#define DMB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DMB_OK = 0,
+  DMB_ERR_ARG = 1,      /* invalid argument or input value (h <= 0, NaN, T < 0, ...) */
+  DMB_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+  DMB_ERR_OOM = 3,      /* device allocation failed */
+  DMB_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+  DMB_ERR_DOMAIN = 5,   /* input outside what the selected rate provider covers */
+  DMB_ERR_STATE = 6     /* calls made in the wrong order (e.g. neighbours before grid) */
+} dmb_status;
+
+typedef enum {
+  DMB_RATE_CLOSED = 0,  /* App. B closed forms via 1F1 (integer n >= -4, n != -3) */
+  DMB_RATE_QUAD = 1,    /* Gauss-Laguerre/Hermite quadrature of Eqs. scrA/scrB */
+  DMB_RATE_MLP = 2      /* learned surrogate of the rate integrals */
+} dmb_rate_mode;
+
+/* Physical and numerical parameters (Sec. 2.4; Table test_params for typical values). */
+typedef struct {
+  double sigma0_cm2;    /* sigma0 in cm^2 */
+  double v0_kms;        /* reference speed of the power law, km/s (> 0) */
+  int32_t n;            /* power-law index, n >= -4 */
+  int32_t periodic;     /* 1: periodic box [0, box)^3 with minimum-image pairs */
+  double m_chi_mp;      /* DM particle mass in m_p (> 0) */
+  double box[3];        /* periodic box sides in kpc (used when periodic = 1) */
+  int32_t rate_mode;    /* dmb_rate_mode */
+  int32_t fp64;         /* 1: all pair arithmetic in float64 (slow on GB300); 0: float32 */
+  uint64_t seed;        /* key of the Philox4x32-10 streams */
+} dmb_params;
+
+/* DM particles (Eq. macroparticle-DF_DM): M_i, x_i, h_i, v_i.  All device pointers. */
+typedef struct {
+  int64_t n;
+  const double *pos;    /* [n][3] kpc */
+  const double *vel;    /* [n][3] km/s */
+  const double *mass;   /* [n] Msun */
+  const double *h;      /* [n] kernel-support length, kpc (> 0) */
+  const uint32_t *id;   /* [n] stable ids, unique within the species; key the RNG */
+} dmb_dm;
+
+/* Gas particles (Eq. macroparticle-DF_B): M_j, x_j, h_j, V_j, T_j, mu_j.  Device pointers. */
+typedef struct {
+  int64_t n;
+  const double *pos;    /* [n][3] kpc */
+  const double *vel;    /* [n][3] bulk velocity, km/s */
+  const double *mass;   /* [n] Msun */
+  const double *h;      /* [n] kpc (> 0) */
+  const double *T;      /* [n] temperature, K (>= 0) */
+  const double *mu;     /* [n] mean molecular mass in m_p (> 0) */
+  const uint32_t *id;   /* [n] stable ids, unique within the species */
+} dmb_gas;
+
+typedef struct dmb_ctx dmb_ctx;
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL: the
+ * legacy default stream).  Validates the parameters, builds the overlap table
+ * (App. D) on the device.  *out is NULL on failure. */
+dmb_status dmb_create(dmb_ctx **out, const dmb_params *p, void *cuda_stream);
+
+/* Free every device buffer of the context.  NULL is accepted. */
+dmb_status dmb_destroy(dmb_ctx *ctx);
+
+/* Text of the last error of this context (or of the last failed dmb_create when ctx
+ * is NULL).  Valid until the next call on the context. */
+const char *dmb_last_error(const dmb_ctx *ctx);
+
+/* Spatial index (the pair search of Sec. 2.4 on a Morton-sorted grid): Morton keys of
+ * both species over one shared frame, LSD radix sort, sorted float copies, and a
+ * bounding-volume tree over chunks of 32 sorted particles with per-node h_max.
+ * Reads positions, velocities, masses, h, T, mu and ids; copies what it needs, so the
+ * caller may change its arrays afterwards.  Inputs are checked on the device
+ * (finite values, h > 0, M > 0, T >= 0, mu > 0; periodic: h_i + h_j < box/2). */
+dmb_status dmb_build_grid(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas);
+
+/* Pair set {(i, j): d_ij < h_i + h_j} (strict; minimum image when periodic) from the
+ * grid of the last dmb_build_grid.  Builds gas-major and DM-major pair lists in the
+ * context.  n_pairs (host, may be NULL) receives the count (synchronises).  If
+ * pairs_out (device, may be NULL) is given it receives min(count, capacity) pairs as
+ * [k][2] uint32 (DM input index, gas input index), grouped by gas. */
+dmb_status dmb_neighbors(dmb_ctx *ctx, int64_t *n_pairs, uint32_t *pairs_out, int64_t capacity);
+
+/* Gas mean field (Eqs. gas-dVdt, gas-dTdt) over the pairs of the last dmb_neighbors,
+ * from the state given to the last dmb_build_grid.  acc: device [N_B][3] float64,
+ * (km/s)^2/kpc; dudt: device [N_B] float64, du_j/dt = (3/(2 mu_j)) dT_j/dt in
+ * (km/s)^3/kpc.  Per-gas sums are accumulated in float64. */
+dmb_status dmb_meanfield_gas(dmb_ctx *ctx, double *acc, double *dudt);
+
+/* DM Monte Carlo (Eqs. dm-update-vels, dm-update-prob, scatter_chi) for time step dt at
+ * step index `step` (both key the Philox streams).  One categorical draw per DM
+ * particle: partners in ascending gas id, P_ij summed exactly; if sum_j P_ij > 1 the
+ * draw is renormalised (the particle scatters surely) and counted.
+ *   vel_out     device [N_chi][3] float64: new DM velocities
+ *   scattered   device [N_chi] uint8 (may be NULL): 1 if the particle scattered
+ *   partner     device [N_chi] uint32 (may be NULL): gas id of the partner, or 0xFFFFFFFF
+ *   p_ratio_max device [N_chi] float32 (may be NULL): max_j P_ij / min(0.1,
+ *               1e-4 ((m_chi + mu_j)/mu_j)^2), the Eq. prob_criterion ratio
+ *   p_total     device [N_chi] float64 (may be NULL): sum_j P_ij */
+dmb_status dmb_mc_scatter_dm(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out,
+                             uint8_t *scattered, uint32_t *partner, float *p_ratio_max,
+                             double *p_total);
+
+/* One whole step: grid, pairs, mean field, Monte Carlo, kicks and float64 sums.
+ * Updates in place (device arrays, the caller's): dm->vel (cast away const),
+ * gas->vel and gas->T (V_j += a_j dt; u_j += du_j/dt dt clamped at 0; T from u).
+ * sums_out (host, 16 doubles, may be NULL; synchronises):
+ *   [0:3] sum_i M_i dv_i (DM, realised)   [3:6] sum_j M_j a_j dt (gas)
+ *   [6] DM kinetic-energy change          [7] gas kinetic + thermal energy change
+ *   [8] sum_i E[dE_i] (App. C)            [9] scatters  [10] renormalised draws
+ *   [11] clamped gas u                    [12] pairs    [13] sum_ij P_ij
+ *   [14] max p_ratio                      [15] decisions within 1e-6 of a threshold */
+dmb_status dmb_step(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t step,
+                    double dt, double *sums_out);
+
+/* Debug/verification: evaluate the device overlap integral used by the pair kernels
+ * for k (d, h_i, h_j) triples.  in: device [k][3] float64; out: device [k] float64.
+ * Uses the table (float32 mode) or the exact evaluator (fp64 mode). */
+dmb_status dmb_debug_overlap(dmb_ctx *ctx, int64_t k, const double *in, double *out);
+
+/* Debug/verification: the device rate provider's normalised integrals for k samples.
+ * in: device [k] float64 x = w^2/(2 varsigma^2); out: device [k][2] float64
+ * (1F1(-(n+1)/2, 5/2; -x), 1F1(-(n+3)/2, 3/2; -x)) as evaluated on the device. */
+dmb_status dmb_debug_rates(dmb_ctx *ctx, int64_t k, const double *in, double *out);
+
+/* Debug/verification: Philox4x32-10 on the device.  ctr: device [k][4] uint32,
+ * out: device [k][4] uint32 with key = params.seed. */
+dmb_status dmb_debug_philox(dmb_ctx *ctx, int64_t k, const uint32_t *ctr, uint32_t *out);
+
+/* Number of kernel launches the context has issued since creation (bench accounting). */
+int64_t dmb_launch_count(const dmb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMB_H */

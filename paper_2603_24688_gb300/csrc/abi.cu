@@ -1,0 +1,478 @@
+// C ABI: context, buffers and the launch sequences of the hybrid interaction step.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "pairs.cuh"
+#include "sort_scan.cuh"
+#include "step.cuh"
+
+namespace {
+
+// Physical constants (CODATA 2018 / IAU); code units kpc, km/s, Msun.
+const double kKB = 1.380649e-16;          // erg/K
+const double kMP = 1.67262192369e-24;     // g
+const double kKPC = 3.0856775814913673e21;  // cm
+const double kMSUN = 1.98841e33;          // g
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+std::string g_create_error;
+
+}  // namespace
+
+struct SpeciesBufs {
+  DevBuf keys0, keys1, vals0, vals1, P, L, V, K, sid, bmin, bmax;
+  int64_t n = 0;
+  int nleaf = 0, p2 = 0;
+};
+
+struct dmb_ctx {
+  dmb_params p;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  RunConst rc;
+  BoxSplit bx;
+  int64_t launches = 0;
+  // device state
+  DevBuf frame, status, frame_part, gtab;
+  SpeciesBufs dm, gas;
+  DevBuf hist, hist_scan, scan_tmp;
+  DevBuf counts, gas_rowptr, gas_rows, dm_rowptr, dm_rows, pcache;
+  DevBuf mf_acc, mf_dudt, e_exp, mc_blocks, mc_max, kick_blocks, sums;
+  DevBuf scratch_vel;
+  uint32_t *h_status = nullptr;   // pinned
+  int64_t *h_tot = nullptr;       // pinned [2]
+  double *h_sums = nullptr;       // pinned [16]
+  // state
+  bool grid_ready = false, pairs_ready = false;
+  int64_t n_pairs = 0;
+  const double *dm_vel = nullptr;   // caller DM velocities of the last build
+};
+
+namespace {
+
+dmb_status fail(dmb_ctx *c, dmb_status s, const std::string &msg) {
+  if (c) c->err = msg; else g_create_error = msg;
+  return s;
+}
+
+dmb_status cuda_fail(dmb_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, DMB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                    \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+bool ensure(DevBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return true;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  const size_t want = bytes + bytes / 8;   // a little slack so slowly growing sizes do not reallocate
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  b.bytes = want;
+  return true;
+}
+
+void release(DevBuf &b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+template <typename T> T *ptr(const DevBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+int next_pow2(int64_t x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+template <typename R>
+SpeciesView<R> view(const SpeciesBufs &s) {
+  SpeciesView<R> v;
+  v.n = s.n;
+  v.P = ptr<typename Vec<R>::v4>(s.P);
+  v.L = ptr<typename Vec<R>::v4>(s.L);
+  v.V = ptr<typename Vec<R>::v4>(s.V);
+  v.K = ptr<typename Vec<R>::v4>(s.K);
+  v.id = ptr<uint32_t>(s.sid);
+  v.perm = ptr<uint32_t>(s.vals0);
+  v.bmin = ptr<float4>(s.bmin);
+  v.bmax = ptr<float4>(s.bmax);
+  v.nleaf = s.nleaf;
+  v.p2 = s.p2;
+  return v;
+}
+
+dmb_status ensure_species(dmb_ctx *ctx, SpeciesBufs &s, int64_t n, bool gas) {
+  const size_t v4b = ctx->p.fp64 ? 32 : 16;
+  s.n = n;
+  s.nleaf = (int)((n + DMB_LEAF - 1) / DMB_LEAF);
+  s.p2 = next_pow2(s.nleaf > 0 ? s.nleaf : 1);
+  bool ok = ensure(s.keys0, n * 8) && ensure(s.keys1, n * 8) && ensure(s.vals0, n * 4) && ensure(s.vals1, n * 4) &&
+            ensure(s.P, n * v4b) && ensure(s.L, n * v4b) && ensure(s.V, n * v4b) && ensure(s.sid, n * 4) &&
+            ensure(s.bmin, (size_t)2 * s.p2 * 16 + 16) && ensure(s.bmax, (size_t)2 * s.p2 * 16 + 16);
+  if (gas) ok = ok && ensure(s.K, n * v4b);
+  else ok = ok && ensure(s.K, 64);
+  if (!ok) return fail(ctx, DMB_ERR_OOM, "device allocation failed for particle buffers");
+  return DMB_OK;
+}
+
+dmb_status ensure_sort_scratch(dmb_ctx *ctx, int64_t n) {
+  const int64_t hist_n = radix_hist_elems(n);
+  const int64_t tmp_n = scan_tmp_elems(hist_n > n + 1 ? hist_n : n + 1);
+  if (!ensure(ctx->hist, hist_n * 4) || !ensure(ctx->hist_scan, (hist_n + 1) * 8) || !ensure(ctx->scan_tmp, tmp_n * 8))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for sort scratch");
+  return DMB_OK;
+}
+
+dmb_status check_status(dmb_ctx *ctx) {
+  CK(cudaMemcpyAsync(ctx->h_status, ctx->status.p, 4, cudaMemcpyDeviceToHost, ctx->stream), "status readback");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+  const uint32_t st = *ctx->h_status;
+  if (st == 0) return DMB_OK;
+  CK(cudaMemsetAsync(ctx->status.p, 0, 4, ctx->stream), "status reset");
+  std::string m = "device input checks failed:";
+  if (st & DMB_BAD_VALUE) m += " non-finite or out-of-range value (need finite x, v; h, M, mu > 0; T >= 0);";
+  if (st & DMB_BAD_PERIODIC) m += " periodic box smaller than 2 (max h_dm + max h_gas);";
+  if (st & DMB_BAD_DOMAIN) m += " rate provider outside its domain;";
+  if (st & DMB_BAD_OVERFLOW) m += " internal list overflow;";
+  return fail(ctx, (st & DMB_BAD_DOMAIN) ? DMB_ERR_DOMAIN : DMB_ERR_ARG, m);
+}
+
+// ---- build_grid ------------------------------------------------------------------------
+template <typename R>
+dmb_status build_grid_impl(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
+  cudaStream_t s = ctx->stream;
+  int64_t *L = &ctx->launches;
+  dmb_status st;
+  if ((st = ensure_species(ctx, ctx->dm, dm->n, false)) != DMB_OK) return st;
+  if ((st = ensure_species(ctx, ctx->gas, gas->n, true)) != DMB_OK) return st;
+  if ((st = ensure_sort_scratch(ctx, dm->n > gas->n ? dm->n : gas->n)) != DMB_OK) return st;
+  CK(launch_frame(dm->pos, dm->h, dm->n, gas->pos, gas->h, gas->n, ctx->p.periodic, ctx->p.box,
+                  ptr<double>(ctx->frame_part), (int64_t)(ctx->frame_part.bytes / 8), ptr<Frame>(ctx->frame),
+                  ptr<uint32_t>(ctx->status), s, L), "frame");
+  const Frame *fr = ptr<Frame>(ctx->frame);
+  SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};
+  const double *pos[2] = {dm->pos, gas->pos};
+  const double *vel[2] = {dm->vel, gas->vel};
+  const double *mass[2] = {dm->mass, gas->mass};
+  const double *hh[2] = {dm->h, gas->h};
+  const double *T[2] = {nullptr, gas->T};
+  const double *mu[2] = {nullptr, gas->mu};
+  const uint32_t *id[2] = {dm->id, gas->id};
+  // Morton bits: enough for the larger species (the frame kernel picks the same rule)
+  const int64_t ntot = dm->n + gas->n;
+  const int bits = (int)fmin(21.0, fmax(10.0, ceil(log2((double)(ntot > 1 ? ntot : 2)) / 3.0) + 7.0));
+  for (int k = 0; k < 2; ++k) {
+    SpeciesBufs &b = *sp[k];
+    if (b.n > 0) {
+      CK(launch_morton(pos[k], b.n, ctx->p.periodic, ctx->p.box, fr, ptr<uint64_t>(b.keys0), ptr<uint32_t>(b.vals0), s,
+                       L), "morton");
+      CK(radix_sort_pairs(ptr<uint64_t>(b.keys0), ptr<uint32_t>(b.vals0), ptr<uint64_t>(b.keys1),
+                          ptr<uint32_t>(b.vals1), b.n, 3 * bits, ptr<uint32_t>(ctx->hist), ptr<int64_t>(ctx->hist_scan),
+                          ptr<int64_t>(ctx->scan_tmp), s, L), "radix sort");
+      CK(launch_gather<R>(pos[k], vel[k], mass[k], hh[k], T[k], mu[k], id[k], b.n, ptr<uint32_t>(b.vals0),
+                          ctx->p.periodic, ctx->p.box, fr, ctx->rc, ptr<typename Vec<R>::v4>(b.P),
+                          ptr<typename Vec<R>::v4>(b.L), ptr<typename Vec<R>::v4>(b.V),
+                          ptr<typename Vec<R>::v4>(b.K), ptr<uint32_t>(b.sid), ptr<uint32_t>(ctx->status), s, L),
+         "gather");
+    }
+    CK(launch_tree<R>(ptr<typename Vec<R>::v4>(b.P), ptr<typename Vec<R>::v4>(b.L), b.n, fr, ptr<float4>(b.bmin),
+                      ptr<float4>(b.bmax), b.p2, s, L), "tree");
+  }
+  ctx->dm_vel = dm->vel;
+  ctx->grid_ready = true;
+  ctx->pairs_ready = false;
+  return DMB_OK;
+}
+
+// ---- neighbours --------------------------------------------------------------------------
+template <typename R>
+dmb_status neighbors_impl(dmb_ctx *ctx) {
+  cudaStream_t s = ctx->stream;
+  int64_t *L = &ctx->launches;
+  const SpeciesView<R> D = view<R>(ctx->dm), G = view<R>(ctx->gas);
+  const Frame *fr = ptr<Frame>(ctx->frame);
+  uint32_t *status = ptr<uint32_t>(ctx->status);
+  const int64_t nmax = D.n > G.n ? D.n : G.n;
+  if (!ensure(ctx->counts, (nmax + 1) * 4 * 2) || !ensure(ctx->gas_rowptr, (G.n + 1) * 8) ||
+      !ensure(ctx->dm_rowptr, (D.n + 1) * 8))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for pair offsets");
+  dmb_status st;
+  if ((st = ensure_sort_scratch(ctx, nmax)) != DMB_OK) return st;
+  uint32_t *cg = ptr<uint32_t>(ctx->counts), *cd = cg + (nmax + 1);
+  CK(launch_pair_search<R>(G, D, ctx->bx, fr, false, cg, nullptr, nullptr, status, s, L), "pair count (gas)");
+  CK(exclusive_scan_u32_i64(cg, ptr<int64_t>(ctx->gas_rowptr), G.n, ptr<int64_t>(ctx->scan_tmp), s, L), "scan");
+  CK(cudaMemcpyAsync(ctx->h_tot, ptr<int64_t>(ctx->gas_rowptr) + G.n, 8, cudaMemcpyDeviceToHost, s), "readback");
+  CK(launch_pair_search<R>(D, G, ctx->bx, fr, false, cd, nullptr, nullptr, status, s, L), "pair count (dm)");
+  // the scan scratch is reused, so the second scan follows the first readback on the stream
+  CK(exclusive_scan_u32_i64(cd, ptr<int64_t>(ctx->dm_rowptr), D.n, ptr<int64_t>(ctx->scan_tmp), s, L), "scan");
+  CK(cudaMemcpyAsync(ctx->h_tot + 1, ptr<int64_t>(ctx->dm_rowptr) + D.n, 8, cudaMemcpyDeviceToHost, s), "readback");
+  if ((st = check_status(ctx)) != DMB_OK) return st;
+  const int64_t ng = G.n > 0 ? ctx->h_tot[0] : 0, nd = D.n > 0 ? ctx->h_tot[1] : 0;
+  if (ng != nd) return fail(ctx, DMB_ERR_STATE, "pair counts of the two search directions differ");
+  const size_t rb = ctx->p.fp64 ? 8 : 4;
+  if (!ensure(ctx->gas_rows, ng * 4) || !ensure(ctx->dm_rows, ng * 4) || !ensure(ctx->pcache, ng * rb))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for pair lists");
+  CK(launch_pair_search<R>(G, D, ctx->bx, fr, true, nullptr, ptr<int64_t>(ctx->gas_rowptr),
+                           ptr<uint32_t>(ctx->gas_rows), status, s, L), "pair emit (gas)");
+  CK(launch_pair_search<R>(D, G, ctx->bx, fr, true, nullptr, ptr<int64_t>(ctx->dm_rowptr),
+                           ptr<uint32_t>(ctx->dm_rows), status, s, L), "pair emit (dm)");
+  ctx->n_pairs = ng;
+  ctx->pairs_ready = true;
+  return DMB_OK;
+}
+
+template <typename R>
+dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp) {
+  const SpeciesView<R> D = view<R>(ctx->dm), G = view<R>(ctx->gas);
+  MfOut o;
+  o.acc = acc;
+  o.dudt = dudt;
+  o.e_exp = e_exp;
+  CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->gas_rowptr), ptr<uint32_t>(ctx->gas_rows),
+                         ptr<float4>(ctx->gtab), ctx->rc, o, ctx->stream, &ctx->launches), "meanfield");
+  return DMB_OK;
+}
+
+int mc_blocks_for(int64_t n) {
+  int64_t b = (n + 7) / 8;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b > 0 ? b : 1);
+}
+
+template <typename R>
+dmb_status mc_impl(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, uint8_t *scat, uint32_t *partner,
+                   float *pratio, double *ptot) {
+  const SpeciesView<R> D = view<R>(ctx->dm), G = view<R>(ctx->gas);
+  const int nb = mc_blocks_for(D.n);
+  if (!ensure(ctx->mc_blocks, (size_t)nb * 8 * 8) || !ensure(ctx->mc_max, (size_t)nb * 8))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for MC partials");
+  McArgs a;
+  a.dt = dt;
+  a.step = step;
+  a.seed = ctx->p.seed;
+  a.id_bits = 32;
+  a.vel_in = ctx->dm_vel;
+  a.vel_out = vel_out;
+  a.scattered = scat;
+  a.partner = partner;
+  a.p_ratio = pratio;
+  a.p_total = ptot;
+  a.block_sums = ptr<double>(ctx->mc_blocks);
+  a.block_max = ptr<double>(ctx->mc_max);
+  if (D.n > 0)
+    CK(launch_mc<R>(D, G, ctx->bx, ptr<int64_t>(ctx->dm_rowptr), ptr<uint32_t>(ctx->dm_rows),
+                    ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), nb, ctx->stream, &ctx->launches), "mc");
+  return DMB_OK;
+}
+
+dmb_status check_dm(dmb_ctx *ctx, const dmb_dm *dm) {
+  if (!dm) return fail(ctx, DMB_ERR_ARG, "dm is NULL");
+  if (dm->n < 0 || dm->n > 0x7fffffffLL) return fail(ctx, DMB_ERR_ARG, "dm->n out of range");
+  if (dm->n > 0 && (!dm->pos || !dm->vel || !dm->mass || !dm->h || !dm->id))
+    return fail(ctx, DMB_ERR_ARG, "dm has a NULL array");
+  return DMB_OK;
+}
+dmb_status check_gas(dmb_ctx *ctx, const dmb_gas *g) {
+  if (!g) return fail(ctx, DMB_ERR_ARG, "gas is NULL");
+  if (g->n < 0 || g->n > 0x7fffffffLL) return fail(ctx, DMB_ERR_ARG, "gas->n out of range");
+  if (g->n > 0 && (!g->pos || !g->vel || !g->mass || !g->h || !g->T || !g->mu || !g->id))
+    return fail(ctx, DMB_ERR_ARG, "gas has a NULL array");
+  return DMB_OK;
+}
+
+}  // namespace
+
+// ======================================================================================
+extern "C" {
+
+dmb_status dmb_create(dmb_ctx **out, const dmb_params *p, void *cuda_stream) {
+  if (!out) return fail(nullptr, DMB_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!p) return fail(nullptr, DMB_ERR_ARG, "params is NULL");
+  if (!(p->sigma0_cm2 >= 0.0) || !isfinite(p->sigma0_cm2)) return fail(nullptr, DMB_ERR_ARG, "sigma0 must be finite and >= 0");
+  if (!(p->v0_kms > 0.0) || !isfinite(p->v0_kms)) return fail(nullptr, DMB_ERR_ARG, "v0 must be > 0");
+  if (p->n < -4 || p->n > 16) return fail(nullptr, DMB_ERR_ARG, "power-law index n must be in [-4, 16]");
+  if (!(p->m_chi_mp > 0.0) || !isfinite(p->m_chi_mp)) return fail(nullptr, DMB_ERR_ARG, "m_chi must be > 0");
+  if (p->rate_mode != DMB_RATE_CLOSED)
+    return fail(nullptr, DMB_ERR_ARG, "only the closed-form rate provider is available in this build");
+  if (p->periodic)
+    for (int k = 0; k < 3; ++k)
+      if (!(p->box[k] > 0.0) || !isfinite(p->box[k])) return fail(nullptr, DMB_ERR_ARG, "periodic box sides must be > 0");
+  dmb_ctx *ctx = new dmb_ctx();
+  ctx->p = *p;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  const double sig_kpc2 = p->sigma0_cm2 / (kKPC * kKPC);
+  ctx->rc.S = sig_kpc2 * (kMSUN / kMP);
+  ctx->rc.m_chi = p->m_chi_mp;
+  ctx->rc.v0 = p->v0_kms;
+  ctx->rc.n = p->n;
+  ctx->rc.alpha = pow(2.0, (p->n + 5) / 2.0) * tgamma(3.0 + p->n / 2.0) / sqrt(M_PI);
+  ctx->rc.kT_over_mp = kKB / kMP / 1e10;
+  ctx->bx.periodic = p->periodic ? 1 : 0;
+  for (int k = 0; k < 3; ++k) {
+    const double Lk = p->periodic ? p->box[k] : 0.0;
+    ctx->bx.L[k] = Lk;
+    ctx->bx.Lhi[k] = (float)Lk;
+    ctx->bx.Llo[k] = (float)(Lk - (double)ctx->bx.Lhi[k]);
+  }
+  ctx->bx.pad = 0.0f;
+  bool ok = ensure(ctx->frame, sizeof(Frame)) && ensure(ctx->status, 16) && ensure(ctx->frame_part, 1024 * 8 * 8) &&
+            ensure(ctx->gtab, (size_t)DMB_GT_NQ * DMB_GT_CELLS * 16) && ensure(ctx->sums, 16 * 8);
+  if (!ok) {
+    dmb_destroy(ctx);
+    return fail(nullptr, DMB_ERR_OOM, "device allocation failed at context creation");
+  }
+  if (cudaMallocHost(&ctx->h_status, 64) != cudaSuccess || cudaMallocHost(&ctx->h_tot, 64) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_sums, 16 * 8) != cudaSuccess) {
+    cudaGetLastError();
+    dmb_destroy(ctx);
+    return fail(nullptr, DMB_ERR_OOM, "pinned host allocation failed");
+  }
+  cudaError_t e = cudaMemsetAsync(ctx->status.p, 0, 16, ctx->stream);
+  if (e == cudaSuccess) e = launch_gtable(ptr<float4>(ctx->gtab), ctx->stream, &ctx->launches);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    std::string m = std::string("context setup: ") + cudaGetErrorString(e);
+    dmb_destroy(ctx);
+    return fail(nullptr, DMB_ERR_CUDA, m);
+  }
+  *out = ctx;
+  return DMB_OK;
+}
+
+dmb_status dmb_destroy(dmb_ctx *ctx) {
+  if (!ctx) return DMB_OK;
+  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  DevBuf *bufs[] = {&ctx->frame, &ctx->status, &ctx->frame_part, &ctx->gtab, &ctx->hist, &ctx->hist_scan,
+                    &ctx->scan_tmp, &ctx->counts, &ctx->gas_rowptr, &ctx->gas_rows, &ctx->dm_rowptr, &ctx->dm_rows,
+                    &ctx->pcache, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
+                    &ctx->kick_blocks, &ctx->sums, &ctx->scratch_vel};
+  for (DevBuf *b : bufs) release(*b);
+  SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};
+  for (SpeciesBufs *s : sp) {
+    DevBuf *sb[] = {&s->keys0, &s->keys1, &s->vals0, &s->vals1, &s->P, &s->L, &s->V, &s->K, &s->sid, &s->bmin, &s->bmax};
+    for (DevBuf *b : sb) release(*b);
+  }
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->h_tot) cudaFreeHost(ctx->h_tot);
+  if (ctx->h_sums) cudaFreeHost(ctx->h_sums);
+  delete ctx;
+  return DMB_OK;
+}
+
+const char *dmb_last_error(const dmb_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int64_t dmb_launch_count(const dmb_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+dmb_status dmb_build_grid(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  dmb_status st;
+  if ((st = check_dm(ctx, dm)) != DMB_OK || (st = check_gas(ctx, gas)) != DMB_OK) return st;
+  return ctx->p.fp64 ? build_grid_impl<double>(ctx, dm, gas) : build_grid_impl<float>(ctx, dm, gas);
+}
+
+dmb_status dmb_neighbors(dmb_ctx *ctx, int64_t *n_pairs, uint32_t *pairs_out, int64_t capacity) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!ctx->grid_ready) return fail(ctx, DMB_ERR_STATE, "dmb_neighbors before dmb_build_grid");
+  dmb_status st = ctx->p.fp64 ? neighbors_impl<double>(ctx) : neighbors_impl<float>(ctx);
+  if (st != DMB_OK) return st;
+  if (n_pairs) *n_pairs = ctx->n_pairs;
+  if (pairs_out && capacity > 0)
+    CK(launch_pairs_out(ptr<int64_t>(ctx->gas_rowptr), ptr<uint32_t>(ctx->gas_rows), ptr<uint32_t>(ctx->gas.vals0),
+                        ptr<uint32_t>(ctx->dm.vals0), ctx->gas.n, capacity, pairs_out, ctx->stream, &ctx->launches),
+       "pairs out");
+  return DMB_OK;
+}
+
+dmb_status dmb_meanfield_gas(dmb_ctx *ctx, double *acc, double *dudt) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!ctx->pairs_ready) return fail(ctx, DMB_ERR_STATE, "dmb_meanfield_gas before dmb_neighbors");
+  if (ctx->gas.n > 0 && (!acc || !dudt)) return fail(ctx, DMB_ERR_ARG, "acc/dudt is NULL");
+  return ctx->p.fp64 ? meanfield_impl<double>(ctx, acc, dudt, nullptr) : meanfield_impl<float>(ctx, acc, dudt, nullptr);
+}
+
+dmb_status dmb_mc_scatter_dm(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, uint8_t *scattered,
+                             uint32_t *partner, float *p_ratio_max, double *p_total) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!ctx->pairs_ready) return fail(ctx, DMB_ERR_STATE, "dmb_mc_scatter_dm before dmb_neighbors");
+  if (!(dt >= 0.0) || !isfinite(dt)) return fail(ctx, DMB_ERR_ARG, "dt must be finite and >= 0");
+  if (ctx->dm.n > 0 && !vel_out) return fail(ctx, DMB_ERR_ARG, "vel_out is NULL");
+  return ctx->p.fp64 ? mc_impl<double>(ctx, step, dt, vel_out, scattered, partner, p_ratio_max, p_total)
+                     : mc_impl<float>(ctx, step, dt, vel_out, scattered, partner, p_ratio_max, p_total);
+}
+
+dmb_status dmb_step(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t step, double dt, double *sums_out) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!(dt >= 0.0) || !isfinite(dt)) return fail(ctx, DMB_ERR_ARG, "dt must be finite and >= 0");
+  dmb_status st;
+  if ((st = dmb_build_grid(ctx, dm, gas)) != DMB_OK) return st;
+  if ((st = dmb_neighbors(ctx, nullptr, nullptr, 0)) != DMB_OK) return st;
+  const int64_t ng = gas->n, nd = dm->n;
+  if (!ensure(ctx->mf_acc, ng * 24) || !ensure(ctx->mf_dudt, ng * 8) || !ensure(ctx->e_exp, ng * 8))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for mean-field scratch");
+  st = ctx->p.fp64 ? meanfield_impl<double>(ctx, ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp))
+                   : meanfield_impl<float>(ctx, ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp));
+  if (st != DMB_OK) return st;
+  // DM velocities are updated in place: the MC reads v_i and writes v_i' for the same particle
+  st = ctx->p.fp64 ? mc_impl<double>(ctx, step, dt, const_cast<double *>(dm->vel), nullptr, nullptr, nullptr, nullptr)
+                   : mc_impl<float>(ctx, step, dt, const_cast<double *>(dm->vel), nullptr, nullptr, nullptr, nullptr);
+  if (st != DMB_OK) return st;
+  const int kb = 152 * 4;
+  if (!ensure(ctx->kick_blocks, (size_t)kb * KICK_NSUM * 8)) return fail(ctx, DMB_ERR_OOM, "kick partials");
+  CK(launch_kick_gas(const_cast<double *>(gas->vel), const_cast<double *>(gas->T), gas->mu, gas->mass,
+                     ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp), ng, dt,
+                     ctx->rc.kT_over_mp, ptr<double>(ctx->kick_blocks), kb, ctx->stream, &ctx->launches), "kick");
+  if (nd <= 0) {
+    CK(cudaMemsetAsync(ctx->mc_blocks.p ? ctx->mc_blocks.p : ctx->sums.p, 0, 8, ctx->stream), "memset");
+  }
+  const int mnb = nd > 0 ? mc_blocks_for(nd) : 0;
+  if (nd <= 0 && !ensure(ctx->mc_blocks, 64)) return fail(ctx, DMB_ERR_OOM, "mc partials");
+  if (nd <= 0 && !ensure(ctx->mc_max, 64)) return fail(ctx, DMB_ERR_OOM, "mc partials");
+  CK(launch_final_sums(ptr<double>(ctx->mc_blocks), ptr<double>(ctx->mc_max), mnb, ptr<double>(ctx->kick_blocks), kb,
+                       dt, (double)ctx->n_pairs, ptr<double>(ctx->sums), ctx->stream, &ctx->launches), "sums");
+  ctx->grid_ready = false;   // the state moved on: rebuild before the next standalone call
+  ctx->pairs_ready = false;
+  if (sums_out) {
+    CK(cudaMemcpyAsync(ctx->h_sums, ctx->sums.p, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream), "sums readback");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    memcpy(sums_out, ctx->h_sums, 16 * 8);
+  }
+  return DMB_OK;
+}
+
+dmb_status dmb_debug_overlap(dmb_ctx *ctx, int64_t k, const double *in, double *out) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  CK(launch_debug_overlap(ptr<float4>(ctx->gtab), ctx->p.fp64, k, in, out, ctx->stream), "debug overlap");
+  return DMB_OK;
+}
+
+dmb_status dmb_debug_rates(dmb_ctx *ctx, int64_t k, const double *in, double *out) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  CK(launch_debug_rates(ctx->p.fp64, ctx->p.n, k, in, out, ctx->stream), "debug rates");
+  return DMB_OK;
+}
+
+dmb_status dmb_debug_philox(dmb_ctx *ctx, int64_t k, const uint32_t *ctr, uint32_t *out) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  CK(launch_debug_philox(k, ctr, out, ctx->p.seed, ctx->stream), "debug philox");
+  return DMB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// Shared device types and helpers of the CUDA path (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dmb.h"
+
+#define DMB_WARP 32
+#define DMB_LEAF 32          // particles per tree leaf (one warp's worth)
+#define DMB_FULL 0xffffffffu
+
+// overlap table: delta nodes on [0, 2], q nodes on [0, 1]
+#define DMB_GT_ND 1025                 // delta nodes on [0, 2]
+#define DMB_GT_NQ 513                  // q nodes on [0, 1]
+#define DMB_GT_CELLS (DMB_GT_ND - 1)
+
+// ---- float / double traits --------------------------------------------------------
+template <typename R> struct Vec;
+template <> struct Vec<float> {
+  typedef float4 v4;
+  static __host__ __device__ __forceinline__ float4 make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+template <> struct Vec<double> {
+  typedef double4_32a v4;
+  static __host__ __device__ __forceinline__ double4_32a make(double a, double b, double c, double d) { return make_double4_32a(a, b, c, d); }
+};
+
+// Arithmetic that the compiler may not contract into FMAs: used where two kernels must
+// reach bit-identical results from the same inputs (the pair predicate and distance).
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// ---- sorted species on the device -------------------------------------------------
+// Positions are split as x - origin = hi + lo with hi an integer multiple of a power of two
+// Delta (so hi differences are exact in float32) and lo in [0, Delta).
+template <typename R> struct SpeciesView {
+  int64_t n;
+  const typename Vec<R>::v4 *P;   // (hi_x, hi_y, hi_z, h)
+  const typename Vec<R>::v4 *L;   // (lo_x, lo_y, lo_z, M)
+  const typename Vec<R>::v4 *V;   // (vx, vy, vz, varsigma [gas] | 0 [dm])
+  const typename Vec<R>::v4 *K;   // gas: (cA, cB, kP0, e = mu/(m_chi + mu)); dm: unused
+  const uint32_t *id;             // stable id
+  const uint32_t *perm;           // sorted position -> caller index
+  const float4 *bmin;             // tree nodes, heap order from 1: (min xyz, h_max)
+  const float4 *bmax;             // (max xyz, unused)
+  int32_t nleaf, p2;              // leaves and the padded power of two
+};
+
+// Periodic box in the split representation.
+struct BoxSplit {
+  int periodic;
+  float Lhi[3], Llo[3];           // float32 split of the box sides
+  double L[3];
+  float pad;                      // conservative padding of tree boxes
+};
+
+// Canonical pair displacement x_a - x_b (minimum image if periodic), identical bits whichever
+// kernel computes it and antisymmetric in (a, b).
+template <typename R>
+__device__ __forceinline__ void pair_dx(const typename Vec<R>::v4 &Pa, const typename Vec<R>::v4 &La,
+                                        const typename Vec<R>::v4 &Pb, const typename Vec<R>::v4 &Lb,
+                                        const BoxSplit &bx, R &dx, R &dy, R &dz) {
+  R hx = sub_rn(Pa.x, Pb.x), hy = sub_rn(Pa.y, Pb.y), hz = sub_rn(Pa.z, Pb.z);   // exact
+  R lx = sub_rn(La.x, Lb.x), ly = sub_rn(La.y, Lb.y), lz = sub_rn(La.z, Lb.z);
+  if (bx.periodic) {
+    const R L0 = (R)bx.Lhi[0], L1 = (R)bx.Lhi[1], L2 = (R)bx.Lhi[2];
+    if (sizeof(R) == 8) {  // float64 path: the box side is exact in double
+      if (hx > (R)(0.5 * bx.L[0])) hx = sub_rn(hx, (R)bx.L[0]); else if (hx < (R)(-0.5 * bx.L[0])) hx = add_rn(hx, (R)bx.L[0]);
+      if (hy > (R)(0.5 * bx.L[1])) hy = sub_rn(hy, (R)bx.L[1]); else if (hy < (R)(-0.5 * bx.L[1])) hy = add_rn(hy, (R)bx.L[1]);
+      if (hz > (R)(0.5 * bx.L[2])) hz = sub_rn(hz, (R)bx.L[2]); else if (hz < (R)(-0.5 * bx.L[2])) hz = add_rn(hz, (R)bx.L[2]);
+    } else {
+      // hi differences in (L/2, L) minus the float side are exact (Sterbenz); the low part
+      // of the side goes with lo
+      if (hx > (R)0.5 * L0) { hx = sub_rn(hx, L0); lx = sub_rn(lx, (R)bx.Llo[0]); }
+      else if (hx < (R)-0.5 * L0) { hx = add_rn(hx, L0); lx = add_rn(lx, (R)bx.Llo[0]); }
+      if (hy > (R)0.5 * L1) { hy = sub_rn(hy, L1); ly = sub_rn(ly, (R)bx.Llo[1]); }
+      else if (hy < (R)-0.5 * L1) { hy = add_rn(hy, L1); ly = add_rn(ly, (R)bx.Llo[1]); }
+      if (hz > (R)0.5 * L2) { hz = sub_rn(hz, L2); lz = sub_rn(lz, (R)bx.Llo[2]); }
+      else if (hz < (R)-0.5 * L2) { hz = add_rn(hz, L2); lz = add_rn(lz, (R)bx.Llo[2]); }
+    }
+  }
+  dx = add_rn(hx, lx);
+  dy = add_rn(hy, ly);
+  dz = add_rn(hz, lz);
+}
+
+template <typename R>
+__device__ __forceinline__ R dist2_rn(R dx, R dy, R dz) {
+  return add_rn(add_rn(mul_rn(dx, dx), mul_rn(dy, dy)), mul_rn(dz, dz));
+}
+
+// Pair predicate d_ab < h_a + h_b, evaluated as d^2 < (h_a + h_b)^2 with fixed rounding.
+template <typename R>
+__device__ __forceinline__ bool pair_test(R d2, R ha, R hb) {
+  R r = add_rn(ha, hb);
+  return d2 < mul_rn(r, r);
+}
+
+// ---- small utilities -----------------------------------------------------------------
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(DMB_FULL, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(DMB_FULL, v, o));
+  return v;
+}
+
+// 128-bit unsigned fixed point with 64 fractional bits: exact, order-independent sums of
+// the Monte Carlo probabilities.
+struct U128 {
+  unsigned long long lo, hi;
+};
+__device__ __forceinline__ U128 u128_add(U128 a, U128 b) {
+  U128 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+  return r;
+}
+__device__ __forceinline__ bool u128_lt(U128 a, U128 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ U128 u128_shfl_xor(U128 a, int o) {
+  U128 r;
+  r.lo = __shfl_xor_sync(DMB_FULL, a.lo, o);
+  r.hi = __shfl_xor_sync(DMB_FULL, a.hi, o);
+  return r;
+}
+__device__ __forceinline__ U128 warp_sum_u128(U128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = u128_add(v, u128_shfl_xor(v, o));
+  return v;
+}
+// Exact conversion of a non-negative float/double to the fixed-point format (values below
+// 2^-64 of a unit truncate; values >= 2^63 saturate).
+__device__ __forceinline__ U128 to_fixed(double p) {
+  U128 r = {0ull, 0ull};
+  if (!(p > 0.0)) return r;
+  if (p >= 9.2233720368547758e18) { r.hi = 0x7fffffffffffffffull; r.lo = ~0ull; return r; }
+  int e;
+  double m = frexp(p, &e);                       // p = m 2^e, m in [0.5, 1)
+  unsigned long long mant = (unsigned long long)ldexp(m, 53);   // 53-bit integer
+  int sh = e - 53 + 64;                          // value = mant * 2^(e-53); fixed = value * 2^64
+  if (sh >= 64) { r.hi = mant << (sh - 64); r.lo = 0; if (sh - 64 > 0) r.hi |= 0; }
+  else if (sh > 0) { r.hi = mant >> (64 - sh); r.lo = mant << sh; }
+  else if (sh > -64) { r.lo = mant >> (-sh); }
+  return r;
+}
+__device__ __forceinline__ U128 to_fixed(float p) { return to_fixed((double)p); }
+__device__ __forceinline__ double fixed_to_double(U128 a) {
+  return ldexp((double)a.hi, 0) + ldexp((double)a.lo, -64);
+}
+// floor(r * a) for a 64-bit fraction r = R 2^-64 and a fixed-point a.
+__device__ __forceinline__ U128 u128_scale(unsigned long long R, U128 a) {
+  U128 r;
+  unsigned long long p_hi_lo = R * a.hi;
+  unsigned long long p_hi_hi = __umul64hi(R, a.hi);
+  unsigned long long p_lo_hi = __umul64hi(R, a.lo);
+  r.lo = p_hi_lo + p_lo_hi;
+  r.hi = p_hi_hi + (r.lo < p_hi_lo ? 1ull : 0ull);
+  return r;
+}

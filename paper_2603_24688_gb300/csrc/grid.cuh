@@ -1,0 +1,50 @@
+// Spatial index: shared frame, Morton keys, sorted float copies, chunk tree.
+#pragma once
+#include "common.cuh"
+
+struct Frame {
+  double origin[3];
+  double span;       // side of the cube holding all particles (periodic: max box side)
+  double delta;      // power of two with span <= 2^23 delta: quantum of the hi parts
+  double key_scale;  // 2^bits / span
+  float pad;         // padding of tree boxes (covers float rounding of the coordinates)
+  int bits;          // Morton bits per axis
+  double hmax_dm, hmax_gas;
+};
+
+// Physical constants of a run, precomputed on the host in float64.
+struct RunConst {
+  double S;          // sigma0 [kpc^2] * Msun / m_p
+  double m_chi;      // m_chi / m_p
+  double v0;         // km/s
+  double alpha;      // alpha_n = 2^((n+5)/2) Gamma(3 + n/2) / sqrt(pi)
+  double kT_over_mp; // k_B / m_p in (km/s)^2 / K
+  int n;
+};
+
+// Status bits raised by the device checks.
+enum : uint32_t {
+  DMB_BAD_VALUE = 1u,      // NaN / Inf or a non-positive h, M, mu, or negative T
+  DMB_BAD_PERIODIC = 2u,   // h_i + h_j >= box / 2 (minimum image ambiguous)
+  DMB_BAD_DOMAIN = 4u,     // rate provider outside its domain
+  DMB_BAD_OVERFLOW = 8u,   // a pair list or stack overflowed
+};
+
+cudaError_t launch_frame(const double *dm_pos, const double *dm_h, int64_t ndm, const double *gas_pos,
+                         const double *gas_h, int64_t ngas, int periodic, const double box[3], double *part,
+                         int64_t part_elems, Frame *frame, uint32_t *status, cudaStream_t s, int64_t *launches);
+
+cudaError_t launch_morton(const double *pos, int64_t n, int periodic, const double box[3], const Frame *frame,
+                          uint64_t *keys, uint32_t *vals, cudaStream_t s, int64_t *launches);
+
+template <typename R>
+cudaError_t launch_gather(const double *pos, const double *vel, const double *mass, const double *h,
+                          const double *T, const double *mu, const uint32_t *id, int64_t n, const uint32_t *perm,
+                          int periodic, const double box[3], const Frame *frame, RunConst rc,
+                          typename Vec<R>::v4 *P, typename Vec<R>::v4 *L, typename Vec<R>::v4 *V,
+                          typename Vec<R>::v4 *K, uint32_t *sid, uint32_t *status, cudaStream_t s,
+                          int64_t *launches);
+
+template <typename R>
+cudaError_t launch_tree(const typename Vec<R>::v4 *P, const typename Vec<R>::v4 *L, int64_t n, const Frame *frame,
+                        float4 *bmin, float4 *bmax, int p2, cudaStream_t s, int64_t *launches);

@@ -1,0 +1,331 @@
+// Pair physics: gas mean field (Eqs. gas-dVdt, gas-dTdt) and DM Monte Carlo
+// (Eqs. dm-update-vels, dm-update-prob, scatter_chi, prob_criterion).
+#include "pairs.cuh"
+#include "physics.cuh"
+
+#define MF_WARPS 8
+#define MC_WARPS 8
+
+// ---- mean field: one warp per gas particle, lanes stride over its DM partners ---------
+template <typename R>
+__global__ void __launch_bounds__(MF_WARPS * 32)
+k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__restrict__ row_ptr,
+            const uint32_t *__restrict__ rows, const float4 *__restrict__ gtab, RunConst rc, MfOut out) {
+  typedef typename Vec<R>::v4 v4;
+  const unsigned lane = threadIdx.x & 31u;
+  const int64_t nwarps = (int64_t)gridDim.x * MF_WARPS;
+  const R inv_v0 = (R)(1.0 / rc.v0);
+  for (int64_t j = (int64_t)blockIdx.x * MF_WARPS + (threadIdx.x >> 5); j < G.n; j += nwarps) {
+    const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
+    const int64_t rs = row_ptr[j], re = row_ptr[j + 1];
+    const R sig = Vj.w;
+    const bool hot = sig > (R)0;
+    const R inv2s2 = hot ? (R)0.5 / (sig * sig) : (R)0;
+    R sx = 0, sy = 0, sz = 0, sw2 = 0, sb = 0, svw = 0;
+    for (int64_t p = rs + lane; p < re; p += 32) {
+      const uint32_t i = rows[p];
+      const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
+      R dx, dy, dz;
+      pair_dx<R>(Pi, Li, Pj, Lj, bx, dx, dy, dz);
+      const R d = sqrt_t(dist2_rn<R>(dx, dy, dz));
+      const R g = overlap_g<R>(gtab, d, Pi.w, Pj.w);
+      const R wx = Vi.x - Vj.x, wy = Vi.y - Vj.y, wz = Vi.z - Vj.z;
+      const R w2 = wx * wx + wy * wy + wz * wz;
+      R FA, FB;
+      if (hot) {
+        rates_FAB<R>(w2 * inv2s2, rc.n, FA, FB);
+      } else {
+        const R wn = sqrt_t(w2);
+        const R sn = ipow<R>(wn * inv_v0, rc.n);
+        FA = sn * wn;
+        FB = sn * wn * w2;
+      }
+      const R t = Li.w * g;          // M_i g_ij
+      const R tA = t * FA;
+      sx += tA * wx;
+      sy += tA * wy;
+      sz += tA * wz;
+      sw2 += tA * w2;
+      sb += t * FB;
+      svw += tA * (Vi.x * wx + Vi.y * wy + Vi.z * wz);
+    }
+    double a0 = warp_sum<double>((double)sx), a1 = warp_sum<double>((double)sy), a2 = warp_sum<double>((double)sz);
+    double b0 = warp_sum<double>((double)sw2), b1 = warp_sum<double>((double)sb), b2 = warp_sum<double>((double)svw);
+    if (lane == 0) {
+      const double cA = (double)Kj.x, cB = (double)Kj.y;
+      const uint32_t c = G.perm[j];
+      out.acc[3 * (int64_t)c + 0] = cA * a0;
+      out.acc[3 * (int64_t)c + 1] = cA * a1;
+      out.acc[3 * (int64_t)c + 2] = cA * a2;
+      out.dudt[c] = cA * b0 - cB * b1;
+      if (out.e_exp) out.e_exp[j] = (double)Lj.w * (cB * b1 - cA * b2);
+    }
+  }
+}
+
+template <typename R>
+cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *row_ptr,
+                             const uint32_t *rows, const float4 *gtab, RunConst rc, MfOut out, cudaStream_t s,
+                             int64_t *launches) {
+  if (G.n <= 0) return cudaSuccess;
+  int64_t blocks = (G.n + MF_WARPS - 1) / MF_WARPS;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_meanfield<R><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, gtab, rc, out);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+template cudaError_t launch_meanfield<float>(SpeciesView<float>, SpeciesView<float>, BoxSplit, const int64_t *,
+                                             const uint32_t *, const float4 *, RunConst, MfOut, cudaStream_t, int64_t *);
+template cudaError_t launch_meanfield<double>(SpeciesView<double>, SpeciesView<double>, BoxSplit, const int64_t *,
+                                              const uint32_t *, const float4 *, RunConst, MfOut, cudaStream_t,
+                                              int64_t *);
+
+// ---- Monte Carlo: one warp per DM particle ---------------------------------------------
+// The sampled partner velocity v^B_ij = V_j + varsigma_j z (z from the pair's Philox block)
+// and P_ij = (M_j/mu_j) g_ij sigma(v_rel) v_rel dt.
+template <typename R>
+__device__ __forceinline__ R pair_probability(const typename Vec<R>::v4 &Pi, const typename Vec<R>::v4 &Li,
+                                              const typename Vec<R>::v4 &Vi, uint32_t id_i,
+                                              const typename Vec<R>::v4 &Pj, const typename Vec<R>::v4 &Lj,
+                                              const typename Vec<R>::v4 &Vj, const typename Vec<R>::v4 &Kj,
+                                              uint32_t id_j, const BoxSplit &bx, const float4 *gtab, int n,
+                                              R inv_v0, R dt, unsigned long long step, uint32_t k0, uint32_t k1,
+                                              R &rx, R &ry, R &rz, R &vrel) {
+  R dx, dy, dz;
+  pair_dx<R>(Pi, Li, Pj, Lj, bx, dx, dy, dz);
+  const R d = sqrt_t(dist2_rn<R>(dx, dy, dz));
+  const R g = overlap_g<R>(gtab, d, Pi.w, Pj.w);
+  const uint4 w = philox4x32_10(pair_counter(id_i, id_j, step), k0, k1);
+  R z0, z1, z2;
+  box_muller3<R>(w, z0, z1, z2);
+  const R sig = Vj.w;
+  rx = Vi.x - (Vj.x + sig * z0);
+  ry = Vi.y - (Vj.y + sig * z1);
+  rz = Vi.z - (Vj.z + sig * z2);
+  vrel = sqrt_t(rx * rx + ry * ry + rz * rz);
+  return Kj.z * dt * g * ipow<R>(vrel * inv_v0, n) * vrel;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(MC_WARPS * 32)
+k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict__ row_ptr,
+     const uint32_t *__restrict__ rows, const float4 *__restrict__ gtab, RunConst rc, McArgs a,
+     R *__restrict__ pcache) {
+  typedef typename Vec<R>::v4 v4;
+  __shared__ double red[MC_WARPS][8];
+  __shared__ float redm[MC_WARPS];
+  const unsigned lane = threadIdx.x & 31u;
+  const int wib = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * MC_WARPS;
+  const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+  const R inv_v0 = (R)(1.0 / rc.v0);
+  const R dt = (R)a.dt;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // lane 0 only: sum M dv (3), dKE, scat, clamp, band, sum P
+  float accm = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * MC_WARPS + wib; i < D.n; i += nwarps) {
+    const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
+    const uint32_t id_i = D.id[i];
+    const int64_t rs = row_ptr[i], re = row_ptr[i + 1];
+    U128 sum = {0ull, 0ull};
+    float rmax = 0.0f;
+    for (int64_t p = rs + lane; p < re; p += 32) {
+      const uint32_t j = rows[p];
+      const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
+      R rx, ry, rz, vr;
+      const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx, gtab, rc.n, inv_v0, dt, a.step,
+                                      k0, k1, rx, ry, rz, vr);
+      pcache[p] = P;
+      sum = u128_add(sum, to_fixed(P));
+      const R e = Kj.w;                                   // mu_j / (m_chi + mu_j)
+      const R cap = fmin((R)0.1, (R)1e-4 / (e * e));      // Eq. prob_criterion
+      rmax = fmaxf(rmax, (float)(P / cap));
+    }
+    const U128 C = warp_sum_u128(sum);
+    rmax = warp_max(rmax);
+    // selection uniform r_i = (k + 1/2) 2^-52, k the top 52 bits of (w0, w3): as a 64-bit fraction
+    const uint4 wd = philox4x32_10(dm_counter(id_i, a.step), k0, k1);
+    const unsigned long long k52 = ((unsigned long long)wd.x << 20) | (unsigned long long)(wd.w >> 12);
+    const unsigned long long R64 = (k52 << 12) | (1ull << 11);
+    const bool clamped = C.hi >= 1ull;                    // sum_j P_ij > 1: renormalise
+    U128 T;
+    if (clamped) T = u128_scale(R64, C); else { T.hi = 0ull; T.lo = R64; }
+    const bool scat = u128_lt(T, C);
+    const double Cd = fixed_to_double(C), Td = fixed_to_double(T);
+    bool band = Cd > 0.0 && fabs(Td - Cd) <= 1e-6 * Cd;
+    double dv0 = 0.0, dv1 = 0.0, dv2 = 0.0;
+    uint32_t partner_id = 0xffffffffu;
+    if (scat) {
+      // binary search over the gas-id bits for the first partner (ascending id) whose
+      // running sum exceeds T
+      uint32_t prefix = 0;
+      U128 base = {0ull, 0ull};
+      for (int b = a.id_bits - 1; b >= 0; --b) {
+        const uint32_t mid = prefix | (1u << b);
+        U128 S = {0ull, 0ull};
+        for (int64_t p = rs + lane; p < re; p += 32) {
+          const uint32_t idj = G.id[rows[p]];
+          if (idj >= prefix && idj < mid) S = u128_add(S, to_fixed(pcache[p]));
+        }
+        S = warp_sum_u128(S);
+        const U128 top = u128_add(base, S);
+        if (!u128_lt(T, top)) { base = top; prefix = mid; }
+      }
+      // the pair with that id
+      int64_t pstar = -1;
+      for (int64_t p0 = rs; p0 < re; p0 += 32) {
+        const int64_t p = p0 + lane;
+        const bool hit = p < re && G.id[rows[p]] == prefix;
+        const unsigned m = __ballot_sync(DMB_FULL, hit);
+        if (m) { pstar = p0 + __ffs(m) - 1; break; }
+      }
+      if (pstar >= 0) {
+        const uint32_t j = rows[pstar];
+        const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
+        R rx, ry, rz, vr;
+        const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx, gtab, rc.n, inv_v0, dt,
+                                        a.step, k0, k1, rx, ry, rz, vr);
+        const double lo = fixed_to_double(base), hi = lo + (double)pcache[pstar];
+        (void)P;
+        band = band || (fabs(Td - lo) <= 1e-6 * hi) || (fabs(Td - hi) <= 1e-6 * hi);
+        // isotropic new direction: cos(theta') = 2u - 1, phi' = 2 pi u'
+        const R ct = (R)2 * uniform23<R>(wd.y) - (R)1;
+        const R st = sqrt_t(fmax((R)0, (R)1 - ct * ct));
+        R sp, cp;
+        if (sizeof(R) == 4) { float s_, c_; sincospif(2.0f * (float)uniform23<float>(wd.z), &s_, &c_); sp = (R)s_; cp = (R)c_; }
+        else { double s_, c_; sincospi(2.0 * uniform23<double>(wd.z), &s_, &c_); sp = (R)s_; cp = (R)c_; }
+        const R f = Kj.w * vr;                             // mu_j/(m_chi + mu_j) v_rel
+        const R inv = (R)1 / vr;
+        dv0 = (double)(f * (st * cp - rx * inv));
+        dv1 = (double)(f * (st * sp - ry * inv));
+        dv2 = (double)(f * (ct - rz * inv));
+        partner_id = prefix;
+      }
+    }
+    if (lane == 0) {
+      const uint32_t c = D.perm[i];
+      const double v0 = a.vel_in[3 * (int64_t)c], v1 = a.vel_in[3 * (int64_t)c + 1], v2 = a.vel_in[3 * (int64_t)c + 2];
+      const double n0 = v0 + dv0, n1 = v1 + dv1, n2 = v2 + dv2;
+      a.vel_out[3 * (int64_t)c] = n0;
+      a.vel_out[3 * (int64_t)c + 1] = n1;
+      a.vel_out[3 * (int64_t)c + 2] = n2;
+      if (a.scattered) a.scattered[c] = (uint8_t)(partner_id != 0xffffffffu);
+      if (a.partner) a.partner[c] = partner_id;
+      if (a.p_ratio) a.p_ratio[c] = rmax;
+      if (a.p_total) a.p_total[c] = Cd;
+      const double M = (double)Li.w;
+      acc[0] += M * (n0 - v0);
+      acc[1] += M * (n1 - v1);
+      acc[2] += M * (n2 - v2);
+      acc[3] += 0.5 * M * ((n0 * n0 + n1 * n1 + n2 * n2) - (v0 * v0 + v1 * v1 + v2 * v2));
+      acc[4] += partner_id != 0xffffffffu ? 1.0 : 0.0;
+      acc[5] += clamped ? 1.0 : 0.0;
+      acc[6] += band ? 1.0 : 0.0;
+      acc[7] += Cd;
+      accm = fmaxf(accm, rmax);
+    }
+  }
+  if (lane == 0) {
+    for (int k = 0; k < 8; ++k) red[wib][k] = acc[k];
+    redm[wib] = accm;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    double s = 0.0;
+    for (int w = 0; w < MC_WARPS; ++w) s += red[w][threadIdx.x];
+    a.block_sums[8 * (int64_t)blockIdx.x + threadIdx.x] = s;
+  }
+  if (threadIdx.x == 0) {
+    float m = 0.0f;
+    for (int w = 0; w < MC_WARPS; ++w) m = fmaxf(m, redm[w]);
+    a.block_max[blockIdx.x] = (double)m;
+  }
+}
+
+template <typename R>
+cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *row_ptr, const uint32_t *rows,
+                      const float4 *gtab, RunConst rc, McArgs a, R *pcache, int blocks, cudaStream_t s,
+                      int64_t *launches) {
+  k_mc<R><<<blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+template cudaError_t launch_mc<float>(SpeciesView<float>, SpeciesView<float>, BoxSplit, const int64_t *,
+                                      const uint32_t *, const float4 *, RunConst, McArgs, float *, int, cudaStream_t,
+                                      int64_t *);
+template cudaError_t launch_mc<double>(SpeciesView<double>, SpeciesView<double>, BoxSplit, const int64_t *,
+                                       const uint32_t *, const float4 *, RunConst, McArgs, double *, int,
+                                       cudaStream_t, int64_t *);
+
+// ---- overlap table and debug evaluators ------------------------------------------------
+__global__ void k_gtable(float4 *__restrict__ T) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)DMB_GT_NQ * DMB_GT_CELLS) return;
+  const int j = (int)(t / DMB_GT_CELLS), i = (int)(t % DMB_GT_CELLS);
+  const double q = (double)j / (double)(DMB_GT_NQ - 1);
+  const double dd = 2.0 / (double)(DMB_GT_ND - 1);
+  float v[4];
+  for (int k = 0; k < 4; ++k) {
+    const int node = i - 1 + k;
+    const double delta = fabs((double)node * dd);   // node -1 mirrors node 1 (g is even in d)
+    v[k] = (float)overlap_G_exact(delta, q);
+  }
+  T[t] = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+cudaError_t launch_gtable(float4 *T, cudaStream_t s, int64_t *launches) {
+  const int64_t n = (int64_t)DMB_GT_NQ * DMB_GT_CELLS;
+  k_gtable<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(T);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+__global__ void k_debug_overlap(const float4 *T, int fp64, int64_t k, const double *in, double *out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= k) return;
+  const double d = in[3 * t], hi = in[3 * t + 1], hj = in[3 * t + 2];
+  if (fp64) out[t] = overlap_g<double>(T, d, hi, hj);
+  else out[t] = (double)overlap_g<float>(T, (float)d, (float)hi, (float)hj);
+}
+cudaError_t launch_debug_overlap(const float4 *T, int fp64, int64_t k, const double *in, double *out, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_debug_overlap<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(T, fp64, k, in, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_debug_rates(int fp64, int n, int64_t k, const double *in, double *out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= k) return;
+  if (fp64) {
+    double a, b;
+    rates_FAB<double>(in[t], n, a, b);
+    out[2 * t] = a;
+    out[2 * t + 1] = b;
+  } else {
+    float a, b;
+    rates_FAB<float>((float)in[t], n, a, b);
+    out[2 * t] = a;
+    out[2 * t + 1] = b;
+  }
+}
+cudaError_t launch_debug_rates(int fp64, int n, int64_t k, const double *in, double *out, cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_debug_rates<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(fp64, n, k, in, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_debug_philox(int64_t k, const uint32_t *ctr, uint32_t *out, unsigned long long seed) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= k) return;
+  const uint4 c = make_uint4(ctr[4 * t], ctr[4 * t + 1], ctr[4 * t + 2], ctr[4 * t + 3]);
+  const uint4 w = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  out[4 * t] = w.x;
+  out[4 * t + 1] = w.y;
+  out[4 * t + 2] = w.z;
+  out[4 * t + 3] = w.w;
+}
+cudaError_t launch_debug_philox(int64_t k, const uint32_t *ctr, uint32_t *out, unsigned long long seed,
+                                cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_debug_philox<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(k, ctr, out, seed);
+  return cudaGetLastError();
+}

@@ -1,0 +1,314 @@
+// Device physics of the interaction step: Philox streams, cubic-spline overlap integral,
+// Maxwellian-averaged rate integrals.
+#pragma once
+#include "common.cuh"
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Counter layouts: pair stream (id_i, id_j, step_lo, step_hi & 0x7fffffff);
+// DM stream (id_i, 0, step_lo, (step_hi & 0x7fffffff) | 0x80000000).
+__device__ __forceinline__ uint4 pair_counter(uint32_t id_dm, uint32_t id_gas, unsigned long long step) {
+  return make_uint4(id_dm, id_gas, (uint32_t)step, (uint32_t)(step >> 32) & 0x7fffffffu);
+}
+__device__ __forceinline__ uint4 dm_counter(uint32_t id_dm, unsigned long long step) {
+  return make_uint4(id_dm, 0u, (uint32_t)step, ((uint32_t)(step >> 32) & 0x7fffffffu) | 0x80000000u);
+}
+
+// u = ((w >> 9) + 1/2) 2^-23: exact in float, in (0, 1).
+template <typename R>
+__device__ __forceinline__ R uniform23(uint32_t w) {
+  return ((R)(w >> 9) + (R)0.5) * (R)1.1920928955078125e-07;
+}
+
+// Three standard normals by Box-Muller from the four words of one Philox block.
+template <typename R>
+__device__ __forceinline__ void box_muller3(uint4 w, R &z0, R &z1, R &z2);
+template <>
+__device__ __forceinline__ void box_muller3<float>(uint4 w, float &z0, float &z1, float &z2) {
+  const float u0 = uniform23<float>(w.x), u1 = uniform23<float>(w.y);
+  const float u2 = uniform23<float>(w.z), u3 = uniform23<float>(w.w);
+  const float r0 = sqrtf(-2.0f * logf(u0)), r2 = sqrtf(-2.0f * logf(u2));
+  float s1, c1, s3, c3;
+  sincospif(2.0f * u1, &s1, &c1);
+  sincospif(2.0f * u3, &s3, &c3);
+  z0 = r0 * c1;
+  z1 = r0 * s1;
+  z2 = r2 * c3;
+}
+template <>
+__device__ __forceinline__ void box_muller3<double>(uint4 w, double &z0, double &z1, double &z2) {
+  const double u0 = uniform23<double>(w.x), u1 = uniform23<double>(w.y);
+  const double u2 = uniform23<double>(w.z), u3 = uniform23<double>(w.w);
+  const double r0 = sqrt(-2.0 * log(u0)), r2 = sqrt(-2.0 * log(u2));
+  double s1, c1, s3, c3;
+  sincospi(2.0 * u1, &s1, &c1);
+  sincospi(2.0 * u3, &s3, &c3);
+  z0 = r0 * c1;
+  z1 = r0 * s1;
+  z2 = r2 * c3;
+}
+
+// ---- cubic-spline kernel and the overlap integral (Sec. 2.4; App. D) ---------------
+// w(u) = (8/pi) {1 - 6u^2 + 6u^3 (u <= 1/2); 2 (1-u)^3 (1/2 < u <= 1); 0}, W = w(r/h)/h^3.
+#define DMB_8_OVER_PI 2.5464790894703255
+
+__device__ __forceinline__ double spline_w(double u) {
+  if (u <= 0.5) return DMB_8_OVER_PI * (1.0 + u * u * (-6.0 + 6.0 * u));
+  if (u <= 1.0) { const double t = 1.0 - u; return DMB_8_OVER_PI * 2.0 * t * t * t; }
+  return 0.0;
+}
+
+// Mean of u w(u) over [y, x] (0 <= y <= x), given the exact width x - y.  On each piece
+// u w(u) = (8/pi) p'(u) with p(u) = u^2/2 - 3u^4/2 + 6u^5/5 (inner) or
+// u^2 - 2u^3 + 3u^4/2 - 2u^5/5 (outer); the difference p(x) - p(y) is written as
+// (x - y) sum_k c_k h_{k-1}(x, y), h the complete homogeneous polynomials, so no
+// cancellation occurs for narrow intervals.
+__device__ __forceinline__ double piece_quot(double x, double y, bool outer) {
+  const double h1 = x + y;
+  const double h2 = x * h1 + y * y;
+  const double h3 = x * h2 + y * y * y;
+  const double y2 = y * y;
+  const double h4 = x * h3 + y2 * y2;
+  if (!outer) return 0.5 * h1 - 1.5 * h3 + 1.2 * h4;
+  return h1 - 2.0 * h2 + 1.5 * h3 - 0.4 * h4;
+}
+__device__ __forceinline__ double mean_uw(double y, double x, double width) {
+  // the whole interval inside one piece (the usual case)
+  if (x <= 0.5) return DMB_8_OVER_PI * piece_quot(x, y, false);
+  if (y >= 1.0) return 0.0;
+  if (y >= 0.5 && x <= 1.0) return DMB_8_OVER_PI * piece_quot(x, y, true);
+  // split at 1/2 and 1
+  double acc = 0.0;
+  if (y < 0.5) acc += (0.5 - y) * piece_quot(0.5, y, false);
+  const double a = fmax(y, 0.5), b = fmin(x, 1.0);
+  if (b > a) acc += (b - a) * piece_quot(b, a, true);
+  return DMB_8_OVER_PI * acc / width;
+}
+
+// Normalised overlap G(delta, q) = g h_a^3 with h_a = max(h_i, h_j), q = h_b / h_a <= 1,
+// delta = d / h_a (App. D).  With the substitution t^2 = s^2 + delta^2 - 2 delta s c the
+// inner angular integral becomes 2 q J(s) / max(s, delta), J the mean of u w(u) over
+// [|s - delta|/q, (s + delta)/q], so
+//     G = (4 pi / q^2) int_0^1 ds s^2 w(s) J(s) / max(s, delta),
+// a piecewise polynomial of degree <= 9 between the breakpoints; 5-point Gauss-Legendre
+// on every piece is exact.  q = 0 gives the limit G = w(delta).
+static __device__ double overlap_G_exact(double delta, double q) {
+  if (delta >= 1.0 + q) return 0.0;
+  if (q <= 0.0) return spline_w(delta);
+  double b[12] = {0.0, 0.5, 1.0, delta, 0.5 * q - delta, q - delta, delta - 0.5 * q,
+                  delta + 0.5 * q, delta - q, delta + q, 0.5 * q, q};
+#pragma unroll
+  for (int k = 0; k < 12; ++k) b[k] = fmin(fmax(b[k], 0.0), 1.0);
+  // sorting network (odd-even transposition, fully unrolled so b stays in registers)
+#pragma unroll
+  for (int pass = 0; pass < 12; ++pass) {
+#pragma unroll
+    for (int k = (pass & 1); k + 1 < 12; k += 2) {
+      const double lo = fmin(b[k], b[k + 1]), hi = fmax(b[k], b[k + 1]);
+      b[k] = lo;
+      b[k + 1] = hi;
+    }
+  }
+  const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831, 0.9061798459386640};
+  const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889, 0.4786286704993665, 0.2369268850561891};
+  const double invq = 1.0 / q;
+  double total = 0.0;
+#pragma unroll
+  for (int k = 0; k < 11; ++k) {
+    const double l = b[k], r = b[k + 1];
+    if (r <= l) continue;
+    const double mid = 0.5 * (l + r), half = 0.5 * (r - l);
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const double s = mid + half * gx[m];
+      const double ws = spline_w(s);
+      const double y = fabs(s - delta) * invq, x = (s + delta) * invq;
+      const double width = 2.0 * fmin(s, delta) * invq;
+      double J;
+      if (width > 0.0) J = mean_uw(y, x, width);
+      else J = x * spline_w(x);                   // degenerate interval: u w(u) at u = s/q
+      acc += gw[m] * s * s * ws * J / fmax(s, delta);
+    }
+    total += half * acc;
+  }
+  return 4.0 * 3.141592653589793 * invq * invq * total;
+}
+
+// Overlap table: quads T[j][i] = (G_{i-1}, G_i, G_{i+1}, G_{i+2}) at q_j = j / (NQ - 1),
+// delta_i = i * DD; cubic Lagrange interpolation in both directions.
+#define DMB_GT_INV_DD 512.0f           // 1 / (2 / (ND - 1))
+#define DMB_GT_INV_DQ 512.0f           // 1 / (1 / (NQ - 1))
+
+__device__ __forceinline__ void lagrange4(float t, float &a, float &b, float &c, float &d) {
+  const float tm1 = t - 1.0f, tp1 = t + 1.0f, tm2 = t - 2.0f;
+  a = -t * tm1 * tm2 * (1.0f / 6.0f);
+  b = tp1 * tm1 * tm2 * 0.5f;
+  c = -tp1 * t * tm2 * 0.5f;
+  d = tp1 * t * tm1 * (1.0f / 6.0f);
+}
+
+__device__ __forceinline__ float overlap_G_table(const float4 *__restrict__ T, float delta, float q) {
+  float fd = delta * DMB_GT_INV_DD;
+  int i0 = (int)fd;
+  i0 = i0 > DMB_GT_CELLS - 1 ? DMB_GT_CELLS - 1 : i0;
+  const float td = fd - (float)i0;
+  float fq = q * DMB_GT_INV_DQ;
+  int j0 = (int)fq;
+  j0 = j0 < 1 ? 1 : (j0 > DMB_GT_NQ - 3 ? DMB_GT_NQ - 3 : j0);
+  const float tq = fq - (float)j0;
+  float wd0, wd1, wd2, wd3, wq0, wq1, wq2, wq3;
+  lagrange4(td, wd0, wd1, wd2, wd3);
+  lagrange4(tq, wq0, wq1, wq2, wq3);
+  const float4 *row = T + (size_t)(j0 - 1) * DMB_GT_CELLS + i0;
+  const float4 a = __ldg(row), b = __ldg(row + DMB_GT_CELLS), c = __ldg(row + 2 * DMB_GT_CELLS),
+               d = __ldg(row + 3 * DMB_GT_CELLS);
+  const float ga = wd0 * a.x + wd1 * a.y + wd2 * a.z + wd3 * a.w;
+  const float gb = wd0 * b.x + wd1 * b.y + wd2 * b.z + wd3 * b.w;
+  const float gc = wd0 * c.x + wd1 * c.y + wd2 * c.z + wd3 * c.w;
+  const float gd = wd0 * d.x + wd1 * d.y + wd2 * d.z + wd3 * d.w;
+  return fmaxf(wq0 * ga + wq1 * gb + wq2 * gc + wq3 * gd, 0.0f);
+}
+
+// g_ij for a pair at distance d (float32: table; float64: exact evaluator).
+template <typename R>
+__device__ __forceinline__ R overlap_g(const float4 *T, R d, R hi, R hj);
+template <>
+__device__ __forceinline__ float overlap_g<float>(const float4 *T, float d, float hi, float hj) {
+  const float ha = fmaxf(hi, hj), hb = fminf(hi, hj);
+  const float inv = 1.0f / ha;
+  const float delta = d * inv;
+  if (delta >= 2.0f) return 0.0f;
+  return overlap_G_table(T, delta, hb * inv) * inv * inv * inv;
+}
+template <>
+__device__ __forceinline__ double overlap_g<double>(const float4 *T, double d, double hi, double hj) {
+  const double ha = fmax(hi, hj), hb = fmin(hi, hj);
+  const double inv = 1.0 / ha;
+  return overlap_G_exact(d * inv, hb * inv) * inv * inv * inv;
+}
+
+// ---- rate integrals (App. B closed forms) --------------------------------------------
+// FA = 1F1(-(n+1)/2, 5/2; -x), FB = 1F1(-(n+3)/2, 3/2; -x), so that
+//   A = (alpha_n/3) (sigma0/v0^n) varsigma^(n+1) FA,  B = alpha_n (sigma0/v0^n) varsigma^(n+3) FB.
+// Even n: with c = (n+6)/2 (a positive integer), 1F1(b - c, b; -x) = G_b(c) where
+// G_b(c) = e^-x 1F1(c, b; x) obeys the three-term recurrence in c (DLMF 13.3.1)
+//   c G(c+1) = (2c - b + x) G(c) + (b - c) G(c-1),   G(0) = e^-x,
+//   G_{3/2}(1) = (sqrt(pi)/2) erf(sqrt x)/sqrt x,
+//   G_{5/2}(1) = (3/2) x^(-3/2) [(sqrt(pi)/2) erf(sqrt x) - sqrt(x) e^-x]   (DLMF 13.6.10),
+// used for x >= 1; below, the positive Kummer series e^-x sum (c)_k x^k / ((b)_k k!).
+// Odd n >= -1: 1F1 with a non-positive integer a is a polynomial (DLMF 13.2.7).
+// n = -3 (FA only): Kummer series up to x = 40, large-x expansion (DLMF 13.7.2) beyond.
+template <typename R> struct RateConst;
+template <> struct RateConst<float> { static constexpr int kSeries = 14; };
+template <> struct RateConst<double> { static constexpr int kSeries = 26; };
+
+__device__ __forceinline__ float erf_t(float x) { return erff(x); }
+__device__ __forceinline__ double erf_t(double x) { return erf(x); }
+__device__ __forceinline__ float exp_t(float x) { return expf(x); }
+__device__ __forceinline__ double exp_t(double x) { return exp(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float pow_t(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double pow_t(double x, double y) { return pow(x, y); }
+
+template <typename R>
+__device__ __forceinline__ R ipow(R x, int n) {
+  R r = (R)1;
+  R b = n < 0 ? (R)1 / x : x;
+  int m = n < 0 ? -n : n;
+  while (m) {
+    if (m & 1) r *= b;
+    b *= b;
+    m >>= 1;
+  }
+  return r;
+}
+
+// generic 1F1(a, b; -x) for b - a > 0 (slow path)
+template <typename R>
+__device__ R hyp1f1_neg_generic(R a, R b, R x) {
+  if (x <= (R)0) return (R)1;
+  if (x < (R)40) {
+    const R c = b - a;
+    R term = 1, sum = 1;
+    for (int k = 0; k < 400; ++k) {
+      term *= (c + k) * x / ((b + k) * (R)(k + 1));
+      sum += term;
+      if (term < sum * (R)1e-17 && (R)k > x) break;
+    }
+    return exp_t(-x) * sum;
+  }
+  const R e = (R)1 + a - b;
+  R term = 1, sum = 1, prev = (R)1e300;
+  for (int k = 0; k < 60; ++k) {
+    term *= (a + k) * (e + k) / ((R)(k + 1) * x);
+    const R at = term < 0 ? -term : term;
+    if (at == (R)0 || at > prev) break;
+    sum += term;
+    prev = at;
+    if (at < (R)1e-17 * (sum < 0 ? -sum : sum)) break;
+  }
+  return exp_t(lgamma(b) - lgamma(b - a)) * pow_t(x, -a) * sum;
+}
+
+template <typename R>
+__device__ __forceinline__ void rates_FAB(R x, int n, R &FA, R &FB) {
+  if ((n & 1) == 0) {
+    const int c = (n + 6) / 2;
+    if (x < (R)1) {
+      // positive Kummer series for both b = 5/2 and b = 3/2
+      R tA = 1, tB = 1, sA = 1, sB = 1;
+#pragma unroll
+      for (int k = 0; k < RateConst<R>::kSeries; ++k) {
+        const R f = (R)(c + k) * x / (R)(k + 1);
+        tA *= f / ((R)2.5 + (R)k);
+        tB *= f / ((R)1.5 + (R)k);
+        sA += tA;
+        sB += tB;
+      }
+      const R e = exp_t(-x);
+      FA = e * sA;
+      FB = e * sB;
+      return;
+    }
+    const R sx = sqrt_t(x), e = exp_t(-x);
+    const R ef = (R)0.88622692545275801 * erf_t(sx);   // (sqrt(pi)/2) erf(sqrt x)
+    R gA0 = e, gA1 = (R)1.5 * (ef - sx * e) / (x * sx);
+    R gB0 = e, gB1 = ef / sx;
+    for (int k = 1; k < c; ++k) {
+      const R gA2 = (((R)(2 * k) - (R)2.5 + x) * gA1 + ((R)2.5 - (R)k) * gA0) / (R)k;
+      const R gB2 = (((R)(2 * k) - (R)1.5 + x) * gB1 + ((R)1.5 - (R)k) * gB0) / (R)k;
+      gA0 = gA1; gA1 = gA2;
+      gB0 = gB1; gB1 = gB2;
+    }
+    FA = gA1;
+    FB = gB1;
+    return;
+  }
+  if (n >= -1) {
+    // terminating series: sum_{k=0}^{m} (a)_k (-x)^k / ((b)_k k!)
+    const int mA = (n + 1) / 2, mB = (n + 3) / 2;
+    R t = 1, s = 1;
+    for (int k = 0; k < mA; ++k) { t *= (R)(-mA + k) * (-x) / (((R)2.5 + (R)k) * (R)(k + 1)); s += t; }
+    FA = s;
+    t = 1; s = 1;
+    for (int k = 0; k < mB; ++k) { t *= (R)(-mB + k) * (-x) / (((R)1.5 + (R)k) * (R)(k + 1)); s += t; }
+    FB = s;
+    return;
+  }
+  // n = -3: FB = 1F1(0, 3/2; -x) = 1; FA = 1F1(1, 5/2; -x)
+  FB = (R)1;
+  FA = hyp1f1_neg_generic<R>((R)1, (R)2.5, x);
+}

@@ -1,0 +1,224 @@
+"""Thin ctypes binding of libdmb.so (the C ABI declared in include/dmb.h).
+
+Argument marshalling only: every step of the interaction runs in the library's CUDA
+kernels.  Device arrays are passed as torch CUDA tensors (float64 / uint32 / uint8 /
+float32, contiguous); host outputs come back as Python values or numpy arrays.
+There is no CPU fallback: if the library cannot be loaded every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdmb.so")
+
+DMB_OK, DMB_ERR_ARG, DMB_ERR_CUDA, DMB_ERR_OOM, DMB_ERR_TIMEOUT, DMB_ERR_DOMAIN, DMB_ERR_STATE = range(7)
+DMB_RATE_CLOSED, DMB_RATE_QUAD, DMB_RATE_MLP = range(3)
+NO_PARTNER = 0xFFFFFFFF
+STATUS_NAMES = {0: "DMB_OK", 1: "DMB_ERR_ARG", 2: "DMB_ERR_CUDA", 3: "DMB_ERR_OOM", 4: "DMB_ERR_TIMEOUT",
+                5: "DMB_ERR_DOMAIN", 6: "DMB_ERR_STATE"}
+
+EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb_neighbors", "dmb_meanfield_gas",
+           "dmb_mc_scatter_dm", "dmb_step", "dmb_debug_overlap", "dmb_debug_rates", "dmb_debug_philox",
+           "dmb_launch_count"]
+
+
+class DmbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("sigma0_cm2", ctypes.c_double), ("v0_kms", ctypes.c_double), ("n", ctypes.c_int32),
+                ("periodic", ctypes.c_int32), ("m_chi_mp", ctypes.c_double), ("box", ctypes.c_double * 3),
+                ("rate_mode", ctypes.c_int32), ("fp64", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class DM(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("mass", ctypes.c_void_p),
+                ("h", ctypes.c_void_p), ("id", ctypes.c_void_p)]
+
+
+class Gas(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("mass", ctypes.c_void_p),
+                ("h", ctypes.c_void_p), ("T", ctypes.c_void_p), ("mu", ctypes.c_void_p), ("id", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libdmb.so once; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2603_24688_gb300.build`")
+    lib = ctypes.CDLL(path)
+    c = ctypes
+    vp, i64, u64, dbl = c.c_void_p, c.c_int64, c.c_uint64, c.c_double
+    sig = {
+        "dmb_create": ([c.POINTER(vp), c.POINTER(Params), vp], c.c_int),
+        "dmb_destroy": ([vp], c.c_int),
+        "dmb_last_error": ([vp], c.c_char_p),
+        "dmb_build_grid": ([vp, c.POINTER(DM), c.POINTER(Gas)], c.c_int),
+        "dmb_neighbors": ([vp, c.POINTER(i64), vp, i64], c.c_int),
+        "dmb_meanfield_gas": ([vp, vp, vp], c.c_int),
+        "dmb_mc_scatter_dm": ([vp, u64, dbl, vp, vp, vp, vp, vp], c.c_int),
+        "dmb_step": ([vp, c.POINTER(DM), c.POINTER(Gas), u64, dbl, vp], c.c_int),
+        "dmb_debug_overlap": ([vp, i64, vp, vp], c.c_int),
+        "dmb_debug_rates": ([vp, i64, vp, vp], c.c_int),
+        "dmb_debug_philox": ([vp, i64, vp, vp], c.c_int),
+        "dmb_launch_count": ([vp], i64),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda:
+        raise ValueError("device arrays must be CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("device arrays must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns a dmb_ctx.  Methods mirror the C entry points with the same names."""
+
+    def __init__(self, sigma0_cm2, n, m_chi_mp, v0_kms=100.0, periodic=False, box=(0.0, 0.0, 0.0), seed=0,
+                 fp64=False, rate_mode=DMB_RATE_CLOSED, stream=None):
+        import torch
+        self.lib = load()
+        p = Params()
+        p.sigma0_cm2 = float(sigma0_cm2)
+        p.v0_kms = float(v0_kms)
+        p.n = int(n)
+        p.periodic = 1 if periodic else 0
+        p.m_chi_mp = float(m_chi_mp)
+        for k in range(3):
+            p.box[k] = float(box[k])
+        p.rate_mode = int(rate_mode)
+        p.fp64 = 1 if fp64 else 0
+        p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        self.params = p
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = self.lib.dmb_create(ctypes.byref(h), ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream))
+        if st != DMB_OK:
+            raise DmbError(st, self.lib.dmb_last_error(None).decode())
+        self.h = h
+        self._keep = []
+
+    @classmethod
+    def from_params(cls, params, fp64=False, stream=None):
+        return cls(params["sigma0_cm2"], params["n"], params["m_chi_mp"], params["v0_kms"], params["periodic"],
+                   tuple(params["box"]), params["seed"], fp64=fp64, stream=stream)
+
+    def _check(self, st):
+        if st != DMB_OK:
+            raise DmbError(st, self.lib.dmb_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.dmb_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def dm_struct(dm):
+        import torch
+        s = DM()
+        s.n = int(dm["h"].numel())
+        s.pos = _ptr(dm["pos"], torch.float64)
+        s.vel = _ptr(dm["vel"], torch.float64)
+        s.mass = _ptr(dm["mass"], torch.float64)
+        s.h = _ptr(dm["h"], torch.float64)
+        s.id = _ptr(dm["id"], torch.int32)
+        return s
+
+    @staticmethod
+    def gas_struct(gas):
+        import torch
+        s = Gas()
+        s.n = int(gas["h"].numel())
+        s.pos = _ptr(gas["pos"], torch.float64)
+        s.vel = _ptr(gas["vel"], torch.float64)
+        s.mass = _ptr(gas["mass"], torch.float64)
+        s.h = _ptr(gas["h"], torch.float64)
+        s.T = _ptr(gas["T"], torch.float64)
+        s.mu = _ptr(gas["mu"], torch.float64)
+        s.id = _ptr(gas["id"], torch.int32)
+        return s
+
+    def dmb_build_grid(self, dm, gas):
+        self._dm_s, self._gas_s = self.dm_struct(dm), self.gas_struct(gas)
+        self._keep = [dm, gas]
+        self._check(self.lib.dmb_build_grid(self.h, ctypes.byref(self._dm_s), ctypes.byref(self._gas_s)))
+
+    def dmb_neighbors(self, pairs_out=None):
+        n = ctypes.c_int64()
+        cap = 0 if pairs_out is None else pairs_out.numel() // 2
+        import torch
+        self._check(self.lib.dmb_neighbors(self.h, ctypes.byref(n), _ptr(pairs_out, torch.int32), cap))
+        return n.value
+
+    def dmb_meanfield_gas(self, acc, dudt):
+        import torch
+        self._check(self.lib.dmb_meanfield_gas(self.h, _ptr(acc, torch.float64), _ptr(dudt, torch.float64)))
+
+    def dmb_mc_scatter_dm(self, step, dt, vel_out, scattered=None, partner=None, p_ratio_max=None, p_total=None):
+        import torch
+        self._check(self.lib.dmb_mc_scatter_dm(self.h, int(step), float(dt), _ptr(vel_out, torch.float64),
+                                               _ptr(scattered, torch.uint8), _ptr(partner, torch.int32),
+                                               _ptr(p_ratio_max, torch.float32), _ptr(p_total, torch.float64)))
+
+    def dmb_step(self, dm, gas, step, dt, want_sums=True):
+        d, g = self.dm_struct(dm), self.gas_struct(gas)
+        sums = (ctypes.c_double * 16)()
+        self._check(self.lib.dmb_step(self.h, ctypes.byref(d), ctypes.byref(g), int(step), float(dt),
+                                      sums if want_sums else None))
+        return np.array(sums[:]) if want_sums else None
+
+    def dmb_debug_overlap(self, inp, out):
+        import torch
+        self._check(self.lib.dmb_debug_overlap(self.h, inp.shape[0], _ptr(inp, torch.float64), _ptr(out, torch.float64)))
+
+    def dmb_debug_rates(self, inp, out):
+        import torch
+        self._check(self.lib.dmb_debug_rates(self.h, inp.shape[0], _ptr(inp, torch.float64), _ptr(out, torch.float64)))
+
+    def dmb_debug_philox(self, ctr, out):
+        import torch
+        self._check(self.lib.dmb_debug_philox(self.h, ctr.shape[0], _ptr(ctr, torch.int32), _ptr(out, torch.int32)))
+
+    def dmb_launch_count(self):
+        return int(self.lib.dmb_launch_count(self.h))
+
+
+def to_device(particles, device="cuda"):
+    """numpy particle dict (workloads format) -> dict of CUDA tensors (ids as int32 bit patterns)."""
+    import torch
+    out = {}
+    for k, v in particles.items():
+        if k == "id":
+            out[k] = torch.from_numpy(np.asarray(v, dtype=np.uint32).view(np.int32).copy()).to(device)
+        else:
+            out[k] = torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).to(device)
+    return out
