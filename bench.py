@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the hybrid DM-baryon interaction step on GB300.
+
+One step = the whole hot path on one synthetic galaxy: Morton grid, pair search in both
+directions, gas mean field, DM Monte Carlo, kicks and float64 sums (dmb_step through the
+C ABI).  Workload: 8M DM in a Hernquist halo + 2M gas in an exponential disk
+(`galaxy10M`), sigma = sigma0 (v/100 km/s)^n.
+
+Metric: DM-gas pair interactions per second (pairs of the step / step time); the line also
+reports particles stepped per second.  `value` is device-resident throughput (inputs in
+HBM); `e2e` repeats the step through the same C ABI with the inputs copied from pinned
+host memory and the results copied back inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dmb|reference] [--n 0]
+
+--impl reference times the FP64 oracle (the method's plain CPU restatement) on bounded
+spatial samples of the same workload.  Under torchrun every rank runs an independent
+replica (the step does not shard across GPUs in this build).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# measured on this GPU model (152 SMs, 128 FP32 lanes per SM): lane operations per clock
+SMS = 152
+LANES = 128
+# algorithmic lane operations per pair (FMA = 1 op, special functions = 1 op), counted from
+# the formulas each kernel evaluates; see DESIGN.md "Rooflines"
+OPS_PER_PAIR = {"meanfield": 150.0, "mc": 256.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dmb", choices=["dmb", "reference"])
+    ap.add_argument("--workload", default="galaxy10M")
+    ap.add_argument("--n", type=int, default=0, help="power-law index of sigma(v)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def make_workload(name, n, seed_offset=0):
+    from paper_2603_24688_gb300 import workloads as W
+    if name == "galaxy10M":
+        return W.galaxy_workload(8_000_000, 2_000_000, seed=W.SEED_BASE + 3 + seed_offset, n=n)
+    if name == "galaxy1M":
+        return W.galaxy_workload(1_000_000, 1_000_000, seed=W.SEED_BASE + 2 + seed_offset, n=n)
+    if name == "box4k":
+        return W.box_workload(seed=W.SEED_BASE + 1 + seed_offset, n=n)
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                   parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(w, budget_s=12.0, target_pairs=150_000, seed=0):
+    """Time the FP64 oracle's full step on a spatial sub-box of the workload.
+
+    The sub-box is a cube around a random gas particle, sized so that it holds about
+    target_pairs pairs; returns (pairs/s, pairs, seconds, description)."""
+    from oracle.pairs import pairs_bruteforce
+    from oracle.step import oracle_step
+    rng = np.random.default_rng(seed)
+    dm, gas = w["dm"], w["gas"]
+    c = gas["pos"][rng.integers(len(gas["h"]))]
+    side = 4.0 * float(np.median(gas["h"]))
+    for _ in range(30):
+        sd = np.all(np.abs(dm["pos"] - c) < side / 2, axis=1)
+        sg = np.all(np.abs(gas["pos"] - c) < side / 2, axis=1)
+        if sd.sum() * sg.sum() > 0:
+            sub_dm = {k: v[sd] for k, v in dm.items()}
+            sub_gas = {k: v[sg] for k, v in gas.items()}
+            pi, pj = pairs_bruteforce(sub_dm, sub_gas, w["params"]["periodic"], w["params"]["box"])
+            if len(pi) >= target_pairs or side > 50:
+                break
+        side *= 1.3
+    t0 = time.perf_counter()
+    out = oracle_step(sub_dm, sub_gas, w["params"], 0, w["dt"], pairs=(pi, pj))
+    t = time.perf_counter() - t0
+    # the pair search is part of the oracle step: time it too
+    t1 = time.perf_counter()
+    pairs_bruteforce(sub_dm, sub_gas, w["params"]["periodic"], w["params"]["box"])
+    t += time.perf_counter() - t1
+    n = len(pi)
+    desc = (f"oracle_step on a {side:.3f} kpc cube of {w['name']} ({len(sub_dm['h'])} DM, "
+            f"{len(sub_gas['h'])} gas, {n} pairs), single numpy thread")
+    return n / t, n, t, desc
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = make_workload(a.workload, a.n)
+    vals = []
+    for k in range(a.warmup + a.steps):
+        rate, npairs, t, desc = cpu_oracle_sample(w, target_pairs=60_000, seed=k)
+        if k >= a.warmup:
+            vals.append((rate, npairs, t))
+    rate = sum(v[1] for v in vals) / sum(v[2] for v in vals)
+    line = {"metric": "pair_interactions_per_s", "value": rate, "unit": "pairs/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(v[2] for v in vals) / len(vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": a.workload + f" (bounded spatial samples), n={a.n}", "rate_provider": "closed"},
+            "cpu_baseline": {"value": rate, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": rate, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+    from paper_2603_24688_gb300 import build, dmb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    peaks, peak_kind = load_peaks()
+
+    w = make_workload(a.workload, a.n, seed_offset=rank)
+    dm = dmb.to_device(w["dm"])
+    gas = dmb.to_device(w["gas"])
+    stream = torch.cuda.current_stream()
+    ctx = dmb.Context.from_params(w["params"], stream=stream)
+    dt = w["dt"]
+    step = 0
+    sums = None
+    for _ in range(a.warmup):
+        sums = ctx.dmb_step(dm, gas, step, dt)
+        step += 1
+    torch.cuda.synchronize()
+    npairs = int(sums[12]) if sums is not None else 0
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region --------------------------------------------------
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if rank == 0 else None
+    ctx.dmb_set_timing(True)
+    launches0 = ctx.dmb_launch_count()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pairs_total = 0
+    for _ in range(a.steps):
+        sums = ctx.dmb_step(dm, gas, step, dt)
+        pairs_total += int(sums[12])
+        step += 1
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.dmb_launch_count() - launches0
+    stage_ms, nsteps = ctx.dmb_stage_times()
+    ctx.dmb_set_timing(False)
+    clk = clocks.stop() if clocks else None
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    pt = torch.tensor([float(pairs_total)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(pt, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    value = float(pt.item()) / (ms_max * 1e-3)
+    nparticles = len(w["dm"]["h"]) + len(w["gas"]["h"])
+
+    # ---- roofline of the dominant kernel ----------------------------------------------
+    names = ["grid", "search", "meanfield", "mc", "kick"]
+    per_step = stage_ms[:5] / max(nsteps, 1)
+    dom = int(np.argmax(per_step))
+    kern = {"grid": "k_radix_scatter+k_gather+k_morton", "search": "k_pair_search",
+            "meanfield": "k_meanfield", "mc": "k_mc", "kick": "k_kick_gas"}[names[dom]]
+    roof = None
+    fmax_ghz = peaks.get("sm_max_mhz", 2070.0) / 1e3
+    alu_peak = SMS * LANES * fmax_ghz * 1e9 / 1e12          # T lane-ops/s
+    if names[dom] in OPS_PER_PAIR:
+        ach = OPS_PER_PAIR[names[dom]] * npairs / (per_step[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s", "frac": ach / alu_peak,
+                "traffic": None, "kernel": kern,
+                "peak_source": "152 SMs x 128 FP32/INT lanes x max SM clock (unit counts, not measured)"}
+    stages = {n: float(v) for n, v in zip(names, per_step)}
+    for n in ("meanfield", "mc"):
+        stages[n + "_frac_alu"] = OPS_PER_PAIR[n] * npairs / (per_step[names.index(n)] * 1e-3) / 1e12 / alu_peak
+
+    # ---- end to end through the C ABI with host buffers ---------------------------------
+    e2e = None
+    if a.e2e_steps > 0:
+        host = {}
+        for sp, src in (("dm", dm), ("gas", gas)):
+            host[sp] = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in src.items()}
+            for k, v in src.items():
+                host[sp][k].copy_(v)
+        out_host = {"dm_vel": torch.empty_like(dm["vel"], device="cpu").pin_memory(),
+                    "gas_vel": torch.empty_like(gas["vel"], device="cpu").pin_memory(),
+                    "gas_T": torch.empty_like(gas["T"], device="cpu").pin_memory()}
+        h2d = sum(v.numel() * v.element_size() for sp in host.values() for v in sp.values())
+        d2h = sum(v.numel() * v.element_size() for v in out_host.values()) + 16 * 8
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(a.e2e_steps):
+            for sp, dst in (("dm", dm), ("gas", gas)):
+                for k, v in dst.items():
+                    v.copy_(host[sp][k], non_blocking=True)
+            ctx.dmb_step(dm, gas, step, dt)
+            step += 1
+            out_host["dm_vel"].copy_(dm["vel"], non_blocking=True)
+            out_host["gas_vel"].copy_(gas["vel"], non_blocking=True)
+            out_host["gas_T"].copy_(gas["T"], non_blocking=True)
+        f1.record(stream)
+        barrier()
+        ms_e = f0.elapsed_time(f1)
+        te = torch.tensor([ms_e], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": npairs * world * a.e2e_steps / (float(te.item()) * 1e-3), "unit": "pairs/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": float(te.item()) / a.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        rate, n_s, t_s, desc = cpu_oracle_sample(w)
+        cpu = {"value": rate, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": "pair_interactions_per_s", "value": value, "unit": "pairs/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 sums", "data": "synthetic",
+                "config": {"workload": f"{a.workload}: {len(w['dm']['h'])} DM Hernquist halo + "
+                                       f"{len(w['gas']['h'])} gas exponential disk, sigma0=1e-24 cm^2, n={a.n}",
+                           "rate_provider": "closed-form 1F1", "pairs_per_step": npairs,
+                           "l2": "inputs (~1 GB) larger than L2; no flush", "parallelism": f"replicas x{world}"},
+                "particles_stepped_per_s": nparticles * world / (ms_max * 1e-3 / a.steps),
+                "stage_ms": stages, "gpu_launches": int(launches), "roofline": roof, "peak_kind": peak_kind,
+                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

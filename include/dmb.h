@@ -161,6 +161,22 @@ dmb_status dmb_debug_rates(dmb_ctx *ctx, int64_t k, const double *in, double *ou
  * out: device [k][4] uint32 with key = params.seed. */
 dmb_status dmb_debug_philox(dmb_ctx *ctx, int64_t k, const uint32_t *ctr, uint32_t *out);
 
+/* Stage timing of dmb_step with CUDA events recorded on the context stream (adds one
+ * event synchronisation per step).  on = 0 disables it.  Resets the accumulators. */
+dmb_status dmb_set_timing(dmb_ctx *ctx, int on);
+
+/* Accumulated stage times since dmb_set_timing or the last call, in ms (host [8]):
+ * [0] grid (frame, keys, sort, gather, tree)  [1] pair search (count, scan, emit, both
+ * directions)  [2] mean field  [3] Monte Carlo  [4] kicks and sums  [5..7] 0.
+ * steps_out (host, may be NULL): steps timed.  Resets the accumulators. */
+dmb_status dmb_stage_times(dmb_ctx *ctx, double *ms_out, int64_t *steps_out);
+
+/* Work counters of the last dmb_neighbors (host [16] uint64).  [0..3] gas-major search,
+ * [4..7] DM-major search, each: tree nodes visited (stage 1), target leaves tiled
+ * (stage 2 count pass), candidate pair tests after the ballot filter (count pass), 0.
+ * Synchronises. */
+dmb_status dmb_search_stats(dmb_ctx *ctx, uint64_t *out16);
+
 /* Number of kernel launches the context has issued since creation (bench accounting). */
 int64_t dmb_launch_count(const dmb_ctx *ctx);
 

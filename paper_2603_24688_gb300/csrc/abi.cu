@@ -29,7 +29,14 @@ std::string g_create_error;
 struct SpeciesBufs {
   DevBuf keys0, keys1, vals0, vals1, P, L, V, K, sid, bmin, bmax;
   int64_t n = 0;
-  int nleaf = 0, p2 = 0;
+  int levels = 0, nodes = 0;
+  int off[DMB_MAX_LEVELS] = {0}, cnt[DMB_MAX_LEVELS] = {0};
+};
+
+// Pair-search scratch of one direction (queries of one species against the other's tree).
+struct SearchBufs {
+  DevBuf item_cnt, item_ptr, items, unit_cnt_leaf, unit_ptr, unit_leaf, unit_item0, unit_cnt, counts, row_ptr, rows;
+  int64_t n_items = 0, n_units = 0, n_pairs = 0;
 };
 
 struct dmb_ctx {
@@ -43,9 +50,10 @@ struct dmb_ctx {
   DevBuf frame, status, frame_part, gtab;
   SpeciesBufs dm, gas;
   DevBuf hist, hist_scan, scan_tmp;
-  DevBuf counts, gas_rowptr, gas_rows, dm_rowptr, dm_rows, pcache;
+  SearchBufs sg, sd;   // gas-major (gas queries, DM tree) and DM-major searches
+  DevBuf pcache;
   DevBuf mf_acc, mf_dudt, e_exp, mc_blocks, mc_max, kick_blocks, sums;
-  DevBuf scratch_vel;
+  DevBuf scratch_vel, search_stats;
   uint32_t *h_status = nullptr;   // pinned
   int64_t *h_tot = nullptr;       // pinned [2]
   double *h_sums = nullptr;       // pinned [16]
@@ -53,6 +61,11 @@ struct dmb_ctx {
   bool grid_ready = false, pairs_ready = false;
   int64_t n_pairs = 0;
   const double *dm_vel = nullptr;   // caller DM velocities of the last build
+  // optional stage timing with CUDA events on the context stream
+  bool timing = false;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t timed_steps = 0;
 };
 
 namespace {
@@ -113,19 +126,18 @@ SpeciesView<R> view(const SpeciesBufs &s) {
   v.perm = ptr<uint32_t>(s.vals0);
   v.bmin = ptr<float4>(s.bmin);
   v.bmax = ptr<float4>(s.bmax);
-  v.nleaf = s.nleaf;
-  v.p2 = s.p2;
+  v.levels = s.levels;
+  for (int k = 0; k < DMB_MAX_LEVELS; ++k) { v.off[k] = s.off[k]; v.cnt[k] = s.cnt[k]; }
   return v;
 }
 
 dmb_status ensure_species(dmb_ctx *ctx, SpeciesBufs &s, int64_t n, bool gas) {
   const size_t v4b = ctx->p.fp64 ? 32 : 16;
   s.n = n;
-  s.nleaf = (int)((n + DMB_LEAF - 1) / DMB_LEAF);
-  s.p2 = next_pow2(s.nleaf > 0 ? s.nleaf : 1);
+  s.nodes = tree_layout(n, &s.levels, s.off, s.cnt);
   bool ok = ensure(s.keys0, n * 8) && ensure(s.keys1, n * 8) && ensure(s.vals0, n * 4) && ensure(s.vals1, n * 4) &&
             ensure(s.P, n * v4b) && ensure(s.L, n * v4b) && ensure(s.V, n * v4b) && ensure(s.sid, n * 4) &&
-            ensure(s.bmin, (size_t)2 * s.p2 * 16 + 16) && ensure(s.bmax, (size_t)2 * s.p2 * 16 + 16);
+            ensure(s.bmin, (size_t)s.nodes * 16) && ensure(s.bmax, (size_t)s.nodes * 16);
   if (gas) ok = ok && ensure(s.K, n * v4b);
   else ok = ok && ensure(s.K, 64);
   if (!ok) return fail(ctx, DMB_ERR_OOM, "device allocation failed for particle buffers");
@@ -193,7 +205,7 @@ dmb_status build_grid_impl(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
          "gather");
     }
     CK(launch_tree<R>(ptr<typename Vec<R>::v4>(b.P), ptr<typename Vec<R>::v4>(b.L), b.n, fr, ptr<float4>(b.bmin),
-                      ptr<float4>(b.bmax), b.p2, s, L), "tree");
+                      ptr<float4>(b.bmax), b.levels, b.off, b.cnt, s, L), "tree");
   }
   ctx->dm_vel = dm->vel;
   ctx->grid_ready = true;
@@ -202,38 +214,100 @@ dmb_status build_grid_impl(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
 }
 
 // ---- neighbours --------------------------------------------------------------------------
+// Stage 1 (candidate leaves) and the unit layout for one direction; needs no host sizes.
+template <typename R>
+dmb_status search_stage1_count(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, SpeciesView<R> O,
+                               unsigned long long *stats) {
+  cudaStream_t s = ctx->stream;
+  int64_t *L = &ctx->launches;
+  const int nleaf = Q.cnt[0];
+  if (!ensure(sb.item_cnt, (size_t)nleaf * 4) || !ensure(sb.item_ptr, (size_t)(nleaf + 1) * 8) ||
+      !ensure(sb.unit_cnt_leaf, (size_t)nleaf * 4) || !ensure(sb.unit_ptr, (size_t)(nleaf + 1) * 8) ||
+      !ensure(sb.counts, (size_t)(Q.n + 1) * 4) || !ensure(sb.row_ptr, (size_t)(Q.n + 1) * 8))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for search offsets");
+  const Frame *fr = ptr<Frame>(ctx->frame);
+  uint32_t *status = ptr<uint32_t>(ctx->status);
+  CK(launch_leaf_pairs<R>(Q, O, ctx->bx, fr, false, ptr<uint32_t>(sb.item_cnt), nullptr, nullptr, status, stats, s, L),
+     "leaf pairs (count)");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(sb.item_cnt), ptr<int64_t>(sb.item_ptr), nleaf, ptr<int64_t>(ctx->scan_tmp),
+                            s, L), "scan");
+  CK(launch_unit_counts(ptr<int64_t>(sb.item_ptr), nleaf, ptr<uint32_t>(sb.unit_cnt_leaf), s, L), "unit counts");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(sb.unit_cnt_leaf), ptr<int64_t>(sb.unit_ptr), nleaf,
+                            ptr<int64_t>(ctx->scan_tmp), s, L), "scan");
+  return DMB_OK;
+}
+
+template <typename R>
+dmb_status search_stage2_count(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, SpeciesView<R> O,
+                               unsigned long long *stats) {
+  cudaStream_t s = ctx->stream;
+  int64_t *L = &ctx->launches;
+  const int nleaf = Q.cnt[0];
+  if (!ensure(sb.items, (size_t)sb.n_items * 4) || !ensure(sb.unit_leaf, (size_t)sb.n_units * 4) ||
+      !ensure(sb.unit_item0, (size_t)sb.n_units * 8) || !ensure(sb.unit_cnt, (size_t)sb.n_units * 32 * 4))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for search lists");
+  const Frame *fr = ptr<Frame>(ctx->frame);
+  uint32_t *status = ptr<uint32_t>(ctx->status);
+  CK(launch_leaf_pairs<R>(Q, O, ctx->bx, fr, true, nullptr, ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), status,
+                          nullptr, s, L), "leaf pairs (emit)");
+  CK(launch_unit_map(ptr<int64_t>(sb.item_ptr), ptr<int64_t>(sb.unit_ptr), nleaf, ptr<uint32_t>(sb.unit_leaf),
+                     ptr<int64_t>(sb.unit_item0), s, L), "unit map");
+  CK(launch_tile<R>(Q, O, ctx->bx, fr, false, ptr<uint32_t>(sb.unit_leaf), ptr<int64_t>(sb.unit_item0),
+                    ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), sb.n_units, ptr<uint32_t>(sb.unit_cnt), nullptr,
+                    nullptr, status, stats, s, L), "tile (count)");
+  CK(launch_unit_prefix(ptr<int64_t>(sb.unit_ptr), nleaf, Q.n, ptr<uint32_t>(sb.unit_cnt), ptr<uint32_t>(sb.counts), s,
+                        L), "unit prefix");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(sb.counts), ptr<int64_t>(sb.row_ptr), Q.n, ptr<int64_t>(ctx->scan_tmp), s, L),
+     "scan");
+  return DMB_OK;
+}
+
+template <typename R>
+dmb_status search_stage2_emit(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, SpeciesView<R> O) {
+  if (!ensure(sb.rows, (size_t)sb.n_pairs * 4)) return fail(ctx, DMB_ERR_OOM, "device allocation failed for pair lists");
+  CK(launch_tile<R>(Q, O, ctx->bx, ptr<Frame>(ctx->frame), true, ptr<uint32_t>(sb.unit_leaf),
+                    ptr<int64_t>(sb.unit_item0), ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), sb.n_units,
+                    ptr<uint32_t>(sb.unit_cnt), ptr<int64_t>(sb.row_ptr), ptr<uint32_t>(sb.rows),
+                    ptr<uint32_t>(ctx->status), nullptr, ctx->stream, &ctx->launches), "tile (emit)");
+  return DMB_OK;
+}
+
 template <typename R>
 dmb_status neighbors_impl(dmb_ctx *ctx) {
   cudaStream_t s = ctx->stream;
-  int64_t *L = &ctx->launches;
   const SpeciesView<R> D = view<R>(ctx->dm), G = view<R>(ctx->gas);
-  const Frame *fr = ptr<Frame>(ctx->frame);
-  uint32_t *status = ptr<uint32_t>(ctx->status);
   const int64_t nmax = D.n > G.n ? D.n : G.n;
-  if (!ensure(ctx->counts, (nmax + 1) * 4 * 2) || !ensure(ctx->gas_rowptr, (G.n + 1) * 8) ||
-      !ensure(ctx->dm_rowptr, (D.n + 1) * 8))
-    return fail(ctx, DMB_ERR_OOM, "device allocation failed for pair offsets");
   dmb_status st;
-  if ((st = ensure_sort_scratch(ctx, nmax)) != DMB_OK) return st;
-  uint32_t *cg = ptr<uint32_t>(ctx->counts), *cd = cg + (nmax + 1);
-  CK(launch_pair_search<R>(G, D, ctx->bx, fr, false, cg, nullptr, nullptr, status, s, L), "pair count (gas)");
-  CK(exclusive_scan_u32_i64(cg, ptr<int64_t>(ctx->gas_rowptr), G.n, ptr<int64_t>(ctx->scan_tmp), s, L), "scan");
-  CK(cudaMemcpyAsync(ctx->h_tot, ptr<int64_t>(ctx->gas_rowptr) + G.n, 8, cudaMemcpyDeviceToHost, s), "readback");
-  CK(launch_pair_search<R>(D, G, ctx->bx, fr, false, cd, nullptr, nullptr, status, s, L), "pair count (dm)");
-  // the scan scratch is reused, so the second scan follows the first readback on the stream
-  CK(exclusive_scan_u32_i64(cd, ptr<int64_t>(ctx->dm_rowptr), D.n, ptr<int64_t>(ctx->scan_tmp), s, L), "scan");
-  CK(cudaMemcpyAsync(ctx->h_tot + 1, ptr<int64_t>(ctx->dm_rowptr) + D.n, 8, cudaMemcpyDeviceToHost, s), "readback");
+  if ((st = ensure_sort_scratch(ctx, nmax + 1)) != DMB_OK) return st;
+  unsigned long long *sst = ptr<unsigned long long>(ctx->search_stats);
+  CK(cudaMemsetAsync(sst, 0, 16 * 8, s), "stats reset");
+  SearchBufs &sg = ctx->sg, &sd = ctx->sd;
+  // stage 1 counts in both directions, then one readback of the list sizes
+  if ((st = search_stage1_count<R>(ctx, sg, G, D, sst)) != DMB_OK) return st;
+  CK(cudaMemcpyAsync(ctx->h_tot + 0, ptr<int64_t>(sg.item_ptr) + G.cnt[0], 8, cudaMemcpyDeviceToHost, s), "readback");
+  CK(cudaMemcpyAsync(ctx->h_tot + 1, ptr<int64_t>(sg.unit_ptr) + G.cnt[0], 8, cudaMemcpyDeviceToHost, s), "readback");
+  if ((st = search_stage1_count<R>(ctx, sd, D, G, sst + 4)) != DMB_OK) return st;
+  CK(cudaMemcpyAsync(ctx->h_tot + 2, ptr<int64_t>(sd.item_ptr) + D.cnt[0], 8, cudaMemcpyDeviceToHost, s), "readback");
+  CK(cudaMemcpyAsync(ctx->h_tot + 3, ptr<int64_t>(sd.unit_ptr) + D.cnt[0], 8, cudaMemcpyDeviceToHost, s), "readback");
   if ((st = check_status(ctx)) != DMB_OK) return st;
-  const int64_t ng = G.n > 0 ? ctx->h_tot[0] : 0, nd = D.n > 0 ? ctx->h_tot[1] : 0;
-  if (ng != nd) return fail(ctx, DMB_ERR_STATE, "pair counts of the two search directions differ");
-  const size_t rb = ctx->p.fp64 ? 8 : 4;
-  if (!ensure(ctx->gas_rows, ng * 4) || !ensure(ctx->dm_rows, ng * 4) || !ensure(ctx->pcache, ng * rb))
-    return fail(ctx, DMB_ERR_OOM, "device allocation failed for pair lists");
-  CK(launch_pair_search<R>(G, D, ctx->bx, fr, true, nullptr, ptr<int64_t>(ctx->gas_rowptr),
-                           ptr<uint32_t>(ctx->gas_rows), status, s, L), "pair emit (gas)");
-  CK(launch_pair_search<R>(D, G, ctx->bx, fr, true, nullptr, ptr<int64_t>(ctx->dm_rowptr),
-                           ptr<uint32_t>(ctx->dm_rows), status, s, L), "pair emit (dm)");
-  ctx->n_pairs = ng;
+  sg.n_items = ctx->h_tot[0];
+  sg.n_units = ctx->h_tot[1];
+  sd.n_items = ctx->h_tot[2];
+  sd.n_units = ctx->h_tot[3];
+  // stage 2 counts, then the pair totals
+  if ((st = search_stage2_count<R>(ctx, sg, G, D, sst)) != DMB_OK) return st;
+  CK(cudaMemcpyAsync(ctx->h_tot + 4, ptr<int64_t>(sg.row_ptr) + G.n, 8, cudaMemcpyDeviceToHost, s), "readback");
+  if ((st = search_stage2_count<R>(ctx, sd, D, G, sst + 4)) != DMB_OK) return st;
+  CK(cudaMemcpyAsync(ctx->h_tot + 5, ptr<int64_t>(sd.row_ptr) + D.n, 8, cudaMemcpyDeviceToHost, s), "readback");
+  if ((st = check_status(ctx)) != DMB_OK) return st;
+  sg.n_pairs = G.n > 0 ? ctx->h_tot[4] : 0;
+  sd.n_pairs = D.n > 0 ? ctx->h_tot[5] : 0;
+  if (sg.n_pairs != sd.n_pairs) return fail(ctx, DMB_ERR_STATE, "pair counts of the two search directions differ");
+  if ((st = search_stage2_emit<R>(ctx, sg, G, D)) != DMB_OK) return st;
+  if ((st = search_stage2_emit<R>(ctx, sd, D, G)) != DMB_OK) return st;
+  if (!ensure(ctx->pcache, (size_t)sd.n_pairs * (ctx->p.fp64 ? 8 : 4)))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for the probability cache");
+  ctx->n_pairs = sg.n_pairs;
   ctx->pairs_ready = true;
   return DMB_OK;
 }
@@ -245,7 +319,7 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
   o.acc = acc;
   o.dudt = dudt;
   o.e_exp = e_exp;
-  CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->gas_rowptr), ptr<uint32_t>(ctx->gas_rows),
+  CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows),
                          ptr<float4>(ctx->gtab), ctx->rc, o, ctx->stream, &ctx->launches), "meanfield");
   return DMB_OK;
 }
@@ -277,7 +351,7 @@ dmb_status mc_impl(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, uint
   a.block_sums = ptr<double>(ctx->mc_blocks);
   a.block_max = ptr<double>(ctx->mc_max);
   if (D.n > 0)
-    CK(launch_mc<R>(D, G, ctx->bx, ptr<int64_t>(ctx->dm_rowptr), ptr<uint32_t>(ctx->dm_rows),
+    CK(launch_mc<R>(D, G, ctx->bx, ptr<int64_t>(ctx->sd.row_ptr), ptr<uint32_t>(ctx->sd.rows),
                     ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), nb, ctx->stream, &ctx->launches), "mc");
   return DMB_OK;
 }
@@ -334,7 +408,8 @@ dmb_status dmb_create(dmb_ctx **out, const dmb_params *p, void *cuda_stream) {
   }
   ctx->bx.pad = 0.0f;
   bool ok = ensure(ctx->frame, sizeof(Frame)) && ensure(ctx->status, 16) && ensure(ctx->frame_part, 1024 * 8 * 8) &&
-            ensure(ctx->gtab, (size_t)DMB_GT_NQ * DMB_GT_CELLS * 16) && ensure(ctx->sums, 16 * 8);
+            ensure(ctx->gtab, (size_t)DMB_GT_NQ * DMB_GT_CELLS * 16) && ensure(ctx->sums, 16 * 8) &&
+            ensure(ctx->search_stats, 16 * 8);
   if (!ok) {
     dmb_destroy(ctx);
     return fail(nullptr, DMB_ERR_OOM, "device allocation failed at context creation");
@@ -360,10 +435,14 @@ dmb_status dmb_create(dmb_ctx **out, const dmb_params *p, void *cuda_stream) {
 dmb_status dmb_destroy(dmb_ctx *ctx) {
   if (!ctx) return DMB_OK;
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  for (SearchBufs *sb : {&ctx->sg, &ctx->sd}) {
+    DevBuf *q[] = {&sb->item_cnt, &sb->item_ptr, &sb->items, &sb->unit_cnt_leaf, &sb->unit_ptr, &sb->unit_leaf,
+                   &sb->unit_item0, &sb->unit_cnt, &sb->counts, &sb->row_ptr, &sb->rows};
+    for (DevBuf *b : q) release(*b);
+  }
   DevBuf *bufs[] = {&ctx->frame, &ctx->status, &ctx->frame_part, &ctx->gtab, &ctx->hist, &ctx->hist_scan,
-                    &ctx->scan_tmp, &ctx->counts, &ctx->gas_rowptr, &ctx->gas_rows, &ctx->dm_rowptr, &ctx->dm_rows,
-                    &ctx->pcache, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
-                    &ctx->kick_blocks, &ctx->sums, &ctx->scratch_vel};
+                    &ctx->scan_tmp, &ctx->pcache, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
+                    &ctx->kick_blocks, &ctx->sums, &ctx->scratch_vel, &ctx->search_stats};
   for (DevBuf *b : bufs) release(*b);
   SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};
   for (SpeciesBufs *s : sp) {
@@ -373,6 +452,8 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->h_tot) cudaFreeHost(ctx->h_tot);
   if (ctx->h_sums) cudaFreeHost(ctx->h_sums);
+  for (int k = 0; k < 6; ++k)
+    if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
   delete ctx;
   return DMB_OK;
 }
@@ -395,7 +476,7 @@ dmb_status dmb_neighbors(dmb_ctx *ctx, int64_t *n_pairs, uint32_t *pairs_out, in
   if (st != DMB_OK) return st;
   if (n_pairs) *n_pairs = ctx->n_pairs;
   if (pairs_out && capacity > 0)
-    CK(launch_pairs_out(ptr<int64_t>(ctx->gas_rowptr), ptr<uint32_t>(ctx->gas_rows), ptr<uint32_t>(ctx->gas.vals0),
+    CK(launch_pairs_out(ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), ptr<uint32_t>(ctx->gas.vals0),
                         ptr<uint32_t>(ctx->dm.vals0), ctx->gas.n, capacity, pairs_out, ctx->stream, &ctx->launches),
        "pairs out");
   return DMB_OK;
@@ -422,18 +503,24 @@ dmb_status dmb_step(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
   if (!(dt >= 0.0) || !isfinite(dt)) return fail(ctx, DMB_ERR_ARG, "dt must be finite and >= 0");
   dmb_status st;
+  const bool tm = ctx->timing;
+  if (tm) CK(cudaEventRecord(ctx->ev[0], ctx->stream), "event");
   if ((st = dmb_build_grid(ctx, dm, gas)) != DMB_OK) return st;
+  if (tm) CK(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
   if ((st = dmb_neighbors(ctx, nullptr, nullptr, 0)) != DMB_OK) return st;
+  if (tm) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
   const int64_t ng = gas->n, nd = dm->n;
   if (!ensure(ctx->mf_acc, ng * 24) || !ensure(ctx->mf_dudt, ng * 8) || !ensure(ctx->e_exp, ng * 8))
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for mean-field scratch");
   st = ctx->p.fp64 ? meanfield_impl<double>(ctx, ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp))
                    : meanfield_impl<float>(ctx, ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp));
   if (st != DMB_OK) return st;
+  if (tm) CK(cudaEventRecord(ctx->ev[3], ctx->stream), "event");
   // DM velocities are updated in place: the MC reads v_i and writes v_i' for the same particle
   st = ctx->p.fp64 ? mc_impl<double>(ctx, step, dt, const_cast<double *>(dm->vel), nullptr, nullptr, nullptr, nullptr)
                    : mc_impl<float>(ctx, step, dt, const_cast<double *>(dm->vel), nullptr, nullptr, nullptr, nullptr);
   if (st != DMB_OK) return st;
+  if (tm) CK(cudaEventRecord(ctx->ev[4], ctx->stream), "event");
   const int kb = 152 * 4;
   if (!ensure(ctx->kick_blocks, (size_t)kb * KICK_NSUM * 8)) return fail(ctx, DMB_ERR_OOM, "kick partials");
   CK(launch_kick_gas(const_cast<double *>(gas->vel), const_cast<double *>(gas->T), gas->mu, gas->mass,
@@ -449,11 +536,48 @@ dmb_status dmb_step(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t
                        dt, (double)ctx->n_pairs, ptr<double>(ctx->sums), ctx->stream, &ctx->launches), "sums");
   ctx->grid_ready = false;   // the state moved on: rebuild before the next standalone call
   ctx->pairs_ready = false;
+  if (tm) {
+    CK(cudaEventRecord(ctx->ev[5], ctx->stream), "event");
+    CK(cudaEventSynchronize(ctx->ev[5]), "event sync");
+    for (int k = 0; k < 5; ++k) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, ctx->ev[k], ctx->ev[k + 1]), "event time");
+      ctx->stage_ms[k] += ms;
+    }
+    ctx->timed_steps += 1;
+  }
   if (sums_out) {
     CK(cudaMemcpyAsync(ctx->h_sums, ctx->sums.p, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream), "sums readback");
     CK(cudaStreamSynchronize(ctx->stream), "synchronise");
     memcpy(sums_out, ctx->h_sums, 16 * 8);
   }
+  return DMB_OK;
+}
+
+dmb_status dmb_set_timing(dmb_ctx *ctx, int on) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (on && !ctx->ev[0])
+    for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&ctx->ev[k]), "event create");
+  ctx->timing = on != 0;
+  for (int k = 0; k < 8; ++k) ctx->stage_ms[k] = 0.0;
+  ctx->timed_steps = 0;
+  return DMB_OK;
+}
+
+dmb_status dmb_stage_times(dmb_ctx *ctx, double *ms_out, int64_t *steps_out) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (ms_out) for (int k = 0; k < 8; ++k) ms_out[k] = ctx->stage_ms[k];
+  if (steps_out) *steps_out = ctx->timed_steps;
+  for (int k = 0; k < 8; ++k) ctx->stage_ms[k] = 0.0;
+  ctx->timed_steps = 0;
+  return DMB_OK;
+}
+
+dmb_status dmb_search_stats(dmb_ctx *ctx, uint64_t *out16) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!out16) return fail(ctx, DMB_ERR_ARG, "out is NULL");
+  CK(cudaMemcpyAsync(out16, ctx->search_stats.p, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream), "stats readback");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronise");
   return DMB_OK;
 }
 

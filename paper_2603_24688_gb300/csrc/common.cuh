@@ -7,6 +7,7 @@
 
 #define DMB_WARP 32
 #define DMB_LEAF 32          // particles per tree leaf (one warp's worth)
+#define DMB_MAX_LEVELS 8     // 32^7 leaves suffice for 2^31 particles
 #define DMB_FULL 0xffffffffu
 
 // overlap table: delta nodes on [0, 2], q nodes on [0, 1]
@@ -45,9 +46,13 @@ template <typename R> struct SpeciesView {
   const typename Vec<R>::v4 *K;   // gas: (cA, cB, kP0, e = mu/(m_chi + mu)); dm: unused
   const uint32_t *id;             // stable id
   const uint32_t *perm;           // sorted position -> caller index
-  const float4 *bmin;             // tree nodes, heap order from 1: (min xyz, h_max)
+  // 32-ary tree: level 0 = leaves of DMB_LEAF consecutive sorted particles, node i of level
+  // l > 0 groups nodes 32i .. 32i+31 of level l-1; level l occupies [off[l], off[l] + cnt[l])
+  const float4 *bmin;             // (min xyz, h_max of the particles below)
   const float4 *bmax;             // (max xyz, unused)
-  int32_t nleaf, p2;              // leaves and the padded power of two
+  int32_t levels;                 // number of levels; the root is level levels-1 (one node)
+  int32_t off[DMB_MAX_LEVELS];
+  int32_t cnt[DMB_MAX_LEVELS];
 };
 
 // Periodic box in the split representation.

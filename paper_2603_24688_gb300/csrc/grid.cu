@@ -222,15 +222,31 @@ template cudaError_t launch_gather<double>(const double *, const double *, const
                                            cudaStream_t, int64_t *);
 
 // ---- chunk tree ------------------------------------------------------------------------
-// Leaves hold DMB_LEAF consecutive sorted particles; nodes use heap order (root 1, children
-// 2k, 2k+1, leaves at [p2, 2 p2)).  Boxes are float with a conservative pad; bmin.w = h_max.
+// Leaves hold DMB_LEAF consecutive sorted particles; every inner node groups 32 consecutive
+// nodes of the level below.  Boxes are float with a conservative pad; bmin.w = h_max.
+int tree_layout(int64_t n, int *levels, int off[DMB_MAX_LEVELS], int cnt[DMB_MAX_LEVELS]) {
+  int64_t c = (n + DMB_LEAF - 1) / DMB_LEAF;
+  if (c < 1) c = 1;
+  int l = 0, total = 0;
+  while (true) {
+    off[l] = total;
+    cnt[l] = (int)c;
+    total += (int)c;
+    ++l;
+    if (c == 1 || l == DMB_MAX_LEVELS) break;
+    c = (c + 31) / 32;
+  }
+  *levels = l;
+  return total;
+}
+
 template <typename R>
 __global__ void k_tree_leaves(const typename Vec<R>::v4 *__restrict__ P, const typename Vec<R>::v4 *__restrict__ L,
-                              int64_t n, int p2, const Frame *__restrict__ frame, float4 *__restrict__ bmin,
+                              int64_t n, int nleaf, const Frame *__restrict__ frame, float4 *__restrict__ bmin,
                               float4 *__restrict__ bmax) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned lane = threadIdx.x & 31u;
-  if (warp >= p2) return;
+  if (warp >= nleaf) return;
   const int64_t i = warp * DMB_LEAF + lane;
   float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
   float hm = -INFINITY;
@@ -252,66 +268,55 @@ __global__ void k_tree_leaves(const typename Vec<R>::v4 *__restrict__ P, const t
   if (lane == 0) {
     const float pad = frame->pad;
     if (hm > -INFINITY) {
-      bmin[p2 + warp] = make_float4(mn[0] - pad, mn[1] - pad, mn[2] - pad, hm * (1.0f + 1e-6f));
-      bmax[p2 + warp] = make_float4(mx[0] + pad, mx[1] + pad, mx[2] + pad, 0.0f);
+      bmin[warp] = make_float4(mn[0] - pad, mn[1] - pad, mn[2] - pad, hm * (1.0f + 1e-6f));
+      bmax[warp] = make_float4(mx[0] + pad, mx[1] + pad, mx[2] + pad, 0.0f);
     } else {
-      bmin[p2 + warp] = make_float4(INFINITY, INFINITY, INFINITY, -INFINITY);
-      bmax[p2 + warp] = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.0f);
+      bmin[warp] = make_float4(INFINITY, INFINITY, INFINITY, -INFINITY);
+      bmax[warp] = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.0f);
     }
   }
 }
 
-// Reduce `levels` levels of the heap upward, starting from the m nodes of one level
-// (heap indices [m, 2m)); each block owns 256 consecutive nodes of that level.
-__global__ void k_tree_reduce(float4 *__restrict__ bmin, float4 *__restrict__ bmax, int m, int levels) {
-  __shared__ float4 smn[256], smx[256];
-  const int t = threadIdx.x;
-  const int width = m < 256 ? m : 256;
-  const int first = m + blockIdx.x * width;
-  if (t < width) { smn[t] = bmin[first + t]; smx[t] = bmax[first + t]; }
-  __syncthreads();
-  int cnt = width;
-  int base = first;
-  for (int l = 0; l < levels; ++l) {
-    const int half = cnt >> 1;
-    float4 a0, a1;
-    if (t < half) {
-      const float4 c0 = smn[2 * t], c1 = smn[2 * t + 1], d0 = smx[2 * t], d1 = smx[2 * t + 1];
-      a0 = make_float4(fminf(c0.x, c1.x), fminf(c0.y, c1.y), fminf(c0.z, c1.z), fmaxf(c0.w, c1.w));
-      a1 = make_float4(fmaxf(d0.x, d1.x), fmaxf(d0.y, d1.y), fmaxf(d0.z, d1.z), 0.0f);
-    }
-    __syncthreads();
-    base >>= 1;
-    if (t < half) {
-      smn[t] = a0;
-      smx[t] = a1;
-      bmin[base + t] = a0;
-      bmax[base + t] = a1;
-    }
-    __syncthreads();
-    cnt = half;
+// one warp per parent: union of its (up to) 32 children
+__global__ void k_tree_level(float4 *__restrict__ bmin, float4 *__restrict__ bmax, int child_off, int child_cnt,
+                             int par_off, int par_cnt) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned lane = threadIdx.x & 31u;
+  if (warp >= par_cnt) return;
+  const int64_t c = warp * 32 + lane;
+  float4 a = make_float4(INFINITY, INFINITY, INFINITY, -INFINITY), b = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.0f);
+  if (c < child_cnt) { a = bmin[child_off + c]; b = bmax[child_off + c]; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a.x = fminf(a.x, __shfl_xor_sync(DMB_FULL, a.x, o));
+    a.y = fminf(a.y, __shfl_xor_sync(DMB_FULL, a.y, o));
+    a.z = fminf(a.z, __shfl_xor_sync(DMB_FULL, a.z, o));
+    a.w = fmaxf(a.w, __shfl_xor_sync(DMB_FULL, a.w, o));
+    b.x = fmaxf(b.x, __shfl_xor_sync(DMB_FULL, b.x, o));
+    b.y = fmaxf(b.y, __shfl_xor_sync(DMB_FULL, b.y, o));
+    b.z = fmaxf(b.z, __shfl_xor_sync(DMB_FULL, b.z, o));
+  }
+  if (lane == 0) {
+    bmin[par_off + warp] = a;
+    bmax[par_off + warp] = make_float4(b.x, b.y, b.z, 0.0f);
   }
 }
 
 template <typename R>
 cudaError_t launch_tree(const typename Vec<R>::v4 *P, const typename Vec<R>::v4 *L, int64_t n, const Frame *frame,
-                        float4 *bmin, float4 *bmax, int p2, cudaStream_t s, int64_t *launches) {
-  const int64_t threads = (int64_t)p2 * 32;
-  k_tree_leaves<R><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(P, L, n, p2, frame, bmin, bmax);
+                        float4 *bmin, float4 *bmax, int levels, const int *off, const int *cnt, cudaStream_t s,
+                        int64_t *launches) {
+  const int64_t t0 = (int64_t)cnt[0] * 32;
+  k_tree_leaves<R><<<(unsigned)((t0 + 255) / 256), 256, 0, s>>>(P, L, n, cnt[0], frame, bmin + off[0], bmax + off[0]);
   if (launches) *launches += 1;
-  int m = p2;
-  while (m > 1) {
-    int levels = 0;
-    int w = m < 256 ? m : 256;
-    while ((1 << (levels + 1)) <= w) ++levels;   // log2(w)
-    const int blocks = m / w;
-    k_tree_reduce<<<blocks, 256, 0, s>>>(bmin, bmax, m, levels);
+  for (int l = 1; l < levels; ++l) {
+    const int64_t t = (int64_t)cnt[l] * 32;
+    k_tree_level<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(bmin, bmax, off[l - 1], cnt[l - 1], off[l], cnt[l]);
     if (launches) *launches += 1;
-    m >>= levels;
   }
   return cudaGetLastError();
 }
 template cudaError_t launch_tree<float>(const float4 *, const float4 *, int64_t, const Frame *, float4 *, float4 *,
-                                        int, cudaStream_t, int64_t *);
+                                        int, const int *, const int *, cudaStream_t, int64_t *);
 template cudaError_t launch_tree<double>(const double4_32a *, const double4_32a *, int64_t, const Frame *, float4 *,
-                                         float4 *, int, cudaStream_t, int64_t *);
+                                         float4 *, int, const int *, const int *, cudaStream_t, int64_t *);

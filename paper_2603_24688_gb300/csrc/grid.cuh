@@ -45,6 +45,10 @@ cudaError_t launch_gather(const double *pos, const double *vel, const double *ma
                           typename Vec<R>::v4 *K, uint32_t *sid, uint32_t *status, cudaStream_t s,
                           int64_t *launches);
 
+// Level layout of the 32-ary tree for n particles; returns the number of nodes.
+int tree_layout(int64_t n, int *levels, int off[DMB_MAX_LEVELS], int cnt[DMB_MAX_LEVELS]);
+
 template <typename R>
 cudaError_t launch_tree(const typename Vec<R>::v4 *P, const typename Vec<R>::v4 *L, int64_t n, const Frame *frame,
-                        float4 *bmin, float4 *bmax, int p2, cudaStream_t s, int64_t *launches);
+                        float4 *bmin, float4 *bmax, int levels, const int *off, const int *cnt, cudaStream_t s,
+                        int64_t *launches);

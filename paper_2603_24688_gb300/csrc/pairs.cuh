@@ -2,9 +2,23 @@
 #pragma once
 #include "grid.cuh"
 
+#define SR_UNIT 64   // target leaves per work unit of the tile stage
+
 template <typename R>
-cudaError_t launch_pair_search(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
-                               uint32_t *counts, const int64_t *row_ptr, uint32_t *rows, uint32_t *status,
+cudaError_t launch_leaf_pairs(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
+                              uint32_t *item_cnt, const int64_t *item_ptr, uint32_t *items, uint32_t *status,
+                              unsigned long long *stats, cudaStream_t s, int64_t *launches);
+cudaError_t launch_unit_counts(const int64_t *item_ptr, int nleaf, uint32_t *unit_cnt, cudaStream_t s,
+                               int64_t *launches);
+cudaError_t launch_unit_map(const int64_t *item_ptr, const int64_t *unit_ptr, int nleaf, uint32_t *unit_leaf,
+                            int64_t *unit_item0, cudaStream_t s, int64_t *launches);
+template <typename R>
+cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
+                        const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
+                        const uint32_t *items, int64_t n_units, uint32_t *unit_cnt, const int64_t *row_ptr,
+                        uint32_t *rows, uint32_t *status, unsigned long long *stats, cudaStream_t s,
+                        int64_t *launches);
+cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, uint32_t *unit_cnt, uint32_t *counts,
                                cudaStream_t s, int64_t *launches);
 
 struct MfOut {

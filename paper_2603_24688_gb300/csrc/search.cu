@@ -1,127 +1,284 @@
-// Warp-cooperative pair search over the chunk tree (count and emit passes).
+// Pair search on the 32-ary chunk trees, in two stages:
+//   1. per query leaf, the target leaves whose boxes come within h_max + h_max (lane-parallel
+//      tests of the 32 children of every visited node), listed in depth-first order;
+//   2. those lists cut into work units of at most SR_UNIT target leaves; one warp per unit
+//      tests its 32 query particles against each target leaf (targets outside the query
+//      leaf's reach are dropped by a ballot first) and counts or writes the pairs.
+// Rows come out in a fixed order (units, then leaves, then particles), so the search is
+// deterministic; both directions use the same bit-exact pair predicate.
 #include "pairs.cuh"
 #include "physics.cuh"
 
 #define SR_WARPS 4
-#define SR_STACK 64
+#define SR_STACK 256
 
 __device__ __forceinline__ float axis_gap(float qa, float qb, float na, float nb) {
   return fmaxf(0.0f, fmaxf(na - qb, qa - nb));
 }
 
+// squared distance between two boxes (minimum image when periodic)
+__device__ __forceinline__ float box_gap2(const float qmn[3], const float qmx[3], const float4 &nmn, const float4 &nmx,
+                                          const BoxSplit &bx) {
+  float d2 = 0.f;
+  const float na[3] = {nmn.x, nmn.y, nmn.z}, nb[3] = {nmx.x, nmx.y, nmx.z};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float gap = axis_gap(qmn[k], qmx[k], na[k], nb[k]);
+    if (bx.periodic) {
+      const float L = bx.Lhi[k];
+      gap = fminf(gap, fminf(axis_gap(qmn[k] + L, qmx[k] + L, na[k], nb[k]), axis_gap(qmn[k] - L, qmx[k] - L, na[k], nb[k])));
+    }
+    d2 += gap * gap;
+  }
+  return d2;
+}
+
+// ---- stage 1: candidate target leaves per query leaf -----------------------------------
 template <typename R, bool EMIT>
 __global__ void __launch_bounds__(SR_WARPS * 32)
-k_pair_search(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict__ frame,
-              uint32_t *__restrict__ counts, const int64_t *__restrict__ row_ptr, uint32_t *__restrict__ rows,
-              uint32_t *status) {
+k_leaf_pairs(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict__ frame,
+             uint32_t *__restrict__ item_cnt, const int64_t *__restrict__ item_ptr, uint32_t *__restrict__ items,
+             uint32_t *status, unsigned long long *__restrict__ stats) {
+  __shared__ int stack[SR_WARPS][SR_STACK];
+  const int wib = threadIdx.x >> 5;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt = (1u << lane) - 1u;
+  const float pad2 = 2.0f * frame->pad;
+  const int nleaf = Q.cnt[0];
+  unsigned long long st_nodes = 0;
+  for (int a = blockIdx.x * SR_WARPS + wib; a < nleaf; a += gridDim.x * SR_WARPS) {
+    const float4 qa = Q.bmin[Q.off[0] + a], qb = Q.bmax[Q.off[0] + a];
+    uint32_t count = 0;
+    const int64_t base = EMIT ? item_ptr[a] : 0;
+    const int64_t lim = EMIT ? item_ptr[a + 1] - base : 0;
+    if (qa.w >= 0.0f) {
+      const float qmn[3] = {qa.x, qa.y, qa.z}, qmx[3] = {qb.x, qb.y, qb.z};
+      const int top = O.levels - 1;
+      if (top == 0) {
+        // a single leaf: test it directly
+        const float4 nmn = O.bmin[O.off[0]], nmx = O.bmax[O.off[0]];
+        const float r = qa.w + nmn.w + pad2;
+        if (nmn.w >= 0.0f && box_gap2(qmn, qmx, nmn, nmx, bx) < r * r) {
+          if (EMIT && lane == 0 && lim > 0) items[base] = 0u;
+          count = 1;
+        }
+      } else {
+        int sp = 0;
+        if (lane == 0) stack[wib][0] = (top << 27) | 0;
+        sp = 1;
+        __syncwarp();
+        while (sp > 0) {
+          const int e = stack[wib][sp - 1];
+          --sp;
+          __syncwarp();
+          const int l = e >> 27, idx = e & ((1 << 27) - 1);
+          ++st_nodes;
+          const int c = idx * 32 + (int)lane;
+          bool pass = false;
+          if (c < O.cnt[l - 1]) {
+            const float4 nmn = O.bmin[O.off[l - 1] + c], nmx = O.bmax[O.off[l - 1] + c];
+            const float r = qa.w + nmn.w + pad2;
+            pass = nmn.w >= 0.0f && box_gap2(qmn, qmx, nmn, nmx, bx) < r * r;
+          }
+          const unsigned m = __ballot_sync(DMB_FULL, pass);
+          const int np = __popc(m);
+          if (l - 1 == 0) {
+            if (EMIT && pass && (int64_t)(count + __popc(m & lt)) < lim) items[base + count + __popc(m & lt)] = (uint32_t)c;
+            count += np;
+          } else if (np) {
+            if (sp + np > SR_STACK) {
+              if (lane == 0) atomicOr(status, DMB_BAD_OVERFLOW);
+              break;
+            }
+            // push in reverse so the lowest child index is popped first
+            if (pass) stack[wib][sp + np - 1 - __popc(m & lt)] = ((l - 1) << 27) | c;
+            sp += np;
+          }
+          __syncwarp();
+        }
+      }
+    }
+    if (!EMIT && lane == 0) item_cnt[a] = count;
+    if (EMIT && lane == 0 && (int64_t)count != item_ptr[a + 1] - item_ptr[a]) atomicOr(status, DMB_BAD_OVERFLOW);
+  }
+  if (stats != nullptr && lane == 0) atomicAdd(&stats[0], st_nodes);
+}
+
+// units per query leaf
+__global__ void k_unit_counts(const int64_t *__restrict__ item_ptr, int nleaf, uint32_t *__restrict__ unit_cnt) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nleaf) return;
+  const int64_t n = item_ptr[a + 1] - item_ptr[a];
+  unit_cnt[a] = (uint32_t)((n + SR_UNIT - 1) / SR_UNIT);
+}
+
+__global__ void k_unit_map(const int64_t *__restrict__ item_ptr, const int64_t *__restrict__ unit_ptr, int nleaf,
+                           uint32_t *__restrict__ unit_leaf, int64_t *__restrict__ unit_item0) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nleaf) return;
+  const int64_t u0 = unit_ptr[a], u1 = unit_ptr[a + 1];
+  for (int64_t u = u0; u < u1; ++u) {
+    unit_leaf[u] = (uint32_t)a;
+    unit_item0[u] = item_ptr[a] + (u - u0) * SR_UNIT;
+  }
+}
+
+// ---- stage 2: tiles of (query leaf) x (target leaf) -------------------------------------
+template <typename R, bool EMIT>
+__global__ void __launch_bounds__(SR_WARPS * 32)
+k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict__ frame,
+       const uint32_t *__restrict__ unit_leaf, const int64_t *__restrict__ unit_item0,
+       const int64_t *__restrict__ item_ptr, const uint32_t *__restrict__ items, int64_t n_units,
+       uint32_t *__restrict__ unit_cnt, const int64_t *__restrict__ row_ptr, uint32_t *__restrict__ rows,
+       uint32_t *status, unsigned long long *__restrict__ stats) {
   typedef typename Vec<R>::v4 v4;
   __shared__ v4 sP[SR_WARPS][DMB_LEAF];
   __shared__ v4 sL[SR_WARPS][DMB_LEAF];
   const int wib = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31u;
-  const int64_t nchunk = (Q.n + 31) / 32;
-  const float pad = frame->pad;
-  for (int64_t chunk = (int64_t)blockIdx.x * SR_WARPS + wib; chunk < nchunk; chunk += (int64_t)gridDim.x * SR_WARPS) {
-    const int64_t qi = chunk * 32 + lane;
+  const float pad2 = 2.0f * frame->pad;
+  unsigned long long st_tests = 0, st_leaves = 0;
+  for (int64_t u = (int64_t)blockIdx.x * SR_WARPS + wib; u < n_units; u += (int64_t)gridDim.x * SR_WARPS) {
+    const int a = (int)unit_leaf[u];
+    const int64_t it0 = unit_item0[u];
+    const int64_t it1 = min(it0 + (int64_t)SR_UNIT, item_ptr[a + 1]);
+    const int64_t qi = (int64_t)a * DMB_LEAF + lane;
     const bool valid = qi < Q.n;
+    const float4 qa = Q.bmin[Q.off[0] + a], qb = Q.bmax[Q.off[0] + a];
+    const float qmn[3] = {qa.x, qa.y, qa.z}, qmx[3] = {qb.x, qb.y, qb.z};
     v4 Pq = Vec<R>::make(0, 0, 0, 0), Lq = Vec<R>::make(0, 0, 0, 0);
-    float c[3] = {0.f, 0.f, 0.f};
-    float hq = 0.f;
-    if (valid) {
-      Pq = Q.P[qi];
-      Lq = Q.L[qi];
-      c[0] = (float)((double)Pq.x + (double)Lq.x);
-      c[1] = (float)((double)Pq.y + (double)Lq.y);
-      c[2] = (float)((double)Pq.z + (double)Lq.z);
-      hq = (float)Pq.w;
-    }
-    float qmn[3], qmx[3], hqm = valid ? hq : 0.f;
-    for (int k = 0; k < 3; ++k) { qmn[k] = valid ? c[k] : INFINITY; qmx[k] = valid ? c[k] : -INFINITY; }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      for (int k = 0; k < 3; ++k) {
-        qmn[k] = fminf(qmn[k], __shfl_xor_sync(DMB_FULL, qmn[k], o));
-        qmx[k] = fmaxf(qmx[k], __shfl_xor_sync(DMB_FULL, qmx[k], o));
-      }
-      hqm = fmaxf(hqm, __shfl_xor_sync(DMB_FULL, hqm, o));
-    }
-    hqm *= (1.0f + 1e-6f);
+    if (valid) { Pq = Q.P[qi]; Lq = Q.L[qi]; }
     uint32_t cnt = 0;
-    int64_t out_base = 0, out_end = 0;
-    if (EMIT && valid) { out_base = row_ptr[qi]; out_end = row_ptr[qi + 1]; }
-    int stack[SR_STACK];
-    int sp = 0;
-    stack[sp++] = 1;
-    while (sp > 0) {
-      const int node = stack[--sp];
-      const float4 nmn = O.bmin[node], nmx = O.bmax[node];
-      if (!(nmn.w >= 0.0f)) continue;                    // empty node
-      float d2 = 0.f;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float na = k == 0 ? nmn.x : (k == 1 ? nmn.y : nmn.z);
-        const float nb = k == 0 ? nmx.x : (k == 1 ? nmx.y : nmx.z);
-        float gap = axis_gap(qmn[k], qmx[k], na, nb);
-        if (bx.periodic) {
-          const float L = bx.Lhi[k];
-          gap = fminf(gap, fminf(axis_gap(qmn[k] + L, qmx[k] + L, na, nb), axis_gap(qmn[k] - L, qmx[k] - L, na, nb)));
-        }
-        d2 += gap * gap;
+    int64_t out = 0, out_end = 0;
+    if (EMIT && valid) {
+      out = row_ptr[qi] + unit_cnt[32 * u + lane];   // unit_cnt holds the exclusive offsets here
+      out_end = row_ptr[qi + 1];
+    }
+    for (int64_t it = it0; it < it1; ++it) {
+      const int64_t base = (int64_t)items[it] * DMB_LEAF;
+      const int nk = (int)min((int64_t)DMB_LEAF, O.n - base);
+      bool keep = false;
+      __syncwarp();
+      if ((int)lane < nk) {
+        const v4 Pk = O.P[base + lane], Lk = O.L[base + lane];
+        sP[wib][lane] = Pk;
+        sL[wib][lane] = Lk;
+        const float c[3] = {(float)((double)Pk.x + (double)Lk.x), (float)((double)Pk.y + (double)Lk.y),
+                            (float)((double)Pk.z + (double)Lk.z)};
+        const float4 pmn = make_float4(c[0], c[1], c[2], 0.f), pmx = make_float4(c[0], c[1], c[2], 0.f);
+        const float r = qa.w + (float)Pk.w + pad2;
+        keep = box_gap2(qmn, qmx, pmn, pmx, bx) < r * r;
       }
-      const float r = hqm + nmn.w + 2.0f * pad;
-      if (d2 >= r * r) continue;
-      if (node >= O.p2) {
-        const int64_t base = (int64_t)(node - O.p2) * DMB_LEAF;
-        if (base >= O.n) continue;
-        const int nk = (int)min((int64_t)DMB_LEAF, O.n - base);
-        __syncwarp();
-        if ((int)lane < nk) { sP[wib][lane] = O.P[base + lane]; sL[wib][lane] = O.L[base + lane]; }
-        __syncwarp();
-        if (valid) {
-          for (int k = 0; k < nk; ++k) {
-            const v4 Pk = sP[wib][k], Lk = sL[wib][k];
-            R dx, dy, dz;
-            pair_dx<R>(Pq, Lq, Pk, Lk, bx, dx, dy, dz);
-            if (pair_test<R>(dist2_rn<R>(dx, dy, dz), Pq.w, Pk.w)) {
-              if (EMIT) {
-                const int64_t at = out_base + cnt;
-                if (at < out_end) rows[at] = (uint32_t)(base + k);
-              }
-              ++cnt;
+      unsigned m = __ballot_sync(DMB_FULL, keep);
+      __syncwarp();
+      ++st_leaves;
+      st_tests += (unsigned long long)__popc(m) * 32ull;
+      if (valid) {
+        while (m) {
+          const int k = __ffs(m) - 1;
+          m &= m - 1;
+          const v4 Pk = sP[wib][k], Lk = sL[wib][k];
+          R dx, dy, dz;
+          pair_dx<R>(Pq, Lq, Pk, Lk, bx, dx, dy, dz);
+          if (pair_test<R>(dist2_rn<R>(dx, dy, dz), Pq.w, Pk.w)) {
+            if (EMIT) {
+              if (out < out_end) rows[out] = (uint32_t)(base + k);
+              ++out;
             }
+            ++cnt;
           }
         }
-      } else {
-        if (sp + 2 > SR_STACK) { atomicOr(status, DMB_BAD_OVERFLOW); break; }
-        stack[sp++] = 2 * node + 1;
-        stack[sp++] = 2 * node;
       }
     }
-    if (valid) {
-      if (!EMIT) counts[qi] = cnt;
-      else if ((int64_t)cnt != out_end - out_base) atomicOr(status, DMB_BAD_OVERFLOW);
-    }
+    if (!EMIT) unit_cnt[32 * u + lane] = valid ? cnt : 0u;
+  }
+  if (stats != nullptr && lane == 0) {
+    atomicAdd(&stats[1], st_leaves);
+    atomicAdd(&stats[2], st_tests);
   }
 }
 
+// per query leaf: exclusive offsets of each unit within every lane's row, and the row counts
+__global__ void k_unit_prefix(const int64_t *__restrict__ unit_ptr, int nleaf, int64_t nq,
+                              uint32_t *__restrict__ unit_cnt, uint32_t *__restrict__ counts) {
+  const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned lane = threadIdx.x & 31u;
+  if (a >= nleaf) return;
+  uint32_t run = 0;
+  for (int64_t u = unit_ptr[a]; u < unit_ptr[a + 1]; ++u) {
+    const uint32_t c = unit_cnt[32 * u + lane];
+    unit_cnt[32 * u + lane] = run;
+    run += c;
+  }
+  const int64_t qi = a * DMB_LEAF + lane;
+  if (qi < nq) counts[qi] = run;
+}
+
+// ---- launchers ---------------------------------------------------------------------------
+static int grid_for(int64_t warps) {
+  int64_t b = (warps + SR_WARPS - 1) / SR_WARPS;
+  if (b > 152 * 128) b = 152 * 128;
+  return (int)(b > 0 ? b : 1);
+}
+
 template <typename R>
-cudaError_t launch_pair_search(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
-                               uint32_t *counts, const int64_t *row_ptr, uint32_t *rows, uint32_t *status,
-                               cudaStream_t s, int64_t *launches) {
-  if (Q.n <= 0) return cudaSuccess;
-  const int64_t nchunk = (Q.n + 31) / 32;
-  int64_t blocks = (nchunk + SR_WARPS - 1) / SR_WARPS;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  if (emit)
-    k_pair_search<R, true><<<(unsigned)blocks, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, counts, row_ptr, rows, status);
-  else
-    k_pair_search<R, false><<<(unsigned)blocks, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, counts, row_ptr, rows, status);
+cudaError_t launch_leaf_pairs(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
+                              uint32_t *item_cnt, const int64_t *item_ptr, uint32_t *items, uint32_t *status,
+                              unsigned long long *stats, cudaStream_t s, int64_t *launches) {
+  const int g = grid_for(Q.cnt[0]);
+  if (emit) k_leaf_pairs<R, true><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, item_cnt, item_ptr, items, status, stats);
+  else k_leaf_pairs<R, false><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, item_cnt, item_ptr, items, status, stats);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
-template cudaError_t launch_pair_search<float>(SpeciesView<float>, SpeciesView<float>, BoxSplit, const Frame *, bool,
-                                               uint32_t *, const int64_t *, uint32_t *, uint32_t *, cudaStream_t,
-                                               int64_t *);
-template cudaError_t launch_pair_search<double>(SpeciesView<double>, SpeciesView<double>, BoxSplit, const Frame *,
-                                                bool, uint32_t *, const int64_t *, uint32_t *, uint32_t *,
-                                                cudaStream_t, int64_t *);
+
+cudaError_t launch_unit_counts(const int64_t *item_ptr, int nleaf, uint32_t *unit_cnt, cudaStream_t s,
+                               int64_t *launches) {
+  k_unit_counts<<<(nleaf + 255) / 256, 256, 0, s>>>(item_ptr, nleaf, unit_cnt);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unit_map(const int64_t *item_ptr, const int64_t *unit_ptr, int nleaf, uint32_t *unit_leaf,
+                            int64_t *unit_item0, cudaStream_t s, int64_t *launches) {
+  k_unit_map<<<(nleaf + 255) / 256, 256, 0, s>>>(item_ptr, unit_ptr, nleaf, unit_leaf, unit_item0);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
+                        const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
+                        const uint32_t *items, int64_t n_units, uint32_t *unit_cnt, const int64_t *row_ptr,
+                        uint32_t *rows, uint32_t *status, unsigned long long *stats, cudaStream_t s,
+                        int64_t *launches) {
+  if (n_units <= 0) return cudaSuccess;
+  const int g = grid_for(n_units);
+  if (emit)
+    k_tile<R, true><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items, n_units,
+                                                unit_cnt, row_ptr, rows, status, stats);
+  else
+    k_tile<R, false><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items, n_units,
+                                                 unit_cnt, row_ptr, rows, status, stats);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, uint32_t *unit_cnt, uint32_t *counts,
+                               cudaStream_t s, int64_t *launches) {
+  const int64_t t = (int64_t)nleaf * 32;
+  k_unit_prefix<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(unit_ptr, nleaf, nq, unit_cnt, counts);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+#define INST(R)                                                                                                     \
+  template cudaError_t launch_leaf_pairs<R>(SpeciesView<R>, SpeciesView<R>, BoxSplit, const Frame *, bool,          \
+                                            uint32_t *, const int64_t *, uint32_t *, uint32_t *,                    \
+                                            unsigned long long *, cudaStream_t, int64_t *);                          \
+  template cudaError_t launch_tile<R>(SpeciesView<R>, SpeciesView<R>, BoxSplit, const Frame *, bool,                \
+                                      const uint32_t *, const int64_t *, const int64_t *, const uint32_t *, int64_t, \
+                                      uint32_t *, const int64_t *, uint32_t *, uint32_t *, unsigned long long *,      \
+                                      cudaStream_t, int64_t *);
+INST(float)
+INST(double)

@@ -21,7 +21,8 @@ STATUS_NAMES = {0: "DMB_OK", 1: "DMB_ERR_ARG", 2: "DMB_ERR_CUDA", 3: "DMB_ERR_OO
 
 EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb_neighbors", "dmb_meanfield_gas",
            "dmb_mc_scatter_dm", "dmb_step", "dmb_debug_overlap", "dmb_debug_rates", "dmb_debug_philox",
-           "dmb_launch_count"]
+           "dmb_launch_count", "dmb_set_timing", "dmb_stage_times",
+           "dmb_search_stats"]
 
 
 class DmbError(RuntimeError):
@@ -72,6 +73,9 @@ def load(path=LIB_PATH):
         "dmb_debug_rates": ([vp, i64, vp, vp], c.c_int),
         "dmb_debug_philox": ([vp, i64, vp, vp], c.c_int),
         "dmb_launch_count": ([vp], i64),
+        "dmb_set_timing": ([vp, c.c_int], c.c_int),
+        "dmb_stage_times": ([vp, c.POINTER(c.c_double), c.POINTER(i64)], c.c_int),
+        "dmb_search_stats": ([vp, c.POINTER(c.c_uint64)], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -210,6 +214,22 @@ class Context:
 
     def dmb_launch_count(self):
         return int(self.lib.dmb_launch_count(self.h))
+
+    def dmb_search_stats(self):
+        """Counters of the last pair search: (4 passes) x (nodes, leaves, tests, 0)."""
+        out = (ctypes.c_uint64 * 16)()
+        self._check(self.lib.dmb_search_stats(self.h, out))
+        return np.array(out[:], dtype=np.uint64).reshape(4, 4)
+
+    def dmb_set_timing(self, on=True):
+        self._check(self.lib.dmb_set_timing(self.h, 1 if on else 0))
+
+    def dmb_stage_times(self):
+        """Return (ms per stage [8], steps) accumulated since the last call."""
+        ms = (ctypes.c_double * 8)()
+        n = ctypes.c_int64()
+        self._check(self.lib.dmb_stage_times(self.h, ms, ctypes.byref(n)))
+        return np.array(ms[:]), n.value
 
 
 def to_device(particles, device="cuda"):
