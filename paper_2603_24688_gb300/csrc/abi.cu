@@ -51,7 +51,7 @@ struct dmb_ctx {
   SpeciesBufs dm, gas;
   DevBuf hist, hist_scan, scan_tmp;
   SearchBufs sg, sd;   // gas-major (gas queries, DM tree) and DM-major searches
-  DevBuf pcache;
+  DevBuf pcache, mf_part, mc_rec;
   DevBuf mf_acc, mf_dudt, e_exp, mc_blocks, mc_max, kick_blocks, sums;
   DevBuf scratch_vel, search_stats;
   uint32_t *h_status = nullptr;   // pinned
@@ -319,14 +319,16 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
   o.acc = acc;
   o.dudt = dudt;
   o.e_exp = e_exp;
+  if (!ensure(ctx->mf_part, (size_t)G.n * 6 * sizeof(R))) return fail(ctx, DMB_ERR_OOM, "mean-field scratch");
   CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows),
-                         ptr<float4>(ctx->gtab), ctx->rc, o, ctx->stream, &ctx->launches), "meanfield");
+                         ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), ctx->stream, &ctx->launches),
+     "meanfield");
   return DMB_OK;
 }
 
-int mc_blocks_for(int64_t n) {
-  int64_t b = (n + 7) / 8;
-  if (b > 152 * 16) b = 152 * 16;
+int mc_blocks_for(int64_t n) {   // blocks of the float64 finish kernel (256 threads)
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
   return (int)(b > 0 ? b : 1);
 }
 
@@ -350,9 +352,11 @@ dmb_status mc_impl(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, uint
   a.p_total = ptot;
   a.block_sums = ptr<double>(ctx->mc_blocks);
   a.block_max = ptr<double>(ctx->mc_max);
+  if (!ensure(ctx->mc_rec, (size_t)D.n * sizeof(McRec))) return fail(ctx, DMB_ERR_OOM, "MC scratch");
   if (D.n > 0)
     CK(launch_mc<R>(D, G, ctx->bx, ptr<int64_t>(ctx->sd.row_ptr), ptr<uint32_t>(ctx->sd.rows),
-                    ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), nb, ctx->stream, &ctx->launches), "mc");
+                    ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), ptr<McRec>(ctx->mc_rec), nb, ctx->stream,
+                    &ctx->launches), "mc");
   return DMB_OK;
 }
 
@@ -441,7 +445,7 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
     for (DevBuf *b : q) release(*b);
   }
   DevBuf *bufs[] = {&ctx->frame, &ctx->status, &ctx->frame_part, &ctx->gtab, &ctx->hist, &ctx->hist_scan,
-                    &ctx->scan_tmp, &ctx->pcache, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
+                    &ctx->scan_tmp, &ctx->pcache, &ctx->mf_part, &ctx->mc_rec, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
                     &ctx->kick_blocks, &ctx->sums, &ctx->scratch_vel, &ctx->search_stats};
   for (DevBuf *b : bufs) release(*b);
   SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};

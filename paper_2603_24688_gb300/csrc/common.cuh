@@ -158,7 +158,23 @@ __device__ __forceinline__ U128 to_fixed(double p) {
   else if (sh > -64) { r.lo = mant >> (-sh); }
   return r;
 }
-__device__ __forceinline__ U128 to_fixed(float p) { return to_fixed((double)p); }
+// float version from the bits alone (no float64 or conversion instructions): p = m 2^(e-150)
+// with the 24-bit significand m, so the fixed-point value is m << (e - 86).
+__device__ __forceinline__ U128 to_fixed(float p) {
+  U128 r = {0ull, 0ull};
+  const uint32_t b = __float_as_uint(p);
+  const int e = (int)((b >> 23) & 0xffu);
+  if ((b >> 31) || e == 0) return r;              // negative, zero or subnormal
+  if (e >= 255) { r.hi = 0x7fffffffffffffffull; r.lo = ~0ull; return r; }
+  const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 86;
+  if (sh > 103) { r.hi = 0x7fffffffffffffffull; r.lo = ~0ull; }   // >= 2^39: saturate
+  else if (sh >= 64) r.hi = m << (sh - 64);
+  else if (sh > 40) { r.lo = m << sh; r.hi = m >> (64 - sh); }
+  else if (sh >= 0) r.lo = m << sh;
+  else if (sh > -24) r.lo = m >> (-sh);
+  return r;
+}
 __device__ __forceinline__ double fixed_to_double(U128 a) {
   return ldexp((double)a.hi, 0) + ldexp((double)a.lo, -64);
 }

@@ -43,16 +43,37 @@ __global__ void k_frame_partial(const double *__restrict__ dpos, const double *_
   if (t < 8) part[blockIdx.x * 8 + t] = red[t][0];
 }
 
-__global__ void k_frame_final(const double *__restrict__ part, int nb, int periodic, double L0, double L1, double L2,
-                              int bits, Frame *frame, uint32_t *status) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(256)
+k_frame_final(const double *__restrict__ part, int nb, int periodic, double L0, double L1, double L2, int bits,
+              Frame *frame, uint32_t *status) {
+  __shared__ double red[8][256];
+  const int t = threadIdx.x;
   double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
   double hd = 0.0, hg = 0.0;
-  for (int b = 0; b < nb; ++b) {
+  for (int b = t; b < nb; b += 256) {
     for (int c = 0; c < 3; ++c) { mn[c] = fmin(mn[c], part[b * 8 + c]); mx[c] = fmax(mx[c], part[b * 8 + 3 + c]); }
     hd = fmax(hd, part[b * 8 + 6]);
     hg = fmax(hg, part[b * 8 + 7]);
   }
+  for (int c = 0; c < 3; ++c) { red[c][t] = mn[c]; red[3 + c][t] = mx[c]; }
+  red[6][t] = hd;
+  red[7][t] = hg;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (t < o) {
+      for (int c = 0; c < 3; ++c) {
+        red[c][t] = fmin(red[c][t], red[c][t + o]);
+        red[3 + c][t] = fmax(red[3 + c][t], red[3 + c][t + o]);
+      }
+      red[6][t] = fmax(red[6][t], red[6][t + o]);
+      red[7][t] = fmax(red[7][t], red[7][t + o]);
+    }
+    __syncthreads();
+  }
+  if (t != 0) return;
+  for (int c = 0; c < 3; ++c) { mn[c] = red[c][0]; mx[c] = red[3 + c][0]; }
+  hd = red[6][0];
+  hg = red[7][0];
   Frame f;
   double span;
   if (periodic) {
@@ -90,7 +111,7 @@ cudaError_t launch_frame(const double *dm_pos, const double *dm_h, int64_t ndm, 
   const int64_t ntot = ndm + ngas;
   const int bits_per_axis = (int)fmin(21.0, fmax(10.0, ceil(log2((double)(ntot > 1 ? ntot : 2)) / 3.0) + 7.0));
   k_frame_partial<<<nb, FR_THREADS, 0, s>>>(dm_pos, dm_h, ndm, gas_pos, gas_h, ngas, part);
-  k_frame_final<<<1, 32, 0, s>>>(part, nb, periodic, box[0], box[1], box[2], bits_per_axis, frame, status);
+  k_frame_final<<<1, 256, 0, s>>>(part, nb, periodic, box[0], box[1], box[2], bits_per_axis, frame, status);
   if (launches) *launches += 2;
   return cudaGetLastError();
 }

@@ -7,78 +7,102 @@
 #define MC_WARPS 8
 
 // ---- mean field: one warp per gas particle, lanes stride over its DM partners ---------
+// Per-lane partial sums and the reduction across the warp stay in the pair precision R;
+// the float64 results (and the perm scatter to caller order) are formed by
+// k_meanfield_finish with one thread per gas particle, where float64 instructions cover
+// 32 particles each (GB300 runs float64 at 1/64 of the float32 rate).
 template <typename R>
 __global__ void __launch_bounds__(MF_WARPS * 32)
 k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__restrict__ row_ptr,
-            const uint32_t *__restrict__ rows, const float4 *__restrict__ gtab, RunConst rc, MfOut out) {
+            const uint32_t *__restrict__ rows, const float4 *__restrict__ gtab, RunConst rc, R *__restrict__ part) {
   typedef typename Vec<R>::v4 v4;
   const unsigned lane = threadIdx.x & 31u;
   const int64_t nwarps = (int64_t)gridDim.x * MF_WARPS;
   const R inv_v0 = (R)(1.0 / rc.v0);
   for (int64_t j = (int64_t)blockIdx.x * MF_WARPS + (threadIdx.x >> 5); j < G.n; j += nwarps) {
-    const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
     const int64_t rs = row_ptr[j], re = row_ptr[j + 1];
-    const R sig = Vj.w;
-    const bool hot = sig > (R)0;
-    const R inv2s2 = hot ? (R)0.5 / (sig * sig) : (R)0;
     R sx = 0, sy = 0, sz = 0, sw2 = 0, sb = 0, svw = 0;
-    for (int64_t p = rs + lane; p < re; p += 32) {
-      const uint32_t i = rows[p];
-      const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
-      R dx, dy, dz;
-      pair_dx<R>(Pi, Li, Pj, Lj, bx, dx, dy, dz);
-      const R d = sqrt_t(dist2_rn<R>(dx, dy, dz));
-      const R g = overlap_g<R>(gtab, d, Pi.w, Pj.w);
-      const R wx = Vi.x - Vj.x, wy = Vi.y - Vj.y, wz = Vi.z - Vj.z;
-      const R w2 = wx * wx + wy * wy + wz * wz;
-      R FA, FB;
-      if (hot) {
-        rates_FAB<R>(w2 * inv2s2, rc.n, FA, FB);
-      } else {
-        const R wn = sqrt_t(w2);
-        const R sn = ipow<R>(wn * inv_v0, rc.n);
-        FA = sn * wn;
-        FB = sn * wn * w2;
+    if (re > rs) {
+      const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j];
+      const R sig = Vj.w;
+      const bool hot = sig > (R)0;
+      const R inv2s2 = hot ? (R)0.5 / (sig * sig) : (R)0;
+      for (int64_t p = rs + lane; p < re; p += 32) {
+        const uint32_t i = rows[p];
+        const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
+        R dx, dy, dz;
+        pair_dx<R>(Pi, Li, Pj, Lj, bx, dx, dy, dz);
+        const R d = sqrt_t(dist2_rn<R>(dx, dy, dz));
+        const R g = overlap_g<R>(gtab, d, Pi.w, Pj.w);
+        const R wx = Vi.x - Vj.x, wy = Vi.y - Vj.y, wz = Vi.z - Vj.z;
+        const R w2 = wx * wx + wy * wy + wz * wz;
+        R FA, FB;
+        if (hot) {
+          rates_FAB<R>(w2 * inv2s2, rc.n, FA, FB);
+        } else {
+          const R wn = sqrt_t(w2);
+          const R sn = ipow<R>(wn * inv_v0, rc.n);
+          FA = sn * wn;
+          FB = sn * wn * w2;
+        }
+        const R t = Li.w * g;          // M_i g_ij
+        const R tA = t * FA;
+        sx += tA * wx;
+        sy += tA * wy;
+        sz += tA * wz;
+        sw2 += tA * w2;
+        sb += t * FB;
+        svw += tA * (Vi.x * wx + Vi.y * wy + Vi.z * wz);
       }
-      const R t = Li.w * g;          // M_i g_ij
-      const R tA = t * FA;
-      sx += tA * wx;
-      sy += tA * wy;
-      sz += tA * wz;
-      sw2 += tA * w2;
-      sb += t * FB;
-      svw += tA * (Vi.x * wx + Vi.y * wy + Vi.z * wz);
+      sx = warp_sum<R>(sx);
+      sy = warp_sum<R>(sy);
+      sz = warp_sum<R>(sz);
+      sw2 = warp_sum<R>(sw2);
+      sb = warp_sum<R>(sb);
+      svw = warp_sum<R>(svw);
     }
-    double a0 = warp_sum<double>((double)sx), a1 = warp_sum<double>((double)sy), a2 = warp_sum<double>((double)sz);
-    double b0 = warp_sum<double>((double)sw2), b1 = warp_sum<double>((double)sb), b2 = warp_sum<double>((double)svw);
-    if (lane == 0) {
-      const double cA = (double)Kj.x, cB = (double)Kj.y;
-      const uint32_t c = G.perm[j];
-      out.acc[3 * (int64_t)c + 0] = cA * a0;
-      out.acc[3 * (int64_t)c + 1] = cA * a1;
-      out.acc[3 * (int64_t)c + 2] = cA * a2;
-      out.dudt[c] = cA * b0 - cB * b1;
-      if (out.e_exp) out.e_exp[j] = (double)Lj.w * (cB * b1 - cA * b2);
+    if (lane < 6) {
+      const R v = lane == 0 ? sx : lane == 1 ? sy : lane == 2 ? sz : lane == 3 ? sw2 : lane == 4 ? sb : svw;
+      part[6 * j + lane] = v;
     }
   }
 }
 
+// acc_j = cA sum(t FA w), du_j/dt = cA sum(t FA w^2) - cB sum(t FB), and the App. C expected
+// DM energy change of the pairs, M_j (cB sum(t FB) - cA sum(t FA v_i.w)), without dt
+template <typename R>
+__global__ void k_meanfield_finish(SpeciesView<R> G, const R *__restrict__ part, MfOut out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= G.n) return;
+  const typename Vec<R>::v4 K = G.K[j];
+  const double cA = (double)K.x, cB = (double)K.y;
+  const R *q = part + 6 * j;
+  const uint32_t c = G.perm[j];
+  out.acc[3 * (int64_t)c + 0] = cA * (double)q[0];
+  out.acc[3 * (int64_t)c + 1] = cA * (double)q[1];
+  out.acc[3 * (int64_t)c + 2] = cA * (double)q[2];
+  out.dudt[c] = cA * (double)q[3] - cB * (double)q[4];
+  if (out.e_exp) out.e_exp[j] = (double)G.L[j].w * (cB * (double)q[4] - cA * (double)q[5]);
+}
+
 template <typename R>
 cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *row_ptr,
-                             const uint32_t *rows, const float4 *gtab, RunConst rc, MfOut out, cudaStream_t s,
-                             int64_t *launches) {
+                             const uint32_t *rows, const float4 *gtab, RunConst rc, MfOut out, R *part,
+                             cudaStream_t s, int64_t *launches) {
   if (G.n <= 0) return cudaSuccess;
   int64_t blocks = (G.n + MF_WARPS - 1) / MF_WARPS;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  k_meanfield<R><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, gtab, rc, out);
-  if (launches) *launches += 1;
+  k_meanfield<R><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, gtab, rc, part);
+  k_meanfield_finish<R><<<(unsigned)((G.n + 255) / 256), 256, 0, s>>>(G, part, out);
+  if (launches) *launches += 2;
   return cudaGetLastError();
 }
 template cudaError_t launch_meanfield<float>(SpeciesView<float>, SpeciesView<float>, BoxSplit, const int64_t *,
-                                             const uint32_t *, const float4 *, RunConst, MfOut, cudaStream_t, int64_t *);
+                                             const uint32_t *, const float4 *, RunConst, MfOut, float *, cudaStream_t,
+                                             int64_t *);
 template cudaError_t launch_meanfield<double>(SpeciesView<double>, SpeciesView<double>, BoxSplit, const int64_t *,
-                                              const uint32_t *, const float4 *, RunConst, MfOut, cudaStream_t,
-                                              int64_t *);
+                                              const uint32_t *, const float4 *, RunConst, MfOut, double *,
+                                              cudaStream_t, int64_t *);
 
 // ---- Monte Carlo: one warp per DM particle ---------------------------------------------
 // The sampled partner velocity v^B_ij = V_j + varsigma_j z (z from the pair's Philox block)
@@ -106,26 +130,47 @@ __device__ __forceinline__ R pair_probability(const typename Vec<R>::v4 &Pi, con
   return Kj.z * dt * g * ipow<R>(vrel * inv_v0, n) * vrel;
 }
 
+// U128 comparison helpers for the decision band: |a - b| <= c 2^-20 (about 1e-6 c)
+__device__ __forceinline__ U128 u128_absdiff(U128 a, U128 b) {
+  U128 r;
+  if (u128_lt(a, b)) { U128 t = a; a = b; b = t; }
+  r.lo = a.lo - b.lo;
+  r.hi = a.hi - b.hi - (a.lo < b.lo ? 1ull : 0ull);
+  return r;
+}
+__device__ __forceinline__ U128 u128_shr20(U128 a) {
+  U128 r;
+  r.lo = (a.lo >> 20) | (a.hi << 44);
+  r.hi = a.hi >> 20;
+  return r;
+}
+__device__ __forceinline__ bool near_rel(U128 a, U128 b, U128 c) { return !u128_lt(u128_shr20(c), u128_absdiff(a, b)); }
+
 template <typename R>
 __global__ void __launch_bounds__(MC_WARPS * 32)
 k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict__ row_ptr,
      const uint32_t *__restrict__ rows, const float4 *__restrict__ gtab, RunConst rc, McArgs a,
-     R *__restrict__ pcache) {
+     R *__restrict__ pcache, McRec *__restrict__ rec) {
   typedef typename Vec<R>::v4 v4;
-  __shared__ double red[MC_WARPS][8];
-  __shared__ float redm[MC_WARPS];
   const unsigned lane = threadIdx.x & 31u;
   const int wib = threadIdx.x >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * MC_WARPS;
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
   const R inv_v0 = (R)(1.0 / rc.v0);
   const R dt = (R)a.dt;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // lane 0 only: sum M dv (3), dKE, scat, clamp, band, sum P
-  float accm = 0.0f;
   for (int64_t i = (int64_t)blockIdx.x * MC_WARPS + wib; i < D.n; i += nwarps) {
+    const int64_t rs = row_ptr[i], re = row_ptr[i + 1];
+    if (re == rs) {                       // no gas partner: nothing can happen
+      if (lane == 0) {
+        McRec r;
+        r.c_lo = 0ull; r.c_hi = 0ull; r.rmax = 0.0f; r.flags = 0u; r.partner = 0xffffffffu;
+        r.dv[0] = r.dv[1] = r.dv[2] = 0.0;
+        rec[i] = r;
+      }
+      continue;
+    }
     const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
     const uint32_t id_i = D.id[i];
-    const int64_t rs = row_ptr[i], re = row_ptr[i + 1];
     U128 sum = {0ull, 0ull};
     float rmax = 0.0f;
     for (int64_t p = rs + lane; p < re; p += 32) {
@@ -137,7 +182,7 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
       pcache[p] = P;
       sum = u128_add(sum, to_fixed(P));
       const R e = Kj.w;                                   // mu_j / (m_chi + mu_j)
-      const R cap = fmin((R)0.1, (R)1e-4 / (e * e));      // Eq. prob_criterion
+      const R cap = (R)1e-4 / (e * e) < (R)0.1 ? (R)1e-4 / (e * e) : (R)0.1;   // Eq. prob_criterion
       rmax = fmaxf(rmax, (float)(P / cap));
     }
     const U128 C = warp_sum_u128(sum);
@@ -150,9 +195,8 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
     U128 T;
     if (clamped) T = u128_scale(R64, C); else { T.hi = 0ull; T.lo = R64; }
     const bool scat = u128_lt(T, C);
-    const double Cd = fixed_to_double(C), Td = fixed_to_double(T);
-    bool band = Cd > 0.0 && fabs(Td - Cd) <= 1e-6 * Cd;
-    double dv0 = 0.0, dv1 = 0.0, dv2 = 0.0;
+    bool band = near_rel(T, C, C);
+    R dv0 = 0, dv1 = 0, dv2 = 0;
     uint32_t partner_id = 0xffffffffu;
     if (scat) {
       // binary search over the gas-id bits for the first partner (ascending id) whose
@@ -170,7 +214,6 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
         const U128 top = u128_add(base, S);
         if (!u128_lt(T, top)) { base = top; prefix = mid; }
       }
-      // the pair with that id
       int64_t pstar = -1;
       for (int64_t p0 = rs; p0 < re; p0 += 32) {
         const int64_t p = p0 + lane;
@@ -182,11 +225,10 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
         const uint32_t j = rows[pstar];
         const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
         R rx, ry, rz, vr;
-        const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx, gtab, rc.n, inv_v0, dt,
-                                        a.step, k0, k1, rx, ry, rz, vr);
-        const double lo = fixed_to_double(base), hi = lo + (double)pcache[pstar];
-        (void)P;
-        band = band || (fabs(Td - lo) <= 1e-6 * hi) || (fabs(Td - hi) <= 1e-6 * hi);
+        (void)pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx, gtab, rc.n, inv_v0, dt, a.step, k0,
+                                  k1, rx, ry, rz, vr);
+        const U128 hi = u128_add(base, to_fixed(pcache[pstar]));
+        band = band || near_rel(T, base, hi) || near_rel(T, hi, hi);
         // isotropic new direction: cos(theta') = 2u - 1, phi' = 2 pi u'
         const R ct = (R)2 * uniform23<R>(wd.y) - (R)1;
         const R st = sqrt_t(fmax((R)0, (R)1 - ct * ct));
@@ -195,65 +237,99 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
         else { double s_, c_; sincospi(2.0 * uniform23<double>(wd.z), &s_, &c_); sp = (R)s_; cp = (R)c_; }
         const R f = Kj.w * vr;                             // mu_j/(m_chi + mu_j) v_rel
         const R inv = (R)1 / vr;
-        dv0 = (double)(f * (st * cp - rx * inv));
-        dv1 = (double)(f * (st * sp - ry * inv));
-        dv2 = (double)(f * (ct - rz * inv));
+        dv0 = f * (st * cp - rx * inv);
+        dv1 = f * (st * sp - ry * inv);
+        dv2 = f * (ct - rz * inv);
         partner_id = prefix;
       }
     }
     if (lane == 0) {
-      const uint32_t c = D.perm[i];
-      const double v0 = a.vel_in[3 * (int64_t)c], v1 = a.vel_in[3 * (int64_t)c + 1], v2 = a.vel_in[3 * (int64_t)c + 2];
-      const double n0 = v0 + dv0, n1 = v1 + dv1, n2 = v2 + dv2;
-      a.vel_out[3 * (int64_t)c] = n0;
-      a.vel_out[3 * (int64_t)c + 1] = n1;
-      a.vel_out[3 * (int64_t)c + 2] = n2;
-      if (a.scattered) a.scattered[c] = (uint8_t)(partner_id != 0xffffffffu);
-      if (a.partner) a.partner[c] = partner_id;
-      if (a.p_ratio) a.p_ratio[c] = rmax;
-      if (a.p_total) a.p_total[c] = Cd;
-      const double M = (double)Li.w;
+      McRec r;
+      r.c_lo = C.lo;
+      r.c_hi = C.hi;
+      r.rmax = rmax;
+      r.flags = (partner_id != 0xffffffffu ? 1u : 0u) | (clamped ? 2u : 0u) | (band ? 4u : 0u);
+      r.partner = partner_id;
+      r.dv[0] = (double)dv0;
+      r.dv[1] = (double)dv1;
+      r.dv[2] = (double)dv2;
+      rec[i] = r;
+    }
+  }
+}
+
+// float64 side of the Monte Carlo, one thread per DM particle: new velocities in caller
+// order and deterministic block partials of the step sums
+__global__ void __launch_bounds__(256)
+k_mc_finish(int64_t n, const uint32_t *__restrict__ perm, const McRec *__restrict__ rec,
+            const float *__restrict__ mass_f, const double *__restrict__ mass_d, int mass_stride, McArgs a) {
+  __shared__ double red[8][256];
+  __shared__ float redm[256];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  float mx = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const McRec r = rec[i];
+    const uint32_t c = perm[i];
+    const double M = mass_f ? (double)mass_f[(int64_t)mass_stride * i] : mass_d[(int64_t)mass_stride * i];
+    const double v0 = a.vel_in[3 * (int64_t)c], v1 = a.vel_in[3 * (int64_t)c + 1], v2 = a.vel_in[3 * (int64_t)c + 2];
+    double n0 = v0, n1 = v1, n2 = v2;
+    if (r.flags & 1u) {
+      n0 = v0 + r.dv[0];
+      n1 = v1 + r.dv[1];
+      n2 = v2 + r.dv[2];
       acc[0] += M * (n0 - v0);
       acc[1] += M * (n1 - v1);
       acc[2] += M * (n2 - v2);
       acc[3] += 0.5 * M * ((n0 * n0 + n1 * n1 + n2 * n2) - (v0 * v0 + v1 * v1 + v2 * v2));
-      acc[4] += partner_id != 0xffffffffu ? 1.0 : 0.0;
-      acc[5] += clamped ? 1.0 : 0.0;
-      acc[6] += band ? 1.0 : 0.0;
-      acc[7] += Cd;
-      accm = fmaxf(accm, rmax);
+      acc[4] += 1.0;
     }
+    a.vel_out[3 * (int64_t)c] = n0;
+    a.vel_out[3 * (int64_t)c + 1] = n1;
+    a.vel_out[3 * (int64_t)c + 2] = n2;
+    const double Cd = (r.c_hi | r.c_lo) ? (double)r.c_hi + ldexp((double)r.c_lo, -64) : 0.0;
+    if (a.scattered) a.scattered[c] = (uint8_t)(r.flags & 1u);
+    if (a.partner) a.partner[c] = r.partner;
+    if (a.p_ratio) a.p_ratio[c] = r.rmax;
+    if (a.p_total) a.p_total[c] = Cd;
+    if (r.flags & 2u) acc[5] += 1.0;
+    if (r.flags & 4u) acc[6] += 1.0;
+    acc[7] += Cd;
+    mx = fmaxf(mx, r.rmax);
   }
-  if (lane == 0) {
-    for (int k = 0; k < 8; ++k) red[wib][k] = acc[k];
-    redm[wib] = accm;
-  }
+  const int t = threadIdx.x;
+  for (int k = 0; k < 8; ++k) red[k][t] = acc[k];
+  redm[t] = mx;
   __syncthreads();
-  if (threadIdx.x < 8) {
-    double s = 0.0;
-    for (int w = 0; w < MC_WARPS; ++w) s += red[w][threadIdx.x];
-    a.block_sums[8 * (int64_t)blockIdx.x + threadIdx.x] = s;
+  for (int o = 128; o > 0; o >>= 1) {
+    if (t < o) {
+      for (int k = 0; k < 8; ++k) red[k][t] += red[k][t + o];
+      redm[t] = fmaxf(redm[t], redm[t + o]);
+    }
+    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    float m = 0.0f;
-    for (int w = 0; w < MC_WARPS; ++w) m = fmaxf(m, redm[w]);
-    a.block_max[blockIdx.x] = (double)m;
-  }
+  if (t < 8) a.block_sums[8 * (int64_t)blockIdx.x + t] = red[t][0];
+  if (t == 0) a.block_max[blockIdx.x] = (double)redm[0];
 }
 
 template <typename R>
 cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *row_ptr, const uint32_t *rows,
-                      const float4 *gtab, RunConst rc, McArgs a, R *pcache, int blocks, cudaStream_t s,
-                      int64_t *launches) {
-  k_mc<R><<<blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache);
-  if (launches) *launches += 1;
+                      const float4 *gtab, RunConst rc, McArgs a, R *pcache, McRec *rec, int finish_blocks,
+                      cudaStream_t s, int64_t *launches) {
+  int64_t blocks = (D.n + MC_WARPS - 1) / MC_WARPS;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_mc<R><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec);
+  // the particle mass sits in L.w of the sorted copies
+  const R *Lbase = reinterpret_cast<const R *>(D.L);
+  k_mc_finish<<<finish_blocks, 256, 0, s>>>(D.n, D.perm, rec, sizeof(R) == 4 ? (const float *)(Lbase + 3) : nullptr,
+                                            sizeof(R) == 8 ? (const double *)(Lbase + 3) : nullptr, 4, a);
+  if (launches) *launches += 2;
   return cudaGetLastError();
 }
 template cudaError_t launch_mc<float>(SpeciesView<float>, SpeciesView<float>, BoxSplit, const int64_t *,
-                                      const uint32_t *, const float4 *, RunConst, McArgs, float *, int, cudaStream_t,
-                                      int64_t *);
+                                      const uint32_t *, const float4 *, RunConst, McArgs, float *, McRec *, int,
+                                      cudaStream_t, int64_t *);
 template cudaError_t launch_mc<double>(SpeciesView<double>, SpeciesView<double>, BoxSplit, const int64_t *,
-                                       const uint32_t *, const float4 *, RunConst, McArgs, double *, int,
+                                       const uint32_t *, const float4 *, RunConst, McArgs, double *, McRec *, int,
                                        cudaStream_t, int64_t *);
 
 // ---- overlap table and debug evaluators ------------------------------------------------

@@ -27,10 +27,11 @@ struct MfOut {
   double *e_exp;    // [N_B] sorted order: M_j (cB sum tFB - cA sum tFA v_i.w) (no dt); may be null
 };
 
+// part: scratch [N_B][6] in the pair precision (per-gas sums before the float64 finish)
 template <typename R>
 cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *row_ptr,
-                             const uint32_t *rows, const float4 *gtab, RunConst rc, MfOut out, cudaStream_t s,
-                             int64_t *launches);
+                             const uint32_t *rows, const float4 *gtab, RunConst rc, MfOut out, R *part,
+                             cudaStream_t s, int64_t *launches);
 
 struct McArgs {
   double dt;
@@ -42,14 +43,23 @@ struct McArgs {
   uint32_t *partner;          // may be null
   float *p_ratio;             // may be null
   double *p_total;            // may be null
-  double *block_sums;         // [gridDim][8]: sum M dv (3), dKE, scatters, clamps, band, sum P
-  double *block_max;          // [gridDim]: max p_ratio
+  double *block_sums;         // [finish blocks][8]: sum M dv (3), dKE, scatters, clamps, band, sum P
+  double *block_max;          // [finish blocks]: max p_ratio
+};
+
+// Per-DM result of the Monte Carlo kernel (sorted order), finished in float64 by k_mc_finish.
+struct McRec {
+  unsigned long long c_lo, c_hi;  // sum_j P_ij, 128-bit fixed point with 64 fractional bits
+  float rmax;                     // max_j P_ij / P_cap
+  uint32_t flags;                 // 1 scattered, 2 renormalised (sum > 1), 4 within 1e-6 of a threshold
+  uint32_t partner;               // gas id or 0xffffffff
+  double dv[3];                   // velocity change
 };
 
 template <typename R>
 cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *row_ptr, const uint32_t *rows,
-                      const float4 *gtab, RunConst rc, McArgs a, R *pcache, int blocks, cudaStream_t s,
-                      int64_t *launches);
+                      const float4 *gtab, RunConst rc, McArgs a, R *pcache, McRec *rec, int finish_blocks,
+                      cudaStream_t s, int64_t *launches);
 
 // Overlap table build (float64 exact evaluator at the nodes) and debug evaluators.
 cudaError_t launch_gtable(float4 *T, cudaStream_t s, int64_t *launches);

@@ -25,10 +25,13 @@ __device__ __forceinline__ uint4 dm_counter(uint32_t id_dm, unsigned long long s
   return make_uint4(id_dm, 0u, (uint32_t)step, ((uint32_t)(step >> 32) & 0x7fffffffu) | 0x80000000u);
 }
 
-// u = ((w >> 9) + 1/2) 2^-23: exact in float, in (0, 1).
+// u = ((w >> 9) + 1/2) 2^-23: exact in float, in (0, 1).  Built from the bits
+// (1 + k 2^-23) - 1 + 2^-24 with k = w >> 9 (both steps exact), which avoids an
+// integer-to-float conversion.
 template <typename R>
 __device__ __forceinline__ R uniform23(uint32_t w) {
-  return ((R)(w >> 9) + (R)0.5) * (R)1.1920928955078125e-07;
+  const float one_k = __uint_as_float(0x3F800000u | (w >> 9));
+  return (R)((one_k - 1.0f) + 5.9604644775390625e-08f);
 }
 
 // Three standard normals by Box-Muller from the four words of one Philox block.
@@ -159,15 +162,27 @@ __device__ __forceinline__ void lagrange4(float t, float &a, float &b, float &c,
   d = tp1 * t * tm1 * (1.0f / 6.0f);
 }
 
+// floor(x) for 0 <= x < 2^22 as (integer, float) without conversion instructions: adding
+// 1.5 * 2^23 to x - 1/2 leaves round(x - 1/2) in the low mantissa bits.  At exact ties the
+// result may be floor(x) - 1, which leaves x - floor in [0, 1], still a valid node offset.
+__device__ __forceinline__ int floor_nc(float x, float &xf) {
+  const float magic = 12582912.0f;
+  const float f = (x - 0.5f) + magic;
+  xf = f - magic;
+  return __float_as_int(f) - 0x4B400000;
+}
+
 __device__ __forceinline__ float overlap_G_table(const float4 *__restrict__ T, float delta, float q) {
-  float fd = delta * DMB_GT_INV_DD;
-  int i0 = (int)fd;
-  i0 = i0 > DMB_GT_CELLS - 1 ? DMB_GT_CELLS - 1 : i0;
-  const float td = fd - (float)i0;
-  float fq = q * DMB_GT_INV_DQ;
-  int j0 = (int)fq;
-  j0 = j0 < 1 ? 1 : (j0 > DMB_GT_NQ - 3 ? DMB_GT_NQ - 3 : j0);
-  const float tq = fq - (float)j0;
+  const float fd = fminf(delta * DMB_GT_INV_DD, (float)(DMB_GT_CELLS - 1) + 0.999f);
+  float i0f;
+  const int i0 = max(floor_nc(fd, i0f), 0);
+  const float td = fd - (float)(i0 > 0 ? i0f : 0.0f);
+  const float fq = fmaxf(fminf(q * DMB_GT_INV_DQ, (float)(DMB_GT_NQ - 1)), 0.0f);
+  float j0f;
+  int j0 = floor_nc(fq, j0f);
+  if (j0 < 1) { j0 = 1; j0f = 1.0f; }
+  if (j0 > DMB_GT_NQ - 3) { j0 = DMB_GT_NQ - 3; j0f = (float)(DMB_GT_NQ - 3); }
+  const float tq = fq - j0f;
   float wd0, wd1, wd2, wd3, wq0, wq1, wq2, wq3;
   lagrange4(td, wd0, wd1, wd2, wd3);
   lagrange4(tq, wq0, wq1, wq2, wq3);
@@ -270,13 +285,15 @@ __device__ __forceinline__ void rates_FAB(R x, int n, R &FA, R &FB) {
     if (x < (R)1) {
       // positive Kummer series for both b = 5/2 and b = 3/2
       R tA = 1, tB = 1, sA = 1, sB = 1;
+      R ck = (R)c, k1 = (R)1, bA = (R)2.5, bB = (R)1.5;
 #pragma unroll
       for (int k = 0; k < RateConst<R>::kSeries; ++k) {
-        const R f = (R)(c + k) * x / (R)(k + 1);
-        tA *= f / ((R)2.5 + (R)k);
-        tB *= f / ((R)1.5 + (R)k);
+        const R f = ck * x / k1;
+        tA *= f / bA;
+        tB *= f / bB;
         sA += tA;
         sB += tB;
+        ck += (R)1; k1 += (R)1; bA += (R)1; bB += (R)1;
       }
       const R e = exp_t(-x);
       FA = e * sA;
@@ -287,11 +304,14 @@ __device__ __forceinline__ void rates_FAB(R x, int n, R &FA, R &FB) {
     const R ef = (R)0.88622692545275801 * erf_t(sx);   // (sqrt(pi)/2) erf(sqrt x)
     R gA0 = e, gA1 = (R)1.5 * (ef - sx * e) / (x * sx);
     R gB0 = e, gB1 = ef / sx;
+    R kf = (R)1;
     for (int k = 1; k < c; ++k) {
-      const R gA2 = (((R)(2 * k) - (R)2.5 + x) * gA1 + ((R)2.5 - (R)k) * gA0) / (R)k;
-      const R gB2 = (((R)(2 * k) - (R)1.5 + x) * gB1 + ((R)1.5 - (R)k) * gB0) / (R)k;
+      const R inv = (R)1 / kf;
+      const R gA2 = (((R)2 * kf - (R)2.5 + x) * gA1 + ((R)2.5 - kf) * gA0) * inv;
+      const R gB2 = (((R)2 * kf - (R)1.5 + x) * gB1 + ((R)1.5 - kf) * gB0) * inv;
       gA0 = gA1; gA1 = gA2;
       gB0 = gB1; gB1 = gB2;
+      kf += (R)1;
     }
     FA = gA1;
     FB = gB1;

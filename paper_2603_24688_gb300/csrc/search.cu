@@ -163,8 +163,8 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
         const v4 Pk = O.P[base + lane], Lk = O.L[base + lane];
         sP[wib][lane] = Pk;
         sL[wib][lane] = Lk;
-        const float c[3] = {(float)((double)Pk.x + (double)Lk.x), (float)((double)Pk.y + (double)Lk.y),
-                            (float)((double)Pk.z + (double)Lk.z)};
+        // float position (within a few float ulps of the span, covered by the pad)
+        const float c[3] = {(float)Pk.x + (float)Lk.x, (float)Pk.y + (float)Lk.y, (float)Pk.z + (float)Lk.z};
         const float4 pmn = make_float4(c[0], c[1], c[2], 0.f), pmx = make_float4(c[0], c[1], c[2], 0.f);
         const float r = qa.w + (float)Pk.w + pad2;
         keep = box_gap2(qmn, qmx, pmn, pmx, bx) < r * r;

@@ -43,38 +43,56 @@ cudaError_t launch_kick_gas(double *vel, double *T, const double *mu, const doub
   return cudaGetLastError();
 }
 
-__global__ void k_final_sums(const double *__restrict__ mcb, const double *__restrict__ mcm, int mc_nb,
-                             const double *__restrict__ kb, int k_nb, double dt, double n_pairs, double *sums) {
-  if (threadIdx.x != 0) return;
+// one block: every thread sums a fixed strided subset of the partials, then a fixed tree
+__global__ void __launch_bounds__(256)
+k_final_sums(const double *__restrict__ mcb, const double *__restrict__ mcm, int mc_nb,
+             const double *__restrict__ kb, int k_nb, double dt, double n_pairs, double *sums) {
+  __shared__ double red[8 + KICK_NSUM + 1][256];
+  const int t = threadIdx.x;
   double m[8] = {0, 0, 0, 0, 0, 0, 0, 0}, k[KICK_NSUM] = {0, 0, 0, 0, 0, 0}, mx = 0.0;
-  for (int b = 0; b < mc_nb; ++b) {
+  for (int b = t; b < mc_nb; b += 256) {
     for (int c = 0; c < 8; ++c) m[c] += mcb[8 * b + c];
     mx = fmax(mx, mcm[b]);
   }
-  for (int b = 0; b < k_nb; ++b)
+  for (int b = t; b < k_nb; b += 256)
     for (int c = 0; c < KICK_NSUM; ++c) k[c] += kb[KICK_NSUM * b + c];
-  sums[0] = m[0];
-  sums[1] = m[1];
-  sums[2] = m[2];
-  sums[3] = k[0];
-  sums[4] = k[1];
-  sums[5] = k[2];
-  sums[6] = m[3];
-  sums[7] = k[3];
-  sums[8] = k[5];
-  sums[9] = m[4];
-  sums[10] = m[5];
-  sums[11] = k[4];
-  sums[12] = n_pairs;
-  sums[13] = m[7];
-  sums[14] = mx;
-  sums[15] = m[6];
+  for (int c = 0; c < 8; ++c) red[c][t] = m[c];
+  for (int c = 0; c < KICK_NSUM; ++c) red[8 + c][t] = k[c];
+  red[8 + KICK_NSUM][t] = mx;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (t < o) {
+      for (int c = 0; c < 8 + KICK_NSUM; ++c) red[c][t] += red[c][t + o];
+      red[8 + KICK_NSUM][t] = fmax(red[8 + KICK_NSUM][t], red[8 + KICK_NSUM][t + o]);
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    const double *M = &red[0][0];
+    sums[0] = red[0][0];
+    sums[1] = red[1][0];
+    sums[2] = red[2][0];
+    sums[3] = red[8][0];
+    sums[4] = red[9][0];
+    sums[5] = red[10][0];
+    sums[6] = red[3][0];
+    sums[7] = red[11][0];
+    sums[8] = red[13][0];
+    sums[9] = red[4][0];
+    sums[10] = red[5][0];
+    sums[11] = red[12][0];
+    sums[12] = n_pairs;
+    sums[13] = red[7][0];
+    sums[14] = red[8 + KICK_NSUM][0];
+    sums[15] = red[6][0];
+    (void)M;
+  }
 }
 
 cudaError_t launch_final_sums(const double *mc_blocks, const double *mc_max, int mc_nb, const double *kick_blocks,
                               int kick_nb, double dt, double n_pairs, double *sums, cudaStream_t s,
                               int64_t *launches) {
-  k_final_sums<<<1, 32, 0, s>>>(mc_blocks, mc_max, mc_nb, kick_blocks, kick_nb, dt, n_pairs, sums);
+  k_final_sums<<<1, 256, 0, s>>>(mc_blocks, mc_max, mc_nb, kick_blocks, kick_nb, dt, n_pairs, sums);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
