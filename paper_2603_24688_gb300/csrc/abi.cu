@@ -51,7 +51,8 @@ struct dmb_ctx {
   SpeciesBufs dm, gas;
   DevBuf hist, hist_scan, scan_tmp;
   SearchBufs sg, sd;   // gas-major (gas queries, DM tree) and DM-major searches
-  DevBuf pcache, mf_part, mc_rec;
+  DevBuf pcache, mf_part, mc_rec, seg_cnt, seg_ptr, seg_row, seg_begin, t_cursor;
+  int64_t n_seg_max = 0;
   DevBuf mf_acc, mf_dudt, e_exp, mc_blocks, mc_max, kick_blocks, sums;
   DevBuf scratch_vel, search_stats;
   uint32_t *h_status = nullptr;   // pinned
@@ -272,6 +273,42 @@ dmb_status search_stage2_emit(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, Sp
   return DMB_OK;
 }
 
+// DM-major lists: transpose of the gas-major lists (counts, scan, atomic placement).
+dmb_status transpose_to_dm(dmb_ctx *ctx, const SearchBufs &sg, SearchBufs &sd, int64_t ng, int64_t nd) {
+  cudaStream_t s = ctx->stream;
+  int64_t *L = &ctx->launches;
+  if (!ensure(sd.counts, (size_t)(nd + 1) * 4) || !ensure(sd.row_ptr, (size_t)(nd + 1) * 8) ||
+      !ensure(ctx->t_cursor, (size_t)(nd + 1) * 4) || !ensure(sd.rows, (size_t)sg.n_pairs * 4))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for DM-major lists");
+  CK(cudaMemsetAsync(sd.counts.p, 0, (size_t)(nd + 1) * 4, s), "memset");
+  CK(cudaMemsetAsync(ctx->t_cursor.p, 0, (size_t)(nd + 1) * 4, s), "memset");
+  CK(launch_transpose_count(ptr<int64_t>(sg.row_ptr), ptr<uint32_t>(sg.rows), ng, ptr<uint32_t>(sd.counts), s, L),
+     "transpose count");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(sd.counts), ptr<int64_t>(sd.row_ptr), nd, ptr<int64_t>(ctx->scan_tmp), s, L),
+     "scan");
+  CK(launch_transpose_fill(ptr<int64_t>(sg.row_ptr), ptr<uint32_t>(sg.rows), ng, ptr<int64_t>(sd.row_ptr),
+                           ptr<uint32_t>(ctx->t_cursor), ptr<uint32_t>(sd.rows), s, L), "transpose fill");
+  sd.n_pairs = sg.n_pairs;
+  return DMB_OK;
+}
+
+// Mean-field segments of the gas rows (upper bound N_B + pairs / MF_SEG, no readback).
+dmb_status build_segments(dmb_ctx *ctx, const SearchBufs &sg, int64_t ng) {
+  cudaStream_t s = ctx->stream;
+  int64_t *L = &ctx->launches;
+  const int64_t nmax = ng + sg.n_pairs / MF_SEG + 1;
+  if (!ensure(ctx->seg_cnt, (size_t)(ng + 1) * 4) || !ensure(ctx->seg_ptr, (size_t)(ng + 1) * 8) ||
+      !ensure(ctx->seg_row, (size_t)nmax * 4) || !ensure(ctx->seg_begin, (size_t)nmax * 8))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for mean-field segments");
+  CK(launch_seg_counts(ptr<int64_t>(sg.row_ptr), ng, MF_SEG, ptr<uint32_t>(ctx->seg_cnt), s, L), "segments");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(ctx->seg_cnt), ptr<int64_t>(ctx->seg_ptr), ng, ptr<int64_t>(ctx->scan_tmp),
+                            s, L), "scan");
+  CK(launch_seg_map(ptr<int64_t>(sg.row_ptr), ptr<int64_t>(ctx->seg_ptr), ng, MF_SEG, ptr<uint32_t>(ctx->seg_row),
+                    ptr<int64_t>(ctx->seg_begin), s, L), "segment map");
+  ctx->n_seg_max = nmax;
+  return DMB_OK;
+}
+
 template <typename R>
 dmb_status neighbors_impl(dmb_ctx *ctx) {
   cudaStream_t s = ctx->stream;
@@ -282,29 +319,21 @@ dmb_status neighbors_impl(dmb_ctx *ctx) {
   unsigned long long *sst = ptr<unsigned long long>(ctx->search_stats);
   CK(cudaMemsetAsync(sst, 0, 16 * 8, s), "stats reset");
   SearchBufs &sg = ctx->sg, &sd = ctx->sd;
-  // stage 1 counts in both directions, then one readback of the list sizes
+  // gas-major search: stage 1 counts, one readback of the list sizes
   if ((st = search_stage1_count<R>(ctx, sg, G, D, sst)) != DMB_OK) return st;
   CK(cudaMemcpyAsync(ctx->h_tot + 0, ptr<int64_t>(sg.item_ptr) + G.cnt[0], 8, cudaMemcpyDeviceToHost, s), "readback");
   CK(cudaMemcpyAsync(ctx->h_tot + 1, ptr<int64_t>(sg.unit_ptr) + G.cnt[0], 8, cudaMemcpyDeviceToHost, s), "readback");
-  if ((st = search_stage1_count<R>(ctx, sd, D, G, sst + 4)) != DMB_OK) return st;
-  CK(cudaMemcpyAsync(ctx->h_tot + 2, ptr<int64_t>(sd.item_ptr) + D.cnt[0], 8, cudaMemcpyDeviceToHost, s), "readback");
-  CK(cudaMemcpyAsync(ctx->h_tot + 3, ptr<int64_t>(sd.unit_ptr) + D.cnt[0], 8, cudaMemcpyDeviceToHost, s), "readback");
   if ((st = check_status(ctx)) != DMB_OK) return st;
   sg.n_items = ctx->h_tot[0];
   sg.n_units = ctx->h_tot[1];
-  sd.n_items = ctx->h_tot[2];
-  sd.n_units = ctx->h_tot[3];
-  // stage 2 counts, then the pair totals
+  // stage 2 counts, then the pair total
   if ((st = search_stage2_count<R>(ctx, sg, G, D, sst)) != DMB_OK) return st;
   CK(cudaMemcpyAsync(ctx->h_tot + 4, ptr<int64_t>(sg.row_ptr) + G.n, 8, cudaMemcpyDeviceToHost, s), "readback");
-  if ((st = search_stage2_count<R>(ctx, sd, D, G, sst + 4)) != DMB_OK) return st;
-  CK(cudaMemcpyAsync(ctx->h_tot + 5, ptr<int64_t>(sd.row_ptr) + D.n, 8, cudaMemcpyDeviceToHost, s), "readback");
   if ((st = check_status(ctx)) != DMB_OK) return st;
   sg.n_pairs = G.n > 0 ? ctx->h_tot[4] : 0;
-  sd.n_pairs = D.n > 0 ? ctx->h_tot[5] : 0;
-  if (sg.n_pairs != sd.n_pairs) return fail(ctx, DMB_ERR_STATE, "pair counts of the two search directions differ");
   if ((st = search_stage2_emit<R>(ctx, sg, G, D)) != DMB_OK) return st;
-  if ((st = search_stage2_emit<R>(ctx, sd, D, G)) != DMB_OK) return st;
+  if ((st = transpose_to_dm(ctx, sg, sd, G.n, D.n)) != DMB_OK) return st;
+  if ((st = build_segments(ctx, sg, G.n)) != DMB_OK) return st;
   if (!ensure(ctx->pcache, (size_t)sd.n_pairs * (ctx->p.fp64 ? 8 : 4)))
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for the probability cache");
   ctx->n_pairs = sg.n_pairs;
@@ -319,10 +348,14 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
   o.acc = acc;
   o.dudt = dudt;
   o.e_exp = e_exp;
-  if (!ensure(ctx->mf_part, (size_t)G.n * 6 * sizeof(R))) return fail(ctx, DMB_ERR_OOM, "mean-field scratch");
-  CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows),
-                         ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), ctx->stream, &ctx->launches),
-     "meanfield");
+  if (!ensure(ctx->mf_part, (size_t)ctx->n_seg_max * 6 * sizeof(R))) return fail(ctx, DMB_ERR_OOM, "mean-field scratch");
+  SegView sv;
+  sv.seg_ptr = ptr<int64_t>(ctx->seg_ptr);
+  sv.seg_row = ptr<uint32_t>(ctx->seg_row);
+  sv.seg_begin = ptr<int64_t>(ctx->seg_begin);
+  CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv,
+                         ctx->n_seg_max, ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), ctx->stream,
+                         &ctx->launches), "meanfield");
   return DMB_OK;
 }
 
@@ -445,7 +478,8 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
     for (DevBuf *b : q) release(*b);
   }
   DevBuf *bufs[] = {&ctx->frame, &ctx->status, &ctx->frame_part, &ctx->gtab, &ctx->hist, &ctx->hist_scan,
-                    &ctx->scan_tmp, &ctx->pcache, &ctx->mf_part, &ctx->mc_rec, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
+                    &ctx->scan_tmp, &ctx->pcache, &ctx->mf_part, &ctx->mc_rec, &ctx->seg_cnt, &ctx->seg_ptr,
+                    &ctx->seg_row, &ctx->seg_begin, &ctx->t_cursor, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
                     &ctx->kick_blocks, &ctx->sums, &ctx->scratch_vel, &ctx->search_stats};
   for (DevBuf *b : bufs) release(*b);
   SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};

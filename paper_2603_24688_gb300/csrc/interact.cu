@@ -14,13 +14,16 @@
 template <typename R>
 __global__ void __launch_bounds__(MF_WARPS * 32)
 k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__restrict__ row_ptr,
-            const uint32_t *__restrict__ rows, const float4 *__restrict__ gtab, RunConst rc, R *__restrict__ part) {
+            const uint32_t *__restrict__ rows, SegView sv, const float4 *__restrict__ gtab, RunConst rc,
+            R *__restrict__ part) {
   typedef typename Vec<R>::v4 v4;
   const unsigned lane = threadIdx.x & 31u;
   const int64_t nwarps = (int64_t)gridDim.x * MF_WARPS;
   const R inv_v0 = (R)(1.0 / rc.v0);
-  for (int64_t j = (int64_t)blockIdx.x * MF_WARPS + (threadIdx.x >> 5); j < G.n; j += nwarps) {
-    const int64_t rs = row_ptr[j], re = row_ptr[j + 1];
+  const int64_t n_seg = sv.seg_ptr[G.n];
+  for (int64_t u = (int64_t)blockIdx.x * MF_WARPS + (threadIdx.x >> 5); u < n_seg; u += nwarps) {
+    const int64_t j = sv.seg_row[u];
+    const int64_t rs = sv.seg_begin[u], re = min(rs + (int64_t)MF_SEG, row_ptr[j + 1]);
     R sx = 0, sy = 0, sz = 0, sw2 = 0, sb = 0, svw = 0;
     if (re > rs) {
       const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j];
@@ -63,7 +66,7 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
     }
     if (lane < 6) {
       const R v = lane == 0 ? sx : lane == 1 ? sy : lane == 2 ? sz : lane == 3 ? sw2 : lane == 4 ? sb : svw;
-      part[6 * j + lane] = v;
+      part[6 * u + lane] = v;
     }
   }
 }
@@ -71,38 +74,41 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
 // acc_j = cA sum(t FA w), du_j/dt = cA sum(t FA w^2) - cB sum(t FB), and the App. C expected
 // DM energy change of the pairs, M_j (cB sum(t FB) - cA sum(t FA v_i.w)), without dt
 template <typename R>
-__global__ void k_meanfield_finish(SpeciesView<R> G, const R *__restrict__ part, MfOut out) {
+__global__ void k_meanfield_finish(SpeciesView<R> G, const int64_t *__restrict__ seg_ptr, const R *__restrict__ part,
+                                   MfOut out) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= G.n) return;
   const typename Vec<R>::v4 K = G.K[j];
   const double cA = (double)K.x, cB = (double)K.y;
-  const R *q = part + 6 * j;
+  double q[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t u = seg_ptr[j]; u < seg_ptr[j + 1]; ++u)   // segments in order: deterministic
+    for (int k = 0; k < 6; ++k) q[k] += (double)part[6 * u + k];
   const uint32_t c = G.perm[j];
-  out.acc[3 * (int64_t)c + 0] = cA * (double)q[0];
-  out.acc[3 * (int64_t)c + 1] = cA * (double)q[1];
-  out.acc[3 * (int64_t)c + 2] = cA * (double)q[2];
-  out.dudt[c] = cA * (double)q[3] - cB * (double)q[4];
-  if (out.e_exp) out.e_exp[j] = (double)G.L[j].w * (cB * (double)q[4] - cA * (double)q[5]);
+  out.acc[3 * (int64_t)c + 0] = cA * q[0];
+  out.acc[3 * (int64_t)c + 1] = cA * q[1];
+  out.acc[3 * (int64_t)c + 2] = cA * q[2];
+  out.dudt[c] = cA * q[3] - cB * q[4];
+  if (out.e_exp) out.e_exp[j] = (double)G.L[j].w * (cB * q[4] - cA * q[5]);
 }
 
 template <typename R>
 cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *row_ptr,
-                             const uint32_t *rows, const float4 *gtab, RunConst rc, MfOut out, R *part,
-                             cudaStream_t s, int64_t *launches) {
+                             const uint32_t *rows, SegView sv, int64_t n_seg_max, const float4 *gtab, RunConst rc,
+                             MfOut out, R *part, cudaStream_t s, int64_t *launches) {
   if (G.n <= 0) return cudaSuccess;
-  int64_t blocks = (G.n + MF_WARPS - 1) / MF_WARPS;
+  int64_t blocks = (n_seg_max + MF_WARPS - 1) / MF_WARPS;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  k_meanfield<R><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, gtab, rc, part);
-  k_meanfield_finish<R><<<(unsigned)((G.n + 255) / 256), 256, 0, s>>>(G, part, out);
+  k_meanfield<R><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc, part);
+  k_meanfield_finish<R><<<(unsigned)((G.n + 255) / 256), 256, 0, s>>>(G, sv.seg_ptr, part, out);
   if (launches) *launches += 2;
   return cudaGetLastError();
 }
 template cudaError_t launch_meanfield<float>(SpeciesView<float>, SpeciesView<float>, BoxSplit, const int64_t *,
-                                             const uint32_t *, const float4 *, RunConst, MfOut, float *, cudaStream_t,
-                                             int64_t *);
+                                             const uint32_t *, SegView, int64_t, const float4 *, RunConst, MfOut,
+                                             float *, cudaStream_t, int64_t *);
 template cudaError_t launch_meanfield<double>(SpeciesView<double>, SpeciesView<double>, BoxSplit, const int64_t *,
-                                              const uint32_t *, const float4 *, RunConst, MfOut, double *,
-                                              cudaStream_t, int64_t *);
+                                              const uint32_t *, SegView, int64_t, const float4 *, RunConst, MfOut,
+                                              double *, cudaStream_t, int64_t *);
 
 // ---- Monte Carlo: one warp per DM particle ---------------------------------------------
 // The sampled partner velocity v^B_ij = V_j + varsigma_j z (z from the pair's Philox block)

@@ -21,17 +21,35 @@ cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const F
 cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, uint32_t *unit_cnt, uint32_t *counts,
                                cudaStream_t s, int64_t *launches);
 
+cudaError_t launch_transpose_count(const int64_t *row_ptr, const uint32_t *rows, int64_t nq, uint32_t *cnt,
+                                   cudaStream_t s, int64_t *launches);
+cudaError_t launch_transpose_fill(const int64_t *row_ptr, const uint32_t *rows, int64_t nq, const int64_t *t_ptr,
+                                  uint32_t *cursor, uint32_t *t_rows, cudaStream_t s, int64_t *launches);
+
+#define MF_SEG 2048  // pairs per mean-field work segment (long rows are split)
+cudaError_t launch_seg_counts(const int64_t *row_ptr, int64_t n, int seg, uint32_t *cnt, cudaStream_t s,
+                              int64_t *launches);
+cudaError_t launch_seg_map(const int64_t *row_ptr, const int64_t *seg_ptr, int64_t n, int seg, uint32_t *seg_row,
+                           int64_t *seg_begin, cudaStream_t s, int64_t *launches);
+
+// Mean-field row segments: segment u covers pairs [begin[u], min(begin[u] + MF_SEG, end of row)).
+struct SegView {
+  const int64_t *seg_ptr;     // [N_B + 1]: segments of gas row j are [seg_ptr[j], seg_ptr[j+1])
+  const uint32_t *seg_row;    // [n_seg]
+  const int64_t *seg_begin;   // [n_seg]
+};
+
 struct MfOut {
   double *acc;      // [N_B][3] caller order
   double *dudt;     // [N_B] caller order
   double *e_exp;    // [N_B] sorted order: M_j (cB sum tFB - cA sum tFA v_i.w) (no dt); may be null
 };
 
-// part: scratch [N_B][6] in the pair precision (per-gas sums before the float64 finish)
+// part: scratch [n_seg][6] in the pair precision (per-segment sums before the float64 finish)
 template <typename R>
 cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *row_ptr,
-                             const uint32_t *rows, const float4 *gtab, RunConst rc, MfOut out, R *part,
-                             cudaStream_t s, int64_t *launches);
+                             const uint32_t *rows, SegView sv, int64_t n_seg_max, const float4 *gtab, RunConst rc,
+                             MfOut out, R *part, cudaStream_t s, int64_t *launches);
 
 struct McArgs {
   double dt;

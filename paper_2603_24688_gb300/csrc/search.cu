@@ -214,6 +214,80 @@ __global__ void k_unit_prefix(const int64_t *__restrict__ unit_ptr, int nleaf, i
   if (qi < nq) counts[qi] = run;
 }
 
+// ---- DM-major lists as the transpose of the gas-major lists ------------------------------
+// The Monte Carlo sums each DM row exactly in fixed point and picks the partner by gas id,
+// so the order inside a DM row does not affect any result; atomics place the entries.
+__global__ void k_transpose_count(const int64_t *__restrict__ row_ptr, const uint32_t *__restrict__ rows, int64_t nq,
+                                  uint32_t *__restrict__ cnt) {
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned lane = threadIdx.x & 31u;
+  if (j >= nq) return;
+  for (int64_t p = row_ptr[j] + lane; p < row_ptr[j + 1]; p += 32) atomicAdd(&cnt[rows[p]], 1u);
+}
+
+__global__ void k_transpose_fill(const int64_t *__restrict__ row_ptr, const uint32_t *__restrict__ rows, int64_t nq,
+                                 const int64_t *__restrict__ t_ptr, uint32_t *__restrict__ cursor,
+                                 uint32_t *__restrict__ t_rows) {
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned lane = threadIdx.x & 31u;
+  if (j >= nq) return;
+  for (int64_t p = row_ptr[j] + lane; p < row_ptr[j + 1]; p += 32) {
+    const uint32_t i = rows[p];
+    const uint32_t k = atomicAdd(&cursor[i], 1u);
+    t_rows[t_ptr[i] + k] = (uint32_t)j;
+  }
+}
+
+cudaError_t launch_transpose_count(const int64_t *row_ptr, const uint32_t *rows, int64_t nq, uint32_t *cnt,
+                                   cudaStream_t s, int64_t *launches) {
+  if (nq <= 0) return cudaSuccess;
+  k_transpose_count<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(row_ptr, rows, nq, cnt);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_fill(const int64_t *row_ptr, const uint32_t *rows, int64_t nq, const int64_t *t_ptr,
+                                  uint32_t *cursor, uint32_t *t_rows, cudaStream_t s, int64_t *launches) {
+  if (nq <= 0) return cudaSuccess;
+  k_transpose_fill<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(row_ptr, rows, nq, t_ptr, cursor, t_rows);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+// ---- row segments: long rows cut into pieces of at most `seg` pairs -------------------
+__global__ void k_seg_counts(const int64_t *__restrict__ row_ptr, int64_t n, int seg, uint32_t *__restrict__ cnt) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int64_t len = row_ptr[j + 1] - row_ptr[j];
+  cnt[j] = (uint32_t)(len > 0 ? (len + seg - 1) / seg : 1);    // empty rows still get one segment
+}
+
+__global__ void k_seg_map(const int64_t *__restrict__ row_ptr, const int64_t *__restrict__ seg_ptr, int64_t n, int seg,
+                          uint32_t *__restrict__ seg_row, int64_t *__restrict__ seg_begin) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  for (int64_t u = seg_ptr[j]; u < seg_ptr[j + 1]; ++u) {
+    seg_row[u] = (uint32_t)j;
+    seg_begin[u] = row_ptr[j] + (u - seg_ptr[j]) * seg;
+  }
+}
+
+cudaError_t launch_seg_counts(const int64_t *row_ptr, int64_t n, int seg, uint32_t *cnt, cudaStream_t s,
+                              int64_t *launches) {
+  if (n <= 0) return cudaSuccess;
+  k_seg_counts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(row_ptr, n, seg, cnt);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_map(const int64_t *row_ptr, const int64_t *seg_ptr, int64_t n, int seg, uint32_t *seg_row,
+                           int64_t *seg_begin, cudaStream_t s, int64_t *launches) {
+  if (n <= 0) return cudaSuccess;
+  k_seg_map<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(row_ptr, seg_ptr, n, seg, seg_row, seg_begin);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}
+
 // ---- launchers ---------------------------------------------------------------------------
 static int grid_for(int64_t warps) {
   int64_t b = (warps + SR_WARPS - 1) / SR_WARPS;
