@@ -120,6 +120,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_across_ranks(ms, pairs, dist=None):
+    """Whole-job numbers: the slowest rank's time and the sum of all ranks' pairs.
+
+    Works on any torch.distributed backend (NCCL tensors live on the GPU, gloo on CPU)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(ms), float(pairs)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    p = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
 def cpu_oracle_sample(w, budget_s=12.0, target_pairs=150_000, seed=0):
     """Time the FP64 oracle's full step on a spatial sub-box of the workload.
 
@@ -235,13 +250,8 @@ def main():
     stage_ms, nsteps = ctx.dmb_stage_times()
     ctx.dmb_set_timing(False)
     clk = clocks.stop() if clocks else None
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    pt = torch.tensor([float(pairs_total)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(pt, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    value = float(pt.item()) / (ms_max * 1e-3)
+    ms_max, pairs_all = reduce_across_ranks(ms, pairs_total, dist)
+    value = pairs_all / (ms_max * 1e-3)
     nparticles = len(w["dm"]["h"]) + len(w["gas"]["h"])
 
     # ---- roofline of the dominant kernel ----------------------------------------------
@@ -290,13 +300,10 @@ def main():
             out_host["gas_T"].copy_(gas["T"], non_blocking=True)
         f1.record(stream)
         barrier()
-        ms_e = f0.elapsed_time(f1)
-        te = torch.tensor([ms_e], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": npairs * world * a.e2e_steps / (float(te.item()) * 1e-3), "unit": "pairs/s",
+        ms_e, pairs_e = reduce_across_ranks(f0.elapsed_time(f1), npairs * a.e2e_steps, dist)
+        e2e = {"value": pairs_e / (ms_e * 1e-3), "unit": "pairs/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": float(te.item()) / a.e2e_steps}
+               "ms_per_step": ms_e / a.e2e_steps}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:

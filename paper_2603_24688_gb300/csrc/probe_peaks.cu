@@ -1,0 +1,54 @@
+// Throughput probe of the arithmetic pipes the pair kernels use: float32 FMA, float64 FMA,
+// the special-function unit (ex2), int32 multiply-add and 32-bit multiply-high (Philox).
+// Independent chains per thread; every thread writes one word so nothing is dead code.
+// Built and run by paper_2603_24688_gb300/peaks.py; not part of libdmb.so.
+#include <cstdio>
+#include <cuda_runtime.h>
+#define ITERS 4096
+__global__ void k_ffma(float* out, float a, float b) {
+  float x0=threadIdx.x, x1=x0+1, x2=x0+2, x3=x0+3, x4=x0+4, x5=x0+5, x6=x0+6, x7=x0+7;
+  for (int i=0;i<ITERS;i++){ x0=fmaf(x0,a,b);x1=fmaf(x1,a,b);x2=fmaf(x2,a,b);x3=fmaf(x3,a,b);
+    x4=fmaf(x4,a,b);x5=fmaf(x5,a,b);x6=fmaf(x6,a,b);x7=fmaf(x7,a,b);}
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3+x4+x5+x6+x7;
+}
+__global__ void k_dfma(double* out, double a, double b) {
+  double x0=threadIdx.x, x1=x0+1, x2=x0+2, x3=x0+3;
+  for (int i=0;i<ITERS/8;i++){ x0=fma(x0,a,b);x1=fma(x1,a,b);x2=fma(x2,a,b);x3=fma(x3,a,b);}
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3;
+}
+__global__ void k_mufu(float* out, float a) {
+  float x0=threadIdx.x*1e-3f, x1=x0+1e-3f, x2=x0+2e-3f, x3=x0+3e-3f;
+  for (int i=0;i<ITERS/4;i++){ x0=exp2f(x0)*a; x1=exp2f(x1)*a; x2=exp2f(x2)*a; x3=exp2f(x3)*a; }
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3;
+}
+__global__ void k_imad(unsigned* out, unsigned a, unsigned b) {
+  unsigned x0=threadIdx.x, x1=x0+1, x2=x0+2, x3=x0+3, x4=x0+4, x5=x0+5, x6=x0+6, x7=x0+7;
+  for (int i=0;i<ITERS;i++){ x0=x0*a+b;x1=x1*a+b;x2=x2*a+b;x3=x3*a+b;x4=x4*a+b;x5=x5*a+b;x6=x6*a+b;x7=x7*a+b;}
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0^x1^x2^x3^x4^x5^x6^x7;
+}
+__global__ void k_mulhi(unsigned* out, unsigned a) {
+  unsigned x0=threadIdx.x, x1=x0+1, x2=x0+2, x3=x0+3;
+  for (int i=0;i<ITERS;i++){ x0=__umulhi(x0,a)^x0;x1=__umulhi(x1,a)^x1;x2=__umulhi(x2,a)^x2;x3=__umulhi(x3,a)^x3;}
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0^x1^x2^x3;
+}
+int main(){
+  int dev=0; cudaDeviceProp p; cudaGetDeviceProperties(&p,dev);
+  printf("name=%s sms=%d l2=%d smem_optin=%zu\n", p.name, p.multiProcessorCount, p.l2CacheSize, p.sharedMemPerBlockOptin);
+  int blocks=p.multiProcessorCount*8, threads=256; size_t n=(size_t)blocks*threads;
+  void* buf; cudaMalloc(&buf, n*8);
+  cudaEvent_t e0,e1; cudaEventCreate(&e0); cudaEventCreate(&e1); float ms;
+  for(int rep=0;rep<2;rep++){
+  cudaEventRecord(e0); k_ffma<<<blocks,threads>>>((float*)buf,0.999f,0.001f); cudaEventRecord(e1); cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms,e0,e1); printf("ffma: %.1f TFLOP/s (fma=2)\n", 2.0*8*ITERS*n/ms/1e9);
+  cudaEventRecord(e0); k_dfma<<<blocks,threads>>>((double*)buf,0.999,0.001); cudaEventRecord(e1); cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms,e0,e1); printf("dfma: %.3f TFLOP/s (fma=2)\n", 2.0*4*(ITERS/8)*n/ms/1e9);
+  cudaEventRecord(e0); k_mufu<<<blocks,threads>>>((float*)buf,0.5f); cudaEventRecord(e1); cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms,e0,e1); printf("ex2: %.2f Tops/s\n", 4.0*(ITERS/4)*n/ms/1e9);
+  cudaEventRecord(e0); k_imad<<<blocks,threads>>>((unsigned*)buf,1664525u,1013904223u); cudaEventRecord(e1); cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms,e0,e1); printf("imad: %.1f Tops/s\n", 8.0*ITERS*n/ms/1e9);
+  cudaEventRecord(e0); k_mulhi<<<blocks,threads>>>((unsigned*)buf,0xD2511F53u); cudaEventRecord(e1); cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms,e0,e1); printf("umulhi+xor: %.1f Tpairs/s\n", 4.0*ITERS*n/ms/1e9);
+  }
+  cudaError_t err=cudaGetLastError(); printf("err=%s\n", cudaGetErrorString(err));
+  cudaFree(buf); return err!=cudaSuccess;
+}

@@ -53,10 +53,10 @@ _lib = None
 def load(path=LIB_PATH):
     """Load libdmb.so once; raises if it is missing (no fallback path exists)."""
     global _lib
-    if _lib is not None:
-        return _lib
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with `python -m paper_2603_24688_gb300.build`")
+    if _lib is not None and path == LIB_PATH:
+        return _lib
     lib = ctypes.CDLL(path)
     c = ctypes
     vp, i64, u64, dbl = c.c_void_p, c.c_int64, c.c_uint64, c.c_double
