@@ -37,6 +37,8 @@ LANES = 128
 # algorithmic lane operations per pair (FMA = 1 op, special functions = 1 op), counted from
 # the formulas each kernel evaluates; see DESIGN.md "Rooflines"
 OPS_PER_PAIR = {"meanfield": 150.0, "mc": 256.0}
+# quadrature provider: 64 nodes x (2 exp + ~14 ops) + the 120 ops of the rest of the pair
+QUAD_OPS_PER_PAIR = 64 * 16 + 120.0
 
 
 def parse():
@@ -46,7 +48,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dmb", choices=["dmb", "reference"])
     ap.add_argument("--workload", default="galaxy10M")
-    ap.add_argument("--n", type=int, default=0, help="power-law index of sigma(v)")
+    ap.add_argument("--n", type=int, default=-2, help="power-law index of sigma(v) = sigma0 (v/100 km/s)^n")
+    ap.add_argument("--rate", default="mlp", choices=["mlp", "quad", "closed"],
+                    help="rate provider of the timed step (the others are timed beside it)")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other rate providers")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -215,7 +220,23 @@ def main():
     dm = dmb.to_device(w["dm"])
     gas = dmb.to_device(w["gas"])
     stream = torch.cuda.current_stream()
-    ctx = dmb.Context.from_params(w["params"], stream=stream)
+    modes = {"closed": dmb.DMB_RATE_CLOSED, "quad": dmb.DMB_RATE_QUAD, "mlp": dmb.DMB_RATE_MLP}
+    prm = w["params"]
+
+    def new_ctx(rate):
+        return dmb.Context(prm["sigma0_cm2"], prm["n"], prm["m_chi_mp"], prm["v0_kms"], prm["periodic"],
+                           tuple(prm["box"]), prm["seed"], rate_mode=modes[rate], stream=stream)
+
+    surrogate = None
+    train_report = None
+    if a.rate == "mlp" or not a.no_compare:
+        tctx = new_ctx("mlp")
+        train_report = tctx.dmb_train_surrogate(nsamples=1 << 20, epochs=24, seed=11)
+        surrogate = tctx.dmb_surrogate_params()
+        tctx.close()
+    ctx = new_ctx(a.rate)
+    if a.rate == "mlp":
+        ctx.dmb_load_surrogate(surrogate)
     dt = w["dt"]
     step = 0
     sums = None
@@ -263,14 +284,63 @@ def main():
     roof = None
     fmax_ghz = peaks.get("sm_max_mhz", 2070.0) / 1e3
     alu_peak = SMS * LANES * fmax_ghz * 1e9 / 1e12          # T lane-ops/s
-    if names[dom] in OPS_PER_PAIR:
-        ach = OPS_PER_PAIR[names[dom]] * npairs / (per_step[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s", "frac": ach / alu_peak,
-                "traffic": None, "kernel": kern,
-                "peak_source": "152 SMs x 128 FP32/INT lanes x max SM clock (unit counts, not measured)"}
+
+    def roofline(stage):
+        k = names.index(stage)
+        t = per_step[k] * 1e-3
+        if stage == "meanfield" and a.rate == "mlp":
+            # the surrogate's two 128 x 128 layers: 2 x 2 x 128 x 128 flop per pair (bf16 tensor cores)
+            peak = peaks.get("bf16_tflops_sustained", 1700.0)
+            ach = 2 * 2 * 128 * 128 * npairs / t / 1e12
+            return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": None, "kernel": "k_meanfield<float, MLP>",
+                    "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind})"}
+        if stage in OPS_PER_PAIR:
+            ops = OPS_PER_PAIR[stage] if not (stage == "meanfield" and a.rate == "quad") else QUAD_OPS_PER_PAIR
+            ach = ops * npairs / t / 1e12
+            return {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s", "frac": ach / alu_peak,
+                    "traffic": None, "kernel": {"meanfield": "k_meanfield", "mc": "k_mc"}[stage],
+                    "peak_source": "152 SMs x 128 FP32/INT lanes x max SM clock (unit counts)"}
+        return None
+
+    order = np.argsort(-per_step)
+    for k in order:                      # the slowest stage that has a per-pair roofline
+        roof = roofline(names[k])
+        if roof is not None:
+            roof["stage_share"] = float(per_step[k] / per_step.sum())
+            break
     stages = {n: float(v) for n, v in zip(names, per_step)}
     for n in ("meanfield", "mc"):
-        stages[n + "_frac_alu"] = OPS_PER_PAIR[n] * npairs / (per_step[names.index(n)] * 1e-3) / 1e12 / alu_peak
+        r = roofline(n)
+        stages[n + "_frac"] = r["frac"] if r else None
+
+    # ---- the other rate providers: mean-field stage time on the same state ------------------
+    providers = {a.rate: {"meanfield_ms": float(per_step[2])}}
+    if not a.no_compare:
+        for rate in ("closed", "quad", "mlp"):
+            if rate == a.rate:
+                continue
+            c2 = new_ctx(rate)
+            if rate == "mlp":
+                c2.dmb_load_surrogate(surrogate)
+            c2.dmb_set_timing(True)
+            dm2 = {k: v.clone() for k, v in dm.items()}
+            gas2 = {k: v.clone() for k, v in gas.items()}
+            for _ in range(2):
+                c2.dmb_step(dm2, gas2, step, dt)
+            ms2, n2 = c2.dmb_stage_times()
+            providers[rate] = {"meanfield_ms": float(ms2[2] / max(n2, 1))}
+            c2.close()
+            del dm2, gas2
+        if "quad" in providers and "mlp" in providers:
+            providers["mlp_speedup_over_quad"] = providers["quad"]["meanfield_ms"] / providers["mlp"]["meanfield_ms"]
+    if train_report is not None:
+        providers["surrogate_training"] = {"seconds": float(train_report[5]), "steps": int(train_report[6]),
+                                           "samples": int(train_report[7]),
+                                           "val_mean_rel_err_A": float(train_report[3]),
+                                           "val_mean_rel_err_B": float(train_report[4]),
+                                           "val_max_rel_err_A": float(train_report[1]),
+                                           "val_max_rel_err_B": float(train_report[2])}
 
     # ---- end to end through the C ABI with host buffers ---------------------------------
     e2e = None
@@ -315,11 +385,16 @@ def main():
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 sums", "data": "synthetic",
                 "config": {"workload": f"{a.workload}: {len(w['dm']['h'])} DM Hernquist halo + "
-                                       f"{len(w['gas']['h'])} gas exponential disk, sigma0=1e-24 cm^2, n={a.n}",
-                           "rate_provider": "closed-form 1F1", "pairs_per_step": npairs,
+                                       f"{len(w['gas']['h'])} gas exponential disk, "
+                                       f"sigma = 1e-24 cm^2 (v / 100 km/s)^{a.n}",
+                           "rate_provider": {"mlp": "learned surrogate (bf16 tensor cores)",
+                                             "quad": "64-point Gauss-Legendre quadrature",
+                                             "closed": "closed-form 1F1"}[a.rate],
+                           "pairs_per_step": npairs,
                            "l2": "inputs (~1 GB) larger than L2; no flush", "parallelism": f"replicas x{world}"},
                 "particles_stepped_per_s": nparticles * world / (ms_max * 1e-3 / a.steps),
-                "stage_ms": stages, "gpu_launches": int(launches), "roofline": roof, "peak_kind": peak_kind,
+                "stage_ms": stages, "rate_providers": providers, "gpu_launches": int(launches), "roofline": roof,
+                "peak_kind": peak_kind,
                 "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line))
     ctx.close()

@@ -48,7 +48,7 @@ typedef enum {
 typedef enum {
   DMB_RATE_CLOSED = 0,  /* App. B closed forms via 1F1 (integer n >= -4, n != -3) */
   DMB_RATE_QUAD = 1,    /* Gauss-Laguerre/Hermite quadrature of Eqs. scrA/scrB */
-  DMB_RATE_MLP = 2      /* learned surrogate of the rate integrals */
+  DMB_RATE_MLP = 2      /* learned surrogate of the rate integrals (float32 only; train or load first) */
 } dmb_rate_mode;
 
 /* Physical and numerical parameters (Sec. 2.4; Table test_params for typical values). */
@@ -152,9 +152,11 @@ dmb_status dmb_step(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t
  * Uses the table (float32 mode) or the exact evaluator (fp64 mode). */
 dmb_status dmb_debug_overlap(dmb_ctx *ctx, int64_t k, const double *in, double *out);
 
-/* Debug/verification: the device rate provider's normalised integrals for k samples.
- * in: device [k] float64 x = w^2/(2 varsigma^2); out: device [k][2] float64
- * (1F1(-(n+1)/2, 5/2; -x), 1F1(-(n+3)/2, 3/2; -x)) as evaluated on the device. */
+/* Debug/verification: the device rate provider's normalised integrals for k samples
+ * (the provider chosen by params.rate_mode).  in: device [k] float64 x = w^2/(2 varsigma^2);
+ * out: device [k][2] float64 (FA, FB) with A = (alpha_n/3)(sigma0/v0^n) varsigma^(n+1) FA and
+ * B = alpha_n (sigma0/v0^n) varsigma^(n+3) FB (App. B); for the power law
+ * FA = 1F1(-(n+1)/2, 5/2; -x), FB = 1F1(-(n+3)/2, 3/2; -x). */
 dmb_status dmb_debug_rates(dmb_ctx *ctx, int64_t k, const double *in, double *out);
 
 /* Debug/verification: Philox4x32-10 on the device.  ctr: device [k][4] uint32,
@@ -176,6 +178,40 @@ dmb_status dmb_stage_times(dmb_ctx *ctx, double *ms_out, int64_t *steps_out);
  * (stage 2 count pass), candidate pair tests after the ballot filter (count pass), 0.
  * Synchronises. */
 dmb_status dmb_search_stats(dmb_ctx *ctx, uint64_t *out16);
+
+/* ---- learned surrogate of the rate integrals (rate_mode = DMB_RATE_MLP) ------------------
+ * A 4 -> 128 -> 128 -> 128 -> 2 MLP (SiLU; bf16 tensor-core hidden layers, float32
+ * accumulation) standing in for FA, FB of Eqs. scrA/scrB (the App. B normalisation).  Inputs
+ * log10(s)/2, log10(tau)/2, log10(m_chi/m_p), n/4 with s = w/varsigma, tau = varsigma^2/v0^2;
+ * outputs the residuals of log FA, log FB against envelopes with the exact small- and large-x
+ * limits.  The paper has no surrogate: it evaluates 1F1 (Sec. 2.4); quadrature is the
+ * reference it is trained on and the fallback outside the training box
+ * (s in [1e-2, 1e2], tau in [1e-3, 1e2], m_chi in [0.5, 10] m_p). */
+
+/* Train on the device: nsamples points drawn with Philox(seed), targets from the float64 device
+ * quadrature, 10% held out; Adam with a cosine schedule, batch 4096, `epochs` passes.
+ * report (host [8], may be NULL): last-batch loss, max and mean relative validation errors of
+ * FA and FB ([1],[2],[3],[4]), seconds, optimiser steps, samples.  Synchronises. */
+dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, uint64_t seed, double *report);
+
+/* Copy the float32 parameter block to host memory (count receives its length; host_out may be
+ * NULL to query it).  Layout: W1[128][4] b1 W2[128][128] b2 W3[128][128] b3 W4[2][128] b4. */
+dmb_status dmb_surrogate_params(dmb_ctx *ctx, float *host_out, int64_t *count);
+
+/* Load a parameter block (host, count floats) as the context's surrogate. */
+dmb_status dmb_load_surrogate(dmb_ctx *ctx, const float *host_params, int64_t count);
+
+/* Raw network outputs for n inputs.  X: device [n][4] float32; Y: device [n][2] float32. */
+dmb_status dmb_surrogate_infer(dmb_ctx *ctx, const float *X, int64_t n, float *Y);
+
+/* Loss and gradient of the mean squared error on a batch (checks the backward kernels).
+ * X: device [B][4], Y: device [B][2] targets, grad: device [count] float32 (dL/dp for
+ * L = sum over the batch and both outputs of (y - target)^2 / B); loss: host, may be NULL. */
+dmb_status dmb_surrogate_grad(dmb_ctx *ctx, const float *X, const float *Y, int32_t B, float *grad, double *loss);
+
+/* Number of pairs of the last mean-field call that fell back to quadrature (outside the
+ * training box).  Synchronises. */
+dmb_status dmb_surrogate_fallbacks(dmb_ctx *ctx, int64_t *out);
 
 /* Number of kernel launches the context has issued since creation (bench accounting). */
 int64_t dmb_launch_count(const dmb_ctx *ctx);

@@ -3,8 +3,14 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 
+#include <chrono>
+#include <random>
+#include <vector>
+
+#include "mlp_host.cuh"
 #include "pairs.cuh"
 #include "sort_scan.cuh"
 #include "step.cuh"
@@ -52,6 +58,11 @@ struct dmb_ctx {
   DevBuf hist, hist_scan, scan_tmp;
   SearchBufs sg, sd;   // gas-major (gas queries, DM tree) and DM-major searches
   DevBuf pcache, mf_part, mc_rec, seg_cnt, seg_ptr, seg_row, seg_begin, t_cursor;
+  // learned surrogate of the rate integrals
+  DevBuf mlp_p, mlp_m, mlp_v, mlp_w2, mlp_w3, mlp_w2t, mlp_w3t, mlp_fallback;
+  bool mlp_ready = false;
+  std::vector<int> mlp_n;        // power-law indices the network was trained for
+  double mlp_box[6] = {-2.0, 2.0, -3.0, 2.0, -0.30102999566398120, 1.0};   // log10 ranges of s, tau, m_chi
   int64_t n_seg_max = 0;
   DevBuf mf_acc, mf_dudt, e_exp, mc_blocks, mc_max, kick_blocks, sums;
   DevBuf scratch_vel, search_stats;
@@ -341,6 +352,65 @@ dmb_status neighbors_impl(dmb_ctx *ctx) {
   return DMB_OK;
 }
 
+// ---- surrogate helpers ---------------------------------------------------------------------
+double alpha_of(int n) { return pow(2.0, (n + 5) / 2.0) * tgamma(3.0 + n / 2.0) / sqrt(M_PI); }
+
+// envelope constants: EA = (1 + cA x)^((n+1)/2), EB = (1 + cB x)^((n+3)/2) with the large-x limits
+// of 1F1(-(n+1)/2, 5/2; -x) and 1F1(-(n+3)/2, 3/2; -x) (DLMF 13.7.2)
+void envelope(int n, double &cA, double &eA, double &cB, double &eB) {
+  const double c = (n + 6) / 2.0;
+  eA = (n + 1) / 2.0;
+  eB = (n + 3) / 2.0;
+  cA = eA != 0.0 ? pow(tgamma(2.5) / tgamma(c), 1.0 / eA) : 1.0;
+  cB = eB != 0.0 ? pow(tgamma(1.5) / tgamma(c), 1.0 / eB) : 1.0;
+}
+
+dmb_status ensure_mlp(dmb_ctx *ctx) {
+  const size_t np = MLP_NPARAM * 4, nw = MLP_H * MLP_H * 2;
+  if (!ensure(ctx->mlp_p, np) || !ensure(ctx->mlp_m, np) || !ensure(ctx->mlp_v, np) || !ensure(ctx->mlp_w2, nw) ||
+      !ensure(ctx->mlp_w3, nw) || !ensure(ctx->mlp_w2t, nw) || !ensure(ctx->mlp_w3t, nw) ||
+      !ensure(ctx->mlp_fallback, 16))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for the surrogate");
+  return DMB_OK;
+}
+
+MlpDev mlp_dev(dmb_ctx *ctx) {
+  MlpDev d;
+  d.p = ptr<float>(ctx->mlp_p);
+  d.m = ptr<float>(ctx->mlp_m);
+  d.v = ptr<float>(ctx->mlp_v);
+  d.w2 = ptr<__nv_bfloat16>(ctx->mlp_w2);
+  d.w3 = ptr<__nv_bfloat16>(ctx->mlp_w3);
+  d.w2t = ptr<__nv_bfloat16>(ctx->mlp_w2t);
+  d.w3t = ptr<__nv_bfloat16>(ctx->mlp_w3t);
+  return d;
+}
+
+MlpRun mlp_run(dmb_ctx *ctx) {
+  MlpRun r;
+  r.p = ptr<float>(ctx->mlp_p);
+  r.w2 = ptr<__nv_bfloat16>(ctx->mlp_w2);
+  r.w3 = ptr<__nv_bfloat16>(ctx->mlp_w3);
+  r.fallback_count = ptr<unsigned long long>(ctx->mlp_fallback);
+  MlpDomain &d = r.dom;
+  d.s_lo = (float)pow(10.0, ctx->mlp_box[0]);
+  d.s_hi = (float)pow(10.0, ctx->mlp_box[1]);
+  d.tau_lo = (float)pow(10.0, ctx->mlp_box[2]);
+  d.tau_hi = (float)pow(10.0, ctx->mlp_box[3]);
+  d.m_lo = (float)pow(10.0, ctx->mlp_box[4]);
+  d.m_hi = (float)pow(10.0, ctx->mlp_box[5]);
+  double cA, eA, cB, eB;
+  envelope(ctx->p.n, cA, eA, cB, eB);
+  d.cA = (float)cA;
+  d.cB = (float)cB;
+  d.eA = (float)eA;
+  d.eB = (float)eB;
+  d.inv_v0sq = (float)(1.0 / (ctx->p.v0_kms * ctx->p.v0_kms));
+  d.log_m = (float)log10(ctx->p.m_chi_mp);
+  d.n4 = (float)(0.25 * ctx->p.n);
+  return r;
+}
+
 template <typename R>
 dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp) {
   const SpeciesView<R> D = view<R>(ctx->dm), G = view<R>(ctx->gas);
@@ -353,8 +423,17 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
   sv.seg_ptr = ptr<int64_t>(ctx->seg_ptr);
   sv.seg_row = ptr<uint32_t>(ctx->seg_row);
   sv.seg_begin = ptr<int64_t>(ctx->seg_begin);
+  MlpRun mr = {};
+  if (ctx->rc.rate_mode == DMB_RATE_MLP) {
+    if (!ctx->mlp_ready) return fail(ctx, DMB_ERR_STATE, "surrogate rate provider selected but no trained network");
+    bool known = false;
+    for (int k : ctx->mlp_n) known = known || k == ctx->p.n;
+    if (!known) return fail(ctx, DMB_ERR_DOMAIN, "the surrogate was not trained for this power-law index");
+    mr = mlp_run(ctx);
+    CK(cudaMemsetAsync(ctx->mlp_fallback.p, 0, 8, ctx->stream), "memset");
+  }
   CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv,
-                         ctx->n_seg_max, ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), ctx->stream,
+                         ctx->n_seg_max, ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr, ctx->stream,
                          &ctx->launches), "meanfield");
   return DMB_OK;
 }
@@ -421,8 +500,10 @@ dmb_status dmb_create(dmb_ctx **out, const dmb_params *p, void *cuda_stream) {
   if (!(p->v0_kms > 0.0) || !isfinite(p->v0_kms)) return fail(nullptr, DMB_ERR_ARG, "v0 must be > 0");
   if (p->n < -4 || p->n > 16) return fail(nullptr, DMB_ERR_ARG, "power-law index n must be in [-4, 16]");
   if (!(p->m_chi_mp > 0.0) || !isfinite(p->m_chi_mp)) return fail(nullptr, DMB_ERR_ARG, "m_chi must be > 0");
-  if (p->rate_mode != DMB_RATE_CLOSED)
-    return fail(nullptr, DMB_ERR_ARG, "only the closed-form rate provider is available in this build");
+  if (p->rate_mode != DMB_RATE_CLOSED && p->rate_mode != DMB_RATE_QUAD && p->rate_mode != DMB_RATE_MLP)
+    return fail(nullptr, DMB_ERR_ARG, "unknown rate provider");
+  if (p->rate_mode == DMB_RATE_MLP && p->fp64)
+    return fail(nullptr, DMB_ERR_ARG, "the surrogate rate provider runs in float32 only");
   if (p->periodic)
     for (int k = 0; k < 3; ++k)
       if (!(p->box[k] > 0.0) || !isfinite(p->box[k])) return fail(nullptr, DMB_ERR_ARG, "periodic box sides must be > 0");
@@ -436,6 +517,7 @@ dmb_status dmb_create(dmb_ctx **out, const dmb_params *p, void *cuda_stream) {
   ctx->rc.n = p->n;
   ctx->rc.alpha = pow(2.0, (p->n + 5) / 2.0) * tgamma(3.0 + p->n / 2.0) / sqrt(M_PI);
   ctx->rc.kT_over_mp = kKB / kMP / 1e10;
+  ctx->rc.rate_mode = p->rate_mode;
   ctx->bx.periodic = p->periodic ? 1 : 0;
   for (int k = 0; k < 3; ++k) {
     const double Lk = p->periodic ? p->box[k] : 0.0;
@@ -479,7 +561,8 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
   }
   DevBuf *bufs[] = {&ctx->frame, &ctx->status, &ctx->frame_part, &ctx->gtab, &ctx->hist, &ctx->hist_scan,
                     &ctx->scan_tmp, &ctx->pcache, &ctx->mf_part, &ctx->mc_rec, &ctx->seg_cnt, &ctx->seg_ptr,
-                    &ctx->seg_row, &ctx->seg_begin, &ctx->t_cursor, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
+                    &ctx->seg_row, &ctx->seg_begin, &ctx->t_cursor, &ctx->mlp_p, &ctx->mlp_m, &ctx->mlp_v,
+                    &ctx->mlp_w2, &ctx->mlp_w3, &ctx->mlp_w2t, &ctx->mlp_w3t, &ctx->mlp_fallback, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
                     &ctx->kick_blocks, &ctx->sums, &ctx->scratch_vel, &ctx->search_stats};
   for (DevBuf *b : bufs) release(*b);
   SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};
@@ -611,6 +694,191 @@ dmb_status dmb_stage_times(dmb_ctx *ctx, double *ms_out, int64_t *steps_out) {
   return DMB_OK;
 }
 
+// ---- surrogate entry points ---------------------------------------------------------------
+dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, uint64_t seed, double *report) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (nsamples < 4096 * 2 || nsamples > (1ll << 27) || epochs < 1 || epochs > 10000)
+    return fail(ctx, DMB_ERR_ARG, "nsamples must be in [8192, 2^27] and epochs in [1, 10000]");
+  dmb_status st;
+  if ((st = ensure_mlp(ctx)) != DMB_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  // training box and power-law indices: {-4, -2, 0, 2} and the context's n
+  MlpDataSpec spec;
+  spec.log_s_lo = ctx->mlp_box[0]; spec.log_s_hi = ctx->mlp_box[1];
+  spec.log_tau_lo = ctx->mlp_box[2]; spec.log_tau_hi = ctx->mlp_box[3];
+  spec.log_m_lo = ctx->mlp_box[4]; spec.log_m_hi = ctx->mlp_box[5];
+  std::vector<int> ns = {-4, -2, 0, 2};
+  if (std::find(ns.begin(), ns.end(), ctx->p.n) == ns.end()) ns.push_back(ctx->p.n);
+  spec.n_count = (int)ns.size();
+  for (int k = 0; k < spec.n_count; ++k) {
+    spec.n_values[k] = ns[k];
+    spec.alpha[k] = alpha_of(ns[k]);
+    envelope(ns[k], spec.cA[k], spec.eA[k], spec.cB[k], spec.eB[k]);
+  }
+  const int B = 4096;
+  const int64_t N = nsamples, Nval = N / 10, Ntr = N - Nval;
+  DevBuf X, Y, idx, A1, A2, Z1, Z2, Z3, A3, dY, loss, dZ3, dZ2, dZ1, part2, part3, grad, Yv;
+  const size_t BH = (size_t)B * MLP_H;
+  bool ok = ensure(X, N * 16) && ensure(Y, N * 8) && ensure(idx, Ntr * 4) && ensure(A1, BH * 2) && ensure(A2, BH * 2) &&
+            ensure(Z1, BH * 4) && ensure(Z2, BH * 4) && ensure(Z3, BH * 4) && ensure(A3, BH * 4) && ensure(dY, B * 8) &&
+            ensure(loss, MLP_TRAIN_BLOCKS * 4) && ensure(dZ3, BH * 2) && ensure(dZ2, BH * 2) && ensure(dZ1, BH * 4) &&
+            ensure(part2, (size_t)MLP_KSLICES * MLP_H * MLP_H * 4) && ensure(part3, (size_t)MLP_KSLICES * MLP_H * MLP_H * 4) &&
+            ensure(grad, MLP_NPARAM * 4) && ensure(Yv, Nval * 8);
+  auto cleanup = [&]() { for (DevBuf *b : {&X, &Y, &idx, &A1, &A2, &Z1, &Z2, &Z3, &A3, &dY, &loss, &dZ3, &dZ2, &dZ1, &part2, &part3, &grad, &Yv}) release(*b); };
+  if (!ok) { cleanup(); return fail(ctx, DMB_ERR_OOM, "device allocation failed for surrogate training"); }
+  cudaError_t e = mlp_make_data(spec, N, seed, ptr<float>(X), ptr<float>(Y), s);
+  // initial weights: uniform(-sqrt(3/fan_in), sqrt(3/fan_in)), zero biases, small output layer
+  std::vector<float> p0(MLP_NPARAM, 0.0f);
+  std::mt19937_64 rng(seed ^ 0x9e3779b97f4a7c15ull);
+  auto fill = [&](int off, int count, int fan_in, float scale) {
+    std::uniform_real_distribution<float> U(-1.0f, 1.0f);
+    const float b = scale * sqrtf(3.0f / (float)fan_in);
+    for (int k = 0; k < count; ++k) p0[off + k] = b * U(rng);
+  };
+  fill(MLP_OFF_W1, MLP_H * MLP_IN, MLP_IN, 1.0f);
+  fill(MLP_OFF_W2, MLP_H * MLP_H, MLP_H, 1.0f);
+  fill(MLP_OFF_W3, MLP_H * MLP_H, MLP_H, 1.0f);
+  fill(MLP_OFF_W4, MLP_OUT * MLP_H, MLP_H, 0.1f);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->mlp_p.p, p0.data(), MLP_NPARAM * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->mlp_m.p, 0, MLP_NPARAM * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->mlp_v.p, 0, MLP_NPARAM * 4, s);
+  MlpDev d = mlp_dev(ctx);
+  if (e == cudaSuccess) e = mlp_refresh(d, s);
+  MlpWork w;
+  w.A1 = ptr<__nv_bfloat16>(A1); w.A2 = ptr<__nv_bfloat16>(A2); w.dZ3 = ptr<__nv_bfloat16>(dZ3); w.dZ2 = ptr<__nv_bfloat16>(dZ2);
+  w.Z1 = ptr<float>(Z1); w.Z2 = ptr<float>(Z2); w.Z3 = ptr<float>(Z3); w.A3 = ptr<float>(A3); w.dY = ptr<float>(dY);
+  w.loss = ptr<float>(loss); w.dZ1 = ptr<float>(dZ1); w.part2 = ptr<float>(part2); w.part3 = ptr<float>(part3);
+  w.grad = ptr<float>(grad);
+  const int steps_per_epoch = (int)(Ntr / B);
+  const int total = steps_per_epoch * epochs;
+  std::vector<int> perm(Ntr);
+  for (int64_t k = 0; k < Ntr; ++k) perm[k] = (int)k;
+  int t_adam = 0;
+  const float lr0 = 2e-3f, lr1 = 2e-5f;
+  for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+    std::shuffle(perm.begin(), perm.end(), rng);
+    e = cudaMemcpyAsync(idx.p, perm.data(), Ntr * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // perm is reused next epoch
+    for (int b = 0; b < steps_per_epoch && e == cudaSuccess; ++b) {
+      ++t_adam;
+      const float frac = (float)t_adam / (float)total;
+      const float lr = lr1 + 0.5f * (lr0 - lr1) * (1.0f + cosf(3.14159265f * frac));
+      e = mlp_train_batch(d, ptr<float>(X), ptr<float>(Y), ptr<int>(idx) + (size_t)b * B, B, w, lr, t_adam, s,
+                          &ctx->launches);
+    }
+  }
+  // last batch loss and the validation errors of FA, FB (relative)
+  std::vector<float> lossh(MLP_TRAIN_BLOCKS), yv(Nval * 2), yt(Nval * 2);
+  if (e == cudaSuccess) e = mlp_infer(d, ptr<float>(X) + Ntr * 4, Nval, ptr<float>(Yv), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lossh.data(), loss.p, MLP_TRAIN_BLOCKS * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(yv.data(), Yv.p, Nval * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(yt.data(), ptr<float>(Y) + Ntr * 2, Nval * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "surrogate training");
+  double lsum = 0.0;
+  for (float v : lossh) lsum += v;
+  double mxA = 0, mxB = 0, meA = 0, meB = 0;
+  for (int64_t k = 0; k < Nval; ++k) {
+    const double ea = fabs(expm1((double)yv[2 * k] - (double)yt[2 * k]));
+    const double eb = fabs(expm1((double)yv[2 * k + 1] - (double)yt[2 * k + 1]));
+    mxA = fmax(mxA, ea); mxB = fmax(mxB, eb); meA += ea; meB += eb;
+  }
+  ctx->mlp_ready = true;
+  ctx->mlp_n = ns;
+  if (report) {
+    report[0] = lsum / ((double)B * MLP_OUT);
+    report[1] = mxA;
+    report[2] = mxB;
+    report[3] = meA / (double)Nval;
+    report[4] = meB / (double)Nval;
+    report[5] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    report[6] = (double)t_adam;
+    report[7] = (double)N;
+  }
+  return DMB_OK;
+}
+
+dmb_status dmb_surrogate_params(dmb_ctx *ctx, float *host_out, int64_t *count) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (count) *count = MLP_NPARAM;
+  if (!host_out) return DMB_OK;
+  if (!ctx->mlp_ready) return fail(ctx, DMB_ERR_STATE, "no surrogate loaded");
+  CK(cudaMemcpyAsync(host_out, ctx->mlp_p.p, MLP_NPARAM * 4, cudaMemcpyDeviceToHost, ctx->stream), "copy");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+  return DMB_OK;
+}
+
+dmb_status dmb_load_surrogate(dmb_ctx *ctx, const float *host_params, int64_t count) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!host_params || count != MLP_NPARAM) return fail(ctx, DMB_ERR_ARG, "expected the full parameter block");
+  dmb_status st;
+  if ((st = ensure_mlp(ctx)) != DMB_OK) return st;
+  CK(cudaMemcpyAsync(ctx->mlp_p.p, host_params, MLP_NPARAM * 4, cudaMemcpyHostToDevice, ctx->stream), "copy");
+  MlpDev d = mlp_dev(ctx);
+  CK(mlp_refresh(d, ctx->stream), "refresh");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+  ctx->mlp_ready = true;
+  ctx->mlp_n = {-4, -2, 0, 2};
+  if (std::find(ctx->mlp_n.begin(), ctx->mlp_n.end(), ctx->p.n) == ctx->mlp_n.end()) ctx->mlp_n.push_back(ctx->p.n);
+  return DMB_OK;
+}
+
+dmb_status dmb_surrogate_infer(dmb_ctx *ctx, const float *X, int64_t n, float *Y) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!ctx->mlp_ready) return fail(ctx, DMB_ERR_STATE, "no surrogate loaded");
+  CK(mlp_infer(mlp_dev(ctx), X, n, Y, ctx->stream), "surrogate inference");
+  return DMB_OK;
+}
+
+dmb_status dmb_surrogate_grad(dmb_ctx *ctx, const float *X, const float *Y, int32_t B, float *grad, double *loss) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!ctx->mlp_ready) return fail(ctx, DMB_ERR_STATE, "no surrogate loaded");
+  if (B < 1 || B > (1 << 20)) return fail(ctx, DMB_ERR_ARG, "batch size out of range");
+  cudaStream_t s = ctx->stream;
+  DevBuf idx, A1, A2, Z1, Z2, Z3, A3, dY, lossb, dZ3, dZ2, dZ1, part2, part3;
+  const size_t BH = (size_t)B * MLP_H;
+  bool ok = ensure(idx, (size_t)B * 4) && ensure(A1, BH * 2) && ensure(A2, BH * 2) && ensure(Z1, BH * 4) &&
+            ensure(Z2, BH * 4) && ensure(Z3, BH * 4) && ensure(A3, BH * 4) && ensure(dY, (size_t)B * 8) &&
+            ensure(lossb, MLP_TRAIN_BLOCKS * 4) && ensure(dZ3, BH * 2) && ensure(dZ2, BH * 2) && ensure(dZ1, BH * 4) &&
+            ensure(part2, (size_t)MLP_KSLICES * MLP_H * MLP_H * 4) && ensure(part3, (size_t)MLP_KSLICES * MLP_H * MLP_H * 4);
+  auto cleanup = [&]() { for (DevBuf *b : {&idx, &A1, &A2, &Z1, &Z2, &Z3, &A3, &dY, &lossb, &dZ3, &dZ2, &dZ1, &part2, &part3}) release(*b); };
+  if (!ok) { cleanup(); return fail(ctx, DMB_ERR_OOM, "device allocation failed"); }
+  std::vector<int> id(B);
+  for (int k = 0; k < B; ++k) id[k] = k;
+  MlpWork w;
+  w.A1 = ptr<__nv_bfloat16>(A1); w.A2 = ptr<__nv_bfloat16>(A2); w.dZ3 = ptr<__nv_bfloat16>(dZ3); w.dZ2 = ptr<__nv_bfloat16>(dZ2);
+  w.Z1 = ptr<float>(Z1); w.Z2 = ptr<float>(Z2); w.Z3 = ptr<float>(Z3); w.A3 = ptr<float>(A3); w.dY = ptr<float>(dY);
+  w.loss = ptr<float>(lossb); w.dZ1 = ptr<float>(dZ1); w.part2 = ptr<float>(part2); w.part3 = ptr<float>(part3);
+  w.grad = grad;
+  MlpDev d = mlp_dev(ctx);
+  std::vector<float> lh(MLP_TRAIN_BLOCKS);
+  cudaError_t e = cudaMemcpyAsync(idx.p, id.data(), (size_t)B * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = mlp_grad(d, X, Y, ptr<int>(idx), B, w, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lh.data(), lossb.p, MLP_TRAIN_BLOCKS * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "surrogate gradient");
+  if (loss) {
+    double t = 0.0;
+    for (float v : lh) t += v;
+    *loss = t / (double)B;   // mean over samples of the summed squared error of the two outputs
+  }
+  return DMB_OK;
+}
+
+dmb_status dmb_surrogate_fallbacks(dmb_ctx *ctx, int64_t *out) {
+  if (!ctx || !out) return fail(ctx, DMB_ERR_ARG, "NULL argument");
+  *out = 0;
+  if (!ctx->mlp_fallback.p) return DMB_OK;
+  unsigned long long v = 0;
+  CK(cudaMemcpyAsync(&v, ctx->mlp_fallback.p, 8, cudaMemcpyDeviceToHost, ctx->stream), "copy");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+  *out = (int64_t)v;
+  return DMB_OK;
+}
+
 dmb_status dmb_search_stats(dmb_ctx *ctx, uint64_t *out16) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
   if (!out16) return fail(ctx, DMB_ERR_ARG, "out is NULL");
@@ -627,7 +895,8 @@ dmb_status dmb_debug_overlap(dmb_ctx *ctx, int64_t k, const double *in, double *
 
 dmb_status dmb_debug_rates(dmb_ctx *ctx, int64_t k, const double *in, double *out) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
-  CK(launch_debug_rates(ctx->p.fp64, ctx->p.n, k, in, out, ctx->stream), "debug rates");
+  CK(launch_debug_rates(ctx->p.fp64, ctx->p.n, ctx->rc.rate_mode, ctx->rc.alpha, k, in, out, ctx->stream),
+     "debug rates");
   return DMB_OK;
 }
 

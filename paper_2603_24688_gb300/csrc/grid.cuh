@@ -20,6 +20,7 @@ struct RunConst {
   double alpha;      // alpha_n = 2^((n+5)/2) Gamma(3 + n/2) / sqrt(pi)
   double kT_over_mp; // k_B / m_p in (km/s)^2 / K
   int n;
+  int rate_mode;     // dmb_rate_mode
 };
 
 // Status bits raised by the device checks.

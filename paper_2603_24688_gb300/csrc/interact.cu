@@ -1,5 +1,6 @@
 // Pair physics: gas mean field (Eqs. gas-dVdt, gas-dTdt) and DM Monte Carlo
 // (Eqs. dm-update-vels, dm-update-prob, scatter_chi, prob_criterion).
+#include "mlp.cuh"
 #include "pairs.cuh"
 #include "physics.cuh"
 
@@ -11,15 +12,34 @@
 // the float64 results (and the perm scatter to caller order) are formed by
 // k_meanfield_finish with one thread per gas particle, where float64 instructions cover
 // 32 particles each (GB300 runs float64 at 1/64 of the float32 rate).
-template <typename R>
+template <typename R, int RM>
 __global__ void __launch_bounds__(MF_WARPS * 32)
 k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__restrict__ row_ptr,
             const uint32_t *__restrict__ rows, SegView sv, const float4 *__restrict__ gtab, RunConst rc,
-            R *__restrict__ part) {
+            R *__restrict__ part, MlpRun mr) {
   typedef typename Vec<R>::v4 v4;
+  extern __shared__ __align__(16) unsigned char mf_smem[];
+  if (RM == DMB_RATE_MLP) {   // the network's weights, once per block
+    MlpSmem &M = *reinterpret_cast<MlpSmem *>(mf_smem);
+    for (int t = threadIdx.x; t < MLP_H * MLP_H / 8; t += blockDim.x) {
+      reinterpret_cast<uint4 *>(M.W2)[t] = reinterpret_cast<const uint4 *>(mr.w2)[t];
+      reinterpret_cast<uint4 *>(M.W3)[t] = reinterpret_cast<const uint4 *>(mr.w3)[t];
+    }
+    for (int t = threadIdx.x; t < MLP_H * MLP_IN; t += blockDim.x) M.W1[t] = mr.p[MLP_OFF_W1 + t];
+    for (int t = threadIdx.x; t < MLP_H; t += blockDim.x) {
+      M.b1[t] = mr.p[MLP_OFF_B1 + t];
+      M.b2[t] = mr.p[MLP_OFF_B2 + t];
+      M.b3[t] = mr.p[MLP_OFF_B3 + t];
+    }
+    for (int t = threadIdx.x; t < MLP_OUT * MLP_H; t += blockDim.x) M.W4[t] = mr.p[MLP_OFF_W4 + t];
+    if (threadIdx.x < MLP_OUT) M.b4[threadIdx.x] = mr.p[MLP_OFF_B4 + threadIdx.x];
+    __syncthreads();
+  }
+  unsigned fallback = 0;
   const unsigned lane = threadIdx.x & 31u;
   const int64_t nwarps = (int64_t)gridDim.x * MF_WARPS;
   const R inv_v0 = (R)(1.0 / rc.v0);
+  const R alpha = (R)rc.alpha;
   const int64_t n_seg = sv.seg_ptr[G.n];
   for (int64_t u = (int64_t)blockIdx.x * MF_WARPS + (threadIdx.x >> 5); u < n_seg; u += nwarps) {
     const int64_t j = sv.seg_row[u];
@@ -30,8 +50,11 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
       const R sig = Vj.w;
       const bool hot = sig > (R)0;
       const R inv2s2 = hot ? (R)0.5 / (sig * sig) : (R)0;
-      for (int64_t p = rs + lane; p < re; p += 32) {
-        const uint32_t i = rows[p];
+      // warp-uniform trip count (the surrogate's tensor-core layers need all 32 lanes)
+      for (int64_t p0 = rs; p0 < re; p0 += 32) {
+        const int64_t p = p0 + lane;
+        const bool valid = p < re;
+        const uint32_t i = rows[valid ? p : rs];
         const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
         R dx, dy, dz;
         pair_dx<R>(Pi, Li, Pj, Lj, bx, dx, dy, dz);
@@ -41,13 +64,51 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
         const R w2 = wx * wx + wy * wy + wz * wz;
         R FA, FB;
         if (hot) {
-          rates_FAB<R>(w2 * inv2s2, rc.n, FA, FB);
+          if (RM == DMB_RATE_QUAD) {
+            rates_quad<R>(w2 * inv2s2, rc.n, alpha, FA, FB);
+          } else if (RM == DMB_RATE_MLP) {
+            const MlpSmem &M = *reinterpret_cast<const MlpSmem *>(mf_smem);
+            const float sgm = (float)sig, sv_ = sqrtf((float)w2) / sgm;
+            float xin[MLP_IN];
+            const bool in_dom = mlp_inputs(mr.dom, sv_, sgm, xin);
+            float yme[MLP_OUT] = {0.f, 0.f};
+            const unsigned gq = lane >> 2;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+              float xl[MLP_IN], xh[MLP_IN], yl[MLP_OUT], yh[MLP_OUT];
+#pragma unroll
+              for (int m = 0; m < MLP_IN; ++m) {
+                xl[m] = __shfl_sync(DMB_FULL, xin[m], 16 * half + gq);
+                xh[m] = __shfl_sync(DMB_FULL, xin[m], 16 * half + gq + 8);
+              }
+              mlp_forward16(M, xl, xh, yl, yh);
+              // row r of this half sits in lanes 4 (r mod 8) .. as y_lo (r < 8) or y_hi (r >= 8)
+              const int r = (int)lane - 16 * half;
+              const int src = 4 * (r & 7);
+#pragma unroll
+              for (int o = 0; o < MLP_OUT; ++o) {
+                const float a = __shfl_sync(DMB_FULL, yl[o], src & 31), b = __shfl_sync(DMB_FULL, yh[o], src & 31);
+                if (r >= 0 && r < 16) yme[o] = r < 8 ? a : b;
+              }
+            }
+            float fa, fb;
+            mlp_outputs(mr.dom, sv_, yme, fa, fb);
+            FA = (R)fa;
+            FB = (R)fb;
+            if (valid && !in_dom) {   // outside the training box: the quadrature, counted
+              rates_quad<R>(w2 * inv2s2, rc.n, alpha, FA, FB);
+              ++fallback;
+            }
+          } else {
+            rates_FAB<R>(w2 * inv2s2, rc.n, FA, FB);
+          }
         } else {
           const R wn = sqrt_t(w2);
           const R sn = ipow<R>(wn * inv_v0, rc.n);
           FA = sn * wn;
           FB = sn * wn * w2;
         }
+        if (!valid) continue;
         const R t = Li.w * g;          // M_i g_ij
         const R tA = t * FA;
         sx += tA * wx;
@@ -68,6 +129,10 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
       const R v = lane == 0 ? sx : lane == 1 ? sy : lane == 2 ? sz : lane == 3 ? sw2 : lane == 4 ? sb : svw;
       part[6 * u + lane] = v;
     }
+  }
+  if (RM == DMB_RATE_MLP && mr.fallback_count) {
+    fallback = warp_sum<unsigned>(fallback);
+    if (lane == 0 && fallback) atomicAdd(mr.fallback_count, (unsigned long long)fallback);
   }
 }
 
@@ -94,21 +159,37 @@ __global__ void k_meanfield_finish(SpeciesView<R> G, const int64_t *__restrict__
 template <typename R>
 cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *row_ptr,
                              const uint32_t *rows, SegView sv, int64_t n_seg_max, const float4 *gtab, RunConst rc,
-                             MfOut out, R *part, cudaStream_t s, int64_t *launches) {
+                             MfOut out, R *part, MlpRun mr, cudaStream_t s, int64_t *launches) {
   if (G.n <= 0) return cudaSuccess;
   int64_t blocks = (n_seg_max + MF_WARPS - 1) / MF_WARPS;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  k_meanfield<R><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc, part);
+  if (rc.rate_mode == DMB_RATE_QUAD) {
+    k_meanfield<R, DMB_RATE_QUAD><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc,
+                                                                              part, mr);
+  } else if (rc.rate_mode == DMB_RATE_MLP) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_meanfield<R, DMB_RATE_MLP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(MlpSmem));
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_meanfield<R, DMB_RATE_MLP><<<(unsigned)blocks, MF_WARPS * 32, sizeof(MlpSmem), s>>>(G, D, bx, row_ptr, rows, sv,
+                                                                                           gtab, rc, part, mr);
+  } else {
+    k_meanfield<R, DMB_RATE_CLOSED><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc,
+                                                                                part, mr);
+  }
   k_meanfield_finish<R><<<(unsigned)((G.n + 255) / 256), 256, 0, s>>>(G, sv.seg_ptr, part, out);
   if (launches) *launches += 2;
   return cudaGetLastError();
 }
 template cudaError_t launch_meanfield<float>(SpeciesView<float>, SpeciesView<float>, BoxSplit, const int64_t *,
                                              const uint32_t *, SegView, int64_t, const float4 *, RunConst, MfOut,
-                                             float *, cudaStream_t, int64_t *);
+                                             float *, MlpRun, cudaStream_t, int64_t *);
 template cudaError_t launch_meanfield<double>(SpeciesView<double>, SpeciesView<double>, BoxSplit, const int64_t *,
                                               const uint32_t *, SegView, int64_t, const float4 *, RunConst, MfOut,
-                                              double *, cudaStream_t, int64_t *);
+                                              double *, MlpRun, cudaStream_t, int64_t *);
 
 // ---- Monte Carlo: one warp per DM particle ---------------------------------------------
 // The sampled partner velocity v^B_ij = V_j + varsigma_j z (z from the pair's Philox block)
@@ -374,24 +455,27 @@ cudaError_t launch_debug_overlap(const float4 *T, int fp64, int64_t k, const dou
   return cudaGetLastError();
 }
 
-__global__ void k_debug_rates(int fp64, int n, int64_t k, const double *in, double *out) {
+__global__ void k_debug_rates(int fp64, int n, int mode, double alpha, int64_t k, const double *in, double *out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= k) return;
   if (fp64) {
     double a, b;
-    rates_FAB<double>(in[t], n, a, b);
+    if (mode == DMB_RATE_QUAD) rates_quad<double>(in[t], n, alpha, a, b);
+    else rates_FAB<double>(in[t], n, a, b);
     out[2 * t] = a;
     out[2 * t + 1] = b;
   } else {
     float a, b;
-    rates_FAB<float>((float)in[t], n, a, b);
+    if (mode == DMB_RATE_QUAD) rates_quad<float>((float)in[t], n, (float)alpha, a, b);
+    else rates_FAB<float>((float)in[t], n, a, b);
     out[2 * t] = a;
     out[2 * t + 1] = b;
   }
 }
-cudaError_t launch_debug_rates(int fp64, int n, int64_t k, const double *in, double *out, cudaStream_t s) {
+cudaError_t launch_debug_rates(int fp64, int n, int mode, double alpha, int64_t k, const double *in, double *out,
+                               cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
-  k_debug_rates<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(fp64, n, k, in, out);
+  k_debug_rates<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(fp64, n, mode, alpha, k, in, out);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,175 @@
+// Learned surrogate of the rate integrals: a 4 -> 128 -> 128 -> 128 -> 2 MLP with SiLU.
+// The two 128 x 128 layers run on the tensor cores (bf16 inputs, float32 accumulation,
+// mma.sync m16n8k16); the first and last layers are float32 on the CUDA cores.  One warp
+// evaluates 16 rows at a time; the accumulator fragment of one layer is, after the
+// activation, exactly the A fragment of the next layer, so activations never leave the
+// registers.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+#define MLP_IN 4
+#define MLP_H 128
+#define MLP_OUT 2
+// float32 parameter block: W1[H][IN] b1[H] W2[H][H] b2[H] W3[H][H] b3[H] W4[OUT][H] b4[OUT]
+#define MLP_OFF_W1 0
+#define MLP_OFF_B1 (MLP_OFF_W1 + MLP_H * MLP_IN)
+#define MLP_OFF_W2 (MLP_OFF_B1 + MLP_H)
+#define MLP_OFF_B2 (MLP_OFF_W2 + MLP_H * MLP_H)
+#define MLP_OFF_W3 (MLP_OFF_B2 + MLP_H)
+#define MLP_OFF_B3 (MLP_OFF_W3 + MLP_H * MLP_H)
+#define MLP_OFF_W4 (MLP_OFF_B3 + MLP_H)
+#define MLP_OFF_B4 (MLP_OFF_W4 + MLP_OUT * MLP_H)
+#define MLP_NPARAM (MLP_OFF_B4 + MLP_OUT)
+
+// Shared-memory image of the network used by the kernels (bf16 copies of W2, W3).
+struct MlpSmem {
+  __nv_bfloat16 W2[MLP_H * MLP_H];
+  __nv_bfloat16 W3[MLP_H * MLP_H];
+  float W1[MLP_H * MLP_IN];
+  float b1[MLP_H], b2[MLP_H], b3[MLP_H];
+  float W4[MLP_OUT * MLP_H];
+  float b4[MLP_OUT];
+};
+
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z) {
+  const float s = 1.0f / (1.0f + __expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x = lo (low 16 bits)
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One 128 -> 128 layer on 16 rows: acc[nt][0..3] = a . W^T (W row-major [out][in] in smem as
+// bf16; out tile nt covers columns nt*8 .. nt*8+7).  A fragments come packed as
+// afrag[kt][0..3] for the 8 k16 blocks.
+__device__ __forceinline__ void mlp_layer_mma(const __nv_bfloat16 *__restrict__ W, const uint32_t afrag[8][4],
+                                              float acc[16][4]) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned g = lane >> 2, tig = lane & 3u;
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt) {
+    acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+    const __nv_bfloat16 *wrow = W + (nt * 8 + g) * MLP_H + tig * 2;
+#pragma unroll
+    for (int kt = 0; kt < 8; ++kt) {
+      const uint32_t b0 = *reinterpret_cast<const uint32_t *>(wrow + kt * 16);
+      const uint32_t b1 = *reinterpret_cast<const uint32_t *>(wrow + kt * 16 + 8);
+      mma_bf16_16816(acc[nt], afrag[kt], b0, b1);
+    }
+  }
+}
+
+// bias + SiLU on an accumulator set, packed into the next layer's A fragments
+__device__ __forceinline__ void mlp_act_pack(float acc[16][4], const float *__restrict__ bias, uint32_t afrag[8][4]) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned tig = lane & 3u;
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt) {
+    const float bb0 = bias[nt * 8 + tig * 2], bb1 = bias[nt * 8 + tig * 2 + 1];
+    acc[nt][0] = silu(acc[nt][0] + bb0);
+    acc[nt][1] = silu(acc[nt][1] + bb1);
+    acc[nt][2] = silu(acc[nt][2] + bb0);
+    acc[nt][3] = silu(acc[nt][3] + bb1);
+  }
+#pragma unroll
+  for (int kt = 0; kt < 8; ++kt) {
+    afrag[kt][0] = pack_bf16(acc[2 * kt][0], acc[2 * kt][1]);
+    afrag[kt][1] = pack_bf16(acc[2 * kt][2], acc[2 * kt][3]);
+    afrag[kt][2] = pack_bf16(acc[2 * kt + 1][0], acc[2 * kt + 1][1]);
+    afrag[kt][3] = pack_bf16(acc[2 * kt + 1][2], acc[2 * kt + 1][3]);
+  }
+}
+
+// Forward of 16 rows.  x_lo / x_hi: the 4 inputs of rows g and g + 8 (g = lane / 4).
+// Returns y for rows g (y_lo) and g + 8 (y_hi), identical in the 4 lanes of a quad.
+__device__ __forceinline__ void mlp_forward16(const MlpSmem &M, const float x_lo[MLP_IN], const float x_hi[MLP_IN],
+                                              float y_lo[MLP_OUT], float y_hi[MLP_OUT]) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned tig = lane & 3u;
+  float acc[16][4];
+  uint32_t afrag[8][4];
+  // layer 1 (float32): z1 = W1 x + b1 at this lane's fragment positions
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int col = nt * 8 + tig * 2 + e;
+      float zl = 0.0f, zh = 0.0f;
+#pragma unroll
+      for (int m = 0; m < MLP_IN; ++m) {
+        zl += M.W1[col * MLP_IN + m] * x_lo[m];
+        zh += M.W1[col * MLP_IN + m] * x_hi[m];
+      }
+      acc[nt][e] = zl;
+      acc[nt][2 + e] = zh;
+    }
+  }
+  mlp_act_pack(acc, M.b1, afrag);
+  mlp_layer_mma(M.W2, afrag, acc);
+  mlp_act_pack(acc, M.b2, afrag);
+  mlp_layer_mma(M.W3, afrag, acc);
+  // layer 3 activation (float32) and the output layer on the CUDA cores
+  float pl[MLP_OUT] = {0.f, 0.f}, ph[MLP_OUT] = {0.f, 0.f};
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int col = nt * 8 + tig * 2 + e;
+      const float al = silu(acc[nt][e] + M.b3[col]);
+      const float ah = silu(acc[nt][2 + e] + M.b3[col]);
+#pragma unroll
+      for (int o = 0; o < MLP_OUT; ++o) {
+        pl[o] += M.W4[o * MLP_H + col] * al;
+        ph[o] += M.W4[o * MLP_H + col] * ah;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < MLP_OUT; ++o) {
+    pl[o] += __shfl_xor_sync(DMB_FULL, pl[o], 1);
+    pl[o] += __shfl_xor_sync(DMB_FULL, pl[o], 2);
+    ph[o] += __shfl_xor_sync(DMB_FULL, ph[o], 1);
+    ph[o] += __shfl_xor_sync(DMB_FULL, ph[o], 2);
+    y_lo[o] = pl[o] + M.b4[o];
+    y_hi[o] = ph[o] + M.b4[o];
+  }
+}
+
+// Surrogate inputs and outputs.  Inputs: log10(s)/2, log10(tau)/2, log10(m_chi/m_p), n/4 with
+// s = w/varsigma, tau = varsigma^2/v0^2.  Outputs: the residuals
+// log FA - log EA and log FB - log EB against the envelopes EA = (1 + cA x)^((n+1)/2),
+// EB = (1 + cB x)^((n+3)/2) (x = s^2/2) that carry the exact small- and large-x behaviour.
+struct MlpDomain {
+  float s_lo, s_hi, tau_lo, tau_hi, m_lo, m_hi;
+  float cA, cB;      // envelope constants for the run's n
+  float eA, eB;      // envelope exponents (n+1)/2, (n+3)/2
+  float inv_v0sq, log_m, n4;
+};
+
+__device__ __forceinline__ bool mlp_inputs(const MlpDomain &d, float s, float sig, float x[MLP_IN]) {
+  const float tau = sig * sig * d.inv_v0sq;
+  x[0] = 0.5f * log10f(s);
+  x[1] = 0.5f * log10f(tau);
+  x[2] = d.log_m;
+  x[3] = d.n4;
+  return s >= d.s_lo && s <= d.s_hi && tau >= d.tau_lo && tau <= d.tau_hi;
+}
+
+__device__ __forceinline__ void mlp_outputs(const MlpDomain &d, float s, const float y[MLP_OUT], float &FA, float &FB) {
+  const float x = 0.5f * s * s;
+  FA = __expf(y[0]) * __powf(1.0f + d.cA * x, d.eA);
+  FB = __expf(y[1]) * __powf(1.0f + d.cB * x, d.eB);
+}

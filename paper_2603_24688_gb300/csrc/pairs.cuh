@@ -1,6 +1,17 @@
 // Pair search, mean field and Monte Carlo kernels.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "grid.cuh"
+#include "mlp.cuh"
+
+// Surrogate handles for the mean-field kernel (rate_mode = DMB_RATE_MLP).
+struct MlpRun {
+  const float *p;                  // float32 parameters
+  const __nv_bfloat16 *w2, *w3;    // bf16 copies of the 128 x 128 layers
+  MlpDomain dom;
+  unsigned long long *fallback_count;
+};
 
 #define SR_UNIT 64   // target leaves per work unit of the tile stage
 
@@ -49,7 +60,7 @@ struct MfOut {
 template <typename R>
 cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *row_ptr,
                              const uint32_t *rows, SegView sv, int64_t n_seg_max, const float4 *gtab, RunConst rc,
-                             MfOut out, R *part, cudaStream_t s, int64_t *launches);
+                             MfOut out, R *part, MlpRun mr, cudaStream_t s, int64_t *launches);
 
 struct McArgs {
   double dt;
@@ -82,6 +93,7 @@ cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int
 // Overlap table build (float64 exact evaluator at the nodes) and debug evaluators.
 cudaError_t launch_gtable(float4 *T, cudaStream_t s, int64_t *launches);
 cudaError_t launch_debug_overlap(const float4 *T, int fp64, int64_t k, const double *in, double *out, cudaStream_t s);
-cudaError_t launch_debug_rates(int fp64, int n, int64_t k, const double *in, double *out, cudaStream_t s);
+cudaError_t launch_debug_rates(int fp64, int n, int mode, double alpha, int64_t k, const double *in, double *out,
+                               cudaStream_t s);
 cudaError_t launch_debug_philox(int64_t k, const uint32_t *ctr, uint32_t *out, unsigned long long seed,
                                 cudaStream_t s);

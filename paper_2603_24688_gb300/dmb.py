@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "DMB_OK", 1: "DMB_ERR_ARG", 2: "DMB_ERR_CUDA", 3: "DMB_ERR_OO
 EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb_neighbors", "dmb_meanfield_gas",
            "dmb_mc_scatter_dm", "dmb_step", "dmb_debug_overlap", "dmb_debug_rates", "dmb_debug_philox",
            "dmb_launch_count", "dmb_set_timing", "dmb_stage_times",
-           "dmb_search_stats"]
+           "dmb_search_stats", "dmb_train_surrogate", "dmb_surrogate_params", "dmb_load_surrogate",
+           "dmb_surrogate_infer", "dmb_surrogate_grad", "dmb_surrogate_fallbacks"]
 
 
 class DmbError(RuntimeError):
@@ -76,6 +77,12 @@ def load(path=LIB_PATH):
         "dmb_set_timing": ([vp, c.c_int], c.c_int),
         "dmb_stage_times": ([vp, c.POINTER(c.c_double), c.POINTER(i64)], c.c_int),
         "dmb_search_stats": ([vp, c.POINTER(c.c_uint64)], c.c_int),
+        "dmb_train_surrogate": ([vp, i64, c.c_int32, u64, c.POINTER(c.c_double)], c.c_int),
+        "dmb_surrogate_params": ([vp, c.POINTER(c.c_float), c.POINTER(i64)], c.c_int),
+        "dmb_load_surrogate": ([vp, c.POINTER(c.c_float), i64], c.c_int),
+        "dmb_surrogate_infer": ([vp, vp, i64, vp], c.c_int),
+        "dmb_surrogate_grad": ([vp, vp, vp, c.c_int32, vp, c.POINTER(c.c_double)], c.c_int),
+        "dmb_surrogate_fallbacks": ([vp, c.POINTER(i64)], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -214,6 +221,41 @@ class Context:
 
     def dmb_launch_count(self):
         return int(self.lib.dmb_launch_count(self.h))
+
+    def dmb_train_surrogate(self, nsamples=1 << 20, epochs=30, seed=1):
+        """Train the rate surrogate on the device; returns the 8-entry report."""
+        rep = (ctypes.c_double * 8)()
+        self._check(self.lib.dmb_train_surrogate(self.h, int(nsamples), int(epochs), int(seed), rep))
+        return np.array(rep[:])
+
+    def dmb_surrogate_params(self):
+        n = ctypes.c_int64()
+        self._check(self.lib.dmb_surrogate_params(self.h, None, ctypes.byref(n)))
+        out = np.zeros(n.value, dtype=np.float32)
+        self._check(self.lib.dmb_surrogate_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                  ctypes.byref(n)))
+        return out
+
+    def dmb_load_surrogate(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self.lib.dmb_load_surrogate(self.h, params.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                params.size))
+
+    def dmb_surrogate_infer(self, X, Y):
+        import torch
+        self._check(self.lib.dmb_surrogate_infer(self.h, _ptr(X, torch.float32), X.shape[0], _ptr(Y, torch.float32)))
+
+    def dmb_surrogate_grad(self, X, Y, grad):
+        import torch
+        loss = ctypes.c_double()
+        self._check(self.lib.dmb_surrogate_grad(self.h, _ptr(X, torch.float32), _ptr(Y, torch.float32), X.shape[0],
+                                                _ptr(grad, torch.float32), ctypes.byref(loss)))
+        return loss.value
+
+    def dmb_surrogate_fallbacks(self):
+        n = ctypes.c_int64()
+        self._check(self.lib.dmb_surrogate_fallbacks(self.h, ctypes.byref(n)))
+        return n.value
 
     def dmb_search_stats(self):
         """Counters of the last pair search: (4 passes) x (nodes, leaves, tests, 0)."""

@@ -108,7 +108,9 @@ def test_call_order_and_parameters():
         dmb.Context(1e-24, -5, 2.0)
     assert e.value.status == dmb.DMB_ERR_ARG
     with pytest.raises(dmb.DmbError):
-        dmb.Context(1e-24, 0, 2.0, rate_mode=dmb.DMB_RATE_MLP)
+        dmb.Context(1e-24, 0, 2.0, rate_mode=7)
+    with pytest.raises(dmb.DmbError):
+        dmb.Context(1e-24, 0, 2.0, rate_mode=dmb.DMB_RATE_MLP, fp64=True)
 
 
 def test_deterministic_repeat():
