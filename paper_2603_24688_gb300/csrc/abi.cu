@@ -59,7 +59,7 @@ struct dmb_ctx {
   SearchBufs sg, sd;   // gas-major (gas queries, DM tree) and DM-major searches
   DevBuf pcache, mf_part, mc_rec, seg_cnt, seg_ptr, seg_row, seg_begin, t_cursor;
   // learned surrogate of the rate integrals
-  DevBuf mlp_p, mlp_m, mlp_v, mlp_w2, mlp_w3, mlp_w2t, mlp_w3t, mlp_fallback;
+  DevBuf mlp_p, mlp_m, mlp_v, mlp_w2, mlp_w3, mlp_w2t, mlp_w3t, mlp_fallback, mlp_rates;
   bool mlp_ready = false;
   std::vector<int> mlp_n;        // power-law indices the network was trained for
   double mlp_box[6] = {-2.0, 2.0, -3.0, 2.0, -0.30102999566398120, 1.0};   // log10 ranges of s, tau, m_chi
@@ -431,6 +431,12 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
     if (!known) return fail(ctx, DMB_ERR_DOMAIN, "the surrogate was not trained for this power-law index");
     mr = mlp_run(ctx);
     CK(cudaMemsetAsync(ctx->mlp_fallback.p, 0, 8, ctx->stream), "memset");
+    if (!ensure(ctx->mlp_rates, (size_t)ctx->sg.n_pairs * 8 + 8)) return fail(ctx, DMB_ERR_OOM, "surrogate rates");
+    mr.rates = ptr<float2>(ctx->mlp_rates);
+    if (sizeof(R) == 4)
+      CK(launch_mlp_pair_rates(view<float>(ctx->gas), view<float>(ctx->dm), ptr<int64_t>(ctx->sg.row_ptr),
+                               ptr<uint32_t>(ctx->sg.rows), sv, ctx->n_seg_max, ctx->rc, mr,
+                               ptr<float2>(ctx->mlp_rates), ctx->stream, &ctx->launches), "surrogate rates");
   }
   CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv,
                          ctx->n_seg_max, ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr, ctx->stream,
@@ -562,7 +568,7 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
   DevBuf *bufs[] = {&ctx->frame, &ctx->status, &ctx->frame_part, &ctx->gtab, &ctx->hist, &ctx->hist_scan,
                     &ctx->scan_tmp, &ctx->pcache, &ctx->mf_part, &ctx->mc_rec, &ctx->seg_cnt, &ctx->seg_ptr,
                     &ctx->seg_row, &ctx->seg_begin, &ctx->t_cursor, &ctx->mlp_p, &ctx->mlp_m, &ctx->mlp_v,
-                    &ctx->mlp_w2, &ctx->mlp_w3, &ctx->mlp_w2t, &ctx->mlp_w3t, &ctx->mlp_fallback, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
+                    &ctx->mlp_w2, &ctx->mlp_w3, &ctx->mlp_w2t, &ctx->mlp_w3t, &ctx->mlp_fallback, &ctx->mlp_rates, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
                     &ctx->kick_blocks, &ctx->sums, &ctx->scratch_vel, &ctx->search_stats};
   for (DevBuf *b : bufs) release(*b);
   SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};

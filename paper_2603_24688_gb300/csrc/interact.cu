@@ -18,23 +18,6 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
             const uint32_t *__restrict__ rows, SegView sv, const float4 *__restrict__ gtab, RunConst rc,
             R *__restrict__ part, MlpRun mr) {
   typedef typename Vec<R>::v4 v4;
-  extern __shared__ __align__(16) unsigned char mf_smem[];
-  if (RM == DMB_RATE_MLP) {   // the network's weights, once per block
-    MlpSmem &M = *reinterpret_cast<MlpSmem *>(mf_smem);
-    for (int t = threadIdx.x; t < MLP_H * MLP_H / 8; t += blockDim.x) {
-      reinterpret_cast<uint4 *>(M.W2)[t] = reinterpret_cast<const uint4 *>(mr.w2)[t];
-      reinterpret_cast<uint4 *>(M.W3)[t] = reinterpret_cast<const uint4 *>(mr.w3)[t];
-    }
-    for (int t = threadIdx.x; t < MLP_H * MLP_IN; t += blockDim.x) M.W1[t] = mr.p[MLP_OFF_W1 + t];
-    for (int t = threadIdx.x; t < MLP_H; t += blockDim.x) {
-      M.b1[t] = mr.p[MLP_OFF_B1 + t];
-      M.b2[t] = mr.p[MLP_OFF_B2 + t];
-      M.b3[t] = mr.p[MLP_OFF_B3 + t];
-    }
-    for (int t = threadIdx.x; t < MLP_OUT * MLP_H; t += blockDim.x) M.W4[t] = mr.p[MLP_OFF_W4 + t];
-    if (threadIdx.x < MLP_OUT) M.b4[threadIdx.x] = mr.p[MLP_OFF_B4 + threadIdx.x];
-    __syncthreads();
-  }
   unsigned fallback = 0;
   const unsigned lane = threadIdx.x & 31u;
   const int64_t nwarps = (int64_t)gridDim.x * MF_WARPS;
@@ -67,38 +50,9 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
           if (RM == DMB_RATE_QUAD) {
             rates_quad<R>(w2 * inv2s2, rc.n, alpha, FA, FB);
           } else if (RM == DMB_RATE_MLP) {
-            const MlpSmem &M = *reinterpret_cast<const MlpSmem *>(mf_smem);
-            const float sgm = (float)sig, sv_ = sqrtf((float)w2) / sgm;
-            float xin[MLP_IN];
-            const bool in_dom = mlp_inputs(mr.dom, sv_, sgm, xin);
-            float yme[MLP_OUT] = {0.f, 0.f};
-            const unsigned gq = lane >> 2;
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-              float xl[MLP_IN], xh[MLP_IN], yl[MLP_OUT], yh[MLP_OUT];
-#pragma unroll
-              for (int m = 0; m < MLP_IN; ++m) {
-                xl[m] = __shfl_sync(DMB_FULL, xin[m], 16 * half + gq);
-                xh[m] = __shfl_sync(DMB_FULL, xin[m], 16 * half + gq + 8);
-              }
-              mlp_forward16(M, xl, xh, yl, yh);
-              // row r of this half sits in lanes 4 (r mod 8) .. as y_lo (r < 8) or y_hi (r >= 8)
-              const int r = (int)lane - 16 * half;
-              const int src = 4 * (r & 7);
-#pragma unroll
-              for (int o = 0; o < MLP_OUT; ++o) {
-                const float a = __shfl_sync(DMB_FULL, yl[o], src & 31), b = __shfl_sync(DMB_FULL, yh[o], src & 31);
-                if (r >= 0 && r < 16) yme[o] = r < 8 ? a : b;
-              }
-            }
-            float fa, fb;
-            mlp_outputs(mr.dom, sv_, yme, fa, fb);
-            FA = (R)fa;
-            FB = (R)fb;
-            if (valid && !in_dom) {   // outside the training box: the quadrature, counted
-              rates_quad<R>(w2 * inv2s2, rc.n, alpha, FA, FB);
-              ++fallback;
-            }
+            const float2 fr = mr.rates[valid ? p : rs];    // from k_mlp_pair_rates
+            FA = (R)fr.x;
+            FB = (R)fr.y;
           } else {
             rates_FAB<R>(w2 * inv2s2, rc.n, FA, FB);
           }
@@ -130,10 +84,125 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
       part[6 * u + lane] = v;
     }
   }
-  if (RM == DMB_RATE_MLP && mr.fallback_count) {
-    fallback = warp_sum<unsigned>(fallback);
-    if (lane == 0 && fallback) atomicAdd(mr.fallback_count, (unsigned long long)fallback);
+  (void)fallback;
+}
+
+// ---- surrogate rates of every gas-major pair (before the mean field) ---------------------
+#define MLP_ACT_OFFSET ((sizeof(MlpSmemPad) + 127) / 128 * 128)
+static_assert(MLP_ACT_OFFSET % 16 == 0, "activation buffers must be 16-byte aligned for ldmatrix");
+static_assert((MLP_LDW * sizeof(__nv_bfloat16)) % 16 == 0, "padded rows must keep 16-byte alignment");
+// One warp per mean-field segment; 32 pairs per iteration: the inputs of pair p0 + r in lane r,
+// layer 1 lane by lane into the warp's activation buffer, the two 128 x 128 layers on the tensor
+// cores (mlp_layer32), the output layer on the CUDA cores.  Pairs outside the training box get
+// the quadrature instead, counted.
+__global__ void __launch_bounds__(MF_WARPS * 32)
+k_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *__restrict__ row_ptr,
+                 const uint32_t *__restrict__ rows, SegView sv, RunConst rc, MlpRun mr, float2 *__restrict__ rates) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  MlpSmemPad &M = *reinterpret_cast<MlpSmemPad *>(smraw);
+  // ldmatrix needs 16-byte aligned rows: the activation buffers start on a 128-byte boundary
+  __nv_bfloat16 *actbuf = reinterpret_cast<__nv_bfloat16 *>(smraw + MLP_ACT_OFFSET);
+  for (int t = threadIdx.x; t < MLP_H * MLP_H / 2; t += blockDim.x) {
+    const int o = (2 * t) / MLP_H, i = (2 * t) % MLP_H;
+    *reinterpret_cast<uint32_t *>(&M.W2[o * MLP_LDW + i]) = *reinterpret_cast<const uint32_t *>(&mr.w2[2 * t]);
+    *reinterpret_cast<uint32_t *>(&M.W3[o * MLP_LDW + i]) = *reinterpret_cast<const uint32_t *>(&mr.w3[2 * t]);
   }
+  for (int t = threadIdx.x; t < MLP_H * MLP_IN; t += blockDim.x) M.W1[t] = mr.p[MLP_OFF_W1 + t];
+  for (int t = threadIdx.x; t < MLP_H; t += blockDim.x) {
+    M.b1[t] = mr.p[MLP_OFF_B1 + t];
+    M.b2[t] = mr.p[MLP_OFF_B2 + t];
+    M.b3[t] = mr.p[MLP_OFF_B3 + t];
+  }
+  for (int t = threadIdx.x; t < MLP_OUT * MLP_H; t += blockDim.x) M.W4[t] = mr.p[MLP_OFF_W4 + t];
+  if (threadIdx.x < MLP_OUT) M.b4[threadIdx.x] = mr.p[MLP_OFF_B4 + threadIdx.x];
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31u;
+  __nv_bfloat16 *act = actbuf + (threadIdx.x >> 5) * 32 * MLP_LDW;
+  const int64_t nwarps = (int64_t)gridDim.x * MF_WARPS;
+  const int64_t n_seg = sv.seg_ptr[G.n];
+  const float alpha = (float)rc.alpha;
+  unsigned fallback = 0;
+  for (int64_t u = (int64_t)blockIdx.x * MF_WARPS + (threadIdx.x >> 5); u < n_seg; u += nwarps) {
+    const int64_t j = sv.seg_row[u];
+    const int64_t rs = sv.seg_begin[u], re = min(rs + (int64_t)MF_SEG, row_ptr[j + 1]);
+    if (re <= rs) continue;
+    const float4 Vj = G.V[j];
+    const float sig = Vj.w;
+    if (!(sig > 0.0f)) continue;                        // cold gas: the mean field uses the exact limit
+    for (int64_t p0 = rs; p0 < re; p0 += 32) {
+      const int64_t p = p0 + lane;
+      const bool valid = p < re;
+      const float4 Vi = D.V[rows[valid ? p : rs]];
+      const float wx = Vi.x - Vj.x, wy = Vi.y - Vj.y, wz = Vi.z - Vj.z;
+      const float w2 = wx * wx + wy * wy + wz * wz;
+      const float sv_ = sqrtf(w2) / sig;
+      float xin[MLP_IN];
+      const bool in_dom = mlp_inputs(mr.dom, fmaxf(sv_, 1e-30f), sig, xin);
+      // layer 1 for this lane's row
+      __nv_bfloat16 *arow = act + lane * MLP_LDW;
+#pragma unroll 4
+      for (int c = 0; c < MLP_H; c += 2) {
+        float z0 = M.b1[c], z1 = M.b1[c + 1];
+#pragma unroll
+        for (int m = 0; m < MLP_IN; ++m) { z0 += M.W1[c * MLP_IN + m] * xin[m]; z1 += M.W1[(c + 1) * MLP_IN + m] * xin[m]; }
+        *reinterpret_cast<uint32_t *>(arow + c) = pack_bf16(silu(z0), silu(z1));
+      }
+      __syncwarp();
+      float y[2][2][MLP_OUT] = {{{0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}}};
+      mlp_layer32(M.W2, M.b2, act, false, M.W4, y);
+      mlp_layer32(M.W3, M.b3, act, true, M.W4, y);
+      // output layer: reduce the partial dot products over the 4 lanes of each quad
+#pragma unroll
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int o = 0; o < MLP_OUT; ++o) {
+            float v = y[m][h][o];
+            v += __shfl_xor_sync(DMB_FULL, v, 1);
+            v += __shfl_xor_sync(DMB_FULL, v, 2);
+            y[m][h][o] = v + M.b4[o];
+          }
+      // row r = lane: held by quad (r mod 16) mod 8 as m = r / 16, half = (r mod 16) / 8
+      const int r = (int)lane, m = r >> 4, hf = (r >> 3) & 1, src = 4 * (r & 7);
+      float yr[MLP_OUT];
+#pragma unroll
+      for (int o = 0; o < MLP_OUT; ++o) {
+        const float c00 = __shfl_sync(DMB_FULL, y[0][0][o], src), c01 = __shfl_sync(DMB_FULL, y[0][1][o], src);
+        const float c10 = __shfl_sync(DMB_FULL, y[1][0][o], src), c11 = __shfl_sync(DMB_FULL, y[1][1][o], src);
+        yr[o] = m == 0 ? (hf == 0 ? c00 : c01) : (hf == 0 ? c10 : c11);
+      }
+      if (valid) {
+        float FA, FB;
+        if (in_dom) {
+          mlp_outputs(mr.dom, sv_, yr, FA, FB);
+        } else {
+          rates_quad<float>(0.5f * sv_ * sv_, rc.n, alpha, FA, FB);
+          ++fallback;
+        }
+        rates[p] = make_float2(FA, FB);
+      }
+    }
+  }
+  fallback = warp_sum<unsigned>(fallback);
+  if (lane == 0 && fallback && mr.fallback_count) atomicAdd(mr.fallback_count, (unsigned long long)fallback);
+}
+
+cudaError_t launch_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *row_ptr,
+                                  const uint32_t *rows, SegView sv, int64_t n_seg_max, RunConst rc, MlpRun mr,
+                                  float2 *rates, cudaStream_t s, int64_t *launches) {
+  const size_t smem = MLP_ACT_OFFSET + (size_t)MF_WARPS * 32 * MLP_LDW * sizeof(__nv_bfloat16);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_pair_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int64_t blocks = (n_seg_max + MF_WARPS - 1) / MF_WARPS;
+  if (blocks > 152 * 2) blocks = 152 * 2;
+  k_mlp_pair_rates<<<(unsigned)blocks, MF_WARPS * 32, smem, s>>>(G, D, row_ptr, rows, sv, rc, mr, rates);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
 }
 
 // acc_j = cA sum(t FA w), du_j/dt = cA sum(t FA w^2) - cB sum(t FB), and the App. C expected
@@ -167,15 +236,8 @@ cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, co
     k_meanfield<R, DMB_RATE_QUAD><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc,
                                                                               part, mr);
   } else if (rc.rate_mode == DMB_RATE_MLP) {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_meanfield<R, DMB_RATE_MLP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)sizeof(MlpSmem));
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
-    k_meanfield<R, DMB_RATE_MLP><<<(unsigned)blocks, MF_WARPS * 32, sizeof(MlpSmem), s>>>(G, D, bx, row_ptr, rows, sv,
-                                                                                           gtab, rc, part, mr);
+    k_meanfield<R, DMB_RATE_MLP><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc,
+                                                                             part, mr);
   } else {
     k_meanfield<R, DMB_RATE_CLOSED><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc,
                                                                                 part, mr);

@@ -33,10 +33,21 @@ struct MlpSmem {
   float b4[MLP_OUT];
 };
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU through the hardware tanh: silu(z) = z sigmoid(z) = (z/2)(1 + tanh(z/2)), one MUFU
+// operation per activation; training and inference use the same function.
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float silu(float z) {
+  const float h = 0.5f * z;
+  return h + h * tanh_fast(h);
+}
 __device__ __forceinline__ float silu_grad(float z) {
-  const float s = 1.0f / (1.0f + __expf(-z));
-  return s * (1.0f + z * (1.0f - s));
+  const float t = tanh_fast(0.5f * z);                  // sigmoid = (1 + t)/2
+  const float sg = 0.5f + 0.5f * t;
+  return sg * (1.0f + z * (1.0f - sg));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -172,4 +183,86 @@ __device__ __forceinline__ void mlp_outputs(const MlpDomain &d, float s, const f
   const float x = 0.5f * s * s;
   FA = __expf(y[0]) * __powf(1.0f + d.cA * x, d.eA);
   FB = __expf(y[1]) * __powf(1.0f + d.cB * x, d.eB);
+}
+
+// ---- batched inference on pairs: 32 rows per warp ---------------------------------------------
+// Weights in shared memory with rows padded to 136 bf16 (272 bytes) so that ldmatrix reads of 8
+// rows hit distinct banks; activations of a warp's 32 rows are staged the same way.
+#define MLP_LDW 136
+struct MlpSmemPad {
+  __nv_bfloat16 W2[MLP_H * MLP_LDW];
+  __nv_bfloat16 W3[MLP_H * MLP_LDW];
+  float W1[MLP_H * MLP_IN];
+  float b1[MLP_H], b2[MLP_H], b3[MLP_H];
+  float W4[MLP_OUT * MLP_H];
+  float b4[MLP_OUT];
+};
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void *p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+// One 128 -> 128 layer for 32 rows (two m16 tiles) reading A from the warp's activation buffer
+// act (row-major, stride MLP_LDW) and W (row-major [out][in], stride MLP_LDW); writes
+// silu(a W^T + bias) back into act (bf16) when `last` is false; when it is true the float32
+// activations go straight into the output layer: yacc[m][h][o] += W4[o][col] a (partial over
+// this lane's columns; rows m*16 + g + 8h).
+__device__ __forceinline__ void mlp_layer32(const __nv_bfloat16 *__restrict__ W, const float *__restrict__ bias,
+                                            __nv_bfloat16 *act, bool last, const float *__restrict__ W4,
+                                            float yacc[2][2][MLP_OUT]) {
+  const unsigned lane = threadIdx.x & 31u, g = lane >> 2, tig = lane & 3u;
+  // A fragments of both m tiles for all 8 k blocks (ldmatrix: lanes 0-15 rows 0-15 at k,
+  // lanes 16-31 rows 0-15 at k + 8)
+  uint32_t af[2][8][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int kt = 0; kt < 8; ++kt) {
+      const __nv_bfloat16 *pa = act + (m * 16 + (lane & 15)) * MLP_LDW + kt * 16 + (lane >> 4) * 8;
+      uint32_t r[4];
+      ldmatrix_x4(r, pa);
+      // ldmatrix order: (rows 0-7, k lo), (rows 8-15, k lo), (rows 0-7, k hi), (rows 8-15, k hi)
+      af[m][kt][0] = r[0];
+      af[m][kt][1] = r[1];
+      af[m][kt][2] = r[2];
+      af[m][kt][3] = r[3];
+    }
+  __syncwarp();
+#pragma unroll
+  for (int nt = 0; nt < 16; ++nt) {
+    float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int kt = 0; kt < 8; kt += 2) {
+      // B fragments of k blocks kt and kt + 1: matrices (n rows, k lo/hi) of both blocks
+      const __nv_bfloat16 *pb = W + (nt * 8 + (lane & 7)) * MLP_LDW + kt * 16 + (lane >> 3) * 8;
+      uint32_t b[4];
+      ldmatrix_x4(b, pb);
+      mma_bf16_16816(c[0], af[0][kt], b[0], b[1]);
+      mma_bf16_16816(c[1], af[1][kt], b[0], b[1]);
+      mma_bf16_16816(c[0], af[0][kt + 1], b[2], b[3]);
+      mma_bf16_16816(c[1], af[1][kt + 1], b[2], b[3]);
+    }
+    const int col = nt * 8 + tig * 2;
+    const float bb0 = bias[col], bb1 = bias[col + 1];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const float v0 = silu(c[m][0] + bb0), v1 = silu(c[m][1] + bb1);
+      const float v2 = silu(c[m][2] + bb0), v3 = silu(c[m][3] + bb1);
+      if (last) {
+#pragma unroll
+        for (int o = 0; o < MLP_OUT; ++o) {
+          const float w0 = W4[o * MLP_H + col], w1 = W4[o * MLP_H + col + 1];
+          yacc[m][0][o] += w0 * v0 + w1 * v1;
+          yacc[m][1][o] += w0 * v2 + w1 * v3;
+        }
+      } else {
+        *reinterpret_cast<uint32_t *>(act + (m * 16 + g) * MLP_LDW + col) = pack_bf16(v0, v1);
+        *reinterpret_cast<uint32_t *>(act + (m * 16 + g + 8) * MLP_LDW + col) = pack_bf16(v2, v3);
+      }
+    }
+  }
+  __syncwarp();
 }

@@ -11,6 +11,7 @@ struct MlpRun {
   const __nv_bfloat16 *w2, *w3;    // bf16 copies of the 128 x 128 layers
   MlpDomain dom;
   unsigned long long *fallback_count;
+  const float2 *rates;             // per gas-major pair (FA, FB) from launch_mlp_pair_rates
 };
 
 #define SR_UNIT 64   // target leaves per work unit of the tile stage
@@ -75,6 +76,10 @@ struct McArgs {
   double *block_sums;         // [finish blocks][8]: sum M dv (3), dKE, scatters, clamps, band, sum P
   double *block_max;          // [finish blocks]: max p_ratio
 };
+
+cudaError_t launch_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *row_ptr,
+                                  const uint32_t *rows, SegView sv, int64_t n_seg_max, RunConst rc, MlpRun mr,
+                                  float2 *rates, cudaStream_t s, int64_t *launches);
 
 // Per-DM result of the Monte Carlo kernel (sorted order), finished in float64 by k_mc_finish.
 struct McRec {
