@@ -147,6 +147,26 @@ dmb_status dmb_mc_scatter_dm(dmb_ctx *ctx, uint64_t step, double dt, double *vel
 dmb_status dmb_step(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t step,
                     double dt, double *sums_out);
 
+/* Parameters of one box of a batched step (the per-box values of the survey's parameter
+ * scan; the power law n, v0, seed and precision are the context's). */
+typedef struct {
+  double box[3];        /* periodic sides, kpc */
+  double sigma0_cm2;    /* this box's sigma0 */
+  double m_chi_mp;      /* this box's m_chi in m_p */
+} dmb_box;
+
+/* One step of many independent periodic boxes at once (the same physics as dmb_step in each
+ * box; no pair ever joins two boxes).  The particles of all boxes are given concatenated in
+ * any order, with dm_box / gas_box (device, uint32 [n]) naming each particle's box in
+ * boxes[0 .. nbox-1] (host).  Every stage runs once over all boxes: the box index is the top
+ * field of the Morton key, boxes occupy disjoint slots of one virtual space, and each pair uses
+ * its box's sides for the minimum image and its box's sigma0 and m_chi.  Requires a periodic
+ * context; h < min(box side)/4 is checked on the device.  sums_out: as dmb_step, over all
+ * boxes. */
+dmb_status dmb_step_batched(dmb_ctx *ctx, const dmb_dm *dm, const uint32_t *dm_box, const dmb_gas *gas,
+                            const uint32_t *gas_box, const dmb_box *boxes, int32_t nbox, uint64_t step, double dt,
+                            double *sums_out);
+
 /* Debug/verification: evaluate the device overlap integral used by the pair kernels
  * for k (d, h_i, h_j) triples.  in: device [k][3] float64; out: device [k] float64.
  * Uses the table (float32 mode) or the exact evaluator (fp64 mode). */

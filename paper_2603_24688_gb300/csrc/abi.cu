@@ -33,7 +33,7 @@ std::string g_create_error;
 }  // namespace
 
 struct SpeciesBufs {
-  DevBuf keys0, keys1, vals0, vals1, P, L, V, K, sid, bmin, bmax;
+  DevBuf keys0, keys1, vals0, vals1, P, L, V, K, sid, bmin, bmax, bid, leaf_box;
   int64_t n = 0;
   int levels = 0, nodes = 0;
   int off[DMB_MAX_LEVELS] = {0}, cnt[DMB_MAX_LEVELS] = {0};
@@ -61,6 +61,11 @@ struct dmb_ctx {
   // learned surrogate of the rate integrals
   DevBuf mlp_p, mlp_m, mlp_v, mlp_w2, mlp_w3, mlp_w2t, mlp_w3t, mlp_fallback, mlp_rates;
   bool mlp_ready = false;
+  // batched boxes (dmb_step_batched): caller box index arrays of the current build and tables
+  const uint32_t *dm_box = nullptr, *gas_box = nullptr;
+  int nbox = 0;
+  double stride = 0.0;
+  DevBuf box_sides, box_params;
   std::vector<int> mlp_n;        // power-law indices the network was trained for
   double mlp_box[6] = {-2.0, 2.0, -3.0, 2.0, -0.30102999566398120, 1.0};   // log10 ranges of s, tau, m_chi
   int64_t n_seg_max = 0;
@@ -127,8 +132,10 @@ int next_pow2(int64_t x) {
 }
 
 template <typename R>
-SpeciesView<R> view(const SpeciesBufs &s) {
+SpeciesView<R> view(const SpeciesBufs &s, bool batched = false) {
   SpeciesView<R> v;
+  v.bid = batched ? ptr<uint16_t>(s.bid) : nullptr;
+  v.leaf_box = batched ? ptr<int2>(s.leaf_box) : nullptr;
   v.n = s.n;
   v.P = ptr<typename Vec<R>::v4>(s.P);
   v.L = ptr<typename Vec<R>::v4>(s.L);
@@ -149,7 +156,8 @@ dmb_status ensure_species(dmb_ctx *ctx, SpeciesBufs &s, int64_t n, bool gas) {
   s.nodes = tree_layout(n, &s.levels, s.off, s.cnt);
   bool ok = ensure(s.keys0, n * 8) && ensure(s.keys1, n * 8) && ensure(s.vals0, n * 4) && ensure(s.vals1, n * 4) &&
             ensure(s.P, n * v4b) && ensure(s.L, n * v4b) && ensure(s.V, n * v4b) && ensure(s.sid, n * 4) &&
-            ensure(s.bmin, (size_t)s.nodes * 16) && ensure(s.bmax, (size_t)s.nodes * 16);
+            ensure(s.bmin, (size_t)s.nodes * 16) && ensure(s.bmax, (size_t)s.nodes * 16) && ensure(s.bid, n * 2 + 16) &&
+            ensure(s.leaf_box, (size_t)s.cnt[0] * 8 + 16);
   if (gas) ok = ok && ensure(s.K, n * v4b);
   else ok = ok && ensure(s.K, 64);
   if (!ok) return fail(ctx, DMB_ERR_OOM, "device allocation failed for particle buffers");
@@ -187,9 +195,35 @@ dmb_status build_grid_impl(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
   if ((st = ensure_species(ctx, ctx->dm, dm->n, false)) != DMB_OK) return st;
   if ((st = ensure_species(ctx, ctx->gas, gas->n, true)) != DMB_OK) return st;
   if ((st = ensure_sort_scratch(ctx, dm->n > gas->n ? dm->n : gas->n)) != DMB_OK) return st;
-  CK(launch_frame(dm->pos, dm->h, dm->n, gas->pos, gas->h, gas->n, ctx->p.periodic, ctx->p.box,
-                  ptr<double>(ctx->frame_part), (int64_t)(ctx->frame_part.bytes / 8), ptr<Frame>(ctx->frame),
-                  ptr<uint32_t>(ctx->status), s, L), "frame");
+  const bool batched = ctx->nbox > 0;
+  const int64_t ntot = dm->n + gas->n;
+  int bits = (int)fmin(21.0, fmax(10.0, ceil(log2((double)(ntot > 1 ? ntot : 2)) / 3.0) + 7.0));
+  int box_bits = 0;
+  if (batched) {
+    while ((1 << box_bits) < ctx->nbox) ++box_bits;
+    bits = (int)fmin((double)bits, floor((63.0 - box_bits) / 3.0));
+    // frame of the virtual space: boxes side by side along x, each in a slot of width `stride`
+    double Lq = 0.0;
+    std::vector<BoxParamDev> hp(ctx->nbox);
+    CK(cudaMemcpy(hp.data(), ctx->box_params.p, sizeof(BoxParamDev) * ctx->nbox, cudaMemcpyDeviceToHost), "box table");
+    for (auto &b : hp) Lq = fmax(Lq, fmax(b.L[0], fmax(b.L[1], b.L[2])));
+    Frame f;
+    for (int c = 0; c < 3; ++c) f.origin[c] = 0.0;
+    f.span = fmax(ctx->nbox * ctx->stride, Lq);
+    int e;
+    frexp(f.span, &e);
+    f.delta = ldexp(1.0, e - 23);
+    f.bits = bits;
+    f.key_scale = ldexp(1.0, bits) / (Lq * (1.0 + 1e-12));
+    f.pad = (float)(4.0 * ldexp(1.0, e) * 1.1920928955078125e-07);
+    f.hmax_dm = f.hmax_gas = 0.0;
+    CK(cudaMemcpyAsync(ctx->frame.p, &f, sizeof(Frame), cudaMemcpyHostToDevice, s), "frame");
+    CK(cudaStreamSynchronize(s), "frame");
+  } else {
+    CK(launch_frame(dm->pos, dm->h, dm->n, gas->pos, gas->h, gas->n, ctx->p.periodic, ctx->p.box,
+                    ptr<double>(ctx->frame_part), (int64_t)(ctx->frame_part.bytes / 8), ptr<Frame>(ctx->frame),
+                    ptr<uint32_t>(ctx->status), s, L), "frame");
+  }
   const Frame *fr = ptr<Frame>(ctx->frame);
   SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};
   const double *pos[2] = {dm->pos, gas->pos};
@@ -199,25 +233,28 @@ dmb_status build_grid_impl(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
   const double *T[2] = {nullptr, gas->T};
   const double *mu[2] = {nullptr, gas->mu};
   const uint32_t *id[2] = {dm->id, gas->id};
-  // Morton bits: enough for the larger species (the frame kernel picks the same rule)
-  const int64_t ntot = dm->n + gas->n;
-  const int bits = (int)fmin(21.0, fmax(10.0, ceil(log2((double)(ntot > 1 ? ntot : 2)) / 3.0) + 7.0));
+  const uint32_t *box_of[2] = {ctx->dm_box, ctx->gas_box};
   for (int k = 0; k < 2; ++k) {
     SpeciesBufs &b = *sp[k];
+    BatchArgs ba;
+    ba.box_of = batched ? box_of[k] : nullptr;
+    ba.bp = batched ? ptr<BoxParamDev>(ctx->box_params) : nullptr;
+    ba.box_bits = box_bits;
     if (b.n > 0) {
-      CK(launch_morton(pos[k], b.n, ctx->p.periodic, ctx->p.box, fr, ptr<uint64_t>(b.keys0), ptr<uint32_t>(b.vals0), s,
-                       L), "morton");
+      CK(launch_morton(pos[k], b.n, ctx->p.periodic, ctx->p.box, fr, ba, ptr<uint64_t>(b.keys0), ptr<uint32_t>(b.vals0),
+                       s, L), "morton");
       CK(radix_sort_pairs(ptr<uint64_t>(b.keys0), ptr<uint32_t>(b.vals0), ptr<uint64_t>(b.keys1),
-                          ptr<uint32_t>(b.vals1), b.n, 3 * bits, ptr<uint32_t>(ctx->hist), ptr<int64_t>(ctx->hist_scan),
-                          ptr<int64_t>(ctx->scan_tmp), s, L), "radix sort");
+                          ptr<uint32_t>(b.vals1), b.n, 3 * bits + box_bits, ptr<uint32_t>(ctx->hist),
+                          ptr<int64_t>(ctx->hist_scan), ptr<int64_t>(ctx->scan_tmp), s, L), "radix sort");
       CK(launch_gather<R>(pos[k], vel[k], mass[k], hh[k], T[k], mu[k], id[k], b.n, ptr<uint32_t>(b.vals0),
-                          ctx->p.periodic, ctx->p.box, fr, ctx->rc, ptr<typename Vec<R>::v4>(b.P),
+                          ctx->p.periodic, ctx->p.box, fr, ctx->rc, ba, ptr<typename Vec<R>::v4>(b.P),
                           ptr<typename Vec<R>::v4>(b.L), ptr<typename Vec<R>::v4>(b.V),
-                          ptr<typename Vec<R>::v4>(b.K), ptr<uint32_t>(b.sid), ptr<uint32_t>(ctx->status), s, L),
-         "gather");
+                          ptr<typename Vec<R>::v4>(b.K), ptr<uint32_t>(b.sid), ptr<uint16_t>(b.bid),
+                          ptr<uint32_t>(ctx->status), s, L), "gather");
     }
     CK(launch_tree<R>(ptr<typename Vec<R>::v4>(b.P), ptr<typename Vec<R>::v4>(b.L), b.n, fr, ptr<float4>(b.bmin),
-                      ptr<float4>(b.bmax), b.levels, b.off, b.cnt, s, L), "tree");
+                      ptr<float4>(b.bmax), b.levels, b.off, b.cnt, batched ? ptr<uint16_t>(b.bid) : nullptr,
+                      ptr<int2>(b.leaf_box), s, L), "tree");
   }
   ctx->dm_vel = dm->vel;
   ctx->grid_ready = true;
@@ -323,7 +360,7 @@ dmb_status build_segments(dmb_ctx *ctx, const SearchBufs &sg, int64_t ng) {
 template <typename R>
 dmb_status neighbors_impl(dmb_ctx *ctx) {
   cudaStream_t s = ctx->stream;
-  const SpeciesView<R> D = view<R>(ctx->dm), G = view<R>(ctx->gas);
+  const SpeciesView<R> D = view<R>(ctx->dm, ctx->nbox > 0), G = view<R>(ctx->gas, ctx->nbox > 0);
   const int64_t nmax = D.n > G.n ? D.n : G.n;
   dmb_status st;
   if ((st = ensure_sort_scratch(ctx, nmax + 1)) != DMB_OK) return st;
@@ -413,7 +450,7 @@ MlpRun mlp_run(dmb_ctx *ctx) {
 
 template <typename R>
 dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp) {
-  const SpeciesView<R> D = view<R>(ctx->dm), G = view<R>(ctx->gas);
+  const SpeciesView<R> D = view<R>(ctx->dm, ctx->nbox > 0), G = view<R>(ctx->gas, ctx->nbox > 0);
   MfOut o;
   o.acc = acc;
   o.dudt = dudt;
@@ -434,7 +471,8 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
     if (!ensure(ctx->mlp_rates, (size_t)ctx->sg.n_pairs * 8 + 8)) return fail(ctx, DMB_ERR_OOM, "surrogate rates");
     mr.rates = ptr<float2>(ctx->mlp_rates);
     if (sizeof(R) == 4)
-      CK(launch_mlp_pair_rates(view<float>(ctx->gas), view<float>(ctx->dm), ptr<int64_t>(ctx->sg.row_ptr),
+      CK(launch_mlp_pair_rates(view<float>(ctx->gas, ctx->nbox > 0), view<float>(ctx->dm, ctx->nbox > 0),
+                               ptr<int64_t>(ctx->sg.row_ptr),
                                ptr<uint32_t>(ctx->sg.rows), sv, ctx->n_seg_max, ctx->rc, mr,
                                ptr<float2>(ctx->mlp_rates), ctx->stream, &ctx->launches), "surrogate rates");
   }
@@ -453,7 +491,7 @@ int mc_blocks_for(int64_t n) {   // blocks of the float64 finish kernel (256 thr
 template <typename R>
 dmb_status mc_impl(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, uint8_t *scat, uint32_t *partner,
                    float *pratio, double *ptot) {
-  const SpeciesView<R> D = view<R>(ctx->dm), G = view<R>(ctx->gas);
+  const SpeciesView<R> D = view<R>(ctx->dm, ctx->nbox > 0), G = view<R>(ctx->gas, ctx->nbox > 0);
   const int nb = mc_blocks_for(D.n);
   if (!ensure(ctx->mc_blocks, (size_t)nb * 8 * 8) || !ensure(ctx->mc_max, (size_t)nb * 8))
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for MC partials");
@@ -568,12 +606,14 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
   DevBuf *bufs[] = {&ctx->frame, &ctx->status, &ctx->frame_part, &ctx->gtab, &ctx->hist, &ctx->hist_scan,
                     &ctx->scan_tmp, &ctx->pcache, &ctx->mf_part, &ctx->mc_rec, &ctx->seg_cnt, &ctx->seg_ptr,
                     &ctx->seg_row, &ctx->seg_begin, &ctx->t_cursor, &ctx->mlp_p, &ctx->mlp_m, &ctx->mlp_v,
-                    &ctx->mlp_w2, &ctx->mlp_w3, &ctx->mlp_w2t, &ctx->mlp_w3t, &ctx->mlp_fallback, &ctx->mlp_rates, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
+                    &ctx->mlp_w2, &ctx->mlp_w3, &ctx->mlp_w2t, &ctx->mlp_w3t, &ctx->mlp_fallback, &ctx->mlp_rates,
+                    &ctx->box_sides, &ctx->box_params, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
                     &ctx->kick_blocks, &ctx->sums, &ctx->scratch_vel, &ctx->search_stats};
   for (DevBuf *b : bufs) release(*b);
   SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};
   for (SpeciesBufs *s : sp) {
-    DevBuf *sb[] = {&s->keys0, &s->keys1, &s->vals0, &s->vals1, &s->P, &s->L, &s->V, &s->K, &s->sid, &s->bmin, &s->bmax};
+    DevBuf *sb[] = {&s->keys0, &s->keys1, &s->vals0, &s->vals1, &s->P, &s->L, &s->V, &s->K, &s->sid, &s->bmin, &s->bmax,
+                    &s->bid, &s->leaf_box};
     for (DevBuf *b : sb) release(*b);
   }
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
@@ -589,11 +629,18 @@ const char *dmb_last_error(const dmb_ctx *ctx) { return ctx ? ctx->err.c_str() :
 
 int64_t dmb_launch_count(const dmb_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
-dmb_status dmb_build_grid(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
-  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+static dmb_status build_grid_checked(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
   dmb_status st;
   if ((st = check_dm(ctx, dm)) != DMB_OK || (st = check_gas(ctx, gas)) != DMB_OK) return st;
   return ctx->p.fp64 ? build_grid_impl<double>(ctx, dm, gas) : build_grid_impl<float>(ctx, dm, gas);
+}
+
+dmb_status dmb_build_grid(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  ctx->nbox = 0;
+  ctx->dm_box = ctx->gas_box = nullptr;
+  ctx->bx.boxes = nullptr;
+  return build_grid_checked(ctx, dm, gas);
 }
 
 dmb_status dmb_neighbors(dmb_ctx *ctx, int64_t *n_pairs, uint32_t *pairs_out, int64_t capacity) {
@@ -626,13 +673,76 @@ dmb_status dmb_mc_scatter_dm(dmb_ctx *ctx, uint64_t step, double dt, double *vel
                      : mc_impl<float>(ctx, step, dt, vel_out, scattered, partner, p_ratio_max, p_total);
 }
 
+static dmb_status step_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t step, double dt,
+                            double *sums_out);
+
 dmb_status dmb_step(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t step, double dt, double *sums_out) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
   if (!(dt >= 0.0) || !isfinite(dt)) return fail(ctx, DMB_ERR_ARG, "dt must be finite and >= 0");
+  ctx->nbox = 0;
+  ctx->dm_box = ctx->gas_box = nullptr;
+  ctx->bx.boxes = nullptr;
+  return step_body(ctx, dm, gas, step, dt, sums_out);
+}
+
+dmb_status dmb_step_batched(dmb_ctx *ctx, const dmb_dm *dm, const uint32_t *dm_box, const dmb_gas *gas,
+                            const uint32_t *gas_box, const dmb_box *boxes, int32_t nbox, uint64_t step, double dt,
+                            double *sums_out) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!(dt >= 0.0) || !isfinite(dt)) return fail(ctx, DMB_ERR_ARG, "dt must be finite and >= 0");
+  if (!ctx->p.periodic) return fail(ctx, DMB_ERR_ARG, "batched boxes need a periodic context");
+  if (nbox < 1 || nbox > 65535 || !boxes) return fail(ctx, DMB_ERR_ARG, "nbox must be in [1, 65535] with a box table");
+  if ((dm && dm->n > 0 && !dm_box) || (gas && gas->n > 0 && !gas_box))
+    return fail(ctx, DMB_ERR_ARG, "box index arrays are required");
+  std::vector<BoxSide> sides(nbox);
+  std::vector<BoxParamDev> bp(nbox);
+  double Lmax = 0.0;
+  for (int b = 0; b < nbox; ++b) {
+    for (int k = 0; k < 3; ++k) {
+      const double L = boxes[b].box[k];
+      if (!(L > 0.0) || !isfinite(L)) return fail(ctx, DMB_ERR_ARG, "box sides must be > 0");
+      Lmax = fmax(Lmax, L);
+    }
+    if (!(boxes[b].sigma0_cm2 >= 0.0) || !(boxes[b].m_chi_mp > 0.0))
+      return fail(ctx, DMB_ERR_ARG, "box sigma0 must be >= 0 and m_chi > 0");
+  }
+  // slots of width 3 Lmax: particles of different boxes are >= 2 Lmax apart, so even after a
+  // minimum-image shift by one side (<= Lmax) they stay >= Lmax > h_i + h_j apart, and a box's
+  // periodic images searched by the tree stay inside its own slot
+  ctx->stride = 3.0 * Lmax;
+  for (int b = 0; b < nbox; ++b) {
+    for (int k = 0; k < 3; ++k) {
+      const double L = boxes[b].box[k];
+      sides[b].L[k] = L;
+      sides[b].Lhi[k] = (float)L;
+      sides[b].Llo[k] = (float)(L - (double)sides[b].Lhi[k]);
+      bp[b].L[k] = L;
+    }
+    bp[b].S = boxes[b].sigma0_cm2 / (kKPC * kKPC) * (kMSUN / kMP);
+    bp[b].m_chi = boxes[b].m_chi_mp;
+    bp[b].offset_x = b * ctx->stride;
+  }
+  if (!ensure(ctx->box_sides, sizeof(BoxSide) * nbox) || !ensure(ctx->box_params, sizeof(BoxParamDev) * nbox))
+    return fail(ctx, DMB_ERR_OOM, "box tables");
+  CK(cudaMemcpy(ctx->box_sides.p, sides.data(), sizeof(BoxSide) * nbox, cudaMemcpyHostToDevice), "box table");
+  CK(cudaMemcpy(ctx->box_params.p, bp.data(), sizeof(BoxParamDev) * nbox, cudaMemcpyHostToDevice), "box table");
+  ctx->nbox = nbox;
+  ctx->dm_box = dm_box;
+  ctx->gas_box = gas_box;
+  ctx->bx.boxes = ptr<BoxSide>(ctx->box_sides);
+  const dmb_status st = step_body(ctx, dm, gas, step, dt, sums_out);
+  ctx->nbox = 0;
+  ctx->dm_box = ctx->gas_box = nullptr;
+  ctx->bx.boxes = nullptr;
+  return st;
+}
+
+static dmb_status step_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t step, double dt,
+                            double *sums_out) {
   dmb_status st;
   const bool tm = ctx->timing;
   if (tm) CK(cudaEventRecord(ctx->ev[0], ctx->stream), "event");
-  if ((st = dmb_build_grid(ctx, dm, gas)) != DMB_OK) return st;
+  if ((st = build_grid_checked(ctx, dm, gas)) != DMB_OK) return st;
   if (tm) CK(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
   if ((st = dmb_neighbors(ctx, nullptr, nullptr, 0)) != DMB_OK) return st;
   if (tm) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");

@@ -46,6 +46,8 @@ template <typename R> struct SpeciesView {
   const typename Vec<R>::v4 *K;   // gas: (cA, cB, kP0, e = mu/(m_chi + mu)); dm: unused
   const uint32_t *id;             // stable id
   const uint32_t *perm;           // sorted position -> caller index
+  const uint16_t *bid;            // batched boxes: box index per sorted particle (else null)
+  const int2 *leaf_box;           // batched boxes: lowest and highest box index per leaf (else null)
   // 32-ary tree: level 0 = leaves of DMB_LEAF consecutive sorted particles, node i of level
   // l > 0 groups nodes 32i .. 32i+31 of level l-1; level l occupies [off[l], off[l] + cnt[l])
   const float4 *bmin;             // (min xyz, h_max of the particles below)
@@ -55,37 +57,51 @@ template <typename R> struct SpeciesView {
   int32_t cnt[DMB_MAX_LEVELS];
 };
 
-// Periodic box in the split representation.
-struct BoxSplit {
-  int periodic;
-  float Lhi[3], Llo[3];           // float32 split of the box sides
+// Sides of one periodic box in the split representation (float hi + float lo, and float64).
+struct BoxSide {
+  float Lhi[3], Llo[3];
   double L[3];
-  float pad;                      // conservative padding of tree boxes
 };
 
-// Canonical pair displacement x_a - x_b (minimum image if periodic), identical bits whichever
-// kernel computes it and antisymmetric in (a, b).
+// Periodic boxes: one (the context's), or a table of per-box sides for batched boxes, each
+// particle carrying its box index.
+struct BoxSplit {
+  int periodic;
+  float Lhi[3], Llo[3];
+  double L[3];
+  float pad;
+  const BoxSide *boxes;           // batched mode: device table indexed by box id, else null
+  __device__ __forceinline__ BoxSide side(int box) const {
+    if (boxes != nullptr) return boxes[box];
+    BoxSide s;
+    for (int k = 0; k < 3; ++k) { s.Lhi[k] = Lhi[k]; s.Llo[k] = Llo[k]; s.L[k] = L[k]; }
+    return s;
+  }
+};
+
+// Canonical pair displacement x_a - x_b (minimum image in the pair's periodic box when
+// periodic), identical bits whichever kernel computes it and antisymmetric in (a, b).
 template <typename R>
 __device__ __forceinline__ void pair_dx(const typename Vec<R>::v4 &Pa, const typename Vec<R>::v4 &La,
-                                        const typename Vec<R>::v4 &Pb, const typename Vec<R>::v4 &Lb,
-                                        const BoxSplit &bx, R &dx, R &dy, R &dz) {
+                                        const typename Vec<R>::v4 &Pb, const typename Vec<R>::v4 &Lb, int periodic,
+                                        const BoxSide &bs, R &dx, R &dy, R &dz) {
   R hx = sub_rn(Pa.x, Pb.x), hy = sub_rn(Pa.y, Pb.y), hz = sub_rn(Pa.z, Pb.z);   // exact
   R lx = sub_rn(La.x, Lb.x), ly = sub_rn(La.y, Lb.y), lz = sub_rn(La.z, Lb.z);
-  if (bx.periodic) {
-    const R L0 = (R)bx.Lhi[0], L1 = (R)bx.Lhi[1], L2 = (R)bx.Lhi[2];
+  if (periodic) {
     if (sizeof(R) == 8) {  // float64 path: the box side is exact in double
-      if (hx > (R)(0.5 * bx.L[0])) hx = sub_rn(hx, (R)bx.L[0]); else if (hx < (R)(-0.5 * bx.L[0])) hx = add_rn(hx, (R)bx.L[0]);
-      if (hy > (R)(0.5 * bx.L[1])) hy = sub_rn(hy, (R)bx.L[1]); else if (hy < (R)(-0.5 * bx.L[1])) hy = add_rn(hy, (R)bx.L[1]);
-      if (hz > (R)(0.5 * bx.L[2])) hz = sub_rn(hz, (R)bx.L[2]); else if (hz < (R)(-0.5 * bx.L[2])) hz = add_rn(hz, (R)bx.L[2]);
+      if (hx > (R)(0.5 * bs.L[0])) hx = sub_rn(hx, (R)bs.L[0]); else if (hx < (R)(-0.5 * bs.L[0])) hx = add_rn(hx, (R)bs.L[0]);
+      if (hy > (R)(0.5 * bs.L[1])) hy = sub_rn(hy, (R)bs.L[1]); else if (hy < (R)(-0.5 * bs.L[1])) hy = add_rn(hy, (R)bs.L[1]);
+      if (hz > (R)(0.5 * bs.L[2])) hz = sub_rn(hz, (R)bs.L[2]); else if (hz < (R)(-0.5 * bs.L[2])) hz = add_rn(hz, (R)bs.L[2]);
     } else {
       // hi differences in (L/2, L) minus the float side are exact (Sterbenz); the low part
       // of the side goes with lo
-      if (hx > (R)0.5 * L0) { hx = sub_rn(hx, L0); lx = sub_rn(lx, (R)bx.Llo[0]); }
-      else if (hx < (R)-0.5 * L0) { hx = add_rn(hx, L0); lx = add_rn(lx, (R)bx.Llo[0]); }
-      if (hy > (R)0.5 * L1) { hy = sub_rn(hy, L1); ly = sub_rn(ly, (R)bx.Llo[1]); }
-      else if (hy < (R)-0.5 * L1) { hy = add_rn(hy, L1); ly = add_rn(ly, (R)bx.Llo[1]); }
-      if (hz > (R)0.5 * L2) { hz = sub_rn(hz, L2); lz = sub_rn(lz, (R)bx.Llo[2]); }
-      else if (hz < (R)-0.5 * L2) { hz = add_rn(hz, L2); lz = add_rn(lz, (R)bx.Llo[2]); }
+      const R L0 = (R)bs.Lhi[0], L1 = (R)bs.Lhi[1], L2 = (R)bs.Lhi[2];
+      if (hx > (R)0.5 * L0) { hx = sub_rn(hx, L0); lx = sub_rn(lx, (R)bs.Llo[0]); }
+      else if (hx < (R)-0.5 * L0) { hx = add_rn(hx, L0); lx = add_rn(lx, (R)bs.Llo[0]); }
+      if (hy > (R)0.5 * L1) { hy = sub_rn(hy, L1); ly = sub_rn(ly, (R)bs.Llo[1]); }
+      else if (hy < (R)-0.5 * L1) { hy = add_rn(hy, L1); ly = add_rn(ly, (R)bs.Llo[1]); }
+      if (hz > (R)0.5 * L2) { hz = sub_rn(hz, L2); lz = sub_rn(lz, (R)bs.Llo[2]); }
+      else if (hz < (R)-0.5 * L2) { hz = add_rn(hz, L2); lz = add_rn(lz, (R)bs.Llo[2]); }
     }
   }
   dx = add_rn(hx, lx);

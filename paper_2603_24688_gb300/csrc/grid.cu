@@ -134,30 +134,39 @@ __device__ __forceinline__ double wrap_coord(double x, double L) {
   return w;
 }
 
+// Single box: 3 x bits Morton key of the position in the frame.  Batched boxes: the box index in
+// the bits above, then the Morton key of the position inside the box (so boxes stay contiguous).
 __global__ void k_morton(const double *__restrict__ pos, int64_t n, int periodic, double L0, double L1, double L2,
-                         const Frame *__restrict__ frame, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                         const Frame *__restrict__ frame, BatchArgs ba, uint64_t *__restrict__ keys,
+                         uint32_t *__restrict__ vals) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Frame f = *frame;
-  const double Ls[3] = {L0, L1, L2};
+  double Ls[3] = {L0, L1, L2};
+  uint64_t boxkey = 0;
+  if (ba.box_of != nullptr) {
+    const uint32_t b = ba.box_of[i];
+    for (int c = 0; c < 3; ++c) Ls[c] = ba.bp[b].L[c];
+    boxkey = (uint64_t)b << (3 * f.bits);
+  }
   const uint64_t top = (1ull << f.bits) - 1ull;
   uint64_t q[3];
   for (int c = 0; c < 3; ++c) {
     double x = pos[3 * i + c];
     if (periodic) x = wrap_coord(x, Ls[c]);
-    double u = (x - f.origin[c]) * f.key_scale;
+    double u = (ba.box_of != nullptr ? x : x - f.origin[c]) * f.key_scale;
     if (!(u >= 0.0)) u = 0.0;                      // also catches NaN (flagged in gather)
     uint64_t k = u >= (double)top ? top : (uint64_t)u;
     q[c] = k;
   }
-  keys[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+  keys[i] = boxkey | spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
   vals[i] = (uint32_t)i;
 }
 
 cudaError_t launch_morton(const double *pos, int64_t n, int periodic, const double box[3], const Frame *frame,
-                          uint64_t *keys, uint32_t *vals, cudaStream_t s, int64_t *launches) {
+                          BatchArgs ba, uint64_t *keys, uint32_t *vals, cudaStream_t s, int64_t *launches) {
   if (n <= 0) return cudaSuccess;
-  k_morton<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, periodic, box[0], box[1], box[2], frame, keys, vals);
+  k_morton<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, n, periodic, box[0], box[1], box[2], frame, ba, keys, vals);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
@@ -168,20 +177,35 @@ __global__ void k_gather(const double *__restrict__ pos, const double *__restric
                          const double *__restrict__ mass, const double *__restrict__ h, const double *__restrict__ T,
                          const double *__restrict__ mu, const uint32_t *__restrict__ id, int64_t n,
                          const uint32_t *__restrict__ perm, int periodic, double L0, double L1, double L2,
-                         const Frame *__restrict__ frame, RunConst rc, typename Vec<R>::v4 *__restrict__ P,
-                         typename Vec<R>::v4 *__restrict__ Lo, typename Vec<R>::v4 *__restrict__ V,
-                         typename Vec<R>::v4 *__restrict__ K, uint32_t *__restrict__ sid, uint32_t *status) {
+                         const Frame *__restrict__ frame, RunConst rc, BatchArgs ba,
+                         typename Vec<R>::v4 *__restrict__ P, typename Vec<R>::v4 *__restrict__ Lo,
+                         typename Vec<R>::v4 *__restrict__ V, typename Vec<R>::v4 *__restrict__ K,
+                         uint32_t *__restrict__ sid, uint16_t *__restrict__ bid, uint32_t *status) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const uint32_t i = perm[s];
   const double delta = frame->delta;
-  const double Ls[3] = {L0, L1, L2};
-  R hi[3], lo[3];
+  double Ls[3] = {L0, L1, L2};
+  double xoff = 0.0;
   bool bad = false;
+  if (ba.box_of != nullptr) {
+    // batched boxes: this box's sides, constants and slot in the virtual space
+    const uint32_t b = ba.box_of[i];
+    const BoxParamDev bp = ba.bp[b];
+    for (int c = 0; c < 3; ++c) Ls[c] = bp.L[c];
+    xoff = bp.offset_x;
+    rc.S = bp.S;
+    rc.m_chi = bp.m_chi;
+    bid[s] = (uint16_t)b;
+    const double hh = h[i];
+    if (!(hh < 0.25 * fmin(Ls[0], fmin(Ls[1], Ls[2])))) atomicOr(status, DMB_BAD_PERIODIC);
+  }
+  R hi[3], lo[3];
   for (int c = 0; c < 3; ++c) {
     double x = pos[3 * (int64_t)i + c];
     bad |= !isfinite(x);
     if (periodic) x = wrap_coord(x, Ls[c]);
+    if (c == 0) x += xoff;
     const double rel = x - frame->origin[c];
     const double hq = floor(rel / delta) * delta;     // k * delta, |k| < 2^24
     hi[c] = (R)hq;
@@ -221,26 +245,27 @@ __global__ void k_gather(const double *__restrict__ pos, const double *__restric
 template <typename R>
 cudaError_t launch_gather(const double *pos, const double *vel, const double *mass, const double *h,
                           const double *T, const double *mu, const uint32_t *id, int64_t n, const uint32_t *perm,
-                          int periodic, const double box[3], const Frame *frame, RunConst rc,
+                          int periodic, const double box[3], const Frame *frame, RunConst rc, BatchArgs ba,
                           typename Vec<R>::v4 *P, typename Vec<R>::v4 *L, typename Vec<R>::v4 *V,
-                          typename Vec<R>::v4 *K, uint32_t *sid, uint32_t *status, cudaStream_t s,
+                          typename Vec<R>::v4 *K, uint32_t *sid, uint16_t *bid, uint32_t *status, cudaStream_t s,
                           int64_t *launches) {
   if (n <= 0) return cudaSuccess;
   k_gather<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pos, vel, mass, h, T, mu, id, n, perm, periodic, box[0],
-                                                          box[1], box[2], frame, rc, P, L, V, K, sid, status);
+                                                          box[1], box[2], frame, rc, ba, P, L, V, K, sid, bid,
+                                                          status);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
 template cudaError_t launch_gather<float>(const double *, const double *, const double *, const double *,
                                           const double *, const double *, const uint32_t *, int64_t,
-                                          const uint32_t *, int, const double *, const Frame *, RunConst, float4 *,
-                                          float4 *, float4 *, float4 *, uint32_t *, uint32_t *, cudaStream_t,
-                                          int64_t *);
+                                          const uint32_t *, int, const double *, const Frame *, RunConst, BatchArgs,
+                                          float4 *, float4 *, float4 *, float4 *, uint32_t *, uint16_t *, uint32_t *,
+                                          cudaStream_t, int64_t *);
 template cudaError_t launch_gather<double>(const double *, const double *, const double *, const double *,
                                            const double *, const double *, const uint32_t *, int64_t,
-                                           const uint32_t *, int, const double *, const Frame *, RunConst,
-                                           double4_32a *, double4_32a *, double4_32a *, double4_32a *, uint32_t *, uint32_t *,
-                                           cudaStream_t, int64_t *);
+                                           const uint32_t *, int, const double *, const Frame *, RunConst, BatchArgs,
+                                           double4_32a *, double4_32a *, double4_32a *, double4_32a *, uint32_t *,
+                                           uint16_t *, uint32_t *, cudaStream_t, int64_t *);
 
 // ---- chunk tree ------------------------------------------------------------------------
 // Leaves hold DMB_LEAF consecutive sorted particles; every inner node groups 32 consecutive
@@ -264,7 +289,7 @@ int tree_layout(int64_t n, int *levels, int off[DMB_MAX_LEVELS], int cnt[DMB_MAX
 template <typename R>
 __global__ void k_tree_leaves(const typename Vec<R>::v4 *__restrict__ P, const typename Vec<R>::v4 *__restrict__ L,
                               int64_t n, int nleaf, const Frame *__restrict__ frame, float4 *__restrict__ bmin,
-                              float4 *__restrict__ bmax) {
+                              float4 *__restrict__ bmax, const uint16_t *__restrict__ bid, int2 *__restrict__ leaf_box) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned lane = threadIdx.x & 31u;
   if (warp >= nleaf) return;
@@ -285,6 +310,15 @@ __global__ void k_tree_leaves(const typename Vec<R>::v4 *__restrict__ P, const t
       mx[k] = fmaxf(mx[k], __shfl_xor_sync(DMB_FULL, mx[k], o));
     }
     hm = fmaxf(hm, __shfl_xor_sync(DMB_FULL, hm, o));
+  }
+  if (bid != nullptr) {
+    int b0 = i < n ? (int)bid[i] : 0x7fffffff, b1 = i < n ? (int)bid[i] : -1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      b0 = min(b0, __shfl_xor_sync(DMB_FULL, b0, o));
+      b1 = max(b1, __shfl_xor_sync(DMB_FULL, b1, o));
+    }
+    if (lane == 0) leaf_box[warp] = make_int2(b1 >= 0 ? b0 : 0, b1 >= 0 ? b1 : 0);
   }
   if (lane == 0) {
     const float pad = frame->pad;
@@ -325,10 +359,11 @@ __global__ void k_tree_level(float4 *__restrict__ bmin, float4 *__restrict__ bma
 
 template <typename R>
 cudaError_t launch_tree(const typename Vec<R>::v4 *P, const typename Vec<R>::v4 *L, int64_t n, const Frame *frame,
-                        float4 *bmin, float4 *bmax, int levels, const int *off, const int *cnt, cudaStream_t s,
-                        int64_t *launches) {
+                        float4 *bmin, float4 *bmax, int levels, const int *off, const int *cnt, const uint16_t *bid,
+                        int2 *leaf_box, cudaStream_t s, int64_t *launches) {
   const int64_t t0 = (int64_t)cnt[0] * 32;
-  k_tree_leaves<R><<<(unsigned)((t0 + 255) / 256), 256, 0, s>>>(P, L, n, cnt[0], frame, bmin + off[0], bmax + off[0]);
+  k_tree_leaves<R><<<(unsigned)((t0 + 255) / 256), 256, 0, s>>>(P, L, n, cnt[0], frame, bmin + off[0], bmax + off[0],
+                                                                 bid, leaf_box);
   if (launches) *launches += 1;
   for (int l = 1; l < levels; ++l) {
     const int64_t t = (int64_t)cnt[l] * 32;
@@ -338,6 +373,8 @@ cudaError_t launch_tree(const typename Vec<R>::v4 *P, const typename Vec<R>::v4 
   return cudaGetLastError();
 }
 template cudaError_t launch_tree<float>(const float4 *, const float4 *, int64_t, const Frame *, float4 *, float4 *,
-                                        int, const int *, const int *, cudaStream_t, int64_t *);
+                                        int, const int *, const int *, const uint16_t *, int2 *, cudaStream_t,
+                                        int64_t *);
 template cudaError_t launch_tree<double>(const double4_32a *, const double4_32a *, int64_t, const Frame *, float4 *,
-                                         float4 *, int, const int *, const int *, cudaStream_t, int64_t *);
+                                         float4 *, int, const int *, const int *, const uint16_t *, int2 *,
+                                         cudaStream_t, int64_t *);

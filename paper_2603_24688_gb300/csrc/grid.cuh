@@ -23,6 +23,20 @@ struct RunConst {
   int rate_mode;     // dmb_rate_mode
 };
 
+// Batched boxes: per-box parameters used by the key and gather kernels (device table).
+struct BoxParamDev {
+  double L[3];        // periodic sides, kpc
+  double S;           // sigma0 [kpc^2] * Msun / m_p of this box
+  double m_chi;       // m_chi / m_p of this box
+  double offset_x;    // x offset of the box's slot in the shared virtual space
+};
+
+struct BatchArgs {
+  const uint32_t *box_of;       // caller: box index per particle (null: single box)
+  const BoxParamDev *bp;        // device table
+  int box_bits;                 // bits of the box index in the key
+};
+
 // Status bits raised by the device checks.
 enum : uint32_t {
   DMB_BAD_VALUE = 1u,      // NaN / Inf or a non-positive h, M, mu, or negative T
@@ -36,14 +50,14 @@ cudaError_t launch_frame(const double *dm_pos, const double *dm_h, int64_t ndm, 
                          int64_t part_elems, Frame *frame, uint32_t *status, cudaStream_t s, int64_t *launches);
 
 cudaError_t launch_morton(const double *pos, int64_t n, int periodic, const double box[3], const Frame *frame,
-                          uint64_t *keys, uint32_t *vals, cudaStream_t s, int64_t *launches);
+                          BatchArgs ba, uint64_t *keys, uint32_t *vals, cudaStream_t s, int64_t *launches);
 
 template <typename R>
 cudaError_t launch_gather(const double *pos, const double *vel, const double *mass, const double *h,
                           const double *T, const double *mu, const uint32_t *id, int64_t n, const uint32_t *perm,
-                          int periodic, const double box[3], const Frame *frame, RunConst rc,
+                          int periodic, const double box[3], const Frame *frame, RunConst rc, BatchArgs ba,
                           typename Vec<R>::v4 *P, typename Vec<R>::v4 *L, typename Vec<R>::v4 *V,
-                          typename Vec<R>::v4 *K, uint32_t *sid, uint32_t *status, cudaStream_t s,
+                          typename Vec<R>::v4 *K, uint32_t *sid, uint16_t *bid, uint32_t *status, cudaStream_t s,
                           int64_t *launches);
 
 // Level layout of the 32-ary tree for n particles; returns the number of nodes.
@@ -51,5 +65,5 @@ int tree_layout(int64_t n, int *levels, int off[DMB_MAX_LEVELS], int cnt[DMB_MAX
 
 template <typename R>
 cudaError_t launch_tree(const typename Vec<R>::v4 *P, const typename Vec<R>::v4 *L, int64_t n, const Frame *frame,
-                        float4 *bmin, float4 *bmax, int levels, const int *off, const int *cnt, cudaStream_t s,
-                        int64_t *launches);
+                        float4 *bmin, float4 *bmax, int levels, const int *off, const int *cnt, const uint16_t *bid,
+                        int2 *leaf_box, cudaStream_t s, int64_t *launches);

@@ -30,6 +30,7 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
     R sx = 0, sy = 0, sz = 0, sw2 = 0, sb = 0, svw = 0;
     if (re > rs) {
       const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j];
+      const BoxSide side = bx.side(G.bid != nullptr ? (int)G.bid[j] : 0);
       const R sig = Vj.w;
       const bool hot = sig > (R)0;
       const R inv2s2 = hot ? (R)0.5 / (sig * sig) : (R)0;
@@ -40,7 +41,7 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
         const uint32_t i = rows[valid ? p : rs];
         const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
         R dx, dy, dz;
-        pair_dx<R>(Pi, Li, Pj, Lj, bx, dx, dy, dz);
+        pair_dx<R>(Pi, Li, Pj, Lj, bx.periodic, side, dx, dy, dz);
         const R d = sqrt_t(dist2_rn<R>(dx, dy, dz));
         const R g = overlap_g<R>(gtab, d, Pi.w, Pj.w);
         const R wx = Vi.x - Vj.x, wy = Vi.y - Vj.y, wz = Vi.z - Vj.z;
@@ -261,11 +262,11 @@ __device__ __forceinline__ R pair_probability(const typename Vec<R>::v4 &Pi, con
                                               const typename Vec<R>::v4 &Vi, uint32_t id_i,
                                               const typename Vec<R>::v4 &Pj, const typename Vec<R>::v4 &Lj,
                                               const typename Vec<R>::v4 &Vj, const typename Vec<R>::v4 &Kj,
-                                              uint32_t id_j, const BoxSplit &bx, const float4 *gtab, int n,
-                                              R inv_v0, R dt, unsigned long long step, uint32_t k0, uint32_t k1,
-                                              R &rx, R &ry, R &rz, R &vrel) {
+                                              uint32_t id_j, int periodic, const BoxSide &side, const float4 *gtab,
+                                              int n, R inv_v0, R dt, unsigned long long step, uint32_t k0,
+                                              uint32_t k1, R &rx, R &ry, R &rz, R &vrel) {
   R dx, dy, dz;
-  pair_dx<R>(Pi, Li, Pj, Lj, bx, dx, dy, dz);
+  pair_dx<R>(Pi, Li, Pj, Lj, periodic, side, dx, dy, dz);
   const R d = sqrt_t(dist2_rn<R>(dx, dy, dz));
   const R g = overlap_g<R>(gtab, d, Pi.w, Pj.w);
   const uint4 w = philox4x32_10(pair_counter(id_i, id_j, step), k0, k1);
@@ -320,14 +321,15 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
     }
     const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
     const uint32_t id_i = D.id[i];
+    const BoxSide side = bx.side(D.bid != nullptr ? (int)D.bid[i] : 0);
     U128 sum = {0ull, 0ull};
     float rmax = 0.0f;
     for (int64_t p = rs + lane; p < re; p += 32) {
       const uint32_t j = rows[p];
       const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
       R rx, ry, rz, vr;
-      const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx, gtab, rc.n, inv_v0, dt, a.step,
-                                      k0, k1, rx, ry, rz, vr);
+      const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx.periodic, side, gtab, rc.n, inv_v0,
+                                      dt, a.step, k0, k1, rx, ry, rz, vr);
       pcache[p] = P;
       sum = u128_add(sum, to_fixed(P));
       const R e = Kj.w;                                   // mu_j / (m_chi + mu_j)
@@ -374,8 +376,8 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
         const uint32_t j = rows[pstar];
         const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
         R rx, ry, rz, vr;
-        (void)pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx, gtab, rc.n, inv_v0, dt, a.step, k0,
-                                  k1, rx, ry, rz, vr);
+        (void)pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx.periodic, side, gtab, rc.n, inv_v0, dt,
+                                  a.step, k0, k1, rx, ry, rz, vr);
         const U128 hi = u128_add(base, to_fixed(pcache[pstar]));
         band = band || near_rel(T, base, hi) || near_rel(T, hi, hi);
         // isotropic new direction: cos(theta') = 2u - 1, phi' = 2 pi u'

@@ -16,20 +16,48 @@ __device__ __forceinline__ float axis_gap(float qa, float qb, float na, float nb
   return fmaxf(0.0f, fmaxf(na - qb, qa - nb));
 }
 
-// squared distance between two boxes (minimum image when periodic)
-__device__ __forceinline__ float box_gap2(const float qmn[3], const float qmx[3], const float4 &nmn, const float4 &nmx,
-                                          const BoxSplit &bx) {
+// squared distance between two boxes (minimum image when periodic, with the sides of up to two
+// boxes: a leaf of batched boxes can straddle two of them)
+__device__ __forceinline__ float box_gap2_one(const float qmn[3], const float qmx[3], const float4 &nmn,
+                                              const float4 &nmx, int periodic, const BoxSide &bs) {
   float d2 = 0.f;
   const float na[3] = {nmn.x, nmn.y, nmn.z}, nb[3] = {nmx.x, nmx.y, nmx.z};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     float gap = axis_gap(qmn[k], qmx[k], na[k], nb[k]);
-    if (bx.periodic) {
-      const float L = bx.Lhi[k];
+    if (periodic) {
+      const float L = bs.Lhi[k];
       gap = fminf(gap, fminf(axis_gap(qmn[k] + L, qmx[k] + L, na[k], nb[k]), axis_gap(qmn[k] - L, qmx[k] - L, na[k], nb[k])));
     }
     d2 += gap * gap;
   }
+  return d2;
+}
+
+struct LeafSides {
+  BoxSide a, b;
+  bool two;
+};
+
+__device__ __forceinline__ LeafSides leaf_sides(const BoxSplit &bx, const int2 *leaf_box, int leaf) {
+  LeafSides ls;
+  if (leaf_box != nullptr) {
+    const int2 r = leaf_box[leaf];
+    ls.a = bx.side(r.x);
+    ls.two = r.y != r.x;
+    ls.b = ls.two ? bx.side(r.y) : ls.a;
+  } else {
+    ls.a = bx.side(0);
+    ls.b = ls.a;
+    ls.two = false;
+  }
+  return ls;
+}
+
+__device__ __forceinline__ float box_gap2(const float qmn[3], const float qmx[3], const float4 &nmn, const float4 &nmx,
+                                          int periodic, const LeafSides &ls) {
+  float d2 = box_gap2_one(qmn, qmx, nmn, nmx, periodic, ls.a);
+  if (periodic && ls.two) d2 = fminf(d2, box_gap2_one(qmn, qmx, nmn, nmx, periodic, ls.b));
   return d2;
 }
 
@@ -53,12 +81,13 @@ k_leaf_pairs(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__res
     const int64_t lim = EMIT ? item_ptr[a + 1] - base : 0;
     if (qa.w >= 0.0f) {
       const float qmn[3] = {qa.x, qa.y, qa.z}, qmx[3] = {qb.x, qb.y, qb.z};
+      const LeafSides ls = leaf_sides(bx, Q.leaf_box, a);
       const int top = O.levels - 1;
       if (top == 0) {
         // a single leaf: test it directly
         const float4 nmn = O.bmin[O.off[0]], nmx = O.bmax[O.off[0]];
         const float r = qa.w + nmn.w + pad2;
-        if (nmn.w >= 0.0f && box_gap2(qmn, qmx, nmn, nmx, bx) < r * r) {
+        if (nmn.w >= 0.0f && box_gap2(qmn, qmx, nmn, nmx, bx.periodic, ls) < r * r) {
           if (EMIT && lane == 0 && lim > 0) items[base] = 0u;
           count = 1;
         }
@@ -78,7 +107,7 @@ k_leaf_pairs(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__res
           if (c < O.cnt[l - 1]) {
             const float4 nmn = O.bmin[O.off[l - 1] + c], nmx = O.bmax[O.off[l - 1] + c];
             const float r = qa.w + nmn.w + pad2;
-            pass = nmn.w >= 0.0f && box_gap2(qmn, qmx, nmn, nmx, bx) < r * r;
+            pass = nmn.w >= 0.0f && box_gap2(qmn, qmx, nmn, nmx, bx.periodic, ls) < r * r;
           }
           const unsigned m = __ballot_sync(DMB_FULL, pass);
           const int np = __popc(m);
@@ -134,9 +163,11 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
   typedef typename Vec<R>::v4 v4;
   __shared__ v4 sP[SR_WARPS][DMB_LEAF];
   __shared__ v4 sL[SR_WARPS][DMB_LEAF];
+  __shared__ uint16_t sB[SR_WARPS][DMB_LEAF];
   const int wib = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31u;
   const float pad2 = 2.0f * frame->pad;
+  const bool boxed = Q.bid != nullptr && O.bid != nullptr;
   unsigned long long st_tests = 0, st_leaves = 0;
   for (int64_t u = (int64_t)blockIdx.x * SR_WARPS + wib; u < n_units; u += (int64_t)gridDim.x * SR_WARPS) {
     const int a = (int)unit_leaf[u];
@@ -148,6 +179,9 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
     const float qmn[3] = {qa.x, qa.y, qa.z}, qmx[3] = {qb.x, qb.y, qb.z};
     v4 Pq = Vec<R>::make(0, 0, 0, 0), Lq = Vec<R>::make(0, 0, 0, 0);
     if (valid) { Pq = Q.P[qi]; Lq = Q.L[qi]; }
+    const LeafSides ls = leaf_sides(bx, Q.leaf_box, a);
+    const BoxSide side_q = (Q.bid != nullptr && valid) ? bx.side(Q.bid[qi]) : ls.a;
+    const uint16_t box_q = (boxed && valid) ? Q.bid[qi] : (uint16_t)0;
     uint32_t cnt = 0;
     int64_t out = 0, out_end = 0;
     if (EMIT && valid) {
@@ -163,11 +197,12 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
         const v4 Pk = O.P[base + lane], Lk = O.L[base + lane];
         sP[wib][lane] = Pk;
         sL[wib][lane] = Lk;
+        if (boxed) sB[wib][lane] = O.bid[base + lane];
         // float position (within a few float ulps of the span, covered by the pad)
         const float c[3] = {(float)Pk.x + (float)Lk.x, (float)Pk.y + (float)Lk.y, (float)Pk.z + (float)Lk.z};
         const float4 pmn = make_float4(c[0], c[1], c[2], 0.f), pmx = make_float4(c[0], c[1], c[2], 0.f);
         const float r = qa.w + (float)Pk.w + pad2;
-        keep = box_gap2(qmn, qmx, pmn, pmx, bx) < r * r;
+        keep = box_gap2(qmn, qmx, pmn, pmx, bx.periodic, ls) < r * r;
       }
       unsigned m = __ballot_sync(DMB_FULL, keep);
       __syncwarp();
@@ -178,8 +213,9 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
           const int k = __ffs(m) - 1;
           m &= m - 1;
           const v4 Pk = sP[wib][k], Lk = sL[wib][k];
+          if (boxed && sB[wib][k] != box_q) continue;     // pairs never join two boxes
           R dx, dy, dz;
-          pair_dx<R>(Pq, Lq, Pk, Lk, bx, dx, dy, dz);
+          pair_dx<R>(Pq, Lq, Pk, Lk, bx.periodic, side_q, dx, dy, dz);
           if (pair_test<R>(dist2_rn<R>(dx, dy, dz), Pq.w, Pk.w)) {
             if (EMIT) {
               if (out < out_end) rows[out] = (uint32_t)(base + k);

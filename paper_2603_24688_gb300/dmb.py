@@ -23,7 +23,7 @@ EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb
            "dmb_mc_scatter_dm", "dmb_step", "dmb_debug_overlap", "dmb_debug_rates", "dmb_debug_philox",
            "dmb_launch_count", "dmb_set_timing", "dmb_stage_times",
            "dmb_search_stats", "dmb_train_surrogate", "dmb_surrogate_params", "dmb_load_surrogate",
-           "dmb_surrogate_infer", "dmb_surrogate_grad", "dmb_surrogate_fallbacks"]
+           "dmb_surrogate_infer", "dmb_surrogate_grad", "dmb_surrogate_fallbacks", "dmb_step_batched"]
 
 
 class DmbError(RuntimeError):
@@ -36,6 +36,10 @@ class Params(ctypes.Structure):
     _fields_ = [("sigma0_cm2", ctypes.c_double), ("v0_kms", ctypes.c_double), ("n", ctypes.c_int32),
                 ("periodic", ctypes.c_int32), ("m_chi_mp", ctypes.c_double), ("box", ctypes.c_double * 3),
                 ("rate_mode", ctypes.c_int32), ("fp64", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class Box(ctypes.Structure):
+    _fields_ = [("box", ctypes.c_double * 3), ("sigma0_cm2", ctypes.c_double), ("m_chi_mp", ctypes.c_double)]
 
 
 class DM(ctypes.Structure):
@@ -83,6 +87,8 @@ def load(path=LIB_PATH):
         "dmb_surrogate_infer": ([vp, vp, i64, vp], c.c_int),
         "dmb_surrogate_grad": ([vp, vp, vp, c.c_int32, vp, c.POINTER(c.c_double)], c.c_int),
         "dmb_surrogate_fallbacks": ([vp, c.POINTER(i64)], c.c_int),
+        "dmb_step_batched": ([vp, c.POINTER(DM), vp, c.POINTER(Gas), vp, c.POINTER(Box), c.c_int32, u64, dbl,
+                              vp], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -205,6 +211,22 @@ class Context:
         sums = (ctypes.c_double * 16)()
         self._check(self.lib.dmb_step(self.h, ctypes.byref(d), ctypes.byref(g), int(step), float(dt),
                                       sums if want_sums else None))
+        return np.array(sums[:]) if want_sums else None
+
+    def dmb_step_batched(self, dm, dm_box, gas, gas_box, boxes, step, dt, want_sums=True):
+        """boxes: sequence of (box[3], sigma0_cm2, m_chi_mp); dm_box / gas_box: CUDA int32 tensors."""
+        import torch
+        d, g = self.dm_struct(dm), self.gas_struct(gas)
+        tbl = (Box * len(boxes))()
+        for k, (bx, sg, mc) in enumerate(boxes):
+            for c in range(3):
+                tbl[k].box[c] = float(bx[c])
+            tbl[k].sigma0_cm2 = float(sg)
+            tbl[k].m_chi_mp = float(mc)
+        sums = (ctypes.c_double * 16)()
+        self._check(self.lib.dmb_step_batched(self.h, ctypes.byref(d), _ptr(dm_box, torch.int32), ctypes.byref(g),
+                                              _ptr(gas_box, torch.int32), tbl, len(boxes), int(step), float(dt),
+                                              sums if want_sums else None))
         return np.array(sums[:]) if want_sums else None
 
     def dmb_debug_overlap(self, inp, out):

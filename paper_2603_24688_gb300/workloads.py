@@ -143,6 +143,37 @@ def galaxy_workload(n_dm=1_000_000, n_gas=1_000_000, M_halo=1e12, a=20.0, R_d=3.
     return dict(name=f"galaxy{n_dm}+{n_gas}", dm=dm, gas=gas, params=params, dt=float(dt))
 
 
+def boxes_workload(nbox=64, n_lo=2 ** 12, n_hi=2 ** 18, sigma_lo=1e-27, sigma_hi=1e-24, m_lo=0.5, m_hi=10.0,
+                   T_lo=1e3, T_hi=1e6, L=1.0, rho=1e10, sigma1d_dm=100.0, n=0, v0_kms=100.0, dt=1e-4,
+                   seed=SEED_BASE + 4):
+    """Many independent periodic boxes: particle counts per species, sigma0, m_chi and the gas
+    temperature drawn log-uniformly per box (the survey's parameter scan).  Returns the boxes'
+    particles concatenated (with per-particle box indices), the per-box parameters and each
+    box's own workload dict."""
+    rng = np.random.default_rng(seed)
+    lu = lambda a, b: float(np.exp(rng.uniform(np.log(a), np.log(b))))
+    per = []
+    for b in range(nbox):
+        nd = int(round(lu(n_lo, n_hi)))
+        ng = int(round(lu(n_lo, n_hi)))
+        w = box_workload(n_dm=nd, n_gas=ng, L=L, rho=rho, T_gas=lu(T_lo, T_hi), sigma1d_dm=sigma1d_dm,
+                         m_chi_mp=lu(m_lo, m_hi), sigma0_cm2=lu(sigma_lo, sigma_hi), n=n, v0_kms=v0_kms, dt=dt,
+                         seed=seed * 1000 + b)
+        per.append(w)
+    cat = lambda sp, k: np.concatenate([w[sp][k] for w in per])
+    dm = {k: cat("dm", k) for k in per[0]["dm"]}
+    gas = {k: cat("gas", k) for k in per[0]["gas"]}
+    # ids unique across boxes (the Philox streams key on ids)
+    dm["id"] = np.arange(len(dm["h"]), dtype=np.uint32)
+    gas["id"] = np.arange(len(gas["h"]), dtype=np.uint32)
+    dm_box = np.concatenate([np.full(len(w["dm"]["h"]), b, np.uint32) for b, w in enumerate(per)])
+    gas_box = np.concatenate([np.full(len(w["gas"]["h"]), b, np.uint32) for b, w in enumerate(per)])
+    boxes = [(tuple(w["params"]["box"]), w["params"]["sigma0_cm2"], w["params"]["m_chi_mp"]) for w in per]
+    params = _params(1e-24, n, 2.0, True, (L, L, L), seed, v0_kms)
+    return dict(name=f"boxes{nbox}", dm=dm, gas=gas, dm_box=dm_box, gas_box=gas_box, boxes=boxes, per_box=per,
+                params=params, dt=float(dt))
+
+
 def subsample(w, frac_or_n_dm, n_gas=None, seed=0):
     """A smaller workload with the same structure (random particle subsets)."""
     rng = np.random.default_rng(seed)
