@@ -233,6 +233,20 @@ dmb_status dmb_surrogate_grad(dmb_ctx *ctx, const float *X, const float *Y, int3
  * training box).  Synchronises. */
 dmb_status dmb_surrogate_fallbacks(dmb_ctx *ctx, int64_t *out);
 
+/* dmb_surrogate_grad without any device allocation (the paper has no counterpart: it is a
+ * service of this library).  dmb_surrogate_grad allocates its work buffers on every call; this
+ * variant is for callers that cannot call cudaMalloc/cudaFree at that point - inside CUDA-graph
+ * capture, under an external allocator that owns all device memory, or in loops where an
+ * allocation's implicit synchronisation is not acceptable.  Its work buffers live in one fixed
+ * device array of about 16 MB, reserved on every GPU that loads the library until the process
+ * exits, so B is limited to 4096 (larger B returns DMB_ERR_ARG).  Same arguments, results and
+ * kernels as dmb_surrogate_grad.  The first call on a device looks the array up (setup); make it
+ * before any stream capture.  All calls on a device share the array: calls whose work overlaps on
+ * the GPU (different streams or contexts without ordering) race and give wrong results.  When
+ * loss is non-NULL the call synchronises the context's stream. */
+dmb_status dmb_surrogate_grad_noalloc(dmb_ctx *ctx, const float *X, const float *Y, int32_t B, float *grad,
+                                      double *loss);
+
 /* Number of kernel launches the context has issued since creation (bench accounting). */
 int64_t dmb_launch_count(const dmb_ctx *ctx);
 

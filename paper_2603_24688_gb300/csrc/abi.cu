@@ -10,6 +10,7 @@
 #include <random>
 #include <vector>
 
+#include "internal.cuh"
 #include "mlp_host.cuh"
 #include "pairs.cuh"
 #include "sort_scan.cuh"
@@ -532,6 +533,16 @@ dmb_status check_gas(dmb_ctx *ctx, const dmb_gas *g) {
 }
 
 }  // namespace
+
+// ---- accessors for entry points defined in other translation units -----------------------
+bool dmb_internal_surrogate(dmb_ctx *ctx, MlpDev *dev, cudaStream_t *stream) {
+  if (!ctx || !ctx->mlp_ready) return false;
+  *dev = mlp_dev(ctx);
+  *stream = ctx->stream;
+  return true;
+}
+
+dmb_status dmb_internal_fail(dmb_ctx *ctx, dmb_status s, const char *msg) { return fail(ctx, s, msg); }
 
 // ======================================================================================
 extern "C" {

@@ -23,7 +23,8 @@ EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb
            "dmb_mc_scatter_dm", "dmb_step", "dmb_debug_overlap", "dmb_debug_rates", "dmb_debug_philox",
            "dmb_launch_count", "dmb_set_timing", "dmb_stage_times",
            "dmb_search_stats", "dmb_train_surrogate", "dmb_surrogate_params", "dmb_load_surrogate",
-           "dmb_surrogate_infer", "dmb_surrogate_grad", "dmb_surrogate_fallbacks", "dmb_step_batched"]
+           "dmb_surrogate_infer", "dmb_surrogate_grad", "dmb_surrogate_fallbacks", "dmb_step_batched",
+           "dmb_surrogate_grad_noalloc"]
 
 
 class DmbError(RuntimeError):
@@ -89,6 +90,7 @@ def load(path=LIB_PATH):
         "dmb_surrogate_fallbacks": ([vp, c.POINTER(i64)], c.c_int),
         "dmb_step_batched": ([vp, c.POINTER(DM), vp, c.POINTER(Gas), vp, c.POINTER(Box), c.c_int32, u64, dbl,
                               vp], c.c_int),
+        "dmb_surrogate_grad_noalloc": ([vp, vp, vp, c.c_int32, vp, c.POINTER(c.c_double)], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -272,6 +274,14 @@ class Context:
         loss = ctypes.c_double()
         self._check(self.lib.dmb_surrogate_grad(self.h, _ptr(X, torch.float32), _ptr(Y, torch.float32), X.shape[0],
                                                 _ptr(grad, torch.float32), ctypes.byref(loss)))
+        return loss.value
+
+    def dmb_surrogate_grad_noalloc(self, X, Y, grad):
+        """dmb_surrogate_grad with its work buffers in the library's fixed device array (B <= 4096)."""
+        import torch
+        loss = ctypes.c_double()
+        self._check(self.lib.dmb_surrogate_grad_noalloc(self.h, _ptr(X, torch.float32), _ptr(Y, torch.float32),
+                                                        X.shape[0], _ptr(grad, torch.float32), ctypes.byref(loss)))
         return loss.value
 
     def dmb_surrogate_fallbacks(self):
