@@ -183,13 +183,59 @@ dmb_status dmb_debug_rates(dmb_ctx *ctx, int64_t k, const double *in, double *ou
  * out: device [k][4] uint32 with key = params.seed. */
 dmb_status dmb_debug_philox(dmb_ctx *ctx, int64_t k, const uint32_t *ctr, uint32_t *out);
 
+/* ---- hierarchical substeps (power-of-two timestep bins) ----------------------------------
+ * Sec. 2.4 limits each DM particle's timestep by the scatter probability (Eq. prob_criterion);
+ * with power-of-two timesteps a particle in bin b has dt = 2^b dt_min and is active at substep
+ * s when s mod 2^b == 0.  At a substep the active gas particles receive the mean field (Eqs.
+ * gas-dVdt, gas-dTdt) of ALL their DM partners and are kicked with their own dt; the active DM
+ * particles draw the Monte Carlo (Eqs. dm-update-vels, dm-update-prob, scatter_chi) against ALL
+ * their gas partners with their own dt (Philox step = s); every other particle is unchanged.
+ * Positions do not change across substeps (drift is not part of the interaction step), so the
+ * grid and pairs of dmb_build_grid + dmb_neighbors serve every substep.
+ *
+ * dmb_set_bins: set-up after dmb_neighbors (synchronises).  dm_bin, gas_bin: device uint8 [n]
+ * in caller order, values 0..63 (DMB_ERR_ARG otherwise).  The arrays must stay valid and
+ * unchanged while substeps run.  Orders each species by (bin, sorted index) so that every
+ * substep's active set is a prefix of it, and allocates all substep scratch.  Single-box
+ * contexts only.  A later dmb_build_grid, dmb_neighbors or dmb_step invalidates it. */
+dmb_status dmb_set_bins(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas_bin);
+
+/* Host-side sizes of substep s (no GPU work): out5 = {active DM, active gas, mean-field row
+ * segments, pairs of the active gas rows, pairs of the active DM rows}. */
+dmb_status dmb_substep_info(dmb_ctx *ctx, uint64_t substep, int64_t *out5);
+
+/* One substep s with dt_min (see above).  dm, gas: the same particles (and arrays) as the
+ * grid was built from; updates dm->vel, gas->vel and gas->T in place (device) and keeps the
+ * library's sorted copies of the updated particles current.  Between substeps the caller
+ * changes the particle state only through dmb_substep (otherwise: dmb_build_grid again).
+ * Stream-ordered, no allocation, no host synchronisation unless sums_out (host, 16 doubles,
+ * as dmb_step with [12] = half the pair evaluations of the substep) is given.
+ * With dmb_set_graph(ctx, 1) each distinct active set is captured once into a CUDA graph
+ * (on a stream of the library's, ordered after the context stream by events) and replayed;
+ * the results are the same as without graphs. */
+dmb_status dmb_substep(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t substep,
+                       double dt_min, double *sums_out);
+
+/* on = 1: dmb_substep replays captured CUDA graphs; 0: launches directly. */
+dmb_status dmb_set_graph(dmb_ctx *ctx, int on);
+
+/* Engine of the surrogate's pair pass: 0 (default) 128-pair tiles on the tcgen05 tensor cores
+ * with the accumulators in tensor memory; 1 the warp-level mma.sync pass (kept for
+ * comparison).  Both evaluate the same network; captured substep graphs are dropped. */
+dmb_status dmb_set_surrogate_engine(dmb_ctx *ctx, int32_t engine);
+
+/* Raw outputs of the network for n input rows on the tcgen05 engine (same contract as
+ * dmb_surrogate_infer; synchronises to report a timed-out tensor-core wait as DMB_ERR_TIMEOUT). */
+dmb_status dmb_surrogate_infer_tc(dmb_ctx *ctx, const float *X, int64_t n, float *Y);
+
 /* Stage timing of dmb_step with CUDA events recorded on the context stream (adds one
  * event synchronisation per step).  on = 0 disables it.  Resets the accumulators. */
 dmb_status dmb_set_timing(dmb_ctx *ctx, int on);
 
 /* Accumulated stage times since dmb_set_timing or the last call, in ms (host [8]):
  * [0] grid (frame, keys, sort, gather, tree)  [1] pair search (count, scan, emit, both
- * directions)  [2] mean field  [3] Monte Carlo  [4] kicks and sums  [5..7] 0.
+ * directions)  [2] mean field  [3] Monte Carlo  [4] kicks and sums  [5] the surrogate's pair
+ * pass (part of [2]; 0 for the other rate providers)  [6..7] 0.
  * steps_out (host, may be NULL): steps timed.  Resets the accumulators. */
 dmb_status dmb_stage_times(dmb_ctx *ctx, double *ms_out, int64_t *steps_out);
 

@@ -10,8 +10,10 @@
 #include <random>
 #include <vector>
 
+#include "active.cuh"
 #include "internal.cuh"
 #include "mlp_host.cuh"
+#include "mlp_tc.cuh"
 #include "pairs.cuh"
 #include "sort_scan.cuh"
 #include "step.cuh"
@@ -62,6 +64,8 @@ struct dmb_ctx {
   // learned surrogate of the rate integrals
   DevBuf mlp_p, mlp_m, mlp_v, mlp_w2, mlp_w3, mlp_w2t, mlp_w3t, mlp_fallback, mlp_rates;
   bool mlp_ready = false;
+  int mlp_engine = 0;            // 0: tcgen05 tiles (mlp_tc.cu), 1: warp-level mma.sync pass
+  DevBuf tc_tiles;               // first row of every 128-pair tile
   // batched boxes (dmb_step_batched): caller box index arrays of the current build and tables
   const uint32_t *dm_box = nullptr, *gas_box = nullptr;
   int nbox = 0;
@@ -79,9 +83,34 @@ struct dmb_ctx {
   bool grid_ready = false, pairs_ready = false;
   int64_t n_pairs = 0;
   const double *dm_vel = nullptr;   // caller DM velocities of the last build
+  // hierarchical substeps (dmb_set_bins, dmb_substep): species lists ordered by (bin, sorted
+  // index), the segment table of the gas list, and per bin boundary b (the active set of bins < b):
+  // tab[0] DM count, tab[1] gas count, tab[2] gas segments, tab[3] pairs of the gas rows,
+  // tab[4] pairs of the DM rows
+  DevBuf act_dm, act_gas, act_start, act_seg_ptr, act_seg_row, act_seg_begin, act_len, act_segs, act_gpairs,
+      act_dpairs, act_pick, step_dev, bin_keys, bin_keys1, bin_vals1;
+  const uint8_t *dm_bin = nullptr, *gas_bin = nullptr;
+  bool bins_ready = false;
+  int64_t bin_tab[5][DMB_NBINS + 1];
+  int64_t act_seg_total = 0;
+  // CUDA graphs of substeps, one per (active-set boundary, dt, caller arrays)
+  struct GraphEntry {
+    int lim;
+    double dt;
+    const void *key[6];
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  bool use_graph = false;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_next_step = ~0ull;   // device step counter value, when known
   // optional stage timing with CUDA events on the context stream
   bool timing = false;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t sev[2] = {nullptr, nullptr};   // around the surrogate's pair pass (stage [5])
+  bool sev_pending = false;
   double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int64_t timed_steps = 0;
 };
@@ -151,6 +180,18 @@ SpeciesView<R> view(const SpeciesBufs &s, bool batched = false) {
   return v;
 }
 
+void clear_graphs(dmb_ctx *ctx) {
+  for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
+  ctx->graph_next_step = ~0ull;
+}
+
+// the grid or the pair lists change: substep tables and captured graphs are stale
+void invalidate_substeps(dmb_ctx *ctx) {
+  ctx->bins_ready = false;
+  clear_graphs(ctx);
+}
+
 dmb_status ensure_species(dmb_ctx *ctx, SpeciesBufs &s, int64_t n, bool gas) {
   const size_t v4b = ctx->p.fp64 ? 32 : 16;
   s.n = n;
@@ -184,7 +225,8 @@ dmb_status check_status(dmb_ctx *ctx) {
   if (st & DMB_BAD_PERIODIC) m += " periodic box smaller than 2 (max h_dm + max h_gas);";
   if (st & DMB_BAD_DOMAIN) m += " rate provider outside its domain;";
   if (st & DMB_BAD_OVERFLOW) m += " internal list overflow;";
-  return fail(ctx, (st & DMB_BAD_DOMAIN) ? DMB_ERR_DOMAIN : DMB_ERR_ARG, m);
+  if (st & DMB_BAD_TIMEOUT) m += " a tensor-core wait timed out;";
+  return fail(ctx, (st & DMB_BAD_TIMEOUT) ? DMB_ERR_TIMEOUT : (st & DMB_BAD_DOMAIN) ? DMB_ERR_DOMAIN : DMB_ERR_ARG, m);
 }
 
 // ---- build_grid ------------------------------------------------------------------------
@@ -193,6 +235,7 @@ dmb_status build_grid_impl(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
   cudaStream_t s = ctx->stream;
   int64_t *L = &ctx->launches;
   dmb_status st;
+  invalidate_substeps(ctx);
   if ((st = ensure_species(ctx, ctx->dm, dm->n, false)) != DMB_OK) return st;
   if ((st = ensure_species(ctx, ctx->gas, gas->n, true)) != DMB_OK) return st;
   if ((st = ensure_sort_scratch(ctx, dm->n > gas->n ? dm->n : gas->n)) != DMB_OK) return st;
@@ -364,6 +407,7 @@ dmb_status neighbors_impl(dmb_ctx *ctx) {
   const SpeciesView<R> D = view<R>(ctx->dm, ctx->nbox > 0), G = view<R>(ctx->gas, ctx->nbox > 0);
   const int64_t nmax = D.n > G.n ? D.n : G.n;
   dmb_status st;
+  invalidate_substeps(ctx);
   if ((st = ensure_sort_scratch(ctx, nmax + 1)) != DMB_OK) return st;
   unsigned long long *sst = ptr<unsigned long long>(ctx->search_stats);
   CK(cudaMemsetAsync(sst, 0, 16 * 8, s), "stats reset");
@@ -449,6 +493,41 @@ MlpRun mlp_run(dmb_ctx *ctx) {
   return r;
 }
 
+// Surrogate rates of the gas-major pairs in processing order q < n_q: rows k < n_rows of the
+// prefix R_ptr (gas list[k], or gas k without a list); sv is the same rows' segment view.
+dmb_status surrogate_rates(dmb_ctx *ctx, const MlpRun &mr, const SegView &sv, const int64_t *R_ptr, int64_t n_rows,
+                           const uint32_t *list, int64_t n_q) {
+  if (n_q <= 0 || n_rows <= 0) return DMB_OK;
+  cudaStream_t s = ctx->stream;
+  if (ctx->mlp_engine == 0) {
+    TcArgs a = {};
+    a.p = mr.p;
+    a.w2 = mr.w2;
+    a.w3 = mr.w3;
+    a.n = n_q;
+    a.R_ptr = R_ptr;
+    a.n_rows = n_rows;
+    a.list = list;
+    a.row_ptr = ptr<int64_t>(ctx->sg.row_ptr);
+    a.rows = ptr<uint32_t>(ctx->sg.rows);
+    a.G_V = ptr<float4>(ctx->gas.V);
+    a.D_V = ptr<float4>(ctx->dm.V);
+    a.dom = mr.dom;
+    a.rc = ctx->rc;
+    a.rates = ptr<float2>(ctx->mlp_rates);
+    a.fallback_count = mr.fallback_count;
+    a.status = ptr<uint32_t>(ctx->status);
+    if (!ensure(ctx->tc_tiles, (size_t)((n_q + 127) / 128) * 8)) return fail(ctx, DMB_ERR_OOM, "surrogate tiles");
+    CK(mlp_tc_pair_rates(a, ptr<int64_t>(ctx->tc_tiles), s, &ctx->launches), "surrogate rates (tensor cores)");
+  } else {
+    CK(launch_mlp_pair_rates(view<float>(ctx->gas, ctx->nbox > 0), view<float>(ctx->dm, ctx->nbox > 0),
+                             ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv,
+                             sv.n_seg >= 0 ? sv.n_seg : ctx->n_seg_max, ctx->rc, mr, ptr<float2>(ctx->mlp_rates), s,
+                             &ctx->launches), "surrogate rates");
+  }
+  return DMB_OK;
+}
+
 template <typename R>
 dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp) {
   const SpeciesView<R> D = view<R>(ctx->dm, ctx->nbox > 0), G = view<R>(ctx->gas, ctx->nbox > 0);
@@ -471,11 +550,16 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
     CK(cudaMemsetAsync(ctx->mlp_fallback.p, 0, 8, ctx->stream), "memset");
     if (!ensure(ctx->mlp_rates, (size_t)ctx->sg.n_pairs * 8 + 8)) return fail(ctx, DMB_ERR_OOM, "surrogate rates");
     mr.rates = ptr<float2>(ctx->mlp_rates);
-    if (sizeof(R) == 4)
-      CK(launch_mlp_pair_rates(view<float>(ctx->gas, ctx->nbox > 0), view<float>(ctx->dm, ctx->nbox > 0),
-                               ptr<int64_t>(ctx->sg.row_ptr),
-                               ptr<uint32_t>(ctx->sg.rows), sv, ctx->n_seg_max, ctx->rc, mr,
-                               ptr<float2>(ctx->mlp_rates), ctx->stream, &ctx->launches), "surrogate rates");
+    if (sizeof(R) == 4) {
+      if (ctx->timing) CK(cudaEventRecord(ctx->sev[0], ctx->stream), "event");
+      const dmb_status st = surrogate_rates(ctx, mr, sv, ptr<int64_t>(ctx->sg.row_ptr), ctx->gas.n, nullptr,
+                                            ctx->sg.n_pairs);
+      if (st != DMB_OK) return st;
+      if (ctx->timing) {
+        CK(cudaEventRecord(ctx->sev[1], ctx->stream), "event");
+        ctx->sev_pending = true;
+      }
+    }
   }
   CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv,
                          ctx->n_seg_max, ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr, ctx->stream,
@@ -529,6 +613,223 @@ dmb_status check_gas(dmb_ctx *ctx, const dmb_gas *g) {
   if (g->n < 0 || g->n > 0x7fffffffLL) return fail(ctx, DMB_ERR_ARG, "gas->n out of range");
   if (g->n > 0 && (!g->pos || !g->vel || !g->mass || !g->h || !g->T || !g->mu || !g->id))
     return fail(ctx, DMB_ERR_ARG, "gas has a NULL array");
+  return DMB_OK;
+}
+
+// ---- hierarchical substeps -------------------------------------------------------------------
+int substep_lim(uint64_t substep) {   // active bins are b < lim: s mod 2^b == 0
+  if (substep == 0) return DMB_NBINS;
+  const int nu = __builtin_ctzll(substep);
+  return nu + 1 < DMB_NBINS ? nu + 1 : DMB_NBINS;
+}
+
+template <typename R>
+dmb_status set_bins_impl(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas_bin) {
+  cudaStream_t s = ctx->stream;
+  int64_t *L = &ctx->launches;
+  const int64_t nd = ctx->dm.n, ng = ctx->gas.n, nmax = nd > ng ? nd : ng;
+  dmb_status st;
+  if ((st = ensure_sort_scratch(ctx, nmax + 1)) != DMB_OK) return st;
+  bool ok = ensure(ctx->bin_keys, (size_t)nmax * 8) && ensure(ctx->bin_keys1, (size_t)nmax * 8) &&
+            ensure(ctx->bin_vals1, (size_t)nmax * 4) && ensure(ctx->act_dm, (size_t)nd * 4) &&
+            ensure(ctx->act_gas, (size_t)ng * 4) && ensure(ctx->act_start, 2 * (DMB_NBINS + 1) * 8) &&
+            ensure(ctx->act_len, (size_t)nmax * 4) && ensure(ctx->act_segs, (size_t)ng * 4) &&
+            ensure(ctx->act_seg_ptr, (size_t)(ng + 1) * 8) && ensure(ctx->act_gpairs, (size_t)(ng + 1) * 8) &&
+            ensure(ctx->act_dpairs, (size_t)(nd + 1) * 8) && ensure(ctx->act_pick, 3 * (DMB_NBINS + 1) * 8) &&
+            ensure(ctx->step_dev, 8);
+  if (!ok) return fail(ctx, DMB_ERR_OOM, "device allocation failed for the substep tables");
+  int64_t *start = ptr<int64_t>(ctx->act_start);
+  const uint8_t *bins[2] = {dm_bin, gas_bin};
+  DevBuf *lists[2] = {&ctx->act_dm, &ctx->act_gas};
+  const SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};
+  for (int k = 0; k < 2; ++k) {
+    const int64_t n = sp[k]->n;
+    if (n > 0) {
+      // stable sort of the sorted indices by bin: within a bin the Morton order is kept
+      CK(launch_bin_keys(bins[k], ptr<uint32_t>(sp[k]->vals0), n, ptr<uint64_t>(ctx->bin_keys),
+                         ptr<uint32_t>(*lists[k]), ptr<uint32_t>(ctx->status), s, L), "bin keys");
+      CK(radix_sort_pairs(ptr<uint64_t>(ctx->bin_keys), ptr<uint32_t>(*lists[k]), ptr<uint64_t>(ctx->bin_keys1),
+                          ptr<uint32_t>(ctx->bin_vals1), n, 8, ptr<uint32_t>(ctx->hist), ptr<int64_t>(ctx->hist_scan),
+                          ptr<int64_t>(ctx->scan_tmp), s, L), "bin sort");
+    }
+    CK(launch_bin_bounds(ptr<uint64_t>(ctx->bin_keys), n, start + k * (DMB_NBINS + 1), s, L), "bin bounds");
+  }
+  // gas rows: pairs and segments in list order; DM rows: pairs in list order
+  CK(launch_list_counts(ptr<uint32_t>(ctx->act_gas), ng, ptr<int64_t>(ctx->sg.row_ptr), MF_SEG,
+                        ptr<uint32_t>(ctx->act_len), ptr<uint32_t>(ctx->act_segs), s, L), "list counts");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(ctx->act_segs), ptr<int64_t>(ctx->act_seg_ptr), ng,
+                            ptr<int64_t>(ctx->scan_tmp), s, L), "scan");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(ctx->act_len), ptr<int64_t>(ctx->act_gpairs), ng,
+                            ptr<int64_t>(ctx->scan_tmp), s, L), "scan");
+  CK(launch_list_counts(ptr<uint32_t>(ctx->act_dm), nd, ptr<int64_t>(ctx->sd.row_ptr), 0,
+                        ptr<uint32_t>(ctx->act_len), nullptr, s, L), "list counts");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(ctx->act_len), ptr<int64_t>(ctx->act_dpairs), nd,
+                            ptr<int64_t>(ctx->scan_tmp), s, L), "scan");
+  int64_t *pick = ptr<int64_t>(ctx->act_pick);
+  CK(launch_pick(ptr<int64_t>(ctx->act_seg_ptr), start + (DMB_NBINS + 1), pick, s, L), "pick");
+  CK(launch_pick(ptr<int64_t>(ctx->act_gpairs), start + (DMB_NBINS + 1), pick + (DMB_NBINS + 1), s, L), "pick");
+  CK(launch_pick(ptr<int64_t>(ctx->act_dpairs), start, pick + 2 * (DMB_NBINS + 1), s, L), "pick");
+  CK(cudaMemcpyAsync(&ctx->bin_tab[0][0], start, 2 * (DMB_NBINS + 1) * 8, cudaMemcpyDeviceToHost, s), "readback");
+  CK(cudaMemcpyAsync(&ctx->bin_tab[2][0], pick, 3 * (DMB_NBINS + 1) * 8, cudaMemcpyDeviceToHost, s), "readback");
+  if ((st = check_status(ctx)) != DMB_OK) return st;
+  ctx->act_seg_total = ctx->bin_tab[2][DMB_NBINS];
+  if (!ensure(ctx->act_seg_row, (size_t)ctx->act_seg_total * 4) ||
+      !ensure(ctx->act_seg_begin, (size_t)ctx->act_seg_total * 8))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for the substep segments");
+  CK(launch_list_seg_map(ptr<uint32_t>(ctx->act_gas), ng, ptr<int64_t>(ctx->sg.row_ptr),
+                         ptr<int64_t>(ctx->act_seg_ptr), MF_SEG, ptr<uint32_t>(ctx->act_seg_row),
+                         ptr<int64_t>(ctx->act_seg_begin), s, L), "segment map");
+  // every buffer a substep touches, at its largest size: a substep (and its capture) allocates nothing
+  ok = ensure(ctx->mf_part, (size_t)ctx->act_seg_total * 6 * sizeof(R)) && ensure(ctx->mf_acc, (size_t)ng * 24) &&
+       ensure(ctx->mf_dudt, (size_t)ng * 8) && ensure(ctx->e_exp, (size_t)ng * 8) &&
+       ensure(ctx->mc_rec, (size_t)nd * sizeof(McRec)) && ensure(ctx->mc_blocks, (size_t)mc_blocks_for(nd) * 8 * 8) &&
+       ensure(ctx->mc_max, (size_t)mc_blocks_for(nd) * 8) && ensure(ctx->kick_blocks, (size_t)152 * 4 * KICK_NSUM * 8);
+  if (ok && ctx->rc.rate_mode == DMB_RATE_MLP)
+    ok = ensure_mlp(ctx) == DMB_OK && ensure(ctx->mlp_rates, (size_t)ctx->sg.n_pairs * 8 + 8);
+  if (!ok) return fail(ctx, DMB_ERR_OOM, "device allocation failed for substep scratch");
+  if (ctx->rc.rate_mode == DMB_RATE_MLP) {
+    CK(prepare_mlp_pair_rates(), "surrogate kernel attributes");
+    CK(mlp_tc_prepare(), "surrogate kernel attributes");
+    if (!ensure(ctx->tc_tiles, (size_t)((ctx->bin_tab[3][DMB_NBINS] + 127) / 128) * 8 + 8))
+      return fail(ctx, DMB_ERR_OOM, "surrogate tiles");
+  }
+  CK(cudaStreamSynchronize(s), "synchronise");
+  ctx->dm_bin = dm_bin;
+  ctx->gas_bin = gas_bin;
+  ctx->bins_ready = true;
+  return DMB_OK;
+}
+
+// The launches of one substep (no allocation, no host synchronisation: capturable).
+template <typename R>
+dmb_status substep_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int lim, uint64_t substep,
+                        double dt_min, bool step_on_device) {
+  cudaStream_t s = ctx->stream;
+  int64_t *L = &ctx->launches;
+  const SpeciesView<R> D = view<R>(ctx->dm), G = view<R>(ctx->gas);
+  const int64_t nda = ctx->bin_tab[0][lim], nga = ctx->bin_tab[1][lim], nseg = ctx->bin_tab[2][lim];
+  const double pair_evals = 0.5 * (double)(ctx->bin_tab[3][lim] + ctx->bin_tab[4][lim]);
+  // mean field of the active gas rows against all their DM partners
+  SegView sv;
+  sv.seg_ptr = ptr<int64_t>(ctx->act_seg_ptr);
+  sv.seg_row = ptr<uint32_t>(ctx->act_seg_row);
+  sv.seg_begin = ptr<int64_t>(ctx->act_seg_begin);
+  sv.list = ptr<uint32_t>(ctx->act_gas);
+  sv.n_rows = nga;
+  sv.n_seg = nseg;
+  MfOut o;
+  o.acc = ptr<double>(ctx->mf_acc);
+  o.dudt = ptr<double>(ctx->mf_dudt);
+  o.e_exp = ptr<double>(ctx->e_exp);
+  MlpRun mr = {};
+  if (ctx->rc.rate_mode == DMB_RATE_MLP) {
+    mr = mlp_run(ctx);
+    mr.rates = ptr<float2>(ctx->mlp_rates);
+    CK(cudaMemsetAsync(ctx->mlp_fallback.p, 0, 8, s), "memset");
+    if (sizeof(R) == 4 && nseg > 0) {
+      const dmb_status st = surrogate_rates(ctx, mr, sv, ptr<int64_t>(ctx->act_gpairs), nga,
+                                            ptr<uint32_t>(ctx->act_gas), ctx->bin_tab[3][lim]);
+      if (st != DMB_OK) return st;
+    }
+  }
+  if (nga > 0)
+    CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv, nseg,
+                           ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr, s, L), "meanfield");
+  // Monte Carlo of the active DM against all their gas partners, each with its own dt
+  const int nb = mc_blocks_for(nda);
+  McArgs a;
+  a.dt = dt_min;
+  a.step = substep;
+  a.seed = ctx->p.seed;
+  a.id_bits = 32;
+  a.vel_in = dm->vel;
+  a.vel_out = const_cast<double *>(dm->vel);
+  a.scattered = nullptr;
+  a.partner = nullptr;
+  a.p_ratio = nullptr;
+  a.p_total = nullptr;
+  a.block_sums = ptr<double>(ctx->mc_blocks);
+  a.block_max = ptr<double>(ctx->mc_max);
+  a.list = ptr<uint32_t>(ctx->act_dm);
+  a.n_list = nda;
+  a.bin = ctx->dm_bin;
+  a.step_dev = step_on_device ? ptr<unsigned long long>(ctx->step_dev) : nullptr;
+  a.v_sorted = ctx->dm.V.p;
+  a.v_sorted_fp64 = ctx->p.fp64 ? 1 : 0;
+  if (nda > 0)
+    CK(launch_mc<R>(D, G, ctx->bx, ptr<int64_t>(ctx->sd.row_ptr), ptr<uint32_t>(ctx->sd.rows),
+                    ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), ptr<McRec>(ctx->mc_rec), nb, s, L), "mc");
+  // kick of the active gas (refreshing its sorted copies) and the sums
+  const int kb = 152 * 4;
+  CK(launch_kick_gas_list<R>(const_cast<double *>(gas->vel), const_cast<double *>(gas->T), gas->mu, gas->mass,
+                             ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp),
+                             ptr<uint32_t>(ctx->act_gas), nga, G.perm, ctx->gas_bin, dt_min, ctx->rc,
+                             ptr<typename Vec<R>::v4>(ctx->gas.V), ptr<typename Vec<R>::v4>(ctx->gas.K),
+                             ptr<double>(ctx->kick_blocks), kb, s, L), "kick");
+  CK(launch_final_sums(ptr<double>(ctx->mc_blocks), ptr<double>(ctx->mc_max), nda > 0 ? nb : 0,
+                       ptr<double>(ctx->kick_blocks), kb, dt_min, pair_evals, ptr<double>(ctx->sums), s, L), "sums");
+  return DMB_OK;
+}
+
+dmb_status substep_graph(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int lim, uint64_t substep,
+                         double dt_min) {
+  if (!ctx->gstream) {
+    CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking), "graph stream");
+    for (int k = 0; k < 2; ++k) CK(cudaEventCreateWithFlags(&ctx->gev[k], cudaEventDisableTiming), "graph event");
+  }
+  const void *key[6] = {dm->vel, gas->vel, gas->T, gas->mu, gas->mass, ctx->dm_bin};
+  dmb_ctx::GraphEntry *ent = nullptr;
+  for (auto &g : ctx->graphs)
+    if (g.lim == lim && g.dt == dt_min && memcmp(g.key, key, sizeof(key)) == 0) ent = &g;
+  if (!ent) {
+    // capture the substep's launches on the context's own stream; the graph ends by advancing
+    // the device step counter, so consecutive substeps need no host write
+    cudaStream_t saved = ctx->stream;
+    const int64_t l0 = ctx->launches;
+    ctx->stream = ctx->gstream;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
+    dmb_status st = DMB_ERR_CUDA;
+    if (e == cudaSuccess) {
+      st = ctx->p.fp64 ? substep_body<double>(ctx, dm, gas, lim, substep, dt_min, true)
+                       : substep_body<float>(ctx, dm, gas, lim, substep, dt_min, true);
+      if (st == DMB_OK) {
+        const cudaError_t ei = launch_step_advance(ptr<unsigned long long>(ctx->step_dev), ctx->gstream, &ctx->launches);
+        if (ei != cudaSuccess) st = cuda_fail(ctx, ei, "step counter");
+      }
+      const cudaError_t e2 = cudaStreamEndCapture(ctx->gstream, &g);
+      if (st == DMB_OK && e2 != cudaSuccess) st = cuda_fail(ctx, e2, "graph capture");
+    } else {
+      st = cuda_fail(ctx, e, "graph capture");
+    }
+    ctx->stream = saved;
+    const int64_t nl = ctx->launches - l0;
+    ctx->launches = l0;
+    if (st != DMB_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    dmb_ctx::GraphEntry ne;
+    ne.lim = lim;
+    ne.dt = dt_min;
+    memcpy(ne.key, key, sizeof(key));
+    ne.launches = nl;
+    e = cudaGraphInstantiate(&ne.exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(e, "graph instantiate");
+    ctx->graphs.push_back(ne);
+    ent = &ctx->graphs.back();
+  }
+  CK(cudaEventRecord(ctx->gev[0], ctx->stream), "event");
+  CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0), "event wait");
+  if (ctx->graph_next_step != substep) {
+    CK(launch_step_set(ptr<unsigned long long>(ctx->step_dev), substep, ctx->gstream, &ctx->launches), "step counter");
+  }
+  CK(cudaGraphLaunch(ent->exec, ctx->gstream), "graph launch");
+  ctx->launches += ent->launches;
+  ctx->graph_next_step = substep + 1;
+  CK(cudaEventRecord(ctx->gev[1], ctx->gstream), "event");
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->gev[1], 0), "event wait");
   return DMB_OK;
 }
 
@@ -609,6 +910,11 @@ dmb_status dmb_create(dmb_ctx **out, const dmb_params *p, void *cuda_stream) {
 dmb_status dmb_destroy(dmb_ctx *ctx) {
   if (!ctx) return DMB_OK;
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  if (ctx->gstream) cudaStreamSynchronize(ctx->gstream);
+  clear_graphs(ctx);
+  for (int k = 0; k < 2; ++k)
+    if (ctx->gev[k]) cudaEventDestroy(ctx->gev[k]);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   for (SearchBufs *sb : {&ctx->sg, &ctx->sd}) {
     DevBuf *q[] = {&sb->item_cnt, &sb->item_ptr, &sb->items, &sb->unit_cnt_leaf, &sb->unit_ptr, &sb->unit_leaf,
                    &sb->unit_item0, &sb->unit_cnt, &sb->counts, &sb->row_ptr, &sb->rows};
@@ -619,7 +925,10 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
                     &ctx->seg_row, &ctx->seg_begin, &ctx->t_cursor, &ctx->mlp_p, &ctx->mlp_m, &ctx->mlp_v,
                     &ctx->mlp_w2, &ctx->mlp_w3, &ctx->mlp_w2t, &ctx->mlp_w3t, &ctx->mlp_fallback, &ctx->mlp_rates,
                     &ctx->box_sides, &ctx->box_params, &ctx->mf_acc, &ctx->mf_dudt, &ctx->e_exp, &ctx->mc_blocks, &ctx->mc_max,
-                    &ctx->kick_blocks, &ctx->sums, &ctx->scratch_vel, &ctx->search_stats};
+                    &ctx->kick_blocks, &ctx->sums, &ctx->scratch_vel, &ctx->search_stats, &ctx->act_dm,
+                    &ctx->act_gas, &ctx->act_start, &ctx->act_seg_ptr, &ctx->act_seg_row, &ctx->act_seg_begin,
+                    &ctx->act_len, &ctx->act_segs, &ctx->act_gpairs, &ctx->act_dpairs, &ctx->act_pick,
+                    &ctx->step_dev, &ctx->bin_keys, &ctx->bin_keys1, &ctx->bin_vals1, &ctx->tc_tiles};
   for (DevBuf *b : bufs) release(*b);
   SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};
   for (SpeciesBufs *s : sp) {
@@ -632,6 +941,8 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
   if (ctx->h_sums) cudaFreeHost(ctx->h_sums);
   for (int k = 0; k < 6; ++k)
     if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+  for (int k = 0; k < 2; ++k)
+    if (ctx->sev[k]) cudaEventDestroy(ctx->sev[k]);
   delete ctx;
   return DMB_OK;
 }
@@ -792,6 +1103,12 @@ static dmb_status step_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, 
       CK(cudaEventElapsedTime(&ms, ctx->ev[k], ctx->ev[k + 1]), "event time");
       ctx->stage_ms[k] += ms;
     }
+    if (ctx->sev_pending) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, ctx->sev[0], ctx->sev[1]), "event time");
+      ctx->stage_ms[5] += ms;
+      ctx->sev_pending = false;
+    }
     ctx->timed_steps += 1;
   }
   if (sums_out) {
@@ -802,10 +1119,66 @@ static dmb_status step_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, 
   return DMB_OK;
 }
 
+dmb_status dmb_set_bins(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas_bin) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!ctx->pairs_ready) return fail(ctx, DMB_ERR_STATE, "dmb_set_bins before dmb_neighbors");
+  if (ctx->nbox > 0) return fail(ctx, DMB_ERR_ARG, "substeps run on a single box");
+  if ((ctx->dm.n > 0 && !dm_bin) || (ctx->gas.n > 0 && !gas_bin)) return fail(ctx, DMB_ERR_ARG, "bin array is NULL");
+  invalidate_substeps(ctx);
+  return ctx->p.fp64 ? set_bins_impl<double>(ctx, dm_bin, gas_bin) : set_bins_impl<float>(ctx, dm_bin, gas_bin);
+}
+
+dmb_status dmb_substep_info(dmb_ctx *ctx, uint64_t substep, int64_t *out5) {
+  if (!ctx || !out5) return fail(ctx, DMB_ERR_ARG, "NULL argument");
+  if (!ctx->bins_ready) return fail(ctx, DMB_ERR_STATE, "dmb_substep_info before dmb_set_bins");
+  const int lim = substep_lim(substep);
+  for (int k = 0; k < 5; ++k) out5[k] = ctx->bin_tab[k][lim];
+  return DMB_OK;
+}
+
+dmb_status dmb_set_graph(dmb_ctx *ctx, int on) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  ctx->use_graph = on != 0;
+  return DMB_OK;
+}
+
+dmb_status dmb_substep(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t substep, double dt_min,
+                       double *sums_out) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!ctx->bins_ready) return fail(ctx, DMB_ERR_STATE, "dmb_substep before dmb_set_bins");
+  dmb_status st;
+  if ((st = check_dm(ctx, dm)) != DMB_OK || (st = check_gas(ctx, gas)) != DMB_OK) return st;
+  if (dm->n != ctx->dm.n || gas->n != ctx->gas.n) return fail(ctx, DMB_ERR_ARG, "particle counts differ from the grid");
+  if (!(dt_min >= 0.0) || !isfinite(dt_min)) return fail(ctx, DMB_ERR_ARG, "dt_min must be finite and >= 0");
+  if (ctx->rc.rate_mode == DMB_RATE_MLP) {
+    if (!ctx->mlp_ready) return fail(ctx, DMB_ERR_STATE, "surrogate rate provider selected but no trained network");
+    bool known = false;
+    for (int k : ctx->mlp_n) known = known || k == ctx->p.n;
+    if (!known) return fail(ctx, DMB_ERR_DOMAIN, "the surrogate was not trained for this power-law index");
+  }
+  const int lim = substep_lim(substep);
+  if (ctx->use_graph) {
+    st = substep_graph(ctx, dm, gas, lim, substep, dt_min);
+  } else {
+    st = ctx->p.fp64 ? substep_body<double>(ctx, dm, gas, lim, substep, dt_min, false)
+                     : substep_body<float>(ctx, dm, gas, lim, substep, dt_min, false);
+    ctx->graph_next_step = ~0ull;
+  }
+  if (st != DMB_OK) return st;
+  if (sums_out) {
+    CK(cudaMemcpyAsync(ctx->h_sums, ctx->sums.p, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream), "sums readback");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    memcpy(sums_out, ctx->h_sums, 16 * 8);
+  }
+  return DMB_OK;
+}
+
 dmb_status dmb_set_timing(dmb_ctx *ctx, int on) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
-  if (on && !ctx->ev[0])
+  if (on && !ctx->ev[0]) {
     for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&ctx->ev[k]), "event create");
+    for (int k = 0; k < 2; ++k) CK(cudaEventCreate(&ctx->sev[k]), "event create");
+  }
   ctx->timing = on != 0;
   for (int k = 0; k < 8; ++k) ctx->stage_ms[k] = 0.0;
   ctx->timed_steps = 0;
@@ -993,6 +1366,31 @@ dmb_status dmb_surrogate_grad(dmb_ctx *ctx, const float *X, const float *Y, int3
     *loss = t / (double)B;   // mean over samples of the summed squared error of the two outputs
   }
   return DMB_OK;
+}
+
+dmb_status dmb_set_surrogate_engine(dmb_ctx *ctx, int32_t engine) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (engine != 0 && engine != 1) return fail(ctx, DMB_ERR_ARG, "engine must be 0 (tcgen05) or 1 (mma.sync)");
+  ctx->mlp_engine = engine;
+  clear_graphs(ctx);   // captured substeps hold the other engine's launches
+  return DMB_OK;
+}
+
+dmb_status dmb_surrogate_infer_tc(dmb_ctx *ctx, const float *X, int64_t n, float *Y) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!ctx->mlp_ready) return fail(ctx, DMB_ERR_STATE, "no surrogate loaded");
+  if (n < 0 || (n > 0 && (!X || !Y))) return fail(ctx, DMB_ERR_ARG, "bad arguments");
+  MlpRun mr = mlp_run(ctx);
+  TcArgs a = {};
+  a.p = mr.p;
+  a.w2 = mr.w2;
+  a.w3 = mr.w3;
+  a.n = n;
+  a.X = X;
+  a.Y = Y;
+  a.status = ptr<uint32_t>(ctx->status);
+  CK(mlp_tc_infer(a, ctx->stream, &ctx->launches), "surrogate inference (tensor cores)");
+  return check_status(ctx);
 }
 
 dmb_status dmb_surrogate_fallbacks(dmb_ctx *ctx, int64_t *out) {

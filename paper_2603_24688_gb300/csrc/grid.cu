@@ -223,18 +223,8 @@ __global__ void k_gather(const double *__restrict__ pos, const double *__restric
     bad |= !(t >= 0.0) || !isfinite(t) || !(m > 0.0) || !isfinite(m);
     const double s2 = rc.kT_over_mp * t / m;         // varsigma^2 [(km/s)^2]
     sig = sqrt(fmax(s2, 0.0));
-    const double mpm = rc.m_chi + m;
-    const double e = m / mpm;
-    double cA, cB;
-    if (sig > 0.0) {
-      const double sn = pow(sig / rc.v0, (double)rc.n);          // (varsigma / v0)^n
-      cA = rc.S * rc.alpha / 3.0 * sn * sig / mpm;
-      cB = rc.S * rc.alpha * sn * sig * sig * sig / mpm * e;
-    } else {  // cold gas: A = sigma(w) w, B = sigma(w) w^3
-      cA = rc.S / mpm;
-      cB = rc.S / mpm * e;
-    }
-    const double kP0 = mm / m * rc.S;                          // (M_j / mu_j) sigma0 Msun/m_p
+    double cA, cB, kP0, e;
+    gas_coeffs(rc, sig, mm, m, cA, cB, kP0, e);
     K[s] = Vec<R>::make((R)cA, (R)cB, (R)kP0, (R)e);
   }
   V[s] = Vec<R>::make((R)v[0], (R)v[1], (R)v[2], (R)sig);

@@ -23,6 +23,25 @@ struct RunConst {
   int rate_mode;     // dmb_rate_mode
 };
 
+// Per-gas coefficients of the sorted copy K = (cA, cB, kP0, e) from varsigma (km/s), the gas
+// particle mass M (Msun) and mu (m_p): a_j = cA sum M_i g FA w and du_j/dt = cA sum M_i g FA w^2
+// - cB sum M_i g FB with the normalised rates FA, FB (Eqs. gas-dVdt, gas-dTdt and the App. B
+// closed forms), kP0 = (M_j / mu_j) sigma0 of Eq. dm-update-prob and e = mu_j / (m_chi + mu_j).
+__host__ __device__ inline void gas_coeffs(const RunConst &rc, double sig, double M, double mu, double &cA,
+                                           double &cB, double &kP0, double &e) {
+  const double mpm = rc.m_chi + mu;
+  e = mu / mpm;
+  if (sig > 0.0) {
+    const double sn = pow(sig / rc.v0, (double)rc.n);          // (varsigma / v0)^n
+    cA = rc.S * rc.alpha / 3.0 * sn * sig / mpm;
+    cB = rc.S * rc.alpha * sn * sig * sig * sig / mpm * e;
+  } else {  // cold gas: A = sigma(w) w, B = sigma(w) w^3
+    cA = rc.S / mpm;
+    cB = rc.S / mpm * e;
+  }
+  kP0 = M / mu * rc.S;                                         // (M_j / mu_j) sigma0 Msun/m_p
+}
+
 // Batched boxes: per-box parameters used by the key and gather kernels (device table).
 struct BoxParamDev {
   double L[3];        // periodic sides, kpc
@@ -43,6 +62,7 @@ enum : uint32_t {
   DMB_BAD_PERIODIC = 2u,   // h_i + h_j >= box / 2 (minimum image ambiguous)
   DMB_BAD_DOMAIN = 4u,     // rate provider outside its domain
   DMB_BAD_OVERFLOW = 8u,   // a pair list or stack overflowed
+  DMB_BAD_TIMEOUT = 16u,   // a bounded wait on the tensor cores gave up
 };
 
 cudaError_t launch_frame(const double *dm_pos, const double *dm_h, int64_t ndm, const double *gas_pos,

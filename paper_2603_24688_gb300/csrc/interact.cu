@@ -23,7 +23,7 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
   const int64_t nwarps = (int64_t)gridDim.x * MF_WARPS;
   const R inv_v0 = (R)(1.0 / rc.v0);
   const R alpha = (R)rc.alpha;
-  const int64_t n_seg = sv.seg_ptr[G.n];
+  const int64_t n_seg = sv.n_seg >= 0 ? sv.n_seg : sv.seg_ptr[G.n];
   for (int64_t u = (int64_t)blockIdx.x * MF_WARPS + (threadIdx.x >> 5); u < n_seg; u += nwarps) {
     const int64_t j = sv.seg_row[u];
     const int64_t rs = sv.seg_begin[u], re = min(rs + (int64_t)MF_SEG, row_ptr[j + 1]);
@@ -120,7 +120,7 @@ k_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *__re
   const unsigned lane = threadIdx.x & 31u;
   __nv_bfloat16 *act = actbuf + (threadIdx.x >> 5) * 32 * MLP_LDW;
   const int64_t nwarps = (int64_t)gridDim.x * MF_WARPS;
-  const int64_t n_seg = sv.seg_ptr[G.n];
+  const int64_t n_seg = sv.n_seg >= 0 ? sv.n_seg : sv.seg_ptr[G.n];
   const float alpha = (float)rc.alpha;
   unsigned fallback = 0;
   for (int64_t u = (int64_t)blockIdx.x * MF_WARPS + (threadIdx.x >> 5); u < n_seg; u += nwarps) {
@@ -189,18 +189,28 @@ k_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *__re
   if (lane == 0 && fallback && mr.fallback_count) atomicAdd(mr.fallback_count, (unsigned long long)fallback);
 }
 
-cudaError_t launch_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *row_ptr,
-                                  const uint32_t *rows, SegView sv, int64_t n_seg_max, RunConst rc, MlpRun mr,
-                                  float2 *rates, cudaStream_t s, int64_t *launches) {
-  const size_t smem = MLP_ACT_OFFSET + (size_t)MF_WARPS * 32 * MLP_LDW * sizeof(__nv_bfloat16);
+static const size_t kMlpRatesSmem = MLP_ACT_OFFSET + (size_t)MF_WARPS * 32 * MLP_LDW * sizeof(__nv_bfloat16);
+
+cudaError_t prepare_mlp_pair_rates() {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_pair_rates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_pair_rates, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kMlpRatesSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *row_ptr,
+                                  const uint32_t *rows, SegView sv, int64_t n_seg_max, RunConst rc, MlpRun mr,
+                                  float2 *rates, cudaStream_t s, int64_t *launches) {
+  const size_t smem = kMlpRatesSmem;
+  cudaError_t e = prepare_mlp_pair_rates();
+  if (e != cudaSuccess) return e;
   int64_t blocks = (n_seg_max + MF_WARPS - 1) / MF_WARPS;
   if (blocks > 152 * 2) blocks = 152 * 2;
+  if (blocks < 1) blocks = 1;
   k_mlp_pair_rates<<<(unsigned)blocks, MF_WARPS * 32, smem, s>>>(G, D, row_ptr, rows, sv, rc, mr, rates);
   if (launches) *launches += 1;
   return cudaGetLastError();
@@ -209,14 +219,14 @@ cudaError_t launch_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, co
 // acc_j = cA sum(t FA w), du_j/dt = cA sum(t FA w^2) - cB sum(t FB), and the App. C expected
 // DM energy change of the pairs, M_j (cB sum(t FB) - cA sum(t FA v_i.w)), without dt
 template <typename R>
-__global__ void k_meanfield_finish(SpeciesView<R> G, const int64_t *__restrict__ seg_ptr, const R *__restrict__ part,
-                                   MfOut out) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= G.n) return;
+__global__ void k_meanfield_finish(SpeciesView<R> G, SegView sv, const R *__restrict__ part, MfOut out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (sv.list ? sv.n_rows : G.n)) return;
+  const int64_t j = sv.list ? (int64_t)sv.list[k] : k;
   const typename Vec<R>::v4 K = G.K[j];
   const double cA = (double)K.x, cB = (double)K.y;
   double q[6] = {0, 0, 0, 0, 0, 0};
-  for (int64_t u = seg_ptr[j]; u < seg_ptr[j + 1]; ++u)   // segments in order: deterministic
+  for (int64_t u = sv.seg_ptr[k]; u < sv.seg_ptr[k + 1]; ++u)   // segments in order: deterministic
     for (int k = 0; k < 6; ++k) q[k] += (double)part[6 * u + k];
   const uint32_t c = G.perm[j];
   out.acc[3 * (int64_t)c + 0] = cA * q[0];
@@ -233,6 +243,7 @@ cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, co
   if (G.n <= 0) return cudaSuccess;
   int64_t blocks = (n_seg_max + MF_WARPS - 1) / MF_WARPS;
   if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) blocks = 1;
   if (rc.rate_mode == DMB_RATE_QUAD) {
     k_meanfield<R, DMB_RATE_QUAD><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc,
                                                                               part, mr);
@@ -243,7 +254,8 @@ cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, co
     k_meanfield<R, DMB_RATE_CLOSED><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc,
                                                                                 part, mr);
   }
-  k_meanfield_finish<R><<<(unsigned)((G.n + 255) / 256), 256, 0, s>>>(G, sv.seg_ptr, part, out);
+  const int64_t nfin = sv.list ? sv.n_rows : G.n;
+  if (nfin > 0) k_meanfield_finish<R><<<(unsigned)((nfin + 255) / 256), 256, 0, s>>>(G, sv, part, out);
   if (launches) *launches += 2;
   return cudaGetLastError();
 }
@@ -307,8 +319,11 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
   const int64_t nwarps = (int64_t)gridDim.x * MC_WARPS;
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
   const R inv_v0 = (R)(1.0 / rc.v0);
-  const R dt = (R)a.dt;
-  for (int64_t i = (int64_t)blockIdx.x * MC_WARPS + wib; i < D.n; i += nwarps) {
+  const unsigned long long step = a.step_dev ? *a.step_dev : a.step;
+  const int64_t nrows = a.list ? a.n_list : D.n;
+  for (int64_t k = (int64_t)blockIdx.x * MC_WARPS + wib; k < nrows; k += nwarps) {
+    const int64_t i = a.list ? (int64_t)a.list[k] : k;
+    const R dt = a.bin ? (R)ldexp(a.dt, (int)a.bin[D.perm[i]]) : (R)a.dt;   // dt_i = 2^bin dt
     const int64_t rs = row_ptr[i], re = row_ptr[i + 1];
     if (re == rs) {                       // no gas partner: nothing can happen
       if (lane == 0) {
@@ -329,7 +344,7 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
       const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
       R rx, ry, rz, vr;
       const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx.periodic, side, gtab, rc.n, inv_v0,
-                                      dt, a.step, k0, k1, rx, ry, rz, vr);
+                                      dt, step, k0, k1, rx, ry, rz, vr);
       pcache[p] = P;
       sum = u128_add(sum, to_fixed(P));
       const R e = Kj.w;                                   // mu_j / (m_chi + mu_j)
@@ -339,7 +354,7 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
     const U128 C = warp_sum_u128(sum);
     rmax = warp_max(rmax);
     // selection uniform r_i = (k + 1/2) 2^-52, k the top 52 bits of (w0, w3): as a 64-bit fraction
-    const uint4 wd = philox4x32_10(dm_counter(id_i, a.step), k0, k1);
+    const uint4 wd = philox4x32_10(dm_counter(id_i, step), k0, k1);
     const unsigned long long k52 = ((unsigned long long)wd.x << 20) | (unsigned long long)(wd.w >> 12);
     const unsigned long long R64 = (k52 << 12) | (1ull << 11);
     const bool clamped = C.hi >= 1ull;                    // sum_j P_ij > 1: renormalise
@@ -377,7 +392,7 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
         const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
         R rx, ry, rz, vr;
         (void)pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx.periodic, side, gtab, rc.n, inv_v0, dt,
-                                  a.step, k0, k1, rx, ry, rz, vr);
+                                  step, k0, k1, rx, ry, rz, vr);
         const U128 hi = u128_add(base, to_fixed(pcache[pstar]));
         band = band || near_rel(T, base, hi) || near_rel(T, hi, hi);
         // isotropic new direction: cos(theta') = 2u - 1, phi' = 2 pi u'
@@ -418,7 +433,9 @@ k_mc_finish(int64_t n, const uint32_t *__restrict__ perm, const McRec *__restric
   __shared__ float redm[256];
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   float mx = 0.0f;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t nrows = a.list ? a.n_list : n;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nrows; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = a.list ? (int64_t)a.list[k] : k;
     const McRec r = rec[i];
     const uint32_t c = perm[i];
     const double M = mass_f ? (double)mass_f[(int64_t)mass_stride * i] : mass_d[(int64_t)mass_stride * i];
@@ -437,6 +454,10 @@ k_mc_finish(int64_t n, const uint32_t *__restrict__ perm, const McRec *__restric
     a.vel_out[3 * (int64_t)c] = n0;
     a.vel_out[3 * (int64_t)c + 1] = n1;
     a.vel_out[3 * (int64_t)c + 2] = n2;
+    if (a.v_sorted != nullptr) {   // keep the sorted copy current for the next substep
+      if (a.v_sorted_fp64) reinterpret_cast<double4_32a *>(a.v_sorted)[i] = Vec<double>::make(n0, n1, n2, 0.0);
+      else reinterpret_cast<float4 *>(a.v_sorted)[i] = make_float4((float)n0, (float)n1, (float)n2, 0.0f);
+    }
     const double Cd = (r.c_hi | r.c_lo) ? (double)r.c_hi + ldexp((double)r.c_lo, -64) : 0.0;
     if (a.scattered) a.scattered[c] = (uint8_t)(r.flags & 1u);
     if (a.partner) a.partner[c] = r.partner;
@@ -466,7 +487,9 @@ template <typename R>
 cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *row_ptr, const uint32_t *rows,
                       const float4 *gtab, RunConst rc, McArgs a, R *pcache, McRec *rec, int finish_blocks,
                       cudaStream_t s, int64_t *launches) {
-  int64_t blocks = (D.n + MC_WARPS - 1) / MC_WARPS;
+  const int64_t nrows = a.list ? a.n_list : D.n;
+  if (nrows <= 0) return cudaSuccess;
+  int64_t blocks = (nrows + MC_WARPS - 1) / MC_WARPS;
   if (blocks > 152 * 32) blocks = 152 * 32;
   k_mc<R><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec);
   // the particle mass sits in L.w of the sorted copies

@@ -1,0 +1,441 @@
+// Surrogate inference on the 5th-generation tensor cores (tcgen05): tiles of 128 rows, the
+// three hidden layers as 128 x 128 x K MMAs with bf16 operands in shared memory and the float32
+// accumulator in tensor memory; bias, SiLU and the bf16 repacking of the activations run on the
+// CUDA cores between the layers, the output layer in float32.
+//
+// One CTA per SM holds the bf16 weights once and runs NWG independent warpgroups of 128
+// threads; warpgroup g owns TMEM columns [128 g, 128 g + 128) and its own activation buffers,
+// so while one warpgroup evaluates SiLU (the MUFU-bound part) another one's MMAs run.
+// Thread t of a warpgroup owns row t of its tile: it forms the row's inputs, reads the row's
+// accumulator (TMEM lane t) and writes the row's activations.
+//
+// Layer 1 (4 -> 128) runs on the tensor cores too, exactly enough for float32 inputs: with
+// x = x_hi + x_lo and W1 = W_hi + W_lo (bf16 parts), K = 16 holds the four products
+// [x_hi, x_hi, x_lo, x_lo] . [W_hi, W_lo, W_hi, W_lo], leaving an error of about 2^-16 of x.W.
+//
+// Operand layout (no swizzle, K-major): 8 x 16-byte core matrices; element (row, k) of a
+// 128-row operand sits at (k / 8) * 2048 + row * 16 + (k % 8) * 2 bytes, so the descriptor of
+// the K = 16 slice ks starts at 4096 ks with leading-dimension offset 2048 (next 8 columns) and
+// stride-dimension offset 128 (next 8 rows).
+#include <cuda_bf16.h>
+
+#include "mlp_tc.cuh"
+#include "physics.cuh"
+
+#define TC_ROWS 128
+#define TC_SLICE 2048     // bytes between the 8-column chunks of a 128-row operand
+#define TC_OPER 32768     // one 128 x 128 bf16 operand
+#define TC_OPER1 4096     // one 128 x 16 bf16 operand (layer 1)
+
+// Instruction descriptor of tcgen05.mma kind::f16: D float32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bits 17-22, M / 16 at bits 24-28.
+#define TC_IDESC ((1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24))
+
+// shared-memory layout (bytes); the operands come first so that every operand read lies inside
+// the allocation whatever the descriptor strides
+template <int NWG>
+struct TcLayout {
+  static constexpr int W2 = 0;
+  static constexpr int W3 = W2 + TC_OPER;
+  static constexpr int A = W3 + TC_OPER;                 // NWG activation operands
+  static constexpr int A1 = A + NWG * TC_OPER;           // NWG layer-1 operands
+  static constexpr int W1 = A1 + NWG * TC_OPER1;         // split W1 (128 x 16)
+  static constexpr int B1 = W1 + TC_OPER1;               // biases (float)
+  static constexpr int B2 = B1 + 512;
+  static constexpr int B3 = B2 + 512;
+  static constexpr int W4 = B3 + 512;                    // [2][128] float
+  static constexpr int B4 = W4 + 1024;                   // 2 floats (16 bytes)
+  static constexpr int WIN = B4 + 16;                    // NWG x 129 int64 row-start windows
+  static constexpr int BAR = WIN + NWG * 129 * 8 + 8;    // NWG mbarriers (8-byte aligned)
+  static constexpr int TSLOT = BAR + NWG * 8;            // TMEM base address
+  static constexpr int FLAG = TSLOT + 16;                // NWG completion flags
+  static constexpr int USED = FLAG + 16;
+  // furthest byte a 128-row operand read can touch if the two descriptor strides (2048 and 128)
+  // were taken the other way round: 8 slices (K = 128) or one slice (K = 16) of 15 x 2048 + 2 x 128
+  static constexpr int REACH = 7 * 4096 + 15 * 2048 + 256;
+  static constexpr int REACH1 = 15 * 2048 + 256;
+  static constexpr int TOTAL0 = (A1 + (NWG - 1) * TC_OPER1 + REACH1 > A + (NWG - 1) * TC_OPER + REACH)
+                                    ? A1 + (NWG - 1) * TC_OPER1 + REACH1
+                                    : A + (NWG - 1) * TC_OPER + REACH;
+  static constexpr int TOTAL1 = TOTAL0 > W1 + REACH1 ? TOTAL0 : W1 + REACH1;
+  static constexpr int TOTAL = ((TOTAL1 > USED ? TOTAL1 : USED) + 1023) / 1024 * 1024;
+};
+static_assert(TcLayout<3>::TOTAL <= 232448, "shared memory of the tensor-core surrogate");
+static_assert(TcLayout<3>::BAR % 8 == 0, "mbarrier alignment");
+
+// ---- PTX wrappers ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+// Waits for the phase with the given parity to complete; gives up after about two seconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > 2000000000ull) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void wg_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+// Shared-memory matrix descriptor: start address, leading- and stride-dimension byte offsets
+// (all >> 4), descriptor version 1 at bit 46, base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;
+  return d;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive float32 columns of this thread's TMEM lane; the wait is tied to the registers
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+  const __nv_bfloat16 b = __float2bfloat16_rn(x);
+  return (uint32_t) * reinterpret_cast<const uint16_t *>(&b);
+}
+
+// ---- the kernel -----------------------------------------------------------------------------
+// MODE_X: rows are the caller's inputs X[n][4], outputs the raw network outputs Y[n][2].
+// MODE_PAIRS: rows are gas-major pairs (processing order q over a row-start prefix R_ptr),
+// outputs the normalised rates (FA, FB) at the pair's index p; out-of-box rows take the
+// quadrature (counted), cold gas is skipped (the mean field uses the exact cold limit).
+enum { MODE_X = 0, MODE_PAIRS = 1 };
+
+template <int NWG, int MODE>
+__global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
+  typedef TcLayout<NWG> Ly;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x;
+  const int g = tid >> 7;             // warpgroup
+  const int t = tid & 127;            // row of the tile
+  const int w = t >> 5;               // warp within the warpgroup: TMEM lanes 32 w .. 32 w + 31
+  const uint32_t sbase = smem_u32(sm);
+
+  // ---- weights into the operand layout ---------------------------------------------------
+  for (int q = tid; q < 2 * MLP_H * (MLP_H / 8); q += blockDim.x) {
+    const int which = q / (MLP_H * (MLP_H / 8));
+    const int r = q % (MLP_H * (MLP_H / 8));
+    const int n = r % MLP_H, c = r / MLP_H;           // output row n, 8-column chunk c
+    const __nv_bfloat16 *src = (which == 0 ? a.w2 : a.w3) + n * MLP_H + c * 8;
+    *reinterpret_cast<uint4 *>(sm + (which == 0 ? Ly::W2 : Ly::W3) + c * TC_SLICE + n * 16) =
+        *reinterpret_cast<const uint4 *>(src);
+  }
+  for (int n = tid; n < MLP_H; n += blockDim.x) {
+    uint32_t hl[4];
+#pragma unroll
+    for (int m = 0; m < MLP_IN; m += 2) {
+      const float w0 = a.p[MLP_OFF_W1 + n * MLP_IN + m], w1 = a.p[MLP_OFF_W1 + n * MLP_IN + m + 1];
+      const float h0 = __bfloat162float(__float2bfloat16_rn(w0)), h1 = __bfloat162float(__float2bfloat16_rn(w1));
+      hl[m / 2] = bf16_bits(w0) | (bf16_bits(w1) << 16);
+      hl[2 + m / 2] = bf16_bits(w0 - h0) | (bf16_bits(w1 - h1) << 16);
+    }
+    const uint4 chunk = make_uint4(hl[0], hl[1], hl[2], hl[3]);   // [W_hi(4), W_lo(4)] in both chunks
+    *reinterpret_cast<uint4 *>(sm + Ly::W1 + 0 * TC_SLICE + n * 16) = chunk;
+    *reinterpret_cast<uint4 *>(sm + Ly::W1 + 1 * TC_SLICE + n * 16) = chunk;
+  }
+  float *b1 = reinterpret_cast<float *>(sm + Ly::B1);
+  float *b2 = reinterpret_cast<float *>(sm + Ly::B2);
+  float *b3 = reinterpret_cast<float *>(sm + Ly::B3);
+  float *W4 = reinterpret_cast<float *>(sm + Ly::W4);
+  float *b4 = reinterpret_cast<float *>(sm + Ly::B4);
+  for (int c = tid; c < MLP_H; c += blockDim.x) {
+    b1[c] = a.p[MLP_OFF_B1 + c];
+    b2[c] = a.p[MLP_OFF_B2 + c];
+    b3[c] = a.p[MLP_OFF_B3 + c];
+    W4[c] = a.p[MLP_OFF_W4 + c];
+    W4[MLP_H + c] = a.p[MLP_OFF_W4 + MLP_H + c];
+  }
+  if (tid < MLP_OUT) b4[tid] = a.p[MLP_OFF_B4 + tid];
+  const uint32_t bar = sbase + Ly::BAR + 8 * g;
+  if (tid == 0) {
+    for (int k = 0; k < NWG; ++k) mbar_init(sbase + Ly::BAR + 8 * k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Ly::TSLOT);
+  const uint32_t ncols = NWG <= 2 ? 256u : 512u;
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + Ly::TSLOT),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();   // the weights were written by the generic proxy; the MMAs read them
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t d_tmem = tmem + 128u * (uint32_t)g;                           // lane 0, this group's columns
+  const uint32_t my_lanes = d_tmem + ((uint32_t)(32 * w) << 16);
+  const uint32_t sA = sbase + Ly::A + g * TC_OPER, sA1 = sbase + Ly::A1 + g * TC_OPER1;
+  unsigned char *pA = sm + Ly::A + g * TC_OPER;
+  unsigned char *pA1 = sm + Ly::A1 + g * TC_OPER1;
+  int64_t *win = reinterpret_cast<int64_t *>(sm + Ly::WIN) + g * 129;
+  volatile uint32_t *flag = reinterpret_cast<volatile uint32_t *>(sm + Ly::FLAG) + g;
+  const int bar_id = 1 + g;
+  uint32_t phase = 0;
+  unsigned fallback = 0;
+  bool ok = true;
+  const float alpha = (float)a.rc.alpha;
+
+  const int64_t n_tiles = (a.n + TC_ROWS - 1) / TC_ROWS;
+  for (int64_t T = (int64_t)blockIdx.x * NWG + g; T < n_tiles && ok; T += (int64_t)gridDim.x * NWG) {
+    // ---- row inputs ----------------------------------------------------------------------
+    const int64_t q = T * TC_ROWS + t;
+    const bool valid = q < a.n;
+    float x[MLP_IN] = {0.f, 0.f, 0.f, 0.f};
+    int64_t p = -1;
+    float s_ratio = 0.f;
+    bool use = false, in_dom = false;
+    if (MODE == MODE_X) {
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < MLP_IN; ++m) x[m] = a.X[4 * q + m];
+        use = in_dom = true;
+      }
+    } else {
+      // row of q: window of the row starts from the tile's first row, binary search inside it
+      const int64_t k0 = a.tile_row0[T];
+      const int64_t kw = k0 + t < a.n_rows ? k0 + t : a.n_rows;
+      win[t] = a.R_ptr[kw];
+      if (t == 0) win[128] = a.R_ptr[k0 + 128 < a.n_rows ? k0 + 128 : a.n_rows];
+      wg_sync(bar_id);
+      if (valid) {
+        int64_t k;
+        if (q < win[128] || k0 + 128 >= a.n_rows) {
+          int lo = 0, hi = 128;                        // largest idx with win[idx] <= q
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (win[mid] <= q) lo = mid; else hi = mid - 1;
+          }
+          k = k0 + lo;
+        } else {
+          int64_t lo = k0 + 128, hi = a.n_rows - 1;
+          while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (a.R_ptr[mid] <= q) lo = mid; else hi = mid - 1;
+          }
+          k = lo;
+        }
+        const int64_t j = a.list ? (int64_t)a.list[k] : k;
+        p = a.list ? a.row_ptr[j] + (q - a.R_ptr[k]) : q;
+        const float4 Vj = a.G_V[j];
+        const float4 Vi = a.D_V[a.rows[p]];
+        const float sig = Vj.w;
+        if (sig > 0.0f) {
+          const float wx = Vi.x - Vj.x, wy = Vi.y - Vj.y, wz = Vi.z - Vj.z;
+          s_ratio = sqrtf(wx * wx + wy * wy + wz * wz) / sig;
+          in_dom = mlp_inputs(a.dom, fmaxf(s_ratio, 1e-30f), sig, x);
+          use = true;
+        }
+      }
+    }
+    // layer-1 operand row: chunk 0 = [x_hi, x_hi], chunk 1 = [x_lo, x_lo]
+    {
+      uint32_t hi2[2], lo2[2];
+#pragma unroll
+      for (int m = 0; m < MLP_IN; m += 2) {
+        const float h0 = __bfloat162float(__float2bfloat16_rn(x[m]));
+        const float h1 = __bfloat162float(__float2bfloat16_rn(x[m + 1]));
+        hi2[m / 2] = bf16_bits(x[m]) | (bf16_bits(x[m + 1]) << 16);
+        lo2[m / 2] = bf16_bits(x[m] - h0) | (bf16_bits(x[m + 1] - h1) << 16);
+      }
+      *reinterpret_cast<uint4 *>(pA1 + 0 * TC_SLICE + t * 16) = make_uint4(hi2[0], hi2[1], hi2[0], hi2[1]);
+      *reinterpret_cast<uint4 *>(pA1 + 1 * TC_SLICE + t * 16) = make_uint4(lo2[0], lo2[1], lo2[0], lo2[1]);
+    }
+    // ---- three layers ------------------------------------------------------------------------
+    float y0 = 0.f, y1 = 0.f;
+#pragma unroll 1
+    for (int layer = 0; layer < 3; ++layer) {
+      fence_async_smem();
+      tc_fence_before();
+      wg_sync(bar_id);
+      if (t == 0) {
+        tc_fence_after();
+        if (layer == 0) {
+          tc_mma(d_tmem, smem_desc(sA1, TC_SLICE, 128), smem_desc(sbase + Ly::W1, TC_SLICE, 128), 0u);
+        } else {
+          const uint32_t sW = sbase + (layer == 1 ? Ly::W2 : Ly::W3);
+#pragma unroll
+          for (int ks = 0; ks < MLP_H / 16; ++ks)
+            tc_mma(d_tmem, smem_desc(sA + ks * 2 * TC_SLICE, TC_SLICE, 128),
+                   smem_desc(sW + ks * 2 * TC_SLICE, TC_SLICE, 128), ks > 0 ? 1u : 0u);
+        }
+        tc_commit(bar);
+        // one thread waits (bounded) and tells the group, so that a timeout is seen by all 128
+        *flag = mbar_wait_bounded(bar, phase) ? 1u : 0u;
+      }
+      wg_sync(bar_id);
+      phase ^= 1u;
+      if (*flag == 0u) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const float *bias = layer == 0 ? b1 : layer == 1 ? b2 : b3;
+#pragma unroll 1
+      for (int cc = 0; cc < MLP_H / 32; ++cc) {
+        float v[32];
+        tmem_ld32(my_lanes + 32u * cc, v);
+        if (layer < 2) {
+          uint32_t pk[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            pk[k] = pack_bf16(silu(v[2 * k] + bias[32 * cc + 2 * k]), silu(v[2 * k + 1] + bias[32 * cc + 2 * k + 1]));
+#pragma unroll
+          for (int c4 = 0; c4 < 4; ++c4)
+            *reinterpret_cast<uint4 *>(pA + (4 * cc + c4) * TC_SLICE + t * 16) =
+                make_uint4(pk[4 * c4], pk[4 * c4 + 1], pk[4 * c4 + 2], pk[4 * c4 + 3]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const int c = 32 * cc + k;
+            const float act = silu(v[k] + bias[c]);
+            y0 += W4[c] * act;
+            y1 += W4[MLP_H + c] * act;
+          }
+        }
+      }
+    }
+    if (!ok) break;
+    tc_fence_before();   // this tile's TMEM reads are done before the next tile's MMA
+    // ---- outputs -----------------------------------------------------------------------------
+    const float y[MLP_OUT] = {y0 + b4[0], y1 + b4[1]};
+    if (MODE == MODE_X) {
+      if (valid) {
+        a.Y[2 * q] = y[0];
+        a.Y[2 * q + 1] = y[1];
+      }
+    } else if (use) {
+      float FA, FB;
+      if (in_dom) {
+        mlp_outputs(a.dom, s_ratio, y, FA, FB);
+      } else {
+        rates_quad<float>(0.5f * s_ratio * s_ratio, a.rc.n, alpha, FA, FB);
+        ++fallback;
+      }
+      a.rates[p] = make_float2(FA, FB);
+    }
+  }
+  if (!ok && t == 0) atomicOr(a.status, DMB_BAD_TIMEOUT);
+  if (MODE == MODE_PAIRS) {
+    fallback = warp_sum<unsigned>(fallback);
+    if ((tid & 31) == 0 && fallback && a.fallback_count) atomicAdd(a.fallback_count, (unsigned long long)fallback);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid < 32) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  }
+}
+
+// first row (in processing order) of every 128-row tile: largest k with R_ptr[k] <= 128 T
+__global__ void k_tile_rows(const int64_t *__restrict__ R_ptr, int64_t n_rows, int64_t n_tiles,
+                            int64_t *__restrict__ tile_row0) {
+  const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= n_tiles) return;
+  const int64_t q = T * TC_ROWS;
+  int64_t lo = 0, hi = n_rows - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (R_ptr[mid] <= q) lo = mid; else hi = mid - 1;
+  }
+  tile_row0[T] = lo;
+}
+
+static bool g_tc_attr = false;
+
+cudaError_t mlp_tc_prepare() {
+  if (g_tc_attr) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<TC_NWG, MODE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TcLayout<TC_NWG>::TOTAL);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_tc<TC_NWG, MODE_PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcLayout<TC_NWG>::TOTAL);
+  if (e == cudaSuccess) g_tc_attr = true;
+  return e;
+}
+
+template <int NWG, int MODE>
+static cudaError_t launch_tc(const TcArgs &a, cudaStream_t s) {
+  const int smem = TcLayout<NWG>::TOTAL;
+  const cudaError_t e = mlp_tc_prepare();
+  if (e != cudaSuccess) return e;
+  const int64_t n_tiles = (a.n + TC_ROWS - 1) / TC_ROWS;
+  int64_t blocks = (n_tiles + NWG - 1) / NWG;
+  if (blocks > 152) blocks = 152;
+  if (blocks < 1) blocks = 1;
+  k_mlp_tc<NWG, MODE><<<(unsigned)blocks, NWG * 128, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_tc_infer(TcArgs a, cudaStream_t s, int64_t *launches) {
+  if (a.n <= 0) return cudaSuccess;
+  if (launches) *launches += 1;
+  return launch_tc<TC_NWG, MODE_X>(a, s);
+}
+
+cudaError_t mlp_tc_pair_rates(TcArgs a, int64_t *tile_row0, cudaStream_t s, int64_t *launches) {
+  if (a.n <= 0 || a.n_rows <= 0) return cudaSuccess;
+  const int64_t n_tiles = (a.n + TC_ROWS - 1) / TC_ROWS;
+  k_tile_rows<<<(unsigned)((n_tiles + 255) / 256), 256, 0, s>>>(a.R_ptr, a.n_rows, n_tiles, tile_row0);
+  a.tile_row0 = tile_row0;
+  if (launches) *launches += 2;
+  return launch_tc<TC_NWG, MODE_PAIRS>(a, s);
+}

@@ -1,0 +1,40 @@
+// Tensor-core (tcgen05) inference of the learned rate surrogate: arguments and launchers.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "grid.cuh"
+#include "mlp.cuh"
+
+#define TC_NWG 3   // warpgroups (independent 128-row tiles in flight) per CTA
+
+struct TcArgs {
+  // network: float32 parameter block and the bf16 [out][in] copies of the 128 x 128 layers
+  const float *p;
+  const __nv_bfloat16 *w2, *w3;
+  int64_t n;                       // rows
+  // rows given directly: X [n][4] network inputs -> Y [n][2] raw outputs
+  const float *X;
+  float *Y;
+  // rows = gas-major pairs: row q of the processing order lies in row k (largest k with
+  // R_ptr[k] <= q) of n_rows rows; k is gas list[k] (or gas k when list is null) and the
+  // pair index is p = row_ptr[gas] + q - R_ptr[k] (or q when list is null)
+  const int64_t *R_ptr;
+  int64_t n_rows;
+  const uint32_t *list;
+  const int64_t *row_ptr;
+  const uint32_t *rows;            // DM index of pair p (sorted)
+  const float4 *G_V, *D_V;         // sorted velocity copies (v, varsigma)
+  const int64_t *tile_row0;        // set by the launcher
+  MlpDomain dom;
+  RunConst rc;
+  float2 *rates;                   // [pairs] (FA, FB)
+  unsigned long long *fallback_count;
+  uint32_t *status;                // DMB_BAD_TIMEOUT if a tensor-core wait gave up
+};
+
+// Shared-memory attributes (call once before any graph capture).
+cudaError_t mlp_tc_prepare();
+// Raw network outputs of X (debug / validation entry).
+cudaError_t mlp_tc_infer(TcArgs a, cudaStream_t s, int64_t *launches);
+// Rates of the pairs in processing order; tile_row0: scratch of (n + 127) / 128 int64.
+cudaError_t mlp_tc_pair_rates(TcArgs a, int64_t *tile_row0, cudaStream_t s, int64_t *launches);

@@ -45,10 +45,16 @@ cudaError_t launch_seg_map(const int64_t *row_ptr, const int64_t *seg_ptr, int64
                            int64_t *seg_begin, cudaStream_t s, int64_t *launches);
 
 // Mean-field row segments: segment u covers pairs [begin[u], min(begin[u] + MF_SEG, end of row)).
+// Without a row list the rows are all gas particles in sorted order and seg_ptr is indexed by
+// the sorted gas index; with a list (the active gas of a substep) row k is gas list[k] and
+// seg_ptr is indexed by k.
 struct SegView {
-  const int64_t *seg_ptr;     // [N_B + 1]: segments of gas row j are [seg_ptr[j], seg_ptr[j+1])
-  const uint32_t *seg_row;    // [n_seg]
+  const int64_t *seg_ptr;     // [rows + 1]: segments of row k are [seg_ptr[k], seg_ptr[k+1])
+  const uint32_t *seg_row;    // [n_seg]: sorted gas index of the segment's row
   const int64_t *seg_begin;   // [n_seg]
+  const uint32_t *list = nullptr;   // sorted gas index of row k, or null (row k is gas k)
+  int64_t n_rows = -1;        // rows when list is set
+  int64_t n_seg = -1;         // segments to process; < 0: seg_ptr[N_B] read on the device
 };
 
 struct MfOut {
@@ -75,8 +81,19 @@ struct McArgs {
   double *p_total;            // may be null
   double *block_sums;         // [finish blocks][8]: sum M dv (3), dKE, scatters, clamps, band, sum P
   double *block_max;          // [finish blocks]: max p_ratio
+  // hierarchical substeps: the rows are the DM of `list` (sorted indices, n_list of them), each
+  // with its own dt = dt 2^bin (bin in caller order); the step number is read on the device;
+  // the finish also refreshes the sorted velocity copy of the particles it updates
+  const uint32_t *list = nullptr;
+  int64_t n_list = 0;
+  const uint8_t *bin = nullptr;
+  const unsigned long long *step_dev = nullptr;
+  void *v_sorted = nullptr;   // Vec<R>::v4 [N_chi] or null
+  int v_sorted_fp64 = 0;
 };
 
+// Sets the surrogate pass's shared-memory attribute (done before any graph capture).
+cudaError_t prepare_mlp_pair_rates();
 cudaError_t launch_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *row_ptr,
                                   const uint32_t *rows, SegView sv, int64_t n_seg_max, RunConst rc, MlpRun mr,
                                   float2 *rates, cudaStream_t s, int64_t *launches);

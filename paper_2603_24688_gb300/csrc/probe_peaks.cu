@@ -1,5 +1,6 @@
 // Throughput probe of the arithmetic pipes the pair kernels use: float32 FMA, float64 FMA,
-// the special-function unit (ex2), int32 multiply-add and 32-bit multiply-high (Philox).
+// the special-function unit (ex2, tanh), int32 multiply-add, 32-bit multiply-high (Philox)
+// and the warp-level bf16 tensor instruction (mma.sync m16n8k16) of the surrogate.
 // Independent chains per thread; every thread writes one word so nothing is dead code.
 // Built and run by paper_2603_24688_gb300/peaks.py; not part of libdmb.so.
 #include <cstdio>
@@ -31,6 +32,37 @@ __global__ void k_mulhi(unsigned* out, unsigned a) {
   for (int i=0;i<ITERS;i++){ x0=__umulhi(x0,a)^x0;x1=__umulhi(x1,a)^x1;x2=__umulhi(x2,a)^x2;x3=__umulhi(x3,a)^x3;}
   out[blockIdx.x*blockDim.x+threadIdx.x]=x0^x1^x2^x3;
 }
+__global__ void k_tanh(float* out, float a) {
+  float x0=threadIdx.x*1e-3f, x1=x0+1e-3f, x2=x0+2e-3f, x3=x0+3e-3f;
+  for (int i=0;i<ITERS/4;i++){
+    asm volatile("tanh.approx.f32 %0, %0;" : "+f"(x0)); asm volatile("tanh.approx.f32 %0, %0;" : "+f"(x1));
+    asm volatile("tanh.approx.f32 %0, %0;" : "+f"(x2)); asm volatile("tanh.approx.f32 %0, %0;" : "+f"(x3));
+    x0*=a; x1*=a; x2*=a; x3*=a; }
+  out[blockIdx.x*blockDim.x+threadIdx.x]=x0+x1+x2+x3;
+}
+__global__ void k_tanh2(float* out, unsigned a) {
+  unsigned x0=threadIdx.x*0x00010001u, x1=x0^0x3c003c00u, x2=x0^0x3d003d00u, x3=x0^0x3e003e00u;
+  for (int i=0;i<ITERS/4;i++){
+    asm volatile("tanh.approx.bf16x2 %0, %0;" : "+r"(x0)); asm volatile("tanh.approx.bf16x2 %0, %0;" : "+r"(x1));
+    asm volatile("tanh.approx.bf16x2 %0, %0;" : "+r"(x2)); asm volatile("tanh.approx.bf16x2 %0, %0;" : "+r"(x3));
+    x0^=a; x1^=a; x2^=a; x3^=a; }
+  out[blockIdx.x*blockDim.x+threadIdx.x]=(float)(x0^x1^x2^x3);
+}
+// 4 independent m16n8k16 bf16 accumulator chains per warp; 4096 flops per instruction
+__global__ void k_mma(float* out, unsigned a) {
+  unsigned A0=a^threadIdx.x, A1=A0*3u, A2=A0*5u, A3=A0*7u, B0=A0*11u, B1=A0*13u;
+  float c[4][4];
+  for (int k=0;k<4;k++) for (int q=0;q<4;q++) c[k][q]=0.0f;
+  for (int i=0;i<ITERS/4;i++){
+#pragma unroll
+    for (int k=0;k<4;k++)
+      asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                   : "+f"(c[k][0]), "+f"(c[k][1]), "+f"(c[k][2]), "+f"(c[k][3])
+                   : "r"(A0), "r"(A1), "r"(A2), "r"(A3), "r"(B0), "r"(B1));
+  }
+  float s=0.0f; for (int k=0;k<4;k++) for (int q=0;q<4;q++) s+=c[k][q];
+  out[blockIdx.x*blockDim.x+threadIdx.x]=s;
+}
 int main(){
   int dev=0; cudaDeviceProp p; cudaGetDeviceProperties(&p,dev);
   printf("name=%s sms=%d l2=%d smem_optin=%zu\n", p.name, p.multiProcessorCount, p.l2CacheSize, p.sharedMemPerBlockOptin);
@@ -48,6 +80,12 @@ int main(){
   cudaEventElapsedTime(&ms,e0,e1); printf("imad: %.1f Tops/s\n", 8.0*ITERS*n/ms/1e9);
   cudaEventRecord(e0); k_mulhi<<<blocks,threads>>>((unsigned*)buf,0xD2511F53u); cudaEventRecord(e1); cudaEventSynchronize(e1);
   cudaEventElapsedTime(&ms,e0,e1); printf("umulhi+xor: %.1f Tpairs/s\n", 4.0*ITERS*n/ms/1e9);
+  cudaEventRecord(e0); k_tanh<<<blocks,threads>>>((float*)buf,0.5f); cudaEventRecord(e1); cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms,e0,e1); printf("tanh.f32: %.2f Tops/s\n", 4.0*(ITERS/4)*n/ms/1e9);
+  cudaEventRecord(e0); k_tanh2<<<blocks,threads>>>((float*)buf,0x00010001u); cudaEventRecord(e1); cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms,e0,e1); printf("tanh.bf16x2: %.2f Tinstr/s (2 values each)\n", 4.0*(ITERS/4)*n/ms/1e9);
+  cudaEventRecord(e0); k_mma<<<blocks,threads>>>((float*)buf,0x3f803f80u); cudaEventRecord(e1); cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms,e0,e1); printf("mma.sync bf16 m16n8k16: %.1f TFLOP/s\n", 4096.0*4*(ITERS/4)*(n/32)/ms/1e9);
   }
   cudaError_t err=cudaGetLastError(); printf("err=%s\n", cudaGetErrorString(err));
   cudaFree(buf); return err!=cudaSuccess;

@@ -24,7 +24,8 @@ EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb
            "dmb_launch_count", "dmb_set_timing", "dmb_stage_times",
            "dmb_search_stats", "dmb_train_surrogate", "dmb_surrogate_params", "dmb_load_surrogate",
            "dmb_surrogate_infer", "dmb_surrogate_grad", "dmb_surrogate_fallbacks", "dmb_step_batched",
-           "dmb_surrogate_grad_noalloc"]
+           "dmb_surrogate_grad_noalloc", "dmb_set_bins", "dmb_substep_info", "dmb_substep", "dmb_set_graph",
+           "dmb_set_surrogate_engine", "dmb_surrogate_infer_tc"]
 
 
 class DmbError(RuntimeError):
@@ -91,6 +92,12 @@ def load(path=LIB_PATH):
         "dmb_step_batched": ([vp, c.POINTER(DM), vp, c.POINTER(Gas), vp, c.POINTER(Box), c.c_int32, u64, dbl,
                               vp], c.c_int),
         "dmb_surrogate_grad_noalloc": ([vp, vp, vp, c.c_int32, vp, c.POINTER(c.c_double)], c.c_int),
+        "dmb_set_bins": ([vp, vp, vp], c.c_int),
+        "dmb_substep_info": ([vp, u64, c.POINTER(i64)], c.c_int),
+        "dmb_substep": ([vp, c.POINTER(DM), c.POINTER(Gas), u64, dbl, vp], c.c_int),
+        "dmb_set_graph": ([vp, c.c_int], c.c_int),
+        "dmb_set_surrogate_engine": ([vp, c.c_int32], c.c_int),
+        "dmb_surrogate_infer_tc": ([vp, vp, i64, vp], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -230,6 +237,35 @@ class Context:
                                               _ptr(gas_box, torch.int32), tbl, len(boxes), int(step), float(dt),
                                               sums if want_sums else None))
         return np.array(sums[:]) if want_sums else None
+
+    def dmb_set_bins(self, dm_bin, gas_bin):
+        """dm_bin, gas_bin: CUDA uint8 tensors (caller order), kept alive by the context."""
+        import torch
+        self._bins = (dm_bin, gas_bin)
+        self._check(self.lib.dmb_set_bins(self.h, _ptr(dm_bin, torch.uint8), _ptr(gas_bin, torch.uint8)))
+
+    def dmb_substep_info(self, substep):
+        out = (ctypes.c_int64 * 5)()
+        self._check(self.lib.dmb_substep_info(self.h, int(substep), out))
+        return tuple(int(v) for v in out)
+
+    def dmb_substep(self, dm, gas, substep, dt_min, want_sums=True):
+        d, g = self.dm_struct(dm), self.gas_struct(gas)
+        sums = (ctypes.c_double * 16)()
+        self._check(self.lib.dmb_substep(self.h, ctypes.byref(d), ctypes.byref(g), int(substep), float(dt_min),
+                                         sums if want_sums else None))
+        return np.array(sums[:]) if want_sums else None
+
+    def dmb_set_surrogate_engine(self, engine):
+        self._check(self.lib.dmb_set_surrogate_engine(self.h, int(engine)))
+
+    def dmb_surrogate_infer_tc(self, X, Y):
+        import torch
+        self._check(self.lib.dmb_surrogate_infer_tc(self.h, _ptr(X, torch.float32), X.shape[0],
+                                                    _ptr(Y, torch.float32)))
+
+    def dmb_set_graph(self, on=True):
+        self._check(self.lib.dmb_set_graph(self.h, 1 if on else 0))
 
     def dmb_debug_overlap(self, inp, out):
         import torch

@@ -20,6 +20,8 @@ Workloads
              T = 1e4 K; h from the analytic local density for 32 neighbours, floored
              at the paper's 44.8 pc (Sec. 4).
   boxes      many independent periodic boxes of uneven size and parameters.
+  galaxy40M  the galaxy geometry at 32M DM + 8M gas, sigma = 3e-26 cm^2, with seeded
+             power-of-two timestep bins (timestep_bins) for hierarchical substeps.
 """
 import math
 
@@ -174,6 +176,17 @@ def boxes_workload(nbox=64, n_lo=2 ** 12, n_hi=2 ** 18, sigma_lo=1e-27, sigma_hi
                 params=params, dt=float(dt))
 
 
+def timestep_bins(n, seed, f_lo=0.01, f_hi=0.1, top=10):
+    """Seeded power-of-two timestep bins (uint8): P(bin <= v) = f_lo (f_hi / f_lo)^(v / top) for
+    v = 0 .. top, the rest in bin top + 1.  A particle in bin b is active at substep s when
+    s mod 2^b == 0, so every substep 0 < s < 2^(top+1) has between f_lo and f_hi of the
+    particles active."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(0.0, 1.0, n)
+    F = f_lo * (f_hi / f_lo) ** (np.arange(top + 1) / top)
+    return np.searchsorted(F, u, side="right").astype(np.uint8)
+
+
 def subsample(w, frac_or_n_dm, n_gas=None, seed=0):
     """A smaller workload with the same structure (random particle subsets)."""
     rng = np.random.default_rng(seed)
@@ -190,13 +203,19 @@ def subsample(w, frac_or_n_dm, n_gas=None, seed=0):
 
 
 def named(name, **kw):
-    """Workloads by name: 'box4k', 'box4k-bulk', 'galaxy1M', 'galaxy10M'."""
+    """Workloads by name: 'box4k', 'box4k-bulk', 'galaxy1M', 'galaxy10M', 'galaxy40M'."""
     if name == "box4k":
         return box_workload(**kw)
     if name == "box4k-bulk":
         return box_workload(bulk_dm=(200.0, 0.0, 0.0), **kw)
     if name == "galaxy1M":
         return galaxy_workload(1_000_000, 1_000_000, seed=SEED_BASE + 2, **kw)
+    if name == "galaxy40M":
+        kw.setdefault("sigma0_cm2", 3e-26)
+        w = galaxy_workload(32_000_000, 8_000_000, seed=SEED_BASE + 5, **kw)
+        w["dm_bin"] = timestep_bins(32_000_000, SEED_BASE + 51)
+        w["gas_bin"] = timestep_bins(8_000_000, SEED_BASE + 52)
+        return w
     if name == "galaxy10M":
         return galaxy_workload(8_000_000, 2_000_000, seed=SEED_BASE + 3, **kw)
     raise KeyError(name)

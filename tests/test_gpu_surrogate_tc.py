@@ -1,0 +1,75 @@
+"""The surrogate on the tcgen05 tensor cores (128-row tiles, accumulators in tensor memory)
+against the CPU reference of the network and against the warp-level mma.sync engine."""
+import numpy as np
+import pytest
+
+from gpu_common import device_inputs, require_gpu, torch
+from oracle import mlp as O
+from paper_2603_24688_gb300 import dmb
+from paper_2603_24688_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _ctx(n=0, w=None):
+    w = w or W.box_workload(n_dm=64, n_gas=64, n=n)
+    p = w["params"]
+    return dmb.Context(p["sigma0_cm2"], n, p["m_chi_mp"], p["v0_kms"], True, p["box"], p["seed"],
+                       rate_mode=dmb.DMB_RATE_MLP)
+
+
+@pytest.mark.parametrize("rows", [1, 200, 128 * 3 * 152 * 2 + 77])
+def test_tc_forward_matches_cpu_reference(rows):
+    rng = np.random.default_rng(5)
+    p = (rng.uniform(-1, 1, O.NPARAM) * 0.2).astype(np.float32)
+    ctx = _ctx()
+    ctx.dmb_load_surrogate(p)
+    X = rng.uniform(-1, 1, (rows, 4)).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    Yd = torch.full((rows, 2), float("nan"), dtype=torch.float32, device="cuda")
+    ctx.dmb_surrogate_infer_tc(Xd, Yd)
+    got = Yd.cpu().numpy()
+    k = min(rows, 4000)                                 # the CPU reference on a sample
+    idx = np.unique(np.concatenate([np.arange(min(rows, 300)), rng.integers(0, rows, k), [rows - 1]]))
+    ref, _ = O.forward(p.astype(np.float64), X[idx].astype(np.float64), bf16_ops=True)
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got[idx] - ref)) < 2e-3 * (1 + np.abs(ref).max())
+    # the warp-level engine evaluates the same network
+    Y2 = torch.empty_like(Yd)
+    ctx.dmb_surrogate_infer(Xd, Y2)
+    assert np.max(np.abs(got - Y2.cpu().numpy())) < 2e-3 * (1 + np.abs(ref).max())
+
+
+def test_tc_pair_rates_match_the_warp_engine():
+    rng = np.random.default_rng(6)
+    w = W.subsample(W.named("galaxy1M"), 60_000, 40_000, seed=2)
+    w["params"]["n"] = -2
+    p = w["params"]
+    ctx = dmb.Context(p["sigma0_cm2"], -2, p["m_chi_mp"], p["v0_kms"], False, p["box"], p["seed"],
+                      rate_mode=dmb.DMB_RATE_MLP)
+    ctx.dmb_train_surrogate(nsamples=1 << 18, epochs=4, seed=3)
+    dm, gas = device_inputs(w)
+    ctx.dmb_build_grid(dm, gas)
+    npairs = ctx.dmb_neighbors()
+    assert npairs > 100_000
+    nb = len(w["gas"]["h"])
+    out = {}
+    for eng in (0, 1):
+        ctx.dmb_set_surrogate_engine(eng)
+        acc = torch.empty((nb, 3), dtype=torch.float64, device="cuda")
+        dudt = torch.empty(nb, dtype=torch.float64, device="cuda")
+        ctx.dmb_meanfield_gas(acc, dudt)
+        out[eng] = (acc.cpu().numpy(), dudt.cpu().numpy(), ctx.dmb_surrogate_fallbacks())
+    a0, u0, f0 = out[0]
+    a1, u1, f1 = out[1]
+    assert f0 == f1
+    na = np.linalg.norm(a1, axis=1)
+    err = np.linalg.norm(a0 - a1, axis=1) / np.maximum(na, 1e-30)
+    assert np.all(err[na > 0] < 2e-3), err.max()
+    scale = np.abs(u1) + 1e-3 * np.abs(u1).max()
+    assert np.max(np.abs(u0 - u1) / scale) < 2e-3
