@@ -197,10 +197,140 @@ def run_reference(a):
     return 0
 
 
+def run_substeps(a, peaks, peak_kind):
+    """Hierarchical substeps of the 32M DM + 8M gas galaxy (power-of-two timestep bins, 1-10% of
+    the particles active per substep): grid and pairs once, then dmb_substep replayed from CUDA
+    graphs with the learned surrogate.  One timed step = one substep."""
+    import torch
+    from paper_2603_24688_gb300 import dmb
+    from paper_2603_24688_gb300 import workloads as W
+    w = W.named("galaxy40M", n=a.n)
+    prm = w["params"]
+    stream = torch.cuda.current_stream()
+    ctx = dmb.Context(prm["sigma0_cm2"], prm["n"], prm["m_chi_mp"], prm["v0_kms"], False, (0.0, 0.0, 0.0),
+                      prm["seed"], rate_mode=dmb.DMB_RATE_MLP, stream=stream)
+    rep = ctx.dmb_train_surrogate(nsamples=1 << 20, epochs=24, seed=11)
+    dm, gas = dmb.to_device(w["dm"]), dmb.to_device(w["gas"])
+    db = torch.from_numpy(w["dm_bin"]).cuda()
+    gb = torch.from_numpy(w["gas_bin"]).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.dmb_build_grid(dm, gas)
+    npairs = ctx.dmb_neighbors()
+    ctx.dmb_set_bins(db, gb)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    dt = w["dt"]
+    out = {}
+    first = 1                  # timed substeps 1 .. K: every bin up to nu(K) active in turn
+    nus = sorted({(s & -s).bit_length() - 1 for s in range(first, first + a.steps)})
+    for graph in (False, True):
+        ctx.dmb_set_graph(graph)
+        # warm-up: W substeps, and (graph mode) one substep of every active set the timed range
+        # uses, so that every graph is captured before the timed region
+        warm = list(range(first, first + a.warmup)) + ([1 << nu for nu in nus] if graph else [])
+        for s in warm:
+            ctx.dmb_substep(dm, gas, s, dt, want_sums=False)
+        evals = act = 0
+        for s in range(first, first + a.steps):
+            info = ctx.dmb_substep_info(s)
+            act += info[0] + info[1]
+            evals += 0.5 * (info[3] + info[4])
+        l0 = ctx.dmb_launch_count()
+        clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]) if graph else None
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for s in range(first, first + a.steps):
+            ctx.dmb_substep(dm, gas, s, dt, want_sums=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[graph] = dict(ms=ms, evals=evals, active=act, launches=ctx.dmb_launch_count() - l0,
+                          clocks=clocks.stop() if clocks else None, first=first)
+    g = out[True]
+    line = {"metric": "pair_interactions_per_s", "value": g["evals"] / (g["ms"] * 1e-3), "unit": "pairs/s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": g["ms"] / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 sums",
+            "data": "synthetic",
+            "config": {"workload": f"galaxy40M: 32000000 DM + 8000000 gas, sigma = 3e-26 cm^2 (v/100 km/s)^{a.n}, "
+                                   f"power-of-two timestep bins, substeps {g['first']}..{g['first'] + a.steps - 1} "
+                                   f"(graph replay) after the grid and pairs were built once",
+                       "rate_provider": "learned surrogate (tcgen05 tensor cores)", "pairs_full": npairs,
+                       "l2": "state (~3 GB) larger than L2; no flush", "parallelism": "replicas x1"},
+            "particles_stepped_per_s": g["active"] / (g["ms"] * 1e-3),
+            "active_fraction": g["active"] / (a.steps * (len(w["dm"]["h"]) + len(w["gas"]["h"]))),
+            "eager": {"ms_per_step": out[False]["ms"] / a.steps,
+                      "pairs_per_s": out[False]["evals"] / (out[False]["ms"] * 1e-3)},
+            "setup_s": setup_s, "gpu_launches": int(g["launches"]), "clocks": g["clocks"],
+            "surrogate_val_mean_rel_err": [float(rep[3]), float(rep[4])], "peak_kind": peak_kind}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def run_boxes(a, peaks, peak_kind):
+    """The batched parameter scan: 64 independent periodic boxes (particle counts, sigma0, m_chi
+    and T drawn per box) stepped together by dmb_step_batched; one timed step = one batched step
+    (grid, pairs, mean field, Monte Carlo, kicks of all boxes)."""
+    import torch
+    from paper_2603_24688_gb300 import dmb
+    from paper_2603_24688_gb300 import workloads as W
+    w = W.boxes_workload(n=a.n)
+    prm = w["params"]
+    stream = torch.cuda.current_stream()
+    ctx = dmb.Context(prm["sigma0_cm2"], prm["n"], prm["m_chi_mp"], prm["v0_kms"], True, tuple(prm["box"]),
+                      prm["seed"], stream=stream)
+    dm, gas = dmb.to_device(w["dm"]), dmb.to_device(w["gas"])
+    dbx = torch.from_numpy(w["dm_box"].view(np.int32)).cuda()
+    gbx = torch.from_numpy(w["gas_box"].view(np.int32)).cuda()
+    step = 0
+    sums = None
+    for _ in range(a.warmup):
+        sums = ctx.dmb_step_batched(dm, dbx, gas, gbx, w["boxes"], step, w["dt"])
+        step += 1
+    npairs = int(sums[12])
+    ctx.dmb_set_timing(True)
+    l0 = ctx.dmb_launch_count()
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        ctx.dmb_step_batched(dm, dbx, gas, gbx, w["boxes"], step, w["dt"], want_sums=False)
+        step += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stage_ms, nsteps = ctx.dmb_stage_times()
+    clk = clocks.stop()
+    nd, ng = len(w["dm"]["h"]), len(w["gas"]["h"])
+    names = ["grid", "search", "meanfield", "mc", "kick"]
+    line = {"metric": "pair_interactions_per_s", "value": npairs * a.steps / (ms * 1e-3), "unit": "pairs/s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 sums",
+            "data": "synthetic",
+            "config": {"workload": f"boxes64: 64 periodic boxes, {nd} DM + {ng} gas in total, per-box sigma0, "
+                                   f"m_chi, T and counts log-uniform", "pairs_per_step": npairs,
+                       "parallelism": "replicas x1"},
+            "particles_stepped_per_s": (nd + ng) * a.steps / (ms * 1e-3),
+            "stage_ms": {n: float(v) / max(nsteps, 1) for n, v in zip(names, stage_ms[:5])},
+            "gpu_launches": int(ctx.dmb_launch_count() - l0), "clocks": clk, "peak_kind": peak_kind}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload in ("galaxy40M", "boxes64"):
+        import torch
+        from paper_2603_24688_gb300 import build
+        build.build()
+        peaks, peak_kind = load_peaks()
+        return (run_substeps if a.workload == "galaxy40M" else run_boxes)(a, peaks, peak_kind)
     import torch
     from paper_2603_24688_gb300 import build, dmb
 

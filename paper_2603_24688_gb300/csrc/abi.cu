@@ -65,7 +65,7 @@ struct dmb_ctx {
   DevBuf mlp_p, mlp_m, mlp_v, mlp_w2, mlp_w3, mlp_w2t, mlp_w3t, mlp_fallback, mlp_rates;
   bool mlp_ready = false;
   int mlp_engine = 0;            // 0: tcgen05 tiles (mlp_tc.cu), 1: warp-level mma.sync pass
-  DevBuf tc_tiles;               // first row of every 128-pair tile
+  DevBuf tc_tiles;               // row of every pair of the surrogate's pass
   // batched boxes (dmb_step_batched): caller box index arrays of the current build and tables
   const uint32_t *dm_box = nullptr, *gas_box = nullptr;
   int nbox = 0;
@@ -74,6 +74,8 @@ struct dmb_ctx {
   std::vector<int> mlp_n;        // power-law indices the network was trained for
   double mlp_box[6] = {-2.0, 2.0, -3.0, 2.0, -0.30102999566398120, 1.0};   // log10 ranges of s, tau, m_chi
   int64_t n_seg_max = 0;
+  int seg_len = MF_SEG, act_seg_len = MF_SEG;   // segment lengths the two segment tables were built with
+  Shapes shp;                                   // launch shapes (defaults or dmb_autotune's choice)
   DevBuf mf_acc, mf_dudt, e_exp, mc_blocks, mc_max, kick_blocks, sums;
   DevBuf scratch_vel, search_stats;
   uint32_t *h_status = nullptr;   // pinned
@@ -324,7 +326,8 @@ dmb_status search_stage1_count(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, S
      "leaf pairs (count)");
   CK(exclusive_scan_u32_i64(ptr<uint32_t>(sb.item_cnt), ptr<int64_t>(sb.item_ptr), nleaf, ptr<int64_t>(ctx->scan_tmp),
                             s, L), "scan");
-  CK(launch_unit_counts(ptr<int64_t>(sb.item_ptr), nleaf, ptr<uint32_t>(sb.unit_cnt_leaf), s, L), "unit counts");
+  CK(launch_unit_counts(ptr<int64_t>(sb.item_ptr), nleaf, ctx->shp.unit, ptr<uint32_t>(sb.unit_cnt_leaf), s, L),
+     "unit counts");
   CK(exclusive_scan_u32_i64(ptr<uint32_t>(sb.unit_cnt_leaf), ptr<int64_t>(sb.unit_ptr), nleaf,
                             ptr<int64_t>(ctx->scan_tmp), s, L), "scan");
   return DMB_OK;
@@ -343,10 +346,10 @@ dmb_status search_stage2_count(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, S
   uint32_t *status = ptr<uint32_t>(ctx->status);
   CK(launch_leaf_pairs<R>(Q, O, ctx->bx, fr, true, nullptr, ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), status,
                           nullptr, s, L), "leaf pairs (emit)");
-  CK(launch_unit_map(ptr<int64_t>(sb.item_ptr), ptr<int64_t>(sb.unit_ptr), nleaf, ptr<uint32_t>(sb.unit_leaf),
+  CK(launch_unit_map(ptr<int64_t>(sb.item_ptr), ptr<int64_t>(sb.unit_ptr), nleaf, ctx->shp.unit, ptr<uint32_t>(sb.unit_leaf),
                      ptr<int64_t>(sb.unit_item0), s, L), "unit map");
   CK(launch_tile<R>(Q, O, ctx->bx, fr, false, ptr<uint32_t>(sb.unit_leaf), ptr<int64_t>(sb.unit_item0),
-                    ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), sb.n_units, ptr<uint32_t>(sb.unit_cnt), nullptr,
+                    ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), sb.n_units, ctx->shp.unit, ptr<uint32_t>(sb.unit_cnt), nullptr,
                     nullptr, status, stats, s, L), "tile (count)");
   CK(launch_unit_prefix(ptr<int64_t>(sb.unit_ptr), nleaf, Q.n, ptr<uint32_t>(sb.unit_cnt), ptr<uint32_t>(sb.counts), s,
                         L), "unit prefix");
@@ -360,7 +363,7 @@ dmb_status search_stage2_emit(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, Sp
   if (!ensure(sb.rows, (size_t)sb.n_pairs * 4)) return fail(ctx, DMB_ERR_OOM, "device allocation failed for pair lists");
   CK(launch_tile<R>(Q, O, ctx->bx, ptr<Frame>(ctx->frame), true, ptr<uint32_t>(sb.unit_leaf),
                     ptr<int64_t>(sb.unit_item0), ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), sb.n_units,
-                    ptr<uint32_t>(sb.unit_cnt), ptr<int64_t>(sb.row_ptr), ptr<uint32_t>(sb.rows),
+                    ctx->shp.unit, ptr<uint32_t>(sb.unit_cnt), ptr<int64_t>(sb.row_ptr), ptr<uint32_t>(sb.rows),
                     ptr<uint32_t>(ctx->status), nullptr, ctx->stream, &ctx->launches), "tile (emit)");
   return DMB_OK;
 }
@@ -384,20 +387,22 @@ dmb_status transpose_to_dm(dmb_ctx *ctx, const SearchBufs &sg, SearchBufs &sd, i
   return DMB_OK;
 }
 
-// Mean-field segments of the gas rows (upper bound N_B + pairs / MF_SEG, no readback).
+// Mean-field segments of the gas rows (upper bound N_B + pairs / seg, no readback).
 dmb_status build_segments(dmb_ctx *ctx, const SearchBufs &sg, int64_t ng) {
   cudaStream_t s = ctx->stream;
   int64_t *L = &ctx->launches;
-  const int64_t nmax = ng + sg.n_pairs / MF_SEG + 1;
+  const int seg = ctx->shp.seg;
+  const int64_t nmax = ng + sg.n_pairs / seg + 1;
   if (!ensure(ctx->seg_cnt, (size_t)(ng + 1) * 4) || !ensure(ctx->seg_ptr, (size_t)(ng + 1) * 8) ||
       !ensure(ctx->seg_row, (size_t)nmax * 4) || !ensure(ctx->seg_begin, (size_t)nmax * 8))
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for mean-field segments");
-  CK(launch_seg_counts(ptr<int64_t>(sg.row_ptr), ng, MF_SEG, ptr<uint32_t>(ctx->seg_cnt), s, L), "segments");
+  CK(launch_seg_counts(ptr<int64_t>(sg.row_ptr), ng, seg, ptr<uint32_t>(ctx->seg_cnt), s, L), "segments");
   CK(exclusive_scan_u32_i64(ptr<uint32_t>(ctx->seg_cnt), ptr<int64_t>(ctx->seg_ptr), ng, ptr<int64_t>(ctx->scan_tmp),
                             s, L), "scan");
-  CK(launch_seg_map(ptr<int64_t>(sg.row_ptr), ptr<int64_t>(ctx->seg_ptr), ng, MF_SEG, ptr<uint32_t>(ctx->seg_row),
+  CK(launch_seg_map(ptr<int64_t>(sg.row_ptr), ptr<int64_t>(ctx->seg_ptr), ng, seg, ptr<uint32_t>(ctx->seg_row),
                     ptr<int64_t>(ctx->seg_begin), s, L), "segment map");
   ctx->n_seg_max = nmax;
+  ctx->seg_len = seg;
   return DMB_OK;
 }
 
@@ -517,8 +522,9 @@ dmb_status surrogate_rates(dmb_ctx *ctx, const MlpRun &mr, const SegView &sv, co
     a.rates = ptr<float2>(ctx->mlp_rates);
     a.fallback_count = mr.fallback_count;
     a.status = ptr<uint32_t>(ctx->status);
-    if (!ensure(ctx->tc_tiles, (size_t)((n_q + 127) / 128) * 8)) return fail(ctx, DMB_ERR_OOM, "surrogate tiles");
-    CK(mlp_tc_pair_rates(a, ptr<int64_t>(ctx->tc_tiles), s, &ctx->launches), "surrogate rates (tensor cores)");
+    if (!ensure(ctx->tc_tiles, (size_t)n_q * 4)) return fail(ctx, DMB_ERR_OOM, "surrogate pair rows");
+    CK(mlp_tc_pair_rates(a, ptr<uint32_t>(ctx->tc_tiles), ctx->shp.tc_wg, s, &ctx->launches),
+       "surrogate rates (tensor cores)");
   } else {
     CK(launch_mlp_pair_rates(view<float>(ctx->gas, ctx->nbox > 0), view<float>(ctx->dm, ctx->nbox > 0),
                              ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv,
@@ -540,6 +546,7 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
   sv.seg_ptr = ptr<int64_t>(ctx->seg_ptr);
   sv.seg_row = ptr<uint32_t>(ctx->seg_row);
   sv.seg_begin = ptr<int64_t>(ctx->seg_begin);
+  sv.seg_len = ctx->seg_len;
   MlpRun mr = {};
   if (ctx->rc.rate_mode == DMB_RATE_MLP) {
     if (!ctx->mlp_ready) return fail(ctx, DMB_ERR_STATE, "surrogate rate provider selected but no trained network");
@@ -562,8 +569,8 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
     }
   }
   CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv,
-                         ctx->n_seg_max, ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr, ctx->stream,
-                         &ctx->launches), "meanfield");
+                         ctx->n_seg_max, ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr,
+                         ctx->shp.mf_bps, ctx->stream, &ctx->launches), "meanfield");
   return DMB_OK;
 }
 
@@ -596,8 +603,8 @@ dmb_status mc_impl(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, uint
   if (!ensure(ctx->mc_rec, (size_t)D.n * sizeof(McRec))) return fail(ctx, DMB_ERR_OOM, "MC scratch");
   if (D.n > 0)
     CK(launch_mc<R>(D, G, ctx->bx, ptr<int64_t>(ctx->sd.row_ptr), ptr<uint32_t>(ctx->sd.rows),
-                    ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), ptr<McRec>(ctx->mc_rec), nb, ctx->stream,
-                    &ctx->launches), "mc");
+                    ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), ptr<McRec>(ctx->mc_rec), nb,
+                    ctx->shp.mc_bps, ctx->stream, &ctx->launches), "mc");
   return DMB_OK;
 }
 
@@ -655,7 +662,8 @@ dmb_status set_bins_impl(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas
     CK(launch_bin_bounds(ptr<uint64_t>(ctx->bin_keys), n, start + k * (DMB_NBINS + 1), s, L), "bin bounds");
   }
   // gas rows: pairs and segments in list order; DM rows: pairs in list order
-  CK(launch_list_counts(ptr<uint32_t>(ctx->act_gas), ng, ptr<int64_t>(ctx->sg.row_ptr), MF_SEG,
+  ctx->act_seg_len = ctx->shp.seg;
+  CK(launch_list_counts(ptr<uint32_t>(ctx->act_gas), ng, ptr<int64_t>(ctx->sg.row_ptr), ctx->act_seg_len,
                         ptr<uint32_t>(ctx->act_len), ptr<uint32_t>(ctx->act_segs), s, L), "list counts");
   CK(exclusive_scan_u32_i64(ptr<uint32_t>(ctx->act_segs), ptr<int64_t>(ctx->act_seg_ptr), ng,
                             ptr<int64_t>(ctx->scan_tmp), s, L), "scan");
@@ -677,7 +685,7 @@ dmb_status set_bins_impl(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas
       !ensure(ctx->act_seg_begin, (size_t)ctx->act_seg_total * 8))
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for the substep segments");
   CK(launch_list_seg_map(ptr<uint32_t>(ctx->act_gas), ng, ptr<int64_t>(ctx->sg.row_ptr),
-                         ptr<int64_t>(ctx->act_seg_ptr), MF_SEG, ptr<uint32_t>(ctx->act_seg_row),
+                         ptr<int64_t>(ctx->act_seg_ptr), ctx->act_seg_len, ptr<uint32_t>(ctx->act_seg_row),
                          ptr<int64_t>(ctx->act_seg_begin), s, L), "segment map");
   // every buffer a substep touches, at its largest size: a substep (and its capture) allocates nothing
   ok = ensure(ctx->mf_part, (size_t)ctx->act_seg_total * 6 * sizeof(R)) && ensure(ctx->mf_acc, (size_t)ng * 24) &&
@@ -690,8 +698,8 @@ dmb_status set_bins_impl(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas
   if (ctx->rc.rate_mode == DMB_RATE_MLP) {
     CK(prepare_mlp_pair_rates(), "surrogate kernel attributes");
     CK(mlp_tc_prepare(), "surrogate kernel attributes");
-    if (!ensure(ctx->tc_tiles, (size_t)((ctx->bin_tab[3][DMB_NBINS] + 127) / 128) * 8 + 8))
-      return fail(ctx, DMB_ERR_OOM, "surrogate tiles");
+    if (!ensure(ctx->tc_tiles, (size_t)ctx->bin_tab[3][DMB_NBINS] * 4 + 16))
+      return fail(ctx, DMB_ERR_OOM, "surrogate pair rows");
   }
   CK(cudaStreamSynchronize(s), "synchronise");
   ctx->dm_bin = dm_bin;
@@ -714,6 +722,7 @@ dmb_status substep_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int 
   sv.seg_ptr = ptr<int64_t>(ctx->act_seg_ptr);
   sv.seg_row = ptr<uint32_t>(ctx->act_seg_row);
   sv.seg_begin = ptr<int64_t>(ctx->act_seg_begin);
+  sv.seg_len = ctx->act_seg_len;
   sv.list = ptr<uint32_t>(ctx->act_gas);
   sv.n_rows = nga;
   sv.n_seg = nseg;
@@ -734,7 +743,8 @@ dmb_status substep_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int 
   }
   if (nga > 0)
     CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv, nseg,
-                           ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr, s, L), "meanfield");
+                           ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr, ctx->shp.mf_bps, s, L),
+       "meanfield");
   // Monte Carlo of the active DM against all their gas partners, each with its own dt
   const int nb = mc_blocks_for(nda);
   McArgs a;
@@ -758,7 +768,8 @@ dmb_status substep_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int 
   a.v_sorted_fp64 = ctx->p.fp64 ? 1 : 0;
   if (nda > 0)
     CK(launch_mc<R>(D, G, ctx->bx, ptr<int64_t>(ctx->sd.row_ptr), ptr<uint32_t>(ctx->sd.rows),
-                    ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), ptr<McRec>(ctx->mc_rec), nb, s, L), "mc");
+                    ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), ptr<McRec>(ctx->mc_rec), nb,
+                    ctx->shp.mc_bps, s, L), "mc");
   // kick of the active gas (refreshing its sorted copies) and the sums
   const int kb = 152 * 4;
   CK(launch_kick_gas_list<R>(const_cast<double *>(gas->vel), const_cast<double *>(gas->T), gas->mu, gas->mass,
@@ -1173,6 +1184,160 @@ dmb_status dmb_substep(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint6
   return DMB_OK;
 }
 
+}  // extern "C"
+
+// ---- autotuner of the launch shapes ----------------------------------------------------------
+static dmb_status check_shapes(dmb_ctx *ctx, const int32_t *v) {
+  if (v[0] < 4 || v[0] > 1024 || v[1] < 128 || v[1] > 65536 || v[2] < 1 || v[2] > 64 || v[3] < 1 || v[3] > 64 ||
+      (v[4] != 2 && v[4] != 3))
+    return fail(ctx, DMB_ERR_ARG, "shapes out of range: unit [4, 1024], seg [128, 65536], blocks per SM [1, 64], "
+                                  "surrogate warpgroups 2 or 3");
+  return DMB_OK;
+}
+
+static void set_shapes(dmb_ctx *ctx, const int32_t *v) {
+  ctx->shp.unit = v[0];
+  ctx->shp.seg = v[1];
+  ctx->shp.mf_bps = v[2];
+  ctx->shp.mc_bps = v[3];
+  ctx->shp.tc_wg = v[4];
+  invalidate_substeps(ctx);   // substep tables and graphs were built with the old shapes
+  ctx->pairs_ready = false;   // the search units and mean-field segments follow the shapes
+}
+
+static void get_shapes(const dmb_ctx *ctx, int32_t *v) {
+  v[0] = ctx->shp.unit;
+  v[1] = ctx->shp.seg;
+  v[2] = ctx->shp.mf_bps;
+  v[3] = ctx->shp.mc_bps;
+  v[4] = ctx->shp.tc_wg;
+}
+
+// device time of one call of f (ms, events on the context stream); the call runs twice and the
+// second (warm) run is the one timed
+template <typename F>
+static dmb_status time_call(dmb_ctx *ctx, cudaEvent_t e0, cudaEvent_t e1, F f, float *ms) {
+  dmb_status st;
+  if ((st = f()) != DMB_OK) return st;
+  CK(cudaEventRecord(e0, ctx->stream), "event");
+  if ((st = f()) != DMB_OK) return st;
+  CK(cudaEventRecord(e1, ctx->stream), "event");
+  CK(cudaEventSynchronize(e1), "event sync");
+  CK(cudaEventElapsedTime(ms, e0, e1), "event time");
+  return DMB_OK;
+}
+
+template <typename R>
+static dmb_status autotune_impl(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, cudaEvent_t e0, cudaEvent_t e1,
+                                double *report) {
+  dmb_status st;
+  float ms = 0.f;
+  int k = 0;
+  // 1. search work units (target leaves per unit): neighbours on the built grid
+  if ((st = build_grid_checked(ctx, dm, gas)) != DMB_OK) return st;
+  float best = 1e30f;
+  int best_unit = ctx->shp.unit;
+  for (int unit : {16, 32, 64, 128}) {
+    ctx->shp.unit = unit;
+    if ((st = time_call(ctx, e0, e1, [&]() { return neighbors_impl<R>(ctx); }, &ms)) != DMB_OK) return st;
+    if (report) report[k++] = ms;
+    if (ms < best) { best = ms; best_unit = unit; }
+  }
+  ctx->shp.unit = best_unit;
+  if ((st = neighbors_impl<R>(ctx)) != DMB_OK) return st;
+  // 2. mean field: segment length x blocks per SM (and the surrogate's warpgroups)
+  const int64_t ng = gas->n, nd = dm->n;
+  if (!ensure(ctx->mf_acc, ng * 24) || !ensure(ctx->mf_dudt, ng * 8) || !ensure(ctx->e_exp, ng * 8) ||
+      !ensure(ctx->scratch_vel, nd * 24 + 8))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for autotuner scratch");
+  auto mf = [&]() {
+    return meanfield_impl<R>(ctx, ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp));
+  };
+  best = 1e30f;
+  int best_seg = ctx->shp.seg, best_mf = ctx->shp.mf_bps;
+  for (int seg : {512, 1024, 2048, 4096}) {
+    ctx->shp.seg = seg;
+    if ((st = build_segments(ctx, ctx->sg, ng)) != DMB_OK) return st;
+    for (int bps : {8, 16, 32}) {
+      ctx->shp.mf_bps = bps;
+      if ((st = time_call(ctx, e0, e1, mf, &ms)) != DMB_OK) return st;
+      if (report) report[k++] = ms;
+      if (ms < best) { best = ms; best_seg = seg; best_mf = bps; }
+    }
+  }
+  ctx->shp.seg = best_seg;
+  ctx->shp.mf_bps = best_mf;
+  if ((st = build_segments(ctx, ctx->sg, ng)) != DMB_OK) return st;
+  if (ctx->rc.rate_mode == DMB_RATE_MLP && sizeof(R) == 4 && ctx->mlp_ready && ctx->mlp_engine == 0) {
+    best = 1e30f;
+    int best_wg = ctx->shp.tc_wg;
+    for (int wg : {2, 3}) {
+      ctx->shp.tc_wg = wg;
+      if ((st = time_call(ctx, e0, e1, mf, &ms)) != DMB_OK) return st;
+      if (report) report[k++] = ms;
+      if (ms < best) { best = ms; best_wg = wg; }
+    }
+    ctx->shp.tc_wg = best_wg;
+  }
+  // 3. Monte Carlo blocks per SM (the caller's velocities are read, the scratch written)
+  best = 1e30f;
+  int best_mc = ctx->shp.mc_bps;
+  for (int bps : {4, 8, 16, 32}) {
+    ctx->shp.mc_bps = bps;
+    if ((st = time_call(ctx, e0, e1, [&]() {
+           return mc_impl<R>(ctx, 0, 0.0, ptr<double>(ctx->scratch_vel), nullptr, nullptr, nullptr, nullptr);
+         }, &ms)) != DMB_OK)
+      return st;
+    if (report) report[k++] = ms;
+    if (ms < best) { best = ms; best_mc = bps; }
+  }
+  ctx->shp.mc_bps = best_mc;
+  return check_status(ctx);
+}
+
+extern "C" {
+
+dmb_status dmb_autotune(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int32_t *shapes_out, double *report) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  dmb_status st;
+  if ((st = check_dm(ctx, dm)) != DMB_OK || (st = check_gas(ctx, gas)) != DMB_OK) return st;
+  if (ctx->nbox > 0) return fail(ctx, DMB_ERR_ARG, "autotune a single-box context");
+  if (ctx->rc.rate_mode == DMB_RATE_MLP && !ctx->mlp_ready)
+    return fail(ctx, DMB_ERR_STATE, "surrogate rate provider selected but no trained network");
+  invalidate_substeps(ctx);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0), "event create");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(ctx, DMB_ERR_CUDA, "event create");
+  }
+  const bool timing = ctx->timing;
+  ctx->timing = false;
+  st = ctx->p.fp64 ? autotune_impl<double>(ctx, dm, gas, e0, e1, report)
+                   : autotune_impl<float>(ctx, dm, gas, e0, e1, report);
+  ctx->timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DMB_OK) return st;
+  if (shapes_out) get_shapes(ctx, shapes_out);
+  return DMB_OK;
+}
+
+dmb_status dmb_set_shapes(dmb_ctx *ctx, const int32_t *shapes) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!shapes) return fail(ctx, DMB_ERR_ARG, "shapes is NULL");
+  dmb_status st;
+  if ((st = check_shapes(ctx, shapes)) != DMB_OK) return st;
+  set_shapes(ctx, shapes);
+  return DMB_OK;
+}
+
+dmb_status dmb_get_shapes(dmb_ctx *ctx, int32_t *shapes_out) {
+  if (!ctx || !shapes_out) return fail(ctx, DMB_ERR_ARG, "NULL argument");
+  get_shapes(ctx, shapes_out);
+  return DMB_OK;
+}
+
 dmb_status dmb_set_timing(dmb_ctx *ctx, int on) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
   if (on && !ctx->ev[0]) {
@@ -1389,7 +1554,7 @@ dmb_status dmb_surrogate_infer_tc(dmb_ctx *ctx, const float *X, int64_t n, float
   a.X = X;
   a.Y = Y;
   a.status = ptr<uint32_t>(ctx->status);
-  CK(mlp_tc_infer(a, ctx->stream, &ctx->launches), "surrogate inference (tensor cores)");
+  CK(mlp_tc_infer(a, ctx->shp.tc_wg, ctx->stream, &ctx->launches), "surrogate inference (tensor cores)");
   return check_status(ctx);
 }
 

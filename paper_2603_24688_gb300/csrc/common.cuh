@@ -79,6 +79,20 @@ struct BoxSplit {
   }
 };
 
+// Geometry of a launch, fixed at compile time so that the open and single-box paths carry no
+// per-box data: open (no periodicity), one periodic box, or batched periodic boxes.
+enum { GEOM_OPEN = 0, GEOM_BOX = 1, GEOM_BOXES = 2 };
+
+template <int GEOM>
+__device__ __forceinline__ BoxSide box_side(const BoxSplit &bx, int box) {
+  if (GEOM == GEOM_BOXES) return bx.boxes[box];
+  BoxSide s;
+  for (int k = 0; k < 3; ++k) { s.Lhi[k] = bx.Lhi[k]; s.Llo[k] = bx.Llo[k]; s.L[k] = bx.L[k]; }
+  return s;
+}
+
+inline int geom_of(const BoxSplit &bx) { return !bx.periodic ? GEOM_OPEN : (bx.boxes ? GEOM_BOXES : GEOM_BOX); }
+
 // Canonical pair displacement x_a - x_b (minimum image in the pair's periodic box when
 // periodic), identical bits whichever kernel computes it and antisymmetric in (a, b).
 template <typename R>

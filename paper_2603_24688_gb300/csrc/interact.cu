@@ -12,7 +12,7 @@
 // the float64 results (and the perm scatter to caller order) are formed by
 // k_meanfield_finish with one thread per gas particle, where float64 instructions cover
 // 32 particles each (GB300 runs float64 at 1/64 of the float32 rate).
-template <typename R, int RM>
+template <typename R, int RM, int GEOM>
 __global__ void __launch_bounds__(MF_WARPS * 32)
 k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__restrict__ row_ptr,
             const uint32_t *__restrict__ rows, SegView sv, const float4 *__restrict__ gtab, RunConst rc,
@@ -26,11 +26,11 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
   const int64_t n_seg = sv.n_seg >= 0 ? sv.n_seg : sv.seg_ptr[G.n];
   for (int64_t u = (int64_t)blockIdx.x * MF_WARPS + (threadIdx.x >> 5); u < n_seg; u += nwarps) {
     const int64_t j = sv.seg_row[u];
-    const int64_t rs = sv.seg_begin[u], re = min(rs + (int64_t)MF_SEG, row_ptr[j + 1]);
+    const int64_t rs = sv.seg_begin[u], re = min(rs + (int64_t)sv.seg_len, row_ptr[j + 1]);
     R sx = 0, sy = 0, sz = 0, sw2 = 0, sb = 0, svw = 0;
     if (re > rs) {
       const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j];
-      const BoxSide side = bx.side(G.bid != nullptr ? (int)G.bid[j] : 0);
+      const BoxSide side = box_side<GEOM>(bx, GEOM == GEOM_BOXES ? (int)G.bid[j] : 0);
       const R sig = Vj.w;
       const bool hot = sig > (R)0;
       const R inv2s2 = hot ? (R)0.5 / (sig * sig) : (R)0;
@@ -41,7 +41,7 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
         const uint32_t i = rows[valid ? p : rs];
         const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
         R dx, dy, dz;
-        pair_dx<R>(Pi, Li, Pj, Lj, bx.periodic, side, dx, dy, dz);
+        pair_dx<R>(Pi, Li, Pj, Lj, GEOM != GEOM_OPEN, side, dx, dy, dz);
         const R d = sqrt_t(dist2_rn<R>(dx, dy, dz));
         const R g = overlap_g<R>(gtab, d, Pi.w, Pj.w);
         const R wx = Vi.x - Vj.x, wy = Vi.y - Vj.y, wz = Vi.z - Vj.z;
@@ -125,7 +125,7 @@ k_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *__re
   unsigned fallback = 0;
   for (int64_t u = (int64_t)blockIdx.x * MF_WARPS + (threadIdx.x >> 5); u < n_seg; u += nwarps) {
     const int64_t j = sv.seg_row[u];
-    const int64_t rs = sv.seg_begin[u], re = min(rs + (int64_t)MF_SEG, row_ptr[j + 1]);
+    const int64_t rs = sv.seg_begin[u], re = min(rs + (int64_t)sv.seg_len, row_ptr[j + 1]);
     if (re <= rs) continue;
     const float4 Vj = G.V[j];
     const float sig = Vj.w;
@@ -239,21 +239,27 @@ __global__ void k_meanfield_finish(SpeciesView<R> G, SegView sv, const R *__rest
 template <typename R>
 cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *row_ptr,
                              const uint32_t *rows, SegView sv, int64_t n_seg_max, const float4 *gtab, RunConst rc,
-                             MfOut out, R *part, MlpRun mr, cudaStream_t s, int64_t *launches) {
+                             MfOut out, R *part, MlpRun mr, int blocks_per_sm, cudaStream_t s, int64_t *launches) {
   if (G.n <= 0) return cudaSuccess;
   int64_t blocks = (n_seg_max + MF_WARPS - 1) / MF_WARPS;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > 152 * (int64_t)blocks_per_sm) blocks = 152 * (int64_t)blocks_per_sm;
   if (blocks < 1) blocks = 1;
-  if (rc.rate_mode == DMB_RATE_QUAD) {
-    k_meanfield<R, DMB_RATE_QUAD><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc,
-                                                                              part, mr);
-  } else if (rc.rate_mode == DMB_RATE_MLP) {
-    k_meanfield<R, DMB_RATE_MLP><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc,
-                                                                             part, mr);
-  } else {
-    k_meanfield<R, DMB_RATE_CLOSED><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc,
-                                                                                part, mr);
+#define MF(RM, G_) k_meanfield<R, RM, G_><<<(unsigned)blocks, MF_WARPS * 32, 0, s>>>(G, D, bx, row_ptr, rows, sv, gtab, rc, part, mr)
+#define MF_GEOM(RM)                                       \
+  switch (geom_of(bx)) {                                  \
+    case GEOM_OPEN: MF(RM, GEOM_OPEN); break;             \
+    case GEOM_BOX: MF(RM, GEOM_BOX); break;               \
+    default: MF(RM, GEOM_BOXES); break;                   \
   }
+  if (rc.rate_mode == DMB_RATE_QUAD) {
+    MF_GEOM(DMB_RATE_QUAD)
+  } else if (rc.rate_mode == DMB_RATE_MLP) {
+    MF_GEOM(DMB_RATE_MLP)
+  } else {
+    MF_GEOM(DMB_RATE_CLOSED)
+  }
+#undef MF_GEOM
+#undef MF
   const int64_t nfin = sv.list ? sv.n_rows : G.n;
   if (nfin > 0) k_meanfield_finish<R><<<(unsigned)((nfin + 255) / 256), 256, 0, s>>>(G, sv, part, out);
   if (launches) *launches += 2;
@@ -261,10 +267,10 @@ cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, co
 }
 template cudaError_t launch_meanfield<float>(SpeciesView<float>, SpeciesView<float>, BoxSplit, const int64_t *,
                                              const uint32_t *, SegView, int64_t, const float4 *, RunConst, MfOut,
-                                             float *, MlpRun, cudaStream_t, int64_t *);
+                                             float *, MlpRun, int, cudaStream_t, int64_t *);
 template cudaError_t launch_meanfield<double>(SpeciesView<double>, SpeciesView<double>, BoxSplit, const int64_t *,
                                               const uint32_t *, SegView, int64_t, const float4 *, RunConst, MfOut,
-                                              double *, MlpRun, cudaStream_t, int64_t *);
+                                              double *, MlpRun, int, cudaStream_t, int64_t *);
 
 // ---- Monte Carlo: one warp per DM particle ---------------------------------------------
 // The sampled partner velocity v^B_ij = V_j + varsigma_j z (z from the pair's Philox block)
@@ -308,8 +314,8 @@ __device__ __forceinline__ U128 u128_shr20(U128 a) {
 }
 __device__ __forceinline__ bool near_rel(U128 a, U128 b, U128 c) { return !u128_lt(u128_shr20(c), u128_absdiff(a, b)); }
 
-template <typename R>
-__global__ void __launch_bounds__(MC_WARPS * 32)
+template <typename R, int GEOM>
+__global__ void __launch_bounds__(MC_WARPS * 32, sizeof(R) == 4 ? 4 : 1)
 k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict__ row_ptr,
      const uint32_t *__restrict__ rows, const float4 *__restrict__ gtab, RunConst rc, McArgs a,
      R *__restrict__ pcache, McRec *__restrict__ rec) {
@@ -321,9 +327,11 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
   const R inv_v0 = (R)(1.0 / rc.v0);
   const unsigned long long step = a.step_dev ? *a.step_dev : a.step;
   const int64_t nrows = a.list ? a.n_list : D.n;
+  const R dt0 = (R)a.dt;
   for (int64_t k = (int64_t)blockIdx.x * MC_WARPS + wib; k < nrows; k += nwarps) {
     const int64_t i = a.list ? (int64_t)a.list[k] : k;
-    const R dt = a.bin ? (R)ldexp(a.dt, (int)a.bin[D.perm[i]]) : (R)a.dt;   // dt_i = 2^bin dt
+    // dt_i = 2^bin dt: a power-of-two scaling, exact in the pair precision
+    const R dt = a.bin ? dt0 * (R)(1ull << a.bin[D.perm[i]]) : dt0;
     const int64_t rs = row_ptr[i], re = row_ptr[i + 1];
     if (re == rs) {                       // no gas partner: nothing can happen
       if (lane == 0) {
@@ -336,14 +344,14 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
     }
     const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
     const uint32_t id_i = D.id[i];
-    const BoxSide side = bx.side(D.bid != nullptr ? (int)D.bid[i] : 0);
+    const BoxSide side = box_side<GEOM>(bx, GEOM == GEOM_BOXES ? (int)D.bid[i] : 0);
     U128 sum = {0ull, 0ull};
     float rmax = 0.0f;
     for (int64_t p = rs + lane; p < re; p += 32) {
       const uint32_t j = rows[p];
       const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
       R rx, ry, rz, vr;
-      const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx.periodic, side, gtab, rc.n, inv_v0,
+      const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0,
                                       dt, step, k0, k1, rx, ry, rz, vr);
       pcache[p] = P;
       sum = u128_add(sum, to_fixed(P));
@@ -391,7 +399,7 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
         const uint32_t j = rows[pstar];
         const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
         R rx, ry, rz, vr;
-        (void)pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], bx.periodic, side, gtab, rc.n, inv_v0, dt,
+        (void)pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0, dt,
                                   step, k0, k1, rx, ry, rz, vr);
         const U128 hi = u128_add(base, to_fixed(pcache[pstar]));
         band = band || near_rel(T, base, hi) || near_rel(T, hi, hi);
@@ -486,12 +494,16 @@ k_mc_finish(int64_t n, const uint32_t *__restrict__ perm, const McRec *__restric
 template <typename R>
 cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *row_ptr, const uint32_t *rows,
                       const float4 *gtab, RunConst rc, McArgs a, R *pcache, McRec *rec, int finish_blocks,
-                      cudaStream_t s, int64_t *launches) {
+                      int blocks_per_sm, cudaStream_t s, int64_t *launches) {
   const int64_t nrows = a.list ? a.n_list : D.n;
   if (nrows <= 0) return cudaSuccess;
   int64_t blocks = (nrows + MC_WARPS - 1) / MC_WARPS;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  k_mc<R><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec);
+  if (blocks > 152 * (int64_t)blocks_per_sm) blocks = 152 * (int64_t)blocks_per_sm;
+  switch (geom_of(bx)) {
+    case GEOM_OPEN: k_mc<R, GEOM_OPEN><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec); break;
+    case GEOM_BOX: k_mc<R, GEOM_BOX><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec); break;
+    default: k_mc<R, GEOM_BOXES><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec); break;
+  }
   // the particle mass sits in L.w of the sorted copies
   const R *Lbase = reinterpret_cast<const R *>(D.L);
   k_mc_finish<<<finish_blocks, 256, 0, s>>>(D.n, D.perm, rec, sizeof(R) == 4 ? (const float *)(Lbase + 3) : nullptr,
@@ -501,10 +513,10 @@ cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int
 }
 template cudaError_t launch_mc<float>(SpeciesView<float>, SpeciesView<float>, BoxSplit, const int64_t *,
                                       const uint32_t *, const float4 *, RunConst, McArgs, float *, McRec *, int,
-                                      cudaStream_t, int64_t *);
+                                      int, cudaStream_t, int64_t *);
 template cudaError_t launch_mc<double>(SpeciesView<double>, SpeciesView<double>, BoxSplit, const int64_t *,
                                        const uint32_t *, const float4 *, RunConst, McArgs, double *, McRec *, int,
-                                       cudaStream_t, int64_t *);
+                                       int, cudaStream_t, int64_t *);
 
 // ---- overlap table and debug evaluators ------------------------------------------------
 __global__ void k_gtable(float4 *__restrict__ T) {

@@ -31,8 +31,7 @@
 // (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bits 17-22, M / 16 at bits 24-28.
 #define TC_IDESC ((1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24))
 
-// shared-memory layout (bytes); the operands come first so that every operand read lies inside
-// the allocation whatever the descriptor strides
+// shared-memory layout (bytes)
 template <int NWG>
 struct TcLayout {
   static constexpr int W2 = 0;
@@ -45,20 +44,10 @@ struct TcLayout {
   static constexpr int B3 = B2 + 512;
   static constexpr int W4 = B3 + 512;                    // [2][128] float
   static constexpr int B4 = W4 + 1024;                   // 2 floats (16 bytes)
-  static constexpr int WIN = B4 + 16;                    // NWG x 129 int64 row-start windows
-  static constexpr int BAR = WIN + NWG * 129 * 8 + 8;    // NWG mbarriers (8-byte aligned)
+  static constexpr int BAR = B4 + 16;                    // NWG mbarriers (8-byte aligned)
   static constexpr int TSLOT = BAR + NWG * 8;            // TMEM base address
   static constexpr int FLAG = TSLOT + 16;                // NWG completion flags
-  static constexpr int USED = FLAG + 16;
-  // furthest byte a 128-row operand read can touch if the two descriptor strides (2048 and 128)
-  // were taken the other way round: 8 slices (K = 128) or one slice (K = 16) of 15 x 2048 + 2 x 128
-  static constexpr int REACH = 7 * 4096 + 15 * 2048 + 256;
-  static constexpr int REACH1 = 15 * 2048 + 256;
-  static constexpr int TOTAL0 = (A1 + (NWG - 1) * TC_OPER1 + REACH1 > A + (NWG - 1) * TC_OPER + REACH)
-                                    ? A1 + (NWG - 1) * TC_OPER1 + REACH1
-                                    : A + (NWG - 1) * TC_OPER + REACH;
-  static constexpr int TOTAL1 = TOTAL0 > W1 + REACH1 ? TOTAL0 : W1 + REACH1;
-  static constexpr int TOTAL = ((TOTAL1 > USED ? TOTAL1 : USED) + 1023) / 1024 * 1024;
+  static constexpr int TOTAL = (FLAG + 16 + 1023) / 1024 * 1024;
 };
 static_assert(TcLayout<3>::TOTAL <= 232448, "shared memory of the tensor-core surrogate");
 static_assert(TcLayout<3>::BAR % 8 == 0, "mbarrier alignment");
@@ -150,6 +139,53 @@ __device__ __forceinline__ uint32_t bf16_bits(float x) {
   return (uint32_t) * reinterpret_cast<const uint16_t *>(&b);
 }
 
+// ---- row gather, in dependent stages --------------------------------------------------------
+// MODE_X: Vi = X[q] (the four network inputs).  MODE_PAIRS: k = prow[q] is the row of q; the
+// pair is p = q (rows are all gas, k = j) or p = row_ptr[list[k]] + q - R_ptr[k] (listed rows);
+// Vi, Vj are the sorted velocity copies of its DM particle i = rows[p] and gas particle j.
+struct RowFetch {
+  int64_t q = -1, k = 0, p = 0;
+  uint32_t i = 0, j = 0;
+  float4 Vi = make_float4(0.f, 0.f, 0.f, 0.f), Vj = make_float4(0.f, 0.f, 0.f, 0.f);
+};
+
+template <int MODE>
+__device__ __forceinline__ void fetch_stage(const TcArgs &a, int64_t q, int stage, RowFetch &f) {
+  if (stage == 0) {
+    f.q = q < a.n ? q : -1;
+    if (f.q < 0) return;
+    if (MODE == 0) {
+      f.p = q;
+      f.Vi = *reinterpret_cast<const float4 *>(a.X + 4 * q);
+    } else {
+      f.k = a.prow[q];
+      if (a.list == nullptr) {
+        f.p = q;
+        f.j = (uint32_t)f.k;
+        f.i = a.rows[q];
+      }
+    }
+    return;
+  }
+  if (MODE == 0 || f.q < 0) return;
+  if (a.list == nullptr) {
+    if (stage == 1) {
+      f.Vj = a.G_V[f.j];
+      f.Vi = a.D_V[f.i];
+    }
+    return;
+  }
+  if (stage == 1) {
+    f.j = a.list[f.k];
+    f.p = a.row_ptr[f.j] + (f.q - a.R_ptr[f.k]);
+  } else if (stage == 2) {
+    f.i = a.rows[f.p];
+    f.Vj = a.G_V[f.j];
+  } else {
+    f.Vi = a.D_V[f.i];
+  }
+}
+
 // ---- the kernel -----------------------------------------------------------------------------
 // MODE_X: rows are the caller's inputs X[n][4], outputs the raw network outputs Y[n][2].
 // MODE_PAIRS: rows are gas-major pairs (processing order q over a row-start prefix R_ptr),
@@ -225,66 +261,44 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
   const uint32_t sA = sbase + Ly::A + g * TC_OPER, sA1 = sbase + Ly::A1 + g * TC_OPER1;
   unsigned char *pA = sm + Ly::A + g * TC_OPER;
   unsigned char *pA1 = sm + Ly::A1 + g * TC_OPER1;
-  int64_t *win = reinterpret_cast<int64_t *>(sm + Ly::WIN) + g * 129;
   volatile uint32_t *flag = reinterpret_cast<volatile uint32_t *>(sm + Ly::FLAG) + g;
   const int bar_id = 1 + g;
   uint32_t phase = 0;
   unsigned fallback = 0;
   bool ok = true;
   const float alpha = (float)a.rc.alpha;
-
   const int64_t n_tiles = (a.n + TC_ROWS - 1) / TC_ROWS;
-  for (int64_t T = (int64_t)blockIdx.x * NWG + g; T < n_tiles && ok; T += (int64_t)gridDim.x * NWG) {
-    // ---- row inputs ----------------------------------------------------------------------
-    const int64_t q = T * TC_ROWS + t;
-    const bool valid = q < a.n;
+  const int64_t stride = (int64_t)gridDim.x * NWG;
+
+  // The inputs of the next tile are gathered while this tile's MMAs run: stage 0 is issued
+  // behind the layer-1 MMA, stage 1 behind layer 2 and stages 2-3 behind layer 3.
+  RowFetch nxt;
+  int64_t T = (int64_t)blockIdx.x * NWG + g;
+  fetch_stage<MODE>(a, T * TC_ROWS + t, 0, nxt);
+  fetch_stage<MODE>(a, 0, 1, nxt);
+  fetch_stage<MODE>(a, 0, 2, nxt);
+  fetch_stage<MODE>(a, 0, 3, nxt);
+  for (; T < n_tiles && ok; T += stride) {
+    // ---- this tile's row inputs (gathered one tile ahead) --------------------------------
     float x[MLP_IN] = {0.f, 0.f, 0.f, 0.f};
-    int64_t p = -1;
+    const int64_t p = nxt.p;
     float s_ratio = 0.f;
     bool use = false, in_dom = false;
-    if (MODE == MODE_X) {
-      if (valid) {
-#pragma unroll
-        for (int m = 0; m < MLP_IN; ++m) x[m] = a.X[4 * q + m];
+    if (nxt.q >= 0) {
+      if (MODE == MODE_X) {
+        x[0] = nxt.Vi.x; x[1] = nxt.Vi.y; x[2] = nxt.Vi.z; x[3] = nxt.Vi.w;
         use = in_dom = true;
-      }
-    } else {
-      // row of q: window of the row starts from the tile's first row, binary search inside it
-      const int64_t k0 = a.tile_row0[T];
-      const int64_t kw = k0 + t < a.n_rows ? k0 + t : a.n_rows;
-      win[t] = a.R_ptr[kw];
-      if (t == 0) win[128] = a.R_ptr[k0 + 128 < a.n_rows ? k0 + 128 : a.n_rows];
-      wg_sync(bar_id);
-      if (valid) {
-        int64_t k;
-        if (q < win[128] || k0 + 128 >= a.n_rows) {
-          int lo = 0, hi = 128;                        // largest idx with win[idx] <= q
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (win[mid] <= q) lo = mid; else hi = mid - 1;
-          }
-          k = k0 + lo;
-        } else {
-          int64_t lo = k0 + 128, hi = a.n_rows - 1;
-          while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (a.R_ptr[mid] <= q) lo = mid; else hi = mid - 1;
-          }
-          k = lo;
-        }
-        const int64_t j = a.list ? (int64_t)a.list[k] : k;
-        p = a.list ? a.row_ptr[j] + (q - a.R_ptr[k]) : q;
-        const float4 Vj = a.G_V[j];
-        const float4 Vi = a.D_V[a.rows[p]];
-        const float sig = Vj.w;
+      } else {
+        const float sig = nxt.Vj.w;
         if (sig > 0.0f) {
-          const float wx = Vi.x - Vj.x, wy = Vi.y - Vj.y, wz = Vi.z - Vj.z;
+          const float wx = nxt.Vi.x - nxt.Vj.x, wy = nxt.Vi.y - nxt.Vj.y, wz = nxt.Vi.z - nxt.Vj.z;
           s_ratio = sqrtf(wx * wx + wy * wy + wz * wz) / sig;
           in_dom = mlp_inputs(a.dom, fmaxf(s_ratio, 1e-30f), sig, x);
           use = true;
         }
       }
     }
+    const int64_t qn = (T + stride) * TC_ROWS + t;    // the next tile's row
     // layer-1 operand row: chunk 0 = [x_hi, x_hi], chunk 1 = [x_lo, x_lo]
     {
       uint32_t hi2[2], lo2[2];
@@ -317,9 +331,18 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
                    smem_desc(sW + ks * 2 * TC_SLICE, TC_SLICE, 128), ks > 0 ? 1u : 0u);
         }
         tc_commit(bar);
-        // one thread waits (bounded) and tells the group, so that a timeout is seen by all 128
-        *flag = mbar_wait_bounded(bar, phase) ? 1u : 0u;
       }
+      // the next tile's gather behind this MMA
+      if (layer == 0) {
+        fetch_stage<MODE>(a, qn, 0, nxt);
+      } else if (layer == 1) {
+        fetch_stage<MODE>(a, 0, 1, nxt);
+      } else {
+        fetch_stage<MODE>(a, 0, 2, nxt);
+        fetch_stage<MODE>(a, 0, 3, nxt);
+      }
+      // one thread waits (bounded) and tells the group, so that a timeout is seen by all 128
+      if (t == 0) *flag = mbar_wait_bounded(bar, phase) ? 1u : 0u;
       wg_sync(bar_id);
       phase ^= 1u;
       if (*flag == 0u) {
@@ -357,9 +380,9 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     // ---- outputs -----------------------------------------------------------------------------
     const float y[MLP_OUT] = {y0 + b4[0], y1 + b4[1]};
     if (MODE == MODE_X) {
-      if (valid) {
-        a.Y[2 * q] = y[0];
-        a.Y[2 * q + 1] = y[1];
+      if (use) {
+        a.Y[2 * p] = y[0];
+        a.Y[2 * p + 1] = y[1];
       }
     } else if (use) {
       float FA, FB;
@@ -385,29 +408,28 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
   }
 }
 
-// first row (in processing order) of every 128-row tile: largest k with R_ptr[k] <= 128 T
-__global__ void k_tile_rows(const int64_t *__restrict__ R_ptr, int64_t n_rows, int64_t n_tiles,
-                            int64_t *__restrict__ tile_row0) {
-  const int64_t T = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (T >= n_tiles) return;
-  const int64_t q = T * TC_ROWS;
-  int64_t lo = 0, hi = n_rows - 1;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (R_ptr[mid] <= q) lo = mid; else hi = mid - 1;
-  }
-  tile_row0[T] = lo;
+// row k of every processing index q: prow[q] = k for q in [R_ptr[k], R_ptr[k + 1]) (warp per row)
+__global__ void k_pair_rows(const int64_t *__restrict__ R_ptr, int64_t n_rows, uint32_t *__restrict__ prow) {
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const unsigned lane = threadIdx.x & 31u;
+  for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_rows; k += nw)
+    for (int64_t q = R_ptr[k] + lane; q < R_ptr[k + 1]; q += 32) prow[q] = (uint32_t)k;
 }
 
 static bool g_tc_attr = false;
 
 cudaError_t mlp_tc_prepare() {
   if (g_tc_attr) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<TC_NWG, MODE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       TcLayout<TC_NWG>::TOTAL);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<3, MODE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TcLayout<3>::TOTAL);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mlp_tc<TC_NWG, MODE_PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TcLayout<TC_NWG>::TOTAL);
+    e = cudaFuncSetAttribute(k_mlp_tc<3, MODE_PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcLayout<3>::TOTAL);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_tc<2, MODE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcLayout<2>::TOTAL);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_tc<2, MODE_PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcLayout<2>::TOTAL);
   if (e == cudaSuccess) g_tc_attr = true;
   return e;
 }
@@ -425,17 +447,18 @@ static cudaError_t launch_tc(const TcArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t mlp_tc_infer(TcArgs a, cudaStream_t s, int64_t *launches) {
+cudaError_t mlp_tc_infer(TcArgs a, int nwg, cudaStream_t s, int64_t *launches) {
   if (a.n <= 0) return cudaSuccess;
   if (launches) *launches += 1;
-  return launch_tc<TC_NWG, MODE_X>(a, s);
+  return nwg == 2 ? launch_tc<2, MODE_X>(a, s) : launch_tc<3, MODE_X>(a, s);
 }
 
-cudaError_t mlp_tc_pair_rates(TcArgs a, int64_t *tile_row0, cudaStream_t s, int64_t *launches) {
+cudaError_t mlp_tc_pair_rates(TcArgs a, uint32_t *prow, int nwg, cudaStream_t s, int64_t *launches) {
   if (a.n <= 0 || a.n_rows <= 0) return cudaSuccess;
-  const int64_t n_tiles = (a.n + TC_ROWS - 1) / TC_ROWS;
-  k_tile_rows<<<(unsigned)((n_tiles + 255) / 256), 256, 0, s>>>(a.R_ptr, a.n_rows, n_tiles, tile_row0);
-  a.tile_row0 = tile_row0;
+  int64_t blocks = (a.n_rows * 32 + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_pair_rows<<<(unsigned)blocks, 256, 0, s>>>(a.R_ptr, a.n_rows, prow);
+  a.prow = prow;
   if (launches) *launches += 2;
-  return launch_tc<TC_NWG, MODE_PAIRS>(a, s);
+  return nwg == 2 ? launch_tc<2, MODE_PAIRS>(a, s) : launch_tc<3, MODE_PAIRS>(a, s);
 }

@@ -5,7 +5,6 @@
 #include "grid.cuh"
 #include "mlp.cuh"
 
-#define TC_NWG 3   // warpgroups (independent 128-row tiles in flight) per CTA
 
 struct TcArgs {
   // network: float32 parameter block and the bf16 [out][in] copies of the 128 x 128 layers
@@ -24,7 +23,7 @@ struct TcArgs {
   const int64_t *row_ptr;
   const uint32_t *rows;            // DM index of pair p (sorted)
   const float4 *G_V, *D_V;         // sorted velocity copies (v, varsigma)
-  const int64_t *tile_row0;        // set by the launcher
+  const uint32_t *prow;            // row k of every q (set by the launcher)
   MlpDomain dom;
   RunConst rc;
   float2 *rates;                   // [pairs] (FA, FB)
@@ -35,6 +34,7 @@ struct TcArgs {
 // Shared-memory attributes (call once before any graph capture).
 cudaError_t mlp_tc_prepare();
 // Raw network outputs of X (debug / validation entry).
-cudaError_t mlp_tc_infer(TcArgs a, cudaStream_t s, int64_t *launches);
-// Rates of the pairs in processing order; tile_row0: scratch of (n + 127) / 128 int64.
-cudaError_t mlp_tc_pair_rates(TcArgs a, int64_t *tile_row0, cudaStream_t s, int64_t *launches);
+// nwg: warpgroups (independent 128-row tiles in flight) per CTA, 2 or 3.
+cudaError_t mlp_tc_infer(TcArgs a, int nwg, cudaStream_t s, int64_t *launches);
+// Rates of the pairs in processing order; prow: scratch of n uint32 (the row of every q).
+cudaError_t mlp_tc_pair_rates(TcArgs a, uint32_t *prow, int nwg, cudaStream_t s, int64_t *launches);

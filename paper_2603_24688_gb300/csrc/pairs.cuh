@@ -14,20 +14,30 @@ struct MlpRun {
   const float2 *rates;             // per gas-major pair (FA, FB) from launch_mlp_pair_rates
 };
 
-#define SR_UNIT 64   // target leaves per work unit of the tile stage
+#define SR_UNIT 64   // default target leaves per work unit of the tile stage
+#define MF_SEG 2048  // default pairs per mean-field work segment (long rows are split)
+
+// Launch shapes: defaults, or the choice of the autotuner (dmb_autotune).
+struct Shapes {
+  int unit = SR_UNIT;   // target leaves per search work unit
+  int seg = MF_SEG;     // pairs per mean-field segment
+  int mf_bps = 32;      // mean-field blocks per SM (grid cap of the persistent loop)
+  int mc_bps = 32;      // Monte Carlo blocks per SM
+  int tc_wg = 3;        // warpgroups (128-pair tiles in flight) per surrogate CTA: 2 or 3
+};
 
 template <typename R>
 cudaError_t launch_leaf_pairs(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
                               uint32_t *item_cnt, const int64_t *item_ptr, uint32_t *items, uint32_t *status,
                               unsigned long long *stats, cudaStream_t s, int64_t *launches);
-cudaError_t launch_unit_counts(const int64_t *item_ptr, int nleaf, uint32_t *unit_cnt, cudaStream_t s,
+cudaError_t launch_unit_counts(const int64_t *item_ptr, int nleaf, int unit, uint32_t *unit_cnt, cudaStream_t s,
                                int64_t *launches);
-cudaError_t launch_unit_map(const int64_t *item_ptr, const int64_t *unit_ptr, int nleaf, uint32_t *unit_leaf,
+cudaError_t launch_unit_map(const int64_t *item_ptr, const int64_t *unit_ptr, int nleaf, int unit, uint32_t *unit_leaf,
                             int64_t *unit_item0, cudaStream_t s, int64_t *launches);
 template <typename R>
 cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
                         const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
-                        const uint32_t *items, int64_t n_units, uint32_t *unit_cnt, const int64_t *row_ptr,
+                        const uint32_t *items, int64_t n_units, int unit, uint32_t *unit_cnt, const int64_t *row_ptr,
                         uint32_t *rows, uint32_t *status, unsigned long long *stats, cudaStream_t s,
                         int64_t *launches);
 cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, uint32_t *unit_cnt, uint32_t *counts,
@@ -38,13 +48,12 @@ cudaError_t launch_transpose_count(const int64_t *row_ptr, const uint32_t *rows,
 cudaError_t launch_transpose_fill(const int64_t *row_ptr, const uint32_t *rows, int64_t nq, const int64_t *t_ptr,
                                   uint32_t *cursor, uint32_t *t_rows, cudaStream_t s, int64_t *launches);
 
-#define MF_SEG 2048  // pairs per mean-field work segment (long rows are split)
 cudaError_t launch_seg_counts(const int64_t *row_ptr, int64_t n, int seg, uint32_t *cnt, cudaStream_t s,
                               int64_t *launches);
 cudaError_t launch_seg_map(const int64_t *row_ptr, const int64_t *seg_ptr, int64_t n, int seg, uint32_t *seg_row,
                            int64_t *seg_begin, cudaStream_t s, int64_t *launches);
 
-// Mean-field row segments: segment u covers pairs [begin[u], min(begin[u] + MF_SEG, end of row)).
+// Mean-field row segments: segment u covers pairs [begin[u], min(begin[u] + seg_len, end of row)).
 // Without a row list the rows are all gas particles in sorted order and seg_ptr is indexed by
 // the sorted gas index; with a list (the active gas of a substep) row k is gas list[k] and
 // seg_ptr is indexed by k.
@@ -55,6 +64,7 @@ struct SegView {
   const uint32_t *list = nullptr;   // sorted gas index of row k, or null (row k is gas k)
   int64_t n_rows = -1;        // rows when list is set
   int64_t n_seg = -1;         // segments to process; < 0: seg_ptr[N_B] read on the device
+  int seg_len = MF_SEG;       // pairs per segment the table was built with
 };
 
 struct MfOut {
@@ -67,7 +77,7 @@ struct MfOut {
 template <typename R>
 cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *row_ptr,
                              const uint32_t *rows, SegView sv, int64_t n_seg_max, const float4 *gtab, RunConst rc,
-                             MfOut out, R *part, MlpRun mr, cudaStream_t s, int64_t *launches);
+                             MfOut out, R *part, MlpRun mr, int blocks_per_sm, cudaStream_t s, int64_t *launches);
 
 struct McArgs {
   double dt;
@@ -110,7 +120,7 @@ struct McRec {
 template <typename R>
 cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *row_ptr, const uint32_t *rows,
                       const float4 *gtab, RunConst rc, McArgs a, R *pcache, McRec *rec, int finish_blocks,
-                      cudaStream_t s, int64_t *launches);
+                      int blocks_per_sm, cudaStream_t s, int64_t *launches);
 
 // Overlap table build (float64 exact evaluator at the nodes) and debug evaluators.
 cudaError_t launch_gtable(float4 *T, cudaStream_t s, int64_t *launches);

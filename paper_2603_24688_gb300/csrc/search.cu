@@ -39,30 +39,32 @@ struct LeafSides {
   bool two;
 };
 
+template <int GEOM>
 __device__ __forceinline__ LeafSides leaf_sides(const BoxSplit &bx, const int2 *leaf_box, int leaf) {
   LeafSides ls;
-  if (leaf_box != nullptr) {
+  if (GEOM == GEOM_BOXES) {
     const int2 r = leaf_box[leaf];
-    ls.a = bx.side(r.x);
+    ls.a = box_side<GEOM>(bx, r.x);
     ls.two = r.y != r.x;
-    ls.b = ls.two ? bx.side(r.y) : ls.a;
+    ls.b = ls.two ? box_side<GEOM>(bx, r.y) : ls.a;
   } else {
-    ls.a = bx.side(0);
+    ls.a = box_side<GEOM>(bx, 0);
     ls.b = ls.a;
     ls.two = false;
   }
   return ls;
 }
 
+template <int GEOM>
 __device__ __forceinline__ float box_gap2(const float qmn[3], const float qmx[3], const float4 &nmn, const float4 &nmx,
-                                          int periodic, const LeafSides &ls) {
-  float d2 = box_gap2_one(qmn, qmx, nmn, nmx, periodic, ls.a);
-  if (periodic && ls.two) d2 = fminf(d2, box_gap2_one(qmn, qmx, nmn, nmx, periodic, ls.b));
+                                          const LeafSides &ls) {
+  float d2 = box_gap2_one(qmn, qmx, nmn, nmx, GEOM != GEOM_OPEN, ls.a);
+  if (GEOM == GEOM_BOXES && ls.two) d2 = fminf(d2, box_gap2_one(qmn, qmx, nmn, nmx, 1, ls.b));
   return d2;
 }
 
 // ---- stage 1: candidate target leaves per query leaf -----------------------------------
-template <typename R, bool EMIT>
+template <typename R, bool EMIT, int GEOM>
 __global__ void __launch_bounds__(SR_WARPS * 32)
 k_leaf_pairs(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict__ frame,
              uint32_t *__restrict__ item_cnt, const int64_t *__restrict__ item_ptr, uint32_t *__restrict__ items,
@@ -81,13 +83,13 @@ k_leaf_pairs(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__res
     const int64_t lim = EMIT ? item_ptr[a + 1] - base : 0;
     if (qa.w >= 0.0f) {
       const float qmn[3] = {qa.x, qa.y, qa.z}, qmx[3] = {qb.x, qb.y, qb.z};
-      const LeafSides ls = leaf_sides(bx, Q.leaf_box, a);
+      const LeafSides ls = leaf_sides<GEOM>(bx, Q.leaf_box, a);
       const int top = O.levels - 1;
       if (top == 0) {
         // a single leaf: test it directly
         const float4 nmn = O.bmin[O.off[0]], nmx = O.bmax[O.off[0]];
         const float r = qa.w + nmn.w + pad2;
-        if (nmn.w >= 0.0f && box_gap2(qmn, qmx, nmn, nmx, bx.periodic, ls) < r * r) {
+        if (nmn.w >= 0.0f && box_gap2<GEOM>(qmn, qmx, nmn, nmx, ls) < r * r) {
           if (EMIT && lane == 0 && lim > 0) items[base] = 0u;
           count = 1;
         }
@@ -107,7 +109,7 @@ k_leaf_pairs(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__res
           if (c < O.cnt[l - 1]) {
             const float4 nmn = O.bmin[O.off[l - 1] + c], nmx = O.bmax[O.off[l - 1] + c];
             const float r = qa.w + nmn.w + pad2;
-            pass = nmn.w >= 0.0f && box_gap2(qmn, qmx, nmn, nmx, bx.periodic, ls) < r * r;
+            pass = nmn.w >= 0.0f && box_gap2<GEOM>(qmn, qmx, nmn, nmx, ls) < r * r;
           }
           const unsigned m = __ballot_sync(DMB_FULL, pass);
           const int np = __popc(m);
@@ -134,30 +136,30 @@ k_leaf_pairs(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__res
 }
 
 // units per query leaf
-__global__ void k_unit_counts(const int64_t *__restrict__ item_ptr, int nleaf, uint32_t *__restrict__ unit_cnt) {
+__global__ void k_unit_counts(const int64_t *__restrict__ item_ptr, int nleaf, int unit, uint32_t *__restrict__ unit_cnt) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= nleaf) return;
   const int64_t n = item_ptr[a + 1] - item_ptr[a];
-  unit_cnt[a] = (uint32_t)((n + SR_UNIT - 1) / SR_UNIT);
+  unit_cnt[a] = (uint32_t)((n + unit - 1) / unit);
 }
 
 __global__ void k_unit_map(const int64_t *__restrict__ item_ptr, const int64_t *__restrict__ unit_ptr, int nleaf,
-                           uint32_t *__restrict__ unit_leaf, int64_t *__restrict__ unit_item0) {
+                           int unit, uint32_t *__restrict__ unit_leaf, int64_t *__restrict__ unit_item0) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= nleaf) return;
   const int64_t u0 = unit_ptr[a], u1 = unit_ptr[a + 1];
   for (int64_t u = u0; u < u1; ++u) {
     unit_leaf[u] = (uint32_t)a;
-    unit_item0[u] = item_ptr[a] + (u - u0) * SR_UNIT;
+    unit_item0[u] = item_ptr[a] + (u - u0) * unit;
   }
 }
 
 // ---- stage 2: tiles of (query leaf) x (target leaf) -------------------------------------
-template <typename R, bool EMIT>
+template <typename R, bool EMIT, int GEOM>
 __global__ void __launch_bounds__(SR_WARPS * 32)
 k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict__ frame,
        const uint32_t *__restrict__ unit_leaf, const int64_t *__restrict__ unit_item0,
-       const int64_t *__restrict__ item_ptr, const uint32_t *__restrict__ items, int64_t n_units,
+       const int64_t *__restrict__ item_ptr, const uint32_t *__restrict__ items, int64_t n_units, int unit,
        uint32_t *__restrict__ unit_cnt, const int64_t *__restrict__ row_ptr, uint32_t *__restrict__ rows,
        uint32_t *status, unsigned long long *__restrict__ stats) {
   typedef typename Vec<R>::v4 v4;
@@ -167,20 +169,20 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
   const int wib = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31u;
   const float pad2 = 2.0f * frame->pad;
-  const bool boxed = Q.bid != nullptr && O.bid != nullptr;
+  const bool boxed = GEOM == GEOM_BOXES;
   unsigned long long st_tests = 0, st_leaves = 0;
   for (int64_t u = (int64_t)blockIdx.x * SR_WARPS + wib; u < n_units; u += (int64_t)gridDim.x * SR_WARPS) {
     const int a = (int)unit_leaf[u];
     const int64_t it0 = unit_item0[u];
-    const int64_t it1 = min(it0 + (int64_t)SR_UNIT, item_ptr[a + 1]);
+    const int64_t it1 = min(it0 + (int64_t)unit, item_ptr[a + 1]);
     const int64_t qi = (int64_t)a * DMB_LEAF + lane;
     const bool valid = qi < Q.n;
     const float4 qa = Q.bmin[Q.off[0] + a], qb = Q.bmax[Q.off[0] + a];
     const float qmn[3] = {qa.x, qa.y, qa.z}, qmx[3] = {qb.x, qb.y, qb.z};
     v4 Pq = Vec<R>::make(0, 0, 0, 0), Lq = Vec<R>::make(0, 0, 0, 0);
     if (valid) { Pq = Q.P[qi]; Lq = Q.L[qi]; }
-    const LeafSides ls = leaf_sides(bx, Q.leaf_box, a);
-    const BoxSide side_q = (Q.bid != nullptr && valid) ? bx.side(Q.bid[qi]) : ls.a;
+    const LeafSides ls = leaf_sides<GEOM>(bx, Q.leaf_box, a);
+    const BoxSide side_q = (GEOM == GEOM_BOXES && valid) ? box_side<GEOM>(bx, Q.bid[qi]) : ls.a;
     const uint16_t box_q = (boxed && valid) ? Q.bid[qi] : (uint16_t)0;
     uint32_t cnt = 0;
     int64_t out = 0, out_end = 0;
@@ -202,7 +204,7 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
         const float c[3] = {(float)Pk.x + (float)Lk.x, (float)Pk.y + (float)Lk.y, (float)Pk.z + (float)Lk.z};
         const float4 pmn = make_float4(c[0], c[1], c[2], 0.f), pmx = make_float4(c[0], c[1], c[2], 0.f);
         const float r = qa.w + (float)Pk.w + pad2;
-        keep = box_gap2(qmn, qmx, pmn, pmx, bx.periodic, ls) < r * r;
+        keep = box_gap2<GEOM>(qmn, qmx, pmn, pmx, ls) < r * r;
       }
       unsigned m = __ballot_sync(DMB_FULL, keep);
       __syncwarp();
@@ -215,7 +217,7 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
           const v4 Pk = sP[wib][k], Lk = sL[wib][k];
           if (boxed && sB[wib][k] != box_q) continue;     // pairs never join two boxes
           R dx, dy, dz;
-          pair_dx<R>(Pq, Lq, Pk, Lk, bx.periodic, side_q, dx, dy, dz);
+          pair_dx<R>(Pq, Lq, Pk, Lk, GEOM != GEOM_OPEN, side_q, dx, dy, dz);
           if (pair_test<R>(dist2_rn<R>(dx, dy, dz), Pq.w, Pk.w)) {
             if (EMIT) {
               if (out < out_end) rows[out] = (uint32_t)(base + k);
@@ -336,22 +338,30 @@ cudaError_t launch_leaf_pairs(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, c
                               uint32_t *item_cnt, const int64_t *item_ptr, uint32_t *items, uint32_t *status,
                               unsigned long long *stats, cudaStream_t s, int64_t *launches) {
   const int g = grid_for(Q.cnt[0]);
-  if (emit) k_leaf_pairs<R, true><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, item_cnt, item_ptr, items, status, stats);
-  else k_leaf_pairs<R, false><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, item_cnt, item_ptr, items, status, stats);
+#define LP(E, G) k_leaf_pairs<R, E, G><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, item_cnt, item_ptr, items, status, stats)
+  switch (geom_of(bx) * 2 + (emit ? 1 : 0)) {
+    case 0: LP(false, GEOM_OPEN); break;
+    case 1: LP(true, GEOM_OPEN); break;
+    case 2: LP(false, GEOM_BOX); break;
+    case 3: LP(true, GEOM_BOX); break;
+    case 4: LP(false, GEOM_BOXES); break;
+    default: LP(true, GEOM_BOXES); break;
+  }
+#undef LP
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
 
-cudaError_t launch_unit_counts(const int64_t *item_ptr, int nleaf, uint32_t *unit_cnt, cudaStream_t s,
+cudaError_t launch_unit_counts(const int64_t *item_ptr, int nleaf, int unit, uint32_t *unit_cnt, cudaStream_t s,
                                int64_t *launches) {
-  k_unit_counts<<<(nleaf + 255) / 256, 256, 0, s>>>(item_ptr, nleaf, unit_cnt);
+  k_unit_counts<<<(nleaf + 255) / 256, 256, 0, s>>>(item_ptr, nleaf, unit, unit_cnt);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
 
-cudaError_t launch_unit_map(const int64_t *item_ptr, const int64_t *unit_ptr, int nleaf, uint32_t *unit_leaf,
+cudaError_t launch_unit_map(const int64_t *item_ptr, const int64_t *unit_ptr, int nleaf, int unit, uint32_t *unit_leaf,
                             int64_t *unit_item0, cudaStream_t s, int64_t *launches) {
-  k_unit_map<<<(nleaf + 255) / 256, 256, 0, s>>>(item_ptr, unit_ptr, nleaf, unit_leaf, unit_item0);
+  k_unit_map<<<(nleaf + 255) / 256, 256, 0, s>>>(item_ptr, unit_ptr, nleaf, unit, unit_leaf, unit_item0);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
@@ -359,17 +369,23 @@ cudaError_t launch_unit_map(const int64_t *item_ptr, const int64_t *unit_ptr, in
 template <typename R>
 cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
                         const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
-                        const uint32_t *items, int64_t n_units, uint32_t *unit_cnt, const int64_t *row_ptr,
+                        const uint32_t *items, int64_t n_units, int unit, uint32_t *unit_cnt, const int64_t *row_ptr,
                         uint32_t *rows, uint32_t *status, unsigned long long *stats, cudaStream_t s,
                         int64_t *launches) {
   if (n_units <= 0) return cudaSuccess;
   const int g = grid_for(n_units);
-  if (emit)
-    k_tile<R, true><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items, n_units,
-                                                unit_cnt, row_ptr, rows, status, stats);
-  else
-    k_tile<R, false><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items, n_units,
-                                                 unit_cnt, row_ptr, rows, status, stats);
+#define TL(E, G)                                                                                                \
+  k_tile<R, E, G><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items, n_units, unit, \
+                                              unit_cnt, row_ptr, rows, status, stats)
+  switch (geom_of(bx) * 2 + (emit ? 1 : 0)) {
+    case 0: TL(false, GEOM_OPEN); break;
+    case 1: TL(true, GEOM_OPEN); break;
+    case 2: TL(false, GEOM_BOX); break;
+    case 3: TL(true, GEOM_BOX); break;
+    case 4: TL(false, GEOM_BOXES); break;
+    default: TL(true, GEOM_BOXES); break;
+  }
+#undef TL
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
@@ -388,7 +404,7 @@ cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, u
                                             unsigned long long *, cudaStream_t, int64_t *);                          \
   template cudaError_t launch_tile<R>(SpeciesView<R>, SpeciesView<R>, BoxSplit, const Frame *, bool,                \
                                       const uint32_t *, const int64_t *, const int64_t *, const uint32_t *, int64_t, \
-                                      uint32_t *, const int64_t *, uint32_t *, uint32_t *, unsigned long long *,      \
+                                      int, uint32_t *, const int64_t *, uint32_t *, uint32_t *, unsigned long long *, \
                                       cudaStream_t, int64_t *);
 INST(float)
 INST(double)

@@ -25,7 +25,8 @@ EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb
            "dmb_search_stats", "dmb_train_surrogate", "dmb_surrogate_params", "dmb_load_surrogate",
            "dmb_surrogate_infer", "dmb_surrogate_grad", "dmb_surrogate_fallbacks", "dmb_step_batched",
            "dmb_surrogate_grad_noalloc", "dmb_set_bins", "dmb_substep_info", "dmb_substep", "dmb_set_graph",
-           "dmb_set_surrogate_engine", "dmb_surrogate_infer_tc"]
+           "dmb_set_surrogate_engine", "dmb_surrogate_infer_tc", "dmb_autotune", "dmb_set_shapes",
+           "dmb_get_shapes"]
 
 
 class DmbError(RuntimeError):
@@ -98,6 +99,9 @@ def load(path=LIB_PATH):
         "dmb_set_graph": ([vp, c.c_int], c.c_int),
         "dmb_set_surrogate_engine": ([vp, c.c_int32], c.c_int),
         "dmb_surrogate_infer_tc": ([vp, vp, i64, vp], c.c_int),
+        "dmb_autotune": ([vp, c.POINTER(DM), c.POINTER(Gas), c.POINTER(c.c_int32), c.POINTER(c.c_double)], c.c_int),
+        "dmb_set_shapes": ([vp, c.POINTER(c.c_int32)], c.c_int),
+        "dmb_get_shapes": ([vp, c.POINTER(c.c_int32)], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -263,6 +267,25 @@ class Context:
         import torch
         self._check(self.lib.dmb_surrogate_infer_tc(self.h, _ptr(X, torch.float32), X.shape[0],
                                                     _ptr(Y, torch.float32)))
+
+    SHAPE_NAMES = ("unit", "seg", "mf_blocks_per_sm", "mc_blocks_per_sm", "tc_warpgroups")
+
+    def dmb_autotune(self, dm, gas):
+        """Returns (shapes dict, candidate times in ms)."""
+        d, g = self.dm_struct(dm), self.gas_struct(gas)
+        sh = (ctypes.c_int32 * 5)()
+        rep = (ctypes.c_double * 22)(*([float("nan")] * 22))
+        self._check(self.lib.dmb_autotune(self.h, ctypes.byref(d), ctypes.byref(g), sh, rep))
+        return dict(zip(self.SHAPE_NAMES, [int(v) for v in sh])), [v for v in rep if v == v]
+
+    def dmb_set_shapes(self, shapes):
+        v = (ctypes.c_int32 * 5)(*[int(shapes[k]) for k in self.SHAPE_NAMES])
+        self._check(self.lib.dmb_set_shapes(self.h, v))
+
+    def dmb_get_shapes(self):
+        v = (ctypes.c_int32 * 5)()
+        self._check(self.lib.dmb_get_shapes(self.h, v))
+        return dict(zip(self.SHAPE_NAMES, [int(x) for x in v]))
 
     def dmb_set_graph(self, on=True):
         self._check(self.lib.dmb_set_graph(self.h, 1 if on else 0))
