@@ -234,13 +234,13 @@ dmb_status dmb_surrogate_infer_tc(dmb_ctx *ctx, const float *X, int64_t n, float
  *              mean-field segment (pairs per warp task, 128..65536; default 2048),
  *              mean-field blocks per SM (grid cap, 1..64; default 32),
  *              Monte Carlo blocks per SM (1..64; default 32),
- *              surrogate warpgroups per CTA (2 or 3; default 3)}.
+ *              surrogate warpgroups per CTA (2..4; default 3)}.
  * dmb_autotune: builds the grid of (dm, gas) and times, with CUDA events on the context stream,
  * each candidate of one shape at a time in the order of the array (the search with units
  * {16, 32, 64, 128}; the mean field with segments {512, 1024, 2048, 4096} x blocks {8, 16, 32}
- * and, with a trained surrogate, warpgroups {2, 3}; the Monte Carlo with blocks {4, 8, 16, 32}),
+ * and, with a trained surrogate, warpgroups {2, 3, 4}; the Monte Carlo with blocks {4, 8, 16, 32}),
  * keeps the fastest of each and leaves the grid and pairs of (dm, gas) built.  The caller's
- * arrays are only read.  shapes_out (host [5]) and report (host, up to 22 doubles: the candidate
+ * arrays are only read.  shapes_out (host [5]) and report (host, up to 23 doubles: the candidate
  * times in ms in the order above) may be NULL.  Synchronises.  Single-box contexts.
  * dmb_set_shapes / dmb_get_shapes: set or read them (setting invalidates pairs and substep tables). */
 dmb_status dmb_autotune(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int32_t *shapes_out, double *report);

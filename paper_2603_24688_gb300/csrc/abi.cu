@@ -1189,9 +1189,9 @@ dmb_status dmb_substep(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint6
 // ---- autotuner of the launch shapes ----------------------------------------------------------
 static dmb_status check_shapes(dmb_ctx *ctx, const int32_t *v) {
   if (v[0] < 4 || v[0] > 1024 || v[1] < 128 || v[1] > 65536 || v[2] < 1 || v[2] > 64 || v[3] < 1 || v[3] > 64 ||
-      (v[4] != 2 && v[4] != 3))
+      v[4] < 2 || v[4] > 4)
     return fail(ctx, DMB_ERR_ARG, "shapes out of range: unit [4, 1024], seg [128, 65536], blocks per SM [1, 64], "
-                                  "surrogate warpgroups 2 or 3");
+                                  "surrogate warpgroups 2..4");
   return DMB_OK;
 }
 
@@ -1271,7 +1271,7 @@ static dmb_status autotune_impl(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *g
   if (ctx->rc.rate_mode == DMB_RATE_MLP && sizeof(R) == 4 && ctx->mlp_ready && ctx->mlp_engine == 0) {
     best = 1e30f;
     int best_wg = ctx->shp.tc_wg;
-    for (int wg : {2, 3}) {
+    for (int wg : {2, 3, 4}) {
       ctx->shp.tc_wg = wg;
       if ((st = time_call(ctx, e0, e1, mf, &ms)) != DMB_OK) return st;
       if (report) report[k++] = ms;

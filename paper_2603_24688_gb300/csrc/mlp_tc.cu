@@ -49,7 +49,7 @@ struct TcLayout {
   static constexpr int FLAG = TSLOT + 16;                // NWG completion flags
   static constexpr int TOTAL = (FLAG + 16 + 1023) / 1024 * 1024;
 };
-static_assert(TcLayout<3>::TOTAL <= 232448, "shared memory of the tensor-core surrogate");
+static_assert(TcLayout<4>::TOTAL <= 232448, "shared memory of the tensor-core surrogate");
 static_assert(TcLayout<3>::BAR % 8 == 0, "mbarrier alignment");
 
 // ---- PTX wrappers ---------------------------------------------------------------------------
@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
   }
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Ly::TSLOT);
   const uint32_t ncols = NWG <= 2 ? 256u : 512u;
+  static_assert(NWG * 128 <= 512, "tensor memory holds at most four 128-column accumulators");
   if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + Ly::TSLOT),
                  "r"(ncols)
@@ -430,6 +431,11 @@ cudaError_t mlp_tc_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_mlp_tc<2, MODE_PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TcLayout<2>::TOTAL);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_tc<4, MODE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcLayout<4>::TOTAL);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mlp_tc<4, MODE_PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcLayout<4>::TOTAL);
   if (e == cudaSuccess) g_tc_attr = true;
   return e;
 }
@@ -450,7 +456,7 @@ static cudaError_t launch_tc(const TcArgs &a, cudaStream_t s) {
 cudaError_t mlp_tc_infer(TcArgs a, int nwg, cudaStream_t s, int64_t *launches) {
   if (a.n <= 0) return cudaSuccess;
   if (launches) *launches += 1;
-  return nwg == 2 ? launch_tc<2, MODE_X>(a, s) : launch_tc<3, MODE_X>(a, s);
+  return nwg == 2 ? launch_tc<2, MODE_X>(a, s) : nwg == 4 ? launch_tc<4, MODE_X>(a, s) : launch_tc<3, MODE_X>(a, s);
 }
 
 cudaError_t mlp_tc_pair_rates(TcArgs a, uint32_t *prow, int nwg, cudaStream_t s, int64_t *launches) {
@@ -460,5 +466,6 @@ cudaError_t mlp_tc_pair_rates(TcArgs a, uint32_t *prow, int nwg, cudaStream_t s,
   k_pair_rows<<<(unsigned)blocks, 256, 0, s>>>(a.R_ptr, a.n_rows, prow);
   a.prow = prow;
   if (launches) *launches += 2;
-  return nwg == 2 ? launch_tc<2, MODE_PAIRS>(a, s) : launch_tc<3, MODE_PAIRS>(a, s);
+  return nwg == 2 ? launch_tc<2, MODE_PAIRS>(a, s)
+                  : nwg == 4 ? launch_tc<4, MODE_PAIRS>(a, s) : launch_tc<3, MODE_PAIRS>(a, s);
 }

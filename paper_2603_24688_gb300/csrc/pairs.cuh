@@ -23,7 +23,7 @@ struct Shapes {
   int seg = MF_SEG;     // pairs per mean-field segment
   int mf_bps = 32;      // mean-field blocks per SM (grid cap of the persistent loop)
   int mc_bps = 32;      // Monte Carlo blocks per SM
-  int tc_wg = 3;        // warpgroups (128-pair tiles in flight) per surrogate CTA: 2 or 3
+  int tc_wg = 3;        // warpgroups (128-pair tiles in flight) per surrogate CTA: 2 to 4
 };
 
 template <typename R>

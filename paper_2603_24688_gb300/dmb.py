@@ -274,7 +274,7 @@ class Context:
         """Returns (shapes dict, candidate times in ms)."""
         d, g = self.dm_struct(dm), self.gas_struct(gas)
         sh = (ctypes.c_int32 * 5)()
-        rep = (ctypes.c_double * 22)(*([float("nan")] * 22))
+        rep = (ctypes.c_double * 23)(*([float("nan")] * 23))
         self._check(self.lib.dmb_autotune(self.h, ctypes.byref(d), ctypes.byref(g), sh, rep))
         return dict(zip(self.SHAPE_NAMES, [int(v) for v in sh])), [v for v in rep if v == v]
 
