@@ -79,7 +79,7 @@ struct dmb_ctx {
   DevBuf mf_acc, mf_dudt, e_exp, mc_blocks, mc_max, kick_blocks, sums;
   DevBuf scratch_vel, search_stats;
   uint32_t *h_status = nullptr;   // pinned
-  int64_t *h_tot = nullptr;       // pinned [2]
+  int64_t *h_tot = nullptr;       // pinned [8]
   double *h_sums = nullptr;       // pinned [16]
   // state
   bool grid_ready = false, pairs_ready = false;
@@ -335,7 +335,7 @@ dmb_status search_stage1_count(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, S
 
 template <typename R>
 dmb_status search_stage2_count(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, SpeciesView<R> O,
-                               unsigned long long *stats) {
+                               unsigned long long *stats, TransposeOut tr) {
   cudaStream_t s = ctx->stream;
   int64_t *L = &ctx->launches;
   const int nleaf = Q.cnt[0];
@@ -349,8 +349,8 @@ dmb_status search_stage2_count(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, S
   CK(launch_unit_map(ptr<int64_t>(sb.item_ptr), ptr<int64_t>(sb.unit_ptr), nleaf, ctx->shp.unit, ptr<uint32_t>(sb.unit_leaf),
                      ptr<int64_t>(sb.unit_item0), s, L), "unit map");
   CK(launch_tile<R>(Q, O, ctx->bx, fr, false, ptr<uint32_t>(sb.unit_leaf), ptr<int64_t>(sb.unit_item0),
-                    ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), sb.n_units, ctx->shp.unit, ptr<uint32_t>(sb.unit_cnt), nullptr,
-                    nullptr, status, stats, s, L), "tile (count)");
+                    ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), sb.n_units, ctx->shp.unit,
+                    ptr<uint32_t>(sb.unit_cnt), nullptr, nullptr, tr, status, stats, s, L), "tile (count)");
   CK(launch_unit_prefix(ptr<int64_t>(sb.unit_ptr), nleaf, Q.n, ptr<uint32_t>(sb.unit_cnt), ptr<uint32_t>(sb.counts), s,
                         L), "unit prefix");
   CK(exclusive_scan_u32_i64(ptr<uint32_t>(sb.counts), ptr<int64_t>(sb.row_ptr), Q.n, ptr<int64_t>(ctx->scan_tmp), s, L),
@@ -359,31 +359,12 @@ dmb_status search_stage2_count(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, S
 }
 
 template <typename R>
-dmb_status search_stage2_emit(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, SpeciesView<R> O) {
+dmb_status search_stage2_emit(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, SpeciesView<R> O, TransposeOut tr) {
   if (!ensure(sb.rows, (size_t)sb.n_pairs * 4)) return fail(ctx, DMB_ERR_OOM, "device allocation failed for pair lists");
   CK(launch_tile<R>(Q, O, ctx->bx, ptr<Frame>(ctx->frame), true, ptr<uint32_t>(sb.unit_leaf),
                     ptr<int64_t>(sb.unit_item0), ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), sb.n_units,
-                    ctx->shp.unit, ptr<uint32_t>(sb.unit_cnt), ptr<int64_t>(sb.row_ptr), ptr<uint32_t>(sb.rows),
+                    ctx->shp.unit, ptr<uint32_t>(sb.unit_cnt), ptr<int64_t>(sb.row_ptr), ptr<uint32_t>(sb.rows), tr,
                     ptr<uint32_t>(ctx->status), nullptr, ctx->stream, &ctx->launches), "tile (emit)");
-  return DMB_OK;
-}
-
-// DM-major lists: transpose of the gas-major lists (counts, scan, atomic placement).
-dmb_status transpose_to_dm(dmb_ctx *ctx, const SearchBufs &sg, SearchBufs &sd, int64_t ng, int64_t nd) {
-  cudaStream_t s = ctx->stream;
-  int64_t *L = &ctx->launches;
-  if (!ensure(sd.counts, (size_t)(nd + 1) * 4) || !ensure(sd.row_ptr, (size_t)(nd + 1) * 8) ||
-      !ensure(ctx->t_cursor, (size_t)(nd + 1) * 4) || !ensure(sd.rows, (size_t)sg.n_pairs * 4))
-    return fail(ctx, DMB_ERR_OOM, "device allocation failed for DM-major lists");
-  CK(cudaMemsetAsync(sd.counts.p, 0, (size_t)(nd + 1) * 4, s), "memset");
-  CK(cudaMemsetAsync(ctx->t_cursor.p, 0, (size_t)(nd + 1) * 4, s), "memset");
-  CK(launch_transpose_count(ptr<int64_t>(sg.row_ptr), ptr<uint32_t>(sg.rows), ng, ptr<uint32_t>(sd.counts), s, L),
-     "transpose count");
-  CK(exclusive_scan_u32_i64(ptr<uint32_t>(sd.counts), ptr<int64_t>(sd.row_ptr), nd, ptr<int64_t>(ctx->scan_tmp), s, L),
-     "scan");
-  CK(launch_transpose_fill(ptr<int64_t>(sg.row_ptr), ptr<uint32_t>(sg.rows), ng, ptr<int64_t>(sd.row_ptr),
-                           ptr<uint32_t>(ctx->t_cursor), ptr<uint32_t>(sd.rows), s, L), "transpose fill");
-  sd.n_pairs = sg.n_pairs;
   return DMB_OK;
 }
 
@@ -424,13 +405,32 @@ dmb_status neighbors_impl(dmb_ctx *ctx) {
   if ((st = check_status(ctx)) != DMB_OK) return st;
   sg.n_items = ctx->h_tot[0];
   sg.n_units = ctx->h_tot[1];
-  // stage 2 counts, then the pair total
-  if ((st = search_stage2_count<R>(ctx, sg, G, D, sst)) != DMB_OK) return st;
+  // stage 2 counts in both directions (the DM-major counts from per-tile column sums), then
+  // the pair total
+  const int64_t nd = D.n;
+  if (!ensure(sd.counts, (size_t)(nd + 1) * 4) || !ensure(sd.row_ptr, (size_t)(nd + 1) * 8) ||
+      !ensure(ctx->t_cursor, (size_t)(nd + 1) * 4))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for DM-major lists");
+  CK(cudaMemsetAsync(sd.counts.p, 0, (size_t)(nd + 1) * 4, s), "memset");
+  TransposeOut trc;
+  trc.cnt = ptr<uint32_t>(sd.counts);
+  if ((st = search_stage2_count<R>(ctx, sg, G, D, sst, trc)) != DMB_OK) return st;
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(sd.counts), ptr<int64_t>(sd.row_ptr), nd, ptr<int64_t>(ctx->scan_tmp), s,
+                            &ctx->launches), "scan");
   CK(cudaMemcpyAsync(ctx->h_tot + 4, ptr<int64_t>(sg.row_ptr) + G.n, 8, cudaMemcpyDeviceToHost, s), "readback");
+  CK(cudaMemcpyAsync(ctx->h_tot + 5, ptr<int64_t>(sd.row_ptr) + nd, 8, cudaMemcpyDeviceToHost, s), "readback");
   if ((st = check_status(ctx)) != DMB_OK) return st;
   sg.n_pairs = G.n > 0 ? ctx->h_tot[4] : 0;
-  if ((st = search_stage2_emit<R>(ctx, sg, G, D)) != DMB_OK) return st;
-  if ((st = transpose_to_dm(ctx, sg, sd, G.n, D.n)) != DMB_OK) return st;
+  sd.n_pairs = nd > 0 ? ctx->h_tot[5] : 0;
+  if (sd.n_pairs != sg.n_pairs) return fail(ctx, DMB_ERR_CUDA, "pair counts of the two directions differ");
+  // emit both directions: gas-major rows in search order, DM-major rows by claimed positions
+  if (!ensure(sd.rows, (size_t)sg.n_pairs * 4)) return fail(ctx, DMB_ERR_OOM, "device allocation failed for DM-major lists");
+  CK(cudaMemsetAsync(ctx->t_cursor.p, 0, (size_t)(nd + 1) * 4, s), "memset");
+  TransposeOut tre;
+  tre.cursor = ptr<uint32_t>(ctx->t_cursor);
+  tre.ptr = ptr<int64_t>(sd.row_ptr);
+  tre.rows = ptr<uint32_t>(sd.rows);
+  if ((st = search_stage2_emit<R>(ctx, sg, G, D, tre)) != DMB_OK) return st;
   if ((st = build_segments(ctx, sg, G.n)) != DMB_OK) return st;
   if (!ensure(ctx->pcache, (size_t)sd.n_pairs * (ctx->p.fp64 ? 8 : 4)))
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for the probability cache");

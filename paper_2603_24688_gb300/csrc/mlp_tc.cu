@@ -13,6 +13,11 @@
 // x = x_hi + x_lo and W1 = W_hi + W_lo (bf16 parts), K = 16 holds the four products
 // [x_hi, x_hi, x_lo, x_lo] . [W_hi, W_lo, W_hi, W_lo], leaving an error of about 2^-16 of x.W.
 //
+// The epilogue does one tanh and one FMA per activation: SiLU(z) = h + h tanh(h) with h = z/2,
+// and the MMAs produce h directly, bias included.  The weights are stored halved (exact in
+// bf16) and one more K = 16 slice per layer multiplies a constant operand row [1, 1, 0, ...]
+// with [b_hi/2, b_lo/2, 0, ...] (bias split into bf16 parts, exact to about 2^-17).
+//
 // Operand layout (no swizzle, K-major): 8 x 16-byte core matrices; element (row, k) of a
 // 128-row operand sits at (k / 8) * 2048 + row * 16 + (k % 8) * 2 bytes, so the descriptor of
 // the K = 16 slice ks starts at 4096 ks with leading-dimension offset 2048 (next 8 columns) and
@@ -36,13 +41,12 @@ template <int NWG>
 struct TcLayout {
   static constexpr int W2 = 0;
   static constexpr int W3 = W2 + TC_OPER;
-  static constexpr int A = W3 + TC_OPER;                 // NWG activation operands
-  static constexpr int A1 = A + NWG * TC_OPER;           // NWG layer-1 operands
-  static constexpr int W1 = A1 + NWG * TC_OPER1;         // split W1 (128 x 16)
-  static constexpr int B1 = W1 + TC_OPER1;               // biases (float)
-  static constexpr int B2 = B1 + 512;
-  static constexpr int B3 = B2 + 512;
-  static constexpr int W4 = B3 + 512;                    // [2][128] float
+  static constexpr int A = W3 + TC_OPER;                 // NWG activation operands (slice 0 of each also
+                                                         // holds the layer-1 operand of a new tile)
+  static constexpr int W1 = A + NWG * TC_OPER;           // split W1 / 2 (128 x 16)
+  static constexpr int ONE = W1 + TC_OPER1;              // constant operand rows [1, 1, 0, ...] (128 x 16)
+  static constexpr int BB = ONE + TC_OPER1;              // 3 bias operands [b_hi/2, b_lo/2, 0, ...] (128 x 16)
+  static constexpr int W4 = BB + 3 * TC_OPER1;           // [2][128] float
   static constexpr int B4 = W4 + 1024;                   // 2 floats (16 bytes)
   static constexpr int BAR = B4 + 16;                    // NWG mbarriers (8-byte aligned)
   static constexpr int TSLOT = BAR + NWG * 8;            // TMEM base address
@@ -134,6 +138,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
   for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// SiLU from h = z / 2: z sigmoid(z) = h + h tanh(h), one MUFU and one FMA
+__device__ __forceinline__ float silu_h(float h) { return fmaf(h, tanh_fast(h), h); }
+
 __device__ __forceinline__ uint32_t bf16_bits(float x) {
   const __nv_bfloat16 b = __float2bfloat16_rn(x);
   return (uint32_t) * reinterpret_cast<const uint16_t *>(&b);
@@ -209,14 +216,18 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     const int r = q % (MLP_H * (MLP_H / 8));
     const int n = r % MLP_H, c = r / MLP_H;           // output row n, 8-column chunk c
     const __nv_bfloat16 *src = (which == 0 ? a.w2 : a.w3) + n * MLP_H + c * 8;
-    *reinterpret_cast<uint4 *>(sm + (which == 0 ? Ly::W2 : Ly::W3) + c * TC_SLICE + n * 16) =
-        *reinterpret_cast<const uint4 *>(src);
+    uint4 v = *reinterpret_cast<const uint4 *>(src);
+    const __nv_bfloat162 half2 = __floats2bfloat162_rn(0.5f, 0.5f);
+    __nv_bfloat162 *hv = reinterpret_cast<__nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) hv[e] = __hmul2(hv[e], half2);   // W / 2, exact
+    *reinterpret_cast<uint4 *>(sm + (which == 0 ? Ly::W2 : Ly::W3) + c * TC_SLICE + n * 16) = v;
   }
   for (int n = tid; n < MLP_H; n += blockDim.x) {
     uint32_t hl[4];
 #pragma unroll
     for (int m = 0; m < MLP_IN; m += 2) {
-      const float w0 = a.p[MLP_OFF_W1 + n * MLP_IN + m], w1 = a.p[MLP_OFF_W1 + n * MLP_IN + m + 1];
+      const float w0 = 0.5f * a.p[MLP_OFF_W1 + n * MLP_IN + m], w1 = 0.5f * a.p[MLP_OFF_W1 + n * MLP_IN + m + 1];
       const float h0 = __bfloat162float(__float2bfloat16_rn(w0)), h1 = __bfloat162float(__float2bfloat16_rn(w1));
       hl[m / 2] = bf16_bits(w0) | (bf16_bits(w1) << 16);
       hl[2 + m / 2] = bf16_bits(w0 - h0) | (bf16_bits(w1 - h1) << 16);
@@ -224,16 +235,22 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     const uint4 chunk = make_uint4(hl[0], hl[1], hl[2], hl[3]);   // [W_hi(4), W_lo(4)] in both chunks
     *reinterpret_cast<uint4 *>(sm + Ly::W1 + 0 * TC_SLICE + n * 16) = chunk;
     *reinterpret_cast<uint4 *>(sm + Ly::W1 + 1 * TC_SLICE + n * 16) = chunk;
+    // constant rows [1, 1, 0, ...] and the bias rows [b_hi/2, b_lo/2, 0, ...] of the three layers
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(sm + Ly::ONE + 0 * TC_SLICE + n * 16) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(sm + Ly::ONE + 1 * TC_SLICE + n * 16) = zero;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const float b = 0.5f * a.p[(l == 0 ? MLP_OFF_B1 : l == 1 ? MLP_OFF_B2 : MLP_OFF_B3) + n];
+      const float bh = __bfloat162float(__float2bfloat16_rn(b));
+      *reinterpret_cast<uint4 *>(sm + Ly::BB + l * TC_OPER1 + 0 * TC_SLICE + n * 16) =
+          make_uint4(bf16_bits(b) | (bf16_bits(b - bh) << 16), 0u, 0u, 0u);
+      *reinterpret_cast<uint4 *>(sm + Ly::BB + l * TC_OPER1 + 1 * TC_SLICE + n * 16) = zero;
+    }
   }
-  float *b1 = reinterpret_cast<float *>(sm + Ly::B1);
-  float *b2 = reinterpret_cast<float *>(sm + Ly::B2);
-  float *b3 = reinterpret_cast<float *>(sm + Ly::B3);
   float *W4 = reinterpret_cast<float *>(sm + Ly::W4);
   float *b4 = reinterpret_cast<float *>(sm + Ly::B4);
   for (int c = tid; c < MLP_H; c += blockDim.x) {
-    b1[c] = a.p[MLP_OFF_B1 + c];
-    b2[c] = a.p[MLP_OFF_B2 + c];
-    b3[c] = a.p[MLP_OFF_B3 + c];
     W4[c] = a.p[MLP_OFF_W4 + c];
     W4[MLP_H + c] = a.p[MLP_OFF_W4 + MLP_H + c];
   }
@@ -259,9 +276,9 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
   const uint32_t tmem = *tslot;
   const uint32_t d_tmem = tmem + 128u * (uint32_t)g;                           // lane 0, this group's columns
   const uint32_t my_lanes = d_tmem + ((uint32_t)(32 * w) << 16);
-  const uint32_t sA = sbase + Ly::A + g * TC_OPER, sA1 = sbase + Ly::A1 + g * TC_OPER1;
+  const uint32_t sA = sbase + Ly::A + g * TC_OPER, sA1 = sA;   // the layer-1 operand is slice 0 of A
   unsigned char *pA = sm + Ly::A + g * TC_OPER;
-  unsigned char *pA1 = sm + Ly::A1 + g * TC_OPER1;
+  unsigned char *pA1 = pA;
   volatile uint32_t *flag = reinterpret_cast<volatile uint32_t *>(sm + Ly::FLAG) + g;
   const int bar_id = 1 + g;
   uint32_t phase = 0;
@@ -331,6 +348,9 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
             tc_mma(d_tmem, smem_desc(sA + ks * 2 * TC_SLICE, TC_SLICE, 128),
                    smem_desc(sW + ks * 2 * TC_SLICE, TC_SLICE, 128), ks > 0 ? 1u : 0u);
         }
+        // + b / 2 through the constant slice
+        tc_mma(d_tmem, smem_desc(sbase + Ly::ONE, TC_SLICE, 128),
+               smem_desc(sbase + Ly::BB + layer * TC_OPER1, TC_SLICE, 128), 1u);
         tc_commit(bar);
       }
       // the next tile's gather behind this MMA
@@ -351,16 +371,15 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
         break;
       }
       tc_fence_after();
-      const float *bias = layer == 0 ? b1 : layer == 1 ? b2 : b3;
 #pragma unroll 1
       for (int cc = 0; cc < MLP_H / 32; ++cc) {
         float v[32];
-        tmem_ld32(my_lanes + 32u * cc, v);
+        tmem_ld32(my_lanes + 32u * cc, v);   // h = z / 2 with the bias
         if (layer < 2) {
           uint32_t pk[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k)
-            pk[k] = pack_bf16(silu(v[2 * k] + bias[32 * cc + 2 * k]), silu(v[2 * k + 1] + bias[32 * cc + 2 * k + 1]));
+            pk[k] = pack_bf16(silu_h(v[2 * k]), silu_h(v[2 * k + 1]));
 #pragma unroll
           for (int c4 = 0; c4 < 4; ++c4)
             *reinterpret_cast<uint4 *>(pA + (4 * cc + c4) * TC_SLICE + t * 16) =
@@ -369,7 +388,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
 #pragma unroll
           for (int k = 0; k < 32; ++k) {
             const int c = 32 * cc + k;
-            const float act = silu(v[k] + bias[c]);
+            const float act = silu_h(v[k]);
             y0 += W4[c] * act;
             y1 += W4[MLP_H + c] * act;
           }

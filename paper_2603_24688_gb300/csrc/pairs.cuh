@@ -23,7 +23,7 @@ struct Shapes {
   int seg = MF_SEG;     // pairs per mean-field segment
   int mf_bps = 32;      // mean-field blocks per SM (grid cap of the persistent loop)
   int mc_bps = 32;      // Monte Carlo blocks per SM
-  int tc_wg = 3;        // warpgroups (128-pair tiles in flight) per surrogate CTA: 2 to 4
+  int tc_wg = 4;        // warpgroups (128-pair tiles in flight) per surrogate CTA: 2 to 4
 };
 
 template <typename R>
@@ -34,19 +34,26 @@ cudaError_t launch_unit_counts(const int64_t *item_ptr, int nleaf, int unit, uin
                                int64_t *launches);
 cudaError_t launch_unit_map(const int64_t *item_ptr, const int64_t *unit_ptr, int nleaf, int unit, uint32_t *unit_leaf,
                             int64_t *unit_item0, cudaStream_t s, int64_t *launches);
+// The transposed (target-major) lists written by the tile stage as it finds the pairs: the
+// count pass adds each tile's pairs to cnt[target]; the emit pass claims positions with
+// cursor[target] and writes the query index at ptr[target] + position (row order within a
+// target follows the tiles' completion, so consumers must not depend on it).
+struct TransposeOut {
+  uint32_t *cnt = nullptr;       // [targets] (count pass)
+  uint32_t *cursor = nullptr;    // [targets], zeroed (emit pass)
+  const int64_t *ptr = nullptr;  // [targets + 1] row starts (emit pass)
+  uint32_t *rows = nullptr;      // [pairs] (emit pass)
+};
+
 template <typename R>
 cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
                         const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
                         const uint32_t *items, int64_t n_units, int unit, uint32_t *unit_cnt, const int64_t *row_ptr,
-                        uint32_t *rows, uint32_t *status, unsigned long long *stats, cudaStream_t s,
+                        uint32_t *rows, TransposeOut tr, uint32_t *status, unsigned long long *stats, cudaStream_t s,
                         int64_t *launches);
 cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, uint32_t *unit_cnt, uint32_t *counts,
                                cudaStream_t s, int64_t *launches);
 
-cudaError_t launch_transpose_count(const int64_t *row_ptr, const uint32_t *rows, int64_t nq, uint32_t *cnt,
-                                   cudaStream_t s, int64_t *launches);
-cudaError_t launch_transpose_fill(const int64_t *row_ptr, const uint32_t *rows, int64_t nq, const int64_t *t_ptr,
-                                  uint32_t *cursor, uint32_t *t_rows, cudaStream_t s, int64_t *launches);
 
 cudaError_t launch_seg_counts(const int64_t *row_ptr, int64_t n, int seg, uint32_t *cnt, cudaStream_t s,
                               int64_t *launches);

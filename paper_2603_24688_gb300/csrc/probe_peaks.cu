@@ -48,6 +48,22 @@ __global__ void k_tanh2(float* out, unsigned a) {
     x0^=a; x1^=a; x2^=a; x3^=a; }
   out[blockIdx.x*blockDim.x+threadIdx.x]=(float)(x0^x1^x2^x3);
 }
+__global__ void k_tanhh2(float* out, unsigned a) {
+  unsigned x0=0x3c003c00u^threadIdx.x, x1=x0^0x00010001u, x2=x0^0x00020002u, x3=x0^0x00030003u;
+  for (int i=0;i<ITERS/4;i++){
+    asm volatile("tanh.approx.f16x2 %0, %0;" : "+r"(x0)); asm volatile("tanh.approx.f16x2 %0, %0;" : "+r"(x1));
+    asm volatile("tanh.approx.f16x2 %0, %0;" : "+r"(x2)); asm volatile("tanh.approx.f16x2 %0, %0;" : "+r"(x3));
+    x0^=a; x1^=a; x2^=a; x3^=a; }
+  out[blockIdx.x*blockDim.x+threadIdx.x]=(float)(x0^x1^x2^x3);
+}
+__global__ void k_ex2h2(float* out, unsigned a) {
+  unsigned x0=0x3c003c00u^threadIdx.x, x1=x0^0x00010001u, x2=x0^0x00020002u, x3=x0^0x00030003u;
+  for (int i=0;i<ITERS/4;i++){
+    asm volatile("ex2.approx.f16x2 %0, %0;" : "+r"(x0)); asm volatile("ex2.approx.f16x2 %0, %0;" : "+r"(x1));
+    asm volatile("ex2.approx.f16x2 %0, %0;" : "+r"(x2)); asm volatile("ex2.approx.f16x2 %0, %0;" : "+r"(x3));
+    x0^=a; x1^=a; x2^=a; x3^=a; }
+  out[blockIdx.x*blockDim.x+threadIdx.x]=(float)(x0^x1^x2^x3);
+}
 // 4 independent m16n8k16 bf16 accumulator chains per warp; 4096 flops per instruction
 __global__ void k_mma(float* out, unsigned a) {
   unsigned A0=a^threadIdx.x, A1=A0*3u, A2=A0*5u, A3=A0*7u, B0=A0*11u, B1=A0*13u;
@@ -84,6 +100,10 @@ int main(){
   cudaEventElapsedTime(&ms,e0,e1); printf("tanh.f32: %.2f Tops/s\n", 4.0*(ITERS/4)*n/ms/1e9);
   cudaEventRecord(e0); k_tanh2<<<blocks,threads>>>((float*)buf,0x00010001u); cudaEventRecord(e1); cudaEventSynchronize(e1);
   cudaEventElapsedTime(&ms,e0,e1); printf("tanh.bf16x2: %.2f Tinstr/s (2 values each)\n", 4.0*(ITERS/4)*n/ms/1e9);
+  cudaEventRecord(e0); k_tanhh2<<<blocks,threads>>>((float*)buf,0x00010001u); cudaEventRecord(e1); cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms,e0,e1); printf("tanh.f16x2: %.2f Tinstr/s (2 values each)\n", 4.0*(ITERS/4)*n/ms/1e9);
+  cudaEventRecord(e0); k_ex2h2<<<blocks,threads>>>((float*)buf,0x80008000u); cudaEventRecord(e1); cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms,e0,e1); printf("ex2.f16x2: %.2f Tinstr/s (2 values each)\n", 4.0*(ITERS/4)*n/ms/1e9);
   cudaEventRecord(e0); k_mma<<<blocks,threads>>>((float*)buf,0x3f803f80u); cudaEventRecord(e1); cudaEventSynchronize(e1);
   cudaEventElapsedTime(&ms,e0,e1); printf("mma.sync bf16 m16n8k16: %.1f TFLOP/s\n", 4096.0*4*(ITERS/4)*(n/32)/ms/1e9);
   }

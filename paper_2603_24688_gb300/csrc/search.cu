@@ -1,11 +1,14 @@
 // Pair search on the 32-ary chunk trees, in two stages:
 //   1. per query leaf, the target leaves whose boxes come within h_max + h_max (lane-parallel
 //      tests of the 32 children of every visited node), listed in depth-first order;
-//   2. those lists cut into work units of at most SR_UNIT target leaves; one warp per unit
+//   2. those lists cut into work units of at most `unit` target leaves; one warp per unit
 //      tests its 32 query particles against each target leaf (targets outside the query
 //      leaf's reach are dropped by a ballot first) and counts or writes the pairs.
-// Rows come out in a fixed order (units, then leaves, then particles), so the search is
-// deterministic; both directions use the same bit-exact pair predicate.
+// Query rows come out in a fixed order (units, then leaves, then particles).  The same pass
+// builds the target-major lists: per (tile, target) a ballot of the pair bits gives the
+// target's new partners, counted (and later placed) with one atomic.  The order inside a
+// target row then follows the tiles' completion; the Monte Carlo, which reads those rows, sums
+// them exactly in fixed point and selects partners by gas id, so no result depends on it.
 #include "pairs.cuh"
 #include "physics.cuh"
 
@@ -161,7 +164,7 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
        const uint32_t *__restrict__ unit_leaf, const int64_t *__restrict__ unit_item0,
        const int64_t *__restrict__ item_ptr, const uint32_t *__restrict__ items, int64_t n_units, int unit,
        uint32_t *__restrict__ unit_cnt, const int64_t *__restrict__ row_ptr, uint32_t *__restrict__ rows,
-       uint32_t *status, unsigned long long *__restrict__ stats) {
+       TransposeOut tr, uint32_t *status, unsigned long long *__restrict__ stats) {
   typedef typename Vec<R>::v4 v4;
   __shared__ v4 sP[SR_WARPS][DMB_LEAF];
   __shared__ v4 sL[SR_WARPS][DMB_LEAF];
@@ -170,6 +173,8 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
   const unsigned lane = threadIdx.x & 31u;
   const float pad2 = 2.0f * frame->pad;
   const bool boxed = GEOM == GEOM_BOXES;
+  const bool tr_on = EMIT ? tr.rows != nullptr : tr.cnt != nullptr;
+  const unsigned lt = (1u << lane) - 1u;
   unsigned long long st_tests = 0, st_leaves = 0;
   for (int64_t u = (int64_t)blockIdx.x * SR_WARPS + wib; u < n_units; u += (int64_t)gridDim.x * SR_WARPS) {
     const int a = (int)unit_leaf[u];
@@ -210,20 +215,39 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
       __syncwarp();
       ++st_leaves;
       st_tests += (unsigned long long)__popc(m) * 32ull;
-      if (valid) {
-        while (m) {
-          const int k = __ffs(m) - 1;
-          m &= m - 1;
-          const v4 Pk = sP[wib][k], Lk = sL[wib][k];
-          if (boxed && sB[wib][k] != box_q) continue;     // pairs never join two boxes
+      while (m) {                                        // warp-uniform: m is a ballot
+        const int k = __ffs(m) - 1;
+        m &= m - 1;
+        const v4 Pk = sP[wib][k], Lk = sL[wib][k];
+        bool hit = valid && !(boxed && sB[wib][k] != box_q);   // pairs never join two boxes
+        if (hit) {
           R dx, dy, dz;
           pair_dx<R>(Pq, Lq, Pk, Lk, GEOM != GEOM_OPEN, side_q, dx, dy, dz);
-          if (pair_test<R>(dist2_rn<R>(dx, dy, dz), Pq.w, Pk.w)) {
-            if (EMIT) {
-              if (out < out_end) rows[out] = (uint32_t)(base + k);
-              ++out;
+          hit = pair_test<R>(dist2_rn<R>(dx, dy, dz), Pq.w, Pk.w);
+        }
+        if (hit) {
+          if (EMIT) {
+            if (out < out_end) rows[out] = (uint32_t)(base + k);
+            ++out;
+          }
+          ++cnt;
+        }
+        if (tr_on) {
+          // the other direction's lists: one atomic per (tile, target) instead of per pair
+          const unsigned col = __ballot_sync(DMB_FULL, hit);
+          if (col) {
+            const int64_t tk = base + k;
+            if (!EMIT) {
+              if (lane == 0) atomicAdd(&tr.cnt[tk], (uint32_t)__popc(col));
+            } else {
+              uint32_t b0 = 0;
+              if (lane == 0) b0 = atomicAdd(&tr.cursor[tk], (uint32_t)__popc(col));
+              b0 = __shfl_sync(DMB_FULL, b0, 0);
+              if (hit) {
+                const int64_t pos = tr.ptr[tk] + b0 + __popc(col & lt);
+                if (pos < tr.ptr[tk + 1]) tr.rows[pos] = (uint32_t)qi;
+              }
             }
-            ++cnt;
           }
         }
       }
@@ -250,46 +274,6 @@ __global__ void k_unit_prefix(const int64_t *__restrict__ unit_ptr, int nleaf, i
   }
   const int64_t qi = a * DMB_LEAF + lane;
   if (qi < nq) counts[qi] = run;
-}
-
-// ---- DM-major lists as the transpose of the gas-major lists ------------------------------
-// The Monte Carlo sums each DM row exactly in fixed point and picks the partner by gas id,
-// so the order inside a DM row does not affect any result; atomics place the entries.
-__global__ void k_transpose_count(const int64_t *__restrict__ row_ptr, const uint32_t *__restrict__ rows, int64_t nq,
-                                  uint32_t *__restrict__ cnt) {
-  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned lane = threadIdx.x & 31u;
-  if (j >= nq) return;
-  for (int64_t p = row_ptr[j] + lane; p < row_ptr[j + 1]; p += 32) atomicAdd(&cnt[rows[p]], 1u);
-}
-
-__global__ void k_transpose_fill(const int64_t *__restrict__ row_ptr, const uint32_t *__restrict__ rows, int64_t nq,
-                                 const int64_t *__restrict__ t_ptr, uint32_t *__restrict__ cursor,
-                                 uint32_t *__restrict__ t_rows) {
-  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned lane = threadIdx.x & 31u;
-  if (j >= nq) return;
-  for (int64_t p = row_ptr[j] + lane; p < row_ptr[j + 1]; p += 32) {
-    const uint32_t i = rows[p];
-    const uint32_t k = atomicAdd(&cursor[i], 1u);
-    t_rows[t_ptr[i] + k] = (uint32_t)j;
-  }
-}
-
-cudaError_t launch_transpose_count(const int64_t *row_ptr, const uint32_t *rows, int64_t nq, uint32_t *cnt,
-                                   cudaStream_t s, int64_t *launches) {
-  if (nq <= 0) return cudaSuccess;
-  k_transpose_count<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(row_ptr, rows, nq, cnt);
-  if (launches) *launches += 1;
-  return cudaGetLastError();
-}
-
-cudaError_t launch_transpose_fill(const int64_t *row_ptr, const uint32_t *rows, int64_t nq, const int64_t *t_ptr,
-                                  uint32_t *cursor, uint32_t *t_rows, cudaStream_t s, int64_t *launches) {
-  if (nq <= 0) return cudaSuccess;
-  k_transpose_fill<<<(unsigned)((nq * 32 + 255) / 256), 256, 0, s>>>(row_ptr, rows, nq, t_ptr, cursor, t_rows);
-  if (launches) *launches += 1;
-  return cudaGetLastError();
 }
 
 // ---- row segments: long rows cut into pieces of at most `seg` pairs -------------------
@@ -370,13 +354,13 @@ template <typename R>
 cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
                         const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
                         const uint32_t *items, int64_t n_units, int unit, uint32_t *unit_cnt, const int64_t *row_ptr,
-                        uint32_t *rows, uint32_t *status, unsigned long long *stats, cudaStream_t s,
+                        uint32_t *rows, TransposeOut tr, uint32_t *status, unsigned long long *stats, cudaStream_t s,
                         int64_t *launches) {
   if (n_units <= 0) return cudaSuccess;
   const int g = grid_for(n_units);
 #define TL(E, G)                                                                                                \
   k_tile<R, E, G><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items, n_units, unit, \
-                                              unit_cnt, row_ptr, rows, status, stats)
+                                              unit_cnt, row_ptr, rows, tr, status, stats)
   switch (geom_of(bx) * 2 + (emit ? 1 : 0)) {
     case 0: TL(false, GEOM_OPEN); break;
     case 1: TL(true, GEOM_OPEN); break;
@@ -404,7 +388,8 @@ cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, u
                                             unsigned long long *, cudaStream_t, int64_t *);                          \
   template cudaError_t launch_tile<R>(SpeciesView<R>, SpeciesView<R>, BoxSplit, const Frame *, bool,                \
                                       const uint32_t *, const int64_t *, const int64_t *, const uint32_t *, int64_t, \
-                                      int, uint32_t *, const int64_t *, uint32_t *, uint32_t *, unsigned long long *, \
+                                      int, uint32_t *, const int64_t *, uint32_t *, TransposeOut, uint32_t *,         \
+                                      unsigned long long *,                                                          \
                                       cudaStream_t, int64_t *);
 INST(float)
 INST(double)
