@@ -215,9 +215,9 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
       __syncwarp();
       ++st_leaves;
       st_tests += (unsigned long long)__popc(m) * 32ull;
-      while (m) {                                        // warp-uniform: m is a ballot
-        const int k = __ffs(m) - 1;
-        m &= m - 1;
+      uint32_t mycol = 0;                                // lane k: the query lanes paired with target k
+      for (unsigned mm = m; mm; mm &= mm - 1) {          // warp-uniform: m is a ballot
+        const int k = __ffs(mm) - 1;
         const v4 Pk = sP[wib][k], Lk = sL[wib][k];
         bool hit = valid && !(boxed && sB[wib][k] != box_q);   // pairs never join two boxes
         if (hit) {
@@ -233,20 +233,29 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
           ++cnt;
         }
         if (tr_on) {
-          // the other direction's lists: one atomic per (tile, target) instead of per pair
           const unsigned col = __ballot_sync(DMB_FULL, hit);
-          if (col) {
-            const int64_t tk = base + k;
-            if (!EMIT) {
-              if (lane == 0) atomicAdd(&tr.cnt[tk], (uint32_t)__popc(col));
-            } else {
-              uint32_t b0 = 0;
-              if (lane == 0) b0 = atomicAdd(&tr.cursor[tk], (uint32_t)__popc(col));
-              b0 = __shfl_sync(DMB_FULL, b0, 0);
-              if (hit) {
-                const int64_t pos = tr.ptr[tk] + b0 + __popc(col & lt);
-                if (pos < tr.ptr[tk + 1]) tr.rows[pos] = (uint32_t)qi;
-              }
+          if ((int)lane == k) mycol = col;
+        }
+      }
+      if (tr_on && m) {
+        // the other direction's lists: lane k owns target k, one atomic per (tile, target),
+        // all targets of the tile at once
+        const int64_t tk = base + lane;
+        if (!EMIT) {
+          if (mycol) atomicAdd(&tr.cnt[tk], (uint32_t)__popc(mycol));
+        } else {
+          int64_t p0 = 0, p1 = 0;
+          if (mycol) {
+            p0 = tr.ptr[tk] + atomicAdd(&tr.cursor[tk], (uint32_t)__popc(mycol));
+            p1 = tr.ptr[tk + 1];
+          }
+          for (unsigned mm = m; mm; mm &= mm - 1) {
+            const int k = __ffs(mm) - 1;
+            const unsigned col = __shfl_sync(DMB_FULL, mycol, k);
+            const int64_t s0 = __shfl_sync(DMB_FULL, p0, k), s1 = __shfl_sync(DMB_FULL, p1, k);
+            if (col & (1u << lane)) {
+              const int64_t pos = s0 + __popc(col & lt);
+              if (pos < s1) tr.rows[pos] = (uint32_t)qi;
             }
           }
         }

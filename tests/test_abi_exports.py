@@ -28,10 +28,21 @@ def test_library_exports_every_declared_symbol():
     lib = dmb.load()
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
-    assert set(dmb.EXPORTS) <= set(_declared())
+    assert set(dmb.EXPORTS) == set(_declared())        # the binding covers every entry point
 
 
 def test_no_fallback_without_library(tmp_path):
     from paper_2603_24688_gb300 import dmb
     with pytest.raises(RuntimeError):
         dmb.load(str(tmp_path / "missing.so"))
+
+
+def test_timestep_bins_keep_every_substep_between_1_and_10_percent():
+    import numpy as np
+    from paper_2603_24688_gb300 import workloads as W
+    b = W.timestep_bins(400_000, 7)
+    assert b.dtype == np.uint8 and b.min() == 0 and b.max() == 11
+    for s in (1, 2, 3, 4, 6, 8, 64, 512, 1024, 1536):
+        frac = np.mean(s % (2.0 ** b) == 0)
+        assert 0.009 < frac < 0.102, (s, frac)
+    assert np.all(0 % (2.0 ** b) == 0)          # substep 0: everything active
