@@ -115,26 +115,31 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// SiLU from h = z / 2: z sigmoid(z) = h + h tanh(h), one MUFU and one FMA
-__device__ __forceinline__ float silu_h(float h) { return fmaf(h, tanh_fast(h), h); }
-
-// 16 consecutive float32 columns of this thread's TMEM lane, issued without waiting; the wait
-// (for every load in flight) is tied to the registers it releases
-__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t r[16]) {
+// 32 consecutive float32 columns of this thread's TMEM lane; the wait is tied to the registers
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait16(uint32_t r[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
                : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
                  "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                 "+r"(r[15])
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
                :
                : "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
+
+// SiLU from h = z / 2: z sigmoid(z) = h + h tanh(h), one MUFU and one FMA
+__device__ __forceinline__ float silu_h(float h) { return fmaf(h, tanh_fast(h), h); }
 
 __device__ __forceinline__ uint32_t bf16_bits(float x) {
   const __nv_bfloat16 b = __float2bfloat16_rn(x);
@@ -366,36 +371,28 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
         break;
       }
       tc_fence_after();
-      // 16 columns at a time (h = z / 2 with the bias), the next 16 loading meanwhile
-      auto consume = [&](const uint32_t r[16], int c16) {
+#pragma unroll 1
+      for (int cc = 0; cc < MLP_H / 32; ++cc) {
+        float v[32];
+        tmem_ld32(my_lanes + 32u * cc, v);   // h = z / 2 with the bias
         if (layer < 2) {
-          uint32_t pk[8];
+          uint32_t pk[16];
 #pragma unroll
-          for (int k = 0; k < 8; ++k)
-            pk[k] = pack_bf16(silu_h(__uint_as_float(r[2 * k])), silu_h(__uint_as_float(r[2 * k + 1])));
-          *reinterpret_cast<uint4 *>(pA + (2 * c16) * TC_SLICE + t * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-          *reinterpret_cast<uint4 *>(pA + (2 * c16 + 1) * TC_SLICE + t * 16) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          for (int k = 0; k < 16; ++k)
+            pk[k] = pack_bf16(silu_h(v[2 * k]), silu_h(v[2 * k + 1]));
+#pragma unroll
+          for (int c4 = 0; c4 < 4; ++c4)
+            *reinterpret_cast<uint4 *>(pA + (4 * cc + c4) * TC_SLICE + t * 16) =
+                make_uint4(pk[4 * c4], pk[4 * c4 + 1], pk[4 * c4 + 2], pk[4 * c4 + 3]);
         } else {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int c = 16 * c16 + k;
-            const float act = silu_h(__uint_as_float(r[k]));
+          for (int k = 0; k < 32; ++k) {
+            const int c = 32 * cc + k;
+            const float act = silu_h(v[k]);
             y0 += W4[c] * act;
             y1 += W4[MLP_H + c] * act;
           }
         }
-      };
-      uint32_t ra[16], rb[16];
-      tmem_ld16_issue(my_lanes, ra);
-      tmem_wait16(ra);
-#pragma unroll 1
-      for (int c16 = 0; c16 < MLP_H / 16; c16 += 2) {
-        tmem_ld16_issue(my_lanes + 16u * (c16 + 1), rb);
-        consume(ra, c16);
-        tmem_wait16(rb);
-        if (c16 + 2 < MLP_H / 16) tmem_ld16_issue(my_lanes + 16u * (c16 + 2), ra);
-        consume(rb, c16 + 1);
-        if (c16 + 2 < MLP_H / 16) tmem_wait16(ra);
       }
     }
     if (!ok) break;
