@@ -328,106 +328,115 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
   const unsigned long long step = a.step_dev ? *a.step_dev : a.step;
   const int64_t nrows = a.list ? a.n_list : D.n;
   const R dt0 = (R)a.dt;
-  for (int64_t k = (int64_t)blockIdx.x * MC_WARPS + wib; k < nrows; k += nwarps) {
-    const int64_t i = a.list ? (int64_t)a.list[k] : k;
-    // dt_i = 2^bin dt: a power-of-two scaling, exact in the pair precision
-    const R dt = a.bin ? dt0 * (R)(1ull << a.bin[D.perm[i]]) : dt0;
-    const int64_t rs = row_ptr[i], re = row_ptr[i + 1];
-    if (re == rs) {                       // no gas partner: nothing can happen
-      if (lane == 0) {
+  // A warp visits 32 consecutive rows at a time: each lane writes the record of its row if the
+  // row is empty (no gas partner: nothing can happen; most DM particles outside the gas disk
+  // have none), and the whole warp then works through the other rows one by one.
+  for (int64_t row0 = ((int64_t)blockIdx.x * MC_WARPS + wib) * 32; row0 < nrows; row0 += nwarps * 32) {
+    const int64_t kl = row0 + lane;
+    int64_t il = 0;
+    bool busy = false;
+    if (kl < nrows) {
+      il = a.list ? (int64_t)a.list[kl] : kl;
+      busy = row_ptr[il + 1] > row_ptr[il];
+      if (!busy) {
         McRec r;
         r.c_lo = 0ull; r.c_hi = 0ull; r.rmax = 0.0f; r.flags = 0u; r.partner = 0xffffffffu;
         r.dv[0] = r.dv[1] = r.dv[2] = 0.0;
-        rec[i] = r;
+        rec[il] = r;
       }
-      continue;
     }
-    const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
-    const uint32_t id_i = D.id[i];
-    const BoxSide side = box_side<GEOM>(bx, GEOM == GEOM_BOXES ? (int)D.bid[i] : 0);
-    U128 sum = {0ull, 0ull};
-    float rmax = 0.0f;
-    for (int64_t p = rs + lane; p < re; p += 32) {
-      const uint32_t j = rows[p];
-      const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
-      R rx, ry, rz, vr;
-      const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0,
-                                      dt, step, k0, k1, rx, ry, rz, vr);
-      pcache[p] = P;
-      sum = u128_add(sum, to_fixed(P));
-      const R e = Kj.w;                                   // mu_j / (m_chi + mu_j)
-      const R cap = (R)1e-4 / (e * e) < (R)0.1 ? (R)1e-4 / (e * e) : (R)0.1;   // Eq. prob_criterion
-      rmax = fmaxf(rmax, (float)(P / cap));
-    }
-    const U128 C = warp_sum_u128(sum);
-    rmax = warp_max(rmax);
-    // selection uniform r_i = (k + 1/2) 2^-52, k the top 52 bits of (w0, w3): as a 64-bit fraction
-    const uint4 wd = philox4x32_10(dm_counter(id_i, step), k0, k1);
-    const unsigned long long k52 = ((unsigned long long)wd.x << 20) | (unsigned long long)(wd.w >> 12);
-    const unsigned long long R64 = (k52 << 12) | (1ull << 11);
-    const bool clamped = C.hi >= 1ull;                    // sum_j P_ij > 1: renormalise
-    U128 T;
-    if (clamped) T = u128_scale(R64, C); else { T.hi = 0ull; T.lo = R64; }
-    const bool scat = u128_lt(T, C);
-    bool band = near_rel(T, C, C);
-    R dv0 = 0, dv1 = 0, dv2 = 0;
-    uint32_t partner_id = 0xffffffffu;
-    if (scat) {
-      // binary search over the gas-id bits for the first partner (ascending id) whose
-      // running sum exceeds T
-      uint32_t prefix = 0;
-      U128 base = {0ull, 0ull};
-      for (int b = a.id_bits - 1; b >= 0; --b) {
-        const uint32_t mid = prefix | (1u << b);
-        U128 S = {0ull, 0ull};
-        for (int64_t p = rs + lane; p < re; p += 32) {
-          const uint32_t idj = G.id[rows[p]];
-          if (idj >= prefix && idj < mid) S = u128_add(S, to_fixed(pcache[p]));
-        }
-        S = warp_sum_u128(S);
-        const U128 top = u128_add(base, S);
-        if (!u128_lt(T, top)) { base = top; prefix = mid; }
-      }
-      int64_t pstar = -1;
-      for (int64_t p0 = rs; p0 < re; p0 += 32) {
-        const int64_t p = p0 + lane;
-        const bool hit = p < re && G.id[rows[p]] == prefix;
-        const unsigned m = __ballot_sync(DMB_FULL, hit);
-        if (m) { pstar = p0 + __ffs(m) - 1; break; }
-      }
-      if (pstar >= 0) {
-        const uint32_t j = rows[pstar];
+    for (unsigned busy_rows = __ballot_sync(DMB_FULL, busy); busy_rows; busy_rows &= busy_rows - 1) {
+      const int64_t i = __shfl_sync(DMB_FULL, il, __ffs(busy_rows) - 1);
+      // dt_i = 2^bin dt: a power-of-two scaling, exact in the pair precision
+      const R dt = a.bin ? dt0 * (R)(1ull << a.bin[D.perm[i]]) : dt0;
+      const int64_t rs = row_ptr[i], re = row_ptr[i + 1];
+      const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
+      const uint32_t id_i = D.id[i];
+      const BoxSide side = box_side<GEOM>(bx, GEOM == GEOM_BOXES ? (int)D.bid[i] : 0);
+      U128 sum = {0ull, 0ull};
+      float rmax = 0.0f;
+      for (int64_t p = rs + lane; p < re; p += 32) {
+        const uint32_t j = rows[p];
         const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
         R rx, ry, rz, vr;
-        (void)pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0, dt,
-                                  step, k0, k1, rx, ry, rz, vr);
-        const U128 hi = u128_add(base, to_fixed(pcache[pstar]));
-        band = band || near_rel(T, base, hi) || near_rel(T, hi, hi);
-        // isotropic new direction: cos(theta') = 2u - 1, phi' = 2 pi u'
-        const R ct = (R)2 * uniform23<R>(wd.y) - (R)1;
-        const R st = sqrt_t(fmax((R)0, (R)1 - ct * ct));
-        R sp, cp;
-        if (sizeof(R) == 4) { float s_, c_; sincospif(2.0f * (float)uniform23<float>(wd.z), &s_, &c_); sp = (R)s_; cp = (R)c_; }
-        else { double s_, c_; sincospi(2.0 * uniform23<double>(wd.z), &s_, &c_); sp = (R)s_; cp = (R)c_; }
-        const R f = Kj.w * vr;                             // mu_j/(m_chi + mu_j) v_rel
-        const R inv = (R)1 / vr;
-        dv0 = f * (st * cp - rx * inv);
-        dv1 = f * (st * sp - ry * inv);
-        dv2 = f * (ct - rz * inv);
-        partner_id = prefix;
+        const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0,
+                                        dt, step, k0, k1, rx, ry, rz, vr);
+        pcache[p] = P;
+        sum = u128_add(sum, to_fixed(P));
+        const R e = Kj.w;                                   // mu_j / (m_chi + mu_j)
+        const R cap = (R)1e-4 / (e * e) < (R)0.1 ? (R)1e-4 / (e * e) : (R)0.1;   // Eq. prob_criterion
+        rmax = fmaxf(rmax, (float)(P / cap));
       }
-    }
-    if (lane == 0) {
-      McRec r;
-      r.c_lo = C.lo;
-      r.c_hi = C.hi;
-      r.rmax = rmax;
-      r.flags = (partner_id != 0xffffffffu ? 1u : 0u) | (clamped ? 2u : 0u) | (band ? 4u : 0u);
-      r.partner = partner_id;
-      r.dv[0] = (double)dv0;
-      r.dv[1] = (double)dv1;
-      r.dv[2] = (double)dv2;
-      rec[i] = r;
+      const U128 C = warp_sum_u128(sum);
+      rmax = warp_max(rmax);
+      // selection uniform r_i = (k + 1/2) 2^-52, k the top 52 bits of (w0, w3): as a 64-bit fraction
+      const uint4 wd = philox4x32_10(dm_counter(id_i, step), k0, k1);
+      const unsigned long long k52 = ((unsigned long long)wd.x << 20) | (unsigned long long)(wd.w >> 12);
+      const unsigned long long R64 = (k52 << 12) | (1ull << 11);
+      const bool clamped = C.hi >= 1ull;                    // sum_j P_ij > 1: renormalise
+      U128 T;
+      if (clamped) T = u128_scale(R64, C); else { T.hi = 0ull; T.lo = R64; }
+      const bool scat = u128_lt(T, C);
+      bool band = near_rel(T, C, C);
+      R dv0 = 0, dv1 = 0, dv2 = 0;
+      uint32_t partner_id = 0xffffffffu;
+      if (scat) {
+        // binary search over the gas-id bits for the first partner (ascending id) whose
+        // running sum exceeds T
+        uint32_t prefix = 0;
+        U128 base = {0ull, 0ull};
+        for (int b = a.id_bits - 1; b >= 0; --b) {
+          const uint32_t mid = prefix | (1u << b);
+          U128 S = {0ull, 0ull};
+          for (int64_t p = rs + lane; p < re; p += 32) {
+            const uint32_t idj = G.id[rows[p]];
+            if (idj >= prefix && idj < mid) S = u128_add(S, to_fixed(pcache[p]));
+          }
+          S = warp_sum_u128(S);
+          const U128 top = u128_add(base, S);
+          if (!u128_lt(T, top)) { base = top; prefix = mid; }
+        }
+        int64_t pstar = -1;
+        for (int64_t p0 = rs; p0 < re; p0 += 32) {
+          const int64_t p = p0 + lane;
+          const bool hit = p < re && G.id[rows[p]] == prefix;
+          const unsigned m = __ballot_sync(DMB_FULL, hit);
+          if (m) { pstar = p0 + __ffs(m) - 1; break; }
+        }
+        if (pstar >= 0) {
+          const uint32_t j = rows[pstar];
+          const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
+          R rx, ry, rz, vr;
+          (void)pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0, dt,
+                                    step, k0, k1, rx, ry, rz, vr);
+          const U128 hi = u128_add(base, to_fixed(pcache[pstar]));
+          band = band || near_rel(T, base, hi) || near_rel(T, hi, hi);
+          // isotropic new direction: cos(theta') = 2u - 1, phi' = 2 pi u'
+          const R ct = (R)2 * uniform23<R>(wd.y) - (R)1;
+          const R st = sqrt_t(fmax((R)0, (R)1 - ct * ct));
+          R sp, cp;
+          if (sizeof(R) == 4) { float s_, c_; sincospif(2.0f * (float)uniform23<float>(wd.z), &s_, &c_); sp = (R)s_; cp = (R)c_; }
+          else { double s_, c_; sincospi(2.0 * uniform23<double>(wd.z), &s_, &c_); sp = (R)s_; cp = (R)c_; }
+          const R f = Kj.w * vr;                             // mu_j/(m_chi + mu_j) v_rel
+          const R inv = (R)1 / vr;
+          dv0 = f * (st * cp - rx * inv);
+          dv1 = f * (st * sp - ry * inv);
+          dv2 = f * (ct - rz * inv);
+          partner_id = prefix;
+        }
+      }
+      if (lane == 0) {
+        McRec r;
+        r.c_lo = C.lo;
+        r.c_hi = C.hi;
+        r.rmax = rmax;
+        r.flags = (partner_id != 0xffffffffu ? 1u : 0u) | (clamped ? 2u : 0u) | (band ? 4u : 0u);
+        r.partner = partner_id;
+        r.dv[0] = (double)dv0;
+        r.dv[1] = (double)dv1;
+        r.dv[2] = (double)dv2;
+        rec[i] = r;
+      }
     }
   }
 }
@@ -497,7 +506,7 @@ cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int
                       int blocks_per_sm, cudaStream_t s, int64_t *launches) {
   const int64_t nrows = a.list ? a.n_list : D.n;
   if (nrows <= 0) return cudaSuccess;
-  int64_t blocks = (nrows + MC_WARPS - 1) / MC_WARPS;
+  int64_t blocks = (nrows + 32 * MC_WARPS - 1) / (32 * MC_WARPS);   // 32 rows per warp visit
   if (blocks > 152 * (int64_t)blocks_per_sm) blocks = 152 * (int64_t)blocks_per_sm;
   switch (geom_of(bx)) {
     case GEOM_OPEN: k_mc<R, GEOM_OPEN><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec); break;
