@@ -328,11 +328,13 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
   const unsigned long long step = a.step_dev ? *a.step_dev : a.step;
   const int64_t nrows = a.list ? a.n_list : D.n;
   const R dt0 = (R)a.dt;
-  // A warp visits 32 consecutive rows at a time: each lane writes the record of its row if the
-  // row is empty (no gas partner: nothing can happen; most DM particles outside the gas disk
-  // have none), and the whole warp then works through the other rows one by one.
-  for (int64_t row0 = ((int64_t)blockIdx.x * MC_WARPS + wib) * 32; row0 < nrows; row0 += nwarps * 32) {
-    const int64_t kl = row0 + lane;
+  // Warp w takes rows w, w + W, w + 2W, ... (W warps in the grid), 32 of them per visit: each
+  // lane writes the record of its row if the row is empty (no gas partner: nothing can happen;
+  // most DM particles outside the gas disk have none), and the whole warp then works through
+  // the other rows one by one.
+  const int64_t warp_id = (int64_t)blockIdx.x * MC_WARPS + wib;
+  for (int64_t row0 = warp_id; row0 < nrows; row0 += 32 * nwarps) {
+    const int64_t kl = row0 + (int64_t)lane * nwarps;
     int64_t il = 0;
     bool busy = false;
     if (kl < nrows) {
@@ -506,7 +508,7 @@ cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int
                       int blocks_per_sm, cudaStream_t s, int64_t *launches) {
   const int64_t nrows = a.list ? a.n_list : D.n;
   if (nrows <= 0) return cudaSuccess;
-  int64_t blocks = (nrows + 32 * MC_WARPS - 1) / (32 * MC_WARPS);   // 32 rows per warp visit
+  int64_t blocks = (nrows + MC_WARPS - 1) / MC_WARPS;
   if (blocks > 152 * (int64_t)blocks_per_sm) blocks = 152 * (int64_t)blocks_per_sm;
   switch (geom_of(bx)) {
     case GEOM_OPEN: k_mc<R, GEOM_OPEN><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec); break;
