@@ -44,7 +44,8 @@ struct SpeciesBufs {
 
 // Pair-search scratch of one direction (queries of one species against the other's tree).
 struct SearchBufs {
-  DevBuf item_cnt, item_ptr, items, unit_cnt_leaf, unit_ptr, unit_leaf, unit_item0, unit_cnt, counts, row_ptr, rows;
+  DevBuf item_cnt, item_ptr, items, unit_cnt_leaf, unit_ptr, unit_leaf, unit_item0, unit_cnt, counts, row_ptr, rows,
+      tmask;
   int64_t n_items = 0, n_units = 0, n_pairs = 0;
 };
 
@@ -340,7 +341,8 @@ dmb_status search_stage2_count(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, S
   int64_t *L = &ctx->launches;
   const int nleaf = Q.cnt[0];
   if (!ensure(sb.items, (size_t)sb.n_items * 4) || !ensure(sb.unit_leaf, (size_t)sb.n_units * 4) ||
-      !ensure(sb.unit_item0, (size_t)sb.n_units * 8) || !ensure(sb.unit_cnt, (size_t)sb.n_units * 32 * 4))
+      !ensure(sb.unit_item0, (size_t)sb.n_units * 8) || !ensure(sb.unit_cnt, (size_t)sb.n_units * 32 * 4) ||
+      !ensure(sb.tmask, (size_t)sb.n_items * 32 * 4))
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for search lists");
   const Frame *fr = ptr<Frame>(ctx->frame);
   uint32_t *status = ptr<uint32_t>(ctx->status);
@@ -350,7 +352,8 @@ dmb_status search_stage2_count(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, S
                      ptr<int64_t>(sb.unit_item0), s, L), "unit map");
   CK(launch_tile<R>(Q, O, ctx->bx, fr, false, ptr<uint32_t>(sb.unit_leaf), ptr<int64_t>(sb.unit_item0),
                     ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), sb.n_units, ctx->shp.unit,
-                    ptr<uint32_t>(sb.unit_cnt), nullptr, nullptr, tr, status, stats, s, L), "tile (count)");
+                    ptr<uint32_t>(sb.unit_cnt), nullptr, nullptr, tr, ptr<uint32_t>(sb.tmask), status, stats, s, L),
+     "tile (count)");
   CK(launch_unit_prefix(ptr<int64_t>(sb.unit_ptr), nleaf, Q.n, ptr<uint32_t>(sb.unit_cnt), ptr<uint32_t>(sb.counts), s,
                         L), "unit prefix");
   CK(exclusive_scan_u32_i64(ptr<uint32_t>(sb.counts), ptr<int64_t>(sb.row_ptr), Q.n, ptr<int64_t>(ctx->scan_tmp), s, L),
@@ -364,7 +367,8 @@ dmb_status search_stage2_emit(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, Sp
   CK(launch_tile<R>(Q, O, ctx->bx, ptr<Frame>(ctx->frame), true, ptr<uint32_t>(sb.unit_leaf),
                     ptr<int64_t>(sb.unit_item0), ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), sb.n_units,
                     ctx->shp.unit, ptr<uint32_t>(sb.unit_cnt), ptr<int64_t>(sb.row_ptr), ptr<uint32_t>(sb.rows), tr,
-                    ptr<uint32_t>(ctx->status), nullptr, ctx->stream, &ctx->launches), "tile (emit)");
+                    ptr<uint32_t>(sb.tmask), ptr<uint32_t>(ctx->status), nullptr, ctx->stream, &ctx->launches),
+     "tile (emit)");
   return DMB_OK;
 }
 
@@ -928,7 +932,7 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   for (SearchBufs *sb : {&ctx->sg, &ctx->sd}) {
     DevBuf *q[] = {&sb->item_cnt, &sb->item_ptr, &sb->items, &sb->unit_cnt_leaf, &sb->unit_ptr, &sb->unit_leaf,
-                   &sb->unit_item0, &sb->unit_cnt, &sb->counts, &sb->row_ptr, &sb->rows};
+                   &sb->unit_item0, &sb->unit_cnt, &sb->counts, &sb->row_ptr, &sb->rows, &sb->tmask};
     for (DevBuf *b : q) release(*b);
   }
   DevBuf *bufs[] = {&ctx->frame, &ctx->status, &ctx->frame_part, &ctx->gtab, &ctx->hist, &ctx->hist_scan,

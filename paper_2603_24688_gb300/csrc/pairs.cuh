@@ -45,12 +45,15 @@ struct TransposeOut {
   uint32_t *rows = nullptr;      // [pairs] (emit pass)
 };
 
+// tmask (optional, [items][32] uint32): the count pass stores each tile's pair masks (entry k:
+// the query lanes paired with target k of the item's leaf) and the emit pass reads them instead
+// of testing the distances again.
 template <typename R>
 cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
                         const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
                         const uint32_t *items, int64_t n_units, int unit, uint32_t *unit_cnt, const int64_t *row_ptr,
-                        uint32_t *rows, TransposeOut tr, uint32_t *status, unsigned long long *stats, cudaStream_t s,
-                        int64_t *launches);
+                        uint32_t *rows, TransposeOut tr, uint32_t *tmask, uint32_t *status, unsigned long long *stats,
+                        cudaStream_t s, int64_t *launches);
 cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, uint32_t *unit_cnt, uint32_t *counts,
                                cudaStream_t s, int64_t *launches);
 

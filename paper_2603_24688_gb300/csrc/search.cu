@@ -9,6 +9,8 @@
 // target's new partners, counted (and later placed) with one atomic.  The order inside a
 // target row then follows the tiles' completion; the Monte Carlo, which reads those rows, sums
 // them exactly in fixed point and selects partners by gas id, so no result depends on it.
+// The count pass keeps every tile's 32 x 32 pair mask (128 bytes per candidate leaf pair); the
+// emit pass reads the masks and writes both lists without testing a distance again.
 #include "pairs.cuh"
 #include "physics.cuh"
 
@@ -64,6 +66,27 @@ __device__ __forceinline__ float box_gap2(const float qmn[3], const float qmx[3]
   float d2 = box_gap2_one(qmn, qmx, nmn, nmx, GEOM != GEOM_OPEN, ls.a);
   if (GEOM == GEOM_BOXES && ls.two) d2 = fminf(d2, box_gap2_one(qmn, qmx, nmn, nmx, 1, ls.b));
   return d2;
+}
+
+// Emit of the target-major lists for one tile: lane k owns target k (mycol = the query lanes
+// paired with it), claims its positions with one atomic, and every query lane writes its entries.
+__device__ __forceinline__ void emit_transposed(const TransposeOut &tr, int64_t base, unsigned lane, unsigned lt,
+                                               unsigned m, uint32_t mycol, int64_t qi) {
+  const int64_t tk = base + lane;
+  int64_t p0 = 0, p1 = 0;
+  if (mycol) {
+    p0 = tr.ptr[tk] + atomicAdd(&tr.cursor[tk], (uint32_t)__popc(mycol));
+    p1 = tr.ptr[tk + 1];
+  }
+  for (unsigned mm = m; mm; mm &= mm - 1) {
+    const int k = __ffs(mm) - 1;
+    const unsigned col = __shfl_sync(DMB_FULL, mycol, k);
+    const int64_t s0 = __shfl_sync(DMB_FULL, p0, k), s1 = __shfl_sync(DMB_FULL, p1, k);
+    if (col & (1u << lane)) {
+      const int64_t pos = s0 + __popc(col & lt);
+      if (pos < s1) tr.rows[pos] = (uint32_t)qi;
+    }
+  }
 }
 
 // ---- stage 1: candidate target leaves per query leaf -----------------------------------
@@ -164,7 +187,7 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
        const uint32_t *__restrict__ unit_leaf, const int64_t *__restrict__ unit_item0,
        const int64_t *__restrict__ item_ptr, const uint32_t *__restrict__ items, int64_t n_units, int unit,
        uint32_t *__restrict__ unit_cnt, const int64_t *__restrict__ row_ptr, uint32_t *__restrict__ rows,
-       TransposeOut tr, uint32_t *status, unsigned long long *__restrict__ stats) {
+       TransposeOut tr, uint32_t *__restrict__ tmask, uint32_t *status, unsigned long long *__restrict__ stats) {
   typedef typename Vec<R>::v4 v4;
   __shared__ v4 sP[SR_WARPS][DMB_LEAF];
   __shared__ v4 sL[SR_WARPS][DMB_LEAF];
@@ -174,6 +197,7 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
   const float pad2 = 2.0f * frame->pad;
   const bool boxed = GEOM == GEOM_BOXES;
   const bool tr_on = EMIT ? tr.rows != nullptr : tr.cnt != nullptr;
+  const bool want_col = tr_on || (!EMIT && tmask != nullptr);
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long st_tests = 0, st_leaves = 0;
   for (int64_t u = (int64_t)blockIdx.x * SR_WARPS + wib; u < n_units; u += (int64_t)gridDim.x * SR_WARPS) {
@@ -197,6 +221,21 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
     }
     for (int64_t it = it0; it < it1; ++it) {
       const int64_t base = (int64_t)items[it] * DMB_LEAF;
+      if (EMIT && tmask != nullptr) {
+        // the count pass left this tile's pair masks (lane k: the query lanes paired with
+        // target k): the emit pass writes the pairs without testing distances again
+        const uint32_t mycol = tmask[32 * it + lane];
+        const unsigned m = __ballot_sync(DMB_FULL, mycol != 0u);
+        for (unsigned mm = m; mm; mm &= mm - 1) {
+          const int k = __ffs(mm) - 1;
+          if (__shfl_sync(DMB_FULL, mycol, k) & (1u << lane)) {
+            if (out < out_end) rows[out] = (uint32_t)(base + k);
+            ++out;
+          }
+        }
+        if (tr_on && m) emit_transposed(tr, base, lane, lt, m, mycol, qi);
+        continue;
+      }
       const int nk = (int)min((int64_t)DMB_LEAF, O.n - base);
       bool keep = false;
       __syncwarp();
@@ -232,32 +271,19 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
           }
           ++cnt;
         }
-        if (tr_on) {
+        if (want_col) {
           const unsigned col = __ballot_sync(DMB_FULL, hit);
           if ((int)lane == k) mycol = col;
         }
       }
+      if (!EMIT && tmask != nullptr) tmask[32 * it + lane] = mycol;
       if (tr_on && m) {
         // the other direction's lists: lane k owns target k, one atomic per (tile, target),
         // all targets of the tile at once
-        const int64_t tk = base + lane;
         if (!EMIT) {
-          if (mycol) atomicAdd(&tr.cnt[tk], (uint32_t)__popc(mycol));
+          if (mycol) atomicAdd(&tr.cnt[base + lane], (uint32_t)__popc(mycol));
         } else {
-          int64_t p0 = 0, p1 = 0;
-          if (mycol) {
-            p0 = tr.ptr[tk] + atomicAdd(&tr.cursor[tk], (uint32_t)__popc(mycol));
-            p1 = tr.ptr[tk + 1];
-          }
-          for (unsigned mm = m; mm; mm &= mm - 1) {
-            const int k = __ffs(mm) - 1;
-            const unsigned col = __shfl_sync(DMB_FULL, mycol, k);
-            const int64_t s0 = __shfl_sync(DMB_FULL, p0, k), s1 = __shfl_sync(DMB_FULL, p1, k);
-            if (col & (1u << lane)) {
-              const int64_t pos = s0 + __popc(col & lt);
-              if (pos < s1) tr.rows[pos] = (uint32_t)qi;
-            }
-          }
+          emit_transposed(tr, base, lane, lt, m, mycol, qi);
         }
       }
     }
@@ -363,13 +389,13 @@ template <typename R>
 cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
                         const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
                         const uint32_t *items, int64_t n_units, int unit, uint32_t *unit_cnt, const int64_t *row_ptr,
-                        uint32_t *rows, TransposeOut tr, uint32_t *status, unsigned long long *stats, cudaStream_t s,
-                        int64_t *launches) {
+                        uint32_t *rows, TransposeOut tr, uint32_t *tmask, uint32_t *status, unsigned long long *stats,
+                        cudaStream_t s, int64_t *launches) {
   if (n_units <= 0) return cudaSuccess;
   const int g = grid_for(n_units);
 #define TL(E, G)                                                                                                \
   k_tile<R, E, G><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items, n_units, unit, \
-                                              unit_cnt, row_ptr, rows, tr, status, stats)
+                                              unit_cnt, row_ptr, rows, tr, tmask, status, stats)
   switch (geom_of(bx) * 2 + (emit ? 1 : 0)) {
     case 0: TL(false, GEOM_OPEN); break;
     case 1: TL(true, GEOM_OPEN); break;
@@ -398,6 +424,7 @@ cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, u
   template cudaError_t launch_tile<R>(SpeciesView<R>, SpeciesView<R>, BoxSplit, const Frame *, bool,                \
                                       const uint32_t *, const int64_t *, const int64_t *, const uint32_t *, int64_t, \
                                       int, uint32_t *, const int64_t *, uint32_t *, TransposeOut, uint32_t *,         \
+                                      uint32_t *,                                                                    \
                                       unsigned long long *,                                                          \
                                       cudaStream_t, int64_t *);
 INST(float)
