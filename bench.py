@@ -44,6 +44,12 @@ QUAD_OPS_PER_PAIR = 64 * 16 + 120.0
 MLP_TANH_PER_PAIR = 3 * 128
 MUFU_LANES = 16
 MLP_TENSOR_FLOP_PER_PAIR = 2.0 * 128 * (16 + 128 + 128)
+# DRAM bytes per pair of the surrogate pass from one ncu capture of the current kernel on galaxy1M
+# (dram__bytes_read.sum + dram__bytes_write.sum = 712 + 639 MB for 85,071,169 pairs), scaled to
+# a launch by its pair count; algorithmic bytes: row index, DM index, two 16-byte velocity
+# copies read and the 8-byte rates written per pair
+MLP_DRAM_BYTES_PER_PAIR = (712.444160e6 + 639.415552e6) / 85071169
+MLP_ALGO_BYTES_PER_PAIR = 4 + 4 + 16 + 16 + 8
 
 
 def parse():
@@ -437,7 +443,10 @@ def main():
             tpeak = peaks.get("bf16_tflops_sustained", 1700.0)
             tach = MLP_TENSOR_FLOP_PER_PAIR * npairs / ts / 1e12
             return {"bound": "alu", "achieved": ach, "peak": mufu_peak, "unit": "T tanh/s", "frac": ach / mufu_peak,
-                    "traffic": None, "kernel": "k_mlp_tc (surrogate pass, 3 tanh layers of 128 per pair)",
+                    "traffic": MLP_DRAM_BYTES_PER_PAIR * npairs, "traffic_unit": "bytes per launch",
+                    "traffic_source": "ncu capture of this kernel on galaxy1M, scaled by the pair count",
+                    "algorithmic_bytes": MLP_ALGO_BYTES_PER_PAIR * npairs,
+                    "kernel": "k_mlp_tc (surrogate pass, 3 tanh layers of 128 per pair)",
                     "peak_source": "152 SMs x 16 MUFU lanes x max SM clock (unit counts); measured tanh 4.94 T/s",
                     "kernel_ms": surrogate_ms,
                     "tensor": {"achieved": tach, "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
