@@ -186,6 +186,12 @@ def cpu_oracle_sample(w, budget_s=12.0, target_pairs=150_000, seed=0):
     return n / t, n, t, desc
 
 
+def workload_desc(a, w):
+    """The config's workload string, the same for both arms."""
+    return (f"{a.workload}: {len(w['dm']['h'])} DM Hernquist halo + {len(w['gas']['h'])} gas exponential disk, "
+            f"sigma = 1e-24 cm^2 (v / 100 km/s)^{a.n}")
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -201,7 +207,8 @@ def run_reference(a):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(v[2] for v in vals) / len(vals),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": a.workload + f" (bounded spatial samples), n={a.n}", "rate_provider": "closed"},
+            "config": {"workload": workload_desc(a, w),
+                       "rate_provider": "closed-form 1F1 (the oracle; timed on bounded spatial samples)"},
             "cpu_baseline": {"value": rate, "unit": "pairs/s", "cores": 1, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": rate, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -542,9 +549,7 @@ def main():
         line = {"metric": "pair_interactions_per_s", "value": value, "unit": "pairs/s", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 sums", "data": "synthetic",
-                "config": {"workload": f"{a.workload}: {len(w['dm']['h'])} DM Hernquist halo + "
-                                       f"{len(w['gas']['h'])} gas exponential disk, "
-                                       f"sigma = 1e-24 cm^2 (v / 100 km/s)^{a.n}",
+                "config": {"workload": workload_desc(a, w),
                            "rate_provider": {"mlp": "learned surrogate (tcgen05 tensor cores)",
                                              "quad": "64-point Gauss-Legendre quadrature",
                                              "closed": "closed-form 1F1"}[a.rate],
