@@ -39,16 +39,17 @@ LANES = 128
 OPS_PER_PAIR = {"meanfield": 150.0, "mc": 256.0}
 # quadrature provider: 64 nodes x (2 exp + ~14 ops) + the 120 ops of the rest of the pair
 QUAD_OPS_PER_PAIR = 64 * 16 + 120.0
-# learned surrogate per pair: 3 x 128 SiLU activations, one hardware tanh each (the MUFU pipe:
-# 16 lanes per SM per clock), and 2 x 128 x (16 + 128 + 128) bf16 tensor-core flop
-MLP_TANH_PER_PAIR = 3 * 128
-MUFU_LANES = 16
-MLP_TENSOR_FLOP_PER_PAIR = 2.0 * 128 * (16 + 128 + 128)
+# learned surrogate per pair: the network's dense contraction, 2 x (4 x 128 + 2 x 128 x 128 +
+# 128 x 2) flop (bf16 tensor cores for the 128-wide layers), and the flop the tensor cores issue
+# for it: 2 x 128 x (16 + 16 + 128 + 16 + 128 + 16) (layer 1 as a K = 16 hi/lo product, one K = 16
+# bias slice per layer).  The squared-ReLU epilogue needs no special function.
+MLP_FLOP_PER_PAIR = 2.0 * (4 * 128 + 2 * 128 * 128 + 128 * 2)
+MLP_TENSOR_FLOP_PER_PAIR = 2.0 * 128 * (16 + 16 + 128 + 16 + 128 + 16)
 # DRAM bytes per pair of the surrogate pass from one ncu capture of the current kernel on galaxy1M
-# (dram__bytes_read.sum + dram__bytes_write.sum = 712 + 639 MB for 85,071,169 pairs), scaled to
-# a launch by its pair count; algorithmic bytes: row index, DM index, two 16-byte velocity
-# copies read and the 8-byte rates written per pair
-MLP_DRAM_BYTES_PER_PAIR = (712.444160e6 + 639.415552e6) / 85071169
+# (dram__bytes_read.sum + dram__bytes_write.sum for the pairs of that launch), scaled to a launch
+# by its pair count; None while the kernel has changed since the capture.  Algorithmic bytes: row
+# index, DM index, two 16-byte velocity copies read and the 8-byte rates written per pair
+MLP_DRAM_BYTES_PER_PAIR = None
 MLP_ALGO_BYTES_PER_PAIR = 4 + 4 + 16 + 16 + 8
 
 
@@ -442,22 +443,22 @@ def main():
         k = names.index(stage)
         t = per_step[k] * 1e-3
         if stage == "meanfield" and a.rate == "mlp" and surrogate_ms > 0:
-            # the surrogate's tensor-core pass (k_mlp_tc) timed alone: bound by the MUFU pipe
-            # (one tanh per activation); its tensor-core rate is reported beside it
+            # the surrogate's tensor-core pass (k_mlp_tc), timed alone inside the step: bound by
+            # the tensor cores (bf16 operands, float32 accumulation)
             ts = surrogate_ms * 1e-3
-            mufu_peak = SMS * MUFU_LANES * fmax_ghz * 1e9 / 1e12
-            ach = MLP_TANH_PER_PAIR * npairs / ts / 1e12
             tpeak = peaks.get("bf16_tflops_sustained", 1700.0)
-            tach = MLP_TENSOR_FLOP_PER_PAIR * npairs / ts / 1e12
-            return {"bound": "alu", "achieved": ach, "peak": mufu_peak, "unit": "T tanh/s", "frac": ach / mufu_peak,
-                    "traffic": MLP_DRAM_BYTES_PER_PAIR * npairs, "traffic_unit": "bytes per launch",
+            ach = MLP_FLOP_PER_PAIR * npairs / ts / 1e12
+            issued = MLP_TENSOR_FLOP_PER_PAIR * npairs / ts / 1e12
+            traffic = None if MLP_DRAM_BYTES_PER_PAIR is None else MLP_DRAM_BYTES_PER_PAIR * npairs
+            return {"bound": "tensor", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s", "frac": ach / tpeak,
+                    "traffic": traffic, "traffic_unit": "bytes per launch",
                     "traffic_source": "ncu capture of this kernel on galaxy1M, scaled by the pair count",
                     "algorithmic_bytes": MLP_ALGO_BYTES_PER_PAIR * npairs,
-                    "kernel": "k_mlp_tc (surrogate pass, 3 tanh layers of 128 per pair)",
-                    "peak_source": "152 SMs x 16 MUFU lanes x max SM clock (unit counts); measured tanh 4.94 T/s",
-                    "kernel_ms": surrogate_ms,
-                    "tensor": {"achieved": tach, "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
-                               "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind})"}}
+                    "kernel": "k_mlp_tc (surrogate pass: 4 -> 128 -> 128 -> 128 -> 2 per pair)",
+                    "flop_per_pair": MLP_FLOP_PER_PAIR,
+                    "issued_tflops": issued, "issued_flop_per_pair": MLP_TENSOR_FLOP_PER_PAIR,
+                    "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind})",
+                    "kernel_ms": surrogate_ms}
         if stage in OPS_PER_PAIR:
             ops = OPS_PER_PAIR[stage] if not (stage == "meanfield" and a.rate == "quad") else QUAD_OPS_PER_PAIR
             ach = ops * npairs / t / 1e12

@@ -265,8 +265,8 @@ dmb_status dmb_stage_times(dmb_ctx *ctx, double *ms_out, int64_t *steps_out);
 dmb_status dmb_search_stats(dmb_ctx *ctx, uint64_t *out16);
 
 /* ---- learned surrogate of the rate integrals (rate_mode = DMB_RATE_MLP) ------------------
- * A 4 -> 128 -> 128 -> 128 -> 2 MLP (SiLU; bf16 tensor-core hidden layers, float32
- * accumulation) standing in for FA, FB of Eqs. scrA/scrB (the App. B normalisation).  Inputs
+ * A 4 -> 128 -> 128 -> 128 -> 2 MLP (squared-ReLU activations max(z, 0)^2; bf16 tensor-core
+ * hidden layers, float32 accumulation) standing in for FA, FB of Eqs. scrA/scrB (the App. B normalisation).  Inputs
  * log10(s)/2, log10(tau)/2, log10(m_chi/m_p), n/4 with s = w/varsigma, tau = varsigma^2/v0^2;
  * outputs the residuals of log FA, log FB against envelopes with the exact small- and large-x
  * limits.  The paper has no surrogate: it evaluates 1F1 (Sec. 2.4); quadrature is the

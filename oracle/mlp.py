@@ -2,7 +2,8 @@
 
 The paper has no surrogate (it evaluates 1F1, Sec. 2.4); this module restates the network the
 library trains, so that the GPU forward and backward kernels can be checked element by
-element: a 4 -> 128 -> 128 -> 128 -> 2 MLP with SiLU, parameters packed as
+element: a 4 -> 128 -> 128 -> 128 -> 2 MLP with the squared ReLU act(z) = max(z, 0)^2 as its
+activation, parameters packed as
 W1[128][4] b1 W2[128][128] b2 W3[128][128] b3 W4[2][128] b4.  The GPU feeds the two
 128 x 128 layers bf16 operands (weights and activations rounded to nearest even) and
 accumulates in float32; `forward(..., bf16=True)` applies the same roundings in float64.
@@ -48,13 +49,15 @@ def bf16(x):
     return b.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def silu(z):
-    return z / (1.0 + np.exp(-z))
+def act(z):
+    """Squared ReLU, max(z, 0)^2."""
+    r = np.maximum(z, 0.0)
+    return r * r
 
 
-def silu_grad(z):
-    s = 1.0 / (1.0 + np.exp(-z))
-    return s * (1.0 + z * (1.0 - s))
+def act_grad(z):
+    """d act / dz = 2 max(z, 0) (continuous, so the loss is once differentiable everywhere)."""
+    return 2.0 * np.maximum(z, 0.0)
 
 
 def forward(p, X, bf16_ops=True):
@@ -62,11 +65,11 @@ def forward(p, X, bf16_ops=True):
     d = unpack(p)
     r = bf16 if bf16_ops else (lambda v: np.asarray(v, dtype=np.float64))
     z1 = X @ d["W1"].T + d["b1"]
-    a1 = r(silu(z1))
+    a1 = r(act(z1))
     z2 = a1 @ r(d["W2"]).T + d["b2"]
-    a2 = r(silu(z2))
+    a2 = r(act(z2))
     z3 = a2 @ r(d["W3"]).T + d["b3"]
-    a3 = silu(z3)
+    a3 = act(z3)
     y = a3 @ d["W4"].T + d["b4"]
     return y, dict(X=X, z1=z1, a1=a1, z2=z2, a2=a2, z3=z3, a3=a3, d=d)
 
@@ -82,15 +85,15 @@ def loss_and_grad(p, X, Y, bf16_ops=True):
     g = {}
     g["W4"] = dy.T @ c["a3"]
     g["b4"] = dy.sum(0)
-    dz3 = (dy @ d["W4"]) * silu_grad(c["z3"])
+    dz3 = (dy @ d["W4"]) * act_grad(c["z3"])
     dz3r = r(dz3)
     g["W3"] = dz3r.T @ c["a2"]
     g["b3"] = dz3r.sum(0)
-    dz2 = (dz3r @ r(d["W3"])) * silu_grad(c["z2"])
+    dz2 = (dz3r @ r(d["W3"])) * act_grad(c["z2"])
     dz2r = r(dz2)
     g["W2"] = dz2r.T @ c["a1"]
     g["b2"] = dz2r.sum(0)
-    dz1 = (dz2r @ r(d["W2"])) * silu_grad(c["z1"])
+    dz1 = (dz2r @ r(d["W2"])) * act_grad(c["z1"])
     g["W1"] = dz1.T @ c["X"]
     g["b1"] = dz1.sum(0)
     return loss, pack(g)

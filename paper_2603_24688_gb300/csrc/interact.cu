@@ -146,7 +146,7 @@ k_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *__re
         float z0 = M.b1[c], z1 = M.b1[c + 1];
 #pragma unroll
         for (int m = 0; m < MLP_IN; ++m) { z0 += M.W1[c * MLP_IN + m] * xin[m]; z1 += M.W1[(c + 1) * MLP_IN + m] * xin[m]; }
-        *reinterpret_cast<uint32_t *>(arow + c) = pack_bf16(silu(z0), silu(z1));
+        *reinterpret_cast<uint32_t *>(arow + c) = pack_bf16(mlp_act(z0), mlp_act(z1));
       }
       __syncwarp();
       float y[2][2][MLP_OUT] = {{{0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}}};

@@ -117,7 +117,7 @@ k_mlp_forward_train(const float *__restrict__ p, const __nv_bfloat16 *__restrict
         if (v1) tb.Z1[r1 * MLP_H + col] = acc[nt][2 + e];
       }
     for (int nt = 0; nt < 16; ++nt)
-      for (int e = 0; e < 4; ++e) acc[nt][e] = silu(acc[nt][e]);
+      for (int e = 0; e < 4; ++e) acc[nt][e] = mlp_act(acc[nt][e]);
     for (int kt = 0; kt < 8; ++kt) {
       af[kt][0] = pack_bf16(acc[2 * kt][0], acc[2 * kt][1]);
       af[kt][1] = pack_bf16(acc[2 * kt][2], acc[2 * kt][3]);
@@ -140,7 +140,7 @@ k_mlp_forward_train(const float *__restrict__ p, const __nv_bfloat16 *__restrict
         if (v1) tb.Z2[r1 * MLP_H + col] = acc[nt][2 + e];
       }
     for (int nt = 0; nt < 16; ++nt)
-      for (int e = 0; e < 4; ++e) acc[nt][e] = silu(acc[nt][e]);
+      for (int e = 0; e < 4; ++e) acc[nt][e] = mlp_act(acc[nt][e]);
     for (int kt = 0; kt < 8; ++kt) {
       af[kt][0] = pack_bf16(acc[2 * kt][0], acc[2 * kt][1]);
       af[kt][1] = pack_bf16(acc[2 * kt][2], acc[2 * kt][3]);
@@ -157,7 +157,7 @@ k_mlp_forward_train(const float *__restrict__ p, const __nv_bfloat16 *__restrict
       for (int e = 0; e < 2; ++e) {
         const int col = nt * 8 + tig * 2 + e;
         const float zl = acc[nt][e] + M.b3[col], zh = acc[nt][2 + e] + M.b3[col];
-        const float al = silu(zl), ah = silu(zh);
+        const float al = mlp_act(zl), ah = mlp_act(zh);
         if (v0) { tb.Z3[r0 * MLP_H + col] = zl; tb.A3[r0 * MLP_H + col] = al; }
         if (v1) { tb.Z3[r1 * MLP_H + col] = zh; tb.A3[r1 * MLP_H + col] = ah; }
         for (int o = 0; o < MLP_OUT; ++o) { pl[o] += M.W4[o * MLP_H + col] * al; ph[o] += M.W4[o * MLP_H + col] * ah; }
@@ -203,14 +203,14 @@ k_mlp_backward(const float *__restrict__ p, const __nv_bfloat16 *__restrict__ w2
     for (int o = 0; o < MLP_OUT; ++o) { dyl[o] = v0 ? tb.dY[2 * r0 + o] : 0.f; dyh[o] = v1 ? tb.dY[2 * r1 + o] : 0.f; }
     float acc[16][4];
     uint32_t af[8][4];
-    // dz3 = (W4^T dy) * silu'(z3)
+    // dz3 = (W4^T dy) * act'(z3)
     for (int nt = 0; nt < 16; ++nt)
       for (int e = 0; e < 2; ++e) {
         const int col = nt * 8 + tig * 2 + e;
         float dl = 0.f, dh = 0.f;
         for (int o = 0; o < MLP_OUT; ++o) { dl += M.W4[o * MLP_H + col] * dyl[o]; dh += M.W4[o * MLP_H + col] * dyh[o]; }
-        acc[nt][e] = v0 ? dl * silu_grad(tb.Z3[r0 * MLP_H + col]) : 0.f;
-        acc[nt][2 + e] = v1 ? dh * silu_grad(tb.Z3[r1 * MLP_H + col]) : 0.f;
+        acc[nt][e] = v0 ? dl * mlp_act_grad(tb.Z3[r0 * MLP_H + col]) : 0.f;
+        acc[nt][2 + e] = v1 ? dh * mlp_act_grad(tb.Z3[r1 * MLP_H + col]) : 0.f;
       }
     for (int kt = 0; kt < 8; ++kt) {
       af[kt][0] = pack_bf16(acc[2 * kt][0], acc[2 * kt][1]);
@@ -221,13 +221,13 @@ k_mlp_backward(const float *__restrict__ p, const __nv_bfloat16 *__restrict__ w2
       if (v0) { *reinterpret_cast<uint32_t *>(&tb.dZ3[r0 * MLP_H + c0]) = af[kt][0]; *reinterpret_cast<uint32_t *>(&tb.dZ3[r0 * MLP_H + c0 + 8]) = af[kt][2]; }
       if (v1) { *reinterpret_cast<uint32_t *>(&tb.dZ3[r1 * MLP_H + c0]) = af[kt][1]; *reinterpret_cast<uint32_t *>(&tb.dZ3[r1 * MLP_H + c0 + 8]) = af[kt][3]; }
     }
-    // da2 = dz3 W3 (W3^T in the W3 slot), dz2 = da2 * silu'(z2)
+    // da2 = dz3 W3 (W3^T in the W3 slot), dz2 = da2 * act'(z2)
     mlp_layer_mma(M.W3, af, acc);
     for (int nt = 0; nt < 16; ++nt)
       for (int e = 0; e < 2; ++e) {
         const int col = nt * 8 + tig * 2 + e;
-        acc[nt][e] = v0 ? acc[nt][e] * silu_grad(tb.Z2[r0 * MLP_H + col]) : 0.f;
-        acc[nt][2 + e] = v1 ? acc[nt][2 + e] * silu_grad(tb.Z2[r1 * MLP_H + col]) : 0.f;
+        acc[nt][e] = v0 ? acc[nt][e] * mlp_act_grad(tb.Z2[r0 * MLP_H + col]) : 0.f;
+        acc[nt][2 + e] = v1 ? acc[nt][2 + e] * mlp_act_grad(tb.Z2[r1 * MLP_H + col]) : 0.f;
       }
     for (int kt = 0; kt < 8; ++kt) {
       af[kt][0] = pack_bf16(acc[2 * kt][0], acc[2 * kt][1]);
@@ -238,13 +238,13 @@ k_mlp_backward(const float *__restrict__ p, const __nv_bfloat16 *__restrict__ w2
       if (v0) { *reinterpret_cast<uint32_t *>(&tb.dZ2[r0 * MLP_H + c0]) = af[kt][0]; *reinterpret_cast<uint32_t *>(&tb.dZ2[r0 * MLP_H + c0 + 8]) = af[kt][2]; }
       if (v1) { *reinterpret_cast<uint32_t *>(&tb.dZ2[r1 * MLP_H + c0]) = af[kt][1]; *reinterpret_cast<uint32_t *>(&tb.dZ2[r1 * MLP_H + c0 + 8]) = af[kt][3]; }
     }
-    // da1 = dz2 W2, dz1 = da1 * silu'(z1)
+    // da1 = dz2 W2, dz1 = da1 * act'(z1)
     mlp_layer_mma(M.W2, af, acc);
     for (int nt = 0; nt < 16; ++nt)
       for (int e = 0; e < 2; ++e) {
         const int col = nt * 8 + tig * 2 + e;
-        if (v0) tb.dZ1[r0 * MLP_H + col] = acc[nt][e] * silu_grad(tb.Z1[r0 * MLP_H + col]);
-        if (v1) tb.dZ1[r1 * MLP_H + col] = acc[nt][2 + e] * silu_grad(tb.Z1[r1 * MLP_H + col]);
+        if (v0) tb.dZ1[r0 * MLP_H + col] = acc[nt][e] * mlp_act_grad(tb.Z1[r0 * MLP_H + col]);
+        if (v1) tb.dZ1[r1 * MLP_H + col] = acc[nt][2 + e] * mlp_act_grad(tb.Z1[r1 * MLP_H + col]);
       }
   }
 }

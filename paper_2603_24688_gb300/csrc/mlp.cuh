@@ -1,4 +1,5 @@
-// Learned surrogate of the rate integrals: a 4 -> 128 -> 128 -> 128 -> 2 MLP with SiLU.
+// Learned surrogate of the rate integrals: a 4 -> 128 -> 128 -> 128 -> 2 MLP whose activation
+// is the squared ReLU, act(z) = max(z, 0)^2.
 // The two 128 x 128 layers run on the tensor cores (bf16 inputs, float32 accumulation,
 // mma.sync m16n8k16); the first and last layers are float32 on the CUDA cores.  One warp
 // evaluates 16 rows at a time; the accumulator fragment of one layer is, after the
@@ -33,22 +34,13 @@ struct MlpSmem {
   float b4[MLP_OUT];
 };
 
-// SiLU through the hardware tanh: silu(z) = z sigmoid(z) = (z/2)(1 + tanh(z/2)), one MUFU
-// operation per activation; training and inference use the same function.
-__device__ __forceinline__ float tanh_fast(float x) {
-  float y;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
+// Squared ReLU: no special function, so the layer epilogues stay off the MUFU pipe; training
+// and inference use the same function.  Its derivative 2 max(z, 0) is continuous.
+__device__ __forceinline__ float mlp_act(float z) {
+  const float r = fmaxf(z, 0.0f);
+  return r * r;
 }
-__device__ __forceinline__ float silu(float z) {
-  const float h = 0.5f * z;
-  return h + h * tanh_fast(h);
-}
-__device__ __forceinline__ float silu_grad(float z) {
-  const float t = tanh_fast(0.5f * z);                  // sigmoid = (1 + t)/2
-  const float sg = 0.5f + 0.5f * t;
-  return sg * (1.0f + z * (1.0f - sg));
-}
+__device__ __forceinline__ float mlp_act_grad(float z) { return 2.0f * fmaxf(z, 0.0f); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x = lo (low 16 bits)
@@ -83,17 +75,17 @@ __device__ __forceinline__ void mlp_layer_mma(const __nv_bfloat16 *__restrict__ 
   }
 }
 
-// bias + SiLU on an accumulator set, packed into the next layer's A fragments
+// bias + activation on an accumulator set, packed into the next layer's A fragments
 __device__ __forceinline__ void mlp_act_pack(float acc[16][4], const float *__restrict__ bias, uint32_t afrag[8][4]) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned tig = lane & 3u;
 #pragma unroll
   for (int nt = 0; nt < 16; ++nt) {
     const float bb0 = bias[nt * 8 + tig * 2], bb1 = bias[nt * 8 + tig * 2 + 1];
-    acc[nt][0] = silu(acc[nt][0] + bb0);
-    acc[nt][1] = silu(acc[nt][1] + bb1);
-    acc[nt][2] = silu(acc[nt][2] + bb0);
-    acc[nt][3] = silu(acc[nt][3] + bb1);
+    acc[nt][0] = mlp_act(acc[nt][0] + bb0);
+    acc[nt][1] = mlp_act(acc[nt][1] + bb1);
+    acc[nt][2] = mlp_act(acc[nt][2] + bb0);
+    acc[nt][3] = mlp_act(acc[nt][3] + bb1);
   }
 #pragma unroll
   for (int kt = 0; kt < 8; ++kt) {
@@ -139,8 +131,8 @@ __device__ __forceinline__ void mlp_forward16(const MlpSmem &M, const float x_lo
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int col = nt * 8 + tig * 2 + e;
-      const float al = silu(acc[nt][e] + M.b3[col]);
-      const float ah = silu(acc[nt][2 + e] + M.b3[col]);
+      const float al = mlp_act(acc[nt][e] + M.b3[col]);
+      const float ah = mlp_act(acc[nt][2 + e] + M.b3[col]);
 #pragma unroll
       for (int o = 0; o < MLP_OUT; ++o) {
         pl[o] += M.W4[o * MLP_H + col] * al;
@@ -207,7 +199,7 @@ __device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void *p) {
 
 // One 128 -> 128 layer for 32 rows (two m16 tiles) reading A from the warp's activation buffer
 // act (row-major, stride MLP_LDW) and W (row-major [out][in], stride MLP_LDW); writes
-// silu(a W^T + bias) back into act (bf16) when `last` is false; when it is true the float32
+// act(a W^T + bias) back into act (bf16) when `last` is false; when it is true the float32
 // activations go straight into the output layer: yacc[m][h][o] += W4[o][col] a (partial over
 // this lane's columns; rows m*16 + g + 8h).
 __device__ __forceinline__ void mlp_layer32(const __nv_bfloat16 *__restrict__ W, const float *__restrict__ bias,
@@ -249,8 +241,8 @@ __device__ __forceinline__ void mlp_layer32(const __nv_bfloat16 *__restrict__ W,
     const float bb0 = bias[col], bb1 = bias[col + 1];
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
-      const float v0 = silu(c[m][0] + bb0), v1 = silu(c[m][1] + bb1);
-      const float v2 = silu(c[m][2] + bb0), v3 = silu(c[m][3] + bb1);
+      const float v0 = mlp_act(c[m][0] + bb0), v1 = mlp_act(c[m][1] + bb1);
+      const float v2 = mlp_act(c[m][2] + bb0), v3 = mlp_act(c[m][3] + bb1);
       if (last) {
 #pragma unroll
         for (int o = 0; o < MLP_OUT; ++o) {

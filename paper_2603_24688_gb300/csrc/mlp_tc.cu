@@ -1,11 +1,11 @@
 // Surrogate inference on the 5th-generation tensor cores (tcgen05): tiles of 128 rows, the
 // three hidden layers as 128 x 128 x K MMAs with bf16 operands in shared memory and the float32
-// accumulator in tensor memory; bias, SiLU and the bf16 repacking of the activations run on the
-// CUDA cores between the layers, the output layer in float32.
+// accumulator in tensor memory; the activation and the bf16 repacking run on the CUDA cores
+// between the layers, the output layer in float32.
 //
 // One CTA per SM holds the bf16 weights once and runs NWG independent warpgroups of 128
 // threads; warpgroup g owns TMEM columns [128 g, 128 g + 128) and its own activation buffers,
-// so while one warpgroup evaluates SiLU (the MUFU-bound part) another one's MMAs run.
+// so while one warpgroup runs its epilogue another one's MMAs run.
 // Thread t of a warpgroup owns row t of its tile: it forms the row's inputs, reads the row's
 // accumulator (TMEM lane t) and writes the row's activations.
 //
@@ -13,10 +13,11 @@
 // x = x_hi + x_lo and W1 = W_hi + W_lo (bf16 parts), K = 16 holds the four products
 // [x_hi, x_hi, x_lo, x_lo] . [W_hi, W_lo, W_hi, W_lo], leaving an error of about 2^-16 of x.W.
 //
-// The epilogue does one tanh and one FMA per activation: SiLU(z) = h + h tanh(h) with h = z/2,
-// and the MMAs produce h directly, bias included.  The weights are stored halved (exact in
-// bf16) and one more K = 16 slice per layer multiplies a constant operand row [1, 1, 0, ...]
-// with [b_hi/2, b_lo/2, 0, ...] (bias split into bf16 parts, exact to about 2^-17).
+// The activation is the squared ReLU, so the epilogue of a hidden layer is one multiply and
+// half a conversion per activation: t = z |z|, then cvt.rn.relu.bf16x2 packs max(t, 0) =
+// max(z, 0)^2 of two columns.  The MMAs produce z with the bias included: one more K = 16
+// slice per layer multiplies a constant operand row [1, 1, 0, ...] with [b_hi, b_lo, 0, ...]
+// (bias split into bf16 parts, exact to about 2^-17).
 //
 // Operand layout (no swizzle, K-major): 8 x 16-byte core matrices; element (row, k) of a
 // 128-row operand sits at (k / 8) * 2048 + row * 16 + (k % 8) * 2 bytes, so the descriptor of
@@ -43,9 +44,9 @@ struct TcLayout {
   static constexpr int W3 = W2 + TC_OPER;
   static constexpr int A = W3 + TC_OPER;                 // NWG activation operands (slice 0 of each also
                                                          // holds the layer-1 operand of a new tile)
-  static constexpr int W1 = A + NWG * TC_OPER;           // split W1 / 2 (128 x 16)
+  static constexpr int W1 = A + NWG * TC_OPER;           // split W1 (128 x 16)
   static constexpr int ONE = W1 + TC_OPER1;              // constant operand rows [1, 1, 0, ...] (128 x 16)
-  static constexpr int BB = ONE + TC_OPER1;              // 3 bias operands [b_hi/2, b_lo/2, 0, ...] (128 x 16)
+  static constexpr int BB = ONE + TC_OPER1;              // 3 bias operands [b_hi, b_lo, 0, ...] (128 x 16)
   static constexpr int W4 = BB + 3 * TC_OPER1;           // [2][128] float
   static constexpr int B4 = W4 + 1024;                   // 2 floats (16 bytes)
   static constexpr int BAR = B4 + 16;                    // NWG mbarriers (8-byte aligned)
@@ -138,8 +139,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
   for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
-// SiLU from h = z / 2: z sigmoid(z) = h + h tanh(h), one MUFU and one FMA
-__device__ __forceinline__ float silu_h(float h) { return fmaf(h, tanh_fast(h), h); }
+// bf16x2 of (max(lo, 0), max(hi, 0)), lo in the low half, each rounded to nearest even
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
 
 __device__ __forceinline__ uint32_t bf16_bits(float x) {
   const __nv_bfloat16 b = __float2bfloat16_rn(x);
@@ -216,18 +221,14 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     const int r = q % (MLP_H * (MLP_H / 8));
     const int n = r % MLP_H, c = r / MLP_H;           // output row n, 8-column chunk c
     const __nv_bfloat16 *src = (which == 0 ? a.w2 : a.w3) + n * MLP_H + c * 8;
-    uint4 v = *reinterpret_cast<const uint4 *>(src);
-    const __nv_bfloat162 half2 = __floats2bfloat162_rn(0.5f, 0.5f);
-    __nv_bfloat162 *hv = reinterpret_cast<__nv_bfloat162 *>(&v);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) hv[e] = __hmul2(hv[e], half2);   // W / 2, exact
+    const uint4 v = *reinterpret_cast<const uint4 *>(src);
     *reinterpret_cast<uint4 *>(sm + (which == 0 ? Ly::W2 : Ly::W3) + c * TC_SLICE + n * 16) = v;
   }
   for (int n = tid; n < MLP_H; n += blockDim.x) {
     uint32_t hl[4];
 #pragma unroll
     for (int m = 0; m < MLP_IN; m += 2) {
-      const float w0 = 0.5f * a.p[MLP_OFF_W1 + n * MLP_IN + m], w1 = 0.5f * a.p[MLP_OFF_W1 + n * MLP_IN + m + 1];
+      const float w0 = a.p[MLP_OFF_W1 + n * MLP_IN + m], w1 = a.p[MLP_OFF_W1 + n * MLP_IN + m + 1];
       const float h0 = __bfloat162float(__float2bfloat16_rn(w0)), h1 = __bfloat162float(__float2bfloat16_rn(w1));
       hl[m / 2] = bf16_bits(w0) | (bf16_bits(w1) << 16);
       hl[2 + m / 2] = bf16_bits(w0 - h0) | (bf16_bits(w1 - h1) << 16);
@@ -235,13 +236,13 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     const uint4 chunk = make_uint4(hl[0], hl[1], hl[2], hl[3]);   // [W_hi(4), W_lo(4)] in both chunks
     *reinterpret_cast<uint4 *>(sm + Ly::W1 + 0 * TC_SLICE + n * 16) = chunk;
     *reinterpret_cast<uint4 *>(sm + Ly::W1 + 1 * TC_SLICE + n * 16) = chunk;
-    // constant rows [1, 1, 0, ...] and the bias rows [b_hi/2, b_lo/2, 0, ...] of the three layers
+    // constant rows [1, 1, 0, ...] and the bias rows [b_hi, b_lo, 0, ...] of the three layers
     const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
     *reinterpret_cast<uint4 *>(sm + Ly::ONE + 0 * TC_SLICE + n * 16) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
     *reinterpret_cast<uint4 *>(sm + Ly::ONE + 1 * TC_SLICE + n * 16) = zero;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-      const float b = 0.5f * a.p[(l == 0 ? MLP_OFF_B1 : l == 1 ? MLP_OFF_B2 : MLP_OFF_B3) + n];
+      const float b = a.p[(l == 0 ? MLP_OFF_B1 : l == 1 ? MLP_OFF_B2 : MLP_OFF_B3) + n];
       const float bh = __bfloat162float(__float2bfloat16_rn(b));
       *reinterpret_cast<uint4 *>(sm + Ly::BB + l * TC_OPER1 + 0 * TC_SLICE + n * 16) =
           make_uint4(bf16_bits(b) | (bf16_bits(b - bh) << 16), 0u, 0u, 0u);
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
             tc_mma(d_tmem, smem_desc(sA + ks * 2 * TC_SLICE, TC_SLICE, 128),
                    smem_desc(sW + ks * 2 * TC_SLICE, TC_SLICE, 128), ks > 0 ? 1u : 0u);
         }
-        // + b / 2 through the constant slice
+        // + b through the constant slice
         tc_mma(d_tmem, smem_desc(sbase + Ly::ONE, TC_SLICE, 128),
                smem_desc(sbase + Ly::BB + layer * TC_OPER1, TC_SLICE, 128), 1u);
         tc_commit(bar);
@@ -374,12 +375,12 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
 #pragma unroll 1
       for (int cc = 0; cc < MLP_H / 32; ++cc) {
         float v[32];
-        tmem_ld32(my_lanes + 32u * cc, v);   // h = z / 2 with the bias
+        tmem_ld32(my_lanes + 32u * cc, v);   // z with the bias
         if (layer < 2) {
           uint32_t pk[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k)
-            pk[k] = pack_bf16(silu_h(v[2 * k]), silu_h(v[2 * k + 1]));
+            pk[k] = pack_relu_bf16(v[2 * k] * fabsf(v[2 * k]), v[2 * k + 1] * fabsf(v[2 * k + 1]));
 #pragma unroll
           for (int c4 = 0; c4 < 4; ++c4)
             *reinterpret_cast<uint4 *>(pA + (4 * cc + c4) * TC_SLICE + t * 16) =
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
 #pragma unroll
           for (int k = 0; k < 32; ++k) {
             const int c = 32 * cc + k;
-            const float act = silu_h(v[k]);
+            const float r = fmaxf(v[k], 0.0f), act = r * r;
             y0 += W4[c] * act;
             y1 += W4[MLP_H + c] * act;
           }
