@@ -41,10 +41,10 @@ OPS_PER_PAIR = {"meanfield": 150.0, "mc": 256.0}
 QUAD_OPS_PER_PAIR = 64 * 16 + 120.0
 # learned surrogate per pair: the network's dense contraction, 2 x (4 x 128 + 2 x 128 x 128 +
 # 128 x 2) flop (bf16 tensor cores for the 128-wide layers), and the flop the tensor cores issue
-# for it: 2 x 128 x (16 + 16 + 128 + 16 + 128 + 16) (layer 1 as a K = 16 hi/lo product, one K = 16
-# bias slice per layer).  The squared-ReLU epilogue needs no special function.
+# for it: 2 x 128 x (16 + 128 + 16 + 128 + 16) (layer 1 and its bias as one K = 16 hi/lo product,
+# one K = 16 bias slice for each of layers 2 and 3).  The squared-ReLU epilogue needs no special function.
 MLP_FLOP_PER_PAIR = 2.0 * (4 * 128 + 2 * 128 * 128 + 128 * 2)
-MLP_TENSOR_FLOP_PER_PAIR = 2.0 * 128 * (16 + 16 + 128 + 16 + 128 + 16)
+MLP_TENSOR_FLOP_PER_PAIR = 2.0 * 128 * (16 + 128 + 16 + 128 + 16)
 # DRAM bytes per pair of the surrogate pass from one ncu capture of the current kernel on galaxy1M
 # (dram__bytes_read.sum + dram__bytes_write.sum for the pairs of that launch), scaled to a launch
 # by its pair count; None while the kernel has changed since the capture.  Algorithmic bytes: row

@@ -10,14 +10,16 @@
 // accumulator (TMEM lane t) and writes the row's activations.
 //
 // Layer 1 (4 -> 128) runs on the tensor cores too, exactly enough for float32 inputs: with
-// x = x_hi + x_lo and W1 = W_hi + W_lo (bf16 parts), K = 16 holds the four products
-// [x_hi, x_hi, x_lo, x_lo] . [W_hi, W_lo, W_hi, W_lo], leaving an error of about 2^-16 of x.W.
+// x = x_hi + x_lo and W1 = W_hi + W_lo (bf16 parts) and the bias b1 = b_hi + b_lo, one K = 16
+// MMA forms [x_hi, x_hi, x_lo, 1, 1, 0, 0] . [W_hi, W_lo, W_hi, b_hi, b_lo, 0, 0] (groups of 4
+// columns, then single ones); the dropped x_lo . W_lo leaves an error of about 2^-17 of |x| |W|.
 //
 // The activation is the squared ReLU, so the epilogue of a hidden layer is one multiply and
 // half a conversion per activation: t = z |z|, then cvt.rn.relu.bf16x2 packs max(t, 0) =
-// max(z, 0)^2 of two columns.  The MMAs produce z with the bias included: one more K = 16
-// slice per layer multiplies a constant operand row [1, 1, 0, ...] with [b_hi, b_lo, 0, ...]
-// (bias split into bf16 parts, exact to about 2^-17).
+// max(z, 0)^2 of two columns.  The MMAs of layers 2 and 3 produce z with the bias included:
+// one more K = 16 slice multiplies a constant operand row [1, 1, 0, ...] with
+// [b_hi, b_lo, 0, ...] (bias split into bf16 parts, exact to about 2^-17).  The output layer
+// runs in float32 on packed two-wide FMAs.
 //
 // Operand layout (no swizzle, K-major): 8 x 16-byte core matrices; element (row, k) of a
 // 128-row operand sits at (k / 8) * 2048 + row * 16 + (k % 8) * 2 bytes, so the descriptor of
@@ -44,15 +46,14 @@ struct TcLayout {
   static constexpr int W3 = W2 + TC_OPER;
   static constexpr int A = W3 + TC_OPER;                 // NWG activation operands (slice 0 of each also
                                                          // holds the layer-1 operand of a new tile)
-  static constexpr int W1 = A + NWG * TC_OPER;           // split W1 (128 x 16)
+  static constexpr int W1 = A + NWG * TC_OPER;           // split W1 and b1 (128 x 16)
   static constexpr int ONE = W1 + TC_OPER1;              // constant operand rows [1, 1, 0, ...] (128 x 16)
-  static constexpr int BB = ONE + TC_OPER1;              // 3 bias operands [b_hi, b_lo, 0, ...] (128 x 16)
-  static constexpr int W4 = BB + 3 * TC_OPER1;           // [2][128] float
+  static constexpr int BB = ONE + TC_OPER1;              // bias operands [b_hi, b_lo, 0, ...] of layers 2, 3
+  static constexpr int W4 = BB + 2 * TC_OPER1;           // [2][128] float
   static constexpr int B4 = W4 + 1024;                   // 2 floats (16 bytes)
   static constexpr int BAR = B4 + 16;                    // NWG mbarriers (8-byte aligned)
   static constexpr int TSLOT = BAR + NWG * 8;            // TMEM base address
-  static constexpr int FLAG = TSLOT + 16;                // NWG completion flags
-  static constexpr int TOTAL = (FLAG + 16 + 1023) / 1024 * 1024;
+  static constexpr int TOTAL = (TSLOT + 16 + 1023) / 1024 * 1024;
 };
 static_assert(TcLayout<4>::TOTAL <= 232448, "shared memory of the tensor-core surrogate");
 static_assert(TcLayout<3>::BAR % 8 == 0, "mbarrier alignment");
@@ -93,6 +94,16 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void wg_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+// barrier of the warpgroup that also returns whether v holds in all 128 threads
+__device__ __forceinline__ bool wg_sync_and(int id, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, %2, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id)
+      : "memory");
+  return r != 0u;
+}
 
 // Shared-memory matrix descriptor: start address, leading- and stride-dimension byte offsets
 // (all >> 4), descriptor version 1 at bit 46, base offset 0, no swizzle.
@@ -233,19 +244,23 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
       hl[m / 2] = bf16_bits(w0) | (bf16_bits(w1) << 16);
       hl[2 + m / 2] = bf16_bits(w0 - h0) | (bf16_bits(w1 - h1) << 16);
     }
-    const uint4 chunk = make_uint4(hl[0], hl[1], hl[2], hl[3]);   // [W_hi(4), W_lo(4)] in both chunks
-    *reinterpret_cast<uint4 *>(sm + Ly::W1 + 0 * TC_SLICE + n * 16) = chunk;
-    *reinterpret_cast<uint4 *>(sm + Ly::W1 + 1 * TC_SLICE + n * 16) = chunk;
-    // constant rows [1, 1, 0, ...] and the bias rows [b_hi, b_lo, 0, ...] of the three layers
+    // bias as [b_hi, b_lo, 0, 0, 0, 0, 0, 0] (bf16 parts)
+    auto bias_chunk = [](float b) {
+      const float bh = __bfloat162float(__float2bfloat16_rn(b));
+      return make_uint4(bf16_bits(b) | (bf16_bits(b - bh) << 16), 0u, 0u, 0u);
+    };
+    const uint4 b1c = bias_chunk(a.p[MLP_OFF_B1 + n]);
+    // chunk 0 = [W_hi(4), W_lo(4)], chunk 1 = [W_hi(4), b_hi, b_lo, 0, 0]
+    *reinterpret_cast<uint4 *>(sm + Ly::W1 + 0 * TC_SLICE + n * 16) = make_uint4(hl[0], hl[1], hl[2], hl[3]);
+    *reinterpret_cast<uint4 *>(sm + Ly::W1 + 1 * TC_SLICE + n * 16) = make_uint4(hl[0], hl[1], b1c.x, 0u);
+    // constant rows [1, 1, 0, ...] and the bias rows of layers 2 and 3
     const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
     *reinterpret_cast<uint4 *>(sm + Ly::ONE + 0 * TC_SLICE + n * 16) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
     *reinterpret_cast<uint4 *>(sm + Ly::ONE + 1 * TC_SLICE + n * 16) = zero;
 #pragma unroll
-    for (int l = 0; l < 3; ++l) {
-      const float b = a.p[(l == 0 ? MLP_OFF_B1 : l == 1 ? MLP_OFF_B2 : MLP_OFF_B3) + n];
-      const float bh = __bfloat162float(__float2bfloat16_rn(b));
+    for (int l = 0; l < 2; ++l) {
       *reinterpret_cast<uint4 *>(sm + Ly::BB + l * TC_OPER1 + 0 * TC_SLICE + n * 16) =
-          make_uint4(bf16_bits(b) | (bf16_bits(b - bh) << 16), 0u, 0u, 0u);
+          bias_chunk(a.p[(l == 0 ? MLP_OFF_B2 : MLP_OFF_B3) + n]);
       *reinterpret_cast<uint4 *>(sm + Ly::BB + l * TC_OPER1 + 1 * TC_SLICE + n * 16) = zero;
     }
   }
@@ -280,7 +295,6 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
   const uint32_t sA = sbase + Ly::A + g * TC_OPER, sA1 = sA;   // the layer-1 operand is slice 0 of A
   unsigned char *pA = sm + Ly::A + g * TC_OPER;
   unsigned char *pA1 = pA;
-  volatile uint32_t *flag = reinterpret_cast<volatile uint32_t *>(sm + Ly::FLAG) + g;
   const int bar_id = 1 + g;
   uint32_t phase = 0;
   unsigned fallback = 0;
@@ -318,7 +332,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
       }
     }
     const int64_t qn = (T + stride) * TC_ROWS + t;    // the next tile's row
-    // layer-1 operand row: chunk 0 = [x_hi, x_hi], chunk 1 = [x_lo, x_lo]
+    // layer-1 operand row: chunk 0 = [x_hi, x_hi], chunk 1 = [x_lo, 1, 1, 0, 0]
     {
       uint32_t hi2[2], lo2[2];
 #pragma unroll
@@ -329,10 +343,10 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
         lo2[m / 2] = bf16_bits(x[m] - h0) | (bf16_bits(x[m + 1] - h1) << 16);
       }
       *reinterpret_cast<uint4 *>(pA1 + 0 * TC_SLICE + t * 16) = make_uint4(hi2[0], hi2[1], hi2[0], hi2[1]);
-      *reinterpret_cast<uint4 *>(pA1 + 1 * TC_SLICE + t * 16) = make_uint4(lo2[0], lo2[1], lo2[0], lo2[1]);
+      *reinterpret_cast<uint4 *>(pA1 + 1 * TC_SLICE + t * 16) = make_uint4(lo2[0], lo2[1], 0x3F803F80u, 0u);
     }
     // ---- three layers ------------------------------------------------------------------------
-    float y0 = 0.f, y1 = 0.f;
+    float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);   // even / odd columns
 #pragma unroll 1
     for (int layer = 0; layer < 3; ++layer) {
       fence_async_smem();
@@ -348,10 +362,10 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
           for (int ks = 0; ks < MLP_H / 16; ++ks)
             tc_mma(d_tmem, smem_desc(sA + ks * 2 * TC_SLICE, TC_SLICE, 128),
                    smem_desc(sW + ks * 2 * TC_SLICE, TC_SLICE, 128), ks > 0 ? 1u : 0u);
+          // + b through the constant slice
+          tc_mma(d_tmem, smem_desc(sbase + Ly::ONE, TC_SLICE, 128),
+                 smem_desc(sbase + Ly::BB + (layer - 1) * TC_OPER1, TC_SLICE, 128), 1u);
         }
-        // + b through the constant slice
-        tc_mma(d_tmem, smem_desc(sbase + Ly::ONE, TC_SLICE, 128),
-               smem_desc(sbase + Ly::BB + layer * TC_OPER1, TC_SLICE, 128), 1u);
         tc_commit(bar);
       }
       // the next tile's gather behind this MMA
@@ -363,11 +377,11 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
         fetch_stage<MODE>(a, 0, 2, nxt);
         fetch_stage<MODE>(a, 0, 3, nxt);
       }
-      // one thread waits (bounded) and tells the group, so that a timeout is seen by all 128
-      if (t == 0) *flag = mbar_wait_bounded(bar, phase) ? 1u : 0u;
-      wg_sync(bar_id);
+      // every thread waits (bounded) for the MMA and the group agrees on the outcome, so that a
+      // timeout is seen by all 128
+      const bool done = wg_sync_and(bar_id, mbar_wait_bounded(bar, phase));
       phase ^= 1u;
-      if (*flag == 0u) {
+      if (!done) {
         ok = false;
         break;
       }
@@ -387,11 +401,12 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
                 make_uint4(pk[4 * c4], pk[4 * c4 + 1], pk[4 * c4 + 2], pk[4 * c4 + 3]);
         } else {
 #pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            const int c = 32 * cc + k;
-            const float r = fmaxf(v[k], 0.0f), act = r * r;
-            y0 += W4[c] * act;
-            y1 += W4[MLP_H + c] * act;
+          for (int k = 0; k < 16; ++k) {
+            const int c = 32 * cc + 2 * k;
+            const float2 r = make_float2(fmaxf(v[2 * k], 0.0f), fmaxf(v[2 * k + 1], 0.0f));
+            const float2 act = __fmul2_rn(r, r);
+            y0 = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + c), act, y0);
+            y1 = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + MLP_H + c), act, y1);
           }
         }
       }
@@ -399,7 +414,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     if (!ok) break;
     tc_fence_before();   // this tile's TMEM reads are done before the next tile's MMA
     // ---- outputs -----------------------------------------------------------------------------
-    const float y[MLP_OUT] = {y0 + b4[0], y1 + b4[1]};
+    const float y[MLP_OUT] = {(y0.x + y0.y) + b4[0], (y1.x + y1.y) + b4[1]};
     if (MODE == MODE_X) {
       if (use) {
         a.Y[2 * p] = y[0];
