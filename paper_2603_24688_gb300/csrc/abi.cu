@@ -484,8 +484,8 @@ MlpRun mlp_run(dmb_ctx *ctx) {
   r.w3 = ptr<__nv_bfloat16>(ctx->mlp_w3);
   r.fallback_count = ptr<unsigned long long>(ctx->mlp_fallback);
   MlpDomain &d = r.dom;
-  d.s_lo = (float)pow(10.0, ctx->mlp_box[0]);
-  d.s_hi = (float)pow(10.0, ctx->mlp_box[1]);
+  d.s2_lo = (float)pow(10.0, 2.0 * ctx->mlp_box[0]);
+  d.s2_hi = (float)pow(10.0, 2.0 * ctx->mlp_box[1]);
   d.tau_lo = (float)pow(10.0, ctx->mlp_box[2]);
   d.tau_hi = (float)pow(10.0, ctx->mlp_box[3]);
   d.m_lo = (float)pow(10.0, ctx->mlp_box[4]);

@@ -136,9 +136,9 @@ k_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *__re
       const float4 Vi = D.V[rows[valid ? p : rs]];
       const float wx = Vi.x - Vj.x, wy = Vi.y - Vj.y, wz = Vi.z - Vj.z;
       const float w2 = wx * wx + wy * wy + wz * wz;
-      const float sv_ = sqrtf(w2) / sig;
+      const float sig2 = sig * sig, s2 = __fdividef(w2, sig2);
       float xin[MLP_IN];
-      const bool in_dom = mlp_inputs(mr.dom, fmaxf(sv_, 1e-30f), sig, xin);
+      const bool in_dom = mlp_inputs(mr.dom, s2, sig2, xin);
       // layer 1 for this lane's row
       __nv_bfloat16 *arow = act + lane * MLP_LDW;
 #pragma unroll 4
@@ -176,9 +176,9 @@ k_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *__re
       if (valid) {
         float FA, FB;
         if (in_dom) {
-          mlp_outputs(mr.dom, sv_, yr, FA, FB);
+          mlp_outputs(mr.dom, s2, yr, FA, FB);
         } else {
-          rates_quad<float>(0.5f * sv_ * sv_, rc.n, alpha, FA, FB);
+          rates_quad<float>(0.5f * s2, rc.n, alpha, FA, FB);
           ++fallback;
         }
         rates[p] = make_float2(FA, FB);

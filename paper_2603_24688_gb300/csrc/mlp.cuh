@@ -156,25 +156,30 @@ __device__ __forceinline__ void mlp_forward16(const MlpSmem &M, const float x_lo
 // log FA - log EA and log FB - log EB against the envelopes EA = (1 + cA x)^((n+1)/2),
 // EB = (1 + cB x)^((n+3)/2) (x = s^2/2) that carry the exact small- and large-x behaviour.
 struct MlpDomain {
-  float s_lo, s_hi, tau_lo, tau_hi, m_lo, m_hi;
+  float s2_lo, s2_hi, tau_lo, tau_hi, m_lo, m_hi;   // training box (s^2 = w^2 / varsigma^2)
   float cA, cB;      // envelope constants for the run's n
   float eA, eB;      // envelope exponents (n+1)/2, (n+3)/2
   float inv_v0sq, log_m, n4;
 };
 
-__device__ __forceinline__ bool mlp_inputs(const MlpDomain &d, float s, float sig, float x[MLP_IN]) {
-  const float tau = sig * sig * d.inv_v0sq;
-  x[0] = 0.5f * log10f(s);
-  x[1] = 0.5f * log10f(tau);
+// Inputs of a pair from s^2 = w^2 / varsigma^2 and varsigma^2, logarithms by the hardware log2
+// (relative error about 2^-22, far below the bf16 parts the network sees); returns whether the
+// pair lies in the training box.  Both inference engines use this, so their fallbacks agree.
+__device__ __forceinline__ bool mlp_inputs(const MlpDomain &d, float s2, float sig2, float x[MLP_IN]) {
+  const float log10_2 = 0.30102999566398120f;
+  const float tau = sig2 * d.inv_v0sq;
+  x[0] = (0.25f * log10_2) * __log2f(fmaxf(s2, 1e-30f));   // log10(s) / 2
+  x[1] = (0.5f * log10_2) * __log2f(fmaxf(tau, 1e-30f));   // log10(tau) / 2
   x[2] = d.log_m;
   x[3] = d.n4;
-  return s >= d.s_lo && s <= d.s_hi && tau >= d.tau_lo && tau <= d.tau_hi;
+  return s2 >= d.s2_lo && s2 <= d.s2_hi && tau >= d.tau_lo && tau <= d.tau_hi;
 }
 
-__device__ __forceinline__ void mlp_outputs(const MlpDomain &d, float s, const float y[MLP_OUT], float &FA, float &FB) {
-  const float x = 0.5f * s * s;
-  FA = __expf(y[0]) * __powf(1.0f + d.cA * x, d.eA);
-  FB = __expf(y[1]) * __powf(1.0f + d.cB * x, d.eB);
+// FA = e^{y0} (1 + cA x)^eA, FB likewise, x = s^2 / 2: one hardware exp and log per output
+__device__ __forceinline__ void mlp_outputs(const MlpDomain &d, float s2, const float y[MLP_OUT], float &FA, float &FB) {
+  const float x = 0.5f * s2;
+  FA = __expf(fmaf(d.eA, __logf(fmaf(d.cA, x, 1.0f)), y[0]));
+  FB = __expf(fmaf(d.eB, __logf(fmaf(d.cB, x, 1.0f)), y[1]));
 }
 
 // ---- batched inference on pairs: 32 rows per warp ---------------------------------------------
