@@ -71,12 +71,15 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
+// Tests the phase; while it is incomplete the thread may sleep up to about 0.1 ms (the
+// suspend-time hint, in ns) and wakes when the phase completes, so waiting threads take few
+// issue slots.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(100000u)
       : "memory");
   return ok != 0u;
 }
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     // ---- this tile's row inputs (gathered one tile ahead) --------------------------------
     float x[MLP_IN] = {0.f, 0.f, 0.f, 0.f};
     const int64_t p = nxt.p;
-    float s_ratio = 0.f;
+    float s2 = 0.f;                                   // (w / varsigma)^2
     bool use = false, in_dom = false;
     if (nxt.q >= 0) {
       if (MODE == MODE_X) {
@@ -325,8 +328,9 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
         const float sig = nxt.Vj.w;
         if (sig > 0.0f) {
           const float wx = nxt.Vi.x - nxt.Vj.x, wy = nxt.Vi.y - nxt.Vj.y, wz = nxt.Vi.z - nxt.Vj.z;
-          s_ratio = sqrtf(wx * wx + wy * wy + wz * wz) / sig;
-          in_dom = mlp_inputs(a.dom, fmaxf(s_ratio, 1e-30f), sig, x);
+          const float sig2 = sig * sig;
+          s2 = __fdividef(wx * wx + wy * wy + wz * wz, sig2);
+          in_dom = mlp_inputs(a.dom, s2, sig2, x);
           use = true;
         }
       }
@@ -346,7 +350,10 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
       *reinterpret_cast<uint4 *>(pA1 + 1 * TC_SLICE + t * 16) = make_uint4(lo2[0], lo2[1], 0x3F803F80u, 0u);
     }
     // ---- three layers ------------------------------------------------------------------------
-    float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);   // even / odd columns
+    // output-layer partial sums: four independent two-wide accumulators per output
+    float2 y0[4], y1[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) y0[u] = y1[u] = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int layer = 0; layer < 3; ++layer) {
       fence_async_smem();
@@ -405,8 +412,8 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
             const int c = 32 * cc + 2 * k;
             const float2 r = make_float2(fmaxf(v[2 * k], 0.0f), fmaxf(v[2 * k + 1], 0.0f));
             const float2 act = __fmul2_rn(r, r);
-            y0 = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + c), act, y0);
-            y1 = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + MLP_H + c), act, y1);
+            y0[k & 3] = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + c), act, y0[k & 3]);
+            y1[k & 3] = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + MLP_H + c), act, y1[k & 3]);
           }
         }
       }
@@ -414,7 +421,9 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     if (!ok) break;
     tc_fence_before();   // this tile's TMEM reads are done before the next tile's MMA
     // ---- outputs -----------------------------------------------------------------------------
-    const float y[MLP_OUT] = {(y0.x + y0.y) + b4[0], (y1.x + y1.y) + b4[1]};
+    const float2 s0 = __fadd2_rn(__fadd2_rn(y0[0], y0[1]), __fadd2_rn(y0[2], y0[3]));
+    const float2 s1 = __fadd2_rn(__fadd2_rn(y1[0], y1[1]), __fadd2_rn(y1[2], y1[3]));
+    const float y[MLP_OUT] = {(s0.x + s0.y) + b4[0], (s1.x + s1.y) + b4[1]};
     if (MODE == MODE_X) {
       if (use) {
         a.Y[2 * p] = y[0];
@@ -423,9 +432,9 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     } else if (use) {
       float FA, FB;
       if (in_dom) {
-        mlp_outputs(a.dom, s_ratio, y, FA, FB);
+        mlp_outputs(a.dom, s2, y, FA, FB);
       } else {
-        rates_quad<float>(0.5f * s_ratio * s_ratio, a.rc.n, alpha, FA, FB);
+        rates_quad<float>(0.5f * s2, a.rc.n, alpha, FA, FB);
         ++fallback;
       }
       a.rates[p] = make_float2(FA, FB);
