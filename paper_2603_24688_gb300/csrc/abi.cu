@@ -260,6 +260,7 @@ dmb_status build_grid_impl(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
     int e;
     frexp(f.span, &e);
     f.delta = ldexp(1.0, e - 23);
+    f.inv_delta = ldexp(1.0, 23 - e);
     f.bits = bits;
     f.key_scale = ldexp(1.0, bits) / (Lq * (1.0 + 1e-12));
     f.pad = (float)(4.0 * ldexp(1.0, e) * 1.1920928955078125e-07);

@@ -94,6 +94,7 @@ k_frame_final(const double *__restrict__ part, int nb, int periodic, double L0, 
   int e;
   frexp(span, &e);                 // span < 2^e
   f.delta = ldexp(1.0, e - 23);
+  f.inv_delta = ldexp(1.0, 23 - e);
   f.bits = bits;
   f.key_scale = ldexp(1.0, bits) / span;
   f.pad = (float)(4.0 * ldexp(1.0, e) * 1.1920928955078125e-07);   // a few float ulps of the span
@@ -184,7 +185,7 @@ __global__ void k_gather(const double *__restrict__ pos, const double *__restric
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const uint32_t i = perm[s];
-  const double delta = frame->delta;
+  const double delta = frame->delta, inv_delta = frame->inv_delta;
   double Ls[3] = {L0, L1, L2};
   double xoff = 0.0;
   bool bad = false;
@@ -207,7 +208,7 @@ __global__ void k_gather(const double *__restrict__ pos, const double *__restric
     if (periodic) x = wrap_coord(x, Ls[c]);
     if (c == 0) x += xoff;
     const double rel = x - frame->origin[c];
-    const double hq = floor(rel / delta) * delta;     // k * delta, |k| < 2^24
+    const double hq = floor(rel * inv_delta) * delta;   // k * delta, |k| < 2^24
     hi[c] = (R)hq;
     lo[c] = (R)(rel - hq);
   }

@@ -6,6 +6,7 @@ struct Frame {
   double origin[3];
   double span;       // side of the cube holding all particles (periodic: max box side)
   double delta;      // power of two with span <= 2^23 delta: quantum of the hi parts
+  double inv_delta;  // 1 / delta (exact)
   double key_scale;  // 2^bits / span
   float pad;         // padding of tree boxes (covers float rounding of the coordinates)
   int bits;          // Morton bits per axis
@@ -29,15 +30,24 @@ struct RunConst {
 // closed forms), kP0 = (M_j / mu_j) sigma0 of Eq. dm-update-prob and e = mu_j / (m_chi + mu_j).
 __host__ __device__ inline void gas_coeffs(const RunConst &rc, double sig, double M, double mu, double &cA,
                                            double &cB, double &kP0, double &e) {
-  const double mpm = rc.m_chi + mu;
-  e = mu / mpm;
+  // float64 division and pow are slow on this GPU (its float64 pipe runs at about 1/70 of
+  // float32): one reciprocal per particle and an integer power by squaring
+  const double inv_mpm = 1.0 / (rc.m_chi + mu);
+  e = mu * inv_mpm;
   if (sig > 0.0) {
-    const double sn = pow(sig / rc.v0, (double)rc.n);          // (varsigma / v0)^n
-    cA = rc.S * rc.alpha / 3.0 * sn * sig / mpm;
-    cB = rc.S * rc.alpha * sn * sig * sig * sig / mpm * e;
+    const double r = sig / rc.v0;
+    double sn = 1.0, b = r;                                    // (varsigma / v0)^|n|
+    for (int k = rc.n < 0 ? -rc.n : rc.n; k > 0; k >>= 1) {
+      if (k & 1) sn *= b;
+      b *= b;
+    }
+    if (rc.n < 0) sn = 1.0 / sn;
+    const double t = rc.S * rc.alpha * sn * sig * inv_mpm;
+    cA = t / 3.0;
+    cB = t * sig * sig * e;
   } else {  // cold gas: A = sigma(w) w, B = sigma(w) w^3
-    cA = rc.S / mpm;
-    cB = rc.S / mpm * e;
+    cA = rc.S * inv_mpm;
+    cB = cA * e;
   }
   kP0 = M / mu * rc.S;                                         // (M_j / mu_j) sigma0 Msun/m_p
 }
