@@ -341,16 +341,43 @@ def run_boxes(a, peaks, peak_kind):
     return 0
 
 
+def run_boxtest(a, peaks, peak_kind):
+    """The App. F periodic-box test (fiducial row of Table test_params, 32^3 + 32^3 particles):
+    `steps` steps of the interaction step plus the drift, after `warmup` steps; the run's own
+    snapshots are not taken inside the timed steps."""
+    import torch
+    from paper_2603_24688_gb300 import boxtest as BT
+    BT.run("fiducial", t_end=a.warmup * 1e-3, dt=1e-3, snap=10 ** 9)
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    r = BT.run("fiducial", t_end=a.steps * 1e-3, dt=1e-3, snap=10 ** 9)
+    clk = clocks.stop()
+    ms = r["ms_per_step"]
+    row = r["row"]
+    n_part = row["N_chi"] + row["N_B"]
+    line = {"metric": "pair_interactions_per_s", "value": r["n_pairs"] / (ms * 1e-3), "unit": "pairs/s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 sums", "data": "synthetic",
+            "config": {"workload": "boxtest: App. F fiducial periodic box, 32^3 DM + 32^3 gas, m_chi = 2 m_p, "
+                                   "sigma = 1e-26 cm^2, V_chi = 200 km/s, T_chi = 1e6 K, T_B = 1e4 K, dt = 1e-3, "
+                                   "dmb_step + drift per step", "pairs_per_step": r["n_pairs"],
+                       "parallelism": "replicas x1"},
+            "particles_stepped_per_s": n_part / (ms * 1e-3), "scatters": r["scatters"],
+            "clocks": clk, "peak_kind": peak_kind}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
-    if a.workload in ("galaxy40M", "boxes64"):
+    if a.workload in ("galaxy40M", "boxes64", "boxtest"):
         import torch
         from paper_2603_24688_gb300 import build
         build.build()
         peaks, peak_kind = load_peaks()
-        return (run_substeps if a.workload == "galaxy40M" else run_boxes)(a, peaks, peak_kind)
+        fn = {"galaxy40M": run_substeps, "boxes64": run_boxes, "boxtest": run_boxtest}[a.workload]
+        return fn(a, peaks, peak_kind)
     import torch
     from paper_2603_24688_gb300 import build, dmb
 

@@ -77,3 +77,24 @@ def test_five_term_expansion_accuracy_against_the_oracle():
             for x in (0.99 * x0, x0, 2 * x0, 1e3, 1e4):
                 ref = hyp1f1_neg(a, b, x)
                 assert abs(_expansion(a, b, x, terms) / ref - 1) < tol, (n, a, b, x)
+
+
+def _mass_mp(text):
+    val, unit = text.split()
+    return {"m_p": 1.0, "GeV": 1.0 / 0.93827208816, "MeV": 1e-3 / 0.93827208816}[unit] * float(val)
+
+
+def test_box_test_rows_are_the_papers_table():
+    from paper_2603_24688_gb300 import boxtest as BT
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "test_params.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                c = [x.strip() for x in line.split("|")]
+                npart = [int(x.split("^")[0]) ** int(x.split("^")[1]) for x in c[9:11]]
+                rows[c[0]] = (_mass_mp(c[1]), float(c[2]), int(c[3]), float(c[4]), float(c[5]), float(c[6]),
+                              float(c[7]), float(c[8]), npart[0], npart[1])
+    assert set(rows) == set(BT.ROWS)
+    for name, want in rows.items():
+        got = BT.ROWS[name]
+        assert all(abs(a - b) <= 1e-12 * abs(b) for a, b in zip(got, want)), (name, got, want)
