@@ -16,7 +16,8 @@ device state:
 * the Jarque-Bera statistic of the dark-matter velocities along each axis (App. F, without
   the factor N).
 
-`ROWS` holds Table test_params (App. F): the fiducial test and the rows that vary one setting.
+`ROWS` holds Table test_params (App. F): the fiducial test, the rows that vary one setting, and
+the recreation of the test of Fischer et al. 2025, Sec. 3.4 (the table's last row).
 Cross sections of the rows with n != 0 are quoted at v0 = c, as the paper writes sigma(v).
 The table gives neither the box side nor the gas molecular weight: runs use L = 1 kpc and
 mu = 1 unless told otherwise.
@@ -47,6 +48,7 @@ ROWS = {
     "m_chi=10MeV": (0.01 / GEV_PER_MP, 2e-27, 0, 200.0, 5e3, 1e4, 1e10, 1e10, 32 ** 3, 32 ** 3),
     "sigma~v^-2": (2.0, 2e-33, -2, 200.0, 1e6, 1e4, 1e10, 1e10, 32 ** 3, 32 ** 3),
     "sigma~v^-4": (2.0, 5e-40, -4, 200.0, 1e6, 1e4, 1e10, 1e10, 32 ** 3, 32 ** 3),
+    "F25 S3.4": (1.0, 1.6726e-23, 0, 0.0, 484.6, 72.69, 1e7, 1e7, 10 ** 5, 21 ** 3),
 }
 
 

@@ -91,7 +91,7 @@ def test_box_test_rows_are_the_papers_table():
         for line in f:
             if line.strip() and not line.startswith("#"):
                 c = [x.strip() for x in line.split("|")]
-                npart = [int(x.split("^")[0]) ** int(x.split("^")[1]) for x in c[9:11]]
+                npart = [int(x.split("^")[0]) ** int(x.split("^")[1]) if "^" in x else int(float(x)) for x in c[9:11]]
                 rows[c[0]] = (_mass_mp(c[1]), float(c[2]), int(c[3]), float(c[4]), float(c[5]), float(c[6]),
                               float(c[7]), float(c[8]), npart[0], npart[1])
     assert set(rows) == set(BT.ROWS)

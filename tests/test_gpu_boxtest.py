@@ -9,7 +9,8 @@ the momentum and the energy, and the expected dark-matter energy change must bal
 gain (App. C).  The Monte Carlo's scatter noise sets the tolerances: about 73,000 scatters over
 the fiducial run move the total energy by about 0.4 % (one standard deviation).  For the
 10 MeV row the dark matter departs from Maxwellian (JB well above 0.01); the paper reports
-that there the prediction transfers momentum faster than the simulation does."""
+that there the prediction transfers momentum faster than the simulation does.  The table's last
+row recreates the test of Fischer et al. 2025, Sec. 3.4, over about 20 Gyr."""
 import numpy as np
 import pytest
 
@@ -18,15 +19,15 @@ from oracle import mbode as M
 pytestmark = pytest.mark.gpu
 
 
-def _run(name):
+def _run(name, t_end=1.0, dt=1e-3):
     from paper_2603_24688_gb300 import boxtest as BT
-    r = BT.run(name, t_end=1.0, dt=1e-3, snap=100)
+    r = BT.run(name, t_end=t_end, dt=dt, snap=100)
     s, row = r["series"], r["row"]
     p = M.params(row["m_chi"], row["mu"], r["rho"][0], r["rho"][1], row["sigma0_cm2"], row["n"],
                  BT.C_KMS if row["n"] != 0 else 100.0)
     y0 = [s["V_chi"][0], s["V_B"][0], s["theta_chi"][0], s["theta_B"][0]]
-    t, ys = M.integrate(y0, p, 1.0, 1000)
-    idx = np.rint(s["t"] / 1e-3).astype(int)
+    t, ys = M.integrate(y0, p, t_end, int(round(t_end / dt)))
+    idx = np.rint(s["t"] / dt).astype(int)
     return r, s, row, ys[idx]
 
 
@@ -56,3 +57,16 @@ def test_non_maxwellian_row_relaxes_slower_than_predicted():
     # the prediction moves the dark matter's bulk velocity towards the gas's faster
     assert s["V_chi"][-1] > ode[-1, 0] + 1.0
     assert np.max(np.abs(s["E"] / s["E"][0] - 1)) < 0.02
+
+
+def test_f25_recreation_energies():
+    """The table's last row (the test of Fischer et al. 2025, Sec. 3.4): proton-mass dark matter,
+    a large constant cross section, a cold and sparse box, 1e5 + 21^3 particles, about 20 Gyr.
+    With no bulk velocities only the energies carry information; they follow the prediction."""
+    r, s, row, ode = _run("F25 S3.4", t_end=20.0, dt=0.02)
+    assert s["JB"].max() < 0.01
+    assert np.max(np.abs(s["theta_chi"] / ode[:, 2] - 1)) < 0.03
+    assert np.max(np.abs(s["theta_B"] / ode[:, 3] - 1)) < 0.03
+    assert np.max(np.abs(s["E"] / s["E"][0] - 1)) < 0.01
+    # the two species approach a common temperature: the dark matter cools, the gas heats
+    assert s["theta_chi"][-1] < 0.7 * s["theta_chi"][0] and s["theta_B"][-1] > 3.0 * s["theta_B"][0]
