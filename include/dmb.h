@@ -200,6 +200,21 @@ dmb_status dmb_debug_philox(dmb_ctx *ctx, int64_t k, const uint32_t *ctr, uint32
  * contexts only.  A later dmb_build_grid, dmb_neighbors or dmb_step invalidates it. */
 dmb_status dmb_set_bins(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas_bin);
 
+/* Timestep feedback (Sec. 2.5, Eq. prob_criterion: a dark-matter particle whose P_ij is too
+ * large takes a smaller timestep next).  p_ratio_max: device float [n], max_j P_ij / min(0.1,
+ * 1e-4 ((m_chi + mu_j) / mu_j)^2) of each particle at its current dt_i = 2^bin dt_min, as
+ * dmb_mc_scatter_dm writes it; dm_bin: device uint8 [n], updated in place.  P_ij is proportional
+ * to dt, so the ratio at bin b' is ratio 2^(b' - b).  A particle with ratio > 1 (or not finite)
+ * moves to the largest bin b' <= b with ratio 2^(b' - b) <= 1 (at least 0); one with ratio < 1/4
+ * moves up one bin if b < max_bin and substep (the next substep) is a multiple of 2^(b+1); all
+ * others keep their bins.  The paper gives the criterion, not this bin arithmetic: the rule is
+ * this library's reading.  active (device uint8 [n] or NULL = all): only particles with a
+ * nonzero flag move.  max_bin in [0, 63] (DMB_ERR_ARG otherwise).  n_changed (host, may be NULL):
+ * the number of bins that moved; when given the call synchronises.  The new bins take effect
+ * through dmb_set_bins. */
+dmb_status dmb_rebin_dm(dmb_ctx *ctx, const float *p_ratio_max, uint8_t *dm_bin, int64_t n, int32_t max_bin,
+                        uint64_t substep, const uint8_t *active, int64_t *n_changed);
+
 /* Host-side sizes of substep s (no GPU work): out5 = {active DM, active gas, mean-field row
  * segments, pairs of the active gas rows, pairs of the active DM rows}. */
 dmb_status dmb_substep_info(dmb_ctx *ctx, uint64_t substep, int64_t *out5);

@@ -82,3 +82,37 @@ def oracle_substep(dm, gas, params, substep, dt_min, dm_bin, gas_bin, pairs=None
     sums[14] = mc["p_ratio_max"].max() if len(Mi) else 0.0
     return dict(acc=acc, dudt=dudt, V_new=V_new, u_new=u_new, T_new=T_new, mc=mc, sums=sums,
                 active_dm=act_d, active_gas=act_g, pairs=(pi, pj), g=g)
+
+
+def rebin(ratio, bins, max_bin, substep=0, active=None):
+    """New timestep bins from the criterion of Eq. prob_criterion (the dt feedback of Sec. 2.5:
+    a particle whose P_ij is too large takes a smaller timestep next).
+
+    ratio: float32 max_j P_ij / min(0.1, 1e-4 ((m_chi + mu_j) / mu_j)^2) of each particle at its
+    current dt_i = 2^b dt_min (the Monte Carlo's p_ratio_max); P_ij is proportional to dt, so the
+    ratio at bin b' is ratio 2^(b' - b).  Rule (the paper gives the criterion, not the bin
+    arithmetic; this is the reading):
+      * ratio > 1 (or not finite): the largest b' <= b with ratio 2^(b' - b) <= 1, at least 0:
+        b' = b - k with k = ceil(log2 ratio), from ratio = m 2^e (m in [1/2, 1)): k = e, or
+        e - 1 when m = 1/2 (ratio an exact power of two);
+      * ratio < 1/4, b < max_bin and the next substep a multiple of 2^(b+1) (the larger step
+        starts at a boundary of the hierarchy): b' = b + 1;
+      * otherwise b' = b.  Inactive particles (active given and 0) keep their bins.
+    """
+    r = np.asarray(ratio, dtype=np.float32)
+    b = np.asarray(bins, dtype=np.int64)
+    out = b.copy()
+    for i in range(len(r)):
+        if active is not None and not active[i]:
+            continue
+        x = r[i]
+        if not np.isfinite(x) or x > 1.0:
+            if not np.isfinite(x):
+                out[i] = 0
+                continue
+            m, e = np.frexp(x)
+            k = int(e) - 1 if m == 0.5 else int(e)
+            out[i] = max(0, int(b[i]) - k)
+        elif x < 0.25 and b[i] < max_bin and substep % (1 << (int(b[i]) + 1)) == 0:
+            out[i] = b[i] + 1
+    return out.astype(np.uint8)

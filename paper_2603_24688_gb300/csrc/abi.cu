@@ -78,7 +78,7 @@ struct dmb_ctx {
   int seg_len = MF_SEG, act_seg_len = MF_SEG;   // segment lengths the two segment tables were built with
   Shapes shp;                                   // launch shapes (defaults or dmb_autotune's choice)
   DevBuf mf_acc, mf_dudt, e_exp, mc_blocks, mc_max, kick_blocks, sums;
-  DevBuf scratch_vel, search_stats;
+  DevBuf scratch_vel, search_stats, rebin_cnt;
   uint32_t *h_status = nullptr;   // pinned
   int64_t *h_tot = nullptr;       // pinned [8]
   double *h_sums = nullptr;       // pinned [16]
@@ -944,7 +944,8 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
                     &ctx->kick_blocks, &ctx->sums, &ctx->scratch_vel, &ctx->search_stats, &ctx->act_dm,
                     &ctx->act_gas, &ctx->act_start, &ctx->act_seg_ptr, &ctx->act_seg_row, &ctx->act_seg_begin,
                     &ctx->act_len, &ctx->act_segs, &ctx->act_gpairs, &ctx->act_dpairs, &ctx->act_pick,
-                    &ctx->step_dev, &ctx->bin_keys, &ctx->bin_keys1, &ctx->bin_vals1, &ctx->tc_tiles};
+                    &ctx->step_dev, &ctx->bin_keys, &ctx->bin_keys1, &ctx->bin_vals1, &ctx->tc_tiles,
+                    &ctx->rebin_cnt};
   for (DevBuf *b : bufs) release(*b);
   SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};
   for (SpeciesBufs *s : sp) {
@@ -1142,6 +1143,26 @@ dmb_status dmb_set_bins(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas_
   if ((ctx->dm.n > 0 && !dm_bin) || (ctx->gas.n > 0 && !gas_bin)) return fail(ctx, DMB_ERR_ARG, "bin array is NULL");
   invalidate_substeps(ctx);
   return ctx->p.fp64 ? set_bins_impl<double>(ctx, dm_bin, gas_bin) : set_bins_impl<float>(ctx, dm_bin, gas_bin);
+}
+
+dmb_status dmb_rebin_dm(dmb_ctx *ctx, const float *p_ratio_max, uint8_t *dm_bin, int64_t n, int32_t max_bin,
+                        uint64_t substep, const uint8_t *active, int64_t *n_changed) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (n < 0 || (n > 0 && (!p_ratio_max || !dm_bin))) return fail(ctx, DMB_ERR_ARG, "NULL array or n < 0");
+  if (max_bin < 0 || max_bin >= DMB_NBINS) return fail(ctx, DMB_ERR_ARG, "max_bin must be in [0, 63]");
+  if (!ensure(ctx->rebin_cnt, 8)) return fail(ctx, DMB_ERR_OOM, "device allocation failed");
+  cudaStream_t s = ctx->stream;
+  unsigned long long *cnt = ptr<unsigned long long>(ctx->rebin_cnt);
+  CK(cudaMemsetAsync(cnt, 0, 8, s), "memset");
+  CK(launch_rebin(p_ratio_max, dm_bin, n, max_bin, (unsigned long long)substep, active, cnt, s, &ctx->launches),
+     "rebin");
+  if (n_changed) {
+    unsigned long long h = 0;
+    CK(cudaMemcpyAsync(&h, cnt, 8, cudaMemcpyDeviceToHost, s), "readback");
+    CK(cudaStreamSynchronize(s), "synchronise");
+    *n_changed = (int64_t)h;
+  }
+  return DMB_OK;
 }
 
 dmb_status dmb_substep_info(dmb_ctx *ctx, uint64_t substep, int64_t *out5) {

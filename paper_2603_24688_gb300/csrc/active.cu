@@ -167,3 +167,44 @@ template cudaError_t launch_kick_gas_list<double>(double *, double *, const doub
                                                   const double *, const double *, const uint32_t *, int64_t,
                                                   const uint32_t *, const uint8_t *, double, RunConst, double4_32a *,
                                                   double4_32a *, double *, int, cudaStream_t, int64_t *);
+
+// A particle whose criterion ratio x = max_j P_ij / cap_j exceeds 1 (or is not finite) moves to
+// the largest bin b' <= b with x 2^(b' - b) <= 1 (P_ij is proportional to dt): with x = m 2^e,
+// m in [1/2, 1), k = ceil(log2 x) is e, or e - 1 when m = 1/2.  One with x < 1/4 moves up one
+// bin when the next substep is a multiple of 2^(b+1) and b < max_bin.  Decisions are integer
+// functions of the float ratio, so they are exact.
+__global__ void k_rebin(const float *__restrict__ ratio, uint8_t *__restrict__ bin, int64_t n, int max_bin,
+                        unsigned long long substep, const uint8_t *__restrict__ active,
+                        unsigned long long *__restrict__ changed) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool moved = false;
+  if (i < n && (active == nullptr || active[i] != 0)) {
+    const float x = ratio[i];
+    const int b = bin[i];
+    int nb = b;
+    if (!isfinite(x)) {
+      nb = 0;
+    } else if (x > 1.0f) {
+      int e;
+      const float m = frexpf(x, &e);
+      const int k = m == 0.5f ? e - 1 : e;
+      nb = b - k < 0 ? 0 : b - k;
+    } else if (x < 0.25f && b < max_bin && (substep & ((2ull << b) - 1ull)) == 0ull) {
+      nb = b + 1;
+    }
+    if (nb != b) {
+      bin[i] = (uint8_t)nb;
+      moved = true;
+    }
+  }
+  const unsigned m = __ballot_sync(DMB_FULL, moved);
+  if ((threadIdx.x & 31u) == 0u && m != 0u) atomicAdd(changed, (unsigned long long)__popc(m));
+}
+
+cudaError_t launch_rebin(const float *ratio, uint8_t *bin, int64_t n, int max_bin, unsigned long long substep,
+                         const uint8_t *active, unsigned long long *changed, cudaStream_t s, int64_t *launches) {
+  if (n <= 0) return cudaSuccess;
+  k_rebin<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ratio, bin, n, max_bin, substep, active, changed);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}

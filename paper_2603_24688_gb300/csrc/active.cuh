@@ -39,3 +39,8 @@ cudaError_t launch_kick_gas_list(double *vel, double *T, const double *mu, const
 // captured substep, so that the next replay runs the next substep).
 cudaError_t launch_step_set(unsigned long long *step, unsigned long long value, cudaStream_t s, int64_t *launches);
 cudaError_t launch_step_advance(unsigned long long *step, cudaStream_t s, int64_t *launches);
+
+// New timestep bins of n particles from the criterion ratios of Eq. prob_criterion (the rule of
+// dmb_rebin_dm); *changed (device) is increased by the number of bins that moved.
+cudaError_t launch_rebin(const float *ratio, uint8_t *bin, int64_t n, int max_bin, unsigned long long substep,
+                         const uint8_t *active, unsigned long long *changed, cudaStream_t s, int64_t *launches);

@@ -26,7 +26,7 @@ EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb
            "dmb_surrogate_infer", "dmb_surrogate_grad", "dmb_surrogate_fallbacks", "dmb_step_batched",
            "dmb_surrogate_grad_noalloc", "dmb_set_bins", "dmb_substep_info", "dmb_substep", "dmb_set_graph",
            "dmb_set_surrogate_engine", "dmb_surrogate_infer_tc", "dmb_autotune", "dmb_set_shapes",
-           "dmb_get_shapes"]
+           "dmb_get_shapes", "dmb_rebin_dm"]
 
 
 class DmbError(RuntimeError):
@@ -102,6 +102,7 @@ def load(path=LIB_PATH):
         "dmb_autotune": ([vp, c.POINTER(DM), c.POINTER(Gas), c.POINTER(c.c_int32), c.POINTER(c.c_double)], c.c_int),
         "dmb_set_shapes": ([vp, c.POINTER(c.c_int32)], c.c_int),
         "dmb_get_shapes": ([vp, c.POINTER(c.c_int32)], c.c_int),
+        "dmb_rebin_dm": ([vp, vp, vp, i64, c.c_int32, u64, vp, c.POINTER(i64)], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -286,6 +287,16 @@ class Context:
         v = (ctypes.c_int32 * 5)()
         self._check(self.lib.dmb_get_shapes(self.h, v))
         return dict(zip(self.SHAPE_NAMES, [int(x) for x in v]))
+
+    def dmb_rebin_dm(self, p_ratio_max, dm_bin, max_bin, substep=0, active=None):
+        """p_ratio_max: CUDA float32 [n]; dm_bin: CUDA uint8 [n] (updated in place); returns the
+        number of bins that moved."""
+        import torch
+        out = ctypes.c_int64()
+        self._check(self.lib.dmb_rebin_dm(self.h, _ptr(p_ratio_max, torch.float32), _ptr(dm_bin, torch.uint8),
+                                          int(dm_bin.numel()), int(max_bin), int(substep),
+                                          _ptr(active, torch.uint8), ctypes.byref(out)))
+        return out.value
 
     def dmb_set_graph(self, on=True):
         self._check(self.lib.dmb_set_graph(self.h, 1 if on else 0))

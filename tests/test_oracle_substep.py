@@ -58,3 +58,33 @@ def test_inactive_particles_untouched_and_dt_linearity():
     P_all = z["mc"]["P"][ad[pi]]
     scale = 2.0 ** db[pi[ad[pi]]].astype(float)
     np.testing.assert_allclose(P_sub, scale * P_all, rtol=1e-14)
+
+
+def test_rebin_rule_against_brute_force():
+    """The new bin is the largest b' <= b whose scaled ratio ratio 2^(b' - b) is <= 1 (found by
+    trying every bin), promotions happen only below 1/4, at a boundary of the larger step and
+    under max_bin, and inactive particles keep their bins."""
+    from oracle.substep import rebin
+    rng = np.random.default_rng(5)
+    n = 4000
+    b = rng.integers(0, 12, n)
+    x = (10.0 ** rng.uniform(-3, 4, n)).astype(np.float32)
+    x[:40] = np.float32(2.0) ** rng.integers(-4, 10, 40).astype(np.float32)     # exact powers of two
+    x[40:45] = [0.0, 1.0, 0.25, np.inf, np.nan]
+    for substep, max_bin in ((0, 11), (8, 11), (0, 5), (3, 63)):
+        act = rng.integers(0, 2, n).astype(bool)
+        nb = rebin(x, b, max_bin, substep, act)
+        for i in range(n):
+            if not act[i]:
+                assert nb[i] == b[i]
+                continue
+            xi = float(x[i])
+            if not np.isfinite(xi):
+                assert nb[i] == 0
+            elif xi > 1.0:
+                ok = [c for c in range(int(b[i]) + 1) if xi * 2.0 ** (c - int(b[i])) <= 1.0]
+                assert nb[i] == (max(ok) if ok else 0), (xi, b[i], nb[i])
+            elif xi < 0.25 and b[i] < max_bin and substep % (1 << (int(b[i]) + 1)) == 0:
+                assert nb[i] == b[i] + 1 and xi * 2.0 <= 0.5
+            else:
+                assert nb[i] == b[i]
