@@ -200,6 +200,19 @@ dmb_status dmb_debug_philox(dmb_ctx *ctx, int64_t k, const uint32_t *ctr, uint32
  * contexts only.  A later dmb_build_grid, dmb_neighbors or dmb_step invalidates it. */
 dmb_status dmb_set_bins(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas_bin);
 
+/* Monte Carlo variant of every later step (dmb_mc_scatter_dm, dmb_step, dmb_step_batched,
+ * dmb_substep).  0 (default): one categorical draw per dark-matter particle per step, the form
+ * of the derivation (Eqs. dm-update-vels, dm-update-prob).  1: the per-pair Bernoulli form in
+ * which Sec. 2.5 applies it: the particle's pairs, in ascending gas id, each scatter when
+ * r_ij < P_ij, with P_ij from the velocity after any earlier scatter of the step.  r_ij and the
+ * new direction come from the pair's Bernoulli Philox stream: counter (id_i, id_j, step_lo,
+ * step_hi & 0x3fffffff | 0x40000000); words 0 and 3 give r_ij with 52 random bits, words 1 and
+ * 2 cos theta' and phi' as for the categorical draw.  Steps must stay below 2^62.  At most 64
+ * scatters per particle and step.  The outputs keep their meaning: p_total and p_ratio_max
+ * from the velocity at the start of the step, partner = the first partner, the new velocity
+ * after all kicks.  DMB_ERR_ARG for other values.  Drops captured substep graphs. */
+dmb_status dmb_set_mc_variant(dmb_ctx *ctx, int32_t variant);
+
 /* Timestep feedback (Sec. 2.5, Eq. prob_criterion: a dark-matter particle whose P_ij is too
  * large takes a smaller timestep next).  p_ratio_max: device float [n], max_j P_ij / min(0.1,
  * 1e-4 ((m_chi + mu_j) / mu_j)^2) of each particle at its current dt_i = 2^bin dt_min, as

@@ -25,7 +25,7 @@ import numpy as np
 from . import units
 from .kernel import overlap_g_vec
 from .meanfield import pair_geometry
-from .philox import dm_uniforms, pair_normals
+from .philox import bern_uniforms, dm_uniforms, pair_normals
 
 NO_PARTNER = 0xFFFFFFFF
 
@@ -104,3 +104,61 @@ def scatter_pair(v_chi, v_B, m_chi, m_B, n_new):
     vc = v_chi + m_B / (m_chi + m_B) * vrel * (n_new - n_old)
     vb = v_B - m_chi / (m_chi + m_B) * vrel * (n_new - n_old)
     return vc, vb
+
+
+def mc_scatter_bernoulli(dm, gas, pi, pj, params, step, dt, g=None, max_scatters=64):
+    """The per-pair Bernoulli form in which Sec. 2.5 applies the Monte Carlo (the GIZMO
+    implementation): the pairs of DM particle i, in ascending gas id, each scatter when
+    r_ij < P_ij, where P_ij (Eq. dm-update-prob, with the pair's sample v^B_ij) is computed from
+    the particle's velocity after any earlier scatter of the step, and the kick is Eq.
+    scatter_chi with the pair's own isotropic direction.  r_ij and the direction come from the
+    Bernoulli stream (oracle/philox.py); at most max_scatters scatters per particle.
+
+    Returns the fields of mc_scatter (C_total and p_ratio_max at the start velocity, partner =
+    the first partner) plus n_scatter, and gap = min over the tested pairs of |r_ij - P_ij| / P_ij."""
+    m_chi = params["m_chi_mp"]
+    nd = len(dm["h"])
+    if g is None:
+        d = pair_geometry(dm, gas, pi, pj, params["periodic"], params["box"])
+        g = overlap_g_vec(d, dm["h"][pi], gas["h"][pj])
+    P0, vB, _ = pair_probabilities(dm, gas, pi, pj, params, step, dt, g)
+    r, cth, phi = bern_uniforms(params["seed"], step, dm["id"][pi].astype(np.uint64), gas["id"][pj].astype(np.uint64))
+    ratio = P0 / pcap(m_chi, gas["mu"][pj])
+    p_ratio_max = np.zeros(nd)
+    np.maximum.at(p_ratio_max, pi, ratio)
+    C_total = np.zeros(nd)
+    np.add.at(C_total, pi, P0)
+    nB = gas["mass"][pj] * units.MSUN_PER_MP / gas["mu"][pj]
+    s0, v0, n = units.sigma_kpc2(params["sigma0_cm2"]), params["v0_kms"], params["n"]
+
+    order = np.lexsort((gas["id"][pj], pi))
+    starts = np.searchsorted(pi[order], np.arange(nd), side="left")
+    ends = np.searchsorted(pi[order], np.arange(nd), side="right")
+    vel_new = dm["vel"].copy()
+    scattered = np.zeros(nd, dtype=bool)
+    partner = np.full(nd, NO_PARTNER, dtype=np.uint64)
+    n_scatter = np.zeros(nd, dtype=np.int64)
+    gap = np.full(nd, np.inf)
+    for i in np.unique(pi):
+        v = dm["vel"][i].copy()
+        for e in order[starts[i]:ends[i]]:
+            rel = v - vB[e]
+            vr = np.sqrt(rel @ rel)
+            P = nB[e] * g[e] * s0 * (vr / v0) ** n * vr * dt
+            if P > 0:
+                gap[i] = min(gap[i], abs(r[e] - P) / P)
+            if r[e] < P:
+                j = pj[e]
+                mu = gas["mu"][j]
+                sth = np.sqrt(max(0.0, 1.0 - cth[e] * cth[e]))
+                n_new = np.array([sth * np.cos(phi[e]), sth * np.sin(phi[e]), cth[e]])
+                v = v + mu / (m_chi + mu) * vr * (n_new - rel / vr)
+                if not scattered[i]:
+                    scattered[i] = True
+                    partner[i] = gas["id"][j]
+                n_scatter[i] += 1
+                if n_scatter[i] == max_scatters:
+                    break
+        vel_new[i] = v
+    return dict(vel_new=vel_new, scattered=scattered, partner=partner, p_ratio_max=p_ratio_max,
+                C_total=C_total, n_scatter=n_scatter, gap=gap)

@@ -17,6 +17,9 @@ Stream layout (the paper only says "draw a random number", Sec. 2.4):
                     r_i = ((w0 << 20 | w3 >> 12) + 0.5) 2^-52 (exact in float64, and an
                     exact 64-bit fixed-point fraction);
                     word 1: cos(theta') = 2u - 1; word 2: phi' = 2 pi u (isotropic direction)
+  Bernoulli    = counter (id_i, id_j, step & 0xffffffff, ((step >> 32) & 0x3fffffff) | 0x40000000)
+                 (the per-pair variant of the Monte Carlo) -> words 0 and 3: r_ij with 52 bits as r_i;
+                 word 1: cos(theta') = 2u - 1; word 2: phi' = 2 pi u
   uniform      = ((word >> 9) + 0.5) * 2^-23, in (0, 1) and exact in float32 and float64
   normals      = Box-Muller: z0, z1 = sqrt(-2 ln u0) (cos, sin)(2 pi u1),
                  z2 = sqrt(-2 ln u2) cos(2 pi u3)
@@ -98,3 +101,15 @@ def dm_uniforms(seed, step, id_i):
     cth = 2.0 * to_uniform(w[1]) - 1.0
     phi = 2.0 * np.pi * to_uniform(w[2])
     return r, cth, phi
+
+
+def bern_words(seed, step, id_i, id_j):
+    k0, k1 = _seed_key(seed)
+    step = int(step)
+    return philox4x32_10(id_i, id_j, step & 0xFFFFFFFF, ((step >> 32) & 0x3FFFFFFF) | 0x40000000, k0, k1)
+
+
+def bern_uniforms(seed, step, id_i, id_j):
+    """(r_ij, cos theta', phi') per pair of the per-pair Bernoulli stream."""
+    w = bern_words(seed, step, id_i, id_j)
+    return to_uniform52(w[0], w[3]), 2.0 * to_uniform(w[1]) - 1.0, 2.0 * np.pi * to_uniform(w[2])

@@ -105,6 +105,7 @@ struct dmb_ctx {
     int64_t launches;
   };
   bool use_graph = false;
+  int mc_variant = 0;             // dmb_set_mc_variant
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
   std::vector<GraphEntry> graphs;
@@ -593,6 +594,7 @@ dmb_status mc_impl(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, uint
   if (!ensure(ctx->mc_blocks, (size_t)nb * 8 * 8) || !ensure(ctx->mc_max, (size_t)nb * 8))
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for MC partials");
   McArgs a;
+  a.variant = ctx->mc_variant;
   a.dt = dt;
   a.step = step;
   a.seed = ctx->p.seed;
@@ -753,6 +755,7 @@ dmb_status substep_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int 
   // Monte Carlo of the active DM against all their gas partners, each with its own dt
   const int nb = mc_blocks_for(nda);
   McArgs a;
+  a.variant = ctx->mc_variant;
   a.dt = dt_min;
   a.step = substep;
   a.seed = ctx->p.seed;
@@ -1170,6 +1173,14 @@ dmb_status dmb_substep_info(dmb_ctx *ctx, uint64_t substep, int64_t *out5) {
   if (!ctx->bins_ready) return fail(ctx, DMB_ERR_STATE, "dmb_substep_info before dmb_set_bins");
   const int lim = substep_lim(substep);
   for (int k = 0; k < 5; ++k) out5[k] = ctx->bin_tab[k][lim];
+  return DMB_OK;
+}
+
+dmb_status dmb_set_mc_variant(dmb_ctx *ctx, int32_t variant) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (variant != 0 && variant != 1) return fail(ctx, DMB_ERR_ARG, "variant must be 0 or 1");
+  if (variant != ctx->mc_variant) clear_graphs(ctx);   // captured substeps hold the old kernel
+  ctx->mc_variant = variant;
   return DMB_OK;
 }
 

@@ -443,6 +443,153 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
   }
 }
 
+// ---- Monte Carlo, the per-pair Bernoulli variant ------------------------------------------
+// Sec. 2.5 as GIZMO applies it: the pairs of DM particle i, in ascending gas id, each scatter
+// when r_ij < P_ij, with P_ij from the particle's velocity at that point, so a scatter changes
+// the probabilities of the pairs after it.  r_ij and the new direction come from the pair's
+// Bernoulli stream (counter word 3 = step_hi | 2^30: words 0, 3 give r_ij with 52 bits, words
+// 1, 2 the isotropic direction); v^B_ij is the pair's usual sample.  On the device: the first
+// hit is the smallest gas id with r < P at the start velocity; after its kick the pairs of
+// larger id are tested again with the new velocity, and so on (at most 64 scatters a step).
+// The record is that of k_mc: C and rmax from the start velocity, partner = the first partner,
+// dv = the sum of the kicks; flag 4 when some r_ij lay within 2^-20 P_ij of P_ij.
+__device__ __forceinline__ uint4 bern_counter(uint32_t id_dm, uint32_t id_gas, unsigned long long step) {
+  return make_uint4(id_dm, id_gas, (uint32_t)step, ((uint32_t)(step >> 32) & 0x3fffffffu) | 0x40000000u);
+}
+__device__ __forceinline__ double uniform52(uint32_t w_hi, uint32_t w_lo) {
+  const unsigned long long k = ((unsigned long long)w_hi << 20) | (unsigned long long)(w_lo >> 12);
+  return ((double)k + 0.5) * 0x1p-52;
+}
+__device__ __forceinline__ uint32_t warp_min_u32(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(DMB_FULL, v, o));
+  return v;
+}
+
+template <typename R, int GEOM>
+__global__ void __launch_bounds__(MC_WARPS * 32, sizeof(R) == 4 ? 2 : 1)
+k_mc_bernoulli(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict__ row_ptr,
+               const uint32_t *__restrict__ rows, const float4 *__restrict__ gtab, RunConst rc, McArgs a,
+               McRec *__restrict__ rec) {
+  typedef typename Vec<R>::v4 v4;
+  const unsigned lane = threadIdx.x & 31u;
+  const int wib = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * MC_WARPS;
+  const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+  const R inv_v0 = (R)(1.0 / rc.v0);
+  const unsigned long long step = a.step_dev ? *a.step_dev : a.step;
+  const int64_t nrows = a.list ? a.n_list : D.n;
+  const R dt0 = (R)a.dt;
+  const uint32_t NONE = 0xffffffffu;
+  const int64_t warp_id = (int64_t)blockIdx.x * MC_WARPS + wib;
+  for (int64_t row0 = warp_id; row0 < nrows; row0 += 32 * nwarps) {
+    const int64_t kl = row0 + (int64_t)lane * nwarps;
+    int64_t il = 0;
+    bool busy = false;
+    if (kl < nrows) {
+      il = a.list ? (int64_t)a.list[kl] : kl;
+      busy = row_ptr[il + 1] > row_ptr[il];
+      if (!busy) {
+        McRec r;
+        r.c_lo = 0ull; r.c_hi = 0ull; r.rmax = 0.0f; r.flags = 0u; r.partner = NONE;
+        r.dv[0] = r.dv[1] = r.dv[2] = 0.0;
+        rec[il] = r;
+      }
+    }
+    for (unsigned busy_rows = __ballot_sync(DMB_FULL, busy); busy_rows; busy_rows &= busy_rows - 1) {
+      const int64_t i = __shfl_sync(DMB_FULL, il, __ffs(busy_rows) - 1);
+      const R dt = a.bin ? dt0 * (R)(1ull << a.bin[D.perm[i]]) : dt0;
+      const int64_t rs = row_ptr[i], re = row_ptr[i + 1];
+      const v4 Pi = D.P[i], Li = D.L[i];
+      v4 Vc = D.V[i];                                   // the particle's velocity as it scatters
+      const uint32_t id_i = D.id[i];
+      const BoxSide side = box_side<GEOM>(bx, GEOM == GEOM_BOXES ? (int)D.bid[i] : 0);
+      U128 sum = {0ull, 0ull};
+      float rmax = 0.0f;
+      bool band = false;
+      uint32_t hit = NONE;
+      for (int64_t p = rs + lane; p < re; p += 32) {
+        const uint32_t j = rows[p];
+        const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
+        const uint32_t idj = G.id[j];
+        R rx, ry, rz, vr;
+        const R P = pair_probability<R>(Pi, Li, Vc, id_i, Pj, Lj, Vj, Kj, idj, GEOM != GEOM_OPEN, side, gtab, rc.n,
+                                        inv_v0, dt, step, k0, k1, rx, ry, rz, vr);
+        sum = u128_add(sum, to_fixed(P));
+        const R e = Kj.w;
+        const R cap = (R)1e-4 / (e * e) < (R)0.1 ? (R)1e-4 / (e * e) : (R)0.1;   // Eq. prob_criterion
+        rmax = fmaxf(rmax, (float)(P / cap));
+        const uint4 wb = philox4x32_10(bern_counter(id_i, idj, step), k0, k1);
+        const double r = uniform52(wb.x, wb.w), Pd = (double)P;
+        band = band || fabs(r - Pd) <= Pd * 0x1p-20;
+        if (r < Pd && idj < hit) hit = idj;
+      }
+      const U128 C = warp_sum_u128(sum);
+      rmax = warp_max(rmax);
+      hit = warp_min_u32(hit);
+      const uint32_t first = hit;
+      R dv0 = 0, dv1 = 0, dv2 = 0;
+      for (int nscat = 0; hit != NONE && nscat < 64; ++nscat) {
+        // the pair of gas id `hit` (every lane evaluates it, so all hold the kick)
+        int64_t pstar = -1;
+        for (int64_t p0 = rs; p0 < re && pstar < 0; p0 += 32) {
+          const int64_t p = p0 + lane;
+          const unsigned m = __ballot_sync(DMB_FULL, p < re && G.id[rows[p]] == hit);
+          if (m) pstar = p0 + __ffs(m) - 1;
+        }
+        if (pstar < 0) break;
+        {
+          const uint32_t j = rows[pstar];
+          const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
+          R rx, ry, rz, vr;
+          (void)pair_probability<R>(Pi, Li, Vc, id_i, Pj, Lj, Vj, Kj, hit, GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0,
+                                    dt, step, k0, k1, rx, ry, rz, vr);
+          const uint4 wb = philox4x32_10(bern_counter(id_i, hit, step), k0, k1);
+          const R ct = (R)2 * uniform23<R>(wb.y) - (R)1;
+          const R st = sqrt_t(fmax((R)0, (R)1 - ct * ct));
+          R sp, cp;
+          if (sizeof(R) == 4) { float s_, c_; sincospif(2.0f * (float)uniform23<float>(wb.z), &s_, &c_); sp = (R)s_; cp = (R)c_; }
+          else { double s_, c_; sincospi(2.0 * uniform23<double>(wb.z), &s_, &c_); sp = (R)s_; cp = (R)c_; }
+          const R f = Kj.w * vr;                             // mu_j/(m_chi + mu_j) v_rel
+          const R inv = (R)1 / vr;
+          const R d0 = f * (st * cp - rx * inv), d1 = f * (st * sp - ry * inv), d2 = f * (ct - rz * inv);
+          Vc.x += d0; Vc.y += d1; Vc.z += d2;
+          dv0 += d0; dv1 += d1; dv2 += d2;
+        }
+        // the next hit among the pairs of larger gas id, with the new velocity
+        uint32_t next = NONE;
+        for (int64_t p = rs + lane; p < re; p += 32) {
+          const uint32_t j = rows[p];
+          const uint32_t idj = G.id[j];
+          if (idj <= hit) continue;
+          const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
+          R rx, ry, rz, vr;
+          const R P = pair_probability<R>(Pi, Li, Vc, id_i, Pj, Lj, Vj, Kj, idj, GEOM != GEOM_OPEN, side, gtab, rc.n,
+                                          inv_v0, dt, step, k0, k1, rx, ry, rz, vr);
+          const uint4 wb = philox4x32_10(bern_counter(id_i, idj, step), k0, k1);
+          const double r = uniform52(wb.x, wb.w), Pd = (double)P;
+          band = band || fabs(r - Pd) <= Pd * 0x1p-20;
+          if (r < Pd && idj < next) next = idj;
+        }
+        hit = warp_min_u32(next);
+      }
+      band = __any_sync(DMB_FULL, band);
+      if (lane == 0) {
+        McRec r;
+        r.c_lo = C.lo;
+        r.c_hi = C.hi;
+        r.rmax = rmax;
+        r.flags = (first != NONE ? 1u : 0u) | (band ? 4u : 0u);
+        r.partner = first;
+        r.dv[0] = (double)dv0;
+        r.dv[1] = (double)dv1;
+        r.dv[2] = (double)dv2;
+        rec[i] = r;
+      }
+    }
+  }
+}
+
 // float64 side of the Monte Carlo, one thread per DM particle: new velocities in caller
 // order and deterministic block partials of the step sums
 __global__ void __launch_bounds__(256)
@@ -510,10 +657,18 @@ cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int
   if (nrows <= 0) return cudaSuccess;
   int64_t blocks = (nrows + MC_WARPS - 1) / MC_WARPS;
   if (blocks > 152 * (int64_t)blocks_per_sm) blocks = 152 * (int64_t)blocks_per_sm;
-  switch (geom_of(bx)) {
-    case GEOM_OPEN: k_mc<R, GEOM_OPEN><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec); break;
-    case GEOM_BOX: k_mc<R, GEOM_BOX><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec); break;
-    default: k_mc<R, GEOM_BOXES><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec); break;
+  if (a.variant == 1) {
+    switch (geom_of(bx)) {
+      case GEOM_OPEN: k_mc_bernoulli<R, GEOM_OPEN><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, rec); break;
+      case GEOM_BOX: k_mc_bernoulli<R, GEOM_BOX><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, rec); break;
+      default: k_mc_bernoulli<R, GEOM_BOXES><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, rec); break;
+    }
+  } else {
+    switch (geom_of(bx)) {
+      case GEOM_OPEN: k_mc<R, GEOM_OPEN><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec); break;
+      case GEOM_BOX: k_mc<R, GEOM_BOX><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec); break;
+      default: k_mc<R, GEOM_BOXES><<<(unsigned)blocks, MC_WARPS * 32, 0, s>>>(D, G, bx, row_ptr, rows, gtab, rc, a, pcache, rec); break;
+    }
   }
   // the particle mass sits in L.w of the sorted copies
   const R *Lbase = reinterpret_cast<const R *>(D.L);

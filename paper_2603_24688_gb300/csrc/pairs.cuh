@@ -110,6 +110,8 @@ struct McArgs {
   const unsigned long long *step_dev = nullptr;
   void *v_sorted = nullptr;   // Vec<R>::v4 [N_chi] or null
   int v_sorted_fp64 = 0;
+  // 0: one categorical draw per DM particle; 1: the per-pair Bernoulli variant (k_mc_bernoulli)
+  int variant = 0;
 };
 
 // Sets the surrogate pass's shared-memory attribute (done before any graph capture).

@@ -26,7 +26,7 @@ EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb
            "dmb_surrogate_infer", "dmb_surrogate_grad", "dmb_surrogate_fallbacks", "dmb_step_batched",
            "dmb_surrogate_grad_noalloc", "dmb_set_bins", "dmb_substep_info", "dmb_substep", "dmb_set_graph",
            "dmb_set_surrogate_engine", "dmb_surrogate_infer_tc", "dmb_autotune", "dmb_set_shapes",
-           "dmb_get_shapes", "dmb_rebin_dm"]
+           "dmb_get_shapes", "dmb_rebin_dm", "dmb_set_mc_variant"]
 
 
 class DmbError(RuntimeError):
@@ -103,6 +103,7 @@ def load(path=LIB_PATH):
         "dmb_set_shapes": ([vp, c.POINTER(c.c_int32)], c.c_int),
         "dmb_get_shapes": ([vp, c.POINTER(c.c_int32)], c.c_int),
         "dmb_rebin_dm": ([vp, vp, vp, i64, c.c_int32, u64, vp, c.POINTER(i64)], c.c_int),
+        "dmb_set_mc_variant": ([vp, c.c_int32], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -297,6 +298,10 @@ class Context:
                                           int(dm_bin.numel()), int(max_bin), int(substep),
                                           _ptr(active, torch.uint8), ctypes.byref(out)))
         return out.value
+
+    def dmb_set_mc_variant(self, variant):
+        """0: one categorical draw per DM particle (default); 1: per-pair Bernoulli draws."""
+        self._check(self.lib.dmb_set_mc_variant(self.h, int(variant)))
 
     def dmb_set_graph(self, on=True):
         self._check(self.lib.dmb_set_graph(self.h, 1 if on else 0))

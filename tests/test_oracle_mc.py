@@ -128,3 +128,62 @@ def test_partner_choice_follows_probabilities():
     e = np.bincount(bins, weights=exp_counts[order], minlength=4) * obs_counts.sum() / total_exp
     chi2 = ((o - e) ** 2 / e).sum()
     assert stats.chi2.sf(chi2, 3) > 1e-4
+
+
+@pytest.mark.parametrize("n", [0, -2])
+def test_bernoulli_variant_mean_matches_expectation(n):
+    # the per-pair Bernoulli form has the same expectation (App. C) as the categorical draw to
+    # first order in P (a scatter changes the later probabilities only at second order)
+    w = _small_box(n)
+    dm, gas, prm, dt = w["dm"], w["gas"], w["params"], w["dt"]
+    pi, pj = pairs_bruteforce(dm, gas, True, prm["box"])
+    d = pair_geometry(dm, gas, pi, pj, True, prm["box"])
+    g = overlap_g_vec(d, dm["h"][pi], gas["h"][pj])
+    E_dv, E_dE, E_P = expected_dm(dm, gas, pi, pj, prm, dt, g)
+    R = 300
+    nd = len(dm["h"])
+    s1 = np.zeros((nd, 3))
+    s2 = np.zeros((nd, 3))
+    nscat = 0
+    for step in range(R):
+        out = M.mc_scatter_bernoulli(dm, gas, pi, pj, prm, step, dt, g)
+        dv = out["vel_new"] - dm["vel"]
+        s1 += dv
+        s2 += dv * dv
+        nscat += out["n_scatter"].sum()
+    mean = s1 / R
+    var = s2 / R - mean ** 2
+    ok = var[:, 0] > 0
+    zz = ((mean - E_dv)[ok] / np.sqrt(var[ok] / R)).reshape(-1)
+    assert abs(np.mean(zz)) < 5 / math.sqrt(zz.size)
+    assert 0.8 < np.median(np.abs(zz)) / 0.6745 < 1.2
+    lam = E_P.sum() * R
+    assert abs(nscat - lam) < 5 * math.sqrt(lam) + 0.05 * lam
+
+
+def test_bernoulli_variant_extremes():
+    # dt -> 0: nothing scatters.  dt huge: the first scatter is the smallest gas id whose r_ij is
+    # below its P_ij at the start velocity (a pair at the edge of the kernel, where g is tiny,
+    # can still miss), later scatters are capped, and a particle whose only pair scatters keeps
+    # its speed relative to that pair's gas sample
+    from oracle.philox import bern_uniforms
+    w = _small_box(0)
+    dm, gas, prm = w["dm"], w["gas"], w["params"]
+    pi, pj = pairs_bruteforce(dm, gas, True, prm["box"])
+    none = M.mc_scatter_bernoulli(dm, gas, pi, pj, prm, 3, 1e-30)
+    assert not none["scattered"].any() and np.array_equal(none["vel_new"], dm["vel"])
+    dt = 1e6
+    allp = M.mc_scatter_bernoulli(dm, gas, pi, pj, prm, 3, dt, max_scatters=8)
+    P0, vB, vrel = M.pair_probabilities(dm, gas, pi, pj, prm, 3, dt)
+    r, _, _ = bern_uniforms(prm["seed"], 3, dm["id"][pi].astype(np.uint64), gas["id"][pj].astype(np.uint64))
+    counts = np.bincount(pi, minlength=len(dm["h"]))
+    assert np.all(allp["n_scatter"] <= np.minimum(counts, 8))
+    assert np.count_nonzero(allp["n_scatter"] == 8) > 0
+    for i in np.unique(pi):
+        hit = (pi == i) & (r < P0)
+        want = gas["id"][pj[hit]].min() if hit.any() else M.NO_PARTNER
+        assert allp["partner"][i] == want
+    for i in np.nonzero(counts == 1)[0][:10]:
+        e = np.nonzero(pi == i)[0][0]
+        if allp["scattered"][i]:
+            assert abs(np.linalg.norm(allp["vel_new"][i] - vB[e]) - vrel[e]) < 1e-9 * vrel[e]
