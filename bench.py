@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--fp64", action="store_true", help="float64 pair arithmetic (the box4k configuration)")
     return ap.parse_args()
 
 
@@ -189,8 +190,14 @@ def cpu_oracle_sample(w, budget_s=12.0, target_pairs=150_000, seed=0):
 
 def workload_desc(a, w):
     """The config's workload string, the same for both arms."""
-    return (f"{a.workload}: {len(w['dm']['h'])} DM Hernquist halo + {len(w['gas']['h'])} gas exponential disk, "
-            f"sigma = 1e-24 cm^2 (v / 100 km/s)^{a.n}")
+    nd, ng = len(w['dm']['h']), len(w['gas']['h'])
+    if w["params"]["periodic"]:
+        L = w["params"]["box"][0]
+        geom = f"periodic {L:g} kpc box, {nd} DM + {ng} gas at uniform positions"
+    else:
+        geom = f"{nd} DM Hernquist halo + {ng} gas exponential disk"
+    prec = ", float64 pair arithmetic" if getattr(a, "fp64", False) else ""
+    return f"{a.workload}: {geom}, sigma = 1e-24 cm^2 (v / 100 km/s)^{a.n}{prec}"
 
 
 def run_reference(a):
@@ -402,7 +409,7 @@ def main():
 
     def new_ctx(rate):
         return dmb.Context(prm["sigma0_cm2"], prm["n"], prm["m_chi_mp"], prm["v0_kms"], prm["periodic"],
-                           tuple(prm["box"]), prm["seed"], rate_mode=modes[rate], stream=stream)
+                           tuple(prm["box"]), prm["seed"], fp64=a.fp64, rate_mode=modes[rate], stream=stream)
 
     surrogate = None
     train_report = None
@@ -576,7 +583,8 @@ def main():
     if rank == 0:
         line = {"metric": "pair_interactions_per_s", "value": value, "unit": "pairs/s", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs, f64 sums", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.fp64 else "f32 pairs, f64 sums",
+                "data": "synthetic",
                 "config": {"workload": workload_desc(a, w),
                            "rate_provider": {"mlp": "learned surrogate (tcgen05 tensor cores)",
                                              "quad": "64-point Gauss-Legendre quadrature",
