@@ -35,7 +35,9 @@ sys.path.insert(0, ROOT)
 SMS = 152
 LANES = 128
 # algorithmic lane operations per pair (FMA = 1 op, special functions = 1 op), counted from
-# the formulas each kernel evaluates; see DESIGN.md "Rooflines"
+# the formulas each kernel evaluates: the overlap table lookup, the pair geometry, the 1F1
+# rates and the float64-free sums for the mean field; Philox, Box-Muller, the overlap and the
+# fixed-point running sum for the Monte Carlo
 OPS_PER_PAIR = {"meanfield": 150.0, "mc": 256.0}
 # quadrature provider: 64 nodes x (2 exp + ~14 ops) + the 120 ops of the rest of the pair
 QUAD_OPS_PER_PAIR = 64 * 16 + 120.0
