@@ -366,8 +366,9 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
         pcache[p] = P;
         sum = u128_add(sum, to_fixed(P));
         const R e = Kj.w;                                   // mu_j / (m_chi + mu_j)
-        const R cap = (R)1e-4 / (e * e) < (R)0.1 ? (R)1e-4 / (e * e) : (R)0.1;   // Eq. prob_criterion
-        rmax = fmaxf(rmax, (float)(P / cap));
+        // Eq. prob_criterion: 1 / min(0.1, 1e-4 / e^2) = max(10, 1e4 e^2), no division
+        const R inv_cap = (R)1e4 * e * e > (R)10 ? (R)1e4 * e * e : (R)10;
+        rmax = fmaxf(rmax, (float)(P * inv_cap));
       }
       const U128 C = warp_sum_u128(sum);
       rmax = warp_max(rmax);
@@ -517,8 +518,9 @@ k_mc_bernoulli(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *_
                                         inv_v0, dt, step, k0, k1, rx, ry, rz, vr);
         sum = u128_add(sum, to_fixed(P));
         const R e = Kj.w;
-        const R cap = (R)1e-4 / (e * e) < (R)0.1 ? (R)1e-4 / (e * e) : (R)0.1;   // Eq. prob_criterion
-        rmax = fmaxf(rmax, (float)(P / cap));
+        // Eq. prob_criterion: 1 / min(0.1, 1e-4 / e^2) = max(10, 1e4 e^2), no division
+        const R inv_cap = (R)1e4 * e * e > (R)10 ? (R)1e4 * e * e : (R)10;
+        rmax = fmaxf(rmax, (float)(P * inv_cap));
         const uint4 wb = philox4x32_10(bern_counter(id_i, idj, step), k0, k1);
         const double r = uniform52(wb.x, wb.w), Pd = (double)P;
         band = band || fabs(r - Pd) <= Pd * 0x1p-20;
