@@ -42,7 +42,7 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
         const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
         R dx, dy, dz;
         pair_dx<R>(Pi, Li, Pj, Lj, GEOM != GEOM_OPEN, side, dx, dy, dz);
-        const R d = sqrt_t(dist2_rn<R>(dx, dy, dz));
+        const R d = sqrt_pair(dist2_rn<R>(dx, dy, dz));
         const R g = overlap_g<R>(gtab, d, Pi.w, Pj.w);
         const R wx = Vi.x - Vj.x, wy = Vi.y - Vj.y, wz = Vi.z - Vj.z;
         const R w2 = wx * wx + wy * wy + wz * wz;
@@ -285,7 +285,7 @@ __device__ __forceinline__ R pair_probability(const typename Vec<R>::v4 &Pi, con
                                               uint32_t k1, R &rx, R &ry, R &rz, R &vrel) {
   R dx, dy, dz;
   pair_dx<R>(Pi, Li, Pj, Lj, periodic, side, dx, dy, dz);
-  const R d = sqrt_t(dist2_rn<R>(dx, dy, dz));
+  const R d = sqrt_pair(dist2_rn<R>(dx, dy, dz));
   const R g = overlap_g<R>(gtab, d, Pi.w, Pj.w);
   const uint4 w = philox4x32_10(pair_counter(id_i, id_j, step), k0, k1);
   R z0, z1, z2;
@@ -294,7 +294,7 @@ __device__ __forceinline__ R pair_probability(const typename Vec<R>::v4 &Pi, con
   rx = Vi.x - (Vj.x + sig * z0);
   ry = Vi.y - (Vj.y + sig * z1);
   rz = Vi.z - (Vj.z + sig * z2);
-  vrel = sqrt_t(rx * rx + ry * ry + rz * rz);
+  vrel = sqrt_pair(rx * rx + ry * ry + rz * rz);
   return Kj.z * dt * g * ipow<R>(vrel * inv_v0, n) * vrel;
 }
 

@@ -3,6 +3,15 @@
 #pragma once
 #include "common.cuh"
 
+// Square roots inside the per-pair loops: the hardware approximation in float32 (a few ulp,
+// sqrt(+0) = +0), the correctly rounded root in float64
+__device__ __forceinline__ float sqrt_pair(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double sqrt_pair(double x) { return sqrt(x); }
+
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------------------------------
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -41,7 +50,7 @@ template <>
 __device__ __forceinline__ void box_muller3<float>(uint4 w, float &z0, float &z1, float &z2) {
   const float u0 = uniform23<float>(w.x), u1 = uniform23<float>(w.y);
   const float u2 = uniform23<float>(w.z), u3 = uniform23<float>(w.w);
-  const float r0 = sqrtf(-2.0f * logf(u0)), r2 = sqrtf(-2.0f * logf(u2));
+  const float r0 = sqrt_pair(-2.0f * logf(u0)), r2 = sqrt_pair(-2.0f * logf(u2));
   float s1, c1, s3, c3;
   sincospif(2.0f * u1, &s1, &c1);
   sincospif(2.0f * u3, &s3, &c3);
