@@ -11,6 +11,13 @@ __device__ __forceinline__ float sqrt_pair(float x) {
   return y;
 }
 __device__ __forceinline__ double sqrt_pair(double x) { return sqrt(x); }
+// Reciprocals inside the per-pair loops, likewise (1/+0 = +inf)
+__device__ __forceinline__ float rcp_pair(float x) {
+  float y;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double rcp_pair(double x) { return 1.0 / x; }
 
 // ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------------------------------
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
@@ -211,7 +218,7 @@ __device__ __forceinline__ R overlap_g(const float4 *T, R d, R hi, R hj);
 template <>
 __device__ __forceinline__ float overlap_g<float>(const float4 *T, float d, float hi, float hj) {
   const float ha = fmaxf(hi, hj), hb = fminf(hi, hj);
-  const float inv = 1.0f / ha;
+  const float inv = rcp_pair(ha);
   const float delta = d * inv;
   if (delta >= 2.0f) return 0.0f;
   return overlap_G_table(T, delta, hb * inv) * inv * inv * inv;
@@ -250,7 +257,7 @@ __device__ __forceinline__ double pow_t(double x, double y) { return pow(x, y); 
 template <typename R>
 __device__ __forceinline__ R ipow(R x, int n) {
   R r = (R)1;
-  R b = n < 0 ? (R)1 / x : x;
+  R b = n < 0 ? rcp_pair(x) : x;
   int m = n < 0 ? -n : n;
   while (m) {
     if (m & 1) r *= b;
