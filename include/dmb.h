@@ -222,7 +222,7 @@ dmb_status dmb_set_mc_variant(dmb_ctx *ctx, int32_t variant);
  * moves up one bin if b < max_bin and substep (the next substep) is a multiple of 2^(b+1); all
  * others keep their bins.  The paper gives the criterion, not this bin arithmetic: the rule is
  * this library's reading.  active (device uint8 [n] or NULL = all): only particles with a
- * nonzero flag move.  max_bin in [0, 63] (DMB_ERR_ARG otherwise).  n_changed (host, may be NULL):
+ * nonzero flag move.  n in [0, 2^31) and max_bin in [0, 63] (DMB_ERR_ARG otherwise).  n_changed (host, may be NULL):
  * the number of bins that moved; when given the call synchronises.  The new bins take effect
  * through dmb_set_bins. */
 dmb_status dmb_rebin_dm(dmb_ctx *ctx, const float *p_ratio_max, uint8_t *dm_bin, int64_t n, int32_t max_bin,

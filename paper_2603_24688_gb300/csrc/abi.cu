@@ -1151,7 +1151,8 @@ dmb_status dmb_set_bins(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas_
 dmb_status dmb_rebin_dm(dmb_ctx *ctx, const float *p_ratio_max, uint8_t *dm_bin, int64_t n, int32_t max_bin,
                         uint64_t substep, const uint8_t *active, int64_t *n_changed) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
-  if (n < 0 || (n > 0 && (!p_ratio_max || !dm_bin))) return fail(ctx, DMB_ERR_ARG, "NULL array or n < 0");
+  if (n < 0 || n > 0x7fffffffLL || (n > 0 && (!p_ratio_max || !dm_bin)))
+    return fail(ctx, DMB_ERR_ARG, "NULL array or n outside [0, 2^31)");
   if (max_bin < 0 || max_bin >= DMB_NBINS) return fail(ctx, DMB_ERR_ARG, "max_bin must be in [0, 63]");
   if (!ensure(ctx->rebin_cnt, 8)) return fail(ctx, DMB_ERR_OOM, "device allocation failed");
   cudaStream_t s = ctx->stream;
