@@ -219,12 +219,19 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
       out = row_ptr[qi] + unit_cnt[32 * u + lane];   // unit_cnt holds the exclusive offsets here
       out_end = row_ptr[qi + 1];
     }
-    for (int64_t it = it0; it < it1; ++it) {
-      const int64_t base = (int64_t)items[it] * DMB_LEAF;
-      if (EMIT && tmask != nullptr) {
-        // the count pass left this tile's pair masks (lane k: the query lanes paired with
-        // target k): the emit pass writes the pairs without testing distances again
-        const uint32_t mycol = tmask[32 * it + lane];
+    if (EMIT && tmask != nullptr) {
+      // the count pass left each tile's pair masks (lane k: the query lanes paired with target
+      // k): the emit pass writes the pairs without testing distances again, loading the next
+      // tile's mask and leaf while it writes this one's
+      uint32_t col_next = it0 < it1 ? tmask[32 * it0 + lane] : 0u;
+      uint32_t leaf_next = it0 < it1 ? items[it0] : 0u;
+      for (int64_t it = it0; it < it1; ++it) {
+        const uint32_t mycol = col_next;
+        const int64_t base = (int64_t)leaf_next * DMB_LEAF;
+        if (it + 1 < it1) {
+          col_next = tmask[32 * (it + 1) + lane];
+          leaf_next = items[it + 1];
+        }
         const unsigned m = __ballot_sync(DMB_FULL, mycol != 0u);
         for (unsigned mm = m; mm; mm &= mm - 1) {
           const int k = __ffs(mm) - 1;
@@ -234,8 +241,11 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
           }
         }
         if (tr_on && m) emit_transposed(tr, base, lane, lt, m, mycol, qi);
-        continue;
       }
+      continue;
+    }
+    for (int64_t it = it0; it < it1; ++it) {
+      const int64_t base = (int64_t)items[it] * DMB_LEAF;
       const int nk = (int)min((int64_t)DMB_LEAF, O.n - base);
       bool keep = false;
       __syncwarp();
