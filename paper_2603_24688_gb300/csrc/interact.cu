@@ -35,10 +35,13 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
       const bool hot = sig > (R)0;
       const R inv2s2 = hot ? (R)0.5 / (sig * sig) : (R)0;
       // warp-uniform trip count (the surrogate's tensor-core layers need all 32 lanes)
+      // each pass loads the next pass's partner index ahead of its own gathers
+      uint32_t i_next = rows[rs + lane < re ? rs + lane : rs];
       for (int64_t p0 = rs; p0 < re; p0 += 32) {
         const int64_t p = p0 + lane;
         const bool valid = p < re;
-        const uint32_t i = rows[valid ? p : rs];
+        const uint32_t i = i_next;
+        if (p0 + 32 < re) i_next = rows[p + 32 < re ? p + 32 : rs];
         const v4 Pi = D.P[i], Li = D.L[i], Vi = D.V[i];
         R dx, dy, dz;
         pair_dx<R>(Pi, Li, Pj, Lj, GEOM != GEOM_OPEN, side, dx, dy, dz);
@@ -357,8 +360,11 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
       const BoxSide side = box_side<GEOM>(bx, GEOM == GEOM_BOXES ? (int)D.bid[i] : 0);
       U128 sum = {0ull, 0ull};
       float rmax = 0.0f;
+      // each pass loads the next pass's partner index ahead of its own gathers
+      uint32_t j_next = rs + lane < re ? rows[rs + lane] : 0u;
       for (int64_t p = rs + lane; p < re; p += 32) {
-        const uint32_t j = rows[p];
+        const uint32_t j = j_next;
+        if (p + 32 < re) j_next = rows[p + 32];
         const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
         R rx, ry, rz, vr;
         const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0,
