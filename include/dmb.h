@@ -262,7 +262,8 @@ dmb_status dmb_surrogate_infer_tc(dmb_ctx *ctx, const float *X, int64_t n, float
  *              mean-field segment (pairs per warp task, 128..65536; default 2048),
  *              mean-field blocks per SM (grid cap, 1..64; default 32),
  *              Monte Carlo blocks per SM (1..64; default 32),
- *              surrogate warpgroups per CTA (2..4; default 4)}.
+ *              surrogate warpgroups per CTA (2..4; default 4; with 2 the activations are
+ *              kept in tensor memory)}.
  * dmb_autotune: builds the grid of (dm, gas) and times, with CUDA events on the context stream,
  * each candidate of one shape at a time in the order of the array (the search with units
  * {16, 32, 64, 128}; the mean field with segments {512, 1024, 2048, 4096} x blocks {8, 16, 32}

@@ -6,6 +6,12 @@
 // One CTA per SM holds the bf16 weights once and runs NWG independent warpgroups of 128
 // threads; warpgroup g owns TMEM columns [128 g, 128 g + 128) and its own activation buffers,
 // so while one warpgroup runs its epilogue another one's MMAs run.
+//
+// With TSA (two warpgroups) the activations stay in tensor memory: the A operand of every
+// layer is read by the MMA from TMEM, written by the epilogue with tcgen05.st (two bf16 per
+// 32-bit column, row = lane), so the loop stores nothing to shared memory and needs no proxy
+// fence.  Warpgroup g then owns columns [256 g, 256 g + 192): A in the first 64 (K = 128 bf16),
+// the accumulator in the next 128; three such groups would not fit in the 512 columns.
 // Thread t of a warpgroup owns row t of its tile: it forms the row's inputs, reads the row's
 // accumulator (TMEM lane t) and writes the row's activations.
 //
@@ -126,6 +132,15 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
       : "memory");
 }
 
+// the same MMA with A read from tensor memory (lane = row, column c = elements 2c, 2c + 1)
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(TC_IDESC), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -152,6 +167,44 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
 #pragma unroll
   for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
+
+// 32 columns without the wait: the registers are valid after tmem_wait_ld and reg_tie32
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t r[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// orders the uses of r after the preceding tmem_wait_ld
+__device__ __forceinline__ void reg_tie32(uint32_t r[32]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
+}
+
+// 16 (8) consecutive 32-bit columns of this thread's TMEM lane; completed by tmem_wait_st
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t r[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t r[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // bf16x2 of (max(lo, 0), max(hi, 0)), lo in the low half, each rounded to nearest even
 __device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
@@ -219,8 +272,9 @@ __device__ __forceinline__ void fetch_stage(const TcArgs &a, int64_t q, int stag
 // quadrature (counted), cold gas is skipped (the mean field uses the exact cold limit).
 enum { MODE_X = 0, MODE_PAIRS = 1 };
 
-template <int NWG, int MODE>
+template <int NWG, int MODE, bool TSA>
 __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
+  static_assert(!TSA || NWG == 2, "activations in tensor memory: two warpgroups of 192 columns");
   typedef TcLayout<NWG> Ly;
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x;
@@ -280,7 +334,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Ly::TSLOT);
-  const uint32_t ncols = NWG <= 2 ? 256u : 512u;
+  const uint32_t ncols = (NWG <= 2 && !TSA) ? 256u : 512u;
   static_assert(NWG * 128 <= 512, "tensor memory holds at most four 128-column accumulators");
   if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + Ly::TSLOT),
@@ -293,8 +347,11 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t d_tmem = tmem + 128u * (uint32_t)g;                           // lane 0, this group's columns
+  // lane 0 of this group's accumulator (and, with TSA, of its A operand)
+  const uint32_t a_tmem = tmem + 256u * (uint32_t)g;
+  const uint32_t d_tmem = TSA ? a_tmem + 64u : tmem + 128u * (uint32_t)g;
   const uint32_t my_lanes = d_tmem + ((uint32_t)(32 * w) << 16);
+  const uint32_t my_a = a_tmem + ((uint32_t)(32 * w) << 16);
   const uint32_t sA = sbase + Ly::A + g * TC_OPER, sA1 = sA;   // the layer-1 operand is slice 0 of A
   unsigned char *pA = sm + Ly::A + g * TC_OPER;
   unsigned char *pA1 = pA;
@@ -346,8 +403,13 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
         hi2[m / 2] = bf16_bits(x[m]) | (bf16_bits(x[m + 1]) << 16);
         lo2[m / 2] = bf16_bits(x[m] - h0) | (bf16_bits(x[m + 1] - h1) << 16);
       }
-      *reinterpret_cast<uint4 *>(pA1 + 0 * TC_SLICE + t * 16) = make_uint4(hi2[0], hi2[1], hi2[0], hi2[1]);
-      *reinterpret_cast<uint4 *>(pA1 + 1 * TC_SLICE + t * 16) = make_uint4(lo2[0], lo2[1], 0x3F803F80u, 0u);
+      if (TSA) {
+        const uint32_t r8[8] = {hi2[0], hi2[1], hi2[0], hi2[1], lo2[0], lo2[1], 0x3F803F80u, 0u};
+        tmem_st8(my_a, r8);
+      } else {
+        *reinterpret_cast<uint4 *>(pA1 + 0 * TC_SLICE + t * 16) = make_uint4(hi2[0], hi2[1], hi2[0], hi2[1]);
+        *reinterpret_cast<uint4 *>(pA1 + 1 * TC_SLICE + t * 16) = make_uint4(lo2[0], lo2[1], 0x3F803F80u, 0u);
+      }
     }
     // ---- three layers ------------------------------------------------------------------------
     // output-layer partial sums: four independent two-wide accumulators per output
@@ -356,19 +418,29 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     for (int u = 0; u < 4; ++u) y0[u] = y1[u] = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int layer = 0; layer < 3; ++layer) {
-      fence_async_smem();
+      if (TSA)
+        tmem_wait_st();   // this thread's row of the A operand is in tensor memory
+      else
+        fence_async_smem();
       tc_fence_before();
       wg_sync(bar_id);
       if (t == 0) {
         tc_fence_after();
         if (layer == 0) {
-          tc_mma(d_tmem, smem_desc(sA1, TC_SLICE, 128), smem_desc(sbase + Ly::W1, TC_SLICE, 128), 0u);
+          if (TSA)
+            tc_mma_ts(d_tmem, a_tmem, smem_desc(sbase + Ly::W1, TC_SLICE, 128), 0u);
+          else
+            tc_mma(d_tmem, smem_desc(sA1, TC_SLICE, 128), smem_desc(sbase + Ly::W1, TC_SLICE, 128), 0u);
         } else {
           const uint32_t sW = sbase + (layer == 1 ? Ly::W2 : Ly::W3);
 #pragma unroll
-          for (int ks = 0; ks < MLP_H / 16; ++ks)
-            tc_mma(d_tmem, smem_desc(sA + ks * 2 * TC_SLICE, TC_SLICE, 128),
-                   smem_desc(sW + ks * 2 * TC_SLICE, TC_SLICE, 128), ks > 0 ? 1u : 0u);
+          for (int ks = 0; ks < MLP_H / 16; ++ks) {
+            if (TSA)
+              tc_mma_ts(d_tmem, a_tmem + 8u * ks, smem_desc(sW + ks * 2 * TC_SLICE, TC_SLICE, 128), ks > 0 ? 1u : 0u);
+            else
+              tc_mma(d_tmem, smem_desc(sA + ks * 2 * TC_SLICE, TC_SLICE, 128),
+                     smem_desc(sW + ks * 2 * TC_SLICE, TC_SLICE, 128), ks > 0 ? 1u : 0u);
+          }
           // + b through the constant slice
           tc_mma(d_tmem, smem_desc(sbase + Ly::ONE, TC_SLICE, 128),
                  smem_desc(sbase + Ly::BB + (layer - 1) * TC_OPER1, TC_SLICE, 128), 1u);
@@ -393,27 +465,59 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
         break;
       }
       tc_fence_after();
-#pragma unroll 1
-      for (int cc = 0; cc < MLP_H / 32; ++cc) {
-        float v[32];
-        tmem_ld32(my_lanes + 32u * cc, v);   // z with the bias
+      if (TSA) {
+        // the whole row of z at once (one wait for four loads): with two warpgroups each warp
+        // has the registers, and the epilogue's latency is what limits it
+        uint32_t r[MLP_H];
+#pragma unroll
+        for (int cc = 0; cc < MLP_H / 32; ++cc) tmem_ld32_nowait(my_lanes + 32u * cc, r + 32 * cc);
+        tmem_wait_ld();
+#pragma unroll
+        for (int cc = 0; cc < MLP_H / 32; ++cc) reg_tie32(r + 32 * cc);
         if (layer < 2) {
-          uint32_t pk[16];
 #pragma unroll
-          for (int k = 0; k < 16; ++k)
-            pk[k] = pack_relu_bf16(v[2 * k] * fabsf(v[2 * k]), v[2 * k + 1] * fabsf(v[2 * k + 1]));
+          for (int cc = 0; cc < MLP_H / 32; ++cc) {
+            uint32_t pk[16];
 #pragma unroll
-          for (int c4 = 0; c4 < 4; ++c4)
-            *reinterpret_cast<uint4 *>(pA + (4 * cc + c4) * TC_SLICE + t * 16) =
-                make_uint4(pk[4 * c4], pk[4 * c4 + 1], pk[4 * c4 + 2], pk[4 * c4 + 3]);
+            for (int k = 0; k < 16; ++k) {
+              const float z0 = __uint_as_float(r[32 * cc + 2 * k]), z1 = __uint_as_float(r[32 * cc + 2 * k + 1]);
+              pk[k] = pack_relu_bf16(z0 * fabsf(z0), z1 * fabsf(z1));
+            }
+            tmem_st16(my_a + 16u * cc, pk);
+          }
         } else {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int c = 32 * cc + 2 * k;
-            const float2 r = make_float2(fmaxf(v[2 * k], 0.0f), fmaxf(v[2 * k + 1], 0.0f));
-            const float2 act = __fmul2_rn(r, r);
+          for (int k = 0; k < MLP_H / 2; ++k) {
+            const int c = 2 * k;
+            const float2 rr = make_float2(fmaxf(__uint_as_float(r[c]), 0.0f), fmaxf(__uint_as_float(r[c + 1]), 0.0f));
+            const float2 act = __fmul2_rn(rr, rr);
             y0[k & 3] = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + c), act, y0[k & 3]);
             y1[k & 3] = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + MLP_H + c), act, y1[k & 3]);
+          }
+        }
+      } else {
+#pragma unroll 1
+        for (int cc = 0; cc < MLP_H / 32; ++cc) {
+          float v[32];
+          tmem_ld32(my_lanes + 32u * cc, v);   // z with the bias
+          if (layer < 2) {
+            uint32_t pk[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+              pk[k] = pack_relu_bf16(v[2 * k] * fabsf(v[2 * k]), v[2 * k + 1] * fabsf(v[2 * k + 1]));
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4)
+              *reinterpret_cast<uint4 *>(pA + (4 * cc + c4) * TC_SLICE + t * 16) =
+                  make_uint4(pk[4 * c4], pk[4 * c4 + 1], pk[4 * c4 + 2], pk[4 * c4 + 3]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int c = 32 * cc + 2 * k;
+              const float2 r = make_float2(fmaxf(v[2 * k], 0.0f), fmaxf(v[2 * k + 1], 0.0f));
+              const float2 act = __fmul2_rn(r, r);
+              y0[k & 3] = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + c), act, y0[k & 3]);
+              y1[k & 3] = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + MLP_H + c), act, y1[k & 3]);
+            }
           }
         }
       }
@@ -465,26 +569,20 @@ static bool g_tc_attr = false;
 
 cudaError_t mlp_tc_prepare() {
   if (g_tc_attr) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<3, MODE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       TcLayout<3>::TOTAL);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mlp_tc<3, MODE_PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TcLayout<3>::TOTAL);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mlp_tc<2, MODE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcLayout<2>::TOTAL);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mlp_tc<2, MODE_PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TcLayout<2>::TOTAL);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mlp_tc<4, MODE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcLayout<4>::TOTAL);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mlp_tc<4, MODE_PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TcLayout<4>::TOTAL);
-  if (e == cudaSuccess) g_tc_attr = true;
-  return e;
+  const void *fns[6] = {(const void *)k_mlp_tc<2, MODE_X, true>, (const void *)k_mlp_tc<2, MODE_PAIRS, true>,
+                        (const void *)k_mlp_tc<3, MODE_X, false>, (const void *)k_mlp_tc<3, MODE_PAIRS, false>,
+                        (const void *)k_mlp_tc<4, MODE_X, false>, (const void *)k_mlp_tc<4, MODE_PAIRS, false>};
+  const int smem[6] = {TcLayout<2>::TOTAL, TcLayout<2>::TOTAL, TcLayout<3>::TOTAL,
+                       TcLayout<3>::TOTAL, TcLayout<4>::TOTAL, TcLayout<4>::TOTAL};
+  for (int k = 0; k < 6; ++k) {
+    const cudaError_t e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem[k]);
+    if (e != cudaSuccess) return e;
+  }
+  g_tc_attr = true;
+  return cudaSuccess;
 }
 
-template <int NWG, int MODE>
+template <int NWG, int MODE, bool TSA = false>
 static cudaError_t launch_tc(const TcArgs &a, cudaStream_t s) {
   const int smem = TcLayout<NWG>::TOTAL;
   const cudaError_t e = mlp_tc_prepare();
@@ -493,14 +591,14 @@ static cudaError_t launch_tc(const TcArgs &a, cudaStream_t s) {
   int64_t blocks = (n_tiles + NWG - 1) / NWG;
   if (blocks > 152) blocks = 152;
   if (blocks < 1) blocks = 1;
-  k_mlp_tc<NWG, MODE><<<(unsigned)blocks, NWG * 128, smem, s>>>(a);
+  k_mlp_tc<NWG, MODE, TSA><<<(unsigned)blocks, NWG * 128, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t mlp_tc_infer(TcArgs a, int nwg, cudaStream_t s, int64_t *launches) {
   if (a.n <= 0) return cudaSuccess;
   if (launches) *launches += 1;
-  return nwg == 2 ? launch_tc<2, MODE_X>(a, s) : nwg == 4 ? launch_tc<4, MODE_X>(a, s) : launch_tc<3, MODE_X>(a, s);
+  return nwg == 2 ? launch_tc<2, MODE_X, true>(a, s) : nwg == 4 ? launch_tc<4, MODE_X>(a, s) : launch_tc<3, MODE_X>(a, s);
 }
 
 cudaError_t mlp_tc_pair_rates(TcArgs a, uint32_t *prow, int nwg, cudaStream_t s, int64_t *launches) {
@@ -510,6 +608,6 @@ cudaError_t mlp_tc_pair_rates(TcArgs a, uint32_t *prow, int nwg, cudaStream_t s,
   k_pair_rows<<<(unsigned)blocks, 256, 0, s>>>(a.R_ptr, a.n_rows, prow);
   a.prow = prow;
   if (launches) *launches += 2;
-  return nwg == 2 ? launch_tc<2, MODE_PAIRS>(a, s)
+  return nwg == 2 ? launch_tc<2, MODE_PAIRS, true>(a, s)
                   : nwg == 4 ? launch_tc<4, MODE_PAIRS>(a, s) : launch_tc<3, MODE_PAIRS>(a, s);
 }

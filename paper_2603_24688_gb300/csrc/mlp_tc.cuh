@@ -34,7 +34,8 @@ struct TcArgs {
 // Shared-memory attributes (call once before any graph capture).
 cudaError_t mlp_tc_prepare();
 // Raw network outputs of X (debug / validation entry).
-// nwg: warpgroups (independent 128-row tiles in flight) per CTA, 2 to 4.
+// nwg: warpgroups (independent 128-row tiles in flight) per CTA, 2 to 4; with 2 the
+// activations stay in tensor memory as the MMAs' A operand.
 cudaError_t mlp_tc_infer(TcArgs a, int nwg, cudaStream_t s, int64_t *launches);
 // Rates of the pairs in processing order; prow: scratch of n uint32 (the row of every q).
 cudaError_t mlp_tc_pair_rates(TcArgs a, uint32_t *prow, int nwg, cudaStream_t s, int64_t *launches);

@@ -1,5 +1,7 @@
 """The surrogate on the tcgen05 tensor cores (128-row tiles, accumulators in tensor memory)
-against the CPU reference of the network and against the warp-level mma.sync engine."""
+against the CPU reference of the network and against the warp-level mma.sync engine, for each
+warpgroup count: 2 (activations kept in tensor memory as the MMAs' A operand), 3 and 4
+(activations in shared memory)."""
 import numpy as np
 import pytest
 
@@ -23,12 +25,20 @@ def _ctx(n=0, w=None):
                        rate_mode=dmb.DMB_RATE_MLP)
 
 
+def _set_wg(ctx, wg):
+    sh = ctx.dmb_get_shapes()
+    sh["tc_warpgroups"] = wg
+    ctx.dmb_set_shapes(sh)
+
+
+@pytest.mark.parametrize("wg", [2, 3, 4])
 @pytest.mark.parametrize("rows", [1, 200, 128 * 3 * 152 * 2 + 77])
-def test_tc_forward_matches_cpu_reference(rows):
+def test_tc_forward_matches_cpu_reference(rows, wg):
     rng = np.random.default_rng(5)
     p = (rng.uniform(-1, 1, O.NPARAM) * 0.2).astype(np.float32)
     ctx = _ctx()
     ctx.dmb_load_surrogate(p)
+    _set_wg(ctx, wg)
     X = rng.uniform(-1, 1, (rows, 4)).astype(np.float32)
     Xd = torch.from_numpy(X).cuda()
     Yd = torch.full((rows, 2), float("nan"), dtype=torch.float32, device="cuda")
@@ -45,7 +55,27 @@ def test_tc_forward_matches_cpu_reference(rows):
     assert np.max(np.abs(got - Y2.cpu().numpy())) < 2e-3 * (1 + np.abs(ref).max())
 
 
-def test_tc_pair_rates_match_the_warp_engine():
+def test_tc_warpgroup_counts_agree_bit_for_bit():
+    """The three kernels issue the same MMAs on the same operands; only where the activations
+    live differs, so their outputs are identical."""
+    rng = np.random.default_rng(8)
+    p = (rng.uniform(-1, 1, O.NPARAM) * 0.2).astype(np.float32)
+    ctx = _ctx()
+    ctx.dmb_load_surrogate(p)
+    rows = 128 * 4 * 152 * 3 + 5
+    Xd = torch.from_numpy(rng.uniform(-1, 1, (rows, 4)).astype(np.float32)).cuda()
+    out = {}
+    for wg in (2, 3, 4):
+        _set_wg(ctx, wg)
+        Yd = torch.full((rows, 2), float("nan"), dtype=torch.float32, device="cuda")
+        ctx.dmb_surrogate_infer_tc(Xd, Yd)
+        out[wg] = Yd.cpu().numpy()
+    assert np.all(np.isfinite(out[4]))
+    assert np.array_equal(out[2], out[4]) and np.array_equal(out[3], out[4])
+
+
+@pytest.mark.parametrize("wg", [2, 4])
+def test_tc_pair_rates_match_the_warp_engine(wg):
     rng = np.random.default_rng(6)
     w = W.subsample(W.named("galaxy1M"), 60_000, 40_000, seed=2)
     w["params"]["n"] = -2
@@ -53,6 +83,7 @@ def test_tc_pair_rates_match_the_warp_engine():
     ctx = dmb.Context(p["sigma0_cm2"], -2, p["m_chi_mp"], p["v0_kms"], False, p["box"], p["seed"],
                       rate_mode=dmb.DMB_RATE_MLP)
     ctx.dmb_train_surrogate(nsamples=1 << 18, epochs=4, seed=3)
+    _set_wg(ctx, wg)
     dm, gas = device_inputs(w)
     ctx.dmb_build_grid(dm, gas)
     npairs = ctx.dmb_neighbors()
