@@ -218,6 +218,26 @@ __device__ __forceinline__ uint32_t bf16_bits(float x) {
   return (uint32_t) * reinterpret_cast<const uint16_t *>(&b);
 }
 
+__device__ __forceinline__ float as_f32(float x) { return x; }
+__device__ __forceinline__ float as_f32(uint32_t x) { return __uint_as_float(x); }
+
+// Output layer, four columns: y_o += W4[o][c] max(z_c, 0)^2 for c = c0 .. c0 + 3 (z as float or
+// raw bits, w = W4 + c0 in shared memory, 16-byte aligned); columns (c0, c0 + 1) go to
+// accumulator k & 3 and (c0 + 2, c0 + 3) to (k + 1) & 3.  One 16-byte load per output row and
+// four columns.
+template <typename Z>
+__device__ __forceinline__ void out_layer4(const Z *z, const float *w, int k, float2 y0[4], float2 y1[4]) {
+  const float4 wa = *reinterpret_cast<const float4 *>(w);
+  const float4 wb = *reinterpret_cast<const float4 *>(w + MLP_H);
+  const float2 r0 = make_float2(fmaxf(as_f32(z[0]), 0.0f), fmaxf(as_f32(z[1]), 0.0f));
+  const float2 r1 = make_float2(fmaxf(as_f32(z[2]), 0.0f), fmaxf(as_f32(z[3]), 0.0f));
+  const float2 a0 = __fmul2_rn(r0, r0), a1 = __fmul2_rn(r1, r1);
+  y0[k & 3] = __ffma2_rn(make_float2(wa.x, wa.y), a0, y0[k & 3]);
+  y1[k & 3] = __ffma2_rn(make_float2(wb.x, wb.y), a0, y1[k & 3]);
+  y0[(k + 1) & 3] = __ffma2_rn(make_float2(wa.z, wa.w), a1, y0[(k + 1) & 3]);
+  y1[(k + 1) & 3] = __ffma2_rn(make_float2(wb.z, wb.w), a1, y1[(k + 1) & 3]);
+}
+
 // ---- row gather, in dependent stages --------------------------------------------------------
 // MODE_X: Vi = X[q] (the four network inputs).  MODE_PAIRS: k = prow[q] is the row of q; the
 // pair is p = q (rows are all gas, k = j) or p = row_ptr[list[k]] + q - R_ptr[k] (listed rows);
@@ -487,13 +507,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
           }
         } else {
 #pragma unroll
-          for (int k = 0; k < MLP_H / 2; ++k) {
-            const int c = 2 * k;
-            const float2 rr = make_float2(fmaxf(__uint_as_float(r[c]), 0.0f), fmaxf(__uint_as_float(r[c + 1]), 0.0f));
-            const float2 act = __fmul2_rn(rr, rr);
-            y0[k & 3] = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + c), act, y0[k & 3]);
-            y1[k & 3] = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + MLP_H + c), act, y1[k & 3]);
-          }
+          for (int k = 0; k < MLP_H / 2; k += 2) out_layer4(r + 2 * k, W4 + 2 * k, k, y0, y1);
         }
       } else {
 #pragma unroll 1
@@ -511,13 +525,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
                   make_uint4(pk[4 * c4], pk[4 * c4 + 1], pk[4 * c4 + 2], pk[4 * c4 + 3]);
           } else {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-              const int c = 32 * cc + 2 * k;
-              const float2 r = make_float2(fmaxf(v[2 * k], 0.0f), fmaxf(v[2 * k + 1], 0.0f));
-              const float2 act = __fmul2_rn(r, r);
-              y0[k & 3] = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + c), act, y0[k & 3]);
-              y1[k & 3] = __ffma2_rn(*reinterpret_cast<const float2 *>(W4 + MLP_H + c), act, y1[k & 3]);
-            }
+            for (int k = 0; k < 16; k += 2) out_layer4(v + 2 * k, W4 + 32 * cc + 2 * k, k, y0, y1);
           }
         }
       }
