@@ -51,7 +51,7 @@ MLP_TENSOR_FLOP_PER_PAIR = 2.0 * 128 * (16 + 128 + 16 + 128 + 16)
 # (dram__bytes_read.sum + dram__bytes_write.sum = 711.8 + 638.9 MB for 85,071,169 pairs), scaled
 # to a launch by its pair count.  Algorithmic bytes: row index, DM index, two 16-byte velocity
 # copies read and the 8-byte rates written per pair
-MLP_DRAM_BYTES_PER_PAIR = (711.824128e6 + 638.946560e6) / 85071169
+MLP_DRAM_BYTES_PER_PAIR = (714.359040e6 + 639.384064e6) / 85071169
 MLP_ALGO_BYTES_PER_PAIR = 4 + 4 + 16 + 16 + 8
 
 
