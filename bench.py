@@ -507,7 +507,9 @@ def main():
     for k in order:                      # the slowest stage that has a per-pair roofline
         roof = roofline(names[k])
         if roof is not None:
-            roof["stage_share"] = float(per_step[k] / per_step.sum())
+            roof["stage_share"] = float(per_step[k] / per_step.sum())    # the stage's share of the step
+            if "kernel_ms" in roof:                                         # the kernel's own share
+                roof["kernel_share"] = float(roof["kernel_ms"] / per_step.sum())
             break
     stages = {n: float(v) for n, v in zip(names, per_step)}
     for n in ("meanfield", "mc"):
