@@ -29,15 +29,18 @@ The integrator is the classical fourth-order Runge-Kutta method with a fixed ste
 """
 import numpy as np
 
+from .aniso import sbar_factor
 from .rates import A_closed, B_closed
 from .units import MSUN_PER_MP, sigma_kpc2, varsigma2_kms2
 
 
-def params(m_chi, m_B, rho_chi, rho_B, sigma0_cm2, n, v0_kms=100.0):
-    """Constants of the ODE in code units (kpc, km/s, Msun; masses in m_p)."""
+def params(m_chi, m_B, rho_chi, rho_B, sigma0_cm2, n, v0_kms=100.0, beta=0.0):
+    """Constants of the ODE in code units (kpc, km/s, Msun; masses in m_p).  The moment
+    equations take the momentum-transfer cross section: sigma0 (1 - beta / 3) for
+    dsigma/dOmega proportional to 1 + beta cos theta (oracle/aniso.py)."""
     ratio = MSUN_PER_MP
     return dict(m_chi=float(m_chi), m_B=float(m_B), n=int(n), v0=float(v0_kms),
-                sigma0=sigma_kpc2(float(sigma0_cm2)),
+                sigma0=sigma_kpc2(float(sigma0_cm2)) * sbar_factor(beta),
                 F_chi=float(rho_chi) * ratio / (m_chi + m_B), F_B=float(rho_B) * ratio / (m_chi + m_B),
                 rho_chi=float(rho_chi), rho_B=float(rho_B))
 

@@ -5,7 +5,9 @@ Eq. dm-update-vels: the new velocity distribution of DM particle i is
 Eq. dm-update-prob:  P_ij = (M_j / mu_j) g_ij sigma(v_rel) v_rel dt,  v_rel = |v_i - v^B_ij|
 with v^B_ij one sample of the gas Maxwellian G(v - V_j, T_j/mu_j) per pair, and
 Eq. scatter_chi:     S_chi = v_i + mu_j/(m_chi + mu_j) v_rel (n' - n),  n = (v_i - v^B)/v_rel,
-n' isotropic (Sec. 2.4: isotropic power-law cross section).
+n' isotropic (Sec. 2.4: isotropic power-law cross section), or, with params["beta"] != 0,
+drawn from dsigma/dOmega proportional to 1 + beta cos theta about n (oracle/aniso.py); P_ij
+keeps the total cross section sigma.
 
 Readings (the paper leaves these open):
   * one categorical draw per DM particle per step (the derivation's form); partners
@@ -23,6 +25,7 @@ the expectation values of App. C (tests/test_oracle_mc.py).
 import numpy as np
 
 from . import units
+from .aniso import new_direction
 from .kernel import overlap_g_vec
 from .meanfield import pair_geometry
 from .philox import bern_uniforms, dm_uniforms, pair_normals
@@ -87,8 +90,7 @@ def mc_scatter(dm, gas, pi, pj, params, step, dt, g=None):
         j = pj[e]
         mu = gas["mu"][j]
         n_old = (dm["vel"][i] - vB[e]) / vrel[e]
-        sth = np.sqrt(max(0.0, 1.0 - cth[i] * cth[i]))
-        n_new = np.array([sth * np.cos(phi[i]), sth * np.sin(phi[i]), cth[i]])
+        n_new = new_direction(n_old, cth[i], phi[i], params.get("beta", 0.0))
         vel_new[i] = dm["vel"][i] + mu / (m_chi + mu) * vrel[e] * (n_new - n_old)
         scattered[i] = True
         partner[i] = gas["id"][j]
@@ -150,8 +152,7 @@ def mc_scatter_bernoulli(dm, gas, pi, pj, params, step, dt, g=None, max_scatters
             if r[e] < P:
                 j = pj[e]
                 mu = gas["mu"][j]
-                sth = np.sqrt(max(0.0, 1.0 - cth[e] * cth[e]))
-                n_new = np.array([sth * np.cos(phi[e]), sth * np.sin(phi[e]), cth[e]])
+                n_new = new_direction(rel / vr, cth[e], phi[e], params.get("beta", 0.0))
                 v = v + mu / (m_chi + mu) * vr * (n_new - rel / vr)
                 if not scattered[i]:
                     scattered[i] = True

@@ -15,6 +15,7 @@ identities checked in tests/test_oracle_step.py.
 import numpy as np
 
 from . import units
+from .aniso import sbar_factor
 from .kernel import overlap_g_vec
 from .pairs import min_image
 from .rates import A_closed_arr, B_closed_arr
@@ -36,7 +37,8 @@ def pair_rates(dm, gas, pi, pj, params, g=None):
     w = dm["vel"][pi] - gas["vel"][pj]
     wn = np.sqrt(np.sum(w * w, axis=1))
     s2 = units.varsigma2_kms2(gas["T"][pj], gas["mu"][pj])
-    sig0 = units.sigma_kpc2(params["sigma0_cm2"])
+    # the exchange rates take the momentum-transfer cross section (oracle/aniso.py)
+    sig0 = units.sigma_kpc2(params["sigma0_cm2"]) * sbar_factor(params.get("beta", 0.0))
     A = A_closed_arr(wn, s2, sig0, params["v0_kms"], params["n"])
     B = B_closed_arr(wn, s2, sig0, params["v0_kms"], params["n"])
     return g, w, A, B
