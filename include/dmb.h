@@ -213,6 +213,20 @@ dmb_status dmb_set_bins(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas_
  * after all kicks.  DMB_ERR_ARG for other values.  Drops captured substep graphs. */
 dmb_status dmb_set_mc_variant(dmb_ctx *ctx, int32_t variant);
 
+/* Anisotropic scattering (Sec. 2.4: the Monte Carlo's probability takes the total cross
+ * section sigma, the gas exchange rates the momentum-transfer cross section sigma_bar; the
+ * power-law runs are isotropic, sigma = sigma_bar).  Sets dsigma/dOmega = sigma(v) (1 + beta
+ * cos theta) / (4 pi), theta the angle between the relative velocity before and after the
+ * collision: the Monte Carlo (both variants) keeps P_ij with sigma and draws cos theta from the
+ * density (1 + beta m) / 2 about the incoming relative velocity (the step's isotropic cosine
+ * word mapped through the inverse cumulative distribution, the azimuth word about an
+ * orthonormal basis of that direction); the mean field, the expected DM energy change and the
+ * gas coefficients take sigma_bar = sigma (1 - beta / 3) (<cos theta> = beta / 3).  beta = 0
+ * (the default) is the isotropic step unchanged.  beta in [-1, 1] (dsigma/dOmega >= 0),
+ * DMB_ERR_ARG otherwise.  A change drops the grid, the pair lists, the substep tables and the
+ * captured graphs (dmb_set_bins again before dmb_substep); dmb_step rebuilds the rest. */
+dmb_status dmb_set_anisotropy(dmb_ctx *ctx, double beta);
+
 /* Timestep feedback (Sec. 2.5, Eq. prob_criterion: a dark-matter particle whose P_ij is too
  * large takes a smaller timestep next).  p_ratio_max: device float [n], max_j P_ij / min(0.1,
  * 1e-4 ((m_chi + mu_j) / mu_j)^2) of each particle at its current dt_i = 2^bin dt_min, as

@@ -95,8 +95,9 @@ def diagnostics(dm, gas, m_chi):
 
 
 def run(name, t_end=1.0, dt=1e-3, snap=50, rate_mode=dmb.DMB_RATE_CLOSED, L=1.0, mu=1.0, seed=W.SEED_BASE + 900,
-        rng_seed=7):
-    """Step a row from t = 0 to t_end; returns the snapshot series and the timing."""
+        rng_seed=7, beta=0.0):
+    """Step a row from t = 0 to t_end; returns the snapshot series and the timing.  beta != 0
+    makes the scattering anisotropic, dsigma/dOmega ~ 1 + beta cos theta (dmb_set_anisotropy)."""
     import torch
     w = setup(name, L, mu, seed)
     prm = w["params"]
@@ -105,6 +106,8 @@ def run(name, t_end=1.0, dt=1e-3, snap=50, rate_mode=dmb.DMB_RATE_CLOSED, L=1.0,
                       rate_mode=rate_mode, stream=stream)
     if rate_mode == dmb.DMB_RATE_MLP:
         ctx.dmb_train_surrogate(nsamples=1 << 20, epochs=24, seed=11)
+    if beta != 0.0:
+        ctx.dmb_set_anisotropy(beta)
     dm, gas = dmb.to_device(w["dm"]), dmb.to_device(w["gas"])
     nsteps = int(round(t_end / dt))
     snaps, times, scat = [], [], 0
@@ -138,6 +141,6 @@ def run(name, t_end=1.0, dt=1e-3, snap=50, rate_mode=dmb.DMB_RATE_CLOSED, L=1.0,
     series["t"] = np.array(times)
     budget = dict(dE_chi=budget[0], dE_gas=budget[1], dE_chi_expected=budget[2], scatters=budget[3],
                   scatters_expected=budget[4])
-    return dict(row=w["row"], series=series, steps=nsteps, dt=dt, scatters=scat, budget=budget,
+    return dict(row=dict(w["row"], beta=beta), series=series, steps=nsteps, dt=dt, scatters=scat, budget=budget,
                 ms_per_step=gpu_ms / nsteps,
                 wall_s=wall, n_pairs=int(s[12]), rho=(snaps[0]["rho_chi"] / L ** 3, snaps[0]["rho_B"] / L ** 3))

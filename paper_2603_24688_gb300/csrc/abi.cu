@@ -106,6 +106,7 @@ struct dmb_ctx {
   };
   bool use_graph = false;
   int mc_variant = 0;             // dmb_set_mc_variant
+  double mc_beta = 0.0;           // dmb_set_anisotropy
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
   std::vector<GraphEntry> graphs;
@@ -595,6 +596,7 @@ dmb_status mc_impl(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, uint
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for MC partials");
   McArgs a;
   a.variant = ctx->mc_variant;
+  a.beta = ctx->mc_beta;
   a.dt = dt;
   a.step = step;
   a.seed = ctx->p.seed;
@@ -756,6 +758,7 @@ dmb_status substep_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int 
   const int nb = mc_blocks_for(nda);
   McArgs a;
   a.variant = ctx->mc_variant;
+  a.beta = ctx->mc_beta;
   a.dt = dt_min;
   a.step = substep;
   a.seed = ctx->p.seed;
@@ -1182,6 +1185,19 @@ dmb_status dmb_set_mc_variant(dmb_ctx *ctx, int32_t variant) {
   if (variant != 0 && variant != 1) return fail(ctx, DMB_ERR_ARG, "variant must be 0 or 1");
   if (variant != ctx->mc_variant) clear_graphs(ctx);   // captured substeps hold the old kernel
   ctx->mc_variant = variant;
+  return DMB_OK;
+}
+
+dmb_status dmb_set_anisotropy(dmb_ctx *ctx, double beta) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!(beta >= -1.0 && beta <= 1.0)) return fail(ctx, DMB_ERR_ARG, "beta must lie in [-1, 1]");
+  if (beta != ctx->mc_beta) {
+    invalidate_substeps(ctx);      // substep tables and captured graphs hold the old constants
+    ctx->grid_ready = false;       // the gas coefficients of the sorted copy carry sigma_bar
+    ctx->pairs_ready = false;
+  }
+  ctx->mc_beta = beta;
+  ctx->rc.sbar = 1.0 - beta / 3.0;
   return DMB_OK;
 }
 

@@ -22,6 +22,9 @@ struct RunConst {
   double kT_over_mp; // k_B / m_p in (km/s)^2 / K
   int n;
   int rate_mode;     // dmb_rate_mode
+  // sigma_bar / sigma: the gas exchange rates take the momentum-transfer cross section,
+  // 1 - beta / 3 for dsigma/dOmega proportional to 1 + beta cos theta (1 when isotropic)
+  double sbar = 1.0;
 };
 
 // Per-gas coefficients of the sorted copy K = (cA, cB, kP0, e) from varsigma (km/s), the gas
@@ -42,11 +45,11 @@ __host__ __device__ inline void gas_coeffs(const RunConst &rc, double sig, doubl
       b *= b;
     }
     if (rc.n < 0) sn = 1.0 / sn;
-    const double t = rc.S * rc.alpha * sn * sig * inv_mpm;
+    const double t = rc.S * rc.sbar * rc.alpha * sn * sig * inv_mpm;
     cA = t / 3.0;
     cB = t * sig * sig * e;
   } else {  // cold gas: A = sigma(w) w, B = sigma(w) w^3
-    cA = rc.S * inv_mpm;
+    cA = rc.S * rc.sbar * inv_mpm;
     cB = cA * e;
   }
   kP0 = M / mu * rc.S;                                         // (M_j / mu_j) sigma0 Msun/m_p

@@ -328,6 +328,7 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
   const int64_t nwarps = (int64_t)gridDim.x * MC_WARPS;
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
   const R inv_v0 = (R)(1.0 / rc.v0);
+  const R beta = (R)a.beta;                          // dsigma/dOmega ~ 1 + beta cos theta
   const unsigned long long step = a.step_dev ? *a.step_dev : a.step;
   const int64_t nrows = a.list ? a.n_list : D.n;
   const R dt0 = (R)a.dt;
@@ -428,9 +429,18 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
           else { double s_, c_; sincospi(2.0 * uniform23<double>(wd.z), &s_, &c_); sp = (R)s_; cp = (R)c_; }
           const R f = Kj.w * vr;                             // mu_j/(m_chi + mu_j) v_rel
           const R inv = (R)1 / vr;
-          dv0 = f * (st * cp - rx * inv);
-          dv1 = f * (st * sp - ry * inv);
-          dv2 = f * (ct - rz * inv);
+          if (beta == (R)0) {
+            dv0 = f * (st * cp - rx * inv);
+            dv1 = f * (st * sp - ry * inv);
+            dv2 = f * (ct - rz * inv);
+          } else {                                           // anisotropic: about the incoming direction
+            const R ux = rx * inv, uy = ry * inv, uz = rz * inv;
+            R nx, ny, nz;
+            aniso_direction<R>(ct, sp, cp, beta, ux, uy, uz, nx, ny, nz);
+            dv0 = f * (nx - ux);
+            dv1 = f * (ny - uy);
+            dv2 = f * (nz - uz);
+          }
           partner_id = prefix;
         }
       }
@@ -484,6 +494,7 @@ k_mc_bernoulli(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *_
   const int64_t nwarps = (int64_t)gridDim.x * MC_WARPS;
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
   const R inv_v0 = (R)(1.0 / rc.v0);
+  const R beta = (R)a.beta;                          // dsigma/dOmega ~ 1 + beta cos theta
   const unsigned long long step = a.step_dev ? *a.step_dev : a.step;
   const int64_t nrows = a.list ? a.n_list : D.n;
   const R dt0 = (R)a.dt;
@@ -560,7 +571,19 @@ k_mc_bernoulli(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *_
           else { double s_, c_; sincospi(2.0 * uniform23<double>(wb.z), &s_, &c_); sp = (R)s_; cp = (R)c_; }
           const R f = Kj.w * vr;                             // mu_j/(m_chi + mu_j) v_rel
           const R inv = (R)1 / vr;
-          const R d0 = f * (st * cp - rx * inv), d1 = f * (st * sp - ry * inv), d2 = f * (ct - rz * inv);
+          R d0, d1, d2;
+          if (beta == (R)0) {
+            d0 = f * (st * cp - rx * inv);
+            d1 = f * (st * sp - ry * inv);
+            d2 = f * (ct - rz * inv);
+          } else {                                           // anisotropic: about the incoming direction
+            const R ux = rx * inv, uy = ry * inv, uz = rz * inv;
+            R nx, ny, nz;
+            aniso_direction<R>(ct, sp, cp, beta, ux, uy, uz, nx, ny, nz);
+            d0 = f * (nx - ux);
+            d1 = f * (ny - uy);
+            d2 = f * (nz - uz);
+          }
           Vc.x += d0; Vc.y += d1; Vc.z += d2;
           dv0 += d0; dv1 += d1; dv2 += d2;
         }

@@ -112,6 +112,8 @@ struct McArgs {
   int v_sorted_fp64 = 0;
   // 0: one categorical draw per DM particle; 1: the per-pair Bernoulli variant (k_mc_bernoulli)
   int variant = 0;
+  // dsigma/dOmega proportional to 1 + beta cos theta (0: isotropic)
+  double beta = 0.0;
 };
 
 // Sets the surrogate pass's shared-memory attribute (done before any graph capture).

@@ -414,3 +414,35 @@ __device__ __forceinline__ void rates_quad(R x, int n, R alpha, R &FA, R &FB) {
     FB = (R)1;
   }
 }
+
+// Post-collision direction of the relative velocity for dsigma/dOmega proportional to
+// 1 + beta cos theta (Sec. 2.4), beta != 0; (rx, ry, rz) is the unit incoming direction, c the
+// step's isotropic cosine (2u - 1) and (sp, cp) its azimuth.  cos theta = m has the density
+// (1 + beta m) / 2, whose cumulative distribution F(m) = (1 + m) [(1 - beta) + beta (1 + m) / 2] / 2
+// = 1 - (1 - m) [(1 + beta) - beta (1 - m) / 2] / 2 is solved for both distances to the poles
+// without cancellation:
+//   1 + m = 2 (1 + c) / ((1 - beta) + sqrt(D)),   1 - m = 2 (1 - c) / ((1 + beta) + sqrt(D)),
+// D = 1 + beta^2 + 2 beta c, formed as (1 - beta)^2 + 2 beta (1 + c) for beta > 0 and as
+// (1 + beta)^2 - 2 beta (1 - c) for beta < 0 (sums of non-negative terms), so that
+// sin theta = sqrt((1 + m)(1 - m)) keeps its relative precision near |m| = 1 (1 - c and 1 + c
+// are exact for the step's c).  The azimuth is measured in the orthonormal basis of Duff
+// et al. (2017), "Building an orthonormal basis, revisited", JCGT 6(1).  (beta = 0 keeps the
+// fixed-axes isotropic form at the call.)
+template <typename R>
+__device__ __forceinline__ void aniso_direction(R c, R sp, R cp, R beta, R rx, R ry, R rz, R &nx, R &ny, R &nz) {
+  const R bm = (R)1 - beta, bp = (R)1 + beta, cpl = (R)1 + c, cmi = (R)1 - c;
+  const R sD = sqrt_t(beta > (R)0 ? bm * bm + (R)2 * beta * cpl : bp * bp - (R)2 * beta * cmi);
+  const R dp = bm + sD, dq = bp + sD;
+  const R p = dp > (R)0 ? (R)2 * cpl / dp : (R)0;       // 1 + m
+  const R q = dq > (R)0 ? (R)2 * cmi / dq : (R)0;       // 1 - m
+  const R m = (R)0.5 * (p - q);
+  const R st = sqrt_t(p * q);
+  const R s = rz >= (R)0 ? (R)1 : (R)-1;
+  const R a = (R)-1 / (s + rz);
+  const R b = rx * ry * a;
+  const R e1x = (R)1 + s * rx * rx * a, e1y = s * b, e1z = -s * rx;
+  const R e2x = b, e2y = s + ry * ry * a, e2z = -ry;
+  nx = m * rx + st * (cp * e1x + sp * e2x);
+  ny = m * ry + st * (cp * e1y + sp * e2y);
+  nz = m * rz + st * (cp * e1z + sp * e2z);
+}

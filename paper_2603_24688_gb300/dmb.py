@@ -26,7 +26,7 @@ EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb
            "dmb_surrogate_infer", "dmb_surrogate_grad", "dmb_surrogate_fallbacks", "dmb_step_batched",
            "dmb_surrogate_grad_noalloc", "dmb_set_bins", "dmb_substep_info", "dmb_substep", "dmb_set_graph",
            "dmb_set_surrogate_engine", "dmb_surrogate_infer_tc", "dmb_autotune", "dmb_set_shapes",
-           "dmb_get_shapes", "dmb_rebin_dm", "dmb_set_mc_variant"]
+           "dmb_get_shapes", "dmb_rebin_dm", "dmb_set_mc_variant", "dmb_set_anisotropy"]
 
 
 class DmbError(RuntimeError):
@@ -104,6 +104,7 @@ def load(path=LIB_PATH):
         "dmb_get_shapes": ([vp, c.POINTER(c.c_int32)], c.c_int),
         "dmb_rebin_dm": ([vp, vp, vp, i64, c.c_int32, u64, vp, c.POINTER(i64)], c.c_int),
         "dmb_set_mc_variant": ([vp, c.c_int32], c.c_int),
+        "dmb_set_anisotropy": ([vp, c.c_double], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -302,6 +303,10 @@ class Context:
     def dmb_set_mc_variant(self, variant):
         """0: one categorical draw per DM particle (default); 1: per-pair Bernoulli draws."""
         self._check(self.lib.dmb_set_mc_variant(self.h, int(variant)))
+
+    def dmb_set_anisotropy(self, beta):
+        """dsigma/dOmega proportional to 1 + beta cos theta, beta in [-1, 1] (0: isotropic)."""
+        self._check(self.lib.dmb_set_anisotropy(self.h, float(beta)))
 
     def dmb_set_graph(self, on=True):
         self._check(self.lib.dmb_set_graph(self.h, 1 if on else 0))
