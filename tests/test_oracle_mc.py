@@ -130,12 +130,14 @@ def test_partner_choice_follows_probabilities():
     assert stats.chi2.sf(chi2, 3) > 1e-4
 
 
-@pytest.mark.parametrize("n", [0, -2])
-def test_bernoulli_variant_mean_matches_expectation(n):
+@pytest.mark.parametrize("n,beta", [(0, 0.0), (-2, 0.0), (0, 0.9)])
+def test_bernoulli_variant_mean_matches_expectation(n, beta):
     # the per-pair Bernoulli form has the same expectation (App. C) as the categorical draw to
-    # first order in P (a scatter changes the later probabilities only at second order)
+    # first order in P (a scatter changes the later probabilities only at second order); with
+    # anisotropic angles (beta != 0) the expectation takes sigma_bar = sigma (1 - beta / 3)
     w = _small_box(n)
-    dm, gas, prm, dt = w["dm"], w["gas"], w["params"], w["dt"]
+    dm, gas, dt = w["dm"], w["gas"], w["dt"]
+    prm = dict(w["params"], beta=beta)
     pi, pj = pairs_bruteforce(dm, gas, True, prm["box"])
     d = pair_geometry(dm, gas, pi, pj, True, prm["box"])
     g = overlap_g_vec(d, dm["h"][pi], gas["h"][pj])
