@@ -149,7 +149,7 @@ def boxes_workload(nbox=64, n_lo=2 ** 12, n_hi=2 ** 18, sigma_lo=1e-27, sigma_hi
                    T_lo=1e3, T_hi=1e6, L=1.0, rho=1e10, sigma1d_dm=100.0, n=0, v0_kms=100.0, dt=1e-4,
                    seed=SEED_BASE + 4):
     """Many independent periodic boxes: particle counts per species, sigma0, m_chi and the gas
-    temperature drawn log-uniformly per box (the survey's parameter scan).  Returns the boxes'
+    temperature drawn log-uniformly per box (a parameter scan over boxes).  Returns the boxes'
     particles concatenated (with per-particle box indices), the per-box parameters and each
     box's own workload dict."""
     rng = np.random.default_rng(seed)
