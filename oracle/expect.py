@@ -17,6 +17,7 @@ import numpy as np
 from . import units
 from .meanfield import pair_rates
 from .rates import R_closed_arr
+from .xsec import R_arr, family
 
 
 def expected_dm(dm, gas, pi, pj, params, dt, g=None):
@@ -36,10 +37,13 @@ def expected_dm(dm, gas, pi, pj, params, dt, g=None):
         np.add.at(E_dv[:, c], pi[order], dv_terms[order, c])
     np.add.at(E_dE, pi[order], dE_terms[order])
     E_P = np.full(nd, np.nan)
-    if params["n"] > -4:
+    if family(params) != "powerlaw" or params["n"] > -4:
         s2 = units.varsigma2_kms2(gas["T"][pj], gas["mu"][pj])
         wn = np.sqrt(np.sum(w * w, axis=1))
-        R = R_closed_arr(wn, s2, units.sigma_kpc2(params["sigma0_cm2"]), params["v0_kms"], params["n"])
+        if family(params) != "powerlaw":
+            R = R_arr(wn, s2, params)
+        else:
+            R = R_closed_arr(wn, s2, units.sigma_kpc2(params["sigma0_cm2"]), params["v0_kms"], params["n"])
         nB = gas["mass"][pj] * units.MSUN_PER_MP / mu
         E_P = np.zeros(nd)
         np.add.at(E_P, pi[order], (nB * g * R * dt)[order])

@@ -30,16 +30,23 @@ The integrator is the classical fourth-order Runge-Kutta method with a fixed ste
 import numpy as np
 
 from .aniso import sbar_factor
-from .rates import A_closed, B_closed
+from .rates import A_closed, A_quad, B_closed, B_quad
 from .units import MSUN_PER_MP, sigma_kpc2, varsigma2_kms2
+from .xsec import sigma_bar_of_v
 
 
-def params(m_chi, m_B, rho_chi, rho_B, sigma0_cm2, n, v0_kms=100.0, beta=0.0):
+def params(m_chi, m_B, rho_chi, rho_B, sigma0_cm2, n, v0_kms=100.0, beta=0.0, v_c_kms=None):
     """Constants of the ODE in code units (kpc, km/s, Msun; masses in m_p).  The moment
     equations take the momentum-transfer cross section: sigma0 (1 - beta / 3) for
-    dsigma/dOmega proportional to 1 + beta cos theta (oracle/aniso.py)."""
+    dsigma/dOmega proportional to 1 + beta cos theta (oracle/aniso.py).  v_c_kms selects the
+    screened law sigma0 / (1 + (v / v_c)^2)^2 instead of the power law (oracle/xsec.py); A and
+    B are then taken by quadrature."""
     ratio = MSUN_PER_MP
-    return dict(m_chi=float(m_chi), m_B=float(m_B), n=int(n), v0=float(v0_kms),
+    sbar_fn = None
+    if v_c_kms is not None:
+        xp = dict(xsec="screened", sigma0_cm2=float(sigma0_cm2), v_c_kms=float(v_c_kms), beta=beta)
+        sbar_fn = lambda u: float(sigma_bar_of_v(u, xp))
+    return dict(m_chi=float(m_chi), m_B=float(m_B), n=int(n), v0=float(v0_kms), sbar_fn=sbar_fn,
                 sigma0=sigma_kpc2(float(sigma0_cm2)) * sbar_factor(beta),
                 F_chi=float(rho_chi) * ratio / (m_chi + m_B), F_B=float(rho_B) * ratio / (m_chi + m_B),
                 rho_chi=float(rho_chi), rho_B=float(rho_B))
@@ -59,8 +66,13 @@ def rhs(y, p):
     Vc, Vb, tc, tb = y
     vth2 = tc + tb
     V = abs(Vc - Vb)
-    A = A_closed(V, vth2, p["sigma0"], p["v0"], p["n"])
-    B = B_closed(V, vth2, p["sigma0"], p["v0"], p["n"])
+    if p.get("sbar_fn") is not None:                 # quadrature; V = 0 read at 1e-9 v_th
+        Vq = max(V, 1e-9 * np.sqrt(vth2))
+        A = A_quad(Vq, vth2, p["sbar_fn"])
+        B = B_quad(Vq, vth2, p["sbar_fn"])
+    else:
+        A = A_closed(V, vth2, p["sigma0"], p["v0"], p["n"])
+        B = B_closed(V, vth2, p["sigma0"], p["v0"], p["n"])
     mc, mb = p["m_chi"], p["m_B"]
     dVc = p["F_B"] * A * (Vb - Vc)
     dVb = p["F_chi"] * A * (Vc - Vb)

@@ -29,6 +29,7 @@ from .aniso import new_direction
 from .kernel import overlap_g_vec
 from .meanfield import pair_geometry
 from .philox import bern_uniforms, dm_uniforms, pair_normals
+from .xsec import family, sigma_of_v
 
 NO_PARTNER = 0xFFFFFFFF
 
@@ -48,7 +49,7 @@ def pair_probabilities(dm, gas, pi, pj, params, step, dt, g=None):
     vB = gas["vel"][pj] + s[:, None] * z
     rel = dm["vel"][pi] - vB
     vrel = np.sqrt(np.sum(rel * rel, axis=1))
-    sig = units.sigma_kpc2(params["sigma0_cm2"]) * (vrel / params["v0_kms"]) ** params["n"]
+    sig = sigma_of_v(vrel, params)
     nB = gas["mass"][pj] * units.MSUN_PER_MP / gas["mu"][pj]
     P = nB * g * sig * vrel * dt
     return P, vB, vrel
@@ -132,6 +133,7 @@ def mc_scatter_bernoulli(dm, gas, pi, pj, params, step, dt, g=None, max_scatters
     np.add.at(C_total, pi, P0)
     nB = gas["mass"][pj] * units.MSUN_PER_MP / gas["mu"][pj]
     s0, v0, n = units.sigma_kpc2(params["sigma0_cm2"]), params["v0_kms"], params["n"]
+    powerlaw = family(params) == "powerlaw"
 
     order = np.lexsort((gas["id"][pj], pi))
     starts = np.searchsorted(pi[order], np.arange(nd), side="left")
@@ -146,7 +148,10 @@ def mc_scatter_bernoulli(dm, gas, pi, pj, params, step, dt, g=None, max_scatters
         for e in order[starts[i]:ends[i]]:
             rel = v - vB[e]
             vr = np.sqrt(rel @ rel)
-            P = nB[e] * g[e] * s0 * (vr / v0) ** n * vr * dt
+            if powerlaw:
+                P = nB[e] * g[e] * s0 * (vr / v0) ** n * vr * dt
+            else:
+                P = nB[e] * g[e] * float(sigma_of_v(vr, params)) * vr * dt
             if P > 0:
                 gap[i] = min(gap[i], abs(r[e] - P) / P)
             if r[e] < P:

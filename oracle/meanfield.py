@@ -19,6 +19,7 @@ from .aniso import sbar_factor
 from .kernel import overlap_g_vec
 from .pairs import min_image
 from .rates import A_closed_arr, B_closed_arr
+from .xsec import A_arr, B_arr, family
 
 
 def pair_geometry(dm, gas, pi, pj, periodic, box):
@@ -37,6 +38,8 @@ def pair_rates(dm, gas, pi, pj, params, g=None):
     w = dm["vel"][pi] - gas["vel"][pj]
     wn = np.sqrt(np.sum(w * w, axis=1))
     s2 = units.varsigma2_kms2(gas["T"][pj], gas["mu"][pj])
+    if family(params) != "powerlaw":                # other sigma(v): quadrature (oracle/xsec.py)
+        return g, w, A_arr(wn, s2, params), B_arr(wn, s2, params)
     # the exchange rates take the momentum-transfer cross section (oracle/aniso.py)
     sig0 = units.sigma_kpc2(params["sigma0_cm2"]) * sbar_factor(params.get("beta", 0.0))
     A = A_closed_arr(wn, s2, sig0, params["v0_kms"], params["n"])
