@@ -46,3 +46,19 @@ def test_timestep_bins_keep_every_substep_between_1_and_10_percent():
         frac = np.mean(s % (2.0 ** b) == 0)
         assert 0.009 < frac < 0.102, (s, frac)
     assert np.all(0 % (2.0 ** b) == 0)          # substep 0: everything active
+
+
+def test_setters_refuse_a_null_context_without_touching_a_gpu():
+    import ctypes
+    from paper_2603_24688_gb300 import build, dmb
+    try:
+        build.build()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    lib = dmb.load()
+    lib.dmb_set_anisotropy.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    lib.dmb_set_anisotropy.restype = ctypes.c_int
+    lib.dmb_set_mc_variant.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    lib.dmb_set_mc_variant.restype = ctypes.c_int
+    assert lib.dmb_set_anisotropy(None, 0.5) == dmb.DMB_ERR_ARG
+    assert lib.dmb_set_mc_variant(None, 0) == dmb.DMB_ERR_ARG
