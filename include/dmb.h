@@ -47,7 +47,7 @@ typedef enum {
 
 typedef enum {
   DMB_RATE_CLOSED = 0,  /* App. B closed forms via 1F1 (integer n >= -4, n != -3) */
-  DMB_RATE_QUAD = 1,    /* Gauss-Laguerre/Hermite quadrature of Eqs. scrA/scrB */
+  DMB_RATE_QUAD = 1,    /* composite 8-panel x 8-point Gauss-Legendre quadrature of Eqs. scrA/scrB (App. B) */
   DMB_RATE_MLP = 2      /* learned surrogate of the rate integrals (float32 only; train or load first) */
 } dmb_rate_mode;
 
@@ -227,6 +227,27 @@ dmb_status dmb_set_mc_variant(dmb_ctx *ctx, int32_t variant);
  * captured graphs (dmb_set_bins again before dmb_substep); dmb_step rebuilds the rest. */
 dmb_status dmb_set_anisotropy(dmb_ctx *ctx, double beta);
 
+/* Velocity law of the cross section (Sec. 2.4: the method takes any sigma(v) whose A and B can be
+ * computed; the power law has the App. B closed forms).  family 0 (the default): the power law of
+ * the parameters, sigma0 (v / v0)^n.  family 1: the screened law sigma(v) = sigma0 / (1 + (v /
+ * v_c)^2)^2 with v_c_kms > 0 (scattering through a massive mediator: flat below v_c, falling as
+ * v^-4 above it).  With it the Monte Carlo takes sigma(v_rel) in P_ij (Eq. dm-update-prob); the
+ * mean field's A and B come from the device quadrature (DMB_RATE_QUAD: the integrand carries
+ * sigma_bar(u) / sigma0, the window is split where the law's poles come near it) or from a
+ * surrogate trained for this law (DMB_RATE_MLP: dmb_train_surrogate after this call; its second
+ * input is then varsigma^2 / v_c^2); the closed forms exist for the power law only, so
+ * DMB_RATE_CLOSED gives DMB_ERR_ARG.  The rates keep the n = 0 normalisation,
+ * A = (alpha_0 / 3) sigma0 varsigma FA and B = alpha_0 sigma0 varsigma^3 FB, with FA, FB functions
+ * of x and q = varsigma^2 / v_c^2.  Composes with dmb_set_anisotropy (sigma_bar = sigma (1 - beta/3)).
+ * A change drops the grid, the pair lists, the substep tables and the captured graphs, as
+ * dmb_set_anisotropy does.  Other family values or v_c <= 0: DMB_ERR_ARG. */
+dmb_status dmb_set_cross_section(dmb_ctx *ctx, int32_t family, double v_c_kms);
+
+/* Debug/verification: the device quadrature of the screened law (see dmb_set_cross_section) at k
+ * points, in the context's precision.  in: device [k][2] float64 (x = w^2 / (2 varsigma^2),
+ * q = varsigma^2 / v_c^2); out: device [k][2] float64 (FA, FB) of the n = 0 normalisation. */
+dmb_status dmb_debug_rates_screened(dmb_ctx *ctx, int64_t k, const double *in, double *out);
+
 /* Timestep feedback (Sec. 2.5, Eq. prob_criterion: a dark-matter particle whose P_ij is too
  * large takes a smaller timestep next).  p_ratio_max: device float [n], max_j P_ij / min(0.1,
  * 1e-4 ((m_chi + mu_j) / mu_j)^2) of each particle at its current dt_i = 2^bin dt_min, as
@@ -351,9 +372,21 @@ dmb_status dmb_surrogate_fallbacks(dmb_ctx *ctx, int64_t *out);
  * kernels as dmb_surrogate_grad.  The first call on a device looks the array up (setup); make it
  * before any stream capture.  All calls on a device share the array: calls whose work overlaps on
  * the GPU (different streams or contexts without ordering) race and give wrong results.  When
- * loss is non-NULL the call synchronises the context's stream. */
+ * loss is non-NULL the call synchronises the context's stream.  The current CUDA device must be
+ * the one the context was created on (DMB_ERR_STATE otherwise); the array's address is looked up
+ * once per device, so a cudaDeviceReset after the first call is not supported. */
 dmb_status dmb_surrogate_grad_noalloc(dmb_ctx *ctx, const float *X, const float *Y, int32_t B, float *grad,
                                       double *loss);
+
+/* Fault injection for the timeout path of the tensor-core surrogate (failure detection; the
+ * paper has no counterpart).  With on = 1 the next tensor-core surrogate launch of this context
+ * (dmb_surrogate_infer_tc, or the surrogate pass of a mean field) leaves out the completion
+ * commit of one MMA (warpgroup 0 of the first CTA, its first layer-1 MMA) and limits its waits
+ * to 1 ms, so that bounded wait runs out.  The kernel then commits again, waits (bounded) for
+ * the MMAs it has in flight, frees its tensor memory and ends normally; the call that
+ * synchronises on it returns DMB_ERR_TIMEOUT and the context stays usable.  Applies to one
+ * launch; on = 0 cancels it; other values: DMB_ERR_ARG.  No GPU fault is involved. */
+dmb_status dmb_debug_tc_timeout(dmb_ctx *ctx, int32_t on);
 
 /* Number of kernel launches the context has issued since creation (bench accounting). */
 int64_t dmb_launch_count(const dmb_ctx *ctx);

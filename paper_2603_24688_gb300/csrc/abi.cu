@@ -67,12 +67,17 @@ struct dmb_ctx {
   bool mlp_ready = false;
   int mlp_engine = 0;            // 0: tcgen05 tiles (mlp_tc.cu), 1: warp-level mma.sync pass
   DevBuf tc_tiles;               // row of every pair of the surrogate's pass
+  bool tc_skip_commit = false;   // dmb_debug_tc_timeout: inject one timed-out wait into the next launch
+  int device = 0;                // the CUDA device the context was created on
   // batched boxes (dmb_step_batched): caller box index arrays of the current build and tables
   const uint32_t *dm_box = nullptr, *gas_box = nullptr;
   int nbox = 0;
   double stride = 0.0;
   DevBuf box_sides, box_params;
   std::vector<int> mlp_n;        // power-law indices the network was trained for
+  int mlp_family = 0;            // velocity law the network was trained for (0 power, 1 screened)
+  int xsec = 0;                  // dmb_set_cross_section: 0 power law, 1 screened law
+  double v_c = 0.0;              // its v_c, km/s
   double mlp_box[6] = {-2.0, 2.0, -3.0, 2.0, -0.30102999566398120, 1.0};   // log10 ranges of s, tau, m_chi
   int64_t n_seg_max = 0;
   int seg_len = MF_SEG, act_seg_len = MF_SEG;   // segment lengths the two segment tables were built with
@@ -480,6 +485,15 @@ MlpDev mlp_dev(dmb_ctx *ctx) {
   return d;
 }
 
+// whether the loaded network was trained for the context's velocity law (and power-law index)
+bool surrogate_covers(const dmb_ctx *ctx) {
+  if (ctx->mlp_family != ctx->xsec) return false;
+  if (ctx->xsec == 1) return true;
+  bool known = false;
+  for (int k : ctx->mlp_n) known = known || k == ctx->p.n;
+  return known;
+}
+
 MlpRun mlp_run(dmb_ctx *ctx) {
   MlpRun r;
   r.p = ptr<float>(ctx->mlp_p);
@@ -494,14 +508,16 @@ MlpRun mlp_run(dmb_ctx *ctx) {
   d.m_lo = (float)pow(10.0, ctx->mlp_box[4]);
   d.m_hi = (float)pow(10.0, ctx->mlp_box[5]);
   double cA, eA, cB, eB;
-  envelope(ctx->p.n, cA, eA, cB, eB);
+  envelope(ctx->rc.n, cA, eA, cB, eB);
   d.cA = (float)cA;
   d.cB = (float)cB;
   d.eA = (float)eA;
   d.eB = (float)eB;
-  d.inv_v0sq = (float)(1.0 / (ctx->p.v0_kms * ctx->p.v0_kms));
+  // the second input: varsigma^2 / v0^2 for the power law, varsigma^2 / v_c^2 for the screened law
+  d.inv_v0sq = ctx->xsec == 1 ? (float)(1.0 / (ctx->v_c * ctx->v_c)) : (float)(1.0 / (ctx->p.v0_kms * ctx->p.v0_kms));
   d.log_m = (float)log10(ctx->p.m_chi_mp);
-  d.n4 = (float)(0.25 * ctx->p.n);
+  d.n4 = (float)(0.25 * ctx->rc.n);
+  d.scr = ctx->xsec == 1 ? 1 : 0;
   return r;
 }
 
@@ -529,6 +545,8 @@ dmb_status surrogate_rates(dmb_ctx *ctx, const MlpRun &mr, const SegView &sv, co
     a.rates = ptr<float2>(ctx->mlp_rates);
     a.fallback_count = mr.fallback_count;
     a.status = ptr<uint32_t>(ctx->status);
+    a.skip_commit = ctx->tc_skip_commit ? 1 : 0;
+    ctx->tc_skip_commit = false;
     if (!ensure(ctx->tc_tiles, (size_t)n_q * 4)) return fail(ctx, DMB_ERR_OOM, "surrogate pair rows");
     CK(mlp_tc_pair_rates(a, ptr<uint32_t>(ctx->tc_tiles), ctx->shp.tc_wg, s, &ctx->launches),
        "surrogate rates (tensor cores)");
@@ -557,9 +575,8 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
   MlpRun mr = {};
   if (ctx->rc.rate_mode == DMB_RATE_MLP) {
     if (!ctx->mlp_ready) return fail(ctx, DMB_ERR_STATE, "surrogate rate provider selected but no trained network");
-    bool known = false;
-    for (int k : ctx->mlp_n) known = known || k == ctx->p.n;
-    if (!known) return fail(ctx, DMB_ERR_DOMAIN, "the surrogate was not trained for this power-law index");
+    if (!surrogate_covers(ctx))
+      return fail(ctx, DMB_ERR_DOMAIN, "the surrogate was not trained for this cross section (law or power-law index)");
     mr = mlp_run(ctx);
     CK(cudaMemsetAsync(ctx->mlp_fallback.p, 0, 8, ctx->stream), "memset");
     if (!ensure(ctx->mlp_rates, (size_t)ctx->sg.n_pairs * 8 + 8)) return fail(ctx, DMB_ERR_OOM, "surrogate rates");
@@ -865,6 +882,8 @@ bool dmb_internal_surrogate(dmb_ctx *ctx, MlpDev *dev, cudaStream_t *stream) {
   return true;
 }
 
+int dmb_internal_device(const dmb_ctx *ctx) { return ctx ? ctx->device : -1; }
+
 dmb_status dmb_internal_fail(dmb_ctx *ctx, dmb_status s, const char *msg) { return fail(ctx, s, msg); }
 
 // ======================================================================================
@@ -885,8 +904,14 @@ dmb_status dmb_create(dmb_ctx **out, const dmb_params *p, void *cuda_stream) {
   if (p->periodic)
     for (int k = 0; k < 3; ++k)
       if (!(p->box[k] > 0.0) || !isfinite(p->box[k])) return fail(nullptr, DMB_ERR_ARG, "periodic box sides must be > 0");
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, DMB_ERR_CUDA, "no current CUDA device");
+  }
   dmb_ctx *ctx = new dmb_ctx();
   ctx->p = *p;
+  ctx->device = device;
   ctx->stream = (cudaStream_t)cuda_stream;
   const double sig_kpc2 = p->sigma0_cm2 / (kKPC * kKPC);
   ctx->rc.S = sig_kpc2 * (kMSUN / kMP);
@@ -1188,6 +1213,34 @@ dmb_status dmb_set_mc_variant(dmb_ctx *ctx, int32_t variant) {
   return DMB_OK;
 }
 
+dmb_status dmb_set_cross_section(dmb_ctx *ctx, int32_t family, double v_c_kms) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (family != 0 && family != 1) return fail(ctx, DMB_ERR_ARG, "family must be 0 (power law) or 1 (screened law)");
+  if (family == 1 && !(v_c_kms > 0.0 && isfinite(v_c_kms))) return fail(ctx, DMB_ERR_ARG, "v_c must be finite and > 0");
+  if (family == 1 && ctx->rc.rate_mode == DMB_RATE_CLOSED)
+    return fail(ctx, DMB_ERR_ARG, "the closed forms exist for the power law only: use the quadrature or the surrogate");
+  const double vc = family == 1 ? v_c_kms : 0.0;
+  if (family != ctx->xsec || vc != ctx->v_c) {
+    invalidate_substeps(ctx);      // substep tables and captured graphs hold the old constants
+    ctx->grid_ready = false;       // the gas coefficients of the sorted copy carry the normalisation
+    ctx->pairs_ready = false;
+  }
+  ctx->xsec = family;
+  ctx->v_c = vc;
+  ctx->rc.xsec = family;
+  ctx->rc.inv_vc2 = family == 1 ? 1.0 / (vc * vc) : 0.0;
+  ctx->rc.n = family == 1 ? 0 : ctx->p.n;
+  ctx->rc.alpha = alpha_of(ctx->rc.n);
+  return DMB_OK;
+}
+
+dmb_status dmb_debug_rates_screened(dmb_ctx *ctx, int64_t k, const double *in, double *out) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (k < 0 || (k > 0 && (!in || !out))) return fail(ctx, DMB_ERR_ARG, "bad arguments");
+  CK(launch_debug_rates_screened(ctx->p.fp64, alpha_of(0), k, in, out, ctx->stream), "debug rates (screened)");
+  return DMB_OK;
+}
+
 dmb_status dmb_set_anisotropy(dmb_ctx *ctx, double beta) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
   if (!(beta >= -1.0 && beta <= 1.0)) return fail(ctx, DMB_ERR_ARG, "beta must lie in [-1, 1]");
@@ -1217,9 +1270,8 @@ dmb_status dmb_substep(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint6
   if (!(dt_min >= 0.0) || !isfinite(dt_min)) return fail(ctx, DMB_ERR_ARG, "dt_min must be finite and >= 0");
   if (ctx->rc.rate_mode == DMB_RATE_MLP) {
     if (!ctx->mlp_ready) return fail(ctx, DMB_ERR_STATE, "surrogate rate provider selected but no trained network");
-    bool known = false;
-    for (int k : ctx->mlp_n) known = known || k == ctx->p.n;
-    if (!known) return fail(ctx, DMB_ERR_DOMAIN, "the surrogate was not trained for this power-law index");
+    if (!surrogate_covers(ctx))
+      return fail(ctx, DMB_ERR_DOMAIN, "the surrogate was not trained for this cross section (law or power-law index)");
   }
   const int lim = substep_lim(substep);
   if (ctx->use_graph) {
@@ -1427,8 +1479,11 @@ dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, u
   spec.log_s_lo = ctx->mlp_box[0]; spec.log_s_hi = ctx->mlp_box[1];
   spec.log_tau_lo = ctx->mlp_box[2]; spec.log_tau_hi = ctx->mlp_box[3];
   spec.log_m_lo = ctx->mlp_box[4]; spec.log_m_hi = ctx->mlp_box[5];
+  // the screened law has one normalisation (n = 0) and takes tau as varsigma^2 / v_c^2
   std::vector<int> ns = {-4, -2, 0, 2};
   if (std::find(ns.begin(), ns.end(), ctx->p.n) == ns.end()) ns.push_back(ctx->p.n);
+  if (ctx->xsec == 1) ns = {0};
+  spec.scr = ctx->xsec == 1 ? 1 : 0;
   spec.n_count = (int)ns.size();
   for (int k = 0; k < spec.n_count; ++k) {
     spec.n_values[k] = ns[k];
@@ -1506,6 +1561,7 @@ dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, u
   }
   ctx->mlp_ready = true;
   ctx->mlp_n = ns;
+  ctx->mlp_family = ctx->xsec;
   if (report) {
     report[0] = lsum / ((double)B * MLP_OUT);
     report[1] = mxA;
@@ -1541,6 +1597,7 @@ dmb_status dmb_load_surrogate(dmb_ctx *ctx, const float *host_params, int64_t co
   ctx->mlp_ready = true;
   ctx->mlp_n = {-4, -2, 0, 2};
   if (std::find(ctx->mlp_n.begin(), ctx->mlp_n.end(), ctx->p.n) == ctx->mlp_n.end()) ctx->mlp_n.push_back(ctx->p.n);
+  ctx->mlp_family = ctx->xsec;   // a loaded block is taken as a network of the current velocity law
   return DMB_OK;
 }
 
@@ -1608,8 +1665,17 @@ dmb_status dmb_surrogate_infer_tc(dmb_ctx *ctx, const float *X, int64_t n, float
   a.X = X;
   a.Y = Y;
   a.status = ptr<uint32_t>(ctx->status);
+  a.skip_commit = ctx->tc_skip_commit ? 1 : 0;
+  ctx->tc_skip_commit = false;
   CK(mlp_tc_infer(a, ctx->shp.tc_wg, ctx->stream, &ctx->launches), "surrogate inference (tensor cores)");
   return check_status(ctx);
+}
+
+dmb_status dmb_debug_tc_timeout(dmb_ctx *ctx, int32_t on) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (on != 0 && on != 1) return fail(ctx, DMB_ERR_ARG, "on must be 0 or 1");
+  ctx->tc_skip_commit = on == 1;
+  return DMB_OK;
 }
 
 dmb_status dmb_surrogate_fallbacks(dmb_ctx *ctx, int64_t *out) {

@@ -25,6 +25,12 @@ struct RunConst {
   // sigma_bar / sigma: the gas exchange rates take the momentum-transfer cross section,
   // 1 - beta / 3 for dsigma/dOmega proportional to 1 + beta cos theta (1 when isotropic)
   double sbar = 1.0;
+  // velocity law of sigma: 0 the power law sigma0 (v / v0)^n; 1 the screened law
+  // sigma0 / (1 + (v / v_c)^2)^2, whose runs carry n = 0 and alpha = alpha_0 (the App. B
+  // normalisation of the n = 0 closed forms), so that FA, FB become functions of x and
+  // varsigma^2 / v_c^2 and the gas coefficients keep their n = 0 form
+  int xsec = 0;
+  double inv_vc2 = 0.0;   // 1 / v_c^2, (km/s)^-2 (0 for the power law)
 };
 
 // Per-gas coefficients of the sorted copy K = (cA, cB, kP0, e) from varsigma (km/s), the gas

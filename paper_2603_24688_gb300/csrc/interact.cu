@@ -22,6 +22,7 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
   const unsigned lane = threadIdx.x & 31u;
   const int64_t nwarps = (int64_t)gridDim.x * MF_WARPS;
   const R inv_v0 = (R)(1.0 / rc.v0);
+  const R inv_vc2 = (R)rc.inv_vc2;
   const R alpha = (R)rc.alpha;
   const int64_t n_seg = sv.n_seg >= 0 ? sv.n_seg : sv.seg_ptr[G.n];
   for (int64_t u = (int64_t)blockIdx.x * MF_WARPS + (threadIdx.x >> 5); u < n_seg; u += nwarps) {
@@ -34,6 +35,7 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
       const R sig = Vj.w;
       const bool hot = sig > (R)0;
       const R inv2s2 = hot ? (R)0.5 / (sig * sig) : (R)0;
+      const R qv = sig * sig * inv_vc2;                 // varsigma^2 / v_c^2 (screened law)
       // warp-uniform trip count (the surrogate's tensor-core layers need all 32 lanes)
       // each pass loads the next pass's partner index ahead of its own gathers
       uint32_t i_next = rows[rs + lane < re ? rs + lane : rs];
@@ -52,7 +54,7 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
         R FA, FB;
         if (hot) {
           if (RM == DMB_RATE_QUAD) {
-            rates_quad<R>(w2 * inv2s2, rc.n, alpha, FA, FB);
+            rates_quad<R>(w2 * inv2s2, rc.n, alpha, FA, FB, qv);
           } else if (RM == DMB_RATE_MLP) {
             const float2 fr = mr.rates[valid ? p : rs];    // from k_mlp_pair_rates
             FA = (R)fr.x;
@@ -62,7 +64,7 @@ k_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *__re
           }
         } else {
           const R wn = sqrt_t(w2);
-          const R sn = ipow<R>(wn * inv_v0, rc.n);
+          const R sn = sigma_ratio<R>(wn, rc.n, inv_v0, inv_vc2);
           FA = sn * wn;
           FB = sn * wn * w2;
         }
@@ -179,9 +181,9 @@ k_mlp_pair_rates(SpeciesView<float> G, SpeciesView<float> D, const int64_t *__re
       if (valid) {
         float FA, FB;
         if (in_dom) {
-          mlp_outputs(mr.dom, s2, yr, FA, FB);
+          mlp_outputs(mr.dom, s2, sig2, yr, FA, FB);
         } else {
-          rates_quad<float>(0.5f * s2, rc.n, alpha, FA, FB);
+          rates_quad<float>(0.5f * s2, rc.n, alpha, FA, FB, sig2 * (float)rc.inv_vc2);
           ++fallback;
         }
         rates[p] = make_float2(FA, FB);
@@ -284,8 +286,8 @@ __device__ __forceinline__ R pair_probability(const typename Vec<R>::v4 &Pi, con
                                               const typename Vec<R>::v4 &Pj, const typename Vec<R>::v4 &Lj,
                                               const typename Vec<R>::v4 &Vj, const typename Vec<R>::v4 &Kj,
                                               uint32_t id_j, int periodic, const BoxSide &side, const float4 *gtab,
-                                              int n, R inv_v0, R dt, unsigned long long step, uint32_t k0,
-                                              uint32_t k1, R &rx, R &ry, R &rz, R &vrel) {
+                                              int n, R inv_v0, R inv_vc2, R dt, unsigned long long step,
+                                              uint32_t k0, uint32_t k1, R &rx, R &ry, R &rz, R &vrel) {
   R dx, dy, dz;
   pair_dx<R>(Pi, Li, Pj, Lj, periodic, side, dx, dy, dz);
   const R d = sqrt_pair(dist2_rn<R>(dx, dy, dz));
@@ -298,7 +300,7 @@ __device__ __forceinline__ R pair_probability(const typename Vec<R>::v4 &Pi, con
   ry = Vi.y - (Vj.y + sig * z1);
   rz = Vi.z - (Vj.z + sig * z2);
   vrel = sqrt_pair(rx * rx + ry * ry + rz * rz);
-  return Kj.z * dt * g * ipow<R>(vrel * inv_v0, n) * vrel;
+  return Kj.z * dt * g * sigma_ratio<R>(vrel, n, inv_v0, inv_vc2) * vrel;
 }
 
 // U128 comparison helpers for the decision band: |a - b| <= c 2^-20 (about 1e-6 c)
@@ -328,6 +330,7 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
   const int64_t nwarps = (int64_t)gridDim.x * MC_WARPS;
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
   const R inv_v0 = (R)(1.0 / rc.v0);
+  const R inv_vc2 = (R)rc.inv_vc2;
   const R beta = (R)a.beta;                          // dsigma/dOmega ~ 1 + beta cos theta
   const unsigned long long step = a.step_dev ? *a.step_dev : a.step;
   const int64_t nrows = a.list ? a.n_list : D.n;
@@ -369,7 +372,7 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
         const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
         R rx, ry, rz, vr;
         const R P = pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0,
-                                        dt, step, k0, k1, rx, ry, rz, vr);
+                                        inv_vc2, dt, step, k0, k1, rx, ry, rz, vr);
         pcache[p] = P;
         sum = u128_add(sum, to_fixed(P));
         const R e = Kj.w;                                   // mu_j / (m_chi + mu_j)
@@ -417,7 +420,7 @@ k_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *__restrict_
           const uint32_t j = rows[pstar];
           const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
           R rx, ry, rz, vr;
-          (void)pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0, dt,
+          (void)pair_probability<R>(Pi, Li, Vi, id_i, Pj, Lj, Vj, Kj, G.id[j], GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0, inv_vc2, dt,
                                     step, k0, k1, rx, ry, rz, vr);
           const U128 hi = u128_add(base, to_fixed(pcache[pstar]));
           band = band || near_rel(T, base, hi) || near_rel(T, hi, hi);
@@ -494,6 +497,7 @@ k_mc_bernoulli(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *_
   const int64_t nwarps = (int64_t)gridDim.x * MC_WARPS;
   const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
   const R inv_v0 = (R)(1.0 / rc.v0);
+  const R inv_vc2 = (R)rc.inv_vc2;
   const R beta = (R)a.beta;                          // dsigma/dOmega ~ 1 + beta cos theta
   const unsigned long long step = a.step_dev ? *a.step_dev : a.step;
   const int64_t nrows = a.list ? a.n_list : D.n;
@@ -532,7 +536,7 @@ k_mc_bernoulli(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *_
         const uint32_t idj = G.id[j];
         R rx, ry, rz, vr;
         const R P = pair_probability<R>(Pi, Li, Vc, id_i, Pj, Lj, Vj, Kj, idj, GEOM != GEOM_OPEN, side, gtab, rc.n,
-                                        inv_v0, dt, step, k0, k1, rx, ry, rz, vr);
+                                        inv_v0, inv_vc2, dt, step, k0, k1, rx, ry, rz, vr);
         sum = u128_add(sum, to_fixed(P));
         const R e = Kj.w;
         // Eq. prob_criterion: 1 / min(0.1, 1e-4 / e^2) = max(10, 1e4 e^2), no division
@@ -562,7 +566,7 @@ k_mc_bernoulli(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *_
           const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
           R rx, ry, rz, vr;
           (void)pair_probability<R>(Pi, Li, Vc, id_i, Pj, Lj, Vj, Kj, hit, GEOM != GEOM_OPEN, side, gtab, rc.n, inv_v0,
-                                    dt, step, k0, k1, rx, ry, rz, vr);
+                                    inv_vc2, dt, step, k0, k1, rx, ry, rz, vr);
           const uint4 wb = philox4x32_10(bern_counter(id_i, hit, step), k0, k1);
           const R ct = (R)2 * uniform23<R>(wb.y) - (R)1;
           const R st = sqrt_t(fmax((R)0, (R)1 - ct * ct));
@@ -596,7 +600,7 @@ k_mc_bernoulli(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *_
           const v4 Pj = G.P[j], Lj = G.L[j], Vj = G.V[j], Kj = G.K[j];
           R rx, ry, rz, vr;
           const R P = pair_probability<R>(Pi, Li, Vc, id_i, Pj, Lj, Vj, Kj, idj, GEOM != GEOM_OPEN, side, gtab, rc.n,
-                                          inv_v0, dt, step, k0, k1, rx, ry, rz, vr);
+                                          inv_v0, inv_vc2, dt, step, k0, k1, rx, ry, rz, vr);
           const uint4 wb = philox4x32_10(bern_counter(id_i, idj, step), k0, k1);
           const double r = uniform52(wb.x, wb.w), Pd = (double)P;
           band = band || fabs(r - Pd) <= Pd * 0x1p-20;
@@ -772,6 +776,29 @@ cudaError_t launch_debug_rates(int fp64, int n, int mode, double alpha, int64_t 
                                cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
   k_debug_rates<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(fp64, n, mode, alpha, k, in, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_debug_rates_screened(int fp64, double alpha0, int64_t k, const double *in, double *out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= k) return;
+  const double x = in[2 * t], q = in[2 * t + 1];
+  if (fp64) {
+    double a, b;
+    rates_quad<double>(x, 0, alpha0, a, b, q);
+    out[2 * t] = a;
+    out[2 * t + 1] = b;
+  } else {
+    float a, b;
+    rates_quad<float>((float)x, 0, (float)alpha0, a, b, (float)q);
+    out[2 * t] = a;
+    out[2 * t + 1] = b;
+  }
+}
+cudaError_t launch_debug_rates_screened(int fp64, double alpha0, int64_t k, const double *in, double *out,
+                                        cudaStream_t s) {
+  if (k <= 0) return cudaSuccess;
+  k_debug_rates_screened<<<(unsigned)((k + 127) / 128), 128, 0, s>>>(fp64, alpha0, k, in, out);
   return cudaGetLastError();
 }
 

@@ -59,14 +59,16 @@ __global__ void k_mlp_data(int64_t N, unsigned long long seed, MlpDataSpec spec,
   const double lm = spec.log_m_lo + (spec.log_m_hi - spec.log_m_lo) * u2;
   const int n = spec.n_values[k];
   const double s = pow(10.0, ls), x = 0.5 * s * s;
+  const double q = spec.scr ? pow(10.0, lt) : 0.0;      // screened law: tau = varsigma^2 / v_c^2
   double FA, FB;
-  rates_quad<double>(x, n, spec.alpha[k], FA, FB);
+  rates_quad<double>(x, n, spec.alpha[k], FA, FB, q);
+  const double ls2 = spec.scr ? 2.0 * log1p(q * (2.0 * x + 3.0)) : 0.0;
   X[4 * i + 0] = (float)(0.5 * ls);
   X[4 * i + 1] = (float)(0.5 * lt);
   X[4 * i + 2] = (float)lm;
   X[4 * i + 3] = (float)(0.25 * n);
-  Y[2 * i + 0] = (float)(log(FA) - spec.eA[k] * log1p(spec.cA[k] * x));
-  Y[2 * i + 1] = (float)(log(FB) - spec.eB[k] * log1p(spec.cB[k] * x));
+  Y[2 * i + 0] = (float)(log(FA) - spec.eA[k] * log1p(spec.cA[k] * x) + ls2);
+  Y[2 * i + 1] = (float)(log(FB) - spec.eB[k] * log1p(spec.cB[k] * x) + ls2);
 }
 
 // ---- training forward: 16-row tiles per warp, intermediates stored for the backward pass ----

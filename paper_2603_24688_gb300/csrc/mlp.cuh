@@ -159,7 +159,8 @@ struct MlpDomain {
   float s2_lo, s2_hi, tau_lo, tau_hi, m_lo, m_hi;   // training box (s^2 = w^2 / varsigma^2)
   float cA, cB;      // envelope constants for the run's n
   float eA, eB;      // envelope exponents (n+1)/2, (n+3)/2
-  float inv_v0sq, log_m, n4;
+  float inv_v0sq, log_m, n4;   // inv_v0sq: 1 / v0^2 (power law) or 1 / v_c^2 (screened law)
+  int scr;                     // 1: the screened law sigma0 / (1 + (v / v_c)^2)^2
 };
 
 // Inputs of a pair from s^2 = w^2 / varsigma^2 and varsigma^2, logarithms by the hardware log2
@@ -175,11 +176,16 @@ __device__ __forceinline__ bool mlp_inputs(const MlpDomain &d, float s2, float s
   return s2 >= d.s2_lo && s2 <= d.s2_hi && tau >= d.tau_lo && tau <= d.tau_hi;
 }
 
-// FA = e^{y0} (1 + cA x)^eA, FB likewise, x = s^2 / 2: one hardware exp and log per output
-__device__ __forceinline__ void mlp_outputs(const MlpDomain &d, float s2, const float y[MLP_OUT], float &FA, float &FB) {
+// FA = e^{y0} (1 + cA x)^eA, FB likewise, x = s^2 / 2: one hardware exp and log per output.
+// The screened law divides both envelopes by (1 + q (2x + 3))^2, q = varsigma^2 / v_c^2: sigma/sigma0
+// at the pair's mean-square speed, which carries the law's v^-4 fall (the n = -4 behaviour of FA,
+// FB at large q), so the network again learns an O(1) correction.
+__device__ __forceinline__ void mlp_outputs(const MlpDomain &d, float s2, float sig2, const float y[MLP_OUT],
+                                            float &FA, float &FB) {
   const float x = 0.5f * s2;
-  FA = __expf(fmaf(d.eA, __logf(fmaf(d.cA, x, 1.0f)), y[0]));
-  FB = __expf(fmaf(d.eB, __logf(fmaf(d.cB, x, 1.0f)), y[1]));
+  const float ls = d.scr ? -2.0f * __logf(fmaf(sig2 * d.inv_v0sq, s2 + 3.0f, 1.0f)) : 0.0f;
+  FA = __expf(fmaf(d.eA, __logf(fmaf(d.cA, x, 1.0f)), y[0] + ls));
+  FB = __expf(fmaf(d.eB, __logf(fmaf(d.cB, x, 1.0f)), y[1] + ls));
 }
 
 // ---- batched inference on pairs: 32 rows per warp ---------------------------------------------

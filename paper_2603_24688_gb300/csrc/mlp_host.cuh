@@ -24,6 +24,9 @@ struct MlpDataSpec {
   int n_count;
   int n_values[MLP_MAX_N];
   double alpha[MLP_MAX_N], cA[MLP_MAX_N], cB[MLP_MAX_N], eA[MLP_MAX_N], eB[MLP_MAX_N];
+  // 1: the screened law; tau is then q = varsigma^2 / v_c^2, the targets its quadrature (n = 0
+  // normalisation) and the envelopes carry the factor 1 / (1 + q (2x + 3))^2
+  int scr = 0;
 };
 
 cudaError_t mlp_refresh(MlpDev &d, cudaStream_t s);

@@ -90,12 +90,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0u;
 }
 
-// Waits for the phase with the given parity to complete; gives up after about two seconds.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// Waits for the phase with the given parity to complete; gives up after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > 2000000000ull) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
 }
 
@@ -379,6 +379,8 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
   uint32_t phase = 0;
   unsigned fallback = 0;
   bool ok = true;
+  bool skip_commit = a.skip_commit != 0 && blockIdx.x == 0 && g == 0;
+  const uint64_t wait_ns = a.wait_ns ? a.wait_ns : 2000000000ull;
   const float alpha = (float)a.rc.alpha;
   const int64_t n_tiles = (a.n + TC_ROWS - 1) / TC_ROWS;
   const int64_t stride = (int64_t)gridDim.x * NWG;
@@ -396,6 +398,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     float x[MLP_IN] = {0.f, 0.f, 0.f, 0.f};
     const int64_t p = nxt.p;
     float s2 = 0.f;                                   // (w / varsigma)^2
+    float sg2 = 0.f;                                  // varsigma^2
     bool use = false, in_dom = false;
     if (nxt.q >= 0) {
       if (MODE == MODE_X) {
@@ -406,6 +409,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
         if (sig > 0.0f) {
           const float wx = nxt.Vi.x - nxt.Vj.x, wy = nxt.Vi.y - nxt.Vj.y, wz = nxt.Vi.z - nxt.Vj.z;
           const float sig2 = sig * sig;
+          sg2 = sig2;
           s2 = __fdividef(wx * wx + wy * wy + wz * wz, sig2);
           in_dom = mlp_inputs(a.dom, s2, sig2, x);
           use = true;
@@ -465,8 +469,10 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
           tc_mma(d_tmem, smem_desc(sbase + Ly::ONE, TC_SLICE, 128),
                  smem_desc(sbase + Ly::BB + (layer - 1) * TC_OPER1, TC_SLICE, 128), 1u);
         }
-        tc_commit(bar);
+        // (fault injection only: the first layer-1 commit of group 0 in CTA 0 is left out)
+        if (!(skip_commit && layer == 0)) tc_commit(bar);
       }
+      skip_commit = false;
       // the next tile's gather behind this MMA
       if (layer == 0) {
         fetch_stage<MODE>(a, qn, 0, nxt);
@@ -478,12 +484,16 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
       }
       // every thread waits (bounded) for the MMA and the group agrees on the outcome, so that a
       // timeout is seen by all 128
-      const bool done = wg_sync_and(bar_id, mbar_wait_bounded(bar, phase));
-      phase ^= 1u;
+      const bool done = wg_sync_and(bar_id, mbar_wait_bounded(bar, phase, wait_ns));
       if (!done) {
+        // the MMAs this group issued may still be in flight: a new commit tracks them, and the
+        // group waits for it (bounded again) before it leaves and the CTA frees tensor memory
+        if (t == 0) tc_commit(bar);
+        (void)wg_sync_and(bar_id, mbar_wait_bounded(bar, phase, wait_ns));
         ok = false;
         break;
       }
+      phase ^= 1u;
       tc_fence_after();
       if (TSA) {
         // the whole row of z at once (one wait for four loads): with two warpgroups each warp
@@ -544,9 +554,9 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     } else if (use) {
       float FA, FB;
       if (in_dom) {
-        mlp_outputs(a.dom, s2, y, FA, FB);
+        mlp_outputs(a.dom, s2, sg2, y, FA, FB);
       } else {
-        rates_quad<float>(0.5f * s2, a.rc.n, alpha, FA, FB);
+        rates_quad<float>(0.5f * s2, a.rc.n, alpha, FA, FB, sg2 * (float)a.rc.inv_vc2);
         ++fallback;
       }
       a.rates[p] = make_float2(FA, FB);
@@ -599,7 +609,9 @@ static cudaError_t launch_tc(const TcArgs &a, cudaStream_t s) {
   int64_t blocks = (n_tiles + NWG - 1) / NWG;
   if (blocks > 152) blocks = 152;
   if (blocks < 1) blocks = 1;
-  k_mlp_tc<NWG, MODE, TSA><<<(unsigned)blocks, NWG * 128, smem, s>>>(a);
+  TcArgs b = a;
+  if (b.skip_commit) b.wait_ns = 1000000ull;   // the injected timeout: 1 ms
+  k_mlp_tc<NWG, MODE, TSA><<<(unsigned)blocks, NWG * 128, smem, s>>>(b);
   return cudaGetLastError();
 }
 

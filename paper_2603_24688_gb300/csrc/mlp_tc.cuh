@@ -29,6 +29,11 @@ struct TcArgs {
   float2 *rates;                   // [pairs] (FA, FB)
   unsigned long long *fallback_count;
   uint32_t *status;                // DMB_BAD_TIMEOUT if a tensor-core wait gave up
+  // limit of every wait on an MMA completion, ns (0: the default, about two seconds)
+  unsigned long long wait_ns;
+  // fault injection for the timeout path: warpgroup 0 of CTA 0 omits the commit of its first
+  // layer-1 MMA, so its wait runs out; the launcher then uses a 1 ms limit
+  int skip_commit;
 };
 
 // Shared-memory attributes (call once before any graph capture).

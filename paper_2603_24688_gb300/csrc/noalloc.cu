@@ -75,6 +75,13 @@ extern "C" dmb_status dmb_surrogate_grad_noalloc(dmb_ctx *ctx, const float *X, c
     return dmb_internal_fail(ctx, DMB_ERR_ARG,
                              "dmb_surrogate_grad_noalloc: batch size must be in [1, 4096] (its fixed work array)");
   if (!X || !Y || !grad) return dmb_internal_fail(ctx, DMB_ERR_ARG, "NULL array");
+  // the array is per device: the one to use is that of the device the context's stream is on
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != dmb_internal_device(ctx)) {
+    cudaGetLastError();
+    return dmb_internal_fail(ctx, DMB_ERR_STATE,
+                             "dmb_surrogate_grad_noalloc: the current CUDA device is not the context's device");
+  }
   unsigned char *base = nullptr;
   cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return dmb_internal_fail(ctx, DMB_ERR_CUDA, cudaGetErrorString(e));

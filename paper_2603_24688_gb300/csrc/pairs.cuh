@@ -141,5 +141,7 @@ cudaError_t launch_gtable(float4 *T, cudaStream_t s, int64_t *launches);
 cudaError_t launch_debug_overlap(const float4 *T, int fp64, int64_t k, const double *in, double *out, cudaStream_t s);
 cudaError_t launch_debug_rates(int fp64, int n, int mode, double alpha, int64_t k, const double *in, double *out,
                                cudaStream_t s);
+cudaError_t launch_debug_rates_screened(int fp64, double alpha0, int64_t k, const double *in, double *out,
+                                        cudaStream_t s);
 cudaError_t launch_debug_philox(int64_t k, const uint32_t *ctr, uint32_t *out, unsigned long long seed,
                                 cudaStream_t s);

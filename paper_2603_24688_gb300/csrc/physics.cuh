@@ -267,6 +267,18 @@ __device__ __forceinline__ R ipow(R x, int n) {
   return r;
 }
 
+// sigma(v) / sigma0 of the run's velocity law: the power law (v / v0)^n, or with inv_vc2 =
+// 1 / v_c^2 > 0 the screened law 1 / (1 + (v / v_c)^2)^2 (a massive mediator; Sec. 2.4 allows
+// any sigma(v) whose A and B can be computed), whose runs carry n = 0.
+template <typename R>
+__device__ __forceinline__ R sigma_ratio(R v, int n, R inv_v0, R inv_vc2) {
+  if (inv_vc2 > (R)0) {
+    const R q = (R)1 + v * v * inv_vc2;
+    return rcp_pair(q * q);
+  }
+  return ipow<R>(v * inv_v0, n);
+}
+
 // generic 1F1(a, b; -x) for b - a > 0 (slow path)
 template <typename R>
 __device__ R hyp1f1_neg_generic(R a, R b, R x) {
@@ -385,12 +397,11 @@ __device__ __forceinline__ void quad_kernels(R t, R s, R &sinhk_k, R &i1k) {
   i1k = (R)0.5 * (em * (ik - ik * ik) + ep * (ik + ik * ik));
 }
 
+// 8 panels of 8-point Gauss-Legendre on [a, b]: sa += sum w t^(n+4) wq(t) i1, sb += ... sinh
 template <typename R>
-__device__ __forceinline__ void rates_quad(R x, int n, R alpha, R &FA, R &FB) {
-  const R s = sqrt_t((R)2 * x);
-  const R a = s > (R)9 ? s - (R)9 : (R)0, b = s + (R)9;
+__device__ __forceinline__ void quad_panels(R a, R b, R s, int n, R q, R &sa, R &sb) {
   const R hw = (b - a) * (R)(0.5 / DMB_QUAD_PANELS);
-  R sa = 0, sb = 0;
+  R pa = 0, pb = 0;
   for (int pnl = 0; pnl < DMB_QUAD_PANELS; ++pnl) {
     const R mid = a + hw * (R)(2 * pnl + 1);
 #pragma unroll
@@ -398,12 +409,35 @@ __device__ __forceinline__ void rates_quad(R x, int n, R alpha, R &FA, R &FB) {
       const R t = mid + hw * (R)c_gl8_x[m];
       R sk, ik;
       quad_kernels<R>(t, s, sk, ik);
-      const R tn = ipow<R>(t, n + 4);
-      sa += (R)c_gl8_w[m] * tn * ik;
-      sb += (R)c_gl8_w[m] * tn * t * sk;
+      R tn = ipow<R>(t, n + 4);
+      if (q > (R)0) {                                 // screened law: sigma_bar(varsigma t) / sigma0
+        const R d = (R)1 + q * t * t;
+        tn /= d * d;
+      }
+      pa += (R)c_gl8_w[m] * tn * ik;
+      pb += (R)c_gl8_w[m] * tn * t * sk;
     }
   }
-  const R c = (R)0.79788456080286536 * hw;          // sqrt(2/pi) times the panel half-width
+  sa += hw * pa;
+  sb += hw * pb;
+}
+
+// q = varsigma^2 / v_c^2 for the screened law (0: the power law).  The screened weight has poles
+// at t = +-i / sqrt(q); when they come closer to the window than a panel is wide (q > 1) the
+// window is split at 4 / sqrt(q) and each part gets its own 8 panels.
+template <typename R>
+__device__ __forceinline__ void rates_quad(R x, int n, R alpha, R &FA, R &FB, R q = (R)0) {
+  const R s = sqrt_t((R)2 * x);
+  const R a = s > (R)9 ? s - (R)9 : (R)0, b = s + (R)9;
+  R sa = 0, sb = 0;
+  const R split = q > (R)1 ? (R)4 / sqrt_t(q) : (R)0;
+  if (split > a && split < b) {
+    quad_panels<R>(a, split, s, n, q, sa, sb);
+    quad_panels<R>(split, b, s, n, q, sa, sb);
+  } else {
+    quad_panels<R>(a, b, s, n, q, sa, sb);
+  }
+  const R c = (R)0.79788456080286536;               // sqrt(2/pi) (the half-widths are in sa, sb)
   // Ahat = c sa / s, with the s -> 0 limit of i1(t s)/s = t/3 carried by the series
   const R Ahat = s > (R)0 ? c * sa / s : (R)0;
   FA = Ahat * (R)3 / alpha;

@@ -26,7 +26,8 @@ EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb
            "dmb_surrogate_infer", "dmb_surrogate_grad", "dmb_surrogate_fallbacks", "dmb_step_batched",
            "dmb_surrogate_grad_noalloc", "dmb_set_bins", "dmb_substep_info", "dmb_substep", "dmb_set_graph",
            "dmb_set_surrogate_engine", "dmb_surrogate_infer_tc", "dmb_autotune", "dmb_set_shapes",
-           "dmb_get_shapes", "dmb_rebin_dm", "dmb_set_mc_variant", "dmb_set_anisotropy"]
+           "dmb_get_shapes", "dmb_rebin_dm", "dmb_set_mc_variant", "dmb_set_anisotropy", "dmb_debug_tc_timeout",
+           "dmb_set_cross_section", "dmb_debug_rates_screened"]
 
 
 class DmbError(RuntimeError):
@@ -105,6 +106,9 @@ def load(path=LIB_PATH):
         "dmb_rebin_dm": ([vp, vp, vp, i64, c.c_int32, u64, vp, c.POINTER(i64)], c.c_int),
         "dmb_set_mc_variant": ([vp, c.c_int32], c.c_int),
         "dmb_set_anisotropy": ([vp, c.c_double], c.c_int),
+        "dmb_debug_tc_timeout": ([vp, c.c_int32], c.c_int),
+        "dmb_set_cross_section": ([vp, c.c_int32, dbl], c.c_int),
+        "dmb_debug_rates_screened": ([vp, i64, vp, vp], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -308,6 +312,15 @@ class Context:
         """dsigma/dOmega proportional to 1 + beta cos theta, beta in [-1, 1] (0: isotropic)."""
         self._check(self.lib.dmb_set_anisotropy(self.h, float(beta)))
 
+    def dmb_set_cross_section(self, family, v_c_kms=0.0):
+        """0: sigma0 (v/v0)^n; 1: the screened law sigma0 / (1 + (v/v_c)^2)^2."""
+        self._check(self.lib.dmb_set_cross_section(self.h, int(family), float(v_c_kms)))
+
+    def dmb_debug_rates_screened(self, inp, out):
+        import torch
+        self._check(self.lib.dmb_debug_rates_screened(self.h, inp.shape[0], _ptr(inp, torch.float64),
+                                                      _ptr(out, torch.float64)))
+
     def dmb_set_graph(self, on=True):
         self._check(self.lib.dmb_set_graph(self.h, 1 if on else 0))
 
@@ -356,13 +369,20 @@ class Context:
                                                 _ptr(grad, torch.float32), ctypes.byref(loss)))
         return loss.value
 
-    def dmb_surrogate_grad_noalloc(self, X, Y, grad):
-        """dmb_surrogate_grad with its work buffers in the library's fixed device array (B <= 4096)."""
+    def dmb_surrogate_grad_noalloc(self, X, Y, grad, want_loss=True):
+        """dmb_surrogate_grad with its work buffers in the library's fixed device array (B <= 4096).
+
+        want_loss=False passes no loss pointer, so the call does not synchronise the stream."""
         import torch
         loss = ctypes.c_double()
         self._check(self.lib.dmb_surrogate_grad_noalloc(self.h, _ptr(X, torch.float32), _ptr(Y, torch.float32),
-                                                        X.shape[0], _ptr(grad, torch.float32), ctypes.byref(loss)))
-        return loss.value
+                                                        X.shape[0], _ptr(grad, torch.float32),
+                                                        ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def dmb_debug_tc_timeout(self, on=True):
+        """Fault injection: the next tensor-core surrogate launch times out one wait (DMB_ERR_TIMEOUT)."""
+        self._check(self.lib.dmb_debug_tc_timeout(self.h, 1 if on else 0))
 
     def dmb_surrogate_fallbacks(self):
         n = ctypes.c_int64()
