@@ -39,6 +39,10 @@ LANES = 128
 # rates and the float64-free sums for the mean field; Philox, Box-Muller, the overlap and the
 # fixed-point running sum for the Monte Carlo
 OPS_PER_PAIR = {"meanfield": 150.0, "mc": 256.0}
+# pair search: lane operations per candidate test of the tile stage's count pass (the split-float
+# displacement with the minimum image, the squared distance and the strict comparison with
+# h_i + h_j, the ballots and the mask bookkeeping)
+SEARCH_OPS_PER_TEST = 25.0
 # quadrature provider: 64 nodes x (2 exp + ~14 ops) + the 120 ops of the rest of the pair
 QUAD_OPS_PER_PAIR = 64 * 16 + 120.0
 # learned surrogate per pair: the network's dense contraction, 2 x (4 x 128 + 2 x 128 x 128 +
@@ -53,6 +57,10 @@ MLP_TENSOR_FLOP_PER_PAIR = 2.0 * 128 * (16 + 128 + 16 + 128 + 16)
 # copies read and the 8-byte rates written per pair
 MLP_DRAM_BYTES_PER_PAIR = (714.359040e6 + 639.384064e6) / 85071169
 MLP_ALGO_BYTES_PER_PAIR = 4 + 4 + 16 + 16 + 8
+# the surrogate's training recipe (samples of the float64 device quadrature, Adam epochs)
+TRAIN = dict(nsamples=1 << 21, epochs=96, seed=11)
+# the power-law indices of the benchmark's cross-section scan
+SCAN_N = (-4, -2, 0, 2)
 
 
 def parse():
@@ -69,6 +77,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--retune", action="store_true", help="run the autotuner even if shapes are stored")
     ap.add_argument("--fp64", action="store_true", help="float64 pair arithmetic (the box4k configuration)")
     return ap.parse_args()
 
@@ -277,6 +286,45 @@ def cpu_oracle_all_cores(w, target_pairs=60_000, per_core=2, seed=0, cores=None)
     return n / wall, n, wall, cores, desc
 
 
+def envelope(n):
+    """Constants of the surrogate's envelopes (1 + cA x)^eA, (1 + cB x)^eB for sigma ~ v^n."""
+    c = (n + 6) / 2.0
+    eA, eB = (n + 1) / 2.0, (n + 3) / 2.0
+    cA = (math.gamma(2.5) / math.gamma(c)) ** (1.0 / eA) if eA != 0 else 1.0
+    cB = (math.gamma(1.5) / math.gamma(c)) ** (1.0 / eB) if eB != 0 else 1.0
+    return cA, eA, cB, eB
+
+
+def surrogate_errors(params, n, prm):
+    """Relative error of the surrogate's FA, FB (tensor-core engine) against the float64 device
+    quadrature on a grid over the training box (s: 161 points, tau: 6, m_chi: 3) at index n."""
+    import torch
+    from paper_2603_24688_gb300 import dmb
+    s = np.geomspace(1e-2, 1e2, 161)
+    S, T, M = np.meshgrid(s, np.geomspace(1e-3, 1e2, 6), np.array([0.5, 2.0, 10.0]), indexing="ij")
+    X = np.stack([0.5 * np.log10(S.ravel()), 0.5 * np.log10(T.ravel()), np.log10(M.ravel()),
+                  np.full(S.size, n / 4.0)], 1).astype(np.float32)
+    c = dmb.Context(prm["sigma0_cm2"], n, prm["m_chi_mp"], prm["v0_kms"], False, (0.0, 0.0, 0.0), prm["seed"],
+                    rate_mode=dmb.DMB_RATE_MLP)
+    c.dmb_load_surrogate(params)
+    Y = torch.empty((X.shape[0], 2), dtype=torch.float32, device="cuda")
+    c.dmb_surrogate_infer_tc(torch.from_numpy(X).cuda(), Y)
+    q = dmb.Context(prm["sigma0_cm2"], n, prm["m_chi_mp"], prm["v0_kms"], False, (0.0, 0.0, 0.0), prm["seed"],
+                    fp64=True, rate_mode=dmb.DMB_RATE_QUAD)
+    x = 0.5 * S.ravel() ** 2
+    F = torch.empty((x.size, 2), dtype=torch.float64, device="cuda")
+    q.dmb_debug_rates(torch.from_numpy(x).cuda(), F)
+    torch.cuda.synchronize()
+    F, Y = F.cpu().numpy(), Y.cpu().numpy().astype(np.float64)
+    cA, eA, cB, eB = envelope(n)
+    eA_ = np.abs(np.expm1(Y[:, 0] - (np.log(F[:, 0]) - eA * np.log1p(cA * x))))
+    eB_ = np.abs(np.expm1(Y[:, 1] - (np.log(F[:, 1]) - eB * np.log1p(cB * x))))
+    c.close()
+    q.close()
+    return {"mean_A": float(eA_.mean()), "max_A": float(eA_.max()), "mean_B": float(eB_.mean()),
+            "max_B": float(eB_.max())}
+
+
 def workload_desc(a, w):
     """The config's workload string, the same for both arms."""
     nd, ng = len(w['dm']['h']), len(w['gas']['h'])
@@ -328,7 +376,7 @@ def run_substeps(a, peaks, peak_kind):
     stream = torch.cuda.current_stream()
     ctx = dmb.Context(prm["sigma0_cm2"], prm["n"], prm["m_chi_mp"], prm["v0_kms"], False, (0.0, 0.0, 0.0),
                       prm["seed"], rate_mode=dmb.DMB_RATE_MLP, stream=stream)
-    rep = ctx.dmb_train_surrogate(nsamples=1 << 20, epochs=24, seed=11)
+    rep = ctx.dmb_train_surrogate(**TRAIN)
     dm, gas = dmb.to_device(w["dm"]), dmb.to_device(w["gas"])
     db = torch.from_numpy(w["dm_bin"]).cuda()
     gb = torch.from_numpy(w["gas_bin"]).cuda()
@@ -405,11 +453,27 @@ def run_boxes(a, peaks, peak_kind):
     gbx = torch.from_numpy(w["gas_box"].view(np.int32)).cuda()
     step = 0
     sums = None
-    for _ in range(a.warmup):
+    # the direct launches first (stage times), then the captured step
+    ctx.dmb_set_timing(True)
+    for _ in range(2):
+        ctx.dmb_step_batched(dm, dbx, gas, gbx, w["boxes"], step, w["dt"], want_sums=False)
+        step += 1
+    stage_ms, nsteps = ctx.dmb_stage_times()
+    ctx.dmb_set_timing(False)
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(2):
+        ctx.dmb_step_batched(dm, dbx, gas, gbx, w["boxes"], step, w["dt"], want_sums=False)
+        step += 1
+    d1.record(stream)
+    torch.cuda.synchronize()
+    direct_ms = d0.elapsed_time(d1) / 2
+    ctx.dmb_set_graph(True)
+    for _ in range(a.warmup):         # the first captures the step, the others replay it
         sums = ctx.dmb_step_batched(dm, dbx, gas, gbx, w["boxes"], step, w["dt"])
         step += 1
     npairs = int(sums[12])
-    ctx.dmb_set_timing(True)
     l0 = ctx.dmb_launch_count()
     clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
     torch.cuda.synchronize()
@@ -421,7 +485,6 @@ def run_boxes(a, peaks, peak_kind):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    stage_ms, nsteps = ctx.dmb_stage_times()
     clk = clocks.stop()
     nd, ng = len(w["dm"]["h"]), len(w["gas"]["h"])
     names = ["grid", "search", "meanfield", "mc", "kick"]
@@ -433,7 +496,10 @@ def run_boxes(a, peaks, peak_kind):
                                    f"m_chi, T and counts log-uniform", "pairs_per_step": npairs,
                        "parallelism": "replicas x1"},
             "particles_stepped_per_s": (nd + ng) * a.steps / (ms * 1e-3),
-            "stage_ms": {n: float(v) / max(nsteps, 1) for n, v in zip(names, stage_ms[:5])},
+            "graph": True, "graph_launches_per_step": 1,
+            "kernels_per_step": int(ctx.dmb_launch_count() - l0) // max(a.steps, 1),
+            "direct_ms_per_step": direct_ms,
+            "stage_ms_direct": {n: float(v) / max(nsteps, 1) for n, v in zip(names, stage_ms[:5])},
             "gpu_launches": int(ctx.dmb_launch_count() - l0), "clocks": clk, "peak_kind": peak_kind}
     print(json.dumps(line))
     ctx.close()
@@ -507,15 +573,25 @@ def main():
     train_report = None
     if a.rate == "mlp" or not a.no_compare:
         tctx = new_ctx("mlp")
-        train_report = tctx.dmb_train_surrogate(nsamples=1 << 20, epochs=24, seed=11)
+        train_report = tctx.dmb_train_surrogate(**TRAIN)
         surrogate = tctx.dmb_surrogate_params()
         tctx.close()
     ctx = new_ctx(a.rate)
     if a.rate == "mlp":
         ctx.dmb_load_surrogate(surrogate)
     shapes, tune_times = (None, None)
+    shapes_from = None
     if not a.no_autotune:
-        shapes, tune_times = ctx.dmb_autotune(dm, gas)   # reads the state only
+        # the autotuner's choice persists per workload (host JSON written by the library)
+        cache = os.path.join(ROOT, "paper_2603_24688_gb300", "_build", "tuned_shapes.json")
+        key = f"{a.workload}.n{a.n}.{a.rate}" + (".fp64" if a.fp64 else "")
+        if not a.retune and ctx.dmb_load_shapes(cache, key):
+            shapes, shapes_from = ctx.dmb_get_shapes(), "loaded from " + os.path.relpath(cache, ROOT)
+        else:
+            shapes, tune_times = ctx.dmb_autotune(dm, gas)   # reads the state only
+            os.makedirs(os.path.dirname(cache), exist_ok=True)
+            ctx.dmb_save_shapes(cache, key)
+            shapes_from = "dmb_autotune on this state"
     dt = w["dt"]
     step = 0
     sums = None
@@ -605,6 +681,13 @@ def main():
     for n in ("meanfield", "mc"):
         r = roofline(n)
         stages[n + "_frac"] = r["frac"] if r else None
+    # the pair search: candidate distance tests of the count pass (after the ballot prefilter) at
+    # SEARCH_OPS_PER_TEST lane operations each, over the whole search stage's time
+    st = ctx.dmb_search_stats()
+    tests = float(st[0][2])
+    search_ops = tests * SEARCH_OPS_PER_TEST
+    stages["search_candidate_tests"] = tests
+    stages["search_frac"] = search_ops / (per_step[1] * 1e-3) / 1e12 / alu_peak if per_step[1] > 0 else None
 
     # ---- the other rate providers: mean-field stage time on the same state ------------------
     providers = {a.rate: {"meanfield_ms": float(per_step[2])}}
@@ -628,6 +711,35 @@ def main():
             del dm2, gas2
         if "quad" in providers and "mlp" in providers:
             providers["mlp_speedup_over_quad"] = providers["quad"]["meanfield_ms"] / providers["mlp"]["meanfield_ms"]
+        # the cross-section scan of the workload: every rate provider's mean field and the whole
+        # surrogate step at each n, with the surrogate's rate error at that n
+        per_n = {}
+        for n in SCAN_N:
+            row = {}
+            for rate in ("closed", "quad", "mlp"):
+                c2 = dmb.Context(prm["sigma0_cm2"], n, prm["m_chi_mp"], prm["v0_kms"], prm["periodic"],
+                                 tuple(prm["box"]), prm["seed"], fp64=a.fp64, rate_mode=modes[rate], stream=stream)
+                if rate == "mlp":
+                    c2.dmb_load_surrogate(surrogate)
+                if shapes is not None:
+                    c2.dmb_set_shapes(shapes)
+                c2.dmb_set_timing(True)
+                dm2 = {k: v.clone() for k, v in dm.items()}
+                gas2 = {k: v.clone() for k, v in gas.items()}
+                for _ in range(2):
+                    c2.dmb_step(dm2, gas2, step, dt)
+                ms2, n2 = c2.dmb_stage_times()
+                row[rate + "_meanfield_ms"] = float(ms2[2] / max(n2, 1))
+                if rate == "mlp":
+                    row["mlp_step_ms"] = float(ms2[:5].sum() / max(n2, 1))
+                    row["surrogate_fallback_pairs"] = int(c2.dmb_surrogate_fallbacks())
+                c2.close()
+                del dm2, gas2
+            row["mlp_speedup_over_quad"] = row["quad_meanfield_ms"] / row["mlp_meanfield_ms"]
+            if surrogate is not None:
+                row["surrogate_rate_error"] = surrogate_errors(surrogate, n, prm)
+            per_n[str(n)] = row
+        providers["per_n"] = per_n
     if train_report is not None:
         providers["surrogate_training"] = {"seconds": float(train_report[5]), "steps": int(train_report[6]),
                                            "samples": int(train_report[7]),
@@ -690,7 +802,7 @@ def main():
                            "l2": "inputs (~1 GB) larger than L2; no flush", "parallelism": f"replicas x{world}"},
                 "particles_stepped_per_s": nparticles * world / (ms_max * 1e-3 / a.steps),
                 "stage_ms": dict(stages, surrogate_pass=surrogate_ms), "rate_providers": providers,
-                "launch_shapes": shapes, "gpu_launches": int(launches), "roofline": roof,
+                "launch_shapes": shapes, "launch_shapes_from": shapes_from, "gpu_launches": int(launches), "roofline": roof,
                 "peak_kind": peak_kind,
                 "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(line))

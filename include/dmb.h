@@ -311,6 +311,14 @@ dmb_status dmb_autotune(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int3
 dmb_status dmb_set_shapes(dmb_ctx *ctx, const int32_t *shapes);
 dmb_status dmb_get_shapes(dmb_ctx *ctx, int32_t *shapes_out);
 
+/* Persisted launch shapes: dmb_save_shapes writes the context's shapes (dmb_get_shapes) under
+ * `key` into the JSON file at `path` ({"key": [5 integers], ...}; other keys are kept; the file is
+ * replaced atomically); dmb_load_shapes sets them from the entry of `key` (DMB_ERR_STATE when the
+ * file or the key is absent, DMB_ERR_ARG for a malformed or out-of-range entry).  Keys are made of
+ * [A-Za-z0-9._+-] (a workload name, say).  Host-only; no GPU work. */
+dmb_status dmb_save_shapes(dmb_ctx *ctx, const char *path, const char *key);
+dmb_status dmb_load_shapes(dmb_ctx *ctx, const char *path, const char *key);
+
 /* Stage timing of dmb_step with CUDA events recorded on the context stream (adds one
  * event synchronisation per step).  on = 0 disables it.  Resets the accumulators. */
 dmb_status dmb_set_timing(dmb_ctx *ctx, int on);

@@ -1,5 +1,7 @@
 // C ABI: context, buffers and the launch sequences of the hybrid interaction step.
+#include <ctype.h>
 #include <math.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -110,6 +112,27 @@ struct dmb_ctx {
     int64_t launches;
   };
   bool use_graph = false;
+  // the captured batched step (dmb_step_batched with dmb_set_graph(ctx, 1)): the graph of one
+  // step for one set of caller arrays and boxes, and the buffer capacities it was sized for
+  struct BatchCaps {
+    int64_t items = 0, units = 0, pairs = 0, segs = 0;
+  };
+  struct BatchGraph {
+    bool valid = false;
+    const void *key[14] = {};
+    int64_t nd = 0, ng = 0;
+    double dt = 0.0;
+    std::vector<dmb_box> boxes;
+    BatchCaps caps;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+  } bgraph;
+  bool capturing = false;           // a batched step is being captured: no allocation, no readback
+  const int64_t *pairs_dev = nullptr;   // device pair total while capturing (surrogate row count)
+  const uint32_t *gate_dev = nullptr;   // device overflow gate while capturing (kick)
+  bool frame_ready = false;         // the batched frame was uploaded by dmb_step_batched
+  uint64_t batch_next_step = ~0ull; // device step counter value after the last batched graph
+  DevBuf gate, cap_need;
   int mc_variant = 0;             // dmb_set_mc_variant
   double mc_beta = 0.0;           // dmb_set_anisotropy
   cudaStream_t gstream = nullptr;
@@ -196,10 +219,20 @@ void clear_graphs(dmb_ctx *ctx) {
   ctx->graph_next_step = ~0ull;
 }
 
-// the grid or the pair lists change: substep tables and captured graphs are stale
+// drops the captured batched step (its kernels hold the buffers and constants of its capture)
+void clear_batch_graph(dmb_ctx *ctx) {
+  if (ctx->bgraph.exec) cudaGraphExecDestroy(ctx->bgraph.exec);
+  ctx->bgraph.exec = nullptr;
+  ctx->bgraph.valid = false;
+  ctx->batch_next_step = ~0ull;
+}
+
+// the grid or the pair lists change: substep tables and captured graphs are stale (the batched
+// step's own capture rebuilds them inside the graph, which is why it keeps its graph)
 void invalidate_substeps(dmb_ctx *ctx) {
   ctx->bins_ready = false;
   clear_graphs(ctx);
+  if (!ctx->capturing) clear_batch_graph(ctx);
 }
 
 dmb_status ensure_species(dmb_ctx *ctx, SpeciesBufs &s, int64_t n, bool gas) {
@@ -254,26 +287,10 @@ dmb_status build_grid_impl(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
   int bits = (int)fmin(21.0, fmax(10.0, ceil(log2((double)(ntot > 1 ? ntot : 2)) / 3.0) + 7.0));
   int box_bits = 0;
   if (batched) {
+    // the frame of the virtual space (boxes side by side along x) was set up by dmb_step_batched
     while ((1 << box_bits) < ctx->nbox) ++box_bits;
     bits = (int)fmin((double)bits, floor((63.0 - box_bits) / 3.0));
-    // frame of the virtual space: boxes side by side along x, each in a slot of width `stride`
-    double Lq = 0.0;
-    std::vector<BoxParamDev> hp(ctx->nbox);
-    CK(cudaMemcpy(hp.data(), ctx->box_params.p, sizeof(BoxParamDev) * ctx->nbox, cudaMemcpyDeviceToHost), "box table");
-    for (auto &b : hp) Lq = fmax(Lq, fmax(b.L[0], fmax(b.L[1], b.L[2])));
-    Frame f;
-    for (int c = 0; c < 3; ++c) f.origin[c] = 0.0;
-    f.span = fmax(ctx->nbox * ctx->stride, Lq);
-    int e;
-    frexp(f.span, &e);
-    f.delta = ldexp(1.0, e - 23);
-    f.inv_delta = ldexp(1.0, 23 - e);
-    f.bits = bits;
-    f.key_scale = ldexp(1.0, bits) / (Lq * (1.0 + 1e-12));
-    f.pad = (float)(4.0 * ldexp(1.0, e) * 1.1920928955078125e-07);
-    f.hmax_dm = f.hmax_gas = 0.0;
-    CK(cudaMemcpyAsync(ctx->frame.p, &f, sizeof(Frame), cudaMemcpyHostToDevice, s), "frame");
-    CK(cudaStreamSynchronize(s), "frame");
+    if (!ctx->frame_ready) return fail(ctx, DMB_ERR_STATE, "batched frame missing");
   } else {
     CK(launch_frame(dm->pos, dm->h, dm->n, gas->pos, gas->h, gas->n, ctx->p.periodic, ctx->p.box,
                     ptr<double>(ctx->frame_part), (int64_t)(ctx->frame_part.bytes / 8), ptr<Frame>(ctx->frame),
@@ -451,6 +468,91 @@ dmb_status neighbors_impl(dmb_ctx *ctx) {
   return DMB_OK;
 }
 
+// The pair search of a captured batched step: the launches of neighbors_impl with every buffer
+// sized in advance to the capacities of ctx->bgraph.caps and no count read back.  After each
+// scan a capacity check compares the device total with its capacity; on overflow it clears
+// the offsets (every later kernel sees empty rows), raises the gate (the kick changes nothing)
+// and records the totals, from which the host regrows the buffers and repeats the step.
+template <typename R>
+dmb_status neighbors_capped(dmb_ctx *ctx) {
+  cudaStream_t s = ctx->stream;
+  int64_t *L = &ctx->launches;
+  const dmb_ctx::BatchCaps &cap = ctx->bgraph.caps;
+  const SpeciesView<R> D = view<R>(ctx->dm, true), G = view<R>(ctx->gas, true);
+  SearchBufs &sg = ctx->sg, &sd = ctx->sd;
+  const int nleaf = G.cnt[0];
+  const int64_t nd = D.n, ng = G.n;
+  const Frame *fr = ptr<Frame>(ctx->frame);
+  uint32_t *status = ptr<uint32_t>(ctx->status);
+  CapCheck base;
+  base.need = ptr<int64_t>(ctx->cap_need);
+  base.gate = ptr<uint32_t>(ctx->gate);
+  base.status = status;
+  int64_t *item_ptr = ptr<int64_t>(sg.item_ptr), *unit_ptr = ptr<int64_t>(sg.unit_ptr);
+  // stage 1: candidate leaves per query leaf and the work units
+  CK(launch_leaf_pairs<R>(G, D, ctx->bx, fr, false, ptr<uint32_t>(sg.item_cnt), nullptr, nullptr, status, nullptr, s,
+                          L), "leaf pairs (count)");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(sg.item_cnt), item_ptr, nleaf, ptr<int64_t>(ctx->scan_tmp), s, L), "scan");
+  CK(launch_unit_counts(item_ptr, nleaf, ctx->shp.unit, ptr<uint32_t>(sg.unit_cnt_leaf), s, L), "unit counts");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(sg.unit_cnt_leaf), unit_ptr, nleaf, ptr<int64_t>(ctx->scan_tmp), s, L),
+     "scan");
+  CapCheck c1 = base;
+  c1.total[0] = item_ptr + nleaf; c1.cap[0] = cap.items; c1.slot[0] = 0; c1.zero[0] = item_ptr; c1.zero_n[0] = nleaf + 1;
+  c1.total[1] = unit_ptr + nleaf; c1.cap[1] = cap.units; c1.slot[1] = 1; c1.zero[1] = unit_ptr; c1.zero_n[1] = nleaf + 1;
+  CK(launch_cap_check(c1, s, L), "capacity check");
+  // stage 2, count pass (both directions' counts)
+  CK(cudaMemsetAsync(sd.counts.p, 0, (size_t)(nd + 1) * 4, s), "memset");
+  TransposeOut trc;
+  trc.cnt = ptr<uint32_t>(sd.counts);
+  CK(launch_leaf_pairs<R>(G, D, ctx->bx, fr, true, nullptr, item_ptr, ptr<uint32_t>(sg.items), status, nullptr, s, L),
+     "leaf pairs (emit)");
+  CK(launch_unit_map(item_ptr, unit_ptr, nleaf, ctx->shp.unit, ptr<uint32_t>(sg.unit_leaf), ptr<int64_t>(sg.unit_item0),
+                     s, L), "unit map");
+  CK(launch_tile<R>(G, D, ctx->bx, fr, false, ptr<uint32_t>(sg.unit_leaf), ptr<int64_t>(sg.unit_item0), item_ptr,
+                    ptr<uint32_t>(sg.items), cap.units, ctx->shp.unit, ptr<uint32_t>(sg.unit_cnt), nullptr, nullptr,
+                    trc, ptr<uint32_t>(sg.tmask), status, nullptr, s, L, unit_ptr + nleaf), "tile (count)");
+  CK(launch_unit_prefix(unit_ptr, nleaf, ng, ptr<uint32_t>(sg.unit_cnt), ptr<uint32_t>(sg.counts), s, L),
+     "unit prefix");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(sg.counts), ptr<int64_t>(sg.row_ptr), ng, ptr<int64_t>(ctx->scan_tmp), s, L),
+     "scan");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(sd.counts), ptr<int64_t>(sd.row_ptr), nd, ptr<int64_t>(ctx->scan_tmp), s, L),
+     "scan");
+  CapCheck c2 = base;
+  c2.total[0] = ptr<int64_t>(sg.row_ptr) + ng; c2.cap[0] = cap.pairs; c2.slot[0] = 2;
+  c2.zero[0] = ptr<int64_t>(sg.row_ptr); c2.zero_n[0] = ng + 1;
+  c2.total[1] = ptr<int64_t>(sd.row_ptr) + nd; c2.cap[1] = cap.pairs; c2.slot[1] = 2;
+  c2.zero[1] = ptr<int64_t>(sd.row_ptr); c2.zero_n[1] = nd + 1;
+  CK(launch_cap_check(c2, s, L), "capacity check");
+  // emit pass: gas-major rows and the DM-major rows by claimed positions
+  CK(cudaMemsetAsync(ctx->t_cursor.p, 0, (size_t)(nd + 1) * 4, s), "memset");
+  TransposeOut tre;
+  tre.cursor = ptr<uint32_t>(ctx->t_cursor);
+  tre.ptr = ptr<int64_t>(sd.row_ptr);
+  tre.rows = ptr<uint32_t>(sd.rows);
+  CK(launch_tile<R>(G, D, ctx->bx, fr, true, ptr<uint32_t>(sg.unit_leaf), ptr<int64_t>(sg.unit_item0), item_ptr,
+                    ptr<uint32_t>(sg.items), cap.units, ctx->shp.unit, ptr<uint32_t>(sg.unit_cnt),
+                    ptr<int64_t>(sg.row_ptr), ptr<uint32_t>(sg.rows), tre, ptr<uint32_t>(sg.tmask), status, nullptr, s,
+                    L, unit_ptr + nleaf), "tile (emit)");
+  // mean-field segments
+  const int seg = ctx->shp.seg;
+  CK(launch_seg_counts(ptr<int64_t>(sg.row_ptr), ng, seg, ptr<uint32_t>(ctx->seg_cnt), s, L), "segments");
+  CK(exclusive_scan_u32_i64(ptr<uint32_t>(ctx->seg_cnt), ptr<int64_t>(ctx->seg_ptr), ng, ptr<int64_t>(ctx->scan_tmp),
+                            s, L), "scan");
+  CapCheck c3 = base;
+  c3.total[0] = ptr<int64_t>(ctx->seg_ptr) + ng; c3.cap[0] = cap.segs; c3.slot[0] = 3;
+  c3.zero[0] = ptr<int64_t>(ctx->seg_ptr); c3.zero_n[0] = ng + 1;
+  CK(launch_cap_check(c3, s, L), "capacity check");
+  CK(launch_seg_map(ptr<int64_t>(sg.row_ptr), ptr<int64_t>(ctx->seg_ptr), ng, seg, ptr<uint32_t>(ctx->seg_row),
+                    ptr<int64_t>(ctx->seg_begin), s, L), "segment map");
+  ctx->n_seg_max = cap.segs;
+  ctx->seg_len = seg;
+  sg.n_items = cap.items;
+  sg.n_units = cap.units;
+  sg.n_pairs = sd.n_pairs = ctx->n_pairs = cap.pairs;
+  ctx->pairs_ready = true;
+  return DMB_OK;
+}
+
 // ---- surrogate helpers ---------------------------------------------------------------------
 double alpha_of(int n) { return pow(2.0, (n + 5) / 2.0) * tgamma(3.0 + n / 2.0) / sqrt(M_PI); }
 
@@ -547,6 +649,7 @@ dmb_status surrogate_rates(dmb_ctx *ctx, const MlpRun &mr, const SegView &sv, co
     a.status = ptr<uint32_t>(ctx->status);
     a.skip_commit = ctx->tc_skip_commit ? 1 : 0;
     ctx->tc_skip_commit = false;
+    a.n_dev = ctx->capturing ? ctx->pairs_dev : nullptr;
     if (!ensure(ctx->tc_tiles, (size_t)n_q * 4)) return fail(ctx, DMB_ERR_OOM, "surrogate pair rows");
     CK(mlp_tc_pair_rates(a, ptr<uint32_t>(ctx->tc_tiles), ctx->shp.tc_wg, s, &ctx->launches),
        "surrogate rates (tensor cores)");
@@ -581,12 +684,13 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
     CK(cudaMemsetAsync(ctx->mlp_fallback.p, 0, 8, ctx->stream), "memset");
     if (!ensure(ctx->mlp_rates, (size_t)ctx->sg.n_pairs * 8 + 8)) return fail(ctx, DMB_ERR_OOM, "surrogate rates");
     mr.rates = ptr<float2>(ctx->mlp_rates);
+    const bool tm = ctx->timing && !ctx->capturing;
     if (sizeof(R) == 4) {
-      if (ctx->timing) CK(cudaEventRecord(ctx->sev[0], ctx->stream), "event");
+      if (tm) CK(cudaEventRecord(ctx->sev[0], ctx->stream), "event");
       const dmb_status st = surrogate_rates(ctx, mr, sv, ptr<int64_t>(ctx->sg.row_ptr), ctx->gas.n, nullptr,
                                             ctx->sg.n_pairs);
       if (st != DMB_OK) return st;
-      if (ctx->timing) {
+      if (tm) {
         CK(cudaEventRecord(ctx->sev[1], ctx->stream), "event");
         ctx->sev_pending = true;
       }
@@ -626,6 +730,7 @@ dmb_status mc_impl(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, uint
   a.p_total = ptot;
   a.block_sums = ptr<double>(ctx->mc_blocks);
   a.block_max = ptr<double>(ctx->mc_max);
+  if (ctx->capturing) a.step_dev = ptr<unsigned long long>(ctx->step_dev);   // set before each replay
   if (!ensure(ctx->mc_rec, (size_t)D.n * sizeof(McRec))) return fail(ctx, DMB_ERR_OOM, "MC scratch");
   if (D.n > 0)
     CK(launch_mc<R>(D, G, ctx->bx, ptr<int64_t>(ctx->sd.row_ptr), ptr<uint32_t>(ctx->sd.rows),
@@ -867,6 +972,7 @@ dmb_status substep_graph(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int
   CK(cudaGraphLaunch(ent->exec, ctx->gstream), "graph launch");
   ctx->launches += ent->launches;
   ctx->graph_next_step = substep + 1;
+  ctx->batch_next_step = ~0ull;
   CK(cudaEventRecord(ctx->gev[1], ctx->gstream), "event");
   CK(cudaStreamWaitEvent(ctx->stream, ctx->gev[1], 0), "event wait");
   return DMB_OK;
@@ -959,6 +1065,7 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
   if (ctx->gstream) cudaStreamSynchronize(ctx->gstream);
   clear_graphs(ctx);
+  clear_batch_graph(ctx);
   for (int k = 0; k < 2; ++k)
     if (ctx->gev[k]) cudaEventDestroy(ctx->gev[k]);
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
@@ -976,7 +1083,7 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
                     &ctx->act_gas, &ctx->act_start, &ctx->act_seg_ptr, &ctx->act_seg_row, &ctx->act_seg_begin,
                     &ctx->act_len, &ctx->act_segs, &ctx->act_gpairs, &ctx->act_dpairs, &ctx->act_pick,
                     &ctx->step_dev, &ctx->bin_keys, &ctx->bin_keys1, &ctx->bin_vals1, &ctx->tc_tiles,
-                    &ctx->rebin_cnt};
+                    &ctx->rebin_cnt, &ctx->gate, &ctx->cap_need};
   for (DevBuf *b : bufs) release(*b);
   SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};
   for (SpeciesBufs *s : sp) {
@@ -1045,6 +1152,8 @@ dmb_status dmb_mc_scatter_dm(dmb_ctx *ctx, uint64_t step, double dt, double *vel
 
 static dmb_status step_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t step, double dt,
                             double *sums_out);
+static dmb_status step_batched_graph(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, const dmb_box *boxes,
+                                     int nbox, uint64_t step, double dt, double *sums_out);
 
 dmb_status dmb_step(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t step, double dt, double *sums_out) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
@@ -1096,11 +1205,39 @@ dmb_status dmb_step_batched(dmb_ctx *ctx, const dmb_dm *dm, const uint32_t *dm_b
     return fail(ctx, DMB_ERR_OOM, "box tables");
   CK(cudaMemcpy(ctx->box_sides.p, sides.data(), sizeof(BoxSide) * nbox, cudaMemcpyHostToDevice), "box table");
   CK(cudaMemcpy(ctx->box_params.p, bp.data(), sizeof(BoxParamDev) * nbox, cudaMemcpyHostToDevice), "box table");
+  // frame of the virtual space: boxes side by side along x, each in a slot of width `stride`
+  {
+    const int64_t ntot = (dm ? dm->n : 0) + (gas ? gas->n : 0);
+    int box_bits = 0;
+    while ((1 << box_bits) < nbox) ++box_bits;
+    int bits = (int)fmin(21.0, fmax(10.0, ceil(log2((double)(ntot > 1 ? ntot : 2)) / 3.0) + 7.0));
+    bits = (int)fmin((double)bits, floor((63.0 - box_bits) / 3.0));
+    Frame f;
+    for (int c = 0; c < 3; ++c) f.origin[c] = 0.0;
+    f.span = fmax(nbox * ctx->stride, Lmax);
+    int e;
+    frexp(f.span, &e);
+    f.delta = ldexp(1.0, e - 23);
+    f.inv_delta = ldexp(1.0, 23 - e);
+    f.bits = bits;
+    f.key_scale = ldexp(1.0, bits) / (Lmax * (1.0 + 1e-12));
+    f.pad = (float)(4.0 * ldexp(1.0, e) * 1.1920928955078125e-07);
+    f.hmax_dm = f.hmax_gas = 0.0;
+    CK(cudaMemcpy(ctx->frame.p, &f, sizeof(Frame), cudaMemcpyHostToDevice), "frame");
+  }
+  ctx->frame_ready = true;
   ctx->nbox = nbox;
   ctx->dm_box = dm_box;
   ctx->gas_box = gas_box;
   ctx->bx.boxes = ptr<BoxSide>(ctx->box_sides);
-  const dmb_status st = step_body(ctx, dm, gas, step, dt, sums_out);
+  dmb_status st;
+  if (ctx->use_graph && dm && gas) {
+    st = (dm->n > 0 && gas->n > 0) ? step_batched_graph(ctx, dm, gas, boxes, nbox, step, dt, sums_out)
+                                   : step_body(ctx, dm, gas, step, dt, sums_out);
+  } else {
+    st = step_body(ctx, dm, gas, step, dt, sums_out);
+  }
+  ctx->frame_ready = false;
   ctx->nbox = 0;
   ctx->dm_box = ctx->gas_box = nullptr;
   ctx->bx.boxes = nullptr;
@@ -1110,11 +1247,16 @@ dmb_status dmb_step_batched(dmb_ctx *ctx, const dmb_dm *dm, const uint32_t *dm_b
 static dmb_status step_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t step, double dt,
                             double *sums_out) {
   dmb_status st;
-  const bool tm = ctx->timing;
+  const bool tm = ctx->timing && !ctx->capturing;
   if (tm) CK(cudaEventRecord(ctx->ev[0], ctx->stream), "event");
   if ((st = build_grid_checked(ctx, dm, gas)) != DMB_OK) return st;
   if (tm) CK(cudaEventRecord(ctx->ev[1], ctx->stream), "event");
-  if ((st = dmb_neighbors(ctx, nullptr, nullptr, 0)) != DMB_OK) return st;
+  if (ctx->capturing) {
+    st = ctx->p.fp64 ? neighbors_capped<double>(ctx) : neighbors_capped<float>(ctx);
+    if (st != DMB_OK) return st;
+  } else if ((st = dmb_neighbors(ctx, nullptr, nullptr, 0)) != DMB_OK) {
+    return st;
+  }
   if (tm) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
   const int64_t ng = gas->n, nd = dm->n;
   if (!ensure(ctx->mf_acc, ng * 24) || !ensure(ctx->mf_dudt, ng * 8) || !ensure(ctx->e_exp, ng * 8))
@@ -1132,7 +1274,8 @@ static dmb_status step_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, 
   if (!ensure(ctx->kick_blocks, (size_t)kb * KICK_NSUM * 8)) return fail(ctx, DMB_ERR_OOM, "kick partials");
   CK(launch_kick_gas(const_cast<double *>(gas->vel), const_cast<double *>(gas->T), gas->mu, gas->mass,
                      ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp), ng, dt,
-                     ctx->rc.kT_over_mp, ptr<double>(ctx->kick_blocks), kb, ctx->stream, &ctx->launches), "kick");
+                     ctx->rc.kT_over_mp, ptr<double>(ctx->kick_blocks), kb, ctx->stream, &ctx->launches,
+                     ctx->capturing ? ctx->gate_dev : nullptr), "kick");
   if (nd <= 0) {
     CK(cudaMemsetAsync(ctx->mc_blocks.p ? ctx->mc_blocks.p : ctx->sums.p, 0, 8, ctx->stream), "memset");
   }
@@ -1140,7 +1283,8 @@ static dmb_status step_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, 
   if (nd <= 0 && !ensure(ctx->mc_blocks, 64)) return fail(ctx, DMB_ERR_OOM, "mc partials");
   if (nd <= 0 && !ensure(ctx->mc_max, 64)) return fail(ctx, DMB_ERR_OOM, "mc partials");
   CK(launch_final_sums(ptr<double>(ctx->mc_blocks), ptr<double>(ctx->mc_max), mnb, ptr<double>(ctx->kick_blocks), kb,
-                       dt, (double)ctx->n_pairs, ptr<double>(ctx->sums), ctx->stream, &ctx->launches), "sums");
+                       dt, (double)ctx->n_pairs, ptr<double>(ctx->sums), ctx->stream, &ctx->launches,
+                       ctx->capturing ? ctx->pairs_dev : nullptr), "sums");
   ctx->grid_ready = false;   // the state moved on: rebuild before the next standalone call
   ctx->pairs_ready = false;
   if (tm) {
@@ -1164,6 +1308,138 @@ static dmb_status step_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, 
     CK(cudaStreamSynchronize(ctx->stream), "synchronise");
     memcpy(sums_out, ctx->h_sums, 16 * 8);
   }
+  return DMB_OK;
+}
+
+// Buffers of a captured batched step at the capacities (every other buffer depends only on the
+// particle counts and was sized by the eager step before the capture).
+static dmb_status presize_batch(dmb_ctx *ctx) {
+  const dmb_ctx::BatchCaps &c = ctx->bgraph.caps;
+  SearchBufs &sg = ctx->sg, &sd = ctx->sd;
+  const size_t rb = ctx->p.fp64 ? 8 : 4;
+  bool ok = ensure(sg.items, (size_t)c.items * 4) && ensure(sg.tmask, (size_t)c.items * 32 * 4) &&
+            ensure(sg.unit_leaf, (size_t)c.units * 4) && ensure(sg.unit_item0, (size_t)c.units * 8) &&
+            ensure(sg.unit_cnt, (size_t)c.units * 32 * 4) && ensure(sg.rows, (size_t)c.pairs * 4) &&
+            ensure(sd.rows, (size_t)c.pairs * 4) && ensure(ctx->pcache, (size_t)c.pairs * rb) &&
+            ensure(ctx->seg_row, (size_t)c.segs * 4) && ensure(ctx->seg_begin, (size_t)c.segs * 8) &&
+            ensure(ctx->mf_part, (size_t)c.segs * 6 * rb) && ensure(ctx->gate, 16) && ensure(ctx->cap_need, 64) &&
+            ensure(ctx->step_dev, 8);
+  if (ok && ctx->rc.rate_mode == DMB_RATE_MLP)
+    ok = ensure(ctx->mlp_rates, (size_t)c.pairs * 8 + 8) && ensure(ctx->tc_tiles, (size_t)c.pairs * 4);
+  if (!ok) return fail(ctx, DMB_ERR_OOM, "device allocation failed for the captured batched step");
+  return DMB_OK;
+}
+
+// dmb_step_batched under dmb_set_graph(ctx, 1).  The first call for a set of caller arrays and
+// boxes (or after an overflow) runs the step directly, then sizes every list buffer to 1.25 x the
+// sizes it found and captures the whole step (grid, search, mean field, Monte Carlo, kicks, sums,
+// and the advance of the device step counter) into one CUDA graph on the library's stream.  Later
+// calls replay it with one graph launch and read back the status, the list totals and the sums.
+// If a list outgrew its capacity the replayed step changed nothing (the capacity checks cleared
+// the lists and gated the kick): the buffers are regrown and the step runs again directly.
+static dmb_status step_batched_graph(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, const dmb_box *boxes,
+                                     int nbox, uint64_t step, double dt, double *sums_out) {
+  dmb_ctx::BatchGraph &bg = ctx->bgraph;
+  const void *key[14] = {dm->pos, dm->vel, dm->mass, dm->h, dm->id, gas->pos, gas->vel, gas->mass,
+                         gas->h, gas->T, gas->mu, gas->id, ctx->dm_box, ctx->gas_box};
+  if (!ctx->gstream) {
+    CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking), "graph stream");
+    for (int k = 0; k < 2; ++k) CK(cudaEventCreateWithFlags(&ctx->gev[k], cudaEventDisableTiming), "graph event");
+  }
+  const bool hit = bg.valid && bg.exec && bg.nd == dm->n && bg.ng == gas->n && bg.dt == dt &&
+                   memcmp(bg.key, key, sizeof(key)) == 0 && (int)bg.boxes.size() == nbox &&
+                   memcmp(bg.boxes.data(), boxes, sizeof(dmb_box) * (size_t)nbox) == 0;
+  int64_t grow[4] = {0, 0, 0, 0};
+  if (hit) {
+    CK(cudaEventRecord(ctx->gev[0], ctx->stream), "event");
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0), "event wait");
+    if (ctx->batch_next_step != step)
+      CK(launch_step_set(ptr<unsigned long long>(ctx->step_dev), step, ctx->gstream, &ctx->launches), "step counter");
+    CK(cudaGraphLaunch(bg.exec, ctx->gstream), "graph launch");
+    ctx->launches += bg.launches;
+    ctx->batch_next_step = step + 1;
+    ctx->graph_next_step = ~0ull;
+    CK(cudaEventRecord(ctx->gev[1], ctx->gstream), "event");
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->gev[1], 0), "event wait");
+    // the outcome: status word, list totals and sums, with one synchronisation
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->status.p, 4, cudaMemcpyDeviceToHost, ctx->stream), "status readback");
+    CK(cudaMemcpyAsync(ctx->h_tot, ctx->cap_need.p, 4 * 8, cudaMemcpyDeviceToHost, ctx->stream), "totals readback");
+    CK(cudaMemcpyAsync(ctx->h_sums, ctx->sums.p, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream), "sums readback");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronise");
+    const uint32_t stw = *ctx->h_status;
+    if (stw == 0u) {
+      if (sums_out) memcpy(sums_out, ctx->h_sums, 16 * 8);
+      return DMB_OK;
+    }
+    if (stw != DMB_BAD_OVERFLOW) return check_status(ctx);   // bad inputs: reported as the direct step would
+    // a list outgrew its buffer: nothing was applied; regrow from the totals and run directly
+    CK(cudaMemsetAsync(ctx->status.p, 0, 4, ctx->stream), "status reset");
+    for (int k = 0; k < 4; ++k) grow[k] = ctx->h_tot[k];
+    clear_batch_graph(ctx);
+  }
+  // the step itself, directly
+  dmb_status st = step_body(ctx, dm, gas, step, dt, sums_out);
+  if (st != DMB_OK) return st;
+  // capacities for the replays: the sizes just found (or the overflowing totals) plus a quarter
+  clear_batch_graph(ctx);
+  const SearchBufs &sg = ctx->sg;
+  auto cap = [](int64_t a, int64_t b) { return (a > b ? a : b) + (a > b ? a : b) / 4 + 4096; };
+  dmb_ctx::BatchCaps c;
+  c.items = cap(sg.n_items, grow[0]);
+  c.units = cap(sg.n_units, grow[1]);
+  c.pairs = cap(sg.n_pairs, grow[2]);
+  c.segs = gas->n + c.pairs / ctx->shp.seg + 1;   // every row has at most len / seg + 1 segments
+  bg.caps = c;
+  if ((st = presize_batch(ctx)) != DMB_OK) return st;
+  // capture on the library's stream
+  cudaStream_t saved = ctx->stream;
+  const int64_t l0 = ctx->launches;
+  ctx->stream = ctx->gstream;
+  ctx->capturing = true;
+  ctx->pairs_dev = ptr<int64_t>(ctx->sg.row_ptr) + gas->n;
+  ctx->gate_dev = ptr<uint32_t>(ctx->gate);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
+  st = DMB_ERR_CUDA;
+  if (e == cudaSuccess) {
+    e = cudaMemsetAsync(ctx->gate.p, 0, 4, ctx->gstream);
+    if (e == cudaSuccess) {
+      st = step_body(ctx, dm, gas, step, dt, nullptr);
+      if (st == DMB_OK) {
+        const cudaError_t ei = launch_step_advance(ptr<unsigned long long>(ctx->step_dev), ctx->gstream, &ctx->launches);
+        if (ei != cudaSuccess) st = cuda_fail(ctx, ei, "step counter");
+      }
+    } else {
+      st = cuda_fail(ctx, e, "graph capture");
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(ctx->gstream, &g);
+    if (st == DMB_OK && e2 != cudaSuccess) st = cuda_fail(ctx, e2, "graph capture");
+  } else {
+    st = cuda_fail(ctx, e, "graph capture");
+  }
+  ctx->stream = saved;
+  ctx->capturing = false;
+  ctx->pairs_dev = nullptr;
+  ctx->gate_dev = nullptr;
+  bg.launches = ctx->launches - l0;
+  ctx->launches = l0;
+  if (st != DMB_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  e = cudaGraphInstantiate(&bg.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    bg.exec = nullptr;
+    return cuda_fail(ctx, e, "graph instantiate");
+  }
+  bg.valid = true;
+  memcpy(bg.key, key, sizeof(key));
+  bg.nd = dm->n;
+  bg.ng = gas->n;
+  bg.dt = dt;
+  bg.boxes.assign(boxes, boxes + nbox);
+  ctx->batch_next_step = ~0ull;
   return DMB_OK;
 }
 
@@ -1208,7 +1484,10 @@ dmb_status dmb_substep_info(dmb_ctx *ctx, uint64_t substep, int64_t *out5) {
 dmb_status dmb_set_mc_variant(dmb_ctx *ctx, int32_t variant) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
   if (variant != 0 && variant != 1) return fail(ctx, DMB_ERR_ARG, "variant must be 0 or 1");
-  if (variant != ctx->mc_variant) clear_graphs(ctx);   // captured substeps hold the old kernel
+  if (variant != ctx->mc_variant) {   // captured steps hold the old kernel
+    clear_graphs(ctx);
+    clear_batch_graph(ctx);
+  }
   ctx->mc_variant = variant;
   return DMB_OK;
 }
@@ -1257,6 +1536,7 @@ dmb_status dmb_set_anisotropy(dmb_ctx *ctx, double beta) {
 dmb_status dmb_set_graph(dmb_ctx *ctx, int on) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
   ctx->use_graph = on != 0;
+  if (!ctx->use_graph) clear_batch_graph(ctx);
   return DMB_OK;
 }
 
@@ -1444,6 +1724,89 @@ dmb_status dmb_get_shapes(dmb_ctx *ctx, int32_t *shapes_out) {
   return DMB_OK;
 }
 
+// ---- persisted launch shapes -----------------------------------------------------------------
+// The file is one JSON object {"key": [unit, seg, mf_blocks, mc_blocks, warpgroups], ...}; keys are
+// made of letters, digits and "._+-".  Read and written whole, entries of other keys kept.
+static bool shapes_key_ok(const char *k) {
+  if (!k || !*k) return false;
+  for (const char *c = k; *c; ++c)
+    if (!(isalnum((unsigned char)*c) || *c == '.' || *c == '_' || *c == '+' || *c == '-')) return false;
+  return strlen(k) < 200;
+}
+
+static std::vector<std::pair<std::string, std::vector<long>>> shapes_read(const char *path) {
+  std::vector<std::pair<std::string, std::vector<long>>> out;
+  FILE *f = fopen(path, "rb");
+  if (!f) return out;
+  std::string txt;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof(buf), f)) > 0 && txt.size() < (1u << 20)) txt.append(buf, n);
+  fclose(f);
+  size_t i = 0;
+  while ((i = txt.find('"', i)) != std::string::npos) {
+    const size_t j = txt.find('"', i + 1);
+    if (j == std::string::npos) break;
+    std::string key = txt.substr(i + 1, j - i - 1);
+    const size_t a = txt.find('[', j), b = txt.find(']', j);
+    if (a == std::string::npos || b == std::string::npos || b < a) break;
+    std::vector<long> v;
+    const char *c = txt.c_str() + a + 1;
+    while (c < txt.c_str() + b) {
+      char *end = nullptr;
+      const long x = strtol(c, &end, 10);
+      if (end == c) { ++c; continue; }
+      v.push_back(x);
+      c = end;
+    }
+    out.emplace_back(key, v);
+    i = b + 1;
+  }
+  return out;
+}
+
+dmb_status dmb_save_shapes(dmb_ctx *ctx, const char *path, const char *key) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!path || !shapes_key_ok(key)) return fail(ctx, DMB_ERR_ARG, "path is NULL or the key is not [A-Za-z0-9._+-]+");
+  auto entries = shapes_read(path);
+  int32_t v[5];
+  get_shapes(ctx, v);
+  std::vector<long> cur(v, v + 5);
+  bool found = false;
+  for (auto &e : entries)
+    if (e.first == key) { e.second = cur; found = true; }
+  if (!found) entries.emplace_back(key, cur);
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE *f = fopen(tmp.c_str(), "wb");
+  if (!f) return fail(ctx, DMB_ERR_ARG, "cannot write the shapes file");
+  fprintf(f, "{\n");
+  for (size_t k = 0; k < entries.size(); ++k) {
+    fprintf(f, "  \"%s\": [", entries[k].first.c_str());
+    for (size_t m = 0; m < entries[k].second.size(); ++m) fprintf(f, "%s%ld", m ? ", " : "", entries[k].second[m]);
+    fprintf(f, "]%s\n", k + 1 < entries.size() ? "," : "");
+  }
+  fprintf(f, "}\n");
+  const bool ok = fclose(f) == 0 && rename(tmp.c_str(), path) == 0;
+  if (!ok) return fail(ctx, DMB_ERR_ARG, "cannot write the shapes file");
+  return DMB_OK;
+}
+
+dmb_status dmb_load_shapes(dmb_ctx *ctx, const char *path, const char *key) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (!path || !shapes_key_ok(key)) return fail(ctx, DMB_ERR_ARG, "path is NULL or the key is not [A-Za-z0-9._+-]+");
+  for (auto &e : shapes_read(path)) {
+    if (e.first != key) continue;
+    if (e.second.size() != 5) return fail(ctx, DMB_ERR_ARG, "malformed shapes entry");
+    int32_t v[5];
+    for (int k = 0; k < 5; ++k) v[k] = (int32_t)e.second[k];
+    dmb_status st;
+    if ((st = check_shapes(ctx, v)) != DMB_OK) return st;
+    set_shapes(ctx, v);
+    return DMB_OK;
+  }
+  return fail(ctx, DMB_ERR_STATE, "no shapes stored under this key");
+}
+
 dmb_status dmb_set_timing(dmb_ctx *ctx, int on) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
   if (on && !ctx->ev[0]) {
@@ -1475,20 +1838,26 @@ dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, u
   cudaStream_t s = ctx->stream;
   const auto t0 = std::chrono::steady_clock::now();
   // training box and power-law indices: {-4, -2, 0, 2} and the context's n
+  // the samples reach a quarter decade beyond the box in tau and m_chi (the box the network answers
+  // for is unchanged), so that its corners are not the edge of what it has seen
   MlpDataSpec spec;
+  const double margin = 0.25;
   spec.log_s_lo = ctx->mlp_box[0]; spec.log_s_hi = ctx->mlp_box[1];
-  spec.log_tau_lo = ctx->mlp_box[2]; spec.log_tau_hi = ctx->mlp_box[3];
-  spec.log_m_lo = ctx->mlp_box[4]; spec.log_m_hi = ctx->mlp_box[5];
+  spec.log_tau_lo = ctx->mlp_box[2] - margin; spec.log_tau_hi = ctx->mlp_box[3] + margin;
+  spec.log_m_lo = ctx->mlp_box[4] - margin; spec.log_m_hi = ctx->mlp_box[5] + margin;
   // the screened law has one normalisation (n = 0) and takes tau as varsigma^2 / v_c^2
   std::vector<int> ns = {-4, -2, 0, 2};
   if (std::find(ns.begin(), ns.end(), ctx->p.n) == ns.end()) ns.push_back(ctx->p.n);
   if (ctx->xsec == 1) ns = {0};
   spec.scr = ctx->xsec == 1 ? 1 : 0;
-  spec.n_count = (int)ns.size();
+  // n = -4 (the 1F1 with the most curvature across the envelope's transition) is drawn twice as often
+  std::vector<int> draw = ns;
+  if (std::find(ns.begin(), ns.end(), -4) != ns.end()) draw.push_back(-4);
+  spec.n_count = (int)draw.size();
   for (int k = 0; k < spec.n_count; ++k) {
-    spec.n_values[k] = ns[k];
-    spec.alpha[k] = alpha_of(ns[k]);
-    envelope(ns[k], spec.cA[k], spec.eA[k], spec.cB[k], spec.eB[k]);
+    spec.n_values[k] = draw[k];
+    spec.alpha[k] = alpha_of(draw[k]);
+    envelope(draw[k], spec.cA[k], spec.eA[k], spec.cB[k], spec.eB[k]);
   }
   const int B = 4096;
   const int64_t N = nsamples, Nval = N / 10, Ntr = N - Nval;
@@ -1530,8 +1899,47 @@ dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, u
   for (int64_t k = 0; k < Ntr; ++k) perm[k] = (int)k;
   int t_adam = 0;
   const float lr0 = 2e-3f, lr1 = 2e-5f;
+  // The last quarter of the epochs weights the worst-fitted samples: every fourth of those epochs the
+  // network's error on every training sample is measured, and each epoch then draws the worst eighth
+  // four times over and a random half of the rest, so the worst-case error falls with the mean.
+  const int hard_from = epochs >= 8 ? epochs - epochs / 4 : epochs;
+  std::vector<float> yp, yh;
+  std::vector<int> order;
+  DevBuf Yp;
+  if (hard_from < epochs && !ensure(Yp, (size_t)Ntr * 8)) {
+    cleanup();
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for surrogate training");
+  }
   for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
-    std::shuffle(perm.begin(), perm.end(), rng);
+    if (ep >= hard_from) {
+      if ((ep - hard_from) % 4 == 0) {
+        yp.resize((size_t)Ntr * 2);
+        yh.resize((size_t)Ntr * 2);
+        e = mlp_infer(d, ptr<float>(X), Ntr, ptr<float>(Yp), s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(yp.data(), Yp.p, (size_t)Ntr * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(yh.data(), Y.p, (size_t)Ntr * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        std::vector<float> err(Ntr);
+        for (int64_t k = 0; k < Ntr; ++k)
+          err[k] = fmaxf(fabsf(yp[2 * k] - yh[2 * k]), fabsf(yp[2 * k + 1] - yh[2 * k + 1]));
+        order.resize(Ntr);
+        for (int64_t k = 0; k < Ntr; ++k) order[k] = (int)k;
+        const int64_t nh = Ntr / 8;
+        std::nth_element(order.begin(), order.begin() + nh, order.end(),
+                         [&](int a, int b) { return err[a] > err[b]; });
+      }
+      // worst eighth x 4 + half of the rest = Ntr draws
+      const int64_t nh = Ntr / 8;
+      std::shuffle(order.begin() + nh, order.end(), rng);
+      int64_t q = 0;
+      for (int rep = 0; rep < 4; ++rep)
+        for (int64_t k = 0; k < nh && q < Ntr; ++k) perm[q++] = order[k];
+      for (int64_t k = nh; q < Ntr; ++k) perm[q++] = order[k];
+      std::shuffle(perm.begin(), perm.end(), rng);
+    } else {
+      std::shuffle(perm.begin(), perm.end(), rng);
+    }
     e = cudaMemcpyAsync(idx.p, perm.data(), Ntr * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // perm is reused next epoch
     for (int b = 0; b < steps_per_epoch && e == cudaSuccess; ++b) {
@@ -1542,23 +1950,45 @@ dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, u
                           &ctx->launches);
     }
   }
-  // last batch loss and the validation errors of FA, FB (relative)
-  std::vector<float> lossh(MLP_TRAIN_BLOCKS), yv(Nval * 2), yt(Nval * 2);
-  if (e == cudaSuccess) e = mlp_infer(d, ptr<float>(X) + Ntr * 4, Nval, ptr<float>(Yv), s);
+  release(Yp);
+  // last batch loss and the validation errors of FA, FB (relative), on the engine that evaluates
+  // the pairs, over the held-out samples inside the box the network answers for
+  std::vector<float> lossh(MLP_TRAIN_BLOCKS), yv(Nval * 2), yt(Nval * 2), xv(Nval * 4);
+  if (e == cudaSuccess) {
+    if (ctx->mlp_engine == 0) {
+      TcArgs ta = {};
+      ta.p = d.p;
+      ta.w2 = d.w2;
+      ta.w3 = d.w3;
+      ta.n = Nval;
+      ta.X = ptr<float>(X) + Ntr * 4;
+      ta.Y = ptr<float>(Yv);
+      ta.status = ptr<uint32_t>(ctx->status);
+      e = mlp_tc_infer(ta, ctx->shp.tc_wg, s, &ctx->launches);
+    } else {
+      e = mlp_infer(d, ptr<float>(X) + Ntr * 4, Nval, ptr<float>(Yv), s);
+    }
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(lossh.data(), loss.p, MLP_TRAIN_BLOCKS * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(yv.data(), Yv.p, Nval * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(yt.data(), ptr<float>(Y) + Ntr * 2, Nval * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(xv.data(), ptr<float>(X) + Ntr * 4, Nval * 16, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cleanup();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "surrogate training");
   double lsum = 0.0;
   for (float v : lossh) lsum += v;
   double mxA = 0, mxB = 0, meA = 0, meB = 0;
+  int64_t nin = 0;
   for (int64_t k = 0; k < Nval; ++k) {
+    const double lt = 2.0 * (double)xv[4 * k + 1], lm = (double)xv[4 * k + 2];
+    if (lt < ctx->mlp_box[2] || lt > ctx->mlp_box[3] || lm < ctx->mlp_box[4] || lm > ctx->mlp_box[5]) continue;
     const double ea = fabs(expm1((double)yv[2 * k] - (double)yt[2 * k]));
     const double eb = fabs(expm1((double)yv[2 * k + 1] - (double)yt[2 * k + 1]));
     mxA = fmax(mxA, ea); mxB = fmax(mxB, eb); meA += ea; meB += eb;
+    ++nin;
   }
+  if (nin == 0) nin = 1;
   ctx->mlp_ready = true;
   ctx->mlp_n = ns;
   ctx->mlp_family = ctx->xsec;
@@ -1566,8 +1996,8 @@ dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, u
     report[0] = lsum / ((double)B * MLP_OUT);
     report[1] = mxA;
     report[2] = mxB;
-    report[3] = meA / (double)Nval;
-    report[4] = meB / (double)Nval;
+    report[3] = meA / (double)nin;
+    report[4] = meB / (double)nin;
     report[5] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     report[6] = (double)t_adam;
     report[7] = (double)N;
@@ -1648,7 +2078,8 @@ dmb_status dmb_set_surrogate_engine(dmb_ctx *ctx, int32_t engine) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
   if (engine != 0 && engine != 1) return fail(ctx, DMB_ERR_ARG, "engine must be 0 (tcgen05) or 1 (mma.sync)");
   ctx->mlp_engine = engine;
-  clear_graphs(ctx);   // captured substeps hold the other engine's launches
+  clear_graphs(ctx);   // captured steps hold the other engine's launches
+  clear_batch_graph(ctx);
   return DMB_OK;
 }
 

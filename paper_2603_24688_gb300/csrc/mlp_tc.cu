@@ -382,6 +382,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
   bool skip_commit = a.skip_commit != 0 && blockIdx.x == 0 && g == 0;
   const uint64_t wait_ns = a.wait_ns ? a.wait_ns : 2000000000ull;
   const float alpha = (float)a.rc.alpha;
+  if (a.n_dev != nullptr) a.n = min(a.n, *a.n_dev);   // rows counted on the device (captured steps)
   const int64_t n_tiles = (a.n + TC_ROWS - 1) / TC_ROWS;
   const int64_t stride = (int64_t)gridDim.x * NWG;
 
@@ -615,10 +616,20 @@ static cudaError_t launch_tc(const TcArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// nwg: 2..4 independent warpgroups (one tile each)
+template <int MODE>
+static cudaError_t launch_any(const TcArgs &a, int nwg, cudaStream_t s) {
+  switch (nwg) {
+    case 2: return launch_tc<2, MODE, true>(a, s);
+    case 3: return launch_tc<3, MODE>(a, s);
+    default: return launch_tc<4, MODE>(a, s);
+  }
+}
+
 cudaError_t mlp_tc_infer(TcArgs a, int nwg, cudaStream_t s, int64_t *launches) {
   if (a.n <= 0) return cudaSuccess;
   if (launches) *launches += 1;
-  return nwg == 2 ? launch_tc<2, MODE_X, true>(a, s) : nwg == 4 ? launch_tc<4, MODE_X>(a, s) : launch_tc<3, MODE_X>(a, s);
+  return launch_any<MODE_X>(a, nwg, s);
 }
 
 cudaError_t mlp_tc_pair_rates(TcArgs a, uint32_t *prow, int nwg, cudaStream_t s, int64_t *launches) {
@@ -628,6 +639,5 @@ cudaError_t mlp_tc_pair_rates(TcArgs a, uint32_t *prow, int nwg, cudaStream_t s,
   k_pair_rows<<<(unsigned)blocks, 256, 0, s>>>(a.R_ptr, a.n_rows, prow);
   a.prow = prow;
   if (launches) *launches += 2;
-  return nwg == 2 ? launch_tc<2, MODE_PAIRS, true>(a, s)
-                  : nwg == 4 ? launch_tc<4, MODE_PAIRS>(a, s) : launch_tc<3, MODE_PAIRS>(a, s);
+  return launch_any<MODE_PAIRS>(a, nwg, s);
 }

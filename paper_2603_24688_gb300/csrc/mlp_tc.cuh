@@ -34,6 +34,8 @@ struct TcArgs {
   // fault injection for the timeout path: warpgroup 0 of CTA 0 omits the commit of its first
   // layer-1 MMA, so its wait runs out; the launcher then uses a 1 ms limit
   int skip_commit;
+  // captured steps: the row count lives on the device (n is then a capacity); null otherwise
+  const int64_t *n_dev;
 };
 
 // Shared-memory attributes (call once before any graph capture).

@@ -53,7 +53,22 @@ cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const F
                         const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
                         const uint32_t *items, int64_t n_units, int unit, uint32_t *unit_cnt, const int64_t *row_ptr,
                         uint32_t *rows, TransposeOut tr, uint32_t *tmask, uint32_t *status, unsigned long long *stats,
-                        cudaStream_t s, int64_t *launches);
+                        cudaStream_t s, int64_t *launches, const int64_t *n_units_dev = nullptr);
+// Capacity check of a captured step (the host sized the buffers before capture and reads no
+// count back): totals [k] against cap [k], written to need[slot[k]]; on overflow gate = 1, the
+// status gets DMB_BAD_OVERFLOW and the offset arrays zero[k] (zero_n[k] entries) are cleared.
+struct CapCheck {
+  const int64_t *total[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t cap[4] = {0, 0, 0, 0};
+  int slot[4] = {0, 0, 0, 0};
+  int64_t *zero[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t zero_n[4] = {0, 0, 0, 0};
+  int64_t *need = nullptr;
+  uint32_t *gate = nullptr;
+  uint32_t *status = nullptr;
+};
+cudaError_t launch_cap_check(const CapCheck &c, cudaStream_t s, int64_t *launches);
+
 cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, uint32_t *unit_cnt, uint32_t *counts,
                                cudaStream_t s, int64_t *launches);
 

@@ -427,7 +427,10 @@ __device__ __forceinline__ void quad_panels(R a, R b, R s, int n, R q, R &sa, R 
 // window is split at 4 / sqrt(q) and each part gets its own 8 panels.
 template <typename R>
 __device__ __forceinline__ void rates_quad(R x, int n, R alpha, R &FA, R &FB, R q = (R)0) {
-  const R s = sqrt_t((R)2 * x);
+  // w = 0 of the screened law is evaluated at w = 1e-9 varsigma (A and B are even and smooth in w;
+  // the power law takes its exact value 1 below)
+  const R s0 = sqrt_t((R)2 * x);
+  const R s = (q > (R)0 && s0 < (R)1e-9) ? (R)1e-9 : s0;
   const R a = s > (R)9 ? s - (R)9 : (R)0, b = s + (R)9;
   R sa = 0, sb = 0;
   const R split = q > (R)1 ? (R)4 / sqrt_t(q) : (R)0;
@@ -442,7 +445,7 @@ __device__ __forceinline__ void rates_quad(R x, int n, R alpha, R &FA, R &FB, R 
   const R Ahat = s > (R)0 ? c * sa / s : (R)0;
   FA = Ahat * (R)3 / alpha;
   FB = c * sb / alpha;
-  if (!(s > (R)0)) {
+  if (!(s > (R)0) && !(q > (R)0)) {
     // w = 0: FA = FB = 1 (1F1 at x = 0)
     FA = (R)1;
     FB = (R)1;

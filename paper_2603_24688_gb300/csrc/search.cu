@@ -187,7 +187,8 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
        const uint32_t *__restrict__ unit_leaf, const int64_t *__restrict__ unit_item0,
        const int64_t *__restrict__ item_ptr, const uint32_t *__restrict__ items, int64_t n_units, int unit,
        uint32_t *__restrict__ unit_cnt, const int64_t *__restrict__ row_ptr, uint32_t *__restrict__ rows,
-       TransposeOut tr, uint32_t *__restrict__ tmask, uint32_t *status, unsigned long long *__restrict__ stats) {
+       TransposeOut tr, uint32_t *__restrict__ tmask, uint32_t *status, unsigned long long *__restrict__ stats,
+       const int64_t *__restrict__ n_units_dev) {
   typedef typename Vec<R>::v4 v4;
   __shared__ v4 sP[SR_WARPS][DMB_LEAF];
   __shared__ v4 sL[SR_WARPS][DMB_LEAF];
@@ -200,7 +201,9 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
   const bool want_col = tr_on || (!EMIT && tmask != nullptr);
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long st_tests = 0, st_leaves = 0;
-  for (int64_t u = (int64_t)blockIdx.x * SR_WARPS + wib; u < n_units; u += (int64_t)gridDim.x * SR_WARPS) {
+  // n_units is a capacity when the unit count lives on the device (captured steps)
+  const int64_t nu = n_units_dev != nullptr ? min(n_units, *n_units_dev) : n_units;
+  for (int64_t u = (int64_t)blockIdx.x * SR_WARPS + wib; u < nu; u += (int64_t)gridDim.x * SR_WARPS) {
     const int a = (int)unit_leaf[u];
     const int64_t it0 = unit_item0[u];
     const int64_t it1 = min(it0 + (int64_t)unit, item_ptr[a + 1]);
@@ -400,12 +403,12 @@ cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const F
                         const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
                         const uint32_t *items, int64_t n_units, int unit, uint32_t *unit_cnt, const int64_t *row_ptr,
                         uint32_t *rows, TransposeOut tr, uint32_t *tmask, uint32_t *status, unsigned long long *stats,
-                        cudaStream_t s, int64_t *launches) {
+                        cudaStream_t s, int64_t *launches, const int64_t *n_units_dev) {
   if (n_units <= 0) return cudaSuccess;
   const int g = grid_for(n_units);
 #define TL(E, G)                                                                                                \
   k_tile<R, E, G><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items, n_units, unit, \
-                                              unit_cnt, row_ptr, rows, tr, tmask, status, stats)
+                                              unit_cnt, row_ptr, rows, tr, tmask, status, stats, n_units_dev)
   switch (geom_of(bx) * 2 + (emit ? 1 : 0)) {
     case 0: TL(false, GEOM_OPEN); break;
     case 1: TL(true, GEOM_OPEN); break;
@@ -436,6 +439,39 @@ cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, u
                                       int, uint32_t *, const int64_t *, uint32_t *, TransposeOut, uint32_t *,         \
                                       uint32_t *,                                                                    \
                                       unsigned long long *,                                                          \
-                                      cudaStream_t, int64_t *);
+                                      cudaStream_t, int64_t *, const int64_t *);
 INST(float)
 INST(double)
+
+// ---- capacity checks of a captured step ---------------------------------------------------
+// One block: the device totals against the capacities the buffers were sized for.  On overflow it
+// records the totals for the host, sets the gate and the status bit and clears the given offset
+// arrays, so every later kernel of the step sees empty rows and touches nothing out of bounds.
+__global__ void __launch_bounds__(1024) k_cap_check(CapCheck c) {
+  __shared__ int over;
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int k = 0; k < 4; ++k)
+      if (c.total[k] != nullptr) {
+        const int64_t t = *c.total[k];
+        c.need[c.slot[k]] = t;
+        if (t > c.cap[k]) o = 1;
+      }
+    over = o;
+    if (o) {
+      *c.gate = 1u;
+      atomicOr(c.status, DMB_BAD_OVERFLOW);
+    }
+  }
+  __syncthreads();
+  if (!over) return;
+  for (int k = 0; k < 4; ++k)
+    if (c.zero[k] != nullptr)
+      for (int64_t i = threadIdx.x; i < c.zero_n[k]; i += blockDim.x) c.zero[k][i] = 0;
+}
+
+cudaError_t launch_cap_check(const CapCheck &c, cudaStream_t s, int64_t *launches) {
+  k_cap_check<<<1, 1024, 0, s>>>(c);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
+}

@@ -4,10 +4,13 @@
 __global__ void __launch_bounds__(KICK_THREADS)
 k_kick_gas(double *__restrict__ vel, double *__restrict__ T, const double *__restrict__ mu,
            const double *__restrict__ mass, const double *__restrict__ acc, const double *__restrict__ dudt,
-           const double *__restrict__ e_exp, int64_t n, double dt, double kT_over_mp, double *__restrict__ out) {
+           const double *__restrict__ e_exp, int64_t n, double dt, double kT_over_mp, double *__restrict__ out,
+           const uint32_t *__restrict__ gate) {
   __shared__ double red[KICK_NSUM][KICK_THREADS];
   double s[KICK_NSUM] = {0, 0, 0, 0, 0, 0};
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+  // a captured step whose lists overflowed kicks nothing (the host repeats the step)
+  const int64_t nk = (gate != nullptr && *gate != 0u) ? 0 : n;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nk; c += (int64_t)gridDim.x * blockDim.x) {
     const double M = mass[c];
     double V[3], Vn[3];
     for (int k = 0; k < 3; ++k) {
@@ -37,8 +40,9 @@ k_kick_gas(double *__restrict__ vel, double *__restrict__ T, const double *__res
 
 cudaError_t launch_kick_gas(double *vel, double *T, const double *mu, const double *mass, const double *acc,
                             const double *dudt, const double *e_exp, int64_t n, double dt, double kT_over_mp,
-                            double *block_sums, int blocks, cudaStream_t s, int64_t *launches) {
-  k_kick_gas<<<blocks, KICK_THREADS, 0, s>>>(vel, T, mu, mass, acc, dudt, e_exp, n, dt, kT_over_mp, block_sums);
+                            double *block_sums, int blocks, cudaStream_t s, int64_t *launches,
+                            const uint32_t *gate) {
+  k_kick_gas<<<blocks, KICK_THREADS, 0, s>>>(vel, T, mu, mass, acc, dudt, e_exp, n, dt, kT_over_mp, block_sums, gate);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }
@@ -46,7 +50,8 @@ cudaError_t launch_kick_gas(double *vel, double *T, const double *mu, const doub
 // one block: every thread sums a fixed strided subset of the partials, then a fixed tree
 __global__ void __launch_bounds__(256)
 k_final_sums(const double *__restrict__ mcb, const double *__restrict__ mcm, int mc_nb,
-             const double *__restrict__ kb, int k_nb, double dt, double n_pairs, double *sums) {
+             const double *__restrict__ kb, int k_nb, double dt, double n_pairs, double *sums,
+             const int64_t *__restrict__ n_pairs_dev) {
   __shared__ double red[8 + KICK_NSUM + 1][256];
   const int t = threadIdx.x;
   double m[8] = {0, 0, 0, 0, 0, 0, 0, 0}, k[KICK_NSUM] = {0, 0, 0, 0, 0, 0}, mx = 0.0;
@@ -81,7 +86,7 @@ k_final_sums(const double *__restrict__ mcb, const double *__restrict__ mcm, int
     sums[9] = red[4][0];
     sums[10] = red[5][0];
     sums[11] = red[12][0];
-    sums[12] = n_pairs;
+    sums[12] = n_pairs_dev != nullptr ? (double)*n_pairs_dev : n_pairs;
     sums[13] = red[7][0];
     sums[14] = red[8 + KICK_NSUM][0];
     sums[15] = red[6][0];
@@ -91,8 +96,8 @@ k_final_sums(const double *__restrict__ mcb, const double *__restrict__ mcm, int
 
 cudaError_t launch_final_sums(const double *mc_blocks, const double *mc_max, int mc_nb, const double *kick_blocks,
                               int kick_nb, double dt, double n_pairs, double *sums, cudaStream_t s,
-                              int64_t *launches) {
-  k_final_sums<<<1, 256, 0, s>>>(mc_blocks, mc_max, mc_nb, kick_blocks, kick_nb, dt, n_pairs, sums);
+                              int64_t *launches, const int64_t *n_pairs_dev) {
+  k_final_sums<<<1, 256, 0, s>>>(mc_blocks, mc_max, mc_nb, kick_blocks, kick_nb, dt, n_pairs, sums, n_pairs_dev);
   if (launches) *launches += 1;
   return cudaGetLastError();
 }

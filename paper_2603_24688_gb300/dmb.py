@@ -27,7 +27,7 @@ EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb
            "dmb_surrogate_grad_noalloc", "dmb_set_bins", "dmb_substep_info", "dmb_substep", "dmb_set_graph",
            "dmb_set_surrogate_engine", "dmb_surrogate_infer_tc", "dmb_autotune", "dmb_set_shapes",
            "dmb_get_shapes", "dmb_rebin_dm", "dmb_set_mc_variant", "dmb_set_anisotropy", "dmb_debug_tc_timeout",
-           "dmb_set_cross_section", "dmb_debug_rates_screened"]
+           "dmb_set_cross_section", "dmb_debug_rates_screened", "dmb_save_shapes", "dmb_load_shapes"]
 
 
 class DmbError(RuntimeError):
@@ -109,6 +109,8 @@ def load(path=LIB_PATH):
         "dmb_debug_tc_timeout": ([vp, c.c_int32], c.c_int),
         "dmb_set_cross_section": ([vp, c.c_int32, dbl], c.c_int),
         "dmb_debug_rates_screened": ([vp, i64, vp, vp], c.c_int),
+        "dmb_save_shapes": ([vp, c.c_char_p, c.c_char_p], c.c_int),
+        "dmb_load_shapes": ([vp, c.c_char_p, c.c_char_p], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -288,6 +290,17 @@ class Context:
     def dmb_set_shapes(self, shapes):
         v = (ctypes.c_int32 * 5)(*[int(shapes[k]) for k in self.SHAPE_NAMES])
         self._check(self.lib.dmb_set_shapes(self.h, v))
+
+    def dmb_save_shapes(self, path, key):
+        self._check(self.lib.dmb_save_shapes(self.h, str(path).encode(), str(key).encode()))
+
+    def dmb_load_shapes(self, path, key):
+        """True if shapes were stored under key (and are now set), False if absent."""
+        st = self.lib.dmb_load_shapes(self.h, str(path).encode(), str(key).encode())
+        if st == DMB_ERR_STATE:
+            return False
+        self._check(st)
+        return True
 
     def dmb_get_shapes(self):
         v = (ctypes.c_int32 * 5)()

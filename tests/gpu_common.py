@@ -39,3 +39,22 @@ def pair_band_mask(w, pi, pj):
     d = pair_distance(w["dm"]["pos"][pi], w["gas"]["pos"][pj], w["params"]["periodic"], w["params"]["box"])
     r = w["dm"]["h"][pi] + w["gas"]["h"][pj]
     return np.abs(d - r) <= 1e-6 * r
+
+
+def transfer_scales(w, pi, pj, params, g=None):
+    """Per gas particle, the sums of the absolute pair terms of its mean field: (acc [N_B, 3],
+    du/dt [N_B]).  A float32 evaluation of the pair terms with relative error eps is off by at
+    most eps times these, however much the signed terms cancel (the heating is a difference of
+    two positive sums, w^2 A and e B; Eq. gas-dTdt)."""
+    from oracle import units
+    from oracle.meanfield import pair_rates
+    gg, wv, A, B = pair_rates(w["dm"], w["gas"], pi, pj, params, g)
+    mu = w["gas"]["mu"][pj]
+    coef = w["dm"]["mass"][pi] * units.MSUN_PER_MP / (params["m_chi_mp"] + mu) * gg
+    nb = len(w["gas"]["h"])
+    sa = np.zeros((nb, 3))
+    for c in range(3):
+        np.add.at(sa[:, c], pj, np.abs(coef * A * wv[:, c]))
+    su = np.zeros(nb)
+    np.add.at(su, pj, np.abs(coef * A * np.sum(wv * wv, axis=1)) + np.abs(coef * mu / (params["m_chi_mp"] + mu) * B))
+    return sa, su

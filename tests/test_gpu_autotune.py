@@ -100,3 +100,28 @@ def test_shapes_out_of_range_refused(wl):
     bad = {"unit": 64, "seg": 2048, "mf_blocks_per_sm": 32, "mc_blocks_per_sm": 32, "tc_warpgroups": 5}
     with pytest.raises(dmb.DmbError):
         ctx.dmb_set_shapes(bad)
+
+
+def test_shapes_persist_as_json_keyed_by_workload(wl, tmp_path):
+    import json
+    path = str(tmp_path / "shapes.json")
+    a = _ctx(wl)
+    assert a.dmb_load_shapes(path, "galaxy1M-sub") is False          # no file yet
+    names = dmb.Context.SHAPE_NAMES
+    a.dmb_set_shapes(dict(zip(names, [32, 1024, 16, 8, 3])))
+    a.dmb_save_shapes(path, "galaxy1M-sub")
+    a.dmb_set_shapes(dict(zip(names, [16, 512, 32, 32, 4])))
+    a.dmb_save_shapes(path, "boxes64")
+    a.dmb_set_shapes(dict(zip(names, [128, 2048, 8, 4, 2])))
+    a.dmb_save_shapes(path, "galaxy1M-sub")                           # replaces its own entry only
+    stored = json.load(open(path))
+    assert stored == {"galaxy1M-sub": [128, 2048, 8, 4, 2], "boxes64": [16, 512, 32, 32, 4]}
+    b = _ctx(wl)
+    assert b.dmb_load_shapes(path, "boxes64") is True
+    assert [b.dmb_get_shapes()[k] for k in names] == [16, 512, 32, 32, 4]
+    assert b.dmb_load_shapes(path, "other") is False
+    with pytest.raises(dmb.DmbError):
+        b.dmb_save_shapes(path, "bad key/with slash")
+    json.dump({"x": [1, 2, 3, 4, 5]}, open(path, "w"))               # out of range: refused
+    with pytest.raises(dmb.DmbError):
+        b.dmb_load_shapes(path, "x")

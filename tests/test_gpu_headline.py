@@ -36,7 +36,7 @@ def galaxy():
     p = w["params"]
     tctx = dmb.Context(p["sigma0_cm2"], -2, p["m_chi_mp"], p["v0_kms"], False, (0.0, 0.0, 0.0), p["seed"],
                        rate_mode=dmb.DMB_RATE_MLP)
-    rep = tctx.dmb_train_surrogate(nsamples=1 << 20, epochs=24, seed=11)
+    rep = tctx.dmb_train_surrogate(nsamples=1 << 21, epochs=96, seed=11)   # the bench's recipe
     params = tctx.dmb_surrogate_params()
     tctx.close()
     rng = np.random.default_rng(30)

@@ -8,7 +8,7 @@ float32 path and 1e-12 relative in the float64 path.
 import numpy as np
 import pytest
 
-from gpu_common import device_inputs, gpu_pairs, make_ctx, pair_band_mask, require_gpu, torch
+from gpu_common import transfer_scales, device_inputs, gpu_pairs, make_ctx, pair_band_mask, require_gpu, torch
 from oracle import philox as OP
 from oracle.kernel import overlap_g_vec
 from oracle.hyp1f1 import hyp1f1_neg_arr
@@ -143,10 +143,10 @@ def test_meanfield_box(box, fp64, mode):
     tol = (TOL64 if fp64 else TOL32) if mode == 0 else (5e-8 if fp64 else 2e-5)
     ea = _rel_vec_err(a, box["acc"])
     eu = _rel_vec_err(u, box["dudt"])
-    # heating sums mix signs (w^2 A - e B); compare against the scale of the larger term
     assert np.percentile(ea, 100) < tol, ea.max()
-    scale_u = np.abs(box["dudt"]) + 1e-3 * np.abs(box["dudt"]).max()
-    assert np.max(np.abs(u - box["dudt"]) / scale_u) < tol
+    # heating sums mix signs (w^2 A - e B): bounded by tol times the sum of the absolute terms
+    _, su = transfer_scales(w, box["pi"], box["pj"], w["params"], box["g"])
+    assert np.all(np.abs(u - box["dudt"]) <= tol * su), np.max(np.abs(u - box["dudt"]) / su)
 
 
 @pytest.mark.parametrize("fp64", [False, True])
@@ -201,5 +201,14 @@ def test_step_box(fp64):
     dV_ref = out["V_new"] - w["gas"]["vel"]
     assert np.all(_rel_vec_err(dV, dV_ref) <= tv)
     np.testing.assert_allclose(gas["T"].cpu().numpy(), out["T_new"], rtol=1e-9 if fp64 else 1e-6)
-    np.testing.assert_allclose(dm["vel"].cpu().numpy(), out["mc"]["vel_new"], rtol=0,
-                               atol=(1e-10 if fp64 else 1e-3) * 100.0)
+    # DM: the same decisions outside the 1e-6 band; the kicks of the common scatters within the
+    # tolerance of the Monte Carlo test; everyone else keeps the exact float64 velocity
+    v = dm["vel"].cpu().numpy()
+    mc = out["mc"]
+    s_got = np.any(v != w["dm"]["vel"], axis=1)
+    band = mc["gap"] <= 1e-6
+    assert not np.any((s_got != mc["scattered"]) & ~band)
+    both = s_got & mc["scattered"]
+    dv, dv_ref = v[both] - w["dm"]["vel"][both], mc["vel_new"][both] - w["dm"]["vel"][both]
+    assert np.all(np.linalg.norm(dv - dv_ref, axis=1) <= 10 * tv * np.linalg.norm(dv_ref, axis=1))
+    assert np.array_equal(v[~s_got], w["dm"]["vel"][~s_got])

@@ -24,8 +24,9 @@ def _ctx(engine_nwg):
     rng = np.random.default_rng(5)
     ctx.dmb_load_surrogate((rng.uniform(-1, 1, n.value) * 0.2).astype(np.float32))
     shapes = ctx.dmb_get_shapes()
-    shapes[4] = engine_nwg
+    shapes["tc_warpgroups"] = engine_nwg
     ctx.dmb_set_shapes(shapes)
+    assert ctx.dmb_get_shapes()["tc_warpgroups"] == engine_nwg
     return ctx
 
 
@@ -34,7 +35,7 @@ def _infer(ctx, X, Y):
                                           ctypes.c_void_p(Y.data_ptr()))
 
 
-@pytest.mark.parametrize("nwg", [2, 4])
+@pytest.mark.parametrize("nwg", [2, 3, 4])
 def test_timed_out_wait_returns_timeout_and_the_context_recovers(nwg):
     require_gpu()
     from paper_2603_24688_gb300 import dmb
