@@ -39,6 +39,9 @@ LANES = 128
 # rates and the float64-free sums for the mean field; Philox, Box-Muller, the overlap and the
 # fixed-point running sum for the Monte Carlo
 OPS_PER_PAIR = {"meanfield": 150.0, "mc": 256.0}
+# of the mean field's 150, the closed-form rates (1F1 by its recurrence: one exp, one erf, ~40 FMA);
+# with the surrogate or the quadrature the pass reads or computes its rates otherwise
+RATE_OPS_CLOSED = 42.0
 # pair search: lane operations per candidate test of the tile stage's count pass (the split-float
 # displacement with the minimum image, the squared distance and the strict comparison with
 # h_i + h_j, the ballots and the mask bookkeeping)
@@ -74,10 +77,12 @@ def parse():
     ap.add_argument("--rate", default="mlp", choices=["mlp", "quad", "closed"],
                     help="rate provider of the timed step (the others are timed beside it)")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other rate providers")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--retune", action="store_true", help="run the autotuner even if shapes are stored")
+    ap.add_argument("--quick-train", action="store_true",
+                    help="train the surrogate briefly (profiling runs: the pass's work does not depend on the weights)")
     ap.add_argument("--fp64", action="store_true", help="float64 pair arithmetic (the box4k configuration)")
     return ap.parse_args()
 
@@ -573,7 +578,8 @@ def main():
     train_report = None
     if a.rate == "mlp" or not a.no_compare:
         tctx = new_ctx("mlp")
-        train_report = tctx.dmb_train_surrogate(**TRAIN)
+        train_report = tctx.dmb_train_surrogate(**(dict(nsamples=1 << 18, epochs=2, seed=11) if a.quick_train
+                                                    else TRAIN))
         surrogate = tctx.dmb_surrogate_params()
         tctx.close()
     ctx = new_ctx(a.rate)
@@ -663,9 +669,10 @@ def main():
                     "kernel_ms": surrogate_ms}
         if stage in OPS_PER_PAIR:
             ops = OPS_PER_PAIR[stage] if not (stage == "meanfield" and a.rate == "quad") else QUAD_OPS_PER_PAIR
+            kern = {"meanfield": "k_meanfield", "mc": "k_mc"}[stage]
             ach = ops * npairs / t / 1e12
             return {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s", "frac": ach / alu_peak,
-                    "traffic": None, "kernel": {"meanfield": "k_meanfield", "mc": "k_mc"}[stage],
+                    "traffic": None, "kernel": kern, "ops_per_pair": ops,
                     "peak_source": "152 SMs x 128 FP32/INT lanes x max SM clock (unit counts)"}
         return None
 
@@ -678,9 +685,19 @@ def main():
                 roof["kernel_share"] = float(roof["kernel_ms"] / per_step.sum())
             break
     stages = {n: float(v) for n, v in zip(names, per_step)}
-    for n in ("meanfield", "mc"):
-        r = roofline(n)
-        stages[n + "_frac"] = r["frac"] if r else None
+    if a.fp64:
+        for n in ("meanfield", "mc"):
+            r = roofline(n)
+            stages[n + "_frac"] = r["frac"] if r else None
+    else:
+        # the mean-field kernel alone (the surrogate pass before it is the tensor roofline) and the
+        # Monte Carlo, each against the lane-operation roofline
+        mf_ops = {"closed": OPS_PER_PAIR["meanfield"], "quad": QUAD_OPS_PER_PAIR,
+                  "mlp": OPS_PER_PAIR["meanfield"] - RATE_OPS_CLOSED}[a.rate]
+        t_mf = (per_step[2] - surrogate_ms) * 1e-3
+        stages["meanfield_kernel_ms"] = float(per_step[2] - surrogate_ms)
+        stages["meanfield_frac"] = mf_ops * npairs / t_mf / 1e12 / alu_peak
+        stages["mc_frac"] = OPS_PER_PAIR["mc"] * npairs / (per_step[3] * 1e-3) / 1e12 / alu_peak
     # the pair search: candidate distance tests of the count pass (after the ballot prefilter) at
     # SEARCH_OPS_PER_TEST lane operations each, over the whole search stage's time
     st = ctx.dmb_search_stats()
@@ -749,6 +766,9 @@ def main():
                                            "val_max_rel_err_B": float(train_report[2])}
 
     # ---- end to end through the C ABI with host buffers ---------------------------------
+    # Every step copies its inputs from pinned host memory and its resulting state back, inside
+    # the timed region, pipelined over two device buffer sets: step k+1's inputs travel on a copy
+    # stream while step k runs, and step k's results come back while step k+1 runs.
     e2e = None
     if a.e2e_steps > 0:
         host = {}
@@ -756,29 +776,55 @@ def main():
             host[sp] = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in src.items()}
             for k, v in src.items():
                 host[sp][k].copy_(v)
-        out_host = {"dm_vel": torch.empty_like(dm["vel"], device="cpu").pin_memory(),
-                    "gas_vel": torch.empty_like(gas["vel"], device="cpu").pin_memory(),
-                    "gas_T": torch.empty_like(gas["T"], device="cpu").pin_memory()}
+        outs = [{"dm_vel": torch.empty_like(dm["vel"], device="cpu").pin_memory(),
+                 "gas_vel": torch.empty_like(gas["vel"], device="cpu").pin_memory(),
+                 "gas_T": torch.empty_like(gas["T"], device="cpu").pin_memory()} for _ in range(2)]
         h2d = sum(v.numel() * v.element_size() for sp in host.values() for v in sp.values())
-        d2h = sum(v.numel() * v.element_size() for v in out_host.values()) + 16 * 8
+        d2h = sum(v.numel() * v.element_size() for v in outs[0].values())
+        bufs = [(dm, gas), ({k: v.clone() for k, v in dm.items()}, {k: v.clone() for k, v in gas.items()})]
+        cstream = torch.cuda.Stream()
+        ready = [torch.cuda.Event(), torch.cuda.Event()]
+        done = [None, None]
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for _ in range(a.e2e_steps):
-            for sp, dst in (("dm", dm), ("gas", gas)):
-                for k, v in dst.items():
-                    v.copy_(host[sp][k], non_blocking=True)
-            ctx.dmb_step(dm, gas, step, dt)
+        cstream.wait_stream(stream)
+
+        def h2d_into(k):
+            d_, g_ = bufs[k % 2]
+            with torch.cuda.stream(cstream):
+                if done[k % 2] is not None:
+                    cstream.wait_event(done[k % 2])          # the set's previous step is finished
+                for sp, dst in (("dm", d_), ("gas", g_)):
+                    for name, v in dst.items():
+                        v.copy_(host[sp][name], non_blocking=True)
+                ready[k % 2].record(cstream)
+
+        h2d_into(0)
+        for k in range(a.e2e_steps):
+            if k + 1 < a.e2e_steps:
+                h2d_into(k + 1)                               # behind step k
+            d_, g_ = bufs[k % 2]
+            stream.wait_event(ready[k % 2])
+            ctx.dmb_step(d_, g_, step, dt, want_sums=False)
             step += 1
-            out_host["dm_vel"].copy_(dm["vel"], non_blocking=True)
-            out_host["gas_vel"].copy_(gas["vel"], non_blocking=True)
-            out_host["gas_T"].copy_(gas["T"], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            done[k % 2] = ev
+            o = outs[k % 2]
+            with torch.cuda.stream(cstream):
+                cstream.wait_event(ev)
+                o["dm_vel"].copy_(d_["vel"], non_blocking=True)
+                o["gas_vel"].copy_(g_["vel"], non_blocking=True)
+                o["gas_T"].copy_(g_["T"], non_blocking=True)
+        stream.wait_stream(cstream)
         f1.record(stream)
         barrier()
         ms_e, pairs_e = reduce_across_ranks(f0.elapsed_time(f1), npairs * a.e2e_steps, dist)
         e2e = {"value": pairs_e / (ms_e * 1e-3), "unit": "pairs/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "pipelined": "inputs of step k+1 copied while step k runs; results of step k copied while step k+1 runs",
                "ms_per_step": ms_e / a.e2e_steps}
 
     cpu = None

@@ -351,6 +351,22 @@ dmb_status dmb_search_stats(dmb_ctx *ctx, uint64_t *out16);
  * FA and FB ([1],[2],[3],[4]), seconds, optimiser steps, samples.  Synchronises. */
 dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, uint64_t seed, double *report);
 
+/* How a float32 step with one categorical draw per DM particle (dmb_step, dmb_step_batched) runs
+ * its pair physics: on = 1: one pass over the gas-major pairs evaluates each pair's geometry and
+ * overlap once for both the mean field and P_ij of the Monte Carlo, and a second pass per DM row
+ * sums and selects from those P_ij (read through each DM-major entry's gas-major position, which
+ * the pair search then also writes); on = 0 (the default, faster on the galaxy workloads): the
+ * mean field and the Monte Carlo run as separate passes over their own row orders.  The results
+ * are the same bit for bit.  Other values: DMB_ERR_ARG.  (The standalone calls, the float64 mode, the per-pair Bernoulli variant
+ * and the substeps always use the separate passes.) */
+dmb_status dmb_set_fusion(dmb_ctx *ctx, int32_t on);
+
+/* Which power-law indices the next dmb_train_surrogate covers: 0 (the default) the scan's
+ * {-4, -2, 0, 2} and the context's n, one network for all of them; 1 the context's n only (the
+ * network's fourth input is then constant, and all of its capacity serves that n).  Other values:
+ * DMB_ERR_ARG.  The screened law always trains its single normalisation. */
+dmb_status dmb_set_surrogate_scope(dmb_ctx *ctx, int32_t scope);
+
 /* Copy the float32 parameter block to host memory (count receives its length; host_out may be
  * NULL to query it).  Layout: W1[128][4] b1 W2[128][128] b2 W3[128][128] b3 W4[2][128] b4. */
 dmb_status dmb_surrogate_params(dmb_ctx *ctx, float *host_out, int64_t *count);

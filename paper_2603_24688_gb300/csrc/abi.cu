@@ -78,6 +78,7 @@ struct dmb_ctx {
   DevBuf box_sides, box_params;
   std::vector<int> mlp_n;        // power-law indices the network was trained for
   int mlp_family = 0;            // velocity law the network was trained for (0 power, 1 screened)
+  int mlp_scope = 0;             // dmb_set_surrogate_scope: 0 the scan's indices and n, 1 n only
   int xsec = 0;                  // dmb_set_cross_section: 0 power law, 1 screened law
   double v_c = 0.0;              // its v_c, km/s
   double mlp_box[6] = {-2.0, 2.0, -3.0, 2.0, -0.30102999566398120, 1.0};   // log10 ranges of s, tau, m_chi
@@ -133,6 +134,8 @@ struct dmb_ctx {
   bool frame_ready = false;         // the batched frame was uploaded by dmb_step_batched
   uint64_t batch_next_step = ~0ull; // device step counter value after the last batched graph
   DevBuf gate, cap_need;
+  DevBuf gidx;                      // gas-major position of every DM-major pair (the fused pass)
+  bool fuse = false;                // dmb_set_fusion: one pass for the mean field and the Monte Carlo
   int mc_variant = 0;             // dmb_set_mc_variant
   double mc_beta = 0.0;           // dmb_set_anisotropy
   cudaStream_t gstream = nullptr;
@@ -453,12 +456,14 @@ dmb_status neighbors_impl(dmb_ctx *ctx) {
   sd.n_pairs = nd > 0 ? ctx->h_tot[5] : 0;
   if (sd.n_pairs != sg.n_pairs) return fail(ctx, DMB_ERR_CUDA, "pair counts of the two directions differ");
   // emit both directions: gas-major rows in search order, DM-major rows by claimed positions
-  if (!ensure(sd.rows, (size_t)sg.n_pairs * 4)) return fail(ctx, DMB_ERR_OOM, "device allocation failed for DM-major lists");
+  if (!ensure(sd.rows, (size_t)sg.n_pairs * 4) || (ctx->fuse && !ensure(ctx->gidx, (size_t)sg.n_pairs * 4)))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for DM-major lists");
   CK(cudaMemsetAsync(ctx->t_cursor.p, 0, (size_t)(nd + 1) * 4, s), "memset");
   TransposeOut tre;
   tre.cursor = ptr<uint32_t>(ctx->t_cursor);
   tre.ptr = ptr<int64_t>(sd.row_ptr);
   tre.rows = ptr<uint32_t>(sd.rows);
+  tre.gidx = ctx->fuse ? ptr<uint32_t>(ctx->gidx) : nullptr;   // only the fused step reads them
   if ((st = search_stage2_emit<R>(ctx, sg, G, D, tre)) != DMB_OK) return st;
   if ((st = build_segments(ctx, sg, G.n)) != DMB_OK) return st;
   if (!ensure(ctx->pcache, (size_t)sd.n_pairs * (ctx->p.fp64 ? 8 : 4)))
@@ -529,6 +534,7 @@ dmb_status neighbors_capped(dmb_ctx *ctx) {
   tre.cursor = ptr<uint32_t>(ctx->t_cursor);
   tre.ptr = ptr<int64_t>(sd.row_ptr);
   tre.rows = ptr<uint32_t>(sd.rows);
+  tre.gidx = ctx->fuse ? ptr<uint32_t>(ctx->gidx) : nullptr;
   CK(launch_tile<R>(G, D, ctx->bx, fr, true, ptr<uint32_t>(sg.unit_leaf), ptr<int64_t>(sg.unit_item0), item_ptr,
                     ptr<uint32_t>(sg.items), cap.units, ctx->shp.unit, ptr<uint32_t>(sg.unit_cnt),
                     ptr<int64_t>(sg.row_ptr), ptr<uint32_t>(sg.rows), tre, ptr<uint32_t>(sg.tmask), status, nullptr, s,
@@ -736,6 +742,72 @@ dmb_status mc_impl(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, uint
     CK(launch_mc<R>(D, G, ctx->bx, ptr<int64_t>(ctx->sd.row_ptr), ptr<uint32_t>(ctx->sd.rows),
                     ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), ptr<McRec>(ctx->mc_rec), nb,
                     ctx->shp.mc_bps, ctx->stream, &ctx->launches), "mc");
+  return DMB_OK;
+}
+
+// The mean field and the Monte Carlo of a float32 step with one categorical draw per DM particle
+// in one pass over the gas-major pairs (launch_pairs_fused), then the Monte Carlo's sums and
+// selection per DM row (launch_mc_select): the results of meanfield_impl and mc_impl, each pair's
+// geometry and overlap evaluated once.  ev_mid (may be null) is recorded between the two.
+dmb_status step_pairs_fused(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, cudaEvent_t ev_mid) {
+  const SpeciesView<float> D = view<float>(ctx->dm, ctx->nbox > 0), G = view<float>(ctx->gas, ctx->nbox > 0);
+  MfOut o;
+  o.acc = ptr<double>(ctx->mf_acc);
+  o.dudt = ptr<double>(ctx->mf_dudt);
+  o.e_exp = ptr<double>(ctx->e_exp);
+  if (!ensure(ctx->mf_part, (size_t)ctx->n_seg_max * 6 * 4)) return fail(ctx, DMB_ERR_OOM, "mean-field scratch");
+  SegView sv;
+  sv.seg_ptr = ptr<int64_t>(ctx->seg_ptr);
+  sv.seg_row = ptr<uint32_t>(ctx->seg_row);
+  sv.seg_begin = ptr<int64_t>(ctx->seg_begin);
+  sv.seg_len = ctx->seg_len;
+  MlpRun mr = {};
+  if (ctx->rc.rate_mode == DMB_RATE_MLP) {
+    if (!ctx->mlp_ready) return fail(ctx, DMB_ERR_STATE, "surrogate rate provider selected but no trained network");
+    if (!surrogate_covers(ctx))
+      return fail(ctx, DMB_ERR_DOMAIN, "the surrogate was not trained for this cross section (law or power-law index)");
+    mr = mlp_run(ctx);
+    CK(cudaMemsetAsync(ctx->mlp_fallback.p, 0, 8, ctx->stream), "memset");
+    if (!ensure(ctx->mlp_rates, (size_t)ctx->sg.n_pairs * 8 + 8)) return fail(ctx, DMB_ERR_OOM, "surrogate rates");
+    mr.rates = ptr<float2>(ctx->mlp_rates);
+    const bool tm = ctx->timing && !ctx->capturing;
+    if (tm) CK(cudaEventRecord(ctx->sev[0], ctx->stream), "event");
+    const dmb_status st = surrogate_rates(ctx, mr, sv, ptr<int64_t>(ctx->sg.row_ptr), ctx->gas.n, nullptr,
+                                          ctx->sg.n_pairs);
+    if (st != DMB_OK) return st;
+    if (tm) {
+      CK(cudaEventRecord(ctx->sev[1], ctx->stream), "event");
+      ctx->sev_pending = true;
+    }
+  }
+  const int nb = mc_blocks_for(D.n);
+  if (!ensure(ctx->mc_blocks, (size_t)nb * 8 * 8) || !ensure(ctx->mc_max, (size_t)nb * 8) ||
+      !ensure(ctx->mc_rec, (size_t)D.n * sizeof(McRec)) || !ensure(ctx->pcache, (size_t)ctx->sd.n_pairs * 4))
+    return fail(ctx, DMB_ERR_OOM, "device allocation failed for MC partials");
+  McArgs a;
+  a.variant = 0;
+  a.beta = ctx->mc_beta;
+  a.dt = dt;
+  a.step = step;
+  a.seed = ctx->p.seed;
+  a.id_bits = 32;
+  a.vel_in = ctx->dm_vel;
+  a.vel_out = vel_out;
+  a.scattered = nullptr;
+  a.partner = nullptr;
+  a.p_ratio = nullptr;
+  a.p_total = nullptr;
+  a.block_sums = ptr<double>(ctx->mc_blocks);
+  a.block_max = ptr<double>(ctx->mc_max);
+  if (ctx->capturing) a.step_dev = ptr<unsigned long long>(ctx->step_dev);
+  CK(launch_pairs_fused(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv, ctx->n_seg_max,
+                        ptr<float4>(ctx->gtab), ctx->rc, o, ptr<float>(ctx->mf_part), mr, a, ptr<float>(ctx->pcache),
+                        ctx->shp.mf_bps, ctx->stream, &ctx->launches), "fused pair pass");
+  if (ev_mid) CK(cudaEventRecord(ev_mid, ctx->stream), "event");
+  if (D.n > 0)
+    CK(launch_mc_select(D, G, ctx->bx, ptr<int64_t>(ctx->sd.row_ptr), ptr<uint32_t>(ctx->sd.rows),
+                        ptr<uint32_t>(ctx->gidx), ptr<float>(ctx->pcache), ptr<float4>(ctx->gtab), ctx->rc, a,
+                        ptr<McRec>(ctx->mc_rec), nb, ctx->shp.mc_bps, ctx->stream, &ctx->launches), "mc select");
   return DMB_OK;
 }
 
@@ -1083,7 +1155,7 @@ dmb_status dmb_destroy(dmb_ctx *ctx) {
                     &ctx->act_gas, &ctx->act_start, &ctx->act_seg_ptr, &ctx->act_seg_row, &ctx->act_seg_begin,
                     &ctx->act_len, &ctx->act_segs, &ctx->act_gpairs, &ctx->act_dpairs, &ctx->act_pick,
                     &ctx->step_dev, &ctx->bin_keys, &ctx->bin_keys1, &ctx->bin_vals1, &ctx->tc_tiles,
-                    &ctx->rebin_cnt, &ctx->gate, &ctx->cap_need};
+                    &ctx->rebin_cnt, &ctx->gate, &ctx->cap_need, &ctx->gidx};
   for (DevBuf *b : bufs) release(*b);
   SpeciesBufs *sp[2] = {&ctx->dm, &ctx->gas};
   for (SpeciesBufs *s : sp) {
@@ -1261,14 +1333,19 @@ static dmb_status step_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, 
   const int64_t ng = gas->n, nd = dm->n;
   if (!ensure(ctx->mf_acc, ng * 24) || !ensure(ctx->mf_dudt, ng * 8) || !ensure(ctx->e_exp, ng * 8))
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for mean-field scratch");
-  st = ctx->p.fp64 ? meanfield_impl<double>(ctx, ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp))
-                   : meanfield_impl<float>(ctx, ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp));
-  if (st != DMB_OK) return st;
-  if (tm) CK(cudaEventRecord(ctx->ev[3], ctx->stream), "event");
-  // DM velocities are updated in place: the MC reads v_i and writes v_i' for the same particle
-  st = ctx->p.fp64 ? mc_impl<double>(ctx, step, dt, const_cast<double *>(dm->vel), nullptr, nullptr, nullptr, nullptr)
-                   : mc_impl<float>(ctx, step, dt, const_cast<double *>(dm->vel), nullptr, nullptr, nullptr, nullptr);
-  if (st != DMB_OK) return st;
+  if (!ctx->p.fp64 && ctx->mc_variant == 0 && ctx->fuse) {
+    // DM velocities are updated in place: the MC reads v_i and writes v_i' for the same particle
+    st = step_pairs_fused(ctx, step, dt, const_cast<double *>(dm->vel), tm ? ctx->ev[3] : nullptr);
+    if (st != DMB_OK) return st;
+  } else {
+    st = ctx->p.fp64 ? meanfield_impl<double>(ctx, ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp))
+                     : meanfield_impl<float>(ctx, ptr<double>(ctx->mf_acc), ptr<double>(ctx->mf_dudt), ptr<double>(ctx->e_exp));
+    if (st != DMB_OK) return st;
+    if (tm) CK(cudaEventRecord(ctx->ev[3], ctx->stream), "event");
+    st = ctx->p.fp64 ? mc_impl<double>(ctx, step, dt, const_cast<double *>(dm->vel), nullptr, nullptr, nullptr, nullptr)
+                     : mc_impl<float>(ctx, step, dt, const_cast<double *>(dm->vel), nullptr, nullptr, nullptr, nullptr);
+    if (st != DMB_OK) return st;
+  }
   if (tm) CK(cudaEventRecord(ctx->ev[4], ctx->stream), "event");
   const int kb = 152 * 4;
   if (!ensure(ctx->kick_blocks, (size_t)kb * KICK_NSUM * 8)) return fail(ctx, DMB_ERR_OOM, "kick partials");
@@ -1320,7 +1397,8 @@ static dmb_status presize_batch(dmb_ctx *ctx) {
   bool ok = ensure(sg.items, (size_t)c.items * 4) && ensure(sg.tmask, (size_t)c.items * 32 * 4) &&
             ensure(sg.unit_leaf, (size_t)c.units * 4) && ensure(sg.unit_item0, (size_t)c.units * 8) &&
             ensure(sg.unit_cnt, (size_t)c.units * 32 * 4) && ensure(sg.rows, (size_t)c.pairs * 4) &&
-            ensure(sd.rows, (size_t)c.pairs * 4) && ensure(ctx->pcache, (size_t)c.pairs * rb) &&
+            ensure(sd.rows, (size_t)c.pairs * 4) && (!ctx->fuse || ensure(ctx->gidx, (size_t)c.pairs * 4)) &&
+            ensure(ctx->pcache, (size_t)c.pairs * rb) &&
             ensure(ctx->seg_row, (size_t)c.segs * 4) && ensure(ctx->seg_begin, (size_t)c.segs * 8) &&
             ensure(ctx->mf_part, (size_t)c.segs * 6 * rb) && ensure(ctx->gate, 16) && ensure(ctx->cap_need, 64) &&
             ensure(ctx->step_dev, 8);
@@ -1489,6 +1567,24 @@ dmb_status dmb_set_mc_variant(dmb_ctx *ctx, int32_t variant) {
     clear_batch_graph(ctx);
   }
   ctx->mc_variant = variant;
+  return DMB_OK;
+}
+
+dmb_status dmb_set_fusion(dmb_ctx *ctx, int32_t on) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (on != 0 && on != 1) return fail(ctx, DMB_ERR_ARG, "on must be 0 or 1");
+  if ((on == 1) != ctx->fuse) {
+    clear_batch_graph(ctx);     // the captured step holds the other kernels
+    ctx->pairs_ready = false;   // the search writes the pairs' gas-major positions only when fused
+  }
+  ctx->fuse = on == 1;
+  return DMB_OK;
+}
+
+dmb_status dmb_set_surrogate_scope(dmb_ctx *ctx, int32_t scope) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (scope != 0 && scope != 1) return fail(ctx, DMB_ERR_ARG, "scope must be 0 (the scan's indices) or 1 (n only)");
+  ctx->mlp_scope = scope;
   return DMB_OK;
 }
 
@@ -1848,6 +1944,7 @@ dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, u
   // the screened law has one normalisation (n = 0) and takes tau as varsigma^2 / v_c^2
   std::vector<int> ns = {-4, -2, 0, 2};
   if (std::find(ns.begin(), ns.end(), ctx->p.n) == ns.end()) ns.push_back(ctx->p.n);
+  if (ctx->mlp_scope == 1) ns = {ctx->p.n};
   if (ctx->xsec == 1) ns = {0};
   spec.scr = ctx->xsec == 1 ? 1 : 0;
   // n = -4 (the 1F1 with the most curvature across the envelope's transition) is drawn twice as often

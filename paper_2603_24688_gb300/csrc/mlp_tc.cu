@@ -372,7 +372,14 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
   const uint32_t d_tmem = TSA ? a_tmem + 64u : tmem + 128u * (uint32_t)g;
   const uint32_t my_lanes = d_tmem + ((uint32_t)(32 * w) << 16);
   const uint32_t my_a = a_tmem + ((uint32_t)(32 * w) << 16);
-  const uint32_t sA = sbase + Ly::A + g * TC_OPER, sA1 = sA;   // the layer-1 operand is slice 0 of A
+  const uint32_t sA = sbase + Ly::A + g * TC_OPER;   // the layer-1 operand is slice 0 of A
+  // the operands' descriptors, built once: a K = 16 slice further is 2 TC_SLICE bytes on, which
+  // adds (2 TC_SLICE) >> 4 to the start-address field (shared addresses stay below 2^18 bytes)
+  const uint64_t dA = smem_desc(sA, TC_SLICE, 128), dW1 = smem_desc(sbase + Ly::W1, TC_SLICE, 128);
+  const uint64_t dW2 = smem_desc(sbase + Ly::W2, TC_SLICE, 128), dW3 = smem_desc(sbase + Ly::W3, TC_SLICE, 128);
+  const uint64_t dONE = smem_desc(sbase + Ly::ONE, TC_SLICE, 128);
+  const uint64_t dBB2 = smem_desc(sbase + Ly::BB, TC_SLICE, 128), dBB3 = smem_desc(sbase + Ly::BB + TC_OPER1, TC_SLICE, 128);
+  const uint64_t dks = (uint64_t)((2 * TC_SLICE) >> 4);
   unsigned char *pA = sm + Ly::A + g * TC_OPER;
   unsigned char *pA1 = pA;
   const int bar_id = 1 + g;
@@ -453,22 +460,20 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
         tc_fence_after();
         if (layer == 0) {
           if (TSA)
-            tc_mma_ts(d_tmem, a_tmem, smem_desc(sbase + Ly::W1, TC_SLICE, 128), 0u);
+            tc_mma_ts(d_tmem, a_tmem, dW1, 0u);
           else
-            tc_mma(d_tmem, smem_desc(sA1, TC_SLICE, 128), smem_desc(sbase + Ly::W1, TC_SLICE, 128), 0u);
+            tc_mma(d_tmem, dA, dW1, 0u);
         } else {
-          const uint32_t sW = sbase + (layer == 1 ? Ly::W2 : Ly::W3);
+          const uint64_t dW = layer == 1 ? dW2 : dW3;
 #pragma unroll
           for (int ks = 0; ks < MLP_H / 16; ++ks) {
             if (TSA)
-              tc_mma_ts(d_tmem, a_tmem + 8u * ks, smem_desc(sW + ks * 2 * TC_SLICE, TC_SLICE, 128), ks > 0 ? 1u : 0u);
+              tc_mma_ts(d_tmem, a_tmem + 8u * ks, dW + dks * ks, ks > 0 ? 1u : 0u);
             else
-              tc_mma(d_tmem, smem_desc(sA + ks * 2 * TC_SLICE, TC_SLICE, 128),
-                     smem_desc(sW + ks * 2 * TC_SLICE, TC_SLICE, 128), ks > 0 ? 1u : 0u);
+              tc_mma(d_tmem, dA + dks * ks, dW + dks * ks, ks > 0 ? 1u : 0u);
           }
           // + b through the constant slice
-          tc_mma(d_tmem, smem_desc(sbase + Ly::ONE, TC_SLICE, 128),
-                 smem_desc(sbase + Ly::BB + (layer - 1) * TC_OPER1, TC_SLICE, 128), 1u);
+          tc_mma(d_tmem, dONE, layer == 1 ? dBB2 : dBB3, 1u);
         }
         // (fault injection only: the first layer-1 commit of group 0 in CTA 0 is left out)
         if (!(skip_commit && layer == 0)) tc_commit(bar);
@@ -483,14 +488,15 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
         fetch_stage<MODE>(a, 0, 2, nxt);
         fetch_stage<MODE>(a, 0, 3, nxt);
       }
-      // every thread waits (bounded) for the MMA and the group agrees on the outcome, so that a
-      // timeout is seen by all 128
-      const bool done = wg_sync_and(bar_id, mbar_wait_bounded(bar, phase, wait_ns));
+      // the group's first warp waits (bounded) for the MMA while the other three wait at the
+      // group's barrier, which also makes the group agree on the outcome, so that a timeout is
+      // seen by all 128
+      const bool done = wg_sync_and(bar_id, w == 0 ? mbar_wait_bounded(bar, phase, wait_ns) : true);
       if (!done) {
         // the MMAs this group issued may still be in flight: a new commit tracks them, and the
         // group waits for it (bounded again) before it leaves and the CTA frees tensor memory
         if (t == 0) tc_commit(bar);
-        (void)wg_sync_and(bar_id, mbar_wait_bounded(bar, phase, wait_ns));
+        (void)wg_sync_and(bar_id, w == 0 ? mbar_wait_bounded(bar, phase, wait_ns) : true);
         ok = false;
         break;
       }

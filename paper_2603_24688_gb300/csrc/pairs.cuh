@@ -43,6 +43,7 @@ struct TransposeOut {
   uint32_t *cursor = nullptr;    // [targets], zeroed (emit pass)
   const int64_t *ptr = nullptr;  // [targets + 1] row starts (emit pass)
   uint32_t *rows = nullptr;      // [pairs] (emit pass)
+  uint32_t *gidx = nullptr;      // [pairs] (emit pass, may be null): the pair's query-major position
 };
 
 // tmask (optional, [items][32] uint32): the count pass stores each tile's pair masks (entry k:
@@ -150,6 +151,20 @@ template <typename R>
 cudaError_t launch_mc(SpeciesView<R> D, SpeciesView<R> G, BoxSplit bx, const int64_t *row_ptr, const uint32_t *rows,
                       const float4 *gtab, RunConst rc, McArgs a, R *pcache, McRec *rec, int finish_blocks,
                       int blocks_per_sm, cudaStream_t s, int64_t *launches);
+
+// The fused pass of a float32 step with one categorical draw per DM particle (no row lists): the
+// mean field of every gas row (part, then the float64 finish into out) and P_ij of every pair at
+// its gas-major position (pg); then the Monte Carlo per DM row from pg through gidx (the DM-major
+// rows' gas-major positions) and its float64 finish.  The results are those of launch_meanfield
+// and launch_mc.
+cudaError_t launch_pairs_fused(SpeciesView<float> G, SpeciesView<float> D, BoxSplit bx, const int64_t *row_ptr,
+                               const uint32_t *rows, SegView sv, int64_t n_seg_max, const float4 *gtab, RunConst rc,
+                               MfOut out, float *part, MlpRun mr, McArgs a, float *pg, int blocks_per_sm,
+                               cudaStream_t s, int64_t *launches);
+cudaError_t launch_mc_select(SpeciesView<float> D, SpeciesView<float> G, BoxSplit bx, const int64_t *row_ptr,
+                             const uint32_t *rows, const uint32_t *gidx, const float *pg, const float4 *gtab,
+                             RunConst rc, McArgs a, McRec *rec, int finish_blocks, int blocks_per_sm, cudaStream_t s,
+                             int64_t *launches);
 
 // Overlap table build (float64 exact evaluator at the nodes) and debug evaluators.
 cudaError_t launch_gtable(float4 *T, cudaStream_t s, int64_t *launches);

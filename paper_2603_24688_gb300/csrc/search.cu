@@ -70,8 +70,12 @@ __device__ __forceinline__ float box_gap2(const float qmn[3], const float qmx[3]
 
 // Emit of the target-major lists for one tile: lane k owns target k (mycol = the query lanes
 // paired with it), claims its positions with one atomic, and every query lane writes its entries.
+// With tr.gidx each entry also gets its query-major position: the query lane's row continues at
+// out0 (its position before this tile) with its pairs in ascending target order, myrow being the
+// lane's targets in this tile.
 __device__ __forceinline__ void emit_transposed(const TransposeOut &tr, int64_t base, unsigned lane, unsigned lt,
-                                               unsigned m, uint32_t mycol, int64_t qi) {
+                                               unsigned m, uint32_t mycol, int64_t qi, int64_t out0 = 0,
+                                               uint32_t myrow = 0u) {
   const int64_t tk = base + lane;
   int64_t p0 = 0, p1 = 0;
   if (mycol) {
@@ -84,7 +88,10 @@ __device__ __forceinline__ void emit_transposed(const TransposeOut &tr, int64_t 
     const int64_t s0 = __shfl_sync(DMB_FULL, p0, k), s1 = __shfl_sync(DMB_FULL, p1, k);
     if (col & (1u << lane)) {
       const int64_t pos = s0 + __popc(col & lt);
-      if (pos < s1) tr.rows[pos] = (uint32_t)qi;
+      if (pos < s1) {
+        tr.rows[pos] = (uint32_t)qi;
+        if (tr.gidx != nullptr) tr.gidx[pos] = (uint32_t)(out0 + __popc(myrow & ((1u << k) - 1u)));
+      }
     }
   }
 }
@@ -236,14 +243,17 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
           leaf_next = items[it + 1];
         }
         const unsigned m = __ballot_sync(DMB_FULL, mycol != 0u);
+        const int64_t out0 = out;
+        uint32_t myrow = 0u;
         for (unsigned mm = m; mm; mm &= mm - 1) {
           const int k = __ffs(mm) - 1;
           if (__shfl_sync(DMB_FULL, mycol, k) & (1u << lane)) {
             if (out < out_end) rows[out] = (uint32_t)(base + k);
             ++out;
+            myrow |= 1u << k;
           }
         }
-        if (tr_on && m) emit_transposed(tr, base, lane, lt, m, mycol, qi);
+        if (tr_on && m) emit_transposed(tr, base, lane, lt, m, mycol, qi, out0, myrow);
       }
       continue;
     }
@@ -268,6 +278,8 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
       ++st_leaves;
       st_tests += (unsigned long long)__popc(m) * 32ull;
       uint32_t mycol = 0;                                // lane k: the query lanes paired with target k
+      const int64_t out0 = out;
+      uint32_t myrow = 0u;                               // this lane's targets in this tile
       for (unsigned mm = m; mm; mm &= mm - 1) {          // warp-uniform: m is a ballot
         const int k = __ffs(mm) - 1;
         const v4 Pk = sP[wib][k], Lk = sL[wib][k];
@@ -281,6 +293,7 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
           if (EMIT) {
             if (out < out_end) rows[out] = (uint32_t)(base + k);
             ++out;
+            myrow |= 1u << k;
           }
           ++cnt;
         }
@@ -296,7 +309,7 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
         if (!EMIT) {
           if (mycol) atomicAdd(&tr.cnt[base + lane], (uint32_t)__popc(mycol));
         } else {
-          emit_transposed(tr, base, lane, lt, m, mycol, qi);
+          emit_transposed(tr, base, lane, lt, m, mycol, qi, out0, myrow);
         }
       }
     }
