@@ -60,6 +60,13 @@ MLP_TENSOR_FLOP_PER_PAIR = 2.0 * 128 * (16 + 128 + 16 + 128 + 16)
 # copies read and the 8-byte rates written per pair
 MLP_DRAM_BYTES_PER_PAIR = (713.150e6 + 639.274496e6) / 85071169
 MLP_ALGO_BYTES_PER_PAIR = 4 + 4 + 16 + 16 + 8
+# The same kernel with the mean field in its epilogue (--surrogate-epilogue 1): its DRAM bytes
+# per pair from one ncu capture on galaxy1M (dram__bytes_read.sum + dram__bytes_write.sum =
+# 782.1 + 82.9 MB for 85,071,169 pairs).
+# Algorithmic bytes: row index, DM index, the two velocity copies and the two position copies
+# (hi, lo) of both particles read per pair, one 24-byte partial sum written per 32 pairs
+MLP_MF_DRAM_BYTES_PER_PAIR = (782.105856e6 + 82.870272e6) / 85071169
+MLP_MF_ALGO_BYTES_PER_PAIR = 4 + 4 + 6 * 16 + 24 / 32
 # the surrogate's training recipe (samples of the float64 device quadrature, Adam epochs)
 TRAIN = dict(nsamples=1 << 21, epochs=96, seed=11)
 # the power-law indices of the benchmark's cross-section scan
@@ -77,6 +84,8 @@ def parse():
     ap.add_argument("--rate", default="mlp", choices=["mlp", "quad", "closed"],
                     help="rate provider of the timed step (the others are timed beside it)")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other rate providers")
+    ap.add_argument("--surrogate-epilogue", type=int, default=0, choices=[0, 1],
+                    help="1: the surrogate's tensor-core kernel sums the mean field itself; 0: it stores the rates")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
@@ -381,6 +390,7 @@ def run_substeps(a, peaks, peak_kind):
     stream = torch.cuda.current_stream()
     ctx = dmb.Context(prm["sigma0_cm2"], prm["n"], prm["m_chi_mp"], prm["v0_kms"], False, (0.0, 0.0, 0.0),
                       prm["seed"], rate_mode=dmb.DMB_RATE_MLP, stream=stream)
+    ctx.dmb_set_surrogate_epilogue(a.surrogate_epilogue)
     rep = ctx.dmb_train_surrogate(**TRAIN)
     dm, gas = dmb.to_device(w["dm"]), dmb.to_device(w["gas"])
     db = torch.from_numpy(w["dm_bin"]).cuda()
@@ -571,8 +581,10 @@ def main():
     prm = w["params"]
 
     def new_ctx(rate):
-        return dmb.Context(prm["sigma0_cm2"], prm["n"], prm["m_chi_mp"], prm["v0_kms"], prm["periodic"],
-                           tuple(prm["box"]), prm["seed"], fp64=a.fp64, rate_mode=modes[rate], stream=stream)
+        c = dmb.Context(prm["sigma0_cm2"], prm["n"], prm["m_chi_mp"], prm["v0_kms"], prm["periodic"],
+                        tuple(prm["box"]), prm["seed"], fp64=a.fp64, rate_mode=modes[rate], stream=stream)
+        c.dmb_set_surrogate_epilogue(a.surrogate_epilogue)
+        return c
 
     surrogate = None
     train_report = None
@@ -657,12 +669,16 @@ def main():
             tpeak = peaks.get("bf16_tflops_sustained", 1700.0)
             ach = MLP_FLOP_PER_PAIR * npairs / ts / 1e12
             issued = MLP_TENSOR_FLOP_PER_PAIR * npairs / ts / 1e12
-            traffic = None if MLP_DRAM_BYTES_PER_PAIR is None else MLP_DRAM_BYTES_PER_PAIR * npairs
+            epi = a.surrogate_epilogue == 1
+            per_pair = MLP_MF_DRAM_BYTES_PER_PAIR if epi else MLP_DRAM_BYTES_PER_PAIR
+            traffic = None if per_pair is None else per_pair * npairs
             return {"bound": "tensor", "achieved": ach, "peak": tpeak, "unit": "TFLOP/s", "frac": ach / tpeak,
                     "traffic": traffic, "traffic_unit": "bytes per launch",
                     "traffic_source": "ncu capture of this kernel on galaxy1M, scaled by the pair count",
-                    "algorithmic_bytes": MLP_ALGO_BYTES_PER_PAIR * npairs,
-                    "kernel": "k_mlp_tc (surrogate pass: 4 -> 128 -> 128 -> 128 -> 2 per pair)",
+                    "algorithmic_bytes": (MLP_MF_ALGO_BYTES_PER_PAIR if epi else MLP_ALGO_BYTES_PER_PAIR) * npairs,
+                    "kernel": ("k_mlp_tc (surrogate 4 -> 128 -> 128 -> 128 -> 2 per pair, with the gas mean field "
+                               "summed in its epilogue; the time includes the float64 finish per gas row)") if epi
+                    else "k_mlp_tc (surrogate pass: 4 -> 128 -> 128 -> 128 -> 2 per pair, rates stored)",
                     "flop_per_pair": MLP_FLOP_PER_PAIR,
                     "issued_tflops": issued, "issued_flop_per_pair": MLP_TENSOR_FLOP_PER_PAIR,
                     "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind})",
@@ -694,9 +710,15 @@ def main():
         # Monte Carlo, each against the lane-operation roofline
         mf_ops = {"closed": OPS_PER_PAIR["meanfield"], "quad": QUAD_OPS_PER_PAIR,
                   "mlp": OPS_PER_PAIR["meanfield"] - RATE_OPS_CLOSED}[a.rate]
-        t_mf = (per_step[2] - surrogate_ms) * 1e-3
-        stages["meanfield_kernel_ms"] = float(per_step[2] - surrogate_ms)
-        stages["meanfield_frac"] = mf_ops * npairs / t_mf / 1e12 / alu_peak
+        if a.rate == "mlp" and a.surrogate_epilogue == 1:
+            # the mean field runs inside the surrogate's kernel: no kernel of its own to time
+            stages["meanfield_kernel_ms"] = None
+            stages["meanfield_frac"] = None
+            stages["meanfield_in"] = "k_mlp_tc epilogue"
+        else:
+            t_mf = (per_step[2] - surrogate_ms) * 1e-3
+            stages["meanfield_kernel_ms"] = float(per_step[2] - surrogate_ms)
+            stages["meanfield_frac"] = mf_ops * npairs / t_mf / 1e12 / alu_peak
         stages["mc_frac"] = OPS_PER_PAIR["mc"] * npairs / (per_step[3] * 1e-3) / 1e12 / alu_peak
     # the pair search: candidate distance tests of the count pass (after the ballot prefilter) at
     # SEARCH_OPS_PER_TEST lane operations each, over the whole search stage's time
@@ -736,6 +758,7 @@ def main():
             for rate in ("closed", "quad", "mlp"):
                 c2 = dmb.Context(prm["sigma0_cm2"], n, prm["m_chi_mp"], prm["v0_kms"], prm["periodic"],
                                  tuple(prm["box"]), prm["seed"], fp64=a.fp64, rate_mode=modes[rate], stream=stream)
+                c2.dmb_set_surrogate_epilogue(a.surrogate_epilogue)
                 if rate == "mlp":
                     c2.dmb_load_surrogate(surrogate)
                 if shapes is not None:

@@ -361,6 +361,17 @@ dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, u
  * and the substeps always use the separate passes.) */
 dmb_status dmb_set_fusion(dmb_ctx *ctx, int32_t on);
 
+/* Where the float32 mean field with the learned surrogate (DMB_RATE_MLP on the tensor-core
+ * engine) sums its pairs (Eqs. gas-dVdt, gas-dTdt): mode = 0 (the default, faster on the galaxy
+ * workloads): the surrogate's tensor-core kernel stores every pair's (FA, FB) and the mean-field
+ * kernel reads them back, summing in segments of the autotuned length.  mode = 1: inside the
+ * surrogate's kernel, which forms each pair's overlap while its last MMA runs and its rates after
+ * the output layer, sums the pair terms per gas row over each warp's 32 pairs and leaves the
+ * float64 sum over those partial sums to one thread per gas row; no rate is stored.  The two
+ * modes differ only in the order of the float32 additions.  The fused pair pass of
+ * dmb_set_fusion(ctx, 1) always reads stored rates.  Other values: DMB_ERR_ARG. */
+dmb_status dmb_set_surrogate_epilogue(dmb_ctx *ctx, int32_t mode);
+
 /* Which power-law indices the next dmb_train_surrogate covers: 0 (the default) the scan's
  * {-4, -2, 0, 2} and the context's n, one network for all of them; 1 the context's n only (the
  * network's fourth input is then constant, and all of its capacity serves that n).  Other values:

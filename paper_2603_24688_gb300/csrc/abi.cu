@@ -69,6 +69,10 @@ struct dmb_ctx {
   bool mlp_ready = false;
   int mlp_engine = 0;            // 0: tcgen05 tiles (mlp_tc.cu), 1: warp-level mma.sync pass
   DevBuf tc_tiles;               // row of every pair of the surrogate's pass
+  // dmb_set_surrogate_epilogue: 1 the tensor-core kernel forms the mean field in its epilogue
+  // (per-warp row sums in tc_part), 0 (faster) it stores each pair's rates for the mean-field kernel
+  int tc_epilogue = 0;
+  DevBuf tc_part;
   bool tc_skip_commit = false;   // dmb_debug_tc_timeout: inject one timed-out wait into the next launch
   int device = 0;                // the CUDA device the context was created on
   // batched boxes (dmb_step_batched): caller box index arrays of the current build and tables
@@ -668,6 +672,55 @@ dmb_status surrogate_rates(dmb_ctx *ctx, const MlpRun &mr, const SegView &sv, co
   return DMB_OK;
 }
 
+// Whether a float32 mean field with the surrogate runs in the tensor-core kernel's epilogue.
+template <typename R>
+bool surrogate_epilogue(const dmb_ctx *ctx) {
+  return sizeof(R) == 4 && ctx->rc.rate_mode == DMB_RATE_MLP && ctx->mlp_engine == 0 && ctx->tc_epilogue == 1;
+}
+
+// The gas mean field of rows k < n_rows of the prefix R_ptr (gas list[k], or gas k without a
+// list) with the surrogate's rates formed and used inside the tensor-core kernel (no rates
+// stored), then the float64 finish into o.
+dmb_status surrogate_meanfield(dmb_ctx *ctx, const MlpRun &mr, const int64_t *R_ptr, int64_t n_rows,
+                               const uint32_t *list, int64_t n_q, const MfOut &o) {
+  if (n_rows <= 0) return DMB_OK;
+  TcArgs a = {};
+  a.p = mr.p;
+  a.w2 = mr.w2;
+  a.w3 = mr.w3;
+  a.n = n_q;
+  a.R_ptr = R_ptr;
+  a.n_rows = n_rows;
+  a.list = list;
+  a.row_ptr = ptr<int64_t>(ctx->sg.row_ptr);
+  a.rows = ptr<uint32_t>(ctx->sg.rows);
+  a.G_V = ptr<float4>(ctx->gas.V);
+  a.D_V = ptr<float4>(ctx->dm.V);
+  a.dom = mr.dom;
+  a.rc = ctx->rc;
+  a.fallback_count = mr.fallback_count;
+  a.status = ptr<uint32_t>(ctx->status);
+  a.skip_commit = ctx->tc_skip_commit ? 1 : 0;
+  ctx->tc_skip_commit = false;
+  a.n_dev = ctx->capturing ? ctx->pairs_dev : nullptr;
+  const SpeciesView<float> G = view<float>(ctx->gas, ctx->nbox > 0), D = view<float>(ctx->dm, ctx->nbox > 0);
+  a.G_P = G.P;
+  a.G_L = G.L;
+  a.D_P = D.P;
+  a.D_L = D.L;
+  a.G_bid = G.bid;
+  a.bx = ctx->bx;
+  a.gtab = ptr<float4>(ctx->gtab);
+  const int64_t nq = n_q > 0 ? n_q : 0;
+  if (!ensure(ctx->tc_tiles, (size_t)nq * 4 + 16) || !ensure(ctx->tc_part, ((size_t)(nq >> 5) + n_rows + 1) * 24))
+    return fail(ctx, DMB_ERR_OOM, "surrogate mean-field scratch");
+  a.part = ptr<float>(ctx->tc_part);
+  CK(mlp_tc_meanfield(a, ptr<uint32_t>(ctx->tc_tiles), ctx->shp.tc_wg, G.K, G.perm, o.acc, o.dudt, o.e_exp,
+                      ctx->stream, &ctx->launches),
+     "surrogate mean field (tensor cores)");
+  return DMB_OK;
+}
+
 template <typename R>
 dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp) {
   const SpeciesView<R> D = view<R>(ctx->dm, ctx->nbox > 0), G = view<R>(ctx->gas, ctx->nbox > 0);
@@ -688,9 +741,20 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
       return fail(ctx, DMB_ERR_DOMAIN, "the surrogate was not trained for this cross section (law or power-law index)");
     mr = mlp_run(ctx);
     CK(cudaMemsetAsync(ctx->mlp_fallback.p, 0, 8, ctx->stream), "memset");
+    const bool tm = ctx->timing && !ctx->capturing;
+    if (surrogate_epilogue<R>(ctx)) {
+      if (tm) CK(cudaEventRecord(ctx->sev[0], ctx->stream), "event");
+      const dmb_status st =
+          surrogate_meanfield(ctx, mr, ptr<int64_t>(ctx->sg.row_ptr), ctx->gas.n, nullptr, ctx->sg.n_pairs, o);
+      if (st != DMB_OK) return st;
+      if (tm) {
+        CK(cudaEventRecord(ctx->sev[1], ctx->stream), "event");
+        ctx->sev_pending = true;
+      }
+      return DMB_OK;
+    }
     if (!ensure(ctx->mlp_rates, (size_t)ctx->sg.n_pairs * 8 + 8)) return fail(ctx, DMB_ERR_OOM, "surrogate rates");
     mr.rates = ptr<float2>(ctx->mlp_rates);
-    const bool tm = ctx->timing && !ctx->capturing;
     if (sizeof(R) == 4) {
       if (tm) CK(cudaEventRecord(ctx->sev[0], ctx->stream), "event");
       const dmb_status st = surrogate_rates(ctx, mr, sv, ptr<int64_t>(ctx->sg.row_ptr), ctx->gas.n, nullptr,
@@ -901,7 +965,8 @@ dmb_status set_bins_impl(dmb_ctx *ctx, const uint8_t *dm_bin, const uint8_t *gas
   if (ctx->rc.rate_mode == DMB_RATE_MLP) {
     CK(prepare_mlp_pair_rates(), "surrogate kernel attributes");
     CK(mlp_tc_prepare(), "surrogate kernel attributes");
-    if (!ensure(ctx->tc_tiles, (size_t)ctx->bin_tab[3][DMB_NBINS] * 4 + 16))
+    if (!ensure(ctx->tc_tiles, (size_t)ctx->bin_tab[3][DMB_NBINS] * 4 + 16) ||
+        !ensure(ctx->tc_part, ((size_t)(ctx->bin_tab[3][DMB_NBINS] >> 5) + (size_t)ctx->gas.n + 1) * 24))
       return fail(ctx, DMB_ERR_OOM, "surrogate pair rows");
   }
   CK(cudaStreamSynchronize(s), "synchronise");
@@ -938,13 +1003,17 @@ dmb_status substep_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int 
     mr = mlp_run(ctx);
     mr.rates = ptr<float2>(ctx->mlp_rates);
     CK(cudaMemsetAsync(ctx->mlp_fallback.p, 0, 8, s), "memset");
-    if (sizeof(R) == 4 && nseg > 0) {
+    if (surrogate_epilogue<R>(ctx)) {
+      const dmb_status st = surrogate_meanfield(ctx, mr, ptr<int64_t>(ctx->act_gpairs), nga,
+                                                ptr<uint32_t>(ctx->act_gas), ctx->bin_tab[3][lim], o);
+      if (st != DMB_OK) return st;
+    } else if (sizeof(R) == 4 && nseg > 0) {
       const dmb_status st = surrogate_rates(ctx, mr, sv, ptr<int64_t>(ctx->act_gpairs), nga,
                                             ptr<uint32_t>(ctx->act_gas), ctx->bin_tab[3][lim]);
       if (st != DMB_OK) return st;
     }
   }
-  if (nga > 0)
+  if (nga > 0 && !surrogate_epilogue<R>(ctx))
     CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv, nseg,
                            ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr, ctx->shp.mf_bps, s, L),
        "meanfield");
@@ -1403,7 +1472,8 @@ static dmb_status presize_batch(dmb_ctx *ctx) {
             ensure(ctx->mf_part, (size_t)c.segs * 6 * rb) && ensure(ctx->gate, 16) && ensure(ctx->cap_need, 64) &&
             ensure(ctx->step_dev, 8);
   if (ok && ctx->rc.rate_mode == DMB_RATE_MLP)
-    ok = ensure(ctx->mlp_rates, (size_t)c.pairs * 8 + 8) && ensure(ctx->tc_tiles, (size_t)c.pairs * 4);
+    ok = ensure(ctx->mlp_rates, (size_t)c.pairs * 8 + 8) && ensure(ctx->tc_tiles, (size_t)c.pairs * 4 + 16) &&
+         ensure(ctx->tc_part, ((size_t)(c.pairs >> 5) + (size_t)ctx->gas.n + 1) * 24);
   if (!ok) return fail(ctx, DMB_ERR_OOM, "device allocation failed for the captured batched step");
   return DMB_OK;
 }
@@ -1578,6 +1648,17 @@ dmb_status dmb_set_fusion(dmb_ctx *ctx, int32_t on) {
     ctx->pairs_ready = false;   // the search writes the pairs' gas-major positions only when fused
   }
   ctx->fuse = on == 1;
+  return DMB_OK;
+}
+
+dmb_status dmb_set_surrogate_epilogue(dmb_ctx *ctx, int32_t mode) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (mode != 0 && mode != 1) return fail(ctx, DMB_ERR_ARG, "mode must be 0 or 1");
+  if (mode != ctx->tc_epilogue) {
+    clear_batch_graph(ctx);     // the captured step holds the other kernels
+    invalidate_substeps(ctx);
+  }
+  ctx->tc_epilogue = mode;
   return DMB_OK;
 }
 

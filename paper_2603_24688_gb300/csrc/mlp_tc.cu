@@ -290,7 +290,11 @@ __device__ __forceinline__ void fetch_stage(const TcArgs &a, int64_t q, int stag
 // MODE_PAIRS: rows are gas-major pairs (processing order q over a row-start prefix R_ptr),
 // outputs the normalised rates (FA, FB) at the pair's index p; out-of-box rows take the
 // quadrature (counted), cold gas is skipped (the mean field uses the exact cold limit).
-enum { MODE_X = 0, MODE_PAIRS = 1 };
+// MODE_MF: the same rows, and the rates go straight into the gas mean field: the pair's
+// geometry (displacement, distance, overlap g, M_i g) is formed while the last layer's MMA runs,
+// the rates (or the cold limit) after the output layer, and the row's six terms are summed per
+// gas row over each warp's 32 rows into the per-segment sums.
+enum { MODE_X = 0, MODE_PAIRS = 1, MODE_MF = 2 };
 
 template <int NWG, int MODE, bool TSA>
 __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
@@ -389,6 +393,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
   bool skip_commit = a.skip_commit != 0 && blockIdx.x == 0 && g == 0;
   const uint64_t wait_ns = a.wait_ns ? a.wait_ns : 2000000000ull;
   const float alpha = (float)a.rc.alpha;
+  const float inv_v0 = (float)(1.0 / a.rc.v0), inv_vc2 = (float)a.rc.inv_vc2;
   if (a.n_dev != nullptr) a.n = min(a.n, *a.n_dev);   // rows counted on the device (captured steps)
   const int64_t n_tiles = (a.n + TC_ROWS - 1) / TC_ROWS;
   const int64_t stride = (int64_t)gridDim.x * NWG;
@@ -408,14 +413,26 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     float s2 = 0.f;                                   // (w / varsigma)^2
     float sg2 = 0.f;                                  // varsigma^2
     bool use = false, in_dom = false;
+    // MODE_MF: the row's gas row k (the segment key; all ones for no row), its particles, the
+    // relative velocity w = v_i - V_j, v_i.w, and later M_i g_ij
+    uint32_t key = 0xFFFFFFFFu, cur_i = 0u, cur_j = 0u;
+    float wx = 0.f, wy = 0.f, wz = 0.f, vdw = 0.f, tM = 0.f;
     if (nxt.q >= 0) {
       if (MODE == MODE_X) {
         x[0] = nxt.Vi.x; x[1] = nxt.Vi.y; x[2] = nxt.Vi.z; x[3] = nxt.Vi.w;
         use = in_dom = true;
       } else {
         const float sig = nxt.Vj.w;
+        wx = nxt.Vi.x - nxt.Vj.x;
+        wy = nxt.Vi.y - nxt.Vj.y;
+        wz = nxt.Vi.z - nxt.Vj.z;
+        if (MODE == MODE_MF) {
+          key = (uint32_t)nxt.k;
+          cur_i = nxt.i;
+          cur_j = nxt.j;
+          vdw = nxt.Vi.x * wx + nxt.Vi.y * wy + nxt.Vi.z * wz;
+        }
         if (sig > 0.0f) {
-          const float wx = nxt.Vi.x - nxt.Vj.x, wy = nxt.Vi.y - nxt.Vj.y, wz = nxt.Vi.z - nxt.Vj.z;
           const float sig2 = sig * sig;
           sg2 = sig2;
           s2 = __fdividef(wx * wx + wy * wy + wz * wz, sig2);
@@ -487,6 +504,16 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
       } else {
         fetch_stage<MODE>(a, 0, 2, nxt);
         fetch_stage<MODE>(a, 0, 3, nxt);
+        if (MODE == MODE_MF && key != 0xFFFFFFFFu) {
+          // the pair's overlap while the last MMA runs (Eq. gas-dVdt's g_ij, the kernels'
+          // canonical displacement and distance)
+          const float4 Pi = a.D_P[cur_i], Li = a.D_L[cur_i], Pj = a.G_P[cur_j], Lj = a.G_L[cur_j];
+          const BoxSide side = a.bx.boxes != nullptr ? a.bx.boxes[a.G_bid[cur_j]] : box_side<GEOM_BOX>(a.bx, 0);
+          float dx, dy, dz;
+          pair_dx<float>(Pi, Li, Pj, Lj, a.bx.periodic, side, dx, dy, dz);
+          const float d = sqrt_pair(dist2_rn<float>(dx, dy, dz));
+          tM = Li.w * overlap_g<float>(a.gtab, d, Pi.w, Pj.w);
+        }
       }
       // the group's first warp waits (bounded) for the MMA while the other three wait at the
       // group's barrier, which also makes the group agree on the outcome, so that a timeout is
@@ -558,6 +585,53 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
         a.Y[2 * p] = y[0];
         a.Y[2 * p + 1] = y[1];
       }
+    } else if (MODE == MODE_MF) {
+      float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (key != 0xFFFFFFFFu) {
+        const float w2 = wx * wx + wy * wy + wz * wz;
+        float FA, FB;
+        if (use) {
+          if (in_dom) {
+            mlp_outputs(a.dom, s2, sg2, y, FA, FB);
+          } else {
+            rates_quad<float>(0.5f * s2, a.rc.n, alpha, FA, FB, sg2 * inv_vc2);
+            ++fallback;
+          }
+        } else {   // cold gas: the exact limit A = sigma(w) w, B = sigma(w) w^3
+          const float wn = sqrt_t(w2);
+          const float sn = sigma_ratio<float>(wn, a.rc.n, inv_v0, inv_vc2);
+          FA = sn * wn;
+          FB = sn * wn * w2;
+        }
+        const float tA = tM * FA;
+        c[0] = tA * wx;
+        c[1] = tA * wy;
+        c[2] = tA * wz;
+        c[3] = tA * w2;
+        c[4] = tM * FB;
+        c[5] = tA * vdw;
+      }
+      // sums over the warp's rows of the same gas row: the keys ascend along the lanes, so after
+      // the step with offset o lane l holds the sum over [l, l + 2o) within its row; the first
+      // lane of each row writes it
+      const unsigned lane = (unsigned)t & 31u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ko = __shfl_down_sync(DMB_FULL, key, o);
+        const bool same = lane + (unsigned)o < 32u && ko == key;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+          const float v = __shfl_down_sync(DMB_FULL, c[m], o);
+          if (same) c[m] += v;
+        }
+      }
+      const uint32_t kp = __shfl_up_sync(DMB_FULL, key, 1);
+      if (key != 0xFFFFFFFFu && (lane == 0u || kp != key)) {
+        float2 *dst = reinterpret_cast<float2 *>(a.part + 6 * ((T * TC_ROWS + t) / 32 + (int64_t)key));
+        dst[0] = make_float2(c[0], c[1]);
+        dst[1] = make_float2(c[2], c[3]);
+        dst[2] = make_float2(c[4], c[5]);
+      }
     } else if (use) {
       float FA, FB;
       if (in_dom) {
@@ -570,7 +644,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) k_mlp_tc(TcArgs a) {
     }
   }
   if (!ok && t == 0) atomicOr(a.status, DMB_BAD_TIMEOUT);
-  if (MODE == MODE_PAIRS) {
+  if (MODE != MODE_X) {
     fallback = warp_sum<unsigned>(fallback);
     if ((tid & 31) == 0 && fallback && a.fallback_count) atomicAdd(a.fallback_count, (unsigned long long)fallback);
   }
@@ -594,12 +668,15 @@ static bool g_tc_attr = false;
 
 cudaError_t mlp_tc_prepare() {
   if (g_tc_attr) return cudaSuccess;
-  const void *fns[6] = {(const void *)k_mlp_tc<2, MODE_X, true>, (const void *)k_mlp_tc<2, MODE_PAIRS, true>,
-                        (const void *)k_mlp_tc<3, MODE_X, false>, (const void *)k_mlp_tc<3, MODE_PAIRS, false>,
-                        (const void *)k_mlp_tc<4, MODE_X, false>, (const void *)k_mlp_tc<4, MODE_PAIRS, false>};
-  const int smem[6] = {TcLayout<2>::TOTAL, TcLayout<2>::TOTAL, TcLayout<3>::TOTAL,
-                       TcLayout<3>::TOTAL, TcLayout<4>::TOTAL, TcLayout<4>::TOTAL};
-  for (int k = 0; k < 6; ++k) {
+  const void *fns[9] = {(const void *)k_mlp_tc<2, MODE_X, true>,      (const void *)k_mlp_tc<2, MODE_PAIRS, true>,
+                        (const void *)k_mlp_tc<2, MODE_MF, true>,     (const void *)k_mlp_tc<3, MODE_X, false>,
+                        (const void *)k_mlp_tc<3, MODE_PAIRS, false>, (const void *)k_mlp_tc<3, MODE_MF, false>,
+                        (const void *)k_mlp_tc<4, MODE_X, false>,     (const void *)k_mlp_tc<4, MODE_PAIRS, false>,
+                        (const void *)k_mlp_tc<4, MODE_MF, false>};
+  const int smem[9] = {TcLayout<2>::TOTAL, TcLayout<2>::TOTAL, TcLayout<2>::TOTAL,
+                       TcLayout<3>::TOTAL, TcLayout<3>::TOTAL, TcLayout<3>::TOTAL,
+                       TcLayout<4>::TOTAL, TcLayout<4>::TOTAL, TcLayout<4>::TOTAL};
+  for (int k = 0; k < 9; ++k) {
     const cudaError_t e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem[k]);
     if (e != cudaSuccess) return e;
   }
@@ -646,4 +723,60 @@ cudaError_t mlp_tc_pair_rates(TcArgs a, uint32_t *prow, int nwg, cudaStream_t s,
   a.prow = prow;
   if (launches) *launches += 2;
   return launch_any<MODE_PAIRS>(a, nwg, s);
+}
+
+// acc_j = cA sum(M_i g FA w), du_j/dt = cA sum(M_i g FA w^2) - cB sum(M_i g FB) and the expected
+// DM energy change M_j (cB sum(M_i g FB) - cA sum(M_i g FA v_i.w)) (no dt) of row k, from the
+// slots q / 32 + k of its processing positions q, summed in float64 in slot order.
+__global__ void k_tc_mf_finish(const int64_t *__restrict__ R_ptr, int64_t n_rows, const uint32_t *__restrict__ list,
+                               const float4 *__restrict__ G_K, const float4 *__restrict__ G_L,
+                               const uint32_t *__restrict__ G_perm, const float *__restrict__ part,
+                               double *__restrict__ acc, double *__restrict__ dudt, double *__restrict__ e_exp) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_rows) return;
+  const int64_t j = list ? (int64_t)list[k] : k;
+  const int64_t q0 = R_ptr[k], q1 = R_ptr[k + 1];
+  double sum[6] = {0, 0, 0, 0, 0, 0};
+  if (q1 > q0) {
+    for (int64_t u = (q0 >> 5) + k; u <= ((q1 - 1) >> 5) + k; ++u) {
+      const float2 *src = reinterpret_cast<const float2 *>(part + 6 * u);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const float2 v = src[m];
+        sum[2 * m] += (double)v.x;
+        sum[2 * m + 1] += (double)v.y;
+      }
+    }
+  }
+  const float4 K = G_K[j];
+  const double cA = (double)K.x, cB = (double)K.y;
+  const uint32_t c = G_perm[j];
+  acc[3 * (int64_t)c + 0] = cA * sum[0];
+  acc[3 * (int64_t)c + 1] = cA * sum[1];
+  acc[3 * (int64_t)c + 2] = cA * sum[2];
+  dudt[c] = cA * sum[3] - cB * sum[4];
+  if (e_exp) e_exp[j] = (double)G_L[j].w * (cB * sum[4] - cA * sum[5]);
+}
+
+cudaError_t mlp_tc_meanfield(TcArgs a, uint32_t *prow, int nwg, const float4 *G_K, const uint32_t *G_perm,
+                             double *acc, double *dudt, double *e_exp, cudaStream_t s, int64_t *launches) {
+  if (a.n_rows <= 0) return cudaSuccess;
+  if (a.n > 0) {
+    int64_t blocks = (a.n_rows * 32 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_pair_rows<<<(unsigned)blocks, 256, 0, s>>>(a.R_ptr, a.n_rows, prow);
+    a.prow = prow;
+    if (launches) *launches += 2;
+    cudaError_t e;
+    switch (nwg) {
+      case 2: e = launch_tc<2, MODE_MF, true>(a, s); break;
+      case 3: e = launch_tc<3, MODE_MF>(a, s); break;
+      default: e = launch_tc<4, MODE_MF>(a, s); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  k_tc_mf_finish<<<(unsigned)((a.n_rows + 255) / 256), 256, 0, s>>>(a.R_ptr, a.n_rows, a.list, G_K, a.G_L, G_perm,
+                                                                    a.part, acc, dudt, e_exp);
+  if (launches) *launches += 1;
+  return cudaGetLastError();
 }

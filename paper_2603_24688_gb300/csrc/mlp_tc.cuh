@@ -36,6 +36,15 @@ struct TcArgs {
   int skip_commit;
   // captured steps: the row count lives on the device (n is then a capacity); null otherwise
   const int64_t *n_dev;
+  // the mean field in the epilogue (mlp_tc_meanfield): sorted positions (hi, h) and (lo, M) of
+  // both species, the gas box index (batched boxes, else null), the periodic boxes, the overlap
+  // table, and the per-segment sums [slots][6] (slot = q / 32 + k for the rows of row k in the
+  // 32 processing positions of one warp)
+  const float4 *G_P, *G_L, *D_P, *D_L;
+  const uint16_t *G_bid;
+  BoxSplit bx;
+  const float4 *gtab;
+  float *part;
 };
 
 // Shared-memory attributes (call once before any graph capture).
@@ -46,3 +55,11 @@ cudaError_t mlp_tc_prepare();
 cudaError_t mlp_tc_infer(TcArgs a, int nwg, cudaStream_t s, int64_t *launches);
 // Rates of the pairs in processing order; prow: scratch of n uint32 (the row of every q).
 cudaError_t mlp_tc_pair_rates(TcArgs a, uint32_t *prow, int nwg, cudaStream_t s, int64_t *launches);
+// The gas mean field (Eqs. gas-dVdt, gas-dTdt) of the same pairs with the rates never stored:
+// each row's pair terms M_i g_ij (FA w, FA w^2, FB, FA v_i.w) are formed in the epilogue, summed
+// per gas row over each warp's 32 rows (a segmented shuffle reduction in a fixed order) into
+// a.part, and a float64 pass over the rows writes acc and du/dt (caller order, through perm) and
+// the expected DM energy change e_exp (sorted order, may be null).  Rows without pairs get zeros.
+// part holds (n >> 5) + n_rows + 1 slots of 6 floats.
+cudaError_t mlp_tc_meanfield(TcArgs a, uint32_t *prow, int nwg, const float4 *G_K, const uint32_t *G_perm,
+                             double *acc, double *dudt, double *e_exp, cudaStream_t s, int64_t *launches);

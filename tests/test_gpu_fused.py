@@ -68,8 +68,11 @@ def test_fused_step_with_other_providers_and_laws():
         a = _steps(_ctx(w, True, **kw), w, 2, w["dt"] * 50.0)
         b = _steps(_ctx(w, False, **kw), w, 2, w["dt"] * 50.0)
         _same(a, b)
-    # the learned surrogate (the same network in both contexts)
+    # the learned surrogate (the same network in both contexts); the fused pass reads stored
+    # rates, so the separate passes must store them too (mode 1 of dmb_set_surrogate_epilogue sums
+    # the mean field inside the surrogate's kernel, in another float32 order)
     ca, cb = _ctx(w, True, rate=dmb.DMB_RATE_MLP), _ctx(w, False, rate=dmb.DMB_RATE_MLP)
+    cb.dmb_set_surrogate_epilogue(0)
     ca.dmb_train_surrogate(nsamples=1 << 15, epochs=2, seed=4)
     cb.dmb_load_surrogate(ca.dmb_surrogate_params())
     _same(_steps(ca, w, 2, w["dt"] * 50.0), _steps(cb, w, 2, w["dt"] * 50.0))

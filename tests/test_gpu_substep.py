@@ -145,3 +145,49 @@ def test_bins_out_of_range_rejected():
         ctx.dmb_set_bins(_u8(db), _u8(np.zeros(2100, np.uint8)))
     with pytest.raises(dmb.DmbError):
         ctx.dmb_substep(dm, gas, 1, w["dt"])
+
+
+def test_substeps_with_the_surrogate_epilogue():
+    """Substeps with the learned surrogate: the mean field summed inside the tensor-core kernel
+    (dmb_set_surrogate_epilogue(1)) against the stored-rates path (the default) on the same state
+    (another float32 summation order: 1e-5), and its graph replay against direct launches (bit for
+    bit)."""
+    w = _w()
+    p = w["params"]
+    db, gb = _bins(2000, 7), _bins(2100, 8)
+
+    def mk(mode, graph, params=None):
+        c = dmb.Context(p["sigma0_cm2"], p["n"], p["m_chi_mp"], p["v0_kms"], p["periodic"], tuple(p["box"]),
+                        p["seed"], rate_mode=dmb.DMB_RATE_MLP)
+        if params is None:
+            c.dmb_train_surrogate(nsamples=1 << 15, epochs=2, seed=5)
+        else:
+            c.dmb_load_surrogate(params)
+        c.dmb_set_surrogate_epilogue(mode)
+        dm, gas = device_inputs(w)
+        c.dmb_build_grid(dm, gas)
+        c.dmb_neighbors()
+        c.dmb_set_bins(_u8(db), _u8(gb))
+        c.dmb_set_graph(graph)
+        return c, dm, gas
+
+    a = mk(1, False)
+    params = a[0].dmb_surrogate_params()
+    b = mk(1, True, params)
+    r = mk(0, False, params)
+    V0 = a[2]["vel"].cpu().numpy()
+    for s in (1, 2, 3, 4, 8, 1):
+        sa = a[0].dmb_substep(a[1], a[2], s, w["dt"])
+        sb = b[0].dmb_substep(b[1], b[2], s, w["dt"])
+        sr = r[0].dmb_substep(r[1], r[2], s, w["dt"])
+        assert np.array_equal(sa, sb), s
+        assert torch.equal(a[1]["vel"], b[1]["vel"]) and torch.equal(a[2]["vel"], b[2]["vel"]), s
+        assert torch.equal(a[2]["T"], b[2]["T"]), s
+        if s == 1:   # same input state in both modes
+            dVa = a[2]["vel"].cpu().numpy() - V0
+            dVr = r[2]["vel"].cpu().numpy() - V0
+            moved = np.linalg.norm(dVr, axis=1) > 0
+            assert moved.sum() > 100
+            assert np.all(_rel_vec_err(dVa[moved], dVr[moved]) <= 1e-5)
+            np.testing.assert_allclose(a[2]["T"].cpu().numpy(), r[2]["T"].cpu().numpy(), rtol=1e-6)
+

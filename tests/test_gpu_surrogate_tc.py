@@ -5,7 +5,7 @@ warpgroup count: 2 (activations kept in tensor memory as the MMAs' A operand), 3
 import numpy as np
 import pytest
 
-from gpu_common import device_inputs, require_gpu, torch
+from gpu_common import device_inputs, require_gpu, torch, transfer_scales
 from oracle import mlp as O
 from paper_2603_24688_gb300 import dmb
 from paper_2603_24688_gb300 import workloads as W
@@ -104,3 +104,68 @@ def test_tc_pair_rates_match_the_warp_engine(wg):
     assert np.all(err[na > 0] < 2e-3), err.max()
     scale = np.abs(u1) + 1e-3 * np.abs(u1).max()
     assert np.max(np.abs(u0 - u1) / scale) < 2e-3
+
+
+def _modes(ctx, w, nb):
+    """The gas mean field with the rates stored (mode 0) and summed in the epilogue (mode 1)."""
+    out = {}
+    for mode in (0, 1):
+        ctx.dmb_set_surrogate_epilogue(mode)
+        acc = torch.full((nb, 3), float("nan"), dtype=torch.float64, device="cuda")
+        dudt = torch.full((nb,), float("nan"), dtype=torch.float64, device="cuda")
+        ctx.dmb_meanfield_gas(acc, dudt)
+        out[mode] = (acc.cpu().numpy(), dudt.cpu().numpy(), ctx.dmb_surrogate_fallbacks())
+    return out
+
+
+def _gpu_pairs(ctx):
+    n = ctx.dmb_neighbors()
+    pairs = torch.empty((n, 2), dtype=torch.int32, device="cuda")
+    ctx.dmb_neighbors(pairs)
+    pp = pairs.cpu().numpy().view(np.uint32).astype(np.int64)
+    return pp[:, 0], pp[:, 1]
+
+
+@pytest.mark.parametrize("wg", [2, 3, 4])
+@pytest.mark.parametrize("where", ["galaxy", "box"])
+def test_mean_field_in_the_epilogue_matches_stored_rates(wg, where):
+    """dmb_set_surrogate_epilogue(1) forms each pair's overlap and rates inside the tensor-core
+    kernel and sums the pair terms per gas row over each warp's 32 pairs; mode 0 (the default)
+    stores the rates for k_meanfield.  The rates and pair terms are the same, the float32
+    summation order differs: every gas row agrees within 1e-5 of the sums of its absolute pair
+    terms (Eqs. gas-dVdt, gas-dTdt), and the fallback counts are equal."""
+    if where == "galaxy":
+        w = W.subsample(W.named("galaxy1M"), 60_000, 40_000, seed=2)
+        w["params"]["n"] = -2
+    else:   # periodic box: the minimum image inside the epilogue, and cold gas rows
+        w = W.box_workload(n_dm=6000, n_gas=5000, seed=41, n=-2)
+        w["gas"]["T"][::7] = 0.0
+    p = w["params"]
+    ctx = dmb.Context(p["sigma0_cm2"], -2, p["m_chi_mp"], p["v0_kms"], p["periodic"], tuple(p["box"]), p["seed"],
+                      rate_mode=dmb.DMB_RATE_MLP)
+    ctx.dmb_train_surrogate(nsamples=1 << 18, epochs=4, seed=3)
+    _set_wg(ctx, wg)
+    dm, gas = device_inputs(w)
+    ctx.dmb_build_grid(dm, gas)
+    pi, pj = _gpu_pairs(ctx)
+    assert len(pi) > 50_000
+    nb = len(w["gas"]["h"])
+    out = _modes(ctx, w, nb)
+    (a0, u0, f0), (a1, u1, f1) = out[0], out[1]
+    assert f0 == f1
+    assert np.all(np.isfinite(a1)) and np.all(np.isfinite(u1))
+    sa, su = transfer_scales(w, pi, pj, dict(p, n=-2))
+    assert np.all(np.abs(a1 - a0) <= 1e-5 * sa), np.max(np.abs(a1 - a0) / np.maximum(sa, 1e-300))
+    assert np.all(np.abs(u1 - u0) <= 1e-5 * su), np.max(np.abs(u1 - u0) / np.maximum(su, 1e-300))
+    # gas particles without partners get exact zeros in both modes
+    lone = np.setdiff1d(np.arange(nb), pj)
+    assert np.all(a1[lone] == 0.0) and np.all(u1[lone] == 0.0)
+
+
+def test_epilogue_mode_argument_checked():
+    ctx = _ctx()
+    with pytest.raises(dmb.DmbError):
+        ctx.dmb_set_surrogate_epilogue(2)
+    ctx.dmb_set_surrogate_epilogue(0)
+    ctx.dmb_set_surrogate_epilogue(1)
+
