@@ -68,7 +68,7 @@ MLP_ALGO_BYTES_PER_PAIR = 4 + 4 + 16 + 16 + 8
 MLP_MF_DRAM_BYTES_PER_PAIR = (782.105856e6 + 82.870272e6) / 85071169
 MLP_MF_ALGO_BYTES_PER_PAIR = 4 + 4 + 6 * 16 + 24 / 32
 # the surrogate's training recipe (samples of the float64 device quadrature, Adam epochs)
-TRAIN = dict(nsamples=1 << 21, epochs=96, seed=11)
+TRAIN = dict(nsamples=1 << 21, epochs=128, seed=11)
 # the power-law indices of the benchmark's cross-section scan
 SCAN_N = (-4, -2, 0, 2)
 
@@ -301,23 +301,34 @@ def cpu_oracle_all_cores(w, target_pairs=60_000, per_core=2, seed=0, cores=None)
 
 
 def envelope(n):
-    """Constants of the surrogate's envelopes (1 + cA x)^eA, (1 + cB x)^eB for sigma ~ v^n."""
-    c = (n + 6) / 2.0
-    eA, eB = (n + 1) / 2.0, (n + 3) / 2.0
-    cA = (math.gamma(2.5) / math.gamma(c)) ** (1.0 / eA) if eA != 0 else 1.0
-    cB = (math.gamma(1.5) / math.gamma(c)) ** (1.0 / eB) if eB != 0 else 1.0
-    return cA, eA, cB, eB
+    """Envelopes (p, q, r, m) of the surrogate's FA and FB for sigma ~ v^n: E = (1 + p x + q x^2 +
+    r x^3)^m with the large-x power of 1F1(a, b; -x) and its first two Taylor coefficients."""
+    def of(a, b):
+        e = -a
+        if e == 0:
+            return 0.0, 0.0, 0.0, 0.0
+        m, k1, k2 = e / 3.0, e / b, e * (e - 1.0) / (2.0 * b * (b + 1.0))
+        p = k1 / m
+        return p, max((k2 - 0.5 * k1 * k1) / m + 0.5 * p * p, 0.0), (math.gamma(b) / math.gamma(b + e)) ** (1.0 / m), m
+    return of(-(n + 1) / 2.0, 2.5), of(-(n + 3) / 2.0, 1.5)
 
 
-def surrogate_errors(params, n, prm):
-    """Relative error of the surrogate's FA, FB (tensor-core engine) against the float64 device
-    quadrature on a grid over the training box (s: 161 points, tau: 6, m_chi: 3) at index n."""
+def workload_tau(w):
+    """(min, max) of tau = varsigma^2 / v0^2 over the workload's hot gas, varsigma^2 = k_B T / (mu m_p)."""
+    kt = 1.380649e-16 / 1.67262192e-24 / 1e10                  # k_B / m_p in (km/s)^2 / K
+    T, mu = w["gas"]["T"], w["gas"]["mu"]
+    hot = T > 0
+    tau = kt * T[hot] / mu[hot] / w["params"]["v0_kms"] ** 2
+    return float(tau.min()), float(tau.max())
+
+
+def rate_errors(params, n, prm, s, tau, m):
+    """Relative errors of the surrogate's FA, FB (tensor-core engine) against the float64 device
+    quadrature at index n, at the inputs (s, tau, m_chi) given as flat arrays."""
     import torch
     from paper_2603_24688_gb300 import dmb
-    s = np.geomspace(1e-2, 1e2, 161)
-    S, T, M = np.meshgrid(s, np.geomspace(1e-3, 1e2, 6), np.array([0.5, 2.0, 10.0]), indexing="ij")
-    X = np.stack([0.5 * np.log10(S.ravel()), 0.5 * np.log10(T.ravel()), np.log10(M.ravel()),
-                  np.full(S.size, n / 4.0)], 1).astype(np.float32)
+    X = np.stack([0.5 * np.log10(s), 0.5 * np.log10(tau), np.log10(m), np.full(s.size, n / 4.0)],
+                 1).astype(np.float32)
     c = dmb.Context(prm["sigma0_cm2"], n, prm["m_chi_mp"], prm["v0_kms"], False, (0.0, 0.0, 0.0), prm["seed"],
                     rate_mode=dmb.DMB_RATE_MLP)
     c.dmb_load_surrogate(params)
@@ -325,18 +336,59 @@ def surrogate_errors(params, n, prm):
     c.dmb_surrogate_infer_tc(torch.from_numpy(X).cuda(), Y)
     q = dmb.Context(prm["sigma0_cm2"], n, prm["m_chi_mp"], prm["v0_kms"], False, (0.0, 0.0, 0.0), prm["seed"],
                     fp64=True, rate_mode=dmb.DMB_RATE_QUAD)
-    x = 0.5 * S.ravel() ** 2
+    x = 0.5 * s.astype(np.float64) ** 2
     F = torch.empty((x.size, 2), dtype=torch.float64, device="cuda")
     q.dmb_debug_rates(torch.from_numpy(x).cuda(), F)
     torch.cuda.synchronize()
     F, Y = F.cpu().numpy(), Y.cpu().numpy().astype(np.float64)
-    cA, eA, cB, eB = envelope(n)
-    eA_ = np.abs(np.expm1(Y[:, 0] - (np.log(F[:, 0]) - eA * np.log1p(cA * x))))
-    eB_ = np.abs(np.expm1(Y[:, 1] - (np.log(F[:, 1]) - eB * np.log1p(cB * x))))
+    envA, envB = envelope(n)
+
+    def log_env(env):
+        p, q, r, m = env
+        return m * np.log1p(x * (p + x * (q + x * r)))
+    eA_ = np.abs(np.expm1(Y[:, 0] - (np.log(F[:, 0]) - log_env(envA))))
+    eB_ = np.abs(np.expm1(Y[:, 1] - (np.log(F[:, 1]) - log_env(envB))))
     c.close()
     q.close()
     return {"mean_A": float(eA_.mean()), "max_A": float(eA_.max()), "mean_B": float(eB_.mean()),
             "max_B": float(eB_.max())}
+
+
+def surrogate_errors(params, n, prm, tau=None, m_chi=None):
+    """rate_errors on a grid over the training box (s: 161 points, tau: 6, m_chi: 3), or with
+    tau = (lo, hi) and m_chi given, over the whole s range at the workload's own tau range (6
+    points, or 1 if lo == hi) and m_chi (s: 641 points)."""
+    if tau is None:
+        s, taus, ms = np.geomspace(1e-2, 1e2, 161), np.geomspace(1e-3, 1e2, 6), np.array([0.5, 2.0, 10.0])
+    else:
+        s = np.geomspace(1e-2, 1e2, 641)
+        taus = np.array([tau[0]]) if tau[0] == tau[1] else np.geomspace(tau[0], tau[1], 6)
+        ms = np.array([m_chi])
+    S, T, M = np.meshgrid(s, taus, ms, indexing="ij")
+    return rate_errors(params, n, prm, S.ravel(), T.ravel(), M.ravel())
+
+
+def workload_pair_inputs(ctx, dm, gas, prm, k=1 << 20, seed=5):
+    """(s, tau) of k pairs drawn uniformly (seeded) from the pair set of (dm, gas), searched on
+    the given context, hot gas only: s = |v_i - V_j| / varsigma_j, tau = varsigma_j^2 / v0^2,
+    varsigma^2 = k_B T / (mu m_p)."""
+    import torch
+    ctx.dmb_build_grid(dm, gas)
+    npairs = ctx.dmb_neighbors()
+    pairs = torch.empty((npairs, 2), dtype=torch.int32, device="cuda")
+    ctx.dmb_neighbors(pairs)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    idx = torch.randint(0, npairs, (k,), device="cuda", generator=g)
+    pi, pj = pairs[idx, 0].long(), pairs[idx, 1].long()
+    del pairs
+    kt = 1.380649e-16 / 1.67262192e-24 / 1e10
+    sig2 = kt * gas["T"][pj] / gas["mu"][pj]
+    hot = sig2 > 0
+    w = torch.linalg.norm(dm["vel"][pi] - gas["vel"][pj], dim=1)
+    s = (w[hot] / torch.sqrt(sig2[hot])).cpu().numpy()
+    tau = (sig2[hot] / prm["v0_kms"] ** 2).cpu().numpy()
+    return s, tau
 
 
 def workload_desc(a, w):
@@ -753,6 +805,7 @@ def main():
         # the cross-section scan of the workload: every rate provider's mean field and the whole
         # surrogate step at each n, with the surrogate's rate error at that n
         per_n = {}
+        pair_inputs = None
         for n in SCAN_N:
             row = {}
             for rate in ("closed", "quad", "mlp"):
@@ -778,6 +831,20 @@ def main():
             row["mlp_speedup_over_quad"] = row["quad_meanfield_ms"] / row["mlp_meanfield_ms"]
             if surrogate is not None:
                 row["surrogate_rate_error"] = surrogate_errors(surrogate, n, prm)
+                # the same over the (s, tau, m_chi) this workload's pairs can reach, and at the
+                # inputs of 2^20 of its pairs drawn at random (those inside the training box; the
+                # others take the quadrature)
+                row["surrogate_rate_error_workload"] = surrogate_errors(surrogate, n, prm, tau=workload_tau(w),
+                                                                        m_chi=prm["m_chi_mp"])
+                if pair_inputs is None:
+                    c3 = new_ctx("closed")
+                    pair_inputs = workload_pair_inputs(c3, dm, gas, prm)
+                    c3.close()
+                ps, pt = pair_inputs
+                inb = (ps >= 1e-2) & (ps <= 1e2) & (pt >= 1e-3) & (pt <= 1e2)
+                pe = rate_errors(surrogate, n, prm, ps[inb], pt[inb], np.full(int(inb.sum()), prm["m_chi_mp"]))
+                pe.update(sampled=int(ps.size), in_box=int(inb.sum()))
+                row["surrogate_rate_error_pairs"] = pe
             per_n[str(n)] = row
         providers["per_n"] = per_n
     if train_report is not None:
@@ -845,10 +912,26 @@ def main():
         f1.record(stream)
         barrier()
         ms_e, pairs_e = reduce_across_ranks(f0.elapsed_time(f1), npairs * a.e2e_steps, dist)
+        # the copies alone (no step running beside them), for the record
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c2 = torch.cuda.Event(enable_timing=True)
+        d_, g_ = bufs[0]
+        c0.record(stream)
+        for sp, dst in (("dm", d_), ("gas", g_)):
+            for name, v in dst.items():
+                v.copy_(host[sp][name], non_blocking=True)
+        c1.record(stream)
+        outs[0]["dm_vel"].copy_(d_["vel"], non_blocking=True)
+        outs[0]["gas_vel"].copy_(g_["vel"], non_blocking=True)
+        outs[0]["gas_T"].copy_(g_["T"], non_blocking=True)
+        c2.record(stream)
+        torch.cuda.synchronize()
         e2e = {"value": pairs_e / (ms_e * 1e-3), "unit": "pairs/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "pipelined": "inputs of step k+1 copied while step k runs; results of step k copied while step k+1 runs",
-               "ms_per_step": ms_e / a.e2e_steps}
+               "ms_per_step": ms_e / a.e2e_steps,
+               "h2d_ms_alone": c0.elapsed_time(c1), "d2h_ms_alone": c1.elapsed_time(c2)}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:

@@ -9,9 +9,10 @@ W1[128][4] b1 W2[128][128] b2 W3[128][128] b3 W4[2][128] b4.  The GPU feeds the 
 accumulates in float32; `forward(..., bf16=True)` applies the same roundings in float64.
 
 Targets (what the network learns): with x = s^2/2 and the App. B closed forms
-FA = 1F1(-(n+1)/2, 5/2; -x), FB = 1F1(-(n+3)/2, 3/2; -x), the outputs are
-log FA - eA log(1 + cA x) and log FB - eB log(1 + cB x), eA = (n+1)/2, eB = (n+3)/2, with
-cA, cB fixed by the large-x limits 1F1(a, b; -x) -> Gamma(b)/Gamma(b-a) x^-a (DLMF 13.7.2).
+FA = 1F1(-(n+1)/2, 5/2; -x), FB = 1F1(-(n+3)/2, 3/2; -x), the outputs are log F - log E for
+each, against the envelope E = (1 + p x + q x^2 + r x^3)^m of F = 1F1(a, b; -x), e = -a, m = e/3:
+r from the large-x limit 1F1(a, b; -x) -> Gamma(b)/Gamma(b-a) x^-a (DLMF 13.7.2), p and q from
+the series 1 + (e/b) x + e(e-1)/(2b(b+1)) x^2 + ... (DLMF 13.2.2), q kept >= 0; E = 1 for e = 0.
 
 Parity: pinned by finite differences of this module's own loss (tests/test_oracle_mlp.py)
 and by the closed-form targets being the pinned oracle rates.
@@ -99,12 +100,27 @@ def loss_and_grad(p, X, Y, bf16_ops=True):
     return loss, pack(g)
 
 
+def envelope_of(a, b):
+    """(p, q, r, m) of the envelope of 1F1(a, b; -x) (module docstring)."""
+    e = -a
+    if e == 0:
+        return 0.0, 0.0, 0.0, 0.0
+    m = e / 3.0
+    k1, k2 = e / b, e * (e - 1.0) / (2.0 * b * (b + 1.0))
+    p = k1 / m
+    q = max((k2 - 0.5 * k1 * k1) / m + 0.5 * p * p, 0.0)
+    r = (math.gamma(b) / math.gamma(b + e)) ** (1.0 / m)
+    return p, q, r, m
+
+
 def envelope(n):
-    c = (n + 6) / 2.0
-    eA, eB = (n + 1) / 2.0, (n + 3) / 2.0
-    cA = (math.gamma(2.5) / math.gamma(c)) ** (1.0 / eA) if eA != 0 else 1.0
-    cB = (math.gamma(1.5) / math.gamma(c)) ** (1.0 / eB) if eB != 0 else 1.0
-    return cA, eA, cB, eB
+    """Envelopes of FA and FB at index n: ((p, q, r, m) of FA, (p, q, r, m) of FB)."""
+    return envelope_of(-(n + 1) / 2.0, 2.5), envelope_of(-(n + 3) / 2.0, 1.5)
+
+
+def log_envelope(env, x):
+    p, q, r, m = env
+    return m * np.log1p(x * (p + x * (q + x * r)))
 
 
 def inputs(s, tau, m_chi, n):
@@ -117,11 +133,11 @@ def targets(s, n):
     x = 0.5 * np.asarray(s, dtype=np.float64) ** 2
     FA = hyp1f1_neg_arr(-(n + 1) / 2.0, 2.5, x)
     FB = hyp1f1_neg_arr(-(n + 3) / 2.0, 1.5, x)
-    cA, eA, cB, eB = envelope(n)
-    return np.stack([np.log(FA) - eA * np.log1p(cA * x), np.log(FB) - eB * np.log1p(cB * x)], axis=1)
+    eA, eB = envelope(n)
+    return np.stack([np.log(FA) - log_envelope(eA, x), np.log(FB) - log_envelope(eB, x)], axis=1)
 
 
 def rates_from_outputs(y, s, n):
     x = 0.5 * np.asarray(s, dtype=np.float64) ** 2
-    cA, eA, cB, eB = envelope(n)
-    return np.exp(y[:, 0]) * (1.0 + cA * x) ** eA, np.exp(y[:, 1]) * (1.0 + cB * x) ** eB
+    eA, eB = envelope(n)
+    return np.exp(y[:, 0] + log_envelope(eA, x)), np.exp(y[:, 1] + log_envelope(eB, x))

@@ -566,14 +566,27 @@ dmb_status neighbors_capped(dmb_ctx *ctx) {
 // ---- surrogate helpers ---------------------------------------------------------------------
 double alpha_of(int n) { return pow(2.0, (n + 5) / 2.0) * tgamma(3.0 + n / 2.0) / sqrt(M_PI); }
 
-// envelope constants: EA = (1 + cA x)^((n+1)/2), EB = (1 + cB x)^((n+3)/2) with the large-x limits
-// of 1F1(-(n+1)/2, 5/2; -x) and 1F1(-(n+3)/2, 3/2; -x) (DLMF 13.7.2)
-void envelope(int n, double &cA, double &eA, double &cB, double &eB) {
-  const double c = (n + 6) / 2.0;
-  eA = (n + 1) / 2.0;
-  eB = (n + 3) / 2.0;
-  cA = eA != 0.0 ? pow(tgamma(2.5) / tgamma(c), 1.0 / eA) : 1.0;
-  cB = eB != 0.0 ? pow(tgamma(1.5) / tgamma(c), 1.0 / eB) : 1.0;
+// Envelope E(x) = (1 + p x + q x^2 + r x^3)^m of F = 1F1(a, b; -x) with e = -a != 0 (FA: a = -(n+1)/2,
+// b = 5/2; FB: a = -(n+3)/2, b = 3/2), m = e/3: r carries the large-x limit F -> Gamma(b)/Gamma(b+e) x^-e
+// (DLMF 13.7.2), p and q the first two Taylor coefficients F = 1 + (e/b) x + e(e-1)/(2b(b+1)) x^2 + ...
+// (DLMF 13.2.2), so the network's target log F - log E vanishes at both ends as O(x^3) and O(1/x);
+// q is kept >= 0 so that the cubic stays positive.  e = 0: E = 1.  env = {p, q, r, m}.
+void envelope_of(double a, double b, double env[4]) {
+  const double e = -a;
+  if (e == 0.0) {
+    env[0] = env[1] = env[2] = env[3] = 0.0;
+    return;
+  }
+  const double m = e / 3.0, k1 = e / b, k2 = e * (e - 1.0) / (2.0 * b * (b + 1.0));
+  const double pc = k1 / m;
+  env[0] = pc;
+  env[1] = fmax((k2 - 0.5 * k1 * k1) / m + 0.5 * pc * pc, 0.0);
+  env[2] = pow(tgamma(b) / tgamma(b + e), 1.0 / m);
+  env[3] = m;
+}
+void envelope(int n, double envA[4], double envB[4]) {
+  envelope_of(-(n + 1) / 2.0, 2.5, envA);
+  envelope_of(-(n + 3) / 2.0, 1.5, envB);
 }
 
 dmb_status ensure_mlp(dmb_ctx *ctx) {
@@ -619,12 +632,12 @@ MlpRun mlp_run(dmb_ctx *ctx) {
   d.tau_hi = (float)pow(10.0, ctx->mlp_box[3]);
   d.m_lo = (float)pow(10.0, ctx->mlp_box[4]);
   d.m_hi = (float)pow(10.0, ctx->mlp_box[5]);
-  double cA, eA, cB, eB;
-  envelope(ctx->rc.n, cA, eA, cB, eB);
-  d.cA = (float)cA;
-  d.cB = (float)cB;
-  d.eA = (float)eA;
-  d.eB = (float)eB;
+  double envA[4], envB[4];
+  envelope(ctx->rc.n, envA, envB);
+  for (int k = 0; k < 4; ++k) {
+    d.envA[k] = (float)envA[k];
+    d.envB[k] = (float)envB[k];
+  }
   // the second input: varsigma^2 / v0^2 for the power law, varsigma^2 / v_c^2 for the screened law
   d.inv_v0sq = ctx->xsec == 1 ? (float)(1.0 / (ctx->v_c * ctx->v_c)) : (float)(1.0 / (ctx->p.v0_kms * ctx->p.v0_kms));
   d.log_m = (float)log10(ctx->p.m_chi_mp);
@@ -2028,14 +2041,15 @@ dmb_status dmb_train_surrogate(dmb_ctx *ctx, int64_t nsamples, int32_t epochs, u
   if (ctx->mlp_scope == 1) ns = {ctx->p.n};
   if (ctx->xsec == 1) ns = {0};
   spec.scr = ctx->xsec == 1 ? 1 : 0;
-  // n = -4 (the 1F1 with the most curvature across the envelope's transition) is drawn twice as often
+  // n = -4 (the 1F1 with the most curvature across the envelope's transition) is drawn three times
+  // as often
   std::vector<int> draw = ns;
-  if (std::find(ns.begin(), ns.end(), -4) != ns.end()) draw.push_back(-4);
+  if (std::find(ns.begin(), ns.end(), -4) != ns.end() && ns.size() > 1) draw.insert(draw.end(), {-4, -4});
   spec.n_count = (int)draw.size();
   for (int k = 0; k < spec.n_count; ++k) {
     spec.n_values[k] = draw[k];
     spec.alpha[k] = alpha_of(draw[k]);
-    envelope(draw[k], spec.cA[k], spec.eA[k], spec.cB[k], spec.eB[k]);
+    envelope(draw[k], spec.envA[k], spec.envB[k]);
   }
   const int B = 4096;
   const int64_t N = nsamples, Nval = N / 10, Ntr = N - Nval;

@@ -67,8 +67,9 @@ __global__ void k_mlp_data(int64_t N, unsigned long long seed, MlpDataSpec spec,
   X[4 * i + 1] = (float)(0.5 * lt);
   X[4 * i + 2] = (float)lm;
   X[4 * i + 3] = (float)(0.25 * n);
-  Y[2 * i + 0] = (float)(log(FA) - spec.eA[k] * log1p(spec.cA[k] * x) + ls2);
-  Y[2 * i + 1] = (float)(log(FB) - spec.eB[k] * log1p(spec.cB[k] * x) + ls2);
+  const double *eA = spec.envA[k], *eB = spec.envB[k];
+  Y[2 * i + 0] = (float)(log(FA) - eA[3] * log1p(x * (eA[0] + x * (eA[1] + x * eA[2]))) + ls2);
+  Y[2 * i + 1] = (float)(log(FB) - eB[3] * log1p(x * (eB[0] + x * (eB[1] + x * eB[2]))) + ls2);
 }
 
 // ---- training forward: 16-row tiles per warp, intermediates stored for the backward pass ----

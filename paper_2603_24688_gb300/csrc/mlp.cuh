@@ -153,12 +153,12 @@ __device__ __forceinline__ void mlp_forward16(const MlpSmem &M, const float x_lo
 
 // Surrogate inputs and outputs.  Inputs: log10(s)/2, log10(tau)/2, log10(m_chi/m_p), n/4 with
 // s = w/varsigma, tau = varsigma^2/v0^2.  Outputs: the residuals
-// log FA - log EA and log FB - log EB against the envelopes EA = (1 + cA x)^((n+1)/2),
-// EB = (1 + cB x)^((n+3)/2) (x = s^2/2) that carry the exact small- and large-x behaviour.
+// log FA - log EA and log FB - log EB against the envelopes E = (1 + p x + q x^2 + r x^3)^m
+// (x = s^2/2, m = (n+1)/6 for FA and (n+3)/6 for FB) that carry the exact large-x power and the
+// first two Taylor coefficients at x = 0.
 struct MlpDomain {
   float s2_lo, s2_hi, tau_lo, tau_hi, m_lo, m_hi;   // training box (s^2 = w^2 / varsigma^2)
-  float cA, cB;      // envelope constants for the run's n
-  float eA, eB;      // envelope exponents (n+1)/2, (n+3)/2
+  float envA[4], envB[4];   // envelope (p, q, r, m) of FA and FB for the run's n
   float inv_v0sq, log_m, n4;   // inv_v0sq: 1 / v0^2 (power law) or 1 / v_c^2 (screened law)
   int scr;                     // 1: the screened law sigma0 / (1 + (v / v_c)^2)^2
 };
@@ -176,7 +176,8 @@ __device__ __forceinline__ bool mlp_inputs(const MlpDomain &d, float s2, float s
   return s2 >= d.s2_lo && s2 <= d.s2_hi && tau >= d.tau_lo && tau <= d.tau_hi;
 }
 
-// FA = e^{y0} (1 + cA x)^eA, FB likewise, x = s^2 / 2: one hardware exp and log per output.
+// FA = e^{y0} (1 + p x + q x^2 + r x^3)^m, FB likewise, x = s^2 / 2: one hardware exp and log per
+// output.
 // The screened law divides both envelopes by (1 + q (2x + 3))^2, q = varsigma^2 / v_c^2: sigma/sigma0
 // at the pair's mean-square speed, which carries the law's v^-4 fall (the n = -4 behaviour of FA,
 // FB at large q), so the network again learns an O(1) correction.
@@ -184,8 +185,10 @@ __device__ __forceinline__ void mlp_outputs(const MlpDomain &d, float s2, float 
                                             float &FA, float &FB) {
   const float x = 0.5f * s2;
   const float ls = d.scr ? -2.0f * __logf(fmaf(sig2 * d.inv_v0sq, s2 + 3.0f, 1.0f)) : 0.0f;
-  FA = __expf(fmaf(d.eA, __logf(fmaf(d.cA, x, 1.0f)), y[0] + ls));
-  FB = __expf(fmaf(d.eB, __logf(fmaf(d.cB, x, 1.0f)), y[1] + ls));
+  const float pA = fmaf(x, fmaf(x, fmaf(x, d.envA[2], d.envA[1]), d.envA[0]), 1.0f);
+  const float pB = fmaf(x, fmaf(x, fmaf(x, d.envB[2], d.envB[1]), d.envB[0]), 1.0f);
+  FA = __expf(fmaf(d.envA[3], __logf(pA), y[0] + ls));
+  FB = __expf(fmaf(d.envB[3], __logf(pB), y[1] + ls));
 }
 
 // ---- batched inference on pairs: 32 rows per warp ---------------------------------------------

@@ -23,7 +23,8 @@ struct MlpDataSpec {
   double log_s_lo, log_s_hi, log_tau_lo, log_tau_hi, log_m_lo, log_m_hi;
   int n_count;
   int n_values[MLP_MAX_N];
-  double alpha[MLP_MAX_N], cA[MLP_MAX_N], cB[MLP_MAX_N], eA[MLP_MAX_N], eB[MLP_MAX_N];
+  double alpha[MLP_MAX_N];
+  double envA[MLP_MAX_N][4], envB[MLP_MAX_N][4];   // envelope (p, q, r, m) of FA and FB per n
   // 1: the screened law; tau is then q = varsigma^2 / v_c^2, the targets its quadrature (n = 0
   // normalisation) and the envelopes carry the factor 1 / (1 + q (2x + 3))^2
   int scr = 0;

@@ -40,10 +40,19 @@ def test_envelopes_carry_the_limits():
     for n in (-4, -2, 0, 2):
         t = O.targets(np.array([1e-4, 3e3]), n)
         assert np.all(np.abs(t) < 2e-3), (n, t)
-        cA, eA, cB, eB = O.envelope(n)
-        x = 1e6
-        assert abs(hyp1f1_neg(-(n + 1) / 2, 2.5, x) / (1 + cA * x) ** eA - 1) < 1e-5
-        assert abs(hyp1f1_neg(-(n + 3) / 2, 1.5, x) / (1 + cB * x) ** eB - 1) < 1e-5
+        eA, eB = O.envelope(n)
+        for env, a, b in ((eA, -(n + 1) / 2, 2.5), (eB, -(n + 3) / 2, 1.5)):
+            # large x: the power law Gamma(b)/Gamma(b-a) x^-a
+            x = 1e6
+            assert abs(hyp1f1_neg(a, b, x) / np.exp(O.log_envelope(env, x)) - 1) < 1e-5
+            # small x: the first two Taylor coefficients, so the residual is third order (a wrong
+            # p leaves O(x) = 1e-3, a wrong q O(x^2) = 1e-6 at x = 1e-3)
+            for x in (1e-3, 2e-3):
+                res = np.log(hyp1f1_neg(a, b, x)) - O.log_envelope(env, x)
+                assert abs(res) < 3e-8 * (x / 1e-3) ** 3, (n, a, x, res)
+            # the cubic inside the envelope has no root on x >= 0
+            p, q, r, m = env
+            assert p > 0 and q >= 0 and r > 0 and m != 0
 
 
 def test_round_trip_rates():
