@@ -86,7 +86,7 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other rate providers")
     ap.add_argument("--surrogate-epilogue", type=int, default=0, choices=[0, 1],
                     help="1: the surrogate's tensor-core kernel sums the mean field itself; 0: it stores the rates")
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--retune", action="store_true", help="run the autotuner even if shapes are stored")
