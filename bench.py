@@ -55,10 +55,10 @@ QUAD_OPS_PER_PAIR = 64 * 16 + 120.0
 MLP_FLOP_PER_PAIR = 2.0 * (4 * 128 + 2 * 128 * 128 + 128 * 2)
 MLP_TENSOR_FLOP_PER_PAIR = 2.0 * 128 * (16 + 128 + 16 + 128 + 16)
 # DRAM bytes per pair of the surrogate pass from one ncu capture of the current kernel on galaxy1M
-# (dram__bytes_read.sum + dram__bytes_write.sum = 713.2 + 639.3 MB for 85,071,169 pairs), scaled
+# (dram__bytes_read.sum + dram__bytes_write.sum = 712.3 + 639.2 MB for 85,071,169 pairs), scaled
 # to a launch by its pair count.  Algorithmic bytes: row index, DM index, two 16-byte velocity
 # copies read and the 8-byte rates written per pair
-MLP_DRAM_BYTES_PER_PAIR = (713.150e6 + 639.274496e6) / 85071169
+MLP_DRAM_BYTES_PER_PAIR = (712.270e6 + 639.172864e6) / 85071169
 MLP_ALGO_BYTES_PER_PAIR = 4 + 4 + 16 + 16 + 8
 # The same kernel with the mean field in its epilogue (--surrogate-epilogue 1): its DRAM bytes
 # per pair from one ncu capture on galaxy1M (dram__bytes_read.sum + dram__bytes_write.sum =
