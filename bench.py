@@ -226,32 +226,42 @@ def host_cpu_count():
 
 
 def _subcubes(w, count, target_pairs, seed):
-    """`count` spatial sub-cubes of the workload around random gas particles, each sized (by a
-    brute-force pair count on the first one) to hold about target_pairs pairs."""
+    """`count` spatial sub-cubes of the workload around random gas particles: the first sized (by
+    a brute-force pair count) to hold about target_pairs pairs, the others of the same side but
+    shrunk where the region is denser, until their DM x gas particle product is at most twice the
+    first cube's.  Returns the cubes and the (min, max) side."""
     from oracle.pairs import pairs_bruteforce
     rng = np.random.default_rng(seed)
     dm, gas = w["dm"], w["gas"]
 
-    def cut(c, side):
-        sd = np.all(np.abs(dm["pos"] - c) < side / 2, axis=1)
-        sg = np.all(np.abs(gas["pos"] - c) < side / 2, axis=1)
-        return {k: v[sd] for k, v in dm.items()}, {k: v[sg] for k, v in gas.items()}
+    def cut(sp_dm, sp_gas, c, side):
+        sd = np.all(np.abs(sp_dm["pos"] - c) < side / 2, axis=1)
+        sg = np.all(np.abs(sp_gas["pos"] - c) < side / 2, axis=1)
+        return {k: v[sd] for k, v in sp_dm.items()}, {k: v[sg] for k, v in sp_gas.items()}
 
     c = gas["pos"][rng.integers(len(gas["h"]))]
     side = 4.0 * float(np.median(gas["h"]))
     for _ in range(30):
-        sub_dm, sub_gas = cut(c, side)
+        sub_dm, sub_gas = cut(dm, gas, c, side)
         if len(sub_dm["h"]) * len(sub_gas["h"]) > 0:
             pi, _ = pairs_bruteforce(sub_dm, sub_gas, w["params"]["periodic"], w["params"]["box"])
             if len(pi) >= target_pairs or side > 50:
                 break
         side *= 1.3
     cubes = [(sub_dm, sub_gas)]
+    cap = 2 * max(len(sub_dm["h"]) * len(sub_gas["h"]), 1)
+    sides = [side]
     while len(cubes) < count:
-        sub_dm, sub_gas = cut(gas["pos"][rng.integers(len(gas["h"]))], side)
+        c = gas["pos"][rng.integers(len(gas["h"]))]
+        s = side
+        sub_dm, sub_gas = cut(dm, gas, c, s)
+        while len(sub_dm["h"]) * len(sub_gas["h"]) > cap and s > 1e-4:
+            s /= 1.3
+            sub_dm, sub_gas = cut(sub_dm, sub_gas, c, s)
         if len(sub_dm["h"]) and len(sub_gas["h"]):
             cubes.append((sub_dm, sub_gas))
-    return cubes, side
+            sides.append(s)
+    return cubes, (min(sides), max(sides))
 
 
 def _oracle_cube_job(job):
@@ -276,7 +286,7 @@ def cpu_oracle_all_cores(w, target_pairs=60_000, per_core=2, seed=0, cores=None)
     Returns (pairs/s over the wall time, pairs, wall seconds, cores, description)."""
     import multiprocessing as mp
     cores = cores or host_cpu_count()
-    cubes, side = _subcubes(w, cores * per_core, target_pairs, seed)
+    cubes, (smin, smax) = _subcubes(w, cores * per_core, target_pairs, seed)
     jobs = [(d, g, w["params"], w["dt"]) for d, g in cubes]
     env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     old = {k: os.environ.get(k) for k in env_keys}
@@ -295,7 +305,7 @@ def cpu_oracle_all_cores(w, target_pairs=60_000, per_core=2, seed=0, cores=None)
             else:
                 os.environ[k] = v
     n = sum(r[0] for r in res)
-    desc = (f"oracle_step (+ brute-force pairs) on {len(jobs)} {side:.3f} kpc cubes of {w['name']} "
+    desc = (f"oracle_step (+ brute-force pairs) on {len(jobs)} cubes of {smin:.3f}-{smax:.3f} kpc of {w['name']} "
             f"({n} pairs in total), {cores} worker processes, one numpy thread each; wall time")
     return n / wall, n, wall, cores, desc
 
