@@ -39,9 +39,17 @@ LANES = 128
 # rates and the float64-free sums for the mean field; Philox, Box-Muller, the overlap and the
 # fixed-point running sum for the Monte Carlo
 OPS_PER_PAIR = {"meanfield": 150.0, "mc": 256.0}
+# of those, the pair's geometry (split-float displacement, distance, the overlap table's bicubic
+# lookup, M_i g); a float32 search with pair weights (dmb_set_pair_weights) evaluates it once per
+# pair in its emit pass and the mean field and the Monte Carlo read the stored weights
+GEOM_OPS_PER_PAIR = 84.0
+OPS_PER_PAIR_F32 = {k: v - GEOM_OPS_PER_PAIR for k, v in OPS_PER_PAIR.items()}
 # of the mean field's 150, the closed-form rates (1F1 by its recurrence: one exp, one erf, ~40 FMA);
 # with the surrogate or the quadrature the pass reads or computes its rates otherwise
 RATE_OPS_CLOSED = 42.0
+# the float32 mean-field kernel's algorithmic bytes per pair with stored weights: row index,
+# weight, the DM velocity copy, and the pair's (FA, FB) with the surrogate
+MF_BYTES_PER_PAIR = {"closed": 4 + 4 + 16.0, "quad": 4 + 4 + 16.0, "mlp": 4 + 4 + 16 + 8.0}
 # pair search: lane operations per candidate test of the tile stage's count pass (the split-float
 # displacement with the minimum image, the squared distance and the strict comparison with
 # h_i + h_j, the ballots and the mask bookkeeping)
@@ -84,6 +92,8 @@ def parse():
     ap.add_argument("--rate", default="mlp", choices=["mlp", "quad", "closed"],
                     help="rate provider of the timed step (the others are timed beside it)")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other rate providers")
+    ap.add_argument("--pair-weights", type=int, default=-1, choices=[-1, 0, 1],
+                    help="dmb_set_pair_weights: -1 the library's default (not for a step's own search), 0 never, 1 always")
     ap.add_argument("--surrogate-epilogue", type=int, default=0, choices=[0, 1],
                     help="1: the surrogate's tensor-core kernel sums the mean field itself; 0: it stores the rates")
     ap.add_argument("--e2e-steps", type=int, default=16)
@@ -453,6 +463,7 @@ def run_substeps(a, peaks, peak_kind):
     ctx = dmb.Context(prm["sigma0_cm2"], prm["n"], prm["m_chi_mp"], prm["v0_kms"], False, (0.0, 0.0, 0.0),
                       prm["seed"], rate_mode=dmb.DMB_RATE_MLP, stream=stream)
     ctx.dmb_set_surrogate_epilogue(a.surrogate_epilogue)
+    ctx.dmb_set_pair_weights(a.pair_weights)
     rep = ctx.dmb_train_surrogate(**TRAIN)
     dm, gas = dmb.to_device(w["dm"]), dmb.to_device(w["gas"])
     db = torch.from_numpy(w["dm_bin"]).cuda()
@@ -506,7 +517,8 @@ def run_substeps(a, peaks, peak_kind):
             "active_fraction": g["active"] / (a.steps * (len(w["dm"]["h"]) + len(w["gas"]["h"]))),
             "eager": {"ms_per_step": out[False]["ms"] / a.steps,
                       "pairs_per_s": out[False]["evals"] / (out[False]["ms"] * 1e-3)},
-            "setup_s": setup_s, "gpu_launches": int(g["launches"]), "clocks": g["clocks"],
+            "setup_s": setup_s, "pair_weights": "stored by the search (dmb_neighbors keeps the pair set)"
+            if a.pair_weights != 0 else "none", "gpu_launches": int(g["launches"]), "clocks": g["clocks"],
             "surrogate_val_mean_rel_err": [float(rep[3]), float(rep[4])], "peak_kind": peak_kind}
     print(json.dumps(line))
     ctx.close()
@@ -525,6 +537,7 @@ def run_boxes(a, peaks, peak_kind):
     stream = torch.cuda.current_stream()
     ctx = dmb.Context(prm["sigma0_cm2"], prm["n"], prm["m_chi_mp"], prm["v0_kms"], True, tuple(prm["box"]),
                       prm["seed"], stream=stream)
+    ctx.dmb_set_pair_weights(a.pair_weights)
     dm, gas = dmb.to_device(w["dm"]), dmb.to_device(w["gas"])
     dbx = torch.from_numpy(w["dm_box"].view(np.int32)).cuda()
     gbx = torch.from_numpy(w["gas_box"].view(np.int32)).cuda()
@@ -646,6 +659,7 @@ def main():
         c = dmb.Context(prm["sigma0_cm2"], prm["n"], prm["m_chi_mp"], prm["v0_kms"], prm["periodic"],
                         tuple(prm["box"]), prm["seed"], fp64=a.fp64, rate_mode=modes[rate], stream=stream)
         c.dmb_set_surrogate_epilogue(a.surrogate_epilogue)
+        c.dmb_set_pair_weights(a.pair_weights)
         return c
 
     surrogate = None
@@ -719,6 +733,8 @@ def main():
             "meanfield": "k_meanfield", "mc": "k_mc", "kick": "k_kick_gas"}[names[dom]]
     roof = None
     fmax_ghz = peaks.get("sm_max_mhz", 2070.0) / 1e3
+    # whether the step's own search stored pair weights (then the geometry is the search's work)
+    w_used = a.pair_weights == 1 and not a.fp64
     alu_peak = SMS * LANES * fmax_ghz * 1e9 / 1e12          # T lane-ops/s
 
     def roofline(stage):
@@ -746,7 +762,9 @@ def main():
                     "peak_source": f"bf16_tflops_sustained of MEASURED_PEAKS.json ({peak_kind})",
                     "kernel_ms": surrogate_ms}
         if stage in OPS_PER_PAIR:
-            ops = OPS_PER_PAIR[stage] if not (stage == "meanfield" and a.rate == "quad") else QUAD_OPS_PER_PAIR
+            table = OPS_PER_PAIR_F32 if w_used else OPS_PER_PAIR
+            ops = table[stage] if not (stage == "meanfield" and a.rate == "quad") else \
+                QUAD_OPS_PER_PAIR - (GEOM_OPS_PER_PAIR if w_used else 0.0)
             kern = {"meanfield": "k_meanfield", "mc": "k_mc"}[stage]
             ach = ops * npairs / t / 1e12
             return {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s", "frac": ach / alu_peak,
@@ -770,8 +788,10 @@ def main():
     else:
         # the mean-field kernel alone (the surrogate pass before it is the tensor roofline) and the
         # Monte Carlo, each against the lane-operation roofline
-        mf_ops = {"closed": OPS_PER_PAIR["meanfield"], "quad": QUAD_OPS_PER_PAIR,
-                  "mlp": OPS_PER_PAIR["meanfield"] - RATE_OPS_CLOSED}[a.rate]
+        table = OPS_PER_PAIR_F32 if w_used else OPS_PER_PAIR
+        mf_ops = {"closed": table["meanfield"], "quad": QUAD_OPS_PER_PAIR - (GEOM_OPS_PER_PAIR if w_used else 0.0),
+                  "mlp": table["meanfield"] - RATE_OPS_CLOSED}[a.rate]
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
         if a.rate == "mlp" and a.surrogate_epilogue == 1:
             # the mean field runs inside the surrogate's kernel: no kernel of its own to time
             stages["meanfield_kernel_ms"] = None
@@ -781,12 +801,16 @@ def main():
             t_mf = (per_step[2] - surrogate_ms) * 1e-3
             stages["meanfield_kernel_ms"] = float(per_step[2] - surrogate_ms)
             stages["meanfield_frac"] = mf_ops * npairs / t_mf / 1e12 / alu_peak
-        stages["mc_frac"] = OPS_PER_PAIR["mc"] * npairs / (per_step[3] * 1e-3) / 1e12 / alu_peak
+            if w_used:   # with the stored weights the kernel streams its pairs: its memory roofline
+                stages["meanfield_hbm_frac"] = MF_BYTES_PER_PAIR[a.rate] * npairs / t_mf / 1e9 / hbm_peak
+        stages["mc_frac"] = table["mc"] * npairs / (per_step[3] * 1e-3) / 1e12 / alu_peak
+        stages["pair_weights"] = bool(w_used)
     # the pair search: candidate distance tests of the count pass (after the ballot prefilter) at
-    # SEARCH_OPS_PER_TEST lane operations each, over the whole search stage's time
+    # SEARCH_OPS_PER_TEST lane operations each, and (float32) the pair geometry of every pair in the
+    # emit pass, over the whole search stage's time
     st = ctx.dmb_search_stats()
     tests = float(st[0][2])
-    search_ops = tests * SEARCH_OPS_PER_TEST
+    search_ops = tests * SEARCH_OPS_PER_TEST + (GEOM_OPS_PER_PAIR * npairs if w_used else 0.0)
     stages["search_candidate_tests"] = tests
     stages["search_frac"] = search_ops / (per_step[1] * 1e-3) / 1e12 / alu_peak if per_step[1] > 0 else None
 
@@ -822,6 +846,7 @@ def main():
                 c2 = dmb.Context(prm["sigma0_cm2"], n, prm["m_chi_mp"], prm["v0_kms"], prm["periodic"],
                                  tuple(prm["box"]), prm["seed"], fp64=a.fp64, rate_mode=modes[rate], stream=stream)
                 c2.dmb_set_surrogate_epilogue(a.surrogate_epilogue)
+                c2.dmb_set_pair_weights(a.pair_weights)
                 if rate == "mlp":
                     c2.dmb_load_surrogate(surrogate)
                 if shapes is not None:

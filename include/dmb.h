@@ -372,6 +372,18 @@ dmb_status dmb_set_fusion(dmb_ctx *ctx, int32_t on);
  * dmb_set_fusion(ctx, 1) always reads stored rates.  Other values: DMB_ERR_ARG. */
 dmb_status dmb_set_surrogate_epilogue(dmb_ctx *ctx, int32_t mode);
 
+/* Pair weights of a float32 pair set: the search's emit pass forms every pair's overlap g_ij
+ * (Eqs. gas-dVdt, dm-update-prob; the canonical displacement and the overlap table, the same
+ * arithmetic as the interaction kernels) and stores M_i g_ij beside each gas-major entry and g_ij
+ * beside each DM-major entry; the mean field and the Monte Carlo then read them instead of
+ * gathering positions and evaluating the table.  Results are the same bit for bit.  The search
+ * pays for them (about the time the two kernels save), so they pay off when a pair set serves
+ * many passes.  mode = -1 (the default): stored when the pair set is kept for later calls, i.e.
+ * by dmb_neighbors (the pair set of dmb_set_bins / dmb_substep and of the standalone
+ * dmb_meanfield_gas / dmb_mc_scatter_dm), not by the search inside dmb_step or dmb_step_batched;
+ * 0: never; 1: always.  Other values: DMB_ERR_ARG.  float64 contexts never store them. */
+dmb_status dmb_set_pair_weights(dmb_ctx *ctx, int32_t mode);
+
 /* Which power-law indices the next dmb_train_surrogate covers: 0 (the default) the scan's
  * {-4, -2, 0, 2} and the context's n, one network for all of them; 1 the context's n only (the
  * network's fourth input is then constant, and all of its capacity serves that n).  Other values:

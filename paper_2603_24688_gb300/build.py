@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdmb.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["abi.cu", "grid.cu", "search.cu", "interact.cu", "step.cu", "sort_scan.cu", "mlp.cu", "noalloc.cu", "active.cu", "mlp_tc.cu"]
+SOURCES = ["abi.cu", "grid.cu", "search.cu", "interact.cu", "meanfield.cu", "fused.cu", "step.cu", "sort_scan.cu",
+           "mlp.cu", "noalloc.cu", "active.cu", "mlp_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

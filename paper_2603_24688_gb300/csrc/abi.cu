@@ -48,6 +48,8 @@ struct SpeciesBufs {
 struct SearchBufs {
   DevBuf item_cnt, item_ptr, items, unit_cnt_leaf, unit_ptr, unit_leaf, unit_item0, unit_cnt, counts, row_ptr, rows,
       tmask;
+  // float32 pair weights beside rows (PairWeights): gas-major M_i g_ij, DM-major g_ij
+  DevBuf w;
   int64_t n_items = 0, n_units = 0, n_pairs = 0;
 };
 
@@ -140,6 +142,10 @@ struct dmb_ctx {
   DevBuf gate, cap_need;
   DevBuf gidx;                      // gas-major position of every DM-major pair (the fused pass)
   bool fuse = false;                // dmb_set_fusion: one pass for the mean field and the Monte Carlo
+  // dmb_set_pair_weights: -1 (auto) the float32 search stores pair weights when its pair set is
+  // kept for later calls (dmb_neighbors); 0 never; 1 always.  w_ready: the current set has them.
+  int weights_mode = -1;
+  bool w_ready = false;
   int mc_variant = 0;             // dmb_set_mc_variant
   double mc_beta = 0.0;           // dmb_set_anisotropy
   cudaStream_t gstream = nullptr;
@@ -338,6 +344,7 @@ dmb_status build_grid_impl(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
   ctx->dm_vel = dm->vel;
   ctx->grid_ready = true;
   ctx->pairs_ready = false;
+  ctx->w_ready = false;
   return DMB_OK;
 }
 
@@ -394,14 +401,38 @@ dmb_status search_stage2_count(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, S
 }
 
 template <typename R>
-dmb_status search_stage2_emit(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, SpeciesView<R> O, TransposeOut tr) {
+dmb_status search_stage2_emit(dmb_ctx *ctx, SearchBufs &sb, SpeciesView<R> Q, SpeciesView<R> O, TransposeOut tr,
+                              PairWeights pw) {
   if (!ensure(sb.rows, (size_t)sb.n_pairs * 4)) return fail(ctx, DMB_ERR_OOM, "device allocation failed for pair lists");
   CK(launch_tile<R>(Q, O, ctx->bx, ptr<Frame>(ctx->frame), true, ptr<uint32_t>(sb.unit_leaf),
                     ptr<int64_t>(sb.unit_item0), ptr<int64_t>(sb.item_ptr), ptr<uint32_t>(sb.items), sb.n_units,
                     ctx->shp.unit, ptr<uint32_t>(sb.unit_cnt), ptr<int64_t>(sb.row_ptr), ptr<uint32_t>(sb.rows), tr,
-                    ptr<uint32_t>(sb.tmask), ptr<uint32_t>(ctx->status), nullptr, ctx->stream, &ctx->launches),
+                    ptr<uint32_t>(sb.tmask), ptr<uint32_t>(ctx->status), nullptr, ctx->stream, &ctx->launches, nullptr,
+                    pw),
      "tile (emit)");
   return DMB_OK;
+}
+
+// The pair weights of a float32 search (none in float64, whose kernels evaluate g exactly).
+template <typename R>
+PairWeights pair_weights(dmb_ctx *ctx) {
+  PairWeights pw;
+  if (sizeof(R) == 4) {
+    pw.q = ptr<float>(ctx->sg.w);
+    pw.t = ptr<float>(ctx->sd.w);
+    pw.gtab = ptr<float4>(ctx->gtab);
+  }
+  return pw;
+}
+// The weights the mean field and the Monte Carlo read: those of the current pair set, if any.
+template <typename R>
+PairWeights ready_weights(dmb_ctx *ctx) {
+  return ctx->w_ready ? pair_weights<R>(ctx) : PairWeights();
+}
+// Whether a search stores weights: reuse = the pair set outlives the call that searched it.
+template <typename R>
+bool want_weights(const dmb_ctx *ctx, bool reuse) {
+  return sizeof(R) == 4 && (ctx->weights_mode == 1 || (ctx->weights_mode == -1 && reuse));
 }
 
 // Mean-field segments of the gas rows (upper bound N_B + pairs / seg, no readback).
@@ -424,7 +455,7 @@ dmb_status build_segments(dmb_ctx *ctx, const SearchBufs &sg, int64_t ng) {
 }
 
 template <typename R>
-dmb_status neighbors_impl(dmb_ctx *ctx) {
+dmb_status neighbors_impl(dmb_ctx *ctx, bool reuse = false) {
   cudaStream_t s = ctx->stream;
   const SpeciesView<R> D = view<R>(ctx->dm, ctx->nbox > 0), G = view<R>(ctx->gas, ctx->nbox > 0);
   const int64_t nmax = D.n > G.n ? D.n : G.n;
@@ -460,7 +491,9 @@ dmb_status neighbors_impl(dmb_ctx *ctx) {
   sd.n_pairs = nd > 0 ? ctx->h_tot[5] : 0;
   if (sd.n_pairs != sg.n_pairs) return fail(ctx, DMB_ERR_CUDA, "pair counts of the two directions differ");
   // emit both directions: gas-major rows in search order, DM-major rows by claimed positions
-  if (!ensure(sd.rows, (size_t)sg.n_pairs * 4) || (ctx->fuse && !ensure(ctx->gidx, (size_t)sg.n_pairs * 4)))
+  const bool w = want_weights<R>(ctx, reuse);
+  if (!ensure(sd.rows, (size_t)sg.n_pairs * 4) || (ctx->fuse && !ensure(ctx->gidx, (size_t)sg.n_pairs * 4)) ||
+      (w && (!ensure(sg.w, (size_t)sg.n_pairs * 4 + 16) || !ensure(sd.w, (size_t)sg.n_pairs * 4 + 16))))
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for DM-major lists");
   CK(cudaMemsetAsync(ctx->t_cursor.p, 0, (size_t)(nd + 1) * 4, s), "memset");
   TransposeOut tre;
@@ -468,7 +501,9 @@ dmb_status neighbors_impl(dmb_ctx *ctx) {
   tre.ptr = ptr<int64_t>(sd.row_ptr);
   tre.rows = ptr<uint32_t>(sd.rows);
   tre.gidx = ctx->fuse ? ptr<uint32_t>(ctx->gidx) : nullptr;   // only the fused step reads them
-  if ((st = search_stage2_emit<R>(ctx, sg, G, D, tre)) != DMB_OK) return st;
+  if ((st = search_stage2_emit<R>(ctx, sg, G, D, tre, w ? pair_weights<R>(ctx) : PairWeights())) != DMB_OK)
+    return st;
+  ctx->w_ready = w;
   if ((st = build_segments(ctx, sg, G.n)) != DMB_OK) return st;
   if (!ensure(ctx->pcache, (size_t)sd.n_pairs * (ctx->p.fp64 ? 8 : 4)))
     return fail(ctx, DMB_ERR_OOM, "device allocation failed for the probability cache");
@@ -542,7 +577,9 @@ dmb_status neighbors_capped(dmb_ctx *ctx) {
   CK(launch_tile<R>(G, D, ctx->bx, fr, true, ptr<uint32_t>(sg.unit_leaf), ptr<int64_t>(sg.unit_item0), item_ptr,
                     ptr<uint32_t>(sg.items), cap.units, ctx->shp.unit, ptr<uint32_t>(sg.unit_cnt),
                     ptr<int64_t>(sg.row_ptr), ptr<uint32_t>(sg.rows), tre, ptr<uint32_t>(sg.tmask), status, nullptr, s,
-                    L, unit_ptr + nleaf), "tile (emit)");
+                    L, unit_ptr + nleaf, want_weights<R>(ctx, false) ? pair_weights<R>(ctx) : PairWeights()),
+     "tile (emit)");
+  ctx->w_ready = want_weights<R>(ctx, false);
   // mean-field segments
   const int seg = ctx->shp.seg;
   CK(launch_seg_counts(ptr<int64_t>(sg.row_ptr), ng, seg, ptr<uint32_t>(ctx->seg_cnt), s, L), "segments");
@@ -781,7 +818,7 @@ dmb_status meanfield_impl(dmb_ctx *ctx, double *acc, double *dudt, double *e_exp
   }
   CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv,
                          ctx->n_seg_max, ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr,
-                         ctx->shp.mf_bps, ctx->stream, &ctx->launches), "meanfield");
+                         ctx->shp.mf_bps, ctx->stream, &ctx->launches, ready_weights<R>(ctx).q), "meanfield");
   return DMB_OK;
 }
 
@@ -815,6 +852,7 @@ dmb_status mc_impl(dmb_ctx *ctx, uint64_t step, double dt, double *vel_out, uint
   a.block_max = ptr<double>(ctx->mc_max);
   if (ctx->capturing) a.step_dev = ptr<unsigned long long>(ctx->step_dev);   // set before each replay
   if (!ensure(ctx->mc_rec, (size_t)D.n * sizeof(McRec))) return fail(ctx, DMB_ERR_OOM, "MC scratch");
+  a.g = ready_weights<R>(ctx).t;
   if (D.n > 0)
     CK(launch_mc<R>(D, G, ctx->bx, ptr<int64_t>(ctx->sd.row_ptr), ptr<uint32_t>(ctx->sd.rows),
                     ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), ptr<McRec>(ctx->mc_rec), nb,
@@ -1028,7 +1066,8 @@ dmb_status substep_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int 
   }
   if (nga > 0 && !surrogate_epilogue<R>(ctx))
     CK(launch_meanfield<R>(G, D, ctx->bx, ptr<int64_t>(ctx->sg.row_ptr), ptr<uint32_t>(ctx->sg.rows), sv, nseg,
-                           ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr, ctx->shp.mf_bps, s, L),
+                           ptr<float4>(ctx->gtab), ctx->rc, o, ptr<R>(ctx->mf_part), mr, ctx->shp.mf_bps, s, L,
+                           ready_weights<R>(ctx).q),
        "meanfield");
   // Monte Carlo of the active DM against all their gas partners, each with its own dt
   const int nb = mc_blocks_for(nda);
@@ -1053,6 +1092,7 @@ dmb_status substep_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, int 
   a.step_dev = step_on_device ? ptr<unsigned long long>(ctx->step_dev) : nullptr;
   a.v_sorted = ctx->dm.V.p;
   a.v_sorted_fp64 = ctx->p.fp64 ? 1 : 0;
+  a.g = ready_weights<R>(ctx).t;
   if (nda > 0)
     CK(launch_mc<R>(D, G, ctx->bx, ptr<int64_t>(ctx->sd.row_ptr), ptr<uint32_t>(ctx->sd.rows),
                     ptr<float4>(ctx->gtab), ctx->rc, a, ptr<R>(ctx->pcache), ptr<McRec>(ctx->mc_rec), nb,
@@ -1277,7 +1317,7 @@ dmb_status dmb_build_grid(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas) {
 dmb_status dmb_neighbors(dmb_ctx *ctx, int64_t *n_pairs, uint32_t *pairs_out, int64_t capacity) {
   if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
   if (!ctx->grid_ready) return fail(ctx, DMB_ERR_STATE, "dmb_neighbors before dmb_build_grid");
-  dmb_status st = ctx->p.fp64 ? neighbors_impl<double>(ctx) : neighbors_impl<float>(ctx);
+  dmb_status st = ctx->p.fp64 ? neighbors_impl<double>(ctx, true) : neighbors_impl<float>(ctx, true);
   if (st != DMB_OK) return st;
   if (n_pairs) *n_pairs = ctx->n_pairs;
   if (pairs_out && capacity > 0)
@@ -1408,8 +1448,8 @@ static dmb_status step_body(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, 
   if (ctx->capturing) {
     st = ctx->p.fp64 ? neighbors_capped<double>(ctx) : neighbors_capped<float>(ctx);
     if (st != DMB_OK) return st;
-  } else if ((st = dmb_neighbors(ctx, nullptr, nullptr, 0)) != DMB_OK) {
-    return st;
+  } else if ((st = ctx->p.fp64 ? neighbors_impl<double>(ctx) : neighbors_impl<float>(ctx)) != DMB_OK) {
+    return st;   // the step's own pair set: no weights unless dmb_set_pair_weights(ctx, 1)
   }
   if (tm) CK(cudaEventRecord(ctx->ev[2], ctx->stream), "event");
   const int64_t ng = gas->n, nd = dm->n;
@@ -1480,6 +1520,8 @@ static dmb_status presize_batch(dmb_ctx *ctx) {
             ensure(sg.unit_leaf, (size_t)c.units * 4) && ensure(sg.unit_item0, (size_t)c.units * 8) &&
             ensure(sg.unit_cnt, (size_t)c.units * 32 * 4) && ensure(sg.rows, (size_t)c.pairs * 4) &&
             ensure(sd.rows, (size_t)c.pairs * 4) && (!ctx->fuse || ensure(ctx->gidx, (size_t)c.pairs * 4)) &&
+            (ctx->p.fp64 || ctx->weights_mode != 1 ||
+             (ensure(sg.w, (size_t)c.pairs * 4 + 16) && ensure(sd.w, (size_t)c.pairs * 4 + 16))) &&
             ensure(ctx->pcache, (size_t)c.pairs * rb) &&
             ensure(ctx->seg_row, (size_t)c.segs * 4) && ensure(ctx->seg_begin, (size_t)c.segs * 8) &&
             ensure(ctx->mf_part, (size_t)c.segs * 6 * rb) && ensure(ctx->gate, 16) && ensure(ctx->cap_need, 64) &&
@@ -1661,6 +1703,19 @@ dmb_status dmb_set_fusion(dmb_ctx *ctx, int32_t on) {
     ctx->pairs_ready = false;   // the search writes the pairs' gas-major positions only when fused
   }
   ctx->fuse = on == 1;
+  return DMB_OK;
+}
+
+dmb_status dmb_set_pair_weights(dmb_ctx *ctx, int32_t mode) {
+  if (!ctx) return fail(nullptr, DMB_ERR_ARG, "ctx is NULL");
+  if (mode < -1 || mode > 1) return fail(ctx, DMB_ERR_ARG, "mode must be -1, 0 or 1");
+  if (mode != ctx->weights_mode) {
+    clear_batch_graph(ctx);     // the captured step holds the other kernels
+    invalidate_substeps(ctx);
+    ctx->pairs_ready = false;   // the next search decides again
+    ctx->w_ready = false;
+  }
+  ctx->weights_mode = mode;
   return DMB_OK;
 }
 

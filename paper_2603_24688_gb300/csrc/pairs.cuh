@@ -46,15 +46,27 @@ struct TransposeOut {
   uint32_t *gidx = nullptr;      // [pairs] (emit pass, may be null): the pair's query-major position
 };
 
+// Pair weights of a float32 search, written by the emit pass from the tile masks: the overlap
+// g_ij (Eqs. gas-dVdt, dm-update-prob) at every target-major entry and the target's mass times
+// g_ij at every query-major entry.  The emit pass forms them from the canonical displacement and
+// the overlap table exactly as the mean-field and Monte Carlo kernels would, which then read them
+// instead of gathering positions.
+struct PairWeights {
+  float *q = nullptr;             // [pairs] query-major: M_target g_ij
+  float *t = nullptr;             // [pairs] target-major: g_ij
+  const float4 *gtab = nullptr;   // overlap table
+};
+
 // tmask (optional, [items][32] uint32): the count pass stores each tile's pair masks (entry k:
 // the query lanes paired with target k of the item's leaf) and the emit pass reads them instead
-// of testing the distances again.
+// of testing the distances again.  pw (emit pass with tmask, float32 only): the pair weights.
 template <typename R>
 cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *frame, bool emit,
                         const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
                         const uint32_t *items, int64_t n_units, int unit, uint32_t *unit_cnt, const int64_t *row_ptr,
                         uint32_t *rows, TransposeOut tr, uint32_t *tmask, uint32_t *status, unsigned long long *stats,
-                        cudaStream_t s, int64_t *launches, const int64_t *n_units_dev = nullptr);
+                        cudaStream_t s, int64_t *launches, const int64_t *n_units_dev = nullptr,
+                        PairWeights pw = PairWeights());
 // Capacity check of a captured step (the host sized the buffers before capture and reads no
 // count back): totals [k] against cap [k], written to need[slot[k]]; on overflow gate = 1, the
 // status gets DMB_BAD_OVERFLOW and the offset arrays zero[k] (zero_n[k] entries) are cleared.
@@ -100,10 +112,13 @@ struct MfOut {
 };
 
 // part: scratch [n_seg][6] in the pair precision (per-segment sums before the float64 finish)
+// wq: float32 steps, M_i g_ij of every gas-major pair (PairWeights::q of the search); the float64
+// path forms g_ij from the positions with the exact evaluator and takes null
 template <typename R>
 cudaError_t launch_meanfield(SpeciesView<R> G, SpeciesView<R> D, BoxSplit bx, const int64_t *row_ptr,
                              const uint32_t *rows, SegView sv, int64_t n_seg_max, const float4 *gtab, RunConst rc,
-                             MfOut out, R *part, MlpRun mr, int blocks_per_sm, cudaStream_t s, int64_t *launches);
+                             MfOut out, R *part, MlpRun mr, int blocks_per_sm, cudaStream_t s, int64_t *launches,
+                             const float *wq);
 
 struct McArgs {
   double dt;
@@ -130,6 +145,9 @@ struct McArgs {
   int variant = 0;
   // dsigma/dOmega proportional to 1 + beta cos theta (0: isotropic)
   double beta = 0.0;
+  // float32 steps: g_ij of every DM-major pair (PairWeights::t of the search), read by the
+  // categorical draw instead of the positions; null in float64 (g from the exact evaluator)
+  const float *g = nullptr;
 };
 
 // Sets the surrogate pass's shared-memory attribute (done before any graph capture).

@@ -189,17 +189,26 @@ __global__ void k_unit_map(const int64_t *__restrict__ item_ptr, const int64_t *
 
 // ---- stage 2: tiles of (query leaf) x (target leaf) -------------------------------------
 template <typename R, bool EMIT, int GEOM>
-__global__ void __launch_bounds__(SR_WARPS * 32)
+__global__ void __launch_bounds__(SR_WARPS * 32, (EMIT && sizeof(R) == 4 && GEOM != GEOM_BOXES) ? 8 : 1)
 k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict__ frame,
        const uint32_t *__restrict__ unit_leaf, const int64_t *__restrict__ unit_item0,
        const int64_t *__restrict__ item_ptr, const uint32_t *__restrict__ items, int64_t n_units, int unit,
        uint32_t *__restrict__ unit_cnt, const int64_t *__restrict__ row_ptr, uint32_t *__restrict__ rows,
        TransposeOut tr, uint32_t *__restrict__ tmask, uint32_t *status, unsigned long long *__restrict__ stats,
-       const int64_t *__restrict__ n_units_dev) {
+       const int64_t *__restrict__ n_units_dev, PairWeights pw) {
   typedef typename Vec<R>::v4 v4;
   __shared__ v4 sP[SR_WARPS][DMB_LEAF];
   __shared__ v4 sL[SR_WARPS][DMB_LEAF];
   __shared__ uint16_t sB[SR_WARPS][DMB_LEAF];
+  // emit pass with pair weights: the query leaf's copies, row ends and boxes; per tile every
+  // target's pair mask and claimed target-major range, every query lane's targets, the prefix
+  // of their counts and the lane's row position
+  __shared__ v4 sQP[SR_WARPS][DMB_LEAF];
+  __shared__ v4 sQL[SR_WARPS][DMB_LEAF];
+  __shared__ int64_t sEnd[SR_WARPS][DMB_LEAF], sOut[SR_WARPS][DMB_LEAF];
+  __shared__ uint16_t sQB[SR_WARPS][DMB_LEAF];
+  __shared__ uint32_t sCol[SR_WARPS][DMB_LEAF], sRow[SR_WARPS][DMB_LEAF], sOff[SR_WARPS][DMB_LEAF];
+  __shared__ int64_t sP0[SR_WARPS][DMB_LEAF], sP1[SR_WARPS][DMB_LEAF];
   const int wib = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31u;
   const float pad2 = 2.0f * frame->pad;
@@ -228,6 +237,102 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
     if (EMIT && valid) {
       out = row_ptr[qi] + unit_cnt[32 * u + lane];   // unit_cnt holds the exclusive offsets here
       out_end = row_ptr[qi + 1];
+    }
+    if (EMIT && tmask != nullptr && sizeof(R) == 4 && pw.q != nullptr) {
+      // as below, and each pair's weights.  The tile's pairs are spread evenly over the lanes
+      // (pair h of the tile, in query-lane then target order, goes to lane h mod 32): the lane
+      // finds the pair's query lane q from the prefix of the per-lane pair counts and its target
+      // k as the r-th pair of that lane, forms the canonical displacement, distance and overlap
+      // g_ij from the staged copies, and writes the query-major entry (row, M_target g_ij) at
+      // lane q's position and the target-major entry (query, g_ij) at target k's claimed range.
+      // Entries land where the plain emit pass puts them.
+      __syncwarp();
+      sQP[wib][lane] = Pq;
+      sQL[wib][lane] = Lq;
+      sEnd[wib][lane] = out_end;
+      if (GEOM == GEOM_BOXES) sQB[wib][lane] = box_q;
+      const int64_t qbase = (int64_t)a * DMB_LEAF;
+      uint32_t col_next = it0 < it1 ? tmask[32 * it0 + lane] : 0u;
+      uint32_t leaf_next = it0 < it1 ? items[it0] : 0u;
+      v4 Pk_next = Vec<R>::make(0, 0, 0, 0), Lk_next = Vec<R>::make(0, 0, 0, 0);
+      if (it0 < it1 && (int64_t)leaf_next * DMB_LEAF + lane < O.n) {
+        Pk_next = O.P[(int64_t)leaf_next * DMB_LEAF + lane];
+        Lk_next = O.L[(int64_t)leaf_next * DMB_LEAF + lane];
+      }
+      for (int64_t it = it0; it < it1; ++it) {
+        const uint32_t mycol = col_next;
+        const int64_t base = (int64_t)leaf_next * DMB_LEAF;
+        __syncwarp();
+        sP[wib][lane] = Pk_next;
+        sL[wib][lane] = Lk_next;
+        if (it + 1 < it1) {
+          col_next = tmask[32 * (it + 1) + lane];
+          leaf_next = items[it + 1];
+          const int64_t nb = (int64_t)leaf_next * DMB_LEAF + lane;
+          if (nb < O.n) {
+            Pk_next = O.P[nb];
+            Lk_next = O.L[nb];
+          }
+        }
+        const unsigned m = __ballot_sync(DMB_FULL, mycol != 0u);
+        if (!m) continue;
+        int64_t p0 = 0, p1 = 0;                          // this lane's claim for target `lane`
+        if (tr_on && mycol) {
+          p0 = tr.ptr[base + lane] + atomicAdd(&tr.cursor[base + lane], (uint32_t)__popc(mycol));
+          p1 = tr.ptr[base + lane + 1];
+        }
+        // this query lane's targets in the tile (bit k: paired with target k) and their count
+        uint32_t myrow = 0u;
+        for (unsigned mm = m; mm; mm &= mm - 1) {
+          const int k = __ffs(mm) - 1;
+          myrow |= ((__shfl_sync(DMB_FULL, mycol, k) >> lane) & 1u) << k;
+        }
+        const uint32_t cnt = (uint32_t)__popc(myrow);
+        uint32_t incl = cnt;                              // inclusive prefix over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t v = __shfl_up_sync(DMB_FULL, incl, o);
+          if ((int)lane >= o) incl += v;
+        }
+        const uint32_t npairs = __shfl_sync(DMB_FULL, incl, 31);
+        sCol[wib][lane] = mycol;
+        sP0[wib][lane] = p0;
+        sP1[wib][lane] = p1;
+        sRow[wib][lane] = myrow;
+        sOff[wib][lane] = incl - cnt;
+        sOut[wib][lane] = out;
+        __syncwarp();
+        for (uint32_t h = lane; h < npairs; h += 32) {
+          int q = 0;                                      // the last lane whose pairs start at or before h
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1)
+            if (sOff[wib][q + step] <= h) q += step;
+          const uint32_t r = h - sOff[wib][q];
+          uint32_t mm = sRow[wib][q];
+          for (uint32_t i = 0; i < r; ++i) mm &= mm - 1;
+          const int k = __ffs(mm) - 1;
+          const v4 Pa = sQP[wib][q], La = sQL[wib][q], Pk = sP[wib][k], Lk = sL[wib][k];
+          const BoxSide side = GEOM == GEOM_BOXES ? box_side<GEOM>(bx, sQB[wib][q]) : ls.a;
+          R dx, dy, dz;
+          pair_dx<R>(Pa, La, Pk, Lk, GEOM != GEOM_OPEN, side, dx, dy, dz);
+          const float g = overlap_g<float>(pw.gtab, sqrt_pair((float)dist2_rn<R>(dx, dy, dz)), (float)Pa.w, (float)Pk.w);
+          const int64_t oq = sOut[wib][q] + r;
+          if (oq < sEnd[wib][q]) {
+            rows[oq] = (uint32_t)(base + k);
+            pw.q[oq] = (float)Lk.w * g;
+          }
+          if (tr_on) {
+            const int64_t pos = sP0[wib][k] + __popc(sCol[wib][k] & ((1u << q) - 1u));
+            if (pos < sP1[wib][k]) {
+              tr.rows[pos] = (uint32_t)(qbase + q);
+              if (pw.t != nullptr) pw.t[pos] = g;
+              if (tr.gidx != nullptr) tr.gidx[pos] = (uint32_t)oq;
+            }
+          }
+        }
+        out += cnt;
+      }
+      continue;
     }
     if (EMIT && tmask != nullptr) {
       // the count pass left each tile's pair masks (lane k: the query lanes paired with target
@@ -416,12 +521,12 @@ cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const F
                         const uint32_t *unit_leaf, const int64_t *unit_item0, const int64_t *item_ptr,
                         const uint32_t *items, int64_t n_units, int unit, uint32_t *unit_cnt, const int64_t *row_ptr,
                         uint32_t *rows, TransposeOut tr, uint32_t *tmask, uint32_t *status, unsigned long long *stats,
-                        cudaStream_t s, int64_t *launches, const int64_t *n_units_dev) {
+                        cudaStream_t s, int64_t *launches, const int64_t *n_units_dev, PairWeights pw) {
   if (n_units <= 0) return cudaSuccess;
   const int g = grid_for(n_units);
 #define TL(E, G)                                                                                                \
   k_tile<R, E, G><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items, n_units, unit, \
-                                              unit_cnt, row_ptr, rows, tr, tmask, status, stats, n_units_dev)
+                                              unit_cnt, row_ptr, rows, tr, tmask, status, stats, n_units_dev, pw)
   switch (geom_of(bx) * 2 + (emit ? 1 : 0)) {
     case 0: TL(false, GEOM_OPEN); break;
     case 1: TL(true, GEOM_OPEN); break;
@@ -452,7 +557,7 @@ cudaError_t launch_unit_prefix(const int64_t *unit_ptr, int nleaf, int64_t nq, u
                                       int, uint32_t *, const int64_t *, uint32_t *, TransposeOut, uint32_t *,         \
                                       uint32_t *,                                                                    \
                                       unsigned long long *,                                                          \
-                                      cudaStream_t, int64_t *, const int64_t *);
+                                      cudaStream_t, int64_t *, const int64_t *, PairWeights);
 INST(float)
 INST(double)
 

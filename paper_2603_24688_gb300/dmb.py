@@ -28,7 +28,7 @@ EXPORTS = ["dmb_create", "dmb_destroy", "dmb_last_error", "dmb_build_grid", "dmb
            "dmb_set_surrogate_engine", "dmb_surrogate_infer_tc", "dmb_autotune", "dmb_set_shapes",
            "dmb_get_shapes", "dmb_rebin_dm", "dmb_set_mc_variant", "dmb_set_anisotropy", "dmb_debug_tc_timeout",
            "dmb_set_cross_section", "dmb_debug_rates_screened", "dmb_save_shapes", "dmb_load_shapes",
-           "dmb_set_surrogate_scope", "dmb_set_fusion", "dmb_set_surrogate_epilogue"]
+           "dmb_set_surrogate_scope", "dmb_set_fusion", "dmb_set_surrogate_epilogue", "dmb_set_pair_weights"]
 
 
 class DmbError(RuntimeError):
@@ -115,6 +115,7 @@ def load(path=LIB_PATH):
         "dmb_set_surrogate_scope": ([vp, c.c_int32], c.c_int),
         "dmb_set_fusion": ([vp, c.c_int32], c.c_int),
         "dmb_set_surrogate_epilogue": ([vp, c.c_int32], c.c_int),
+        "dmb_set_pair_weights": ([vp, c.c_int32], c.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -341,6 +342,10 @@ class Context:
     def dmb_set_fusion(self, on=True):
         """1: one pass evaluates each pair for the mean field and the Monte Carlo; 0: separate passes."""
         self._check(self.lib.dmb_set_fusion(self.h, 1 if on else 0))
+
+    def dmb_set_pair_weights(self, mode):
+        """-1: stored for pair sets kept for later calls (dmb_neighbors); 0: never; 1: always."""
+        self._check(self.lib.dmb_set_pair_weights(self.h, int(mode)))
 
     def dmb_set_surrogate_epilogue(self, mode):
         """1: the surrogate's tensor-core kernel sums the mean field itself; 0: it stores the rates."""
