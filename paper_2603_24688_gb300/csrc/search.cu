@@ -188,8 +188,9 @@ __global__ void k_unit_map(const int64_t *__restrict__ item_ptr, const int64_t *
 }
 
 // ---- stage 2: tiles of (query leaf) x (target leaf) -------------------------------------
-template <typename R, bool EMIT, int GEOM>
-__global__ void __launch_bounds__(SR_WARPS * 32, (EMIT && sizeof(R) == 4 && GEOM != GEOM_BOXES) ? 8 : 1)
+// W: the emit pass also writes the pair weights (float32, with the tile masks)
+template <typename R, bool EMIT, int GEOM, bool W>
+__global__ void __launch_bounds__(SR_WARPS * 32, (W && GEOM != GEOM_BOXES) ? 8 : 0)
 k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict__ frame,
        const uint32_t *__restrict__ unit_leaf, const int64_t *__restrict__ unit_item0,
        const int64_t *__restrict__ item_ptr, const uint32_t *__restrict__ items, int64_t n_units, int unit,
@@ -200,15 +201,6 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
   __shared__ v4 sP[SR_WARPS][DMB_LEAF];
   __shared__ v4 sL[SR_WARPS][DMB_LEAF];
   __shared__ uint16_t sB[SR_WARPS][DMB_LEAF];
-  // emit pass with pair weights: the query leaf's copies, row ends and boxes; per tile every
-  // target's pair mask and claimed target-major range, every query lane's targets, the prefix
-  // of their counts and the lane's row position
-  __shared__ v4 sQP[SR_WARPS][DMB_LEAF];
-  __shared__ v4 sQL[SR_WARPS][DMB_LEAF];
-  __shared__ int64_t sEnd[SR_WARPS][DMB_LEAF], sOut[SR_WARPS][DMB_LEAF];
-  __shared__ uint16_t sQB[SR_WARPS][DMB_LEAF];
-  __shared__ uint32_t sCol[SR_WARPS][DMB_LEAF], sRow[SR_WARPS][DMB_LEAF], sOff[SR_WARPS][DMB_LEAF];
-  __shared__ int64_t sP0[SR_WARPS][DMB_LEAF], sP1[SR_WARPS][DMB_LEAF];
   const int wib = threadIdx.x >> 5;
   const unsigned lane = threadIdx.x & 31u;
   const float pad2 = 2.0f * frame->pad;
@@ -238,7 +230,16 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
       out = row_ptr[qi] + unit_cnt[32 * u + lane];   // unit_cnt holds the exclusive offsets here
       out_end = row_ptr[qi + 1];
     }
-    if (EMIT && tmask != nullptr && sizeof(R) == 4 && pw.q != nullptr) {
+    if constexpr (W) {
+      // the query leaf's copies, row ends and boxes; per tile every target's pair mask and claimed
+      // target-major range, every query lane's targets, the prefix of their counts and the
+      // lane's row position
+      __shared__ v4 sQP[SR_WARPS][DMB_LEAF];
+      __shared__ v4 sQL[SR_WARPS][DMB_LEAF];
+      __shared__ int64_t sEnd[SR_WARPS][DMB_LEAF], sOut[SR_WARPS][DMB_LEAF];
+      __shared__ uint16_t sQB[SR_WARPS][DMB_LEAF];
+      __shared__ uint32_t sCol[SR_WARPS][DMB_LEAF], sRow[SR_WARPS][DMB_LEAF], sOff[SR_WARPS][DMB_LEAF];
+      __shared__ int64_t sP0[SR_WARPS][DMB_LEAF], sP1[SR_WARPS][DMB_LEAF];
       // as below, and each pair's weights.  The tile's pairs are spread evenly over the lanes
       // (pair h of the tile, in query-lane then target order, goes to lane h mod 32): the lane
       // finds the pair's query lane q from the prefix of the per-lane pair counts and its target
@@ -524,9 +525,26 @@ cudaError_t launch_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const F
                         cudaStream_t s, int64_t *launches, const int64_t *n_units_dev, PairWeights pw) {
   if (n_units <= 0) return cudaSuccess;
   const int g = grid_for(n_units);
+#define TLW(G, W_)                                                                                                \
+  k_tile<R, true, G, W_><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items, n_units, \
+                                                     unit, unit_cnt, row_ptr, rows, tr, tmask, status, stats,         \
+                                                     n_units_dev, pw)
+  if constexpr (sizeof(R) == 4) {
+    if (emit && tmask != nullptr && pw.q != nullptr) {
+      switch (geom_of(bx)) {
+        case GEOM_OPEN: TLW(GEOM_OPEN, true); break;
+        case GEOM_BOX: TLW(GEOM_BOX, true); break;
+        default: TLW(GEOM_BOXES, true); break;
+      }
+      if (launches) *launches += 1;
+      return cudaGetLastError();
+    }
+  }
+#undef TLW
 #define TL(E, G)                                                                                                \
-  k_tile<R, E, G><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items, n_units, unit, \
-                                              unit_cnt, row_ptr, rows, tr, tmask, status, stats, n_units_dev, pw)
+  k_tile<R, E, G, false><<<g, SR_WARPS * 32, 0, s>>>(Q, O, bx, frame, unit_leaf, unit_item0, item_ptr, items,     \
+                                                     n_units, unit, unit_cnt, row_ptr, rows, tr, tmask, status,    \
+                                                     stats, n_units_dev, PairWeights())
   switch (geom_of(bx) * 2 + (emit ? 1 : 0)) {
     case 0: TL(false, GEOM_OPEN); break;
     case 1: TL(true, GEOM_OPEN); break;
