@@ -221,6 +221,9 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
     const float qmn[3] = {qa.x, qa.y, qa.z}, qmx[3] = {qb.x, qb.y, qb.z};
     v4 Pq = Vec<R>::make(0, 0, 0, 0), Lq = Vec<R>::make(0, 0, 0, 0);
     if (valid) { Pq = Q.P[qi]; Lq = Q.L[qi]; }
+    // the query's negated hi and lo parts (two-wide distance test of the open geometry)
+    const float2 nq_hxy = make_float2(-(float)Pq.x, -(float)Pq.y), nq_lxy = make_float2(-(float)Lq.x, -(float)Lq.y);
+    const float nq_hz = -(float)Pq.z, nq_lz = -(float)Lq.z;
     const LeafSides ls = leaf_sides<GEOM>(bx, Q.leaf_box, a);
     const BoxSide side_q = (GEOM == GEOM_BOXES && valid) ? box_side<GEOM>(bx, Q.bid[qi]) : ls.a;
     const uint16_t box_q = (boxed && valid) ? Q.bid[qi] : (uint16_t)0;
@@ -389,11 +392,26 @@ k_tile(SpeciesView<R> Q, SpeciesView<R> O, BoxSplit bx, const Frame *__restrict_
       for (unsigned mm = m; mm; mm &= mm - 1) {          // warp-uniform: m is a ballot
         const int k = __ffs(mm) - 1;
         const v4 Pk = sP[wib][k], Lk = sL[wib][k];
-        bool hit = valid && !(boxed && sB[wib][k] != box_q);   // pairs never join two boxes
-        if (hit) {
-          R dx, dy, dz;
-          pair_dx<R>(Pq, Lq, Pk, Lk, GEOM != GEOM_OPEN, side_q, dx, dy, dz);
-          hit = pair_test<R>(dist2_rn<R>(dx, dy, dz), Pq.w, Pk.w);
+        bool hit;
+        if constexpr (GEOM == GEOM_OPEN && sizeof(R) == 4) {
+          // the canonical displacement and squared distance of pair_dx and dist2_rn with the x and
+          // y components on two-wide float32 instructions (each lane of one rounds as the scalar
+          // form does); the target minus the query is the exact negation of pair_dx's query
+          // minus target, so the squares, and the predicate, are the same bits
+          const float2 hxy = __fadd2_rn(make_float2((float)Pk.x, (float)Pk.y), nq_hxy);
+          const float2 lxy = __fadd2_rn(make_float2((float)Lk.x, (float)Lk.y), nq_lxy);
+          const float2 dxy = __fadd2_rn(hxy, lxy);
+          const float dz = __fadd_rn(__fadd_rn((float)Pk.z, nq_hz), __fadd_rn((float)Lk.z, nq_lz));
+          const float2 sq = __fmul2_rn(dxy, dxy);
+          const float d2 = __fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(dz, dz));
+          hit = valid && pair_test<float>(d2, (float)Pq.w, (float)Pk.w);
+        } else {
+          hit = valid && !(boxed && sB[wib][k] != box_q);   // pairs never join two boxes
+          if (hit) {
+            R dx, dy, dz;
+            pair_dx<R>(Pq, Lq, Pk, Lk, GEOM != GEOM_OPEN, side_q, dx, dy, dz);
+            hit = pair_test<R>(dist2_rn<R>(dx, dy, dz), Pq.w, Pk.w);
+          }
         }
         if (hit) {
           if (EMIT) {
