@@ -333,6 +333,31 @@ def envelope(n):
     return of(-(n + 1) / 2.0, 2.5), of(-(n + 3) / 2.0, 1.5)
 
 
+def bind_to_gpu_numa_node(dev):
+    """Bind this process to the CPUs of the NUMA node the GPU hangs off (sysfs), so that host
+    memory it allocates from now on (first touch) is local to the GPU; returns the node or None."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (getattr(p, "pci_domain_id", 0), p.pci_bus_id, p.pci_device_id)
+        with open(f"/sys/bus/pci/devices/{bus}/numa_node") as f:
+            node = int(f.read().strip())
+        if node < 0:
+            return None
+        with open(f"/sys/devices/system/node/node{node}/cpulist") as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return node
+    except (AttributeError, OSError, ValueError):
+        return None
+
+
 def workload_tau(w):
     """(min, max) of tau = varsigma^2 / v0^2 over the workload's hot gas, varsigma^2 = k_B T / (mu m_p)."""
     kt = 1.380649e-16 / 1.67262192e-24 / 1e10                  # k_B / m_p in (km/s)^2 / K
@@ -896,6 +921,10 @@ def main():
     # stream while step k runs, and step k's results come back while step k+1 runs.
     e2e = None
     if a.e2e_steps > 0:
+        # the pinned host buffers on the GPU's own NUMA node (first touch by a thread bound to its
+        # CPUs), so that the copies do not cross between host sockets
+        cpus_before = os.sched_getaffinity(0)
+        numa_node = bind_to_gpu_numa_node(torch.cuda.current_device())
         host = {}
         for sp, src in (("dm", dm), ("gas", gas)):
             host[sp] = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in src.items()}
@@ -966,7 +995,9 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "pipelined": "inputs of step k+1 copied while step k runs; results of step k copied while step k+1 runs",
                "ms_per_step": ms_e / a.e2e_steps,
-               "h2d_ms_alone": c0.elapsed_time(c1), "d2h_ms_alone": c1.elapsed_time(c2)}
+               "h2d_ms_alone": c0.elapsed_time(c1), "d2h_ms_alone": c1.elapsed_time(c2),
+               "host_numa_node": numa_node}
+        os.sched_setaffinity(0, cpus_before)      # the CPU baseline below uses every host core
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
