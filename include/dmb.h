@@ -147,7 +147,7 @@ dmb_status dmb_mc_scatter_dm(dmb_ctx *ctx, uint64_t step, double dt, double *vel
 dmb_status dmb_step(dmb_ctx *ctx, const dmb_dm *dm, const dmb_gas *gas, uint64_t step,
                     double dt, double *sums_out);
 
-/* Parameters of one box of a batched step (the per-box values of the survey's parameter
+/* Parameters of one box of a batched step (the values that vary from box to box in a parameter
  * scan; the power law n, v0, seed and precision are the context's). */
 typedef struct {
   double box[3];        /* periodic sides, kpc */
