@@ -354,8 +354,8 @@ def bind_to_gpu_numa_node(dev):
             return None
         os.sched_setaffinity(0, cpus)
         return node
-    except (AttributeError, OSError, ValueError):
-        return None
+    except (AttributeError, OSError, ValueError, RuntimeError, AssertionError):
+        return None                      # no device, no sysfs entry or no per-node CPU list
 
 
 def workload_tau(w):
