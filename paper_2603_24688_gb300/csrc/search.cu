@@ -10,7 +10,9 @@
 // target row then follows the tiles' completion; the Monte Carlo, which reads those rows, sums
 // them exactly in fixed point and selects partners by gas id, so no result depends on it.
 // The count pass keeps every tile's 32 x 32 pair mask (128 bytes per candidate leaf pair); the
-// emit pass reads the masks and writes both lists without testing a distance again.
+// emit pass reads the masks and writes both lists without testing a distance again.  A float32
+// emit pass can also form every pair's overlap g_ij and store it beside both lists (PairWeights),
+// for pair sets that serve many interaction passes.
 #include "pairs.cuh"
 #include "physics.cuh"
 
