@@ -120,6 +120,22 @@ def test_substeps_with_and_without_weights():
             assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("kw", [dict(beta=0.6), dict(rate=dmb.DMB_RATE_QUAD, screened=60.0)])
+def test_steps_with_weights_under_other_laws(kw):
+    # anisotropic angles and the screened velocity law act on the pair's probability and kick,
+    # not on g_ij: the stored weights serve them unchanged
+    w = W.box_workload(n_dm=3000, n_gas=2500, seed=75, n=-2)
+    runs = []
+    for mode in (1, 0):
+        c = _ctx(w, mode, kw.get("rate", dmb.DMB_RATE_CLOSED))
+        if "beta" in kw:
+            c.dmb_set_anisotropy(kw["beta"])
+        if "screened" in kw:
+            c.dmb_set_cross_section(1, kw["screened"])
+        runs.append(_steps(c, w, 2, w["dt"] * 50.0))
+    _same(runs[0], runs[1])
+
+
 def test_mode_argument_checked():
     c = _ctx(W.named("box4k"), -1)
     with pytest.raises(dmb.DmbError):
